@@ -1,0 +1,138 @@
+"""Geometric multigrid with the patch smoother, and preconditioned CG (oracle).
+
+Test infrastructure only.
+
+* Mesh hierarchy M_1 c ... c M_L (Section 2): every level is the unit
+  square/cube with N_l = N_c * 2^(l-1) cells per direction.  The vertices of
+  a coarser level are the fine-level vertices with even indices (topological
+  nestedness; the coarse cells are the multilinear images of those vertices).
+  The coefficient of a coarse cell is the arithmetic mean of its 2^d children.
+* Transfers: prolongation is the embedding through the reference cells
+  (a fine node's value is the coarse cell's function at the fine node's
+  position in the coarse reference cell); restriction is its transpose
+  (Section 2).
+* V-cycle: one multiplicative patch-smoother sweep before (colours in
+  increasing order) and one after (colours reversed, so that the V-cycle is
+  symmetric and can precondition CG), coarse problem solved by a dense
+  Cholesky factorisation.
+* Outer solver: preconditioned CG from u = 0, stopping when
+  ||r_k||_2 <= rtol ||r_0||_2.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from . import fem, patch as pt, rules
+
+
+def coarsen(mesh: fem.StructuredMesh) -> fem.StructuredMesh:
+    d, N = mesh.dim, mesh.N
+    assert N % 2 == 0
+    Nc = N // 2
+    X = mesh.coords.reshape(*([N + 1] * d), d)          # reversed axes: [z][y][x] or [y][x]
+    sl = tuple([slice(None, None, 2)] * d)
+    Xc = X[sl].reshape(-1, d)
+    kap = mesh.kappa.reshape(*([N] * d))
+    kc = np.zeros([Nc] * d)
+    for off in fem._lex(d, 2):
+        idx = tuple(slice(off[d - 1 - a], None, 2) for a in range(d))   # array axes are reversed
+        kc += kap[idx]
+    kc /= 2 ** d
+    return fem.StructuredMesh(d, Nc, Xc, kc.reshape(-1))
+
+
+def hierarchy(mesh: fem.StructuredMesh, coarse_N: int):
+    out = [mesh]
+    while out[-1].N > coarse_N:
+        out.append(coarsen(out[-1]))
+    assert out[-1].N == coarse_N
+    return out[::-1]                     # coarsest first
+
+
+def prolongation(coarse: fem.StructuredMesh, fine: fem.StructuredMesh, q: int) -> sp.csr_matrix:
+    """Embedding V_coarse -> V_fine on all nodes (reference-cell embedding)."""
+    d = fine.dim
+    gl = rules.gauss_lobatto_nodes(q)
+    rows, cols, vals = [], [], []
+    for nf in range(fine.n_nodes(q)):
+        m = fine.node_multi(q, nf)
+        fc = [min(m[a] // q, fine.N - 1) for a in range(d)]          # a fine cell holding the node
+        cc = [fc[a] // 2 for a in range(d)]                           # its parent
+        xi = [(fc[a] % 2 + gl[m[a] - q * fc[a]]) / 2.0 for a in range(d)]
+        for loc in fem._lex(d, q + 1):
+            val = 1.0
+            for a in range(d):
+                val *= rules.lagrange(gl, xi[a])[0, loc[a]]
+            if abs(val) > 0.0:
+                rows.append(nf)
+                cols.append(coarse.node_index(q, [q * cc[a] + loc[a] for a in range(d)]))
+                vals.append(val)
+    return sp.coo_matrix((vals, (rows, cols)), shape=(fine.n_nodes(q), coarse.n_nodes(q))).tocsr()
+
+
+class GMG:
+    def __init__(self, fine: fem.StructuredMesh, p: int, coarse_N: int, smoother_args=None):
+        self.p = p
+        self.meshes = hierarchy(fine, coarse_N)
+        self.free = [m.free_mask(p) for m in self.meshes]
+        self.A = []
+        for m, f in zip(self.meshes, self.free):
+            self.A.append(fem.operator_with_dirichlet(m.assemble(p), f))
+        self.P = []
+        for l in range(1, len(self.meshes)):
+            Pm = prolongation(self.meshes[l - 1], self.meshes[l], p)
+            Df = sp.diags(self.free[l].astype(float))
+            Dc = sp.diags(self.free[l - 1].astype(float))
+            self.P.append((Df @ Pm @ Dc).tocsr())
+        sa = {} if smoother_args is None else smoother_args
+        self.smoothers = [None] + [pt.PatchSmoother(m, p, **sa) for m in self.meshes[1:]]
+        f0 = self.free[0]
+        Ac = self.A[0].toarray()[np.ix_(f0, f0)]
+        self.chol = sla.cho_factor(Ac, lower=True)
+
+    def coarse_solve(self, b):
+        x = np.zeros_like(b)
+        f0 = self.free[0]
+        x[f0] = sla.cho_solve(self.chol, b[f0])
+        return x
+
+    def vcycle(self, b, l=None):
+        l = len(self.meshes) - 1 if l is None else l
+        if l == 0:
+            return self.coarse_solve(b)
+        S = self.smoothers[l]
+        x = S.sweep(np.zeros_like(b), b, reverse=False)
+        r = b - self.A[l] @ x
+        e = self.vcycle(self.P[l - 1].T @ r, l - 1)
+        x = x + self.P[l - 1] @ e
+        x = S.sweep(x, b, reverse=True)
+        return x
+
+
+def pcg(A, b, M, rtol=1e-8, maxit=200):
+    """Preconditioned CG from x = 0; returns (x, iterations, relres history)."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    r0 = np.linalg.norm(r)
+    hist = [1.0]
+    if r0 == 0.0:
+        return x, 0, hist
+    z = M(r)
+    p = z.copy()
+    rz = r @ z
+    for it in range(1, maxit + 1):
+        Ap = A @ p
+        alpha = rz / (p @ Ap)
+        x = x + alpha * p
+        r = r - alpha * Ap
+        rel = np.linalg.norm(r) / r0
+        hist.append(rel)
+        if rel <= rtol:
+            return x, it, hist
+        z = M(r)
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, maxit, hist

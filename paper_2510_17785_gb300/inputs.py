@@ -1,0 +1,164 @@
+"""Seeded synthetic inputs for the patch-smoother workloads.
+
+This module is shared by the CUDA path's tests and benchmark and by the CPU
+oracle's tests.  It holds none of the method's arithmetic: it only produces
+vertex coordinates of structured hexahedral/quadrilateral meshes of the unit
+square/cube (with seeded vertex perturbations), per-cell coefficients and
+right-hand-side vectors in the global lexicographic DoF layout.
+
+Layouts (all lexicographic, x fastest):
+  * vertices: ``(N+1)**dim`` rows of ``dim`` coordinates;
+  * cells:    ``N**dim`` entries;
+  * DoFs:     ``(p*N+1)**dim`` entries (Dirichlet DoFs included, set to 0).
+
+The workloads follow the paper's test problems (Section 4: unit square/cube
+refined uniformly, interior vertices displaced; Section 3.3: coefficient
+jumps) with the sizes of the five benchmark configurations.  One
+``numpy.random.default_rng(seed)`` stream draws, in this order: vertex
+perturbation, coefficient, right-hand side.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Optional
+
+import numpy as np
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    """One synthetic problem: mesh size, degree, perturbation, coefficient, RHS."""
+    name: str
+    dim: int
+    N: int                 # cells per direction on the finest mesh
+    p: int                 # polynomial degree
+    perturb: float         # vertex displacement as a fraction of h = 1/N
+    law: str               # "uniform": each component U(-perturb*h, perturb*h);
+                           # "sphere": length perturb*h, direction uniform on S^{d-1}
+    kappa: tuple           # ("const", value) or ("loguniform", log10_lo, log10_hi)
+    rhs: str               # "uniform" (U[-1,1] on free DoFs) or "manufactured"
+    seed: int
+    coarse_N: int = 2      # cells per direction on the coarsest h-level
+
+    @property
+    def n_dofs(self) -> int:
+        return (self.p * self.N + 1) ** self.dim
+
+    @property
+    def n_free(self) -> int:
+        return (self.p * self.N - 1) ** self.dim
+
+    @property
+    def n_patches(self) -> int:
+        return (self.N - 1) ** self.dim
+
+    def with_(self, **kw) -> "Workload":
+        return dataclasses.replace(self, **kw)
+
+
+# The five benchmark workloads (seed 1000 + index).
+C1 = Workload("c1_2d_q4_n16", 2, 16, 4, 0.0, "uniform", ("const", 1.0), "uniform", 1001)
+C2 = Workload("c2_3d_q4_n32_perturbed", 3, 32, 4, 0.25, "uniform", ("const", 1.0),
+              "manufactured", 1002, coarse_N=2)
+C3 = Workload("c3_3d_q7_n48_varcoef", 3, 48, 7, 0.25, "uniform", ("loguniform", -3.0, 3.0),
+              "uniform", 1003, coarse_N=3)
+C5 = Workload("c5_3d_q8_n64_varcoef", 3, 64, 8, 0.25, "uniform", ("loguniform", -2.0, 2.0),
+              "uniform", 1005, coarse_N=2)
+WORKLOADS = {w.name: w for w in (C1, C2, C3, C5)}
+
+
+def grid_vertices(dim: int, N: int) -> np.ndarray:
+    """Unperturbed vertices of the N^dim grid on the unit square/cube."""
+    t = np.arange(N + 1, dtype=np.float64) / N
+    axes = np.meshgrid(*([t] * dim), indexing="ij")  # axes[k] varies along index k
+    # lexicographic with x fastest: reverse the 'ij' order
+    cols = [axes[dim - 1 - k].reshape(-1) for k in range(dim)]
+    # axes[0] is the slowest index; for x fastest, x must come from the last axis
+    return np.stack(cols, axis=1).copy()
+
+
+def interior_vertex_mask(dim: int, N: int) -> np.ndarray:
+    idx = np.indices((N + 1,) * dim).reshape(dim, -1)  # idx[0] slowest
+    inner = np.all((idx > 0) & (idx < N), axis=0)
+    return inner
+
+
+def perturbation(rng: np.random.Generator, dim: int, N: int, frac: float, law: str) -> np.ndarray:
+    """Displacements of all vertices (zero on the boundary)."""
+    nv = (N + 1) ** dim
+    h = 1.0 / N
+    if law == "uniform":
+        disp = rng.uniform(-frac * h, frac * h, size=(nv, dim))
+    elif law == "sphere":
+        g = rng.standard_normal(size=(nv, dim))
+        g /= np.linalg.norm(g, axis=1, keepdims=True)
+        disp = frac * h * g
+    else:
+        raise ValueError(law)
+    disp[~interior_vertex_mask(dim, N)] = 0.0
+    return disp
+
+
+def kappa_cells(rng: np.random.Generator, dim: int, N: int, spec: tuple) -> np.ndarray:
+    nc = N ** dim
+    if spec[0] == "const":
+        return np.full(nc, float(spec[1]))
+    if spec[0] == "loguniform":
+        return 10.0 ** rng.uniform(spec[1], spec[2], size=nc)
+    raise ValueError(spec)
+
+
+def free_dof_mask(dim: int, p: int, N: int) -> np.ndarray:
+    M = p * N + 1
+    idx = np.indices((M,) * dim).reshape(dim, -1)
+    return np.all((idx > 0) & (idx < M - 1), axis=0)
+
+
+def rhs_uniform(rng: np.random.Generator, dim: int, p: int, N: int) -> np.ndarray:
+    b = rng.uniform(-1.0, 1.0, size=(p * N + 1) ** dim)
+    b[~free_dof_mask(dim, p, N)] = 0.0
+    return b
+
+
+@dataclasses.dataclass
+class Problem:
+    workload: Workload
+    coords: np.ndarray          # ((N+1)^d, d) float64
+    kappa: np.ndarray           # (N^d,) float64
+    rhs: Optional[np.ndarray]   # ((pN+1)^d,) float64, or None for "manufactured"
+
+
+def make_problem(w: Workload) -> Problem:
+    rng = np.random.default_rng(w.seed)
+    x = grid_vertices(w.dim, w.N)
+    if w.perturb > 0.0:
+        x = x + perturbation(rng, w.dim, w.N, w.perturb, w.law)
+    kap = kappa_cells(rng, w.dim, w.N, w.kappa)
+    b = rhs_uniform(rng, w.dim, w.p, w.N) if w.rhs == "uniform" else None
+    return Problem(w, x, kap, b)
+
+
+def random_vector(seed: int, dim: int, p: int, N: int, free_only: bool = True) -> np.ndarray:
+    """A seeded U[-1,1] vector in the DoF layout (zero on Dirichlet DoFs)."""
+    rng = np.random.default_rng(seed)
+    v = rng.uniform(-1.0, 1.0, size=(p * N + 1) ** dim)
+    if free_only:
+        v[~free_dof_mask(dim, p, N)] = 0.0
+    return v
+
+
+def sample_patches(seed: int, n_patches: int, k: int) -> np.ndarray:
+    """k distinct patch ids drawn without replacement (sorted)."""
+    rng = np.random.default_rng(seed)
+    k = min(k, n_patches)
+    return np.sort(rng.choice(n_patches, size=k, replace=False)).astype(np.int64)
+
+
+def single_patch_vertices(dim: int, delta: float, direction: np.ndarray) -> np.ndarray:
+    """Vertices of a 2^d-cell patch of unit cells ([0,2]^d) with the centre vertex moved
+    by delta * (patch width 2) along ``direction`` (normalised here)."""
+    x = grid_vertices(dim, 2) * 2.0
+    c = (3 ** dim) // 2
+    u = np.asarray(direction, dtype=np.float64)
+    x[c] += delta * 2.0 * u / np.linalg.norm(u)
+    return x

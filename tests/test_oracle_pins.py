@@ -1,0 +1,480 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+No GPU.  Each test checks the oracle against something other than itself:
+closed forms, library routines for special cases, invariants, brute force on
+tiny inputs, or numbers printed in the paper (tests/golden/).
+"""
+import math
+import os
+
+import numpy as np
+import numpy.polynomial.chebyshev as npcheb
+import numpy.polynomial.legendre as npleg
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import fem, gmg, lanczos as lz, patch as pt, rules
+from paper_2510_17785_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- 1D rules
+@pytest.mark.parametrize("n", range(1, 12))
+def test_gauss_rule_exactness(n):
+    x, w = rules.gauss(n)
+    assert abs(w.sum() - 1.0) < 1e-14
+    for k in range(2 * n):
+        assert abs((w * x ** k).sum() - 1.0 / (k + 1)) < 1e-14
+    # not exact one degree higher: it really is the n-point rule
+    ref = 0.5 ** (2 * n) / (2 * n + 1)
+    assert abs((w * (x - 0.5) ** (2 * n)).sum() - ref) > 1e-6 * ref
+
+
+@pytest.mark.parametrize("q", range(1, 16))
+def test_gauss_lobatto_nodes_are_roots_of_dP(q):
+    x = rules.gauss_lobatto_nodes(q)
+    assert x[0] == 0.0 and x[-1] == 1.0
+    assert np.all(np.diff(x) > 0)
+    assert np.allclose(x, 1.0 - x[::-1], atol=1e-15)
+    if q >= 2:
+        c = np.zeros(q + 1)
+        c[q] = 1.0
+        ref = np.sort(np.real(npleg.legroots(npleg.legder(c))))
+        assert np.allclose(2.0 * x[1:-1] - 1.0, ref, atol=1e-13)
+
+
+@pytest.mark.parametrize("q", [1, 2, 4, 7, 8])
+def test_lagrange_values_and_derivatives(q):
+    nodes = rules.gauss_lobatto_nodes(q)
+    assert np.allclose(rules.lagrange(nodes, nodes), np.eye(q + 1), atol=1e-13)
+    xs = np.linspace(0.03, 0.97, 9)
+    D = rules.lagrange_deriv(nodes, xs)
+    for j in range(q + 1):
+        poly = np.polynomial.Polynomial.fit(nodes, np.eye(q + 1)[j], q, domain=[0, 1], window=[0, 1])
+        assert np.allclose(D[:, j], poly.deriv()(xs), atol=1e-8 * 10 ** (q / 2))
+        assert np.allclose(rules.lagrange(nodes, xs)[:, j], poly(xs), atol=1e-9 * 10 ** (q / 2))
+
+
+# ---------------------------------------------------------- element matrices
+def test_q1_closed_forms():
+    X2 = np.array([[0, 0], [1, 0], [0, 1], [1, 1.0]])
+    K2 = np.array([[4, -1, -1, -2], [-1, 4, -2, -1], [-1, -2, 4, -1], [-2, -1, -1, 4]]) / 6.0
+    assert np.allclose(fem.element_matrix(X2, 1.0, 1), K2, atol=1e-15)
+    X3 = np.array([[(v >> k) & 1 for k in range(3)] for v in range(8)], dtype=float)
+    K3 = fem.element_matrix(X3, 1.0, 1)
+    for a in range(8):
+        for b in range(8):
+            hd = bin(a ^ b).count("1")
+            ref = {0: 1 / 3, 1: 0.0, 2: -1 / 12, 3: -1 / 12}[hd]
+            assert abs(K3[a, b] - ref) < 1e-15
+
+
+def _random_cell(dim, seed, amp=0.15):
+    rng = np.random.default_rng(seed)
+    X = np.array([[(v >> k) & 1 for k in range(dim)] for v in range(2 ** dim)], dtype=float)
+    return X + rng.uniform(-amp, amp, size=X.shape)
+
+
+def _shoelace(X):
+    # bilinear quad vertices in lexicographic order -> counter-clockwise polygon 0,1,3,2
+    P = X[[0, 1, 3, 2]]
+    return 0.5 * abs(np.dot(P[:, 0], np.roll(P[:, 1], -1)) - np.dot(P[:, 1], np.roll(P[:, 0], -1)))
+
+
+@pytest.mark.parametrize("dim,q", [(2, 1), (2, 3), (2, 5), (3, 1), (3, 2), (3, 4)])
+def test_element_matrix_invariants(dim, q):
+    X = _random_cell(dim, 7 * q + dim)
+    kap = 2.5
+    A = fem.element_matrix(X, kap, q)
+    assert np.allclose(A, A.T, atol=1e-13 * np.abs(A).max())
+    assert np.abs(A @ np.ones(len(A))).max() < 1e-12 * np.abs(A).max()     # constants in the kernel
+    ev = np.linalg.eigvalsh(A)
+    assert ev[0] > -1e-12 * ev[-1] and ev[1] > 1e-8 * ev[-1]                # PSD, one-dim kernel
+    # energy of a physically linear function u = a . x: kappa |a|^2 |cell| exactly
+    # (u is multilinear in the reference coordinates, so it lies in Q_q; the integrand
+    # is det J, integrated exactly by the (q+1)-point Gauss rule)
+    gl = rules.gauss_lobatto_nodes(q)
+    ref_nodes = np.array([[gl[i[k]] for k in range(dim)] for i in fem._lex(dim, q + 1)])
+    Nq, _ = fem.q1_shape(dim, ref_nodes)
+    xn = Nq @ X
+    a = np.arange(1, dim + 1, dtype=float)
+    u = xn @ a
+    if dim == 2:
+        vol = _shoelace(X)
+    else:
+        pts, wts = fem.tensor_rule(3, 6)
+        vol = np.sum(wts * np.linalg.det(fem.jacobians(X, pts)))
+    assert abs(u @ A @ u - kap * (a @ a) * vol) < 1e-12 * kap * (a @ a)
+
+
+def test_element_matrix_rigid_motion_and_scaling():
+    X = _random_cell(3, 3)
+    A = fem.element_matrix(X, 1.0, 3)
+    th = 0.7
+    R = np.array([[np.cos(th), -np.sin(th), 0], [np.sin(th), np.cos(th), 0], [0, 0, 1.0]])
+    Xr = X @ R.T + np.array([3.0, -1.0, 2.0])
+    assert np.allclose(fem.element_matrix(Xr, 1.0, 3), A, atol=1e-12)
+    assert np.allclose(fem.element_matrix(0.25 * X, 1.0, 3), 0.25 * A, atol=1e-12)   # h^(d-2)
+
+
+# ----------------------------------------------------------------- meshes
+def _read_golden(name):
+    rows = []
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            rows.append(line.split())
+    return rows
+
+
+def _fmt3(n):
+    """Three significant digits with k / M suffixes, as printed in the tables:
+    both the rounded and the truncated display (the Kershaw 2D column of the
+    paper truncates, e.g. 37^2 = 1369 is printed 1.36k; the others round)."""
+    for div, suf in ((1e6, "M"), (1e3, "k")):
+        if n >= div:
+            v = n / div
+            digits = max(3 - len(str(int(v))), 0)
+            scale = 10 ** digits
+            trunc = math.floor(v * scale) / scale
+            return {f"{v:.{digits}f}{suf}", f"{trunc:.{digits}f}{suf}"}
+    return {str(n)}
+
+
+def test_dof_counts_match_paper_tables():
+    for dim, p, L, printed in _read_golden("dof_counts_cartesian.txt"):
+        dim, p, L = int(dim), int(p), int(L)
+        N = 2 ** L
+        m = fem.StructuredMesh(dim, N, inputs.grid_vertices(dim, N), np.ones(N ** dim))
+        assert printed in _fmt3(m.n_nodes(p)), (dim, p, L)
+    for dim, p, L, printed in _read_golden("dof_counts_kershaw.txt"):
+        dim, p, L = int(dim), int(p), int(L)
+        assert printed in _fmt3((p * 3 * 2 ** L + 1) ** dim), (dim, p, L)
+
+
+@pytest.mark.parametrize("dim,thr", [(2, math.sqrt(2) / 4), (3, math.sqrt(3) / 6)])
+def test_degeneracy_threshold(dim, thr):
+    """Section 3.2: a Cartesian patch degenerates when the centre vertex moves by
+    more than (1/2)(sqrt(2)/2) resp. (1/2)(sqrt(3)/3) of the patch width."""
+    direction = np.ones(dim)
+    for factor, ok in ((1 - 1e-6, True), (1 + 1e-6, False)):
+        X = inputs.single_patch_vertices(dim, thr * factor, direction)
+        m = fem.StructuredMesh(dim, 2, X, np.ones(2 ** dim))
+        dets = np.concatenate([fem.corner_dets(m.cell_vertices(m.cell_multi(c))) for c in range(m.n_cells)])
+        assert (dets.min() > 0) == ok
+
+
+# ------------------------------------------------------------------ patches
+def _mesh(dim, N, perturb, seed, kappa=("const", 1.0)):
+    w = inputs.Workload("t", dim, N, 1, perturb, "uniform", kappa, "uniform", seed)
+    pr = inputs.make_problem(w)
+    return fem.StructuredMesh(dim, N, pr.coords, pr.kappa)
+
+
+@pytest.mark.parametrize("dim,N,q,v", [(2, 4, 3, (1, 2)), (2, 4, 2, (3, 3)), (3, 3, 2, (1, 2, 1))])
+def test_patch_matrix_is_principal_submatrix(dim, N, q, v):
+    m = _mesh(dim, N, 0.2, 11, ("loguniform", -1, 1))
+    Ag = m.assemble(q).toarray()
+    P = pt.Patch(m, v, [q])
+    lv = P.lv[q]
+    assert len(lv.interior) == (2 * q - 1) ** dim and len(lv.closure) == (2 * q + 1) ** dim
+    assert np.allclose(lv.A, Ag[np.ix_(lv.interior, lv.interior)], atol=1e-13)
+    assert np.allclose(lv.A_ic, Ag[np.ix_(lv.interior, lv.closure)], atol=1e-13)
+    # Evaluate (eq. main:4) is the global residual restricted to the patch interior
+    rng = np.random.default_rng(1)
+    u, b = rng.uniform(-1, 1, m.n_nodes(q)), rng.uniform(-1, 1, m.n_nodes(q))
+    assert np.allclose(P.residual(u, b), (b - Ag @ u)[lv.interior], atol=1e-12)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_coarse_scalar_is_q1_vertex_diagonal(dim):
+    """Section 3.1, coarse solver: A_{j,1} is the Q1 diagonal entry at the vertex;
+    8/3 * h^(d-2) on a Cartesian patch with kappa = 1."""
+    N = 4
+    m = _mesh(dim, N, 0.0, 0)
+    P = pt.Patch(m, (2,) * dim, [2, 1])
+    h = 1.0 / N
+    assert abs(P.lv[1].A[0, 0] - 8.0 / 3.0 * h ** (dim - 2)) < 1e-14
+    mp = _mesh(dim, N, 0.2, 5)
+    Pp = pt.Patch(mp, (2,) * dim, [2, 1])
+    Ag = mp.assemble(1).toarray()
+    c = mp.node_index(1, (2,) * dim)
+    assert abs(Pp.lv[1].A[0, 0] - Ag[c, c]) < 1e-14
+
+
+@pytest.mark.parametrize("dim,qc,qf", [(2, 1, 2), (2, 2, 4), (2, 3, 7), (3, 2, 4), (3, 1, 2)])
+def test_p_embedding_exact_on_polynomials(dim, qc, qf):
+    """Section 3.1, transfer operators: the prolongation is the embedding, so it
+    maps the nodal values of a coarse-space function to its fine nodal values."""
+    N = 2
+    m = _mesh(dim, N, 0.0, 0)
+    P = pt.Patch(m, (1,) * dim, [qf, qc])
+    Pm = P.P[(qc, qf)]
+    Xc = m.node_coords(qc)[P.lv[qc].interior]
+    Xf = m.node_coords(qf)[P.lv[qf].interior]
+    if qc == 1:
+        f = lambda X: np.prod(1.0 - np.abs(2.0 * X - 1.0), axis=1)         # the hat function
+    else:
+        f = lambda X: np.prod(X * (1.0 - X) * (1.0 + X), axis=1) if qc >= 3 else np.prod(X * (1.0 - X), axis=1)
+    assert np.allclose(Pm @ f(Xc), f(Xf), atol=1e-14)
+
+
+@pytest.mark.parametrize("dim,p", [(2, 4), (2, 7), (3, 4)])
+def test_galerkin_identity_on_affine_patches(dim, p):
+    """Section 3.1, level operators: with exact quadrature (affine cells, constant
+    coefficient per cell) re-evaluation with the coarse basis equals the Galerkin
+    product R A P."""
+    m = _mesh(dim, 2, 0.0, 0)
+    S = np.eye(dim) + 0.3 * np.triu(np.ones((dim, dim)), 1)       # a shear keeps cells affine
+    m.coords = m.coords @ S.T
+    m.kappa = np.array([1.0, 7.0, 0.5, 3.0, 2.0, 1.0, 4.0, 0.25][: 2 ** dim])
+    levels = pt.levels_halving(p)
+    P = pt.Patch(m, (1,) * dim, levels)
+    for qc, qf in zip(levels[1:], levels[:-1]):
+        Pm = P.P[(qc, qf)]
+        G = Pm.T @ P.lv[qf].A @ Pm
+        assert np.allclose(G, P.lv[qc].A, atol=1e-12 * np.abs(G).max())
+    # trilinear distortion: quadrature no longer exact, the identity breaks
+    md = _mesh(dim, 2, 0.2, 3)
+    Pd = pt.Patch(md, (1,) * dim, levels)
+    Pm = Pd.P[(levels[1], levels[0])]
+    assert np.abs(Pm.T @ Pd.lv[levels[0]].A @ Pm - Pd.lv[levels[1]].A).max() > 1e-8
+
+
+# ---------------------------------------------------------------- smoothers
+def test_chebyshev_error_polynomial():
+    """Degree-k Chebyshev from zero: I - S_k A has eigenvalues
+    T_k((theta - lam)/delta) / T_k(theta/delta) on the eigenvectors of D^-1 A."""
+    m = _mesh(2, 2, 0.2, 4)
+    P = pt.Patch(m, (1, 1), [4])
+    lv = P.lv[4]
+    n = len(lv.diag)
+    lo, hi = 0.3, 2.2
+    for k in (1, 2, 3, 5):
+        S = np.column_stack([pt.chebyshev(lv.A, lv.diag, e, np.zeros(n), lo, hi, k, zero_start=True)
+                             for e in np.eye(n)])
+        E = np.eye(n) - S @ lv.A
+        lam, V = np.linalg.eig(np.diag(1.0 / lv.diag) @ lv.A)
+        lam = np.real(lam)
+        theta, delta = 0.5 * (hi + lo), 0.5 * (hi - lo)
+        Tk = np.zeros(k + 1)
+        Tk[k] = 1.0
+        ref = npcheb.chebval((theta - lam) / delta, Tk) / npcheb.chebval(theta / delta, Tk)
+        got = np.real(np.linalg.solve(V, E @ V))
+        assert np.allclose(got, np.diag(ref), atol=1e-10)
+        # the non-zero start applies the same polynomial to the error
+        d0 = np.linspace(-1, 1, n)
+        r = np.sin(np.arange(n))
+        d1 = pt.chebyshev(lv.A, lv.diag, r, d0, lo, hi, k)
+        x = np.linalg.solve(lv.A, r)
+        assert np.allclose(x - d1, E @ (x - d0), atol=1e-10)
+
+
+def test_chebyshev_degree1_is_damped_jacobi():
+    m = _mesh(2, 2, 0.1, 4)
+    lv = pt.Patch(m, (1, 1), [3]).lv[3]
+    r = np.cos(np.arange(len(lv.diag)))
+    d0 = 0.1 * np.ones(len(r))
+    lo, hi = 0.25, 1.9
+    a = pt.chebyshev(lv.A, lv.diag, r, d0, lo, hi, 1)
+    b = pt.jacobi(lv.A, lv.diag, r, d0, 2.0 / (lo + hi), 1)
+    assert np.allclose(a, b, atol=1e-15)
+
+
+@pytest.mark.parametrize("dim,p,kind", [(2, 4, "chebyshev"), (2, 4, "jacobi"), (2, 7, "chebyshev"),
+                                        (3, 4, "chebyshev"), (3, 2, "jacobi")])
+def test_vcycle_symmetric_contractive_and_exact_limit(dim, p, kind):
+    """Algorithm 2 with equal pre/post smoothers is a symmetric operator; it
+    contracts the error in the A-norm; 25 cycles solve the patch problem
+    (the paper's 'nearly exact' N_MG = 25, Section 4)."""
+    m = _mesh(dim, 2, 0.25, 9, ("loguniform", -1, 1))
+    levels = pt.levels_halving(p)
+    P = pt.Patch(m, (1,) * dim, levels)
+    sm = pt.Smoother(kind=kind)
+    bounds = lz.exact_bounds_fn()(P, 0)
+    A = P.lv[p].A
+    B = pt.vcycle_matrix(P, sm, bounds)
+    assert np.abs(B - B.T).max() < 1e-12 * np.abs(B).max()
+    ev = np.linalg.eigvals(np.eye(len(A)) - B @ A)
+    rho = np.abs(ev).max()
+    assert rho < 0.9
+    rng = np.random.default_rng(2)
+    r = rng.uniform(-1, 1, len(A))
+    x = np.linalg.solve(A, r)
+    anorm = lambda v: math.sqrt(v @ A @ v)
+    # E = I - B A is self-adjoint in the A inner product, so N cycles from zero
+    # reduce the A-norm error by at most rho^N
+    for n in (2, 5, 25):
+        d = pt.local_solve(P, r, sm, bounds, n_cycles=n)
+        assert anorm(x - d) <= (rho ** n * (1 + 1e-8) + 1e-13) * anorm(x)
+    assert anorm(x - d) < 1e-6 * anorm(x)
+
+
+def test_single_patch_iterations_loose_paper_pin():
+    """Section 3.2 (text of fig:iter_vs_p_Jacobi_cartesian): CG with one Jacobi
+    p-MG V-cycle on an undeformed 2D Cartesian patch takes about 10 iterations
+    at p = 3.  A loose check: within +-3 of the printed value."""
+    rows = _read_golden("single_patch_iterations.txt")
+    for dim, p, approx in rows:
+        dim, p, approx = int(dim), int(p), int(approx)
+        if p > 7:
+            continue          # p = 15 is covered by the slow test below
+        m = _mesh(dim, 2, 0.0, 0)
+        P = pt.Patch(m, (1,) * dim, pt.levels_paper(p))
+        sm = pt.Smoother(kind="jacobi", omega=0.5)
+        b = np.random.default_rng(0).uniform(-1, 1, len(P.lv[p].diag))
+        _, it, _ = gmg.pcg(P.lv[p].A, b, lambda r: pt.local_solve(P, r, sm, {}), 1e-8, 100)
+        assert abs(it - approx) <= 3, (p, it)
+
+
+# ------------------------------------------------------------------- sweeps
+def test_sweep_single_patch_brute_force():
+    """2x2 mesh, one patch: u_new = u + Pi^T B (b - A u) with B the V-cycle
+    operator, checked by dense algebra on the global matrix."""
+    m = _mesh(2, 2, 0.2, 8)
+    p = 4
+    S = pt.PatchSmoother(m, p, bounds_fn=lz.exact_bounds_fn())
+    Ag = m.assemble(p).toarray()
+    rng = np.random.default_rng(3)
+    u = rng.uniform(-1, 1, m.n_nodes(p)) * m.free_mask(p)
+    b = rng.uniform(-1, 1, m.n_nodes(p)) * m.free_mask(p)
+    P = S.patch((1, 1))
+    I = P.lv[p].interior
+    B = pt.vcycle_matrix(P, S.sm, S.bounds((1, 1)))
+    ref = u.copy()
+    ref[I] += B @ (b - Ag @ u)[I]
+    assert np.allclose(S.sweep(u, b), ref, atol=1e-13)
+
+
+def test_sweep_patches_of_one_colour_commute():
+    m = _mesh(2, 6, 0.2, 12)
+    p = 2
+    S = pt.PatchSmoother(m, p, bounds_fn=lz.exact_bounds_fn())
+    rng = np.random.default_rng(4)
+    u = rng.uniform(-1, 1, m.n_nodes(p)) * m.free_mask(p)
+    b = rng.uniform(-1, 1, m.n_nodes(p)) * m.free_mask(p)
+    a = S.sweep(u, b, within="increasing")
+    c = S.sweep(u, b, within="decreasing")
+    assert np.array_equal(a, c)            # one add per DoF and colour: identical bits
+    # but the colour order matters (the smoother is multiplicative)
+    assert np.abs(S.sweep(u, b, reverse=True) - a).max() > 1e-6
+
+
+def test_multiplicative_sweep_reduces_energy_error():
+    m = _mesh(2, 6, 0.2, 12)
+    p = 3
+    S = pt.PatchSmoother(m, p, bounds_fn=lz.exact_bounds_fn())
+    free = m.free_mask(p)
+    A = fem.operator_with_dirichlet(m.assemble(p), free)
+    rng = np.random.default_rng(5)
+    x = rng.uniform(-1, 1, m.n_nodes(p)) * free
+    b = A @ x
+    u = np.zeros_like(b)
+    e0 = np.sqrt(x @ A @ x)
+    u = S.sweep(u, b)
+    e1 = np.sqrt((x - u) @ A @ (x - u))
+    assert e1 < 0.7 * e0
+
+
+# ------------------------------------------------------------------ Lanczos
+def test_splitmix64_published_stream():
+    """SplitMix64 reference outputs for state 1234567 (the published test vector of
+    the generator)."""
+    seed = 1234567
+    got = []
+    for i in range(5):
+        got.append(lz.splitmix64((seed + (i + 1) * lz.GOLDEN) & lz.MASK))
+    assert got == [6457827717110365317, 3203168211198807973, 9817491932198370423,
+                   4593380528125082431, 16408922859458223821]
+
+
+def test_sturm_bisection_matches_dense_eigs():
+    rng = np.random.default_rng(6)
+    a, b = rng.uniform(0, 2, 12), rng.uniform(0.1, 1, 11)
+    T = np.diag(a) + np.diag(b, 1) + np.diag(b, -1)
+    ev = np.linalg.eigvalsh(T)
+    lo, hi = lz.extreme_eigs(a, b)
+    assert abs(lo - ev[0]) < 1e-13 and abs(hi - ev[-1]) < 1e-13
+    for x in np.linspace(ev[0] - 0.1, ev[-1] + 0.1, 17):
+        assert lz.sturm_count(a, b, x) == int(np.sum(ev < x))
+
+
+@pytest.mark.parametrize("dim,q", [(2, 2), (2, 4), (3, 2)])
+def test_lanczos_extremes(dim, q):
+    m = _mesh(dim, 2, 0.2, 13)
+    lv = pt.Patch(m, (1,) * dim, [q]).lv[q]
+    s = 1.0 / np.sqrt(lv.diag)
+    ev = np.linalg.eigvalsh(s[:, None] * lv.A * s[None, :])
+    n = len(ev)
+    lo, hi, tmin, tmax = lz.patch_bounds(lv.A, lv.diag, 0, 0, q, k=n)
+    assert abs(tmax - ev[-1]) < 1e-9 and abs(tmin - ev[0]) < 1e-9
+    _, _, tmin16, tmax16 = lz.patch_bounds(lv.A, lv.diag, 0, 0, q, k=min(8, n - 1))
+    assert ev[0] - 1e-12 <= tmin16 and tmax16 <= ev[-1] + 1e-12      # Ritz values interlace
+    assert tmax16 > 0.9 * ev[-1]
+
+
+# --------------------------------------------------------------- GMG + CG
+def test_h_prolongation_exact_on_uniform_mesh():
+    """Section 2: the prolongation is the embedding; on a uniform mesh a global
+    polynomial of degree <= q is reproduced exactly."""
+    fine = _mesh(2, 4, 0.0, 0)
+    coarse = gmg.coarsen(fine)
+    q = 3
+    Pm = gmg.prolongation(coarse, fine, q)
+    f = lambda X: X[:, 0] ** 3 - 2 * X[:, 0] * X[:, 1] ** 2 + X[:, 1]
+    assert np.allclose(Pm @ f(coarse.node_coords(q)), f(fine.node_coords(q)), atol=1e-13)
+
+
+def _l2_error(mesh, q, uh, exact):
+    err = 0.0
+    nq = q + 3
+    pts, wts = fem.tensor_rule(mesh.dim, nq)
+    phi, _ = fem.basis_at(mesh.dim, q, nq)
+    Nq, _ = fem.q1_shape(mesh.dim, pts)
+    for ci in range(mesh.n_cells):
+        c = mesh.cell_multi(ci)
+        X = mesh.cell_vertices(c)
+        det = np.linalg.det(fem.jacobians(X, pts))
+        vals = phi @ uh[mesh.cell_nodes(q, c)]
+        err += np.sum(wts * det * (vals - exact(Nq @ X)) ** 2)
+    return math.sqrt(err)
+
+
+@pytest.mark.parametrize("q", [1, 2, 3])
+def test_manufactured_solution_convergence_rate(q):
+    """L2 error O(h^{q+1}) for -Laplace u = f with u = sin(pi x) sin(pi y) on a
+    perturbed mesh (perturbation scaled with h, so the mesh family is regular)."""
+    exact = lambda X: np.sin(np.pi * X[:, 0]) * np.sin(np.pi * X[:, 1])
+    f = lambda X: 2 * np.pi ** 2 * exact(X)
+    errs = []
+    for N in (4, 8, 16):
+        m = _mesh(2, N, 0.2, 21)
+        free = m.free_mask(q)
+        A = m.assemble(q).tocsr()[free][:, free]
+        b = m.load_vector(f, q, q + 2)[free]
+        uh = np.zeros(m.n_nodes(q))
+        uh[free] = spla.spsolve(A.tocsc(), b)
+        errs.append(_l2_error(m, q, uh, exact))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert rates[-1] > q + 1 - 0.3, (errs, rates)
+
+
+@pytest.mark.parametrize("kind", ["chebyshev", "jacobi"])
+def test_gmg_preconditioned_cg(kind):
+    m = _mesh(2, 8, 0.25, 31, ("loguniform", -1, 1))
+    p = 3
+    sa = dict(sm=pt.Smoother(kind=kind), bounds_fn=lz.lanczos_bounds_fn(seed=7))
+    G = gmg.GMG(m, p, 2, smoother_args=sa)
+    A = G.A[-1]
+    free = G.free[-1]
+    rng = np.random.default_rng(8)
+    b = rng.uniform(-1, 1, len(free)) * free
+    x, it, hist = gmg.pcg(A, b, G.vcycle, 1e-8, 60)
+    assert hist[-1] <= 1e-8 and it <= 20
+    x_ref = np.zeros_like(b)
+    x_ref[free] = spla.spsolve(A.tocsr()[free][:, free].tocsc(), b[free])
+    assert np.linalg.norm(x - x_ref) < 1e-6 * np.linalg.norm(x_ref)
+    # the symmetric V-cycle is a symmetric operator
+    y1, y2 = rng.uniform(-1, 1, len(b)) * free, rng.uniform(-1, 1, len(b)) * free
+    assert abs(y1 @ G.vcycle(y2) - y2 @ G.vcycle(y1)) < 1e-12 * abs(y1 @ G.vcycle(y1))
