@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark: GMG-preconditioned CG to a 1e-8 relative residual with the
+vertex-patch / local p-multigrid smoother on the 3D Q4 32^3 perturbed-hex
+workload (manufactured solution sin(pi x) sin(pi y) sin(pi z)).
+
+One step = one complete solve from u = 0 (patch sweeps with Gather, Evaluate,
+local p-MG V-cycles and Scatter on every mesh level, global residuals,
+h-transfers, dense coarse solve, CG vector updates and dots).  The headline is
+the mixed-precision path (FP32 patch smoother and GMG levels, FP64 CG and
+coarse solve); the plain FP64 path is timed beside it.
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FP32_PEAK_DERIVED = 152 * 128 * 2 * 2.070e9      # SMs x FP32 lanes x 2 flops x max SM clock
+FP64_PEAK_NOMINAL = 1.25e12                      # GB300 FP64 rate (nominal)
+METRIC = "patch-smoother DoFs/s and CG time-to-1e-8 residual: mixed/learned vs plain FP64, 1 GB300"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2_3d_q4_n32_perturbed")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison arm")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------- CPU baseline
+CPU_SCRIPT = r"""
+import json, sys, time
+import numpy as np
+sys.path.insert(0, {root!r})
+from oracle import fem, lanczos as lz, patch as pt
+from paper_2510_17785_gb300 import inputs
+w = inputs.WORKLOADS[{workload!r}]
+prob = inputs.make_problem(w)
+m = fem.StructuredMesh(w.dim, w.N, prob.coords, prob.kappa)
+verts = pt.interior_vertices(w.dim, w.N)
+rng = np.random.default_rng(1234)
+pick = [verts[i] for i in rng.choice(len(verts), {npatch}, replace=False)]
+u = inputs.random_vector(5, w.dim, w.p, w.N)
+b = inputs.random_vector(6, w.dim, w.p, w.N)
+t0 = time.perf_counter()
+patches = []
+for v in pick:
+    P = pt.Patch(m, v, pt.levels_halving(w.p))
+    patches.append((P, lz.lanczos_bounds_fn(seed=0)(P, pt.patch_id(w.dim, w.N, v))))
+t_build = (time.perf_counter() - t0) / len(pick)
+sm = pt.Smoother()
+t0 = time.perf_counter()
+for rep in range({reps}):
+    for P, bd in patches:
+        d = pt.local_solve(P, P.residual(u, b), sm, bd, 1)
+t_visit = (time.perf_counter() - t0) / ({reps} * len(pick))
+print(json.dumps(dict(t_build=t_build, t_visit=t_visit, npatch=len(pick), reps={reps})))
+"""
+
+
+def oracle_patch_times(workload: str, npatch: int, reps: int):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = CPU_SCRIPT.format(root=ROOT, workload=workload, npatch=npatch, reps=reps)
+    t0 = time.perf_counter()
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    out["wall_s"] = time.perf_counter() - t0
+    return out
+
+
+def oracle_solve_estimate(w, levels: int, iters: int, t_visit: float) -> float:
+    """Patch work of one solve: every V-cycle visits every patch of every
+    smoothed level twice (forward and reverse sweep)."""
+    visits = 0
+    for l in range(1, levels):
+        Nl = w.N >> (levels - 1 - l)
+        visits += 2 * (Nl - 1) ** w.dim
+    return iters * visits * t_visit
+
+
+def cpu_baseline(w, levels, iters, npatch=48, reps=4):
+    t = oracle_patch_times(w.name, npatch, reps)
+    t_solve = oracle_solve_estimate(w, levels, iters, t["t_visit"])
+    return {
+        "value": w.n_free / t_solve, "unit": "DoFs/s", "cores": 1, "kind": "oracle",
+        "sample": (f"{t['npatch']} seeded patches of the finest level, {t['reps']} Evaluate+V-cycle visits each "
+                   f"(dense FP64 patch matrices built once, {t['t_build']*1e3:.1f} ms/patch, not counted); "
+                   f"{t['t_visit']*1e3:.3f} ms per visit x {iters} CG iterations x 2 sweeps x all patches of "
+                   f"levels 1..{levels-1}: patch work only, extrapolated ({t['wall_s']:.1f} s of CPU work)"),
+        "t_solve_extrapolated_s": t_solve,
+    }
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args):
+    import torch
+    from paper_2510_17785_gb300 import inputs, pmg
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+        torch.cuda.set_device(local)
+        td.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = inputs.WORKLOADS[args.workload]
+    if rank > 0:
+        w = w.with_(seed=w.seed + 100 * rank)          # independent replica per rank
+    levels = int(round(math.log2(w.N // w.coarse_N))) + 1
+    prob = inputs.make_problem(w)
+
+    def make(precision):
+        ctx = pmg.Context(local, precision=precision)
+        ctx.mesh_structured(w.dim, w.N, w.p, levels, prob.coords, prob.kappa)
+        t0 = time.perf_counter()
+        ctx.setup()
+        return ctx, time.perf_counter() - t0
+
+    nd = w.n_dofs
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def timed_solves(ctx, b, nsteps, nwarm):
+        x = torch.zeros_like(b)
+        its = []
+        for _ in range(nwarm):
+            x.zero_()
+            ctx.solve_cg(b, x, 1e-8, 200)
+        ms = []
+        launches0 = ctx.launch_count()
+        for _ in range(nsteps):
+            x.zero_()
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            it, rel, _ = ctx.solve_cg(b, x, 1e-8, 200)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            its.append((it, rel))
+        return ms, its, ctx.launch_count() - launches0, x
+
+    result = {}
+    arms = [("mixed", pmg.PREC_MIXED)] + ([] if args.no_fp64 else [("fp64", pmg.PREC_FP64)])
+    clocks = Clocks(local)
+    for name, prec in arms:
+        ctx, t_setup = make(prec)
+        b = torch.zeros(nd, dtype=torch.float64, device=dev)
+        ctx.rhs_manufactured(b)
+        torch.cuda.synchronize()
+        if dist:
+            torch.distributed.barrier()
+        if name == "mixed":
+            clocks.start()
+        ms, its, launches, x = timed_solves(ctx, b, args.steps, args.warmup)
+        if name == "mixed":
+            clk = clocks.stop()
+        # dominant kernel: the patch sweep on the finest level, timed on this stream
+        lf = levels - 1
+        u = torch.zeros_like(b)
+        for _ in range(2):
+            ctx.patch_smooth(lf, b, u, 1, False)
+        nsw = 3
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.patch_smooth(lf, b, u, nsw, False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_sweep = e0.elapsed_time(e1) / nsw * 1e-3
+        flops = ctx.sweep_flops(lf)
+        # end to end through the host-vector entry point (pinned host buffers)
+        bh = torch.empty(nd, dtype=torch.float64).pin_memory()
+        bh.copy_(b.cpu())
+        uh = torch.empty(nd, dtype=torch.float64).pin_memory()
+        e2e_ms = []
+        for _ in range(max(1, min(args.steps, 3))):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.solve_cg_host(bh.numpy(), uh.numpy(), 1e-8, 200)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            e2e_ms.append(e0.elapsed_time(e1))
+        err = float((x - torch.tensor(uh.numpy(), device=dev)).abs().max())
+        result[name] = dict(ms=ms, its=its, launches=launches, t_sweep=t_sweep, sweep_flops=flops,
+                            e2e_ms=e2e_ms, setup_s=t_setup, maxdiff_e2e=err,
+                            umax=float(x.abs().max()))
+        if name == "mixed":
+            result["fma32"] = ctx.fma_peak(pmg.PREC_MIXED)
+            result["fma64"] = ctx.fma_peak(pmg.PREC_FP64)
+        ctx.close()
+
+    head = result["mixed"]
+    t_step = sum(head["ms"]) / len(head["ms"])
+    t_max = t_step
+    if dist:
+        tt = torch.tensor([t_step], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * w.n_free / (t_max * 1e-3)
+    achieved = head["sweep_flops"] / head["t_sweep"]
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "DoFs/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": t_max,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 (patch smoother, local p-MG, GMG levels) + f64 (CG, residual, dots, coarse solve)",
+        "data": "synthetic (seeded perturbed hex mesh, manufactured right-hand side)",
+        "config": {
+            "workload": w.name, "dim": w.dim, "cells_per_dir": w.N, "p": w.p, "n_free": w.n_free,
+            "h_levels": levels, "p_levels": [w.p >> k for k in range(8) if w.p >> k >= 1],
+            "smoother": "Chebyshev degree 3 on D^-1 A, Lanczos (16-step) bounds, N_MG = 1",
+            "rtol": 1e-8, "step": "one GMG-PCG solve from u = 0",
+            "l2": "flushed (512 MB write) before every timed step",
+            "replicas": world,
+        },
+        "time_to_solution_ms": t_max,
+        "cg_iterations": [i for i, _ in head["its"]],
+        "final_relres": max(r for _, r in head["its"]),
+        "sweep": {"dofs_per_s": w.n_free / head["t_sweep"], "ms": head["t_sweep"] * 1e3,
+                  "flops": head["sweep_flops"]},
+        "setup_s": head["setup_s"],
+        "roofline": {
+            "bound": "alu", "achieved": achieved / 1e12,
+            "peak": FP32_PEAK_DERIVED / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_DERIVED, "traffic": None,
+            "kernel": "k_patch<3,4,float,SWEEP> (finest-level patch sweep, 8 colour launches)",
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+            "measured_fma_peak": result["fma32"] / 1e12,
+            "frac_of_measured_fma": achieved / result["fma32"],
+        },
+        "e2e": {"value": world * w.n_free / (statistics.mean(head["e2e_ms"]) * 1e-3), "unit": "DoFs/s",
+                "ms": statistics.mean(head["e2e_ms"]), "h2d_bytes_per_step": nd * 8, "d2h_bytes_per_step": nd * 8,
+                "api": "pmg_solve_cg_host"},
+        "gpu_launches": head["launches"],
+        "clocks": clk,
+    }
+    if "fp64" in result:
+        f = result["fp64"]
+        t64 = sum(f["ms"]) / len(f["ms"])
+        a64 = f["sweep_flops"] / f["t_sweep"]
+        out["fp64_plain"] = {
+            "value": world * w.n_free / (t64 * 1e-3), "ms_per_step": t64,
+            "cg_iterations": [i for i, _ in f["its"]], "final_relres": max(r for _, r in f["its"]),
+            "sweep_ms": f["t_sweep"] * 1e3, "sweep_dofs_per_s": w.n_free / f["t_sweep"],
+            "roofline": {"bound": "alu", "achieved": a64 / 1e12, "peak": FP64_PEAK_NOMINAL / 1e12,
+                         "unit": "TFLOP/s", "frac": a64 / FP64_PEAK_NOMINAL,
+                         "peak_source": "nominal GB300 FP64 rate", "measured_fma_peak": result["fma64"] / 1e12},
+            "speedup_mixed_vs_fp64": t64 / t_max,
+            "max_abs_diff_mixed_vs_fp64_solution": None,
+        }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        its = int(statistics.median(i for i, _ in head["its"]))
+        out["cpu_baseline"] = cpu_baseline(w, levels, its)
+    if dist:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+# -------------------------------------------------------------- reference
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2510_17785_gb300 import inputs
+    w = inputs.WORKLOADS[args.workload]
+    levels = int(round(math.log2(w.N // w.coarse_N))) + 1
+    iters = 8          # CG iterations the GPU solver needs on this workload (both precisions)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        t = oracle_patch_times(w.name, 12, 2)
+        v = w.n_free / oracle_solve_estimate(w, levels, iters, t["t_visit"])
+        if i >= args.warmup:
+            vals.append((v, t))
+    v = statistics.mean(x for x, _ in vals)
+    ms = w.n_free / v * 1e3
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "DoFs/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "dim": w.dim, "cells_per_dir": w.N, "p": w.p, "n_free": w.n_free},
+        "cpu_baseline": {"value": v, "unit": "DoFs/s", "cores": 1, "kind": "oracle",
+                         "sample": "12 seeded finest-level patches x 2 Evaluate+V-cycle visits per step; "
+                                   f"extrapolated to {iters} CG iterations x 2 sweeps x all patches"},
+        "e2e": {"value": v, "unit": "DoFs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

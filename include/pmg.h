@@ -1,0 +1,210 @@
+/*
+ * pmg.h -- C ABI of the GB300 vertex-patch smoother with a nested matrix-free
+ * p-multigrid local solver (M. Wichrowski, "Local Solvers for High-Order Patch
+ * Smoothers via p-Multigrid", arXiv 2510.17785).
+ *
+ * The library discretises a(u, v) = int kappa grad u . grad v (Section 2,
+ * eq. bilinear-form) with continuous Q_p Lagrange elements on Gauss-Lobatto
+ * support points over a structured (N^d cells, d = 2 or 3) mesh of the unit
+ * square/cube whose vertices may be displaced arbitrarily (Q1 cell geometry),
+ * with homogeneous Dirichlet conditions on the boundary.  Integrals use the
+ * (q+1)-point Gauss rule per direction at degree q.
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns an int status (PMG_OK = 0 or a PMG_ERR_* code);
+ *    pmg_last_error() returns a message for the last failure on a context.
+ *  - Host arrays passed in are caller-owned and copied before the call returns.
+ *  - Vector arguments named *_dev are caller-owned DEVICE pointers to FP64
+ *    arrays of length (p*N_l+1)^d in the global lexicographic DoF order of
+ *    level l (x fastest).  Entries on Dirichlet DoFs are ignored on input and
+ *    written as 0 on output.  The library never frees caller memory.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *    stream.  Calls are asynchronous on that stream unless stated otherwise.
+ *  - Mesh level l = 0 is the coarsest mesh, l = n_levels-1 the finest.
+ *  - The context owns every derived structure (geometry tensors, diagonals,
+ *    patch lists, eigenvalue bounds, coarse factor, work vectors).
+ *  - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef PMG_H
+#define PMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+enum {
+  PMG_OK = 0,
+  PMG_ERR_ARG = 1,           /* invalid argument (size, pointer, state)        */
+  PMG_ERR_CUDA = 2,          /* a CUDA runtime call failed                     */
+  PMG_ERR_DEGENERATE = 3,    /* det J <= 0 at a Gauss point or vertex of a cell */
+  PMG_ERR_NOT_CONVERGED = 4, /* the solver hit maxit before rtol              */
+  PMG_ERR_NUMERIC = 5,       /* NaN or Inf in a residual norm                  */
+  PMG_ERR_TIMEOUT = 6,       /* a bounded device wait gave up                  */
+  PMG_ERR_UNSUPPORTED = 7    /* e.g. p > 8, or a precision/degree combination  */
+};
+
+/* ---- options ----------------------------------------------------------- */
+enum { PMG_SMOOTHER_CHEBYSHEV = 0, PMG_SMOOTHER_JACOBI = 1 };
+enum { PMG_BOUNDS_LANCZOS = 0, PMG_BOUNDS_FIXED = 1, PMG_BOUNDS_USER = 2 };
+enum { PMG_PREC_FP64 = 0,  /* everything in FP64                               */
+       PMG_PREC_MIXED = 1  /* patch smoother, local p-MG and GMG levels in FP32;
+                              outer CG, its residuals and dots, and the coarse
+                              solve in FP64                                   */ };
+
+typedef struct pmg_options {
+  int smoother;          /* PMG_SMOOTHER_*: smoother on every local p-level    */
+  int cheb_degree;       /* Chebyshev polynomial degree (k), >= 1              */
+  double jacobi_omega;   /* damping of the Jacobi smoother (paper: 1/2)        */
+  int n_mg;              /* local V-cycles per patch solve (N_MG, >= 1)        */
+  int bounds;            /* PMG_BOUNDS_*: source of the Chebyshev intervals    */
+  int lanczos_steps;     /* Lanczos steps per (patch, p-level)                 */
+  double bound_safety;   /* hi = safety * theta_max                            */
+  double bound_ratio;    /* lo = max(theta_min, hi / ratio)                    */
+  double fixed_lo, fixed_hi; /* interval used with PMG_BOUNDS_FIXED           */
+  uint64_t seed;         /* seed of the Lanczos start vectors                  */
+  int precision;         /* PMG_PREC_*                                         */
+} pmg_options;
+
+typedef struct pmg_ctx pmg_ctx;
+
+/* Fill `opt` with the defaults: Chebyshev degree 3, N_MG = 1, Lanczos bounds
+ * with 16 steps, safety 1.1, ratio 10, omega 0.5, seed 0, FP64. */
+void pmg_default_options(pmg_options* opt);
+
+/* Create a context on CUDA device `device`; `opt` may be NULL (defaults).
+ * On success *out owns the context; release it with pmg_destroy. */
+int pmg_create(int device, const pmg_options* opt, pmg_ctx** out);
+int pmg_destroy(pmg_ctx* ctx);
+const char* pmg_last_error(const pmg_ctx* ctx);
+
+/* ---- mesh and coefficient (Section 2: mesh hierarchy M_1 c ... c M_L) ---
+ * Upload the finest mesh of a structured hierarchy: `dim` in {2,3}; N cells
+ * per direction on the finest level; degree p in 1..8; n_levels >= 1 h-levels
+ * with N_l = N / 2^(n_levels-1-l) cells per direction (N must be divisible by
+ * 2^(n_levels-1)).  coords: ((N+1)^dim x dim) FP64 vertex coordinates in
+ * lexicographic vertex order (x fastest); vertices of coarser levels are the
+ * finest-level vertices with even indices.  kappa: N^dim FP64 cell values of
+ * the coefficient (paper: mu); a coarse cell takes the arithmetic mean of its
+ * 2^dim children.  Boundary vertices must lie on the boundary of the unit
+ * square/cube for the Dirichlet data to mean what it says (not checked). */
+int pmg_mesh_structured(pmg_ctx* ctx, int dim, int N, int p, int n_levels,
+                        const double* coords, const double* kappa);
+
+/* Build everything the solver needs (geometry tensors on every level and
+ * p-level, level diagonals, patch and colour lists, Chebyshev bounds, coarse
+ * Cholesky factor).  Returns PMG_ERR_DEGENERATE if a cell has det J <= 0 at
+ * any Gauss point or vertex (Section 3.2 excludes such degenerate cells).
+ * Synchronises the device. */
+int pmg_setup(pmg_ctx* ctx);
+
+/* DoF counts of mesh level l: total (p N_l + 1)^d and free (p N_l - 1)^d. */
+int pmg_num_dofs(const pmg_ctx* ctx, int level, int64_t* total, int64_t* n_free);
+/* Number of vertex patches (interior vertices, (N_l - 1)^d) and colours (2^d). */
+int pmg_num_patches(const pmg_ctx* ctx, int level, int64_t* n_patches, int* n_colours);
+/* Levels of the local p-hierarchy (Section 3.1): writes up to 8 degrees,
+ * p, floor(p/2), ..., 1, into degrees[], their count into *n. */
+int pmg_p_levels(const pmg_ctx* ctx, int* degrees, int* n);
+
+/* ---- operator (eq. matrix) --------------------------------------------
+ * Au = A_l u on mesh level l at degree p; rows of Dirichlet DoFs are 0.
+ * Deterministic (cells are processed in 2^d parity classes). */
+int pmg_apply(pmg_ctx* ctx, int level, const double* u_dev, double* Au_dev, void* stream);
+
+/* ---- patch smoother (Section 2.1, Algorithm 1) --------------------------
+ * Multiplicative vertex-patch sweep on mesh level l: for every colour c in
+ * 0..2^d-1 (reversed if `reverse`), every patch j of colour c computes
+ *   Gather    u_j = Pi_j-bar u, b_j = Pi_j b            (eq. gather)
+ *   Evaluate  r_j = b_j - Pi_j A_j-bar u_j             (eq. main:4)
+ *   Solve     d_j = N_MG local p-MG V-cycles on r_j    (eq. main:5, Alg. 2)
+ *   Scatter   u += Pi_j^T d_j                          (eq. scatter)
+ * Patches of one colour share no cell, so they run concurrently and the
+ * result equals the sequential sweep in colour-major order.  u_dev is
+ * updated in place; n_sweeps sweeps are applied. */
+int pmg_patch_smooth(pmg_ctx* ctx, int level, const double* b_dev, double* u_dev,
+                     int n_sweeps, int reverse, void* stream);
+/* One colour of the sweep above (colour in 0..2^d-1). */
+int pmg_patch_smooth_colour(pmg_ctx* ctx, int level, int colour, const double* b_dev,
+                            double* u_dev, void* stream);
+
+/* ---- local solver (Section 3, Algorithm 2) ------------------------------
+ * For n patches of mesh level l given by patch_ids_dev (device int64, patch
+ * numbering lexicographic over interior vertices, x fastest), apply n_cycles
+ * V-cycles (the first from d = 0) to the local right-hand sides r_dev and
+ * write the corrections d_dev.  r_dev and d_dev are device FP64 arrays of
+ * n x (2p-1)^d values, patch-interior DoFs in lexicographic order (x fastest). */
+int pmg_local_vcycle(pmg_ctx* ctx, int level, int64_t n, const int64_t* patch_ids_dev,
+                     const double* r_dev, double* d_dev, int n_cycles, void* stream);
+
+/* ---- Chebyshev intervals -----------------------------------------------
+ * Per (mesh level, p-level q > 1, patch) interval [lo, hi] for D^-1 A_{j,q}.
+ * pmg_get_bounds writes n_patches x n_plevels pairs (lo, hi) as FP64, p-level
+ * index fastest (index 0 = degree p), into host memory; entries of q = 1 are 0.
+ * pmg_set_bounds uploads such an array (used with PMG_BOUNDS_USER, or to
+ * override).  pmg_compute_bounds recomputes them with the configured source.
+ * Lanczos: k steps on D^-1/2 A D^-1/2 with full reorthogonalisation,
+ * start vector 1 + (u - 1/2), u from counter-based SplitMix64. */
+int pmg_get_bounds(pmg_ctx* ctx, int level, double* lohi_host);
+int pmg_set_bounds(pmg_ctx* ctx, int level, const double* lohi_host);
+int pmg_compute_bounds(pmg_ctx* ctx, int source);
+/* Raw Lanczos extreme Ritz values (theta_min, theta_max) per (patch, p-level),
+ * same layout as pmg_get_bounds. */
+int pmg_get_ritz(pmg_ctx* ctx, int level, double* tminmax_host);
+
+/* ---- global solver (Section 2; GMG preconditioned CG) ------------------
+ * One GMG V-cycle on the finest level: x = B b with one forward patch sweep
+ * before and one reversed sweep after the coarse-grid correction, dense
+ * Cholesky on level 0.  Symmetric, so it preconditions CG. */
+int pmg_gmg_vcycle(pmg_ctx* ctx, const double* b_dev, double* x_dev, void* stream);
+
+/* Preconditioned CG on the finest level from u = 0 until
+ * ||r_k||_2 <= rtol ||b||_2 or maxit iterations.  Writes *iters and *relres
+ * (host).  Synchronises `stream` once per iteration (one 8-byte read).
+ * Returns PMG_ERR_NOT_CONVERGED at maxit, PMG_ERR_NUMERIC on NaN/Inf. */
+int pmg_solve_cg(pmg_ctx* ctx, const double* b_dev, double* u_dev, double rtol, int maxit,
+                 int* iters, double* relres, void* stream);
+
+/* Same solve with host vectors: copies b in, solves, copies u out. */
+int pmg_solve_cg_host(pmg_ctx* ctx, const double* b_host, double* u_host, double rtol,
+                      int maxit, int* iters, double* relres, void* stream);
+
+/* Load vector b_i = int f phi_i on the finest level for the manufactured
+ * solution u = prod_k sin(pi x_k) (f = d pi^2 u), Gauss rule with p+2 points
+ * per direction; Dirichlet entries 0. */
+int pmg_rhs_manufactured(pmg_ctx* ctx, double* b_dev, void* stream);
+
+/* ---- integer structures (bit-exact tests) -------------------------------
+ * Colour of every patch of level l (uint8, patch order as above). */
+int pmg_get_colours(const pmg_ctx* ctx, int level, uint8_t* colours_host);
+/* Patch map of level l: for each patch its 2^d cells (int64, cell order
+ * lexicographic inside the patch, x fastest) followed by the global DoF id of
+ * its closure origin (lowest corner node). Writes n_patches x (2^d + 1). */
+int pmg_get_patch_map(const pmg_ctx* ctx, int level, int64_t* map_host);
+
+/* Inverse level diagonal 1/diag(A_{l,q}) of mesh level l at p-level index k
+ * (degree p >> k), device FP64 output of (q N_l + 1)^d entries (Dirichlet 0). */
+int pmg_get_inv_diag(pmg_ctx* ctx, int level, int k, double* out_dev, void* stream);
+
+/* Algorithmic flop count of one forward patch sweep on mesh level l (the
+ * operator applies of Evaluate, smoothing and residuals, by the
+ * sum-factorisation count 4d 1D sweeps + the quadrature-point product per
+ * cell, plus the p-transfers). */
+double pmg_sweep_flops(const pmg_ctx* ctx, int level);
+
+/* ---- measurement ----------------------------------------------------------
+ * Number of kernels this context has launched so far (kernel nodes of a CUDA
+ * graph count once per graph launch). */
+int pmg_launch_count(const pmg_ctx* ctx, int64_t* n);
+
+/* FMA-pipe peak microbenchmark on the context's device: a grid of
+ * independent FMA chains in FP64 (precision = PMG_PREC_FP64) or FP32
+ * (PMG_PREC_MIXED), sized to fill every SM; writes the achieved FLOP/s
+ * (2 flops per FMA).  Synchronises the device. */
+int pmg_fma_peak(pmg_ctx* ctx, int precision, double* flops_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PMG_H */

@@ -1,0 +1,12 @@
+// Kernels for d = 3 in FP32, and the precision-generic FP32 helpers.
+#include "kernels_impl.cuh"
+PMG_INSTANTIATE_DIM_T(3, float)
+namespace pmg {
+template int launch_fma_chain<float>(float*, int, int, int, cudaStream_t);
+template int launch_band_sweep<float>(const float*, float*, const double*, const int*, int, int, int, size_t, size_t,
+                                      int, cudaStream_t);
+template int launch_fill<float>(float*, size_t, float, cudaStream_t);
+template int launch_sub_from<float>(const float*, float*, size_t, cudaStream_t);
+template int launch_add_to<float>(const float*, float*, size_t, cudaStream_t);
+template int launch_coarse_gemv<float>(const double*, const int*, int, const float*, float*, cudaStream_t);
+}  // namespace pmg

@@ -1,0 +1,273 @@
+// Definitions of the launchers declared in launch.h.  Included by the four
+// kern_<d>d_<prec>.cu translation units, each of which instantiates them for
+// its own dimension and precision (and owns its own constant tables).
+#pragma once
+#include "global.cuh"
+#include "launch.h"
+
+namespace pmg {
+
+inline int grid_for(size_t work, int threads) {
+  size_t g = (work + threads - 1) / threads;
+  if (g > 152 * 32) g = 152 * 32;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+#define PMG_CHECK_LAUNCH()                              \
+  do {                                                  \
+    if (cudaPeekAtLastError() != cudaSuccess) return ST_CUDA; \
+  } while (0)
+
+template <int DIM, typename T>
+int upload_tables(const Tables<double>& h64, const Tables<float>& h32, const Rules& r) {
+  return upload_tables_tu(h64, h32, r) == cudaSuccess ? ST_OK : ST_CUDA;
+}
+
+template <int DIM, int P, typename T>
+int launch_patch_P(int mode, const PatchArgs<T>& a, cudaStream_t s) {
+  using C = Config<DIM, P, T>;
+  if constexpr (!C::fits) {
+    return ST_UNSUPPORTED;
+  } else {
+    if (a.n_items <= 0) return ST_OK;
+    const int grid = (a.n_items + C::PPB - 1) / C::PPB;
+    if (mode == MODE_SWEEP) {
+      static bool attr = false;
+      if (!attr) {
+        if (cudaFuncSetAttribute(k_patch<DIM, P, T, MODE_SWEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)C::smem) != cudaSuccess)
+          return ST_CUDA;
+        attr = true;
+      }
+      k_patch<DIM, P, T, MODE_SWEEP><<<grid, C::NT, C::smem, s>>>(a);
+    } else {
+      static bool attr = false;
+      if (!attr) {
+        if (cudaFuncSetAttribute(k_patch<DIM, P, T, MODE_LOCAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)C::smem) != cudaSuccess)
+          return ST_CUDA;
+        attr = true;
+      }
+      k_patch<DIM, P, T, MODE_LOCAL><<<grid, C::NT, C::smem, s>>>(a);
+    }
+    PMG_CHECK_LAUNCH();
+    return ST_OK;
+  }
+}
+
+template <int DIM, typename T>
+int launch_patch(int P, int mode, const PatchArgs<T>& a, cudaStream_t s) {
+  switch (P) {
+    case 1: return launch_patch_P<DIM, 1, T>(mode, a, s);
+    case 2: return launch_patch_P<DIM, 2, T>(mode, a, s);
+    case 3: return launch_patch_P<DIM, 3, T>(mode, a, s);
+    case 4: return launch_patch_P<DIM, 4, T>(mode, a, s);
+    case 5: return launch_patch_P<DIM, 5, T>(mode, a, s);
+    case 6: return launch_patch_P<DIM, 6, T>(mode, a, s);
+    case 7: return launch_patch_P<DIM, 7, T>(mode, a, s);
+    case 8: return launch_patch_P<DIM, 8, T>(mode, a, s);
+    default: return ST_UNSUPPORTED;
+  }
+}
+
+template <int DIM, int P, typename T>
+void patch_config_P(size_t* smem, int* ppb, int* nt) {
+  using C = Config<DIM, P, T>;
+  *smem = C::fits ? C::smem : 0;
+  *ppb = C::fits ? C::PPB : 0;
+  *nt = C::NT;
+}
+
+template <int DIM, typename T>
+void patch_config(int P, size_t* smem, int* ppb, int* nt) {
+  switch (P) {
+    case 1: return patch_config_P<DIM, 1, T>(smem, ppb, nt);
+    case 2: return patch_config_P<DIM, 2, T>(smem, ppb, nt);
+    case 3: return patch_config_P<DIM, 3, T>(smem, ppb, nt);
+    case 4: return patch_config_P<DIM, 4, T>(smem, ppb, nt);
+    case 5: return patch_config_P<DIM, 5, T>(smem, ppb, nt);
+    case 6: return patch_config_P<DIM, 6, T>(smem, ppb, nt);
+    case 7: return patch_config_P<DIM, 7, T>(smem, ppb, nt);
+    case 8: return patch_config_P<DIM, 8, T>(smem, ppb, nt);
+    default: *smem = 0; *ppb = 0; *nt = 0;
+  }
+}
+
+template <int DIM, int Q, typename T>
+int launch_lanczos_Q(const LanczosArgs<T>& a, cudaStream_t s) {
+  constexpr size_t smem = lanczos_smem<DIM, Q, T>();
+  if constexpr (smem > 227 * 1024) {
+    return ST_UNSUPPORTED;
+  } else {
+    if (a.n_items <= 0) return ST_OK;
+    if (a.ksteps > 64) return ST_ARG;
+    static bool attr = false;
+    if (!attr) {
+      if (cudaFuncSetAttribute(k_lanczos<DIM, Q, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess)
+        return ST_CUDA;
+      attr = true;
+    }
+    k_lanczos<DIM, Q, T><<<a.n_items, 256, smem, s>>>(a);
+    PMG_CHECK_LAUNCH();
+    return ST_OK;
+  }
+}
+
+template <int DIM, typename T>
+int launch_lanczos(int q, const LanczosArgs<T>& a, cudaStream_t s) {
+  switch (q) {
+    case 2: return launch_lanczos_Q<DIM, 2, T>(a, s);
+    case 3: return launch_lanczos_Q<DIM, 3, T>(a, s);
+    case 4: return launch_lanczos_Q<DIM, 4, T>(a, s);
+    case 5: return launch_lanczos_Q<DIM, 5, T>(a, s);
+    case 6: return launch_lanczos_Q<DIM, 6, T>(a, s);
+    case 7: return launch_lanczos_Q<DIM, 7, T>(a, s);
+    case 8: return launch_lanczos_Q<DIM, 8, T>(a, s);
+    default: return ST_UNSUPPORTED;
+  }
+}
+
+template <int DIM, int Q, typename T>
+int launch_cell_apply_Q(const T* u, T* out, const T* G, int N, cudaStream_t s) {
+  constexpr int NT = DIM == 3 ? 128 : 64;
+  constexpr int CPB = DIM == 3 ? (Q <= 2 ? 4 : (Q <= 5 ? 2 : 1)) : (Q <= 4 ? 8 : 4);
+  using CA = CellApply<DIM, Q, T, NT, CPB>;
+  static bool attr = false;
+  if (!attr) {
+    if (cudaFuncSetAttribute(k_cell_apply<DIM, Q, T, NT, CPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)CA::smem) != cudaSuccess)
+      return ST_CUDA;
+    attr = true;
+  }
+  size_t M = (size_t)Q * N + 1, total = 1;
+  for (int ax = 0; ax < DIM; ++ax) total *= M;
+  k_fill<T><<<grid_for(total, 256), 256, 0, s>>>(out, total, T(0));
+  const int Nh = (N + 1) / 2;
+  int nclass = 1;
+  for (int ax = 0; ax < DIM; ++ax) nclass *= Nh;
+  const int grid = (nclass + CPB - 1) / CPB;
+  for (int par = 0; par < (1 << DIM); ++par)
+    k_cell_apply<DIM, Q, T, NT, CPB><<<grid, NT, CA::smem, s>>>(u, out, G, N, par);
+  PMG_CHECK_LAUNCH();
+  return ST_OK;
+}
+
+template <int DIM, typename T>
+int launch_cell_apply(int q, const T* u, T* out, const T* G, int N, cudaStream_t s) {
+  switch (q) {
+    case 1: return launch_cell_apply_Q<DIM, 1, T>(u, out, G, N, s);
+    case 2: return launch_cell_apply_Q<DIM, 2, T>(u, out, G, N, s);
+    case 3: return launch_cell_apply_Q<DIM, 3, T>(u, out, G, N, s);
+    case 4: return launch_cell_apply_Q<DIM, 4, T>(u, out, G, N, s);
+    case 5: return launch_cell_apply_Q<DIM, 5, T>(u, out, G, N, s);
+    case 6: return launch_cell_apply_Q<DIM, 6, T>(u, out, G, N, s);
+    case 7: return launch_cell_apply_Q<DIM, 7, T>(u, out, G, N, s);
+    case 8: return launch_cell_apply_Q<DIM, 8, T>(u, out, G, N, s);
+    default: return ST_UNSUPPORTED;
+  }
+}
+
+template <int DIM, typename T>
+int launch_geometry(const double* coords, const double* kappa, int N, int q, T* G, int* err, cudaStream_t s) {
+  size_t ncell = 1, ngc = 1;
+  for (int ax = 0; ax < DIM; ++ax) { ncell *= N; ngc *= (q + 1); }
+  k_geometry<DIM, T><<<grid_for(ncell * ngc, 256), 256, 0, s>>>(coords, kappa, N, q, G, err);
+  PMG_CHECK_LAUNCH();
+  return ST_OK;
+}
+
+template <int DIM>
+int launch_diag(const double* G64, int N, int q, double* diag, double* dinv64, float* dinv32, cudaStream_t s) {
+  const size_t M = (size_t)q * N + 1;
+  size_t total = 1, ngc = 1;
+  for (int ax = 0; ax < DIM; ++ax) { total *= M; ngc *= (q + 1); }
+  k_fill<double><<<grid_for(total, 256), 256, 0, s>>>(diag, total, 0.0);
+  const int Nh = (N + 1) / 2;
+  size_t nclass = 1;
+  for (int ax = 0; ax < DIM; ++ax) nclass *= Nh;
+  for (int par = 0; par < (1 << DIM); ++par)
+    k_diag<DIM><<<grid_for(nclass * ngc, 128), 128, 0, s>>>(G64, N, q, par, diag);
+  k_invert_diag<DIM, float><<<grid_for(total, 256), 256, 0, s>>>(diag, (int)M, dinv64, dinv32);
+  PMG_CHECK_LAUNCH();
+  return ST_OK;
+}
+
+template <int DIM>
+int launch_rhs_manufactured(const double* coords, int N, int q, double* b, cudaStream_t s) {
+  const size_t M = (size_t)q * N + 1;
+  size_t total = 1, nn = 1;
+  for (int ax = 0; ax < DIM; ++ax) { total *= M; nn *= (q + 1); }
+  k_fill<double><<<grid_for(total, 256), 256, 0, s>>>(b, total, 0.0);
+  const int Nh = (N + 1) / 2;
+  size_t nclass = 1;
+  for (int ax = 0; ax < DIM; ++ax) nclass *= Nh;
+  for (int par = 0; par < (1 << DIM); ++par)
+    k_rhs_manufactured<DIM><<<grid_for(nclass * nn, 128), 128, 0, s>>>(coords, N, q, par, b);
+  PMG_CHECK_LAUNCH();
+  return ST_OK;
+}
+
+template <typename T>
+int launch_band_sweep(const T* in, T* out, const double* W, const int* start, int width, int Lin, int Lout, size_t O,
+                      size_t I, int mask, cudaStream_t s) {
+  const size_t total = O * (size_t)Lout * I;
+  k_band_sweep<T><<<grid_for(total, 256), 256, 0, s>>>(in, out, W, start, width, Lin, Lout, O, I, mask);
+  PMG_CHECK_LAUNCH();
+  return ST_OK;
+}
+
+template <typename T>
+int launch_fill(T* x, size_t n, T v, cudaStream_t s) {
+  k_fill<T><<<grid_for(n, 256), 256, 0, s>>>(x, n, v);
+  PMG_CHECK_LAUNCH();
+  return ST_OK;
+}
+template <typename T>
+int launch_sub_from(const T* x, T* y, size_t n, cudaStream_t s) {
+  k_sub_from<T><<<grid_for(n, 256), 256, 0, s>>>(x, y, n);
+  PMG_CHECK_LAUNCH();
+  return ST_OK;
+}
+template <typename T>
+int launch_add_to(const T* x, T* y, size_t n, cudaStream_t s) {
+  k_add_to<T><<<grid_for(n, 256), 256, 0, s>>>(x, y, n);
+  PMG_CHECK_LAUNCH();
+  return ST_OK;
+}
+template <int DIM, typename T>
+int launch_mask_boundary(T* x, int M, cudaStream_t s) {
+  size_t total = 1;
+  for (int ax = 0; ax < DIM; ++ax) total *= M;
+  k_mask_boundary<DIM, T><<<grid_for(total, 256), 256, 0, s>>>(x, M);
+  PMG_CHECK_LAUNCH();
+  return ST_OK;
+}
+template <typename T>
+int launch_coarse_gemv(const double* Ainv, const int* freeidx, int nf, const T* b, T* x, cudaStream_t s) {
+  const int warps = nf < 152 * 16 ? nf : 152 * 16;
+  k_coarse_gemv<T><<<(warps * 32 + 255) / 256, 256, 0, s>>>(Ainv, freeidx, nf, b, x);
+  PMG_CHECK_LAUNCH();
+  return ST_OK;
+}
+
+template <typename T>
+int launch_fma_chain(T* out, int grid, int block, int iters, cudaStream_t s) {
+  k_fma_chain<T><<<grid, block, 0, s>>>(out, iters, T(0.9999999), T(1e-7));
+  PMG_CHECK_LAUNCH();
+  return ST_OK;
+}
+
+}  // namespace pmg
+
+#define PMG_INSTANTIATE_DIM_T(DIM, T)                                                                       \
+  namespace pmg {                                                                                           \
+  template int upload_tables<DIM, T>(const Tables<double>&, const Tables<float>&, const Rules&);            \
+  template int launch_patch<DIM, T>(int, int, const PatchArgs<T>&, cudaStream_t);                           \
+  template void patch_config<DIM, T>(int, size_t*, int*, int*);                                             \
+  template int launch_lanczos<DIM, T>(int, const LanczosArgs<T>&, cudaStream_t);                            \
+  template int launch_cell_apply<DIM, T>(int, const T*, T*, const T*, int, cudaStream_t);                   \
+  template int launch_geometry<DIM, T>(const double*, const double*, int, int, T*, int*, cudaStream_t);     \
+  template int launch_mask_boundary<DIM, T>(T*, int, cudaStream_t);                                         \
+  }

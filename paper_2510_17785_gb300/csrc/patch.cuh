@@ -1,0 +1,684 @@
+// Vertex-patch smoother with the nested p-multigrid local solver.
+//
+// Paper Section 2.1 and Algorithm 1: for each patch j (the 2^d cells around
+// an interior vertex), Gather u and b (eq. gather), Evaluate the local
+// residual r_j = b_j - Pi_j A_j-bar u_j (eq. main:4), Solve d_j ~ A_j^-1 r_j
+// (eq. main:5) and Scatter u += Pi_j^T d_j (eq. scatter).  Section 3 and
+// Algorithm 2: the local solve is a V-cycle over p-levels p, p/2, ..., 1 with a
+// smoother on each level (damped Jacobi, or Chebyshev iteration on D^-1 A),
+// p-restriction/prolongation by 1D interpolation matrices applied per
+// direction, and the exact 1x1 solve on p = 1.
+//
+// GPU mapping: one CTA handles PPB patches of one colour (patches of one
+// colour share no cell, so their interior DoF sets are disjoint and the
+// in-place scatter is race-free).  Every vector of every p-level lives in
+// shared memory; the operator is the sum-factorised block apply of sf.cuh on
+// the 2^d-cell patch, with the per-point geometry tensors G read from global
+// memory (L1/L2 resident across the applies of one patch).
+#pragma once
+#include "sf.cuh"
+
+namespace pmg {
+
+enum { MODE_SWEEP = 0, MODE_LOCAL = 1 };
+
+__host__ __device__ constexpr int nlevels(int P) { return P <= 1 ? 1 : 1 + nlevels(P >> 1); }
+
+template <typename T>
+struct LevelArgs {
+  const T* G;          // geometry tensors of degree q: [cells][ncomp][(q+1)^d]
+  const T* dinv;       // 1 / diag(A_q) on the global degree-q grid, 0 on Dirichlet
+  const T* bounds;     // [patches][2]: Chebyshev interval (lo, hi), q > 1
+};
+
+template <typename T>
+struct PatchArgs {
+  int N;                       // cells per direction
+  int n_items;                 // patches handled by this launch
+  const int32_t* list;         // patch ids (this colour), or NULL: item i = patch ids_dev[i]
+  const int64_t* ids64;        // patch ids for MODE_LOCAL
+  LevelArgs<T> lv[8];
+  T* u;                        // MODE_SWEEP: degree-p global vector, updated in place
+  const T* b;                  // MODE_SWEEP: right-hand side
+  const T* r_in;               // MODE_LOCAL: [n_items][Ni]
+  T* d_out;                    // MODE_LOCAL: [n_items][Ni]
+  int smoother;                // 0 Chebyshev, 1 Jacobi
+  int cheb_degree;
+  double omega;
+  int n_mg;
+  int* err;                    // device error flag
+};
+
+template <int DIM, int P>
+struct Layout {
+  static constexpr int NL = nlevels(P);
+  __host__ __device__ static constexpr int q(int k) { return P >> k; }
+  __host__ __device__ static constexpr int ni(int k) { return q(k) == 1 ? 1 : ipow(2 * q(k) - 1, DIM); }
+  __host__ __device__ static constexpr int lb(int k) { return q(k) == 1 ? 4 : 6 * ni(k); }
+  __host__ __device__ static constexpr int off(int k) { return k == 0 ? 0 : off(k - 1) + lb(k - 1); }
+  // per-level vectors
+  __host__ __device__ static constexpr int R_(int k) { return off(k); }
+  __host__ __device__ static constexpr int D_(int k) { return off(k) + ni(k); }
+  __host__ __device__ static constexpr int RES(int k) { return off(k) + 2 * ni(k); }
+  __host__ __device__ static constexpr int DIR(int k) { return off(k) + 3 * ni(k); }
+  __host__ __device__ static constexpr int AD(int k) { return q(k) == 1 ? off(k) + 3 : off(k) + 4 * ni(k); }
+  __host__ __device__ static constexpr int DINV(int k) { return q(k) == 1 ? off(k) + 2 : off(k) + 5 * ni(k); }
+  static constexpr int CLOS = off(NL);
+  static constexpr int NN0 = ipow(2 * P + 1, DIM);
+  static constexpr int SCR = CLOS + NN0;
+  static constexpr int SCRATCH = Dims<DIM, 2, P>::SCRATCH;
+  static constexpr int COEF = SCR + SCRATCH;      // per level: 1/theta, c1[1..7], c2[1..7]
+  static constexpr int NCOEF = 16;
+  static constexpr int PS_RAW = COEF + NL * NCOEF;
+  static constexpr int PS = (PS_RAW + 3) & ~3;    // per-patch stride in elements
+};
+
+template <int DIM, int P, typename T>
+struct Config {
+  static constexpr int NT = (DIM == 3) ? 256 : 128;
+  static constexpr size_t bytes_per_patch =
+      sizeof(T) * Layout<DIM, P>::PS + sizeof(int) * ((1 << DIM) + 4);
+  static constexpr int PPB_MAX = (DIM == 3) ? (P <= 2 ? 4 : 1) : (P <= 2 ? 8 : (P <= 4 ? 4 : 2));
+  static constexpr size_t SMEM_LIMIT = 227 * 1024;
+  static constexpr int PPB_FIT = (int)(SMEM_LIMIT / bytes_per_patch);
+  static constexpr int PPB = PPB_FIT < PPB_MAX ? (PPB_FIT < 1 ? 1 : PPB_FIT) : PPB_MAX;
+  static constexpr size_t smem = bytes_per_patch * PPB;
+  static constexpr bool fits = bytes_per_patch <= SMEM_LIMIT;
+};
+
+template <int DIM, int P, typename T, int MODE>
+struct PatchKernel {
+  using L = Layout<DIM, P>;
+  using C = Config<DIM, P, T>;
+  static constexpr int NT = C::NT, PPB = C::PPB, NL = L::NL, PS = L::PS;
+  static constexpr int NCELL = 1 << DIM;
+
+  T* sm;           // per-patch arrays, stride PS
+  int* cells;      // [PPB][NCELL + 4]: global cell ids, then patch id, vertex index parts
+  const PatchArgs<T>* a;
+
+  __device__ T* vec(int pp, int off) const { return sm + pp * PS + off; }
+
+  template <int K>
+  __device__ auto gfun() const {
+    constexpr int q = P >> K;
+    constexpr int stride = Dims<DIM, 2, q>::NCOMP * ipow(q + 1, DIM);
+    const T* G = a->lv[K].G;
+    const int* cl = cells;
+    return [G, cl](int pp, int slot) { return G + (size_t)cl[pp * (NCELL + 4) + slot] * stride; };
+  }
+
+  // out = A_q in on interior vectors of level K
+  template <int K>
+  __device__ void apply_int(int in_off, int out_off) {
+    constexpr int q = P >> K;
+    SF<DIM, 2, q, T, NT, PPB>::template apply<true, false>(vec(0, in_off), PS, vec(0, out_off), PS,
+                                                          vec(0, L::SCR), PS, gfun<K>());
+  }
+
+  // ---- p-transfers between level K (degree qf) and K+1 (degree qc = qf/2)
+  // Prolongation along axis AX on interior nodes: [O][Mc][I] -> [O][Mf][I]
+  template <int K, int AX, bool ACC>
+  __device__ static void prol_item(const T* __restrict__ in, T* __restrict__ out, int item, int Mc, int Mf,
+                                   int I) {
+    constexpr int qf = P >> K, qc = qf >> 1;
+    const int c = item & 1, pi = item >> 1;
+    const int i = pi % I, o = pi / I;
+    const T* src = in + o * Mc * I + i;
+    T* dst = out + o * Mf * I + i;
+    T v[qc + 1];
+#pragma unroll
+    for (int b = 0; b <= qc; ++b) {
+      const int kc = qc * c + b;
+      v[b] = (kc >= 1 && kc <= 2 * qc - 1) ? src[(kc - 1) * I] : T(0);
+    }
+    const int amax = (c == 0) ? qf : qf - 1;
+#pragma unroll
+    for (int a = 1; a <= qf; ++a) {
+      if (a > amax) break;
+      T s = T(0);
+#pragma unroll
+      for (int b = 0; b <= qc; ++b) s += tabE<T>(qf, a, b) * v[b];
+      const int kf = qf * c + a;
+      T* p = dst + (kf - 1) * I;
+      *p = ACC ? *p + s : s;
+    }
+  }
+
+  // Restriction (transpose) along axis AX: [O][Mf][I] -> [O][Mc][I]
+  template <int K>
+  __device__ static void rest_item(const T* __restrict__ in, T* __restrict__ out, int item, int Mc, int Mf,
+                                   int I) {
+    constexpr int qf = P >> K, qc = qf >> 1;
+    const int c = item & 1, pi = item >> 1;
+    const int i = pi % I, o = pi / I;
+    const T* src = in + o * Mf * I + i;
+    T* dst = out + o * Mc * I + i;
+    T f[qf];
+    // fine nodes defined by cell c: c = 0 -> k_f = 1..qf, c = 1 -> k_f = qf+1..2qf-1
+#pragma unroll
+    for (int a = 1; a <= qf; ++a) {
+      const int kf = qf * c + a;
+      f[a - 1] = (kf <= 2 * qf - 1) ? src[(kf - 1) * I] : T(0);
+    }
+    if (c == 0) {
+      T w[qf];
+#pragma unroll
+      for (int a = 1; a < qf; ++a) w[a - 1] = src[(qf + a - 1) * I];
+#pragma unroll
+      for (int b = 1; b <= qc; ++b) {
+        T s = T(0);
+#pragma unroll
+        for (int a = 1; a <= qf; ++a) s += tabE<T>(qf, a, b) * f[a - 1];
+        if (b == qc) {
+#pragma unroll
+          for (int a = 1; a < qf; ++a) s += tabE<T>(qf, a, 0) * w[a - 1];
+        }
+        dst[(b - 1) * I] = s;
+      }
+    } else {
+#pragma unroll
+      for (int b = 1; b < qc; ++b) {
+        T s = T(0);
+#pragma unroll
+        for (int a = 1; a < qf; ++a) s += tabE<T>(qf, a, b) * f[a - 1];
+        dst[(qc + b - 1) * I] = s;
+      }
+    }
+  }
+
+  // r_{K+1} = E^T res_K
+  template <int K>
+  __device__ void restrict_res() {
+    constexpr int qf = P >> K, qc = qf >> 1;
+    constexpr int Mf = 2 * qf - 1, Mc = (qc == 1) ? 1 : 2 * qc - 1;
+    T* t = vec(0, L::SCR);
+    if constexpr (DIM == 3) {
+      coop<NT, PPB, Mf * Mf * 2>([&](int pp, int it) {
+        rest_item<K>(vec(pp, L::RES(K)), t + pp * PS, it, Mc, Mf, 1);
+      });
+      __syncthreads();
+      coop<NT, PPB, Mf * Mc * 2>([&](int pp, int it) {
+        rest_item<K>(t + pp * PS, t + pp * PS + Mf * Mf * Mc, it, Mc, Mf, Mc);
+      });
+      __syncthreads();
+      coop<NT, PPB, Mc * Mc * 2>([&](int pp, int it) {
+        rest_item<K>(t + pp * PS + Mf * Mf * Mc, vec(pp, L::R_(K + 1)), it, Mc, Mf, Mc * Mc);
+      });
+      __syncthreads();
+    } else {
+      coop<NT, PPB, Mf * 2>([&](int pp, int it) { rest_item<K>(vec(pp, L::RES(K)), t + pp * PS, it, Mc, Mf, 1); });
+      __syncthreads();
+      coop<NT, PPB, Mc * 2>([&](int pp, int it) {
+        rest_item<K>(t + pp * PS, vec(pp, L::R_(K + 1)), it, Mc, Mf, Mc);
+      });
+      __syncthreads();
+    }
+  }
+
+  // d_K += E d_{K+1}
+  template <int K>
+  __device__ void prolong_add() {
+    constexpr int qf = P >> K, qc = qf >> 1;
+    constexpr int Mf = 2 * qf - 1, Mc = (qc == 1) ? 1 : 2 * qc - 1;
+    T* t = vec(0, L::SCR);
+    if constexpr (DIM == 3) {
+      coop<NT, PPB, Mc * Mc * 2>([&](int pp, int it) {
+        prol_item<K, 0, false>(vec(pp, L::D_(K + 1)), t + pp * PS, it, Mc, Mf, 1);
+      });
+      __syncthreads();
+      coop<NT, PPB, Mc * Mf * 2>([&](int pp, int it) {
+        prol_item<K, 1, false>(t + pp * PS, t + pp * PS + Mc * Mc * Mf, it, Mc, Mf, Mf);
+      });
+      __syncthreads();
+      coop<NT, PPB, Mf * Mf * 2>([&](int pp, int it) {
+        prol_item<K, 2, true>(t + pp * PS + Mc * Mc * Mf, vec(pp, L::D_(K)), it, Mc, Mf, Mf * Mf);
+      });
+      __syncthreads();
+    } else {
+      coop<NT, PPB, Mc * 2>([&](int pp, int it) {
+        prol_item<K, 0, false>(vec(pp, L::D_(K + 1)), t + pp * PS, it, Mc, Mf, 1);
+      });
+      __syncthreads();
+      coop<NT, PPB, Mf * 2>([&](int pp, int it) {
+        prol_item<K, 1, true>(t + pp * PS, vec(pp, L::D_(K)), it, Mc, Mf, Mf);
+      });
+      __syncthreads();
+    }
+  }
+
+  // ---- smoother on level K: d <- S(d; r), zero_start => d = 0 on entry
+  template <int K>
+  __device__ void smooth(bool zero_start) {
+    constexpr int NI = L::ni(K);
+    if (a->smoother == 1) {   // damped Jacobi, d += omega D^-1 (r - A d)
+      const T om = T(a->omega);
+      if (zero_start) {
+        coop<NT, PPB, NI>([&](int pp, int i) { vec(pp, L::D_(K))[i] = om * vec(pp, L::DINV(K))[i] * vec(pp, L::R_(K))[i]; });
+        __syncthreads();
+      } else {
+        apply_int<K>(L::D_(K), L::AD(K));
+        coop<NT, PPB, NI>([&](int pp, int i) {
+          T* d = vec(pp, L::D_(K));
+          d[i] += om * vec(pp, L::DINV(K))[i] * (vec(pp, L::R_(K))[i] - vec(pp, L::AD(K))[i]);
+        });
+        __syncthreads();
+      }
+      return;
+    }
+    // Chebyshev iteration (three-term recurrence on D^-1 A over [lo, hi])
+    const int deg = a->cheb_degree;
+    if (!zero_start) apply_int<K>(L::D_(K), L::AD(K));
+    coop<NT, PPB, NI>([&](int pp, int i) {
+      const T* cf = vec(pp, L::COEF + K * L::NCOEF);
+      const T rr = zero_start ? vec(pp, L::R_(K))[i] : vec(pp, L::R_(K))[i] - vec(pp, L::AD(K))[i];
+      const T res = vec(pp, L::DINV(K))[i] * rr;
+      const T dir = res * cf[0];
+      vec(pp, L::RES(K))[i] = res;
+      vec(pp, L::DIR(K))[i] = dir;
+      T* d = vec(pp, L::D_(K));
+      d[i] = zero_start ? dir : d[i] + dir;
+    });
+    __syncthreads();
+#pragma unroll 1
+    for (int it = 1; it < deg; ++it) {
+      apply_int<K>(L::DIR(K), L::AD(K));
+      coop<NT, PPB, NI>([&](int pp, int i) {
+        const T* cf = vec(pp, L::COEF + K * L::NCOEF);
+        const T c1 = cf[it], c2 = cf[7 + it];
+        const T res = vec(pp, L::RES(K))[i] - vec(pp, L::DINV(K))[i] * vec(pp, L::AD(K))[i];
+        const T dir = c1 * vec(pp, L::DIR(K))[i] + c2 * res;
+        vec(pp, L::RES(K))[i] = res;
+        vec(pp, L::DIR(K))[i] = dir;
+        vec(pp, L::D_(K))[i] += dir;
+      });
+      __syncthreads();
+    }
+  }
+
+  // ---- Algorithm 2
+  template <int K>
+  __device__ void vcycle(bool zero_start) {
+    constexpr int q = P >> K;
+    if constexpr (q == 1) {
+      coop<NT, PPB, 1>([&](int pp, int) { vec(pp, L::D_(K))[0] = vec(pp, L::R_(K))[0] * vec(pp, L::DINV(K))[0]; });
+      __syncthreads();
+    } else {
+      constexpr int NI = L::ni(K);
+      smooth<K>(zero_start);                                      // pre-smoothing
+      apply_int<K>(L::D_(K), L::AD(K));                           // residual
+      coop<NT, PPB, NI>([&](int pp, int i) { vec(pp, L::RES(K))[i] = vec(pp, L::R_(K))[i] - vec(pp, L::AD(K))[i]; });
+      __syncthreads();
+      restrict_res<K>();                                          // restriction
+      vcycle<K + 1>(true);                                        // coarse correction
+      prolong_add<K>();                                           // prolongation
+      smooth<K>(false);                                           // post-smoothing
+    }
+  }
+
+  // ---- per-patch set-up: ids, cell list, level diagonals, Chebyshev coefficients
+  __device__ void setup_patch(int pp, int item, bool active) {
+    int pid = 0;
+    if (active) {
+      if (MODE == MODE_SWEEP) pid = a->list[item];
+      else pid = (int)a->ids64[item];
+    }
+    const int N = a->N, Nv = N - 1;
+    int v[3] = {1, 1, 1};
+    int rem = pid;
+    for (int ax = 0; ax < DIM; ++ax) { v[ax] = 1 + rem % Nv; rem /= Nv; }
+    int* cl = cells + pp * (NCELL + 4);
+    for (int s = 0; s < NCELL; ++s) {
+      int id = 0, mul = 1;
+      for (int ax = 0; ax < DIM; ++ax) { id += (v[ax] - 1 + ((s >> ax) & 1)) * mul; mul *= N; }
+      cl[s] = active ? id : 0;
+    }
+    cl[NCELL] = pid;
+    cl[NCELL + 1] = active ? 1 : 0;
+    cl[NCELL + 2] = v[0] + (N + 1) * (v[1] + (N + 1) * (DIM == 3 ? v[2] : 0));
+  }
+
+  __device__ int patch_vertex(int pp, int ax) const {
+    const int* cl = cells + pp * (NCELL + 4);
+    const int N = a->N;
+    int vid = cl[NCELL + 2];
+    for (int k = 0; k < ax; ++k) vid /= (N + 1);
+    return vid % (N + 1);
+  }
+
+  // global index on the degree-q grid of patch-local node (k_x, k_y[, k_z]) in [0, 2q]
+  template <int q>
+  __device__ size_t gindex(int pp, int i) const {
+    constexpr int Mq = 2 * q + 1;
+    const int N = a->N;
+    const size_t Mg = (size_t)q * N + 1;
+    size_t idx = 0, mul = 1;
+    int rem = i;
+#pragma unroll
+    for (int ax = 0; ax < DIM; ++ax) {
+      const int k = rem % Mq;
+      rem /= Mq;
+      idx += (size_t)(q * (patch_vertex(pp, ax) - 1) + k) * mul;
+      mul *= Mg;
+    }
+    return idx;
+  }
+  // same for interior node i of the (2q-1)^d interior box
+  template <int q>
+  __device__ size_t gindex_int(int pp, int i) const {
+    constexpr int Mi = 2 * q - 1;
+    const int N = a->N;
+    const size_t Mg = (size_t)q * N + 1;
+    size_t idx = 0, mul = 1;
+    int rem = i;
+#pragma unroll
+    for (int ax = 0; ax < DIM; ++ax) {
+      const int k = rem % Mi;
+      rem /= Mi;
+      idx += (size_t)(q * (patch_vertex(pp, ax) - 1) + 1 + k) * mul;
+      mul *= Mg;
+    }
+    return idx;
+  }
+
+  template <int K>
+  __device__ void load_level() {
+    constexpr int q = P >> K;
+    if constexpr (q == 1) {
+      coop<NT, PPB, 1>([&](int pp, int) {
+        const bool act = cells[pp * (NCELL + 4) + NCELL + 1];
+        const int N = a->N;
+        size_t idx = 0, mul = 1;
+        for (int ax = 0; ax < DIM; ++ax) { idx += (size_t)patch_vertex(pp, ax) * mul; mul *= (N + 1); }
+        vec(pp, L::DINV(K))[0] = act ? a->lv[K].dinv[idx] : T(0);
+      });
+    } else {
+      constexpr int NI = L::ni(K);
+      coop<NT, PPB, NI>([&](int pp, int i) {
+        const bool act = cells[pp * (NCELL + 4) + NCELL + 1];
+        vec(pp, L::DINV(K))[i] = act ? a->lv[K].dinv[gindex_int<q>(pp, i)] : T(0);
+      });
+      // Chebyshev coefficients (FP64 scalars, rounded to T)
+      if (a->smoother == 0) {
+        for (int pp = threadIdx.x; pp < PPB; pp += NT) {
+          const bool act = cells[pp * (NCELL + 4) + NCELL + 1];
+          const int pid = cells[pp * (NCELL + 4) + NCELL];
+          double lo = 1.0, hi = 2.0;
+          if (act) { lo = (double)a->lv[K].bounds[2 * (size_t)pid]; hi = (double)a->lv[K].bounds[2 * (size_t)pid + 1]; }
+          const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
+          const double sigma = theta / delta;
+          double rho = 1.0 / sigma;
+          T* cf = vec(pp, L::COEF + K * L::NCOEF);
+          cf[0] = T(1.0 / theta);
+          for (int i = 1; i < 8; ++i) {
+            const double rn = 1.0 / (2.0 * sigma - rho);
+            cf[i] = T(rn * rho);
+            cf[7 + i] = T((2.0 * rn) / delta);
+            rho = rn;
+          }
+        }
+      }
+    }
+    if constexpr (K + 1 < NL) load_level<K + 1>();
+  }
+
+  __device__ void run() {
+    const int item0 = blockIdx.x * PPB;
+    for (int pp = threadIdx.x; pp < PPB; pp += NT) setup_patch(pp, item0 + pp, item0 + pp < a->n_items);
+    __syncthreads();
+    load_level<0>();
+    constexpr int NI0 = L::ni(0);
+    if (MODE == MODE_SWEEP) {
+      // Gather: closure of u, interior of b
+      constexpr int NN0 = L::NN0;
+      coop<NT, PPB, NN0>([&](int pp, int i) {
+        const bool act = cells[pp * (NCELL + 4) + NCELL + 1];
+        vec(pp, L::CLOS)[i] = act ? a->u[gindex<P>(pp, i)] : T(0);
+      });
+      coop<NT, PPB, NI0>([&](int pp, int i) {
+        const bool act = cells[pp * (NCELL + 4) + NCELL + 1];
+        vec(pp, L::R_(0))[i] = act ? a->b[gindex_int<P>(pp, i)] : T(0);
+      });
+      __syncthreads();
+      // Evaluate: r = b - A u on the patch interior
+      if constexpr (P > 1) {
+        SF<DIM, 2, P, T, NT, PPB>::template apply<false, false>(vec(0, L::CLOS), PS, vec(0, L::AD(0)), PS,
+                                                               vec(0, L::SCR), PS, gfun<0>());
+      } else {
+        SF<DIM, 2, 1, T, NT, PPB>::template apply<false, false>(vec(0, L::CLOS), PS, vec(0, L::AD(0)), PS,
+                                                               vec(0, L::SCR), PS, gfun<0>());
+      }
+      coop<NT, PPB, NI0>([&](int pp, int i) { vec(pp, L::R_(0))[i] -= vec(pp, L::AD(0))[i]; });
+      __syncthreads();
+    } else {
+      coop<NT, PPB, NI0>([&](int pp, int i) {
+        const bool act = cells[pp * (NCELL + 4) + NCELL + 1];
+        vec(pp, L::R_(0))[i] = act ? a->r_in[(size_t)(item0 + pp) * NI0 + i] : T(0);
+      });
+      __syncthreads();
+    }
+    // Solve: N_MG V-cycles, the first from d = 0
+#pragma unroll 1
+    for (int cyc = 0; cyc < a->n_mg; ++cyc) vcycle<0>(cyc == 0);
+    // Scatter
+    if (MODE == MODE_SWEEP) {
+      coop<NT, PPB, NI0>([&](int pp, int i) {
+        const bool act = cells[pp * (NCELL + 4) + NCELL + 1];
+        if (act) a->u[gindex_int<P>(pp, i)] += vec(pp, L::D_(0))[i];
+      });
+    } else {
+      coop<NT, PPB, NI0>([&](int pp, int i) {
+        const bool act = cells[pp * (NCELL + 4) + NCELL + 1];
+        if (act) a->d_out[(size_t)(item0 + pp) * NI0 + i] = vec(pp, L::D_(0))[i];
+      });
+    }
+  }
+};
+
+template <int DIM, int P, typename T, int MODE>
+__global__ void __launch_bounds__(Config<DIM, P, T>::NT) k_patch(const __grid_constant__ PatchArgs<T> args) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using PK = PatchKernel<DIM, P, T, MODE>;
+  PK k;
+  k.sm = reinterpret_cast<T*>(smem_raw);
+  k.cells = reinterpret_cast<int*>(smem_raw + sizeof(T) * (size_t)PK::PS * PK::PPB);
+  k.a = &args;
+  k.run();
+}
+
+// ------------------------------------------------------------------------
+// Lanczos estimate of the extreme eigenvalues of D^-1/2 A_{j,q} D^-1/2 for
+// one p-level K of a batch of patches (one patch per CTA).  Full
+// reorthogonalisation (two classical Gram-Schmidt passes); the basis lives in
+// global scratch [n_items][ksteps][Ni].  Start vector 1 + (u - 1/2), u from
+// counter-based SplitMix64 with counter (patch << 20) | (q << 16) | i.
+// The extreme eigenvalues of the tridiagonal matrix come from Sturm-sequence
+// bisection on its Gershgorin interval.
+template <typename T>
+struct LanczosArgs {
+  int N;
+  int n_items;
+  int first_patch;        // patch id of item 0 (items are consecutive patches)
+  const T* G;
+  const T* dinv;
+  double* V;              // scratch [n_items][ksteps][Ni] (FP64 basis)
+  int ksteps;
+  uint64_t seed;
+  double safety, ratio;
+  double* ritz;           // [patches][2] (theta_min, theta_max), FP64
+  T* bounds;              // [patches][2] (lo, hi)
+};
+
+__device__ __forceinline__ uint64_t splitmix64_dev(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <int NT>
+__device__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NT / 32; ++i) s += red[i];
+    red[NT / 32] = s;
+  }
+  __syncthreads();
+  return red[NT / 32];
+}
+
+__device__ inline int sturm_count_dev(const double* al, const double* be, int n, double x) {
+  int cnt = 0;
+  double d = 1.0;
+  for (int i = 0; i < n; ++i) {
+    d = al[i] - x - (i > 0 ? be[i - 1] * be[i - 1] / d : 0.0);
+    if (d == 0.0) d = -1e-300;
+    if (d < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+template <int DIM, int Q, typename T>
+__global__ void __launch_bounds__(256) k_lanczos(const __grid_constant__ LanczosArgs<T> a) {
+  constexpr int NT = 256;
+  using Dm = Dims<DIM, 2, Q>;
+  constexpr int NI = Dm::NI;
+  constexpr int NCELL = 1 << DIM;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sv = reinterpret_cast<T*>(smem_raw);          // S v input (T)
+  T* sAd = sv + NI;                                  // A output
+  T* scr = sAd + NI;                                 // apply scratch
+  double* dv = reinterpret_cast<double*>(scr + Dm::SCRATCH + 2);   // v (FP64)
+  dv = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(dv) + 15) & ~uintptr_t(15));
+  double* dw = dv + NI;
+  double* ds = dw + NI;                              // sqrt(dinv)
+  double* red = ds + NI;                             // reduction scratch (NT/32 + 1)
+  double* al = red + NT / 32 + 2;                    // alpha[ksteps]
+  double* be = al + 64;                              // beta[ksteps]
+  double* cf = be + 64;                              // CGS coefficients[ksteps]
+  int* cl = reinterpret_cast<int*>(cf + 64);
+
+  const int item = blockIdx.x;
+  if (item >= a.n_items) return;
+  const int pid = a.first_patch + item;
+  const int N = a.N, Nv = N - 1;
+  int v[3] = {1, 1, 1};
+  {
+    int rem = pid;
+    for (int ax = 0; ax < DIM; ++ax) { v[ax] = 1 + rem % Nv; rem /= Nv; }
+  }
+  if (threadIdx.x < NCELL) {
+    int id = 0, mul = 1;
+    for (int ax = 0; ax < DIM; ++ax) { id += (v[ax] - 1 + ((threadIdx.x >> ax) & 1)) * mul; mul *= N; }
+    cl[threadIdx.x] = id;
+  }
+  const size_t Mg = (size_t)Q * N + 1;
+  for (int i = threadIdx.x; i < NI; i += NT) {
+    size_t idx = 0, mul = 1;
+    int rem = i;
+    for (int ax = 0; ax < DIM; ++ax) {
+      const int k = rem % (2 * Q - 1);
+      rem /= (2 * Q - 1);
+      idx += (size_t)(Q * (v[ax] - 1) + 1 + k) * mul;
+      mul *= Mg;
+    }
+    ds[i] = sqrt((double)a.dinv[idx]);
+    const uint64_t ctr = ((uint64_t)pid << 20) | ((uint64_t)Q << 16) | (uint64_t)i;
+    const uint64_t z = splitmix64_dev(a.seed + (ctr + 1ull) * 0x9E3779B97F4A7C15ull);
+    dv[i] = 1.0 + ((double)(z >> 11) * 0x1.0p-53 - 0.5);
+  }
+  __syncthreads();
+  const int k = a.ksteps < NI ? a.ksteps : NI;
+  double* Vb = a.V + (size_t)item * a.ksteps * NI;
+  {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < NI; i += NT) s += dv[i] * dv[i];
+    const double nrm = sqrt(block_sum<NT>(s, red));
+    for (int i = threadIdx.x; i < NI; i += NT) dv[i] /= nrm;
+    __syncthreads();
+  }
+  const int* clp = cl;
+  const T* G = a.G;
+  auto gf = [G, clp](int, int slot) { return G + (size_t)clp[slot] * (Dm::NCOMP * Dm::NGC); };
+  int nal = 0;
+  for (int j = 0; j < k; ++j) {
+    for (int i = threadIdx.x; i < NI; i += NT) {
+      Vb[(size_t)j * NI + i] = dv[i];
+      sv[i] = T(ds[i] * dv[i]);
+    }
+    __syncthreads();
+    SF<DIM, 2, Q, T, NT, 1>::template apply<true, false>(sv, 0, sAd, 0, scr, 0, gf);
+    double s = 0.0;
+    for (int i = threadIdx.x; i < NI; i += NT) {
+      dw[i] = ds[i] * (double)sAd[i];
+      s += dv[i] * dw[i];
+    }
+    const double alpha = block_sum<NT>(s, red);
+    if (threadIdx.x == 0) al[j] = alpha;
+    nal = j + 1;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int m = 0; m <= j; ++m) {
+        double t = 0.0;
+        for (int i = threadIdx.x; i < NI; i += NT) t += Vb[(size_t)m * NI + i] * dw[i];
+        const double c = block_sum<NT>(t, red);
+        if (threadIdx.x == 0) cf[m] = c;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < NI; i += NT) {
+        double w = dw[i];
+        for (int m = 0; m <= j; ++m) w -= cf[m] * Vb[(size_t)m * NI + i];
+        dw[i] = w;
+      }
+      __syncthreads();
+    }
+    if (j == k - 1) break;
+    double t = 0.0;
+    for (int i = threadIdx.x; i < NI; i += NT) t += dw[i] * dw[i];
+    const double b = sqrt(block_sum<NT>(t, red));
+    if (b <= 1e-300) break;
+    if (threadIdx.x == 0) be[j] = b;
+    for (int i = threadIdx.x; i < NI; i += NT) dv[i] = dw[i] / b;
+    __syncthreads();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int n = nal;
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < n; ++i) {
+      const double bl = i > 0 ? fabs(be[i - 1]) : 0.0, br = i < n - 1 ? fabs(be[i]) : 0.0;
+      lo = fmin(lo, al[i] - bl - br);
+      hi = fmax(hi, al[i] + bl + br);
+    }
+    double ext[2];
+    for (int e = 0; e < 2; ++e) {
+      const int kidx = e == 0 ? 0 : n - 1;
+      double x0 = lo, x1 = hi;
+      for (int it = 0; it < 100; ++it) {
+        const double mid = 0.5 * (x0 + x1);
+        if (sturm_count_dev(al, be, n, mid) > kidx) x1 = mid;
+        else x0 = mid;
+      }
+      ext[e] = 0.5 * (x0 + x1);
+    }
+    const double bhi = a.safety * ext[1];
+    const double blo = fmax(ext[0], bhi / a.ratio);
+    a.ritz[2 * (size_t)pid] = ext[0];
+    a.ritz[2 * (size_t)pid + 1] = ext[1];
+    a.bounds[2 * (size_t)pid] = T(blo);
+    a.bounds[2 * (size_t)pid + 1] = T(bhi);
+  }
+}
+
+template <int DIM, int Q, typename T>
+constexpr size_t lanczos_smem() {
+  using Dm = Dims<DIM, 2, Q>;
+  return sizeof(T) * (2 * Dm::NI + Dm::SCRATCH + 2) + 16 +
+         sizeof(double) * (3 * Dm::NI + 256 / 32 + 2 + 3 * 64) + sizeof(int) * 16;
+}
+
+}  // namespace pmg

@@ -1,0 +1,1176 @@
+// C ABI of the library (include/pmg.h): context, structured mesh hierarchy,
+// set-up, patch smoother, local p-MG V-cycle, GMG V-cycle and preconditioned
+// CG.  Every numerical step runs in the kernels of kern_*.cu; this file holds
+// host-side orchestration, the 1D tables and the dense coarse factorisation.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pmg.h"
+#include "basis.h"
+#include "launch.h"
+
+using namespace pmg;
+
+namespace {
+
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+};
+
+struct PLevel {
+  int q = 0;
+  double* G64 = nullptr;
+  float* G32 = nullptr;
+  double* dinv64 = nullptr;
+  float* dinv32 = nullptr;
+  double* bounds64 = nullptr;
+  float* bounds32 = nullptr;
+  double* ritz = nullptr;
+};
+
+struct HLevel {
+  int N = 0;
+  size_t nd = 0;        // (pN+1)^d
+  size_t ncells = 0;
+  size_t npatch = 0;
+  double* coords = nullptr;
+  double* kappa = nullptr;
+  PLevel pl[8];
+  int32_t* colour_list[8] = {nullptr};
+  int ncolour[8] = {0};
+  std::vector<uint8_t> colours;     // host copy, per patch
+  // GMG work vectors
+  double *x64 = nullptr, *b64 = nullptr, *r64 = nullptr;
+  float *x32 = nullptr, *b32 = nullptr, *r32 = nullptr;
+  // transfer tables from level l-1 (fine = this level)
+  double* PW = nullptr;
+  int* Ps = nullptr;
+  double* RW = nullptr;
+  int* Rs = nullptr;
+  int Rwidth = 0;
+};
+
+}  // namespace
+
+struct pmg_ctx {
+  int device = 0;
+  pmg_options opt{};
+  std::string err;
+  int dim = 0, N = 0, p = 0, nlev = 0;
+  int npl = 0;
+  int plevels[8] = {0};
+  std::vector<double> h_coords, h_kappa;
+  std::vector<HLevel> L;
+  bool mesh_ok = false, setup_ok = false;
+  int* d_err = nullptr;
+  // coarse solve
+  double* Ainv = nullptr;
+  int* freeidx = nullptr;
+  int nf = 0;
+  // transfer temporaries (largest), per precision
+  double *t64a = nullptr, *t64b = nullptr;
+  float *t32a = nullptr, *t32b = nullptr;
+  // user-facing FP32 staging buffers (mixed precision API calls)
+  float *s32a = nullptr, *s32b = nullptr;
+  // CG
+  double *cg_x = nullptr, *cg_r = nullptr, *cg_z = nullptr, *cg_p = nullptr, *cg_Ap = nullptr;
+  double *partial = nullptr, *scal = nullptr;
+  double* h_rr = nullptr;   // pinned
+  double *stage_b = nullptr, *stage_u = nullptr;   // device staging for the host-vector solve
+  cudaStream_t stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  int64_t graph_launches_per_iter = 0;   // kernels recorded in one CG iteration graph
+  int64_t launches = 0;                  // kernels launched so far
+  std::vector<void*> allocs;
+};
+
+// ---------------------------------------------------------------------------
+namespace {
+
+int fail(pmg_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CU(...)                                                                     \
+  do {                                                                              \
+    cudaError_t e_ = (__VA_ARGS__);                                                 \
+    if (e_ != cudaSuccess)                                                          \
+      return fail(ctx, PMG_ERR_CUDA, std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define ST(...)                                                                   \
+  do {                                                                            \
+    int s_ = (__VA_ARGS__);                                                       \
+    if (s_ != ST_OK) {                                                            \
+      if (s_ == ST_CUDA) {                                                        \
+        cudaError_t e_ = cudaGetLastError();                                      \
+        return fail(ctx, PMG_ERR_CUDA, std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_)); \
+      }                                                                           \
+      return fail(ctx, s_, std::string(#__VA_ARGS__) + " failed");                \
+    }                                                                             \
+  } while (0)
+
+// ST() plus the number of kernels the call launched
+#define LK(n, ...)                \
+  do {                            \
+    ST(__VA_ARGS__);              \
+    ctx->launches += (n);         \
+  } while (0)
+
+template <typename T>
+int dalloc(pmg_ctx* ctx, T** p, size_t n) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+  if (e != cudaSuccess) return fail(ctx, PMG_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  ctx->allocs.push_back(q);
+  *p = reinterpret_cast<T*>(q);
+  return PMG_OK;
+}
+#define DALLOC(ptr, n)                        \
+  do {                                        \
+    int s_ = dalloc(ctx, &(ptr), (n));        \
+    if (s_ != PMG_OK) return s_;              \
+  } while (0)
+
+size_t ipow_sz(size_t b, int e) {
+  size_t r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
+}
+
+// ---- dispatch on dimension -------------------------------------------------
+template <typename T>
+int patch_launch(pmg_ctx* c, int mode, const PatchArgs<T>& a, cudaStream_t s) {
+  return c->dim == 2 ? launch_patch<2, T>(c->p, mode, a, s) : launch_patch<3, T>(c->p, mode, a, s);
+}
+template <typename T>
+int cell_apply(pmg_ctx* c, int q, const T* u, T* out, const T* G, int N, cudaStream_t s) {
+  return c->dim == 2 ? launch_cell_apply<2, T>(q, u, out, G, N, s) : launch_cell_apply<3, T>(q, u, out, G, N, s);
+}
+template <typename T>
+int mask_boundary(pmg_ctx* c, T* x, int M, cudaStream_t s) {
+  return c->dim == 2 ? launch_mask_boundary<2, T>(x, M, s) : launch_mask_boundary<3, T>(x, M, s);
+}
+
+template <typename T>
+const T* Gof(const PLevel& pl);
+template <>
+const double* Gof<double>(const PLevel& pl) { return pl.G64; }
+template <>
+const float* Gof<float>(const PLevel& pl) { return pl.G32; }
+template <typename T>
+const T* Dinvof(const PLevel& pl);
+template <>
+const double* Dinvof<double>(const PLevel& pl) { return pl.dinv64; }
+template <>
+const float* Dinvof<float>(const PLevel& pl) { return pl.dinv32; }
+template <typename T>
+const T* Boundsof(const PLevel& pl);
+template <>
+const double* Boundsof<double>(const PLevel& pl) { return pl.bounds64; }
+template <>
+const float* Boundsof<float>(const PLevel& pl) { return pl.bounds32; }
+
+template <typename T>
+PatchArgs<T> patch_args(pmg_ctx* c, int level) {
+  PatchArgs<T> a;
+  std::memset(&a, 0, sizeof(a));
+  HLevel& h = c->L[level];
+  a.N = h.N;
+  for (int k = 0; k < c->npl; ++k) {
+    a.lv[k].G = Gof<T>(h.pl[k]);
+    a.lv[k].dinv = Dinvof<T>(h.pl[k]);
+    a.lv[k].bounds = Boundsof<T>(h.pl[k]);
+  }
+  a.smoother = c->opt.smoother;
+  a.cheb_degree = c->opt.cheb_degree;
+  a.omega = c->opt.jacobi_omega;
+  a.n_mg = c->opt.n_mg;
+  a.err = c->d_err;
+  return a;
+}
+
+template <typename T>
+int sweep_colour(pmg_ctx* ctx, int level, int colour, const T* b, T* u, cudaStream_t s) {
+  HLevel& h = ctx->L[level];
+  PatchArgs<T> a = patch_args<T>(ctx, level);
+  a.list = h.colour_list[colour];
+  a.n_items = h.ncolour[colour];
+  a.u = u;
+  a.b = b;
+  LK(1, patch_launch<T>(ctx, MODE_SWEEP, a, s));
+  return PMG_OK;
+}
+
+template <typename T>
+int sweep(pmg_ctx* ctx, int level, const T* b, T* u, bool reverse, cudaStream_t s) {
+  const int nc = 1 << ctx->dim;
+  for (int i = 0; i < nc; ++i) {
+    const int c = reverse ? nc - 1 - i : i;
+    int st = sweep_colour<T>(ctx, level, c, b, u, s);
+    if (st) return st;
+  }
+  return PMG_OK;
+}
+
+// h-transfers by DIM band sweeps
+template <typename T>
+int prolongate(pmg_ctx* ctx, int lf, const T* xc, T* xf, T* ta, T* tb, cudaStream_t s) {
+  HLevel& f = ctx->L[lf];
+  const int p = ctx->p;
+  const int Mc = p * ctx->L[lf - 1].N + 1, Mf = p * f.N + 1;
+  if (ctx->dim == 2) {
+    LK(1, launch_band_sweep<T>(xc, ta, f.PW, f.Ps, p + 1, Mc, Mf, Mc, 1, 1, s));          // x
+    LK(1, launch_band_sweep<T>(ta, xf, f.PW, f.Ps, p + 1, Mc, Mf, 1, Mf, 1, s));          // y
+  } else {
+    LK(1, launch_band_sweep<T>(xc, ta, f.PW, f.Ps, p + 1, Mc, Mf, (size_t)Mc * Mc, 1, 1, s));
+    LK(1, launch_band_sweep<T>(ta, tb, f.PW, f.Ps, p + 1, Mc, Mf, Mc, Mf, 1, s));
+    LK(1, launch_band_sweep<T>(tb, xf, f.PW, f.Ps, p + 1, Mc, Mf, 1, (size_t)Mf * Mf, 1, s));
+  }
+  return PMG_OK;
+}
+
+template <typename T>
+int restrict_(pmg_ctx* ctx, int lf, const T* rf, T* rc, T* ta, T* tb, cudaStream_t s) {
+  HLevel& f = ctx->L[lf];
+  const int p = ctx->p;
+  const int Mc = p * ctx->L[lf - 1].N + 1, Mf = p * f.N + 1;
+  const int w = f.Rwidth;
+  if (ctx->dim == 2) {
+    LK(1, launch_band_sweep<T>(rf, ta, f.RW, f.Rs, w, Mf, Mc, Mf, 1, 1, s));
+    LK(1, launch_band_sweep<T>(ta, rc, f.RW, f.Rs, w, Mf, Mc, 1, Mc, 1, s));
+  } else {
+    LK(1, launch_band_sweep<T>(rf, ta, f.RW, f.Rs, w, Mf, Mc, (size_t)Mf * Mf, 1, 1, s));
+    LK(1, launch_band_sweep<T>(ta, tb, f.RW, f.Rs, w, Mf, Mc, Mf, Mc, 1, s));
+    LK(1, launch_band_sweep<T>(tb, rc, f.RW, f.Rs, w, Mf, Mc, 1, (size_t)Mc * Mc, 1, s));
+  }
+  return PMG_OK;
+}
+
+template <typename T>
+T* Xof(HLevel& h);
+template <>
+double* Xof<double>(HLevel& h) { return h.x64; }
+template <>
+float* Xof<float>(HLevel& h) { return h.x32; }
+template <typename T>
+T* Bof(HLevel& h);
+template <>
+double* Bof<double>(HLevel& h) { return h.b64; }
+template <>
+float* Bof<float>(HLevel& h) { return h.b32; }
+template <typename T>
+T* Rof(HLevel& h);
+template <>
+double* Rof<double>(HLevel& h) { return h.r64; }
+template <>
+float* Rof<float>(HLevel& h) { return h.r32; }
+template <typename T>
+T* TA(pmg_ctx* c);
+template <>
+double* TA<double>(pmg_ctx* c) { return c->t64a; }
+template <>
+float* TA<float>(pmg_ctx* c) { return c->t32a; }
+template <typename T>
+T* TB(pmg_ctx* c);
+template <>
+double* TB<double>(pmg_ctx* c) { return c->t64b; }
+template <>
+float* TB<float>(pmg_ctx* c) { return c->t32b; }
+
+// GMG V-cycle on level l: x_l = B_l b_l (both in the level's work vectors)
+template <typename T>
+int vcycle(pmg_ctx* ctx, int l, cudaStream_t s) {
+  HLevel& h = ctx->L[l];
+  T* x = Xof<T>(h);
+  T* b = Bof<T>(h);
+  LK(1, launch_fill<T>(x, h.nd, T(0), s));
+  if (l == 0) {
+    LK(1, launch_coarse_gemv<T>(ctx->Ainv, ctx->freeidx, ctx->nf, b, x, s));
+    return PMG_OK;
+  }
+  int st = sweep<T>(ctx, l, b, x, false, s);                     // pre-smoothing
+  if (st) return st;
+  T* r = Rof<T>(h);
+  LK(1 + (1 << ctx->dim), cell_apply<T>(ctx, ctx->p, x, r, Gof<T>(h.pl[0]), h.N, s));   // r = b - A x
+  LK(1, launch_sub_from<T>(b, r, h.nd, s));
+  HLevel& hc = ctx->L[l - 1];
+  st = restrict_<T>(ctx, l, r, Bof<T>(hc), TA<T>(ctx), TB<T>(ctx), s);
+  if (st) return st;
+  st = vcycle<T>(ctx, l - 1, s);
+  if (st) return st;
+  st = prolongate<T>(ctx, l, Xof<T>(hc), r, TA<T>(ctx), TB<T>(ctx), s);
+  if (st) return st;
+  LK(1, launch_add_to<T>(r, x, h.nd, s));
+  return sweep<T>(ctx, l, b, x, true, s);                         // post-smoothing
+}
+
+// z = M r on the finest level (FP64 in and out)
+int precondition(pmg_ctx* ctx, const double* r, double* z, cudaStream_t s) {
+  const int lf = ctx->nlev - 1;
+  HLevel& h = ctx->L[lf];
+  if (ctx->opt.precision == PMG_PREC_MIXED) {
+    LK(1, launch_cast_d2f(r, h.b32, h.nd, s));
+    int st = vcycle<float>(ctx, lf, s);
+    if (st) return st;
+    LK(1, launch_cast_f2d(h.x32, z, h.nd, s));
+  } else {
+    CU(cudaMemcpyAsync(h.b64, r, h.nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    int st = vcycle<double>(ctx, lf, s);
+    if (st) return st;
+    CU(cudaMemcpyAsync(z, h.x64, h.nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  return PMG_OK;
+}
+
+// ---- host dense Cholesky and inverse of the coarse matrix -------------------
+bool cholesky_inverse(std::vector<double>& A, int n) {
+  // A (n x n, row-major, SPD) -> lower factor L in place
+  for (int j = 0; j < n; ++j) {
+    double d = A[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) d -= A[(size_t)j * n + k] * A[(size_t)j * n + k];
+    if (!(d > 0.0)) return false;
+    d = std::sqrt(d);
+    A[(size_t)j * n + j] = d;
+#pragma omp parallel for schedule(static)
+    for (int i = j + 1; i < n; ++i) {
+      double s = A[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) s -= A[(size_t)i * n + k] * A[(size_t)j * n + k];
+      A[(size_t)i * n + j] = s / d;
+    }
+  }
+  // inverse: solve L L^T X = I column by column
+  std::vector<double> X((size_t)n * n, 0.0);
+#pragma omp parallel for schedule(dynamic)
+  for (int c = 0; c < n; ++c) {
+    std::vector<double> y(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) s -= A[(size_t)i * n + k] * y[k];
+      y[i] = s / A[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double s = y[i];
+      for (int k = i + 1; k < n; ++k) s -= A[(size_t)k * n + i] * y[k];
+      y[i] = s / A[(size_t)i * n + i];
+    }
+    for (int i = 0; i < n; ++i) X[(size_t)i * n + c] = y[i];
+  }
+  A.swap(X);
+  return true;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+void pmg_default_options(pmg_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->smoother = PMG_SMOOTHER_CHEBYSHEV;
+  o->cheb_degree = 3;
+  o->jacobi_omega = 0.5;
+  o->n_mg = 1;
+  o->bounds = PMG_BOUNDS_LANCZOS;
+  o->lanczos_steps = 16;
+  o->bound_safety = 1.1;
+  o->bound_ratio = 10.0;
+  o->fixed_lo = 0.2;
+  o->fixed_hi = 2.0;
+  o->seed = 0;
+  o->precision = PMG_PREC_FP64;
+}
+
+int pmg_create(int device, const pmg_options* opt, pmg_ctx** out) {
+  if (!out) return PMG_ERR_ARG;
+  *out = nullptr;
+  pmg_ctx* ctx = new pmg_ctx();
+  ctx->device = device;
+  if (opt) ctx->opt = *opt;
+  else pmg_default_options(&ctx->opt);
+  const pmg_options& o = ctx->opt;
+  if (o.cheb_degree < 1 || o.cheb_degree > 8 || o.n_mg < 1 || o.lanczos_steps < 1 || o.lanczos_steps > 64 ||
+      (o.smoother != 0 && o.smoother != 1) || (o.precision != 0 && o.precision != 1) || o.bounds < 0 ||
+      o.bounds > 2 || !(o.bound_safety > 0) || !(o.bound_ratio >= 1)) {
+    delete ctx;
+    return PMG_ERR_ARG;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) {
+    delete ctx;
+    return PMG_ERR_CUDA;
+  }
+  if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess || cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_rr, sizeof(double)) != cudaSuccess) {
+    delete ctx;
+    return PMG_ERR_CUDA;
+  }
+  *out = ctx;
+  return PMG_OK;
+}
+
+int pmg_destroy(pmg_ctx* ctx) {
+  if (!ctx) return PMG_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  for (void* p : ctx->allocs) cudaFree(p);
+  if (ctx->d_err) cudaFree(ctx->d_err);
+  if (ctx->h_rr) cudaFreeHost(ctx->h_rr);
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return PMG_OK;
+}
+
+const char* pmg_last_error(const pmg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int pmg_mesh_structured(pmg_ctx* ctx, int dim, int N, int p, int n_levels, const double* coords,
+                        const double* kappa) {
+  if (!ctx) return PMG_ERR_ARG;
+  if (dim != 2 && dim != 3) return fail(ctx, PMG_ERR_ARG, "dim must be 2 or 3");
+  if (p < 1 || p > 8) return fail(ctx, PMG_ERR_UNSUPPORTED, "degree must be in 1..8");
+  if (n_levels < 1 || N < 2 || !coords || !kappa) return fail(ctx, PMG_ERR_ARG, "bad mesh arguments");
+  if (N % (1 << (n_levels - 1)) != 0) return fail(ctx, PMG_ERR_ARG, "N must be divisible by 2^(n_levels-1)");
+  if (N / (1 << (n_levels - 1)) < 2) return fail(ctx, PMG_ERR_ARG, "coarsest mesh needs at least 2 cells per direction");
+  if (ctx->mesh_ok) return fail(ctx, PMG_ERR_ARG, "mesh already uploaded");
+  size_t sz, pb;
+  int ppb, nt;
+  if (dim == 2) patch_config<2, double>(p, &sz, &ppb, &nt);
+  else patch_config<3, double>(p, &sz, &ppb, &nt);
+  size_t sz32;
+  if (dim == 2) patch_config<2, float>(p, &sz32, &ppb, &nt);
+  else patch_config<3, float>(p, &sz32, &ppb, &nt);
+  (void)pb;
+  if ((ctx->opt.precision == PMG_PREC_FP64 && sz == 0) || sz32 == 0)
+    return fail(ctx, PMG_ERR_UNSUPPORTED, "patch working set of this degree does not fit in shared memory in this precision");
+  ctx->dim = dim;
+  ctx->N = N;
+  ctx->p = p;
+  ctx->nlev = n_levels;
+  ctx->npl = 0;
+  for (int q = p; q >= 1; q >>= 1) ctx->plevels[ctx->npl++] = q;
+  const size_t nv = ipow_sz(N + 1, dim), nc = ipow_sz(N, dim);
+  ctx->h_coords.assign(coords, coords + nv * dim);
+  ctx->h_kappa.assign(kappa, kappa + nc);
+  for (size_t i = 0; i < nc; ++i)
+    if (!std::isfinite(kappa[i]) || !(kappa[i] > 0)) return fail(ctx, PMG_ERR_ARG, "kappa must be positive and finite");
+  for (size_t i = 0; i < nv * dim; ++i)
+    if (!std::isfinite(coords[i])) return fail(ctx, PMG_ERR_ARG, "coordinates must be finite");
+  ctx->mesh_ok = true;
+  return PMG_OK;
+}
+
+int pmg_setup(pmg_ctx* ctx) {
+  if (!ctx || !ctx->mesh_ok) return fail(ctx, PMG_ERR_ARG, "upload a mesh first");
+  if (ctx->setup_ok) return fail(ctx, PMG_ERR_ARG, "already set up");
+  CU(cudaSetDevice(ctx->device));
+  const int d = ctx->dim, p = ctx->p;
+  cudaStream_t s = ctx->stream;
+  {
+    Tables<double> t64;
+    Tables<float> t32;
+    Rules r;
+    build_tables(t64, t32, r);
+    ST(upload_tables<2, double>(t64, t32, r));
+    ST(upload_tables<3, double>(t64, t32, r));
+    ST(upload_tables<2, float>(t64, t32, r));
+    ST(upload_tables<3, float>(t64, t32, r));
+  }
+  const bool mixed = ctx->opt.precision == PMG_PREC_MIXED;
+  // ---- levels: coordinates (even-index subsampling), kappa (mean of children)
+  ctx->L.assign(ctx->nlev, HLevel());
+  std::vector<double> X = ctx->h_coords, K = ctx->h_kappa;
+  for (int l = ctx->nlev - 1; l >= 0; --l) {
+    HLevel& h = ctx->L[l];
+    h.N = ctx->N >> (ctx->nlev - 1 - l);
+    const int Nl = h.N;
+    if (l < ctx->nlev - 1) {
+      const int Nf = 2 * Nl;
+      std::vector<double> Xc(ipow_sz(Nl + 1, d) * d), Kc(ipow_sz(Nl, d), 0.0);
+      for (size_t v = 0; v < ipow_sz(Nl + 1, d); ++v) {
+        size_t rem = v, fid = 0, mul = 1;
+        for (int ax = 0; ax < d; ++ax) {
+          const size_t i = rem % (Nl + 1);
+          rem /= (Nl + 1);
+          fid += 2 * i * mul;
+          mul *= (Nf + 1);
+        }
+        for (int k = 0; k < d; ++k) Xc[v * d + k] = X[fid * d + k];
+      }
+      for (size_t c = 0; c < ipow_sz(Nl, d); ++c) {
+        size_t rem = c;
+        int ci[3] = {0, 0, 0};
+        for (int ax = 0; ax < d; ++ax) { ci[ax] = (int)(rem % Nl); rem /= Nl; }
+        double sum = 0.0;
+        for (int ch = 0; ch < (1 << d); ++ch) {
+          size_t fid = 0, mul = 1;
+          for (int ax = 0; ax < d; ++ax) { fid += (size_t)(2 * ci[ax] + ((ch >> ax) & 1)) * mul; mul *= Nf; }
+          sum += K[fid];
+        }
+        Kc[c] = sum / (1 << d);
+      }
+      X.swap(Xc);
+      K.swap(Kc);
+    }
+    h.nd = ipow_sz((size_t)p * Nl + 1, d);
+    h.ncells = ipow_sz(Nl, d);
+    h.npatch = ipow_sz(Nl - 1, d);
+    DALLOC(h.coords, X.size());
+    DALLOC(h.kappa, K.size());
+    CU(cudaMemcpy(h.coords, X.data(), X.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h.kappa, K.data(), K.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  // ---- geometry tensors and level diagonals
+  double* diag = nullptr;
+  DALLOC(diag, ctx->L.back().nd);
+  for (int l = 0; l < ctx->nlev; ++l) {
+    HLevel& h = ctx->L[l];
+    for (int k = 0; k < ctx->npl; ++k) {
+      PLevel& pl = h.pl[k];
+      pl.q = ctx->plevels[k];
+      const int q = pl.q;
+      const size_t ng = h.ncells * (size_t)(d * (d + 1) / 2) * ipow_sz(q + 1, d);
+      const size_t ndq = ipow_sz((size_t)q * h.N + 1, d);
+      DALLOC(pl.G64, ng);
+      DALLOC(pl.dinv64, ndq);
+      DALLOC(pl.dinv32, ndq);
+      if (d == 2) ST(launch_geometry<2, double>(h.coords, h.kappa, h.N, q, pl.G64, ctx->d_err, s));
+      else ST(launch_geometry<3, double>(h.coords, h.kappa, h.N, q, pl.G64, ctx->d_err, s));
+      if (mixed) {
+        DALLOC(pl.G32, ng);
+        if (d == 2) ST(launch_geometry<2, float>(h.coords, h.kappa, h.N, q, pl.G32, ctx->d_err, s));
+        else ST(launch_geometry<3, float>(h.coords, h.kappa, h.N, q, pl.G32, ctx->d_err, s));
+      }
+      if (d == 2) ST(launch_diag<2>(pl.G64, h.N, q, diag, pl.dinv64, pl.dinv32, s));
+      else ST(launch_diag<3>(pl.G64, h.N, q, diag, pl.dinv64, pl.dinv32, s));
+      DALLOC(pl.bounds64, 2 * std::max<size_t>(h.npatch, 1));
+      DALLOC(pl.bounds32, 2 * std::max<size_t>(h.npatch, 1));
+      DALLOC(pl.ritz, 2 * std::max<size_t>(h.npatch, 1));
+      CU(cudaMemsetAsync(pl.ritz, 0, 2 * std::max<size_t>(h.npatch, 1) * sizeof(double), s));
+    }
+  }
+  int herr = 0;
+  CU(cudaMemcpyAsync(&herr, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  if (herr) return fail(ctx, PMG_ERR_DEGENERATE, "det J <= 0 at a Gauss point of some cell");
+  // ---- patches and colours (colour bit k = parity of the vertex index k)
+  for (int l = 0; l < ctx->nlev; ++l) {
+    HLevel& h = ctx->L[l];
+    const int Nv = h.N - 1;
+    std::vector<std::vector<int32_t>> lists(1 << d);
+    h.colours.assign(h.npatch, 0);
+    for (size_t j = 0; j < h.npatch; ++j) {
+      size_t rem = j;
+      int c = 0;
+      for (int ax = 0; ax < d; ++ax) {
+        const int v = 1 + (int)(rem % Nv);
+        rem /= Nv;
+        c |= (v & 1) << ax;
+      }
+      h.colours[j] = (uint8_t)c;
+      lists[c].push_back((int32_t)j);
+    }
+    for (int c = 0; c < (1 << d); ++c) {
+      h.ncolour[c] = (int)lists[c].size();
+      DALLOC(h.colour_list[c], lists[c].size());
+      if (!lists[c].empty())
+        CU(cudaMemcpy(h.colour_list[c], lists[c].data(), lists[c].size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
+  }
+  // ---- work vectors and transfer tables
+  size_t tmax = 1;
+  for (int l = 0; l < ctx->nlev; ++l) {
+    HLevel& h = ctx->L[l];
+    DALLOC(h.x64, h.nd);
+    DALLOC(h.b64, h.nd);
+    DALLOC(h.r64, h.nd);
+    if (mixed) {
+      DALLOC(h.x32, h.nd);
+      DALLOC(h.b32, h.nd);
+      DALLOC(h.r32, h.nd);
+    }
+    if (l > 0) {
+      const int Mc = p * ctx->L[l - 1].N + 1, Mf = p * h.N + 1;
+      tmax = std::max(tmax, ipow_sz(Mf, d - 1) * Mc);
+      tmax = std::max(tmax, ipow_sz(Mc, d - 1) * Mf);
+      std::vector<double> W, RW;
+      std::vector<int> S, RS;
+      h_prolongation_band(p, ctx->L[l - 1].N, W, S);
+      h_restriction_band(p, ctx->L[l - 1].N, RW, RS, h.Rwidth);
+      DALLOC(h.PW, W.size());
+      DALLOC(h.Ps, S.size());
+      DALLOC(h.RW, RW.size());
+      DALLOC(h.Rs, RS.size());
+      CU(cudaMemcpy(h.PW, W.data(), W.size() * sizeof(double), cudaMemcpyHostToDevice));
+      CU(cudaMemcpy(h.Ps, S.data(), S.size() * sizeof(int), cudaMemcpyHostToDevice));
+      CU(cudaMemcpy(h.RW, RW.data(), RW.size() * sizeof(double), cudaMemcpyHostToDevice));
+      CU(cudaMemcpy(h.Rs, RS.data(), RS.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
+  }
+  DALLOC(ctx->t64a, tmax);
+  DALLOC(ctx->t64b, tmax);
+  if (mixed) {
+    DALLOC(ctx->t32a, tmax);
+    DALLOC(ctx->t32b, tmax);
+  }
+  {
+    const size_t nfin = ctx->L.back().nd;
+    size_t nloc = 0;
+    for (int l = 0; l < ctx->nlev; ++l)
+      nloc = std::max(nloc, ctx->L[l].npatch * ipow_sz(2 * p - 1, d));
+    DALLOC(ctx->s32a, std::max(nfin, nloc));
+    DALLOC(ctx->s32b, std::max(nfin, nloc));
+  }
+  // ---- coarse matrix by applying the coarsest operator to unit vectors
+  {
+    HLevel& h = ctx->L[0];
+    const int M = p * h.N + 1;
+    std::vector<int> fidx;
+    for (size_t i = 0; i < h.nd; ++i) {
+      size_t rem = i;
+      bool bnd = false;
+      for (int ax = 0; ax < d; ++ax) {
+        const int k = (int)(rem % M);
+        rem /= M;
+        bnd = bnd || k == 0 || k == M - 1;
+      }
+      if (!bnd) fidx.push_back((int)i);
+    }
+    const int nf = (int)fidx.size();
+    ctx->nf = nf;
+    std::vector<double> A((size_t)nf * nf, 0.0), col(h.nd);
+    for (int j = 0; j < nf; ++j) {
+      CU(cudaMemsetAsync(h.x64, 0, h.nd * sizeof(double), s));
+      const double one = 1.0;
+      CU(cudaMemcpyAsync(h.x64 + fidx[j], &one, sizeof(double), cudaMemcpyHostToDevice, s));
+      LK(1 + (1 << ctx->dim), cell_apply<double>(ctx, p, h.x64, h.r64, h.pl[0].G64, h.N, s));
+      CU(cudaMemcpyAsync(col.data(), h.r64, h.nd * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+      for (int i = 0; i < nf; ++i) A[(size_t)i * nf + j] = col[fidx[i]];
+    }
+    // symmetrise the rounding
+    for (int i = 0; i < nf; ++i)
+      for (int j = 0; j < i; ++j) {
+        const double v = 0.5 * (A[(size_t)i * nf + j] + A[(size_t)j * nf + i]);
+        A[(size_t)i * nf + j] = A[(size_t)j * nf + i] = v;
+      }
+    if (!cholesky_inverse(A, nf)) return fail(ctx, PMG_ERR_NUMERIC, "coarse matrix is not positive definite");
+    DALLOC(ctx->Ainv, A.size());
+    DALLOC(ctx->freeidx, fidx.size());
+    CU(cudaMemcpy(ctx->Ainv, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(ctx->freeidx, fidx.data(), fidx.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
+  // ---- CG vectors
+  {
+    const size_t n = ctx->L.back().nd;
+    DALLOC(ctx->cg_x, n);
+    DALLOC(ctx->cg_r, n);
+    DALLOC(ctx->cg_z, n);
+    DALLOC(ctx->cg_p, n);
+    DALLOC(ctx->cg_Ap, n);
+    DALLOC(ctx->stage_b, n);
+    DALLOC(ctx->stage_u, n);
+    DALLOC(ctx->partial, DOT_BLOCKS);
+    DALLOC(ctx->scal, S_NSLOT);
+  }
+  ctx->setup_ok = true;
+  // ---- Chebyshev bounds
+  int st = pmg_compute_bounds(ctx, ctx->opt.bounds);
+  if (st) {
+    ctx->setup_ok = false;
+    return st;
+  }
+  // warm-up V-cycle on a zero vector: every kernel of the preconditioner runs
+  // once (and gets its shared-memory attribute) before any graph capture
+  CU(cudaMemsetAsync(ctx->cg_r, 0, ctx->L.back().nd * sizeof(double), s));
+  st = precondition(ctx, ctx->cg_r, ctx->cg_z, s);
+  if (st) {
+    ctx->setup_ok = false;
+    return st;
+  }
+  CU(cudaStreamSynchronize(s));
+  return PMG_OK;
+}
+
+int pmg_compute_bounds(pmg_ctx* ctx, int source) {
+  if (!ctx || !ctx->setup_ok) return fail(ctx, PMG_ERR_ARG, "not set up");
+  cudaStream_t s = ctx->stream;
+  const int d = ctx->dim;
+  if (source == PMG_BOUNDS_USER) return PMG_OK;
+  for (int l = 0; l < ctx->nlev; ++l) {
+    HLevel& h = ctx->L[l];
+    if (h.npatch == 0) continue;
+    for (int k = 0; k < ctx->npl; ++k) {
+      PLevel& pl = h.pl[k];
+      if (pl.q == 1) continue;
+      if (source == PMG_BOUNDS_FIXED) {
+        std::vector<double> v(2 * h.npatch);
+        for (size_t j = 0; j < h.npatch; ++j) { v[2 * j] = ctx->opt.fixed_lo; v[2 * j + 1] = ctx->opt.fixed_hi; }
+        CU(cudaMemcpy(pl.bounds64, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice));
+        LK(1, launch_cast_d2f(pl.bounds64, pl.bounds32, v.size(), s));
+        continue;
+      }
+      if (source != PMG_BOUNDS_LANCZOS) return fail(ctx, PMG_ERR_ARG, "unknown bounds source");
+      const size_t ni = ipow_sz(2 * pl.q - 1, d);
+      const size_t chunk = std::max<size_t>(1, std::min<size_t>(h.npatch, (size_t)(512u << 20) / (ctx->opt.lanczos_steps * ni * 8)));
+      double* V = nullptr;
+      DALLOC(V, chunk * ctx->opt.lanczos_steps * ni);
+      for (size_t j0 = 0; j0 < h.npatch; j0 += chunk) {
+        const int n = (int)std::min(chunk, h.npatch - j0);
+        LanczosArgs<double> a;
+        a.N = h.N;
+        a.n_items = n;
+        a.first_patch = (int)j0;
+        a.G = pl.G64;
+        a.dinv = pl.dinv64;
+        a.V = V;
+        a.ksteps = ctx->opt.lanczos_steps;
+        a.seed = ctx->opt.seed;
+        a.safety = ctx->opt.bound_safety;
+        a.ratio = ctx->opt.bound_ratio;
+        a.ritz = pl.ritz;
+        a.bounds = pl.bounds64;
+        int r = d == 2 ? launch_lanczos<2, double>(pl.q, a, s) : launch_lanczos<3, double>(pl.q, a, s);
+        if (r == ST_UNSUPPORTED) {
+          // the FP64 working set does not fit: FP32 operator, FP64 Lanczos vectors
+          LanczosArgs<float> b;
+          b.N = a.N;
+          b.n_items = a.n_items;
+          b.first_patch = a.first_patch;
+          b.G = pl.G32;
+          b.dinv = pl.dinv32;
+          b.V = V;
+          b.ksteps = a.ksteps;
+          b.seed = a.seed;
+          b.safety = a.safety;
+          b.ratio = a.ratio;
+          b.ritz = pl.ritz;
+          b.bounds = pl.bounds32;
+          if (!pl.G32) return fail(ctx, PMG_ERR_UNSUPPORTED, "Lanczos at this degree needs the FP32 geometry (mixed precision)");
+          ST(d == 2 ? launch_lanczos<2, float>(pl.q, b, s) : launch_lanczos<3, float>(pl.q, b, s));
+          LK(1, launch_cast_f2d(pl.bounds32, pl.bounds64, 2 * h.npatch, s));
+        } else {
+          ST(r);
+        }
+      }
+      CU(cudaStreamSynchronize(s));
+      LK(1, launch_cast_d2f(pl.bounds64, pl.bounds32, 2 * h.npatch, s));
+    }
+  }
+  CU(cudaStreamSynchronize(s));
+  return PMG_OK;
+}
+
+int pmg_num_dofs(const pmg_ctx* ctx, int level, int64_t* total, int64_t* n_free) {
+  if (!ctx || !ctx->mesh_ok || level < 0 || level >= ctx->nlev) return PMG_ERR_ARG;
+  const int Nl = ctx->N >> (ctx->nlev - 1 - level);
+  if (total) *total = (int64_t)ipow_sz((size_t)ctx->p * Nl + 1, ctx->dim);
+  if (n_free) *n_free = (int64_t)ipow_sz((size_t)ctx->p * Nl - 1, ctx->dim);
+  return PMG_OK;
+}
+
+int pmg_num_patches(const pmg_ctx* ctx, int level, int64_t* n_patches, int* n_colours) {
+  if (!ctx || !ctx->mesh_ok || level < 0 || level >= ctx->nlev) return PMG_ERR_ARG;
+  const int Nl = ctx->N >> (ctx->nlev - 1 - level);
+  if (n_patches) *n_patches = (int64_t)ipow_sz(Nl - 1, ctx->dim);
+  if (n_colours) *n_colours = 1 << ctx->dim;
+  return PMG_OK;
+}
+
+int pmg_p_levels(const pmg_ctx* ctx, int* degrees, int* n) {
+  if (!ctx || !ctx->mesh_ok || !n) return PMG_ERR_ARG;
+  *n = ctx->npl;
+  if (degrees)
+    for (int k = 0; k < ctx->npl; ++k) degrees[k] = ctx->plevels[k];
+  return PMG_OK;
+}
+
+static int check_level(pmg_ctx* ctx, int level) {
+  if (!ctx) return PMG_ERR_ARG;
+  if (!ctx->setup_ok) return fail(ctx, PMG_ERR_ARG, "call pmg_setup first");
+  if (level < 0 || level >= ctx->nlev) return fail(ctx, PMG_ERR_ARG, "level out of range");
+  return PMG_OK;
+}
+
+int pmg_apply(pmg_ctx* ctx, int level, const double* u, double* Au, void* stream) {
+  int st = check_level(ctx, level);
+  if (st) return st;
+  if (!u || !Au) return fail(ctx, PMG_ERR_ARG, "null vector");
+  HLevel& h = ctx->L[level];
+  LK(1 + (1 << ctx->dim), cell_apply<double>(ctx, ctx->p, u, Au, h.pl[0].G64, h.N, (cudaStream_t)stream));
+  return PMG_OK;
+}
+
+int pmg_patch_smooth_colour(pmg_ctx* ctx, int level, int colour, const double* b, double* u, void* stream) {
+  int st = check_level(ctx, level);
+  if (st) return st;
+  if (colour < 0 || colour >= (1 << ctx->dim)) return fail(ctx, PMG_ERR_ARG, "colour out of range");
+  if (!b || !u) return fail(ctx, PMG_ERR_ARG, "null vector");
+  cudaStream_t s = (cudaStream_t)stream;
+  HLevel& h = ctx->L[level];
+  if (ctx->opt.precision == PMG_PREC_MIXED) {
+    LK(1, launch_cast_d2f(b, ctx->s32a, h.nd, s));
+    LK(1, launch_cast_d2f(u, ctx->s32b, h.nd, s));
+    st = sweep_colour<float>(ctx, level, colour, ctx->s32a, ctx->s32b, s);
+    if (st) return st;
+    LK(1, launch_cast_f2d(ctx->s32b, u, h.nd, s));
+    return PMG_OK;
+  }
+  return sweep_colour<double>(ctx, level, colour, b, u, s);
+}
+
+int pmg_patch_smooth(pmg_ctx* ctx, int level, const double* b, double* u, int n_sweeps, int reverse, void* stream) {
+  int st = check_level(ctx, level);
+  if (st) return st;
+  if (!b || !u || n_sweeps < 0) return fail(ctx, PMG_ERR_ARG, "bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  HLevel& h = ctx->L[level];
+  if (ctx->opt.precision == PMG_PREC_MIXED) {
+    LK(1, launch_cast_d2f(b, ctx->s32a, h.nd, s));
+    LK(1, launch_cast_d2f(u, ctx->s32b, h.nd, s));
+    for (int i = 0; i < n_sweeps; ++i) {
+      st = sweep<float>(ctx, level, ctx->s32a, ctx->s32b, reverse != 0, s);
+      if (st) return st;
+    }
+    LK(1, launch_cast_f2d(ctx->s32b, u, h.nd, s));
+    return PMG_OK;
+  }
+  for (int i = 0; i < n_sweeps; ++i) {
+    st = sweep<double>(ctx, level, b, u, reverse != 0, s);
+    if (st) return st;
+  }
+  return PMG_OK;
+}
+
+int pmg_local_vcycle(pmg_ctx* ctx, int level, int64_t n, const int64_t* ids, const double* r, double* dout,
+                     int n_cycles, void* stream) {
+  int st = check_level(ctx, level);
+  if (st) return st;
+  if (n < 0 || (n > 0 && (!ids || !r || !dout)) || n_cycles < 1) return fail(ctx, PMG_ERR_ARG, "bad arguments");
+  if (n == 0) return PMG_OK;
+  HLevel& h = ctx->L[level];
+  if ((size_t)n > h.npatch) return fail(ctx, PMG_ERR_ARG, "more patches than the level has");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t ni = ipow_sz(2 * ctx->p - 1, ctx->dim);
+  if (ctx->opt.precision == PMG_PREC_MIXED) {
+    PatchArgs<float> a = patch_args<float>(ctx, level);
+    a.n_mg = n_cycles;
+    a.ids64 = ids;
+    a.n_items = (int)n;
+    LK(1, launch_cast_d2f(r, ctx->s32a, (size_t)n * ni, s));
+    a.r_in = ctx->s32a;
+    a.d_out = ctx->s32b;
+    LK(1, patch_launch<float>(ctx, MODE_LOCAL, a, s));
+    LK(1, launch_cast_f2d(ctx->s32b, dout, (size_t)n * ni, s));
+    return PMG_OK;
+  }
+  PatchArgs<double> a = patch_args<double>(ctx, level);
+  a.n_mg = n_cycles;
+  a.ids64 = ids;
+  a.n_items = (int)n;
+  a.r_in = r;
+  a.d_out = dout;
+  LK(1, patch_launch<double>(ctx, MODE_LOCAL, a, s));
+  return PMG_OK;
+}
+
+int pmg_get_bounds(pmg_ctx* ctx, int level, double* lohi) {
+  int st = check_level(ctx, level);
+  if (st) return st;
+  HLevel& h = ctx->L[level];
+  std::vector<double> out(2 * h.npatch * ctx->npl, 0.0), tmp(2 * h.npatch);
+  CU(cudaStreamSynchronize(ctx->stream));
+  for (int k = 0; k < ctx->npl; ++k) {
+    if (h.pl[k].q == 1 || h.npatch == 0) continue;
+    CU(cudaMemcpy(tmp.data(), h.pl[k].bounds64, tmp.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (size_t j = 0; j < h.npatch; ++j) {
+      out[(j * ctx->npl + k) * 2] = tmp[2 * j];
+      out[(j * ctx->npl + k) * 2 + 1] = tmp[2 * j + 1];
+    }
+  }
+  std::memcpy(lohi, out.data(), out.size() * sizeof(double));
+  return PMG_OK;
+}
+
+int pmg_get_ritz(pmg_ctx* ctx, int level, double* tm) {
+  int st = check_level(ctx, level);
+  if (st) return st;
+  HLevel& h = ctx->L[level];
+  std::vector<double> out(2 * h.npatch * ctx->npl, 0.0), tmp(2 * h.npatch);
+  CU(cudaStreamSynchronize(ctx->stream));
+  for (int k = 0; k < ctx->npl; ++k) {
+    if (h.pl[k].q == 1 || h.npatch == 0) continue;
+    CU(cudaMemcpy(tmp.data(), h.pl[k].ritz, tmp.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (size_t j = 0; j < h.npatch; ++j) {
+      out[(j * ctx->npl + k) * 2] = tmp[2 * j];
+      out[(j * ctx->npl + k) * 2 + 1] = tmp[2 * j + 1];
+    }
+  }
+  std::memcpy(tm, out.data(), out.size() * sizeof(double));
+  return PMG_OK;
+}
+
+int pmg_set_bounds(pmg_ctx* ctx, int level, const double* lohi) {
+  int st = check_level(ctx, level);
+  if (st) return st;
+  HLevel& h = ctx->L[level];
+  std::vector<double> tmp(2 * h.npatch);
+  for (int k = 0; k < ctx->npl; ++k) {
+    if (h.pl[k].q == 1 || h.npatch == 0) continue;
+    for (size_t j = 0; j < h.npatch; ++j) {
+      const double lo = lohi[(j * ctx->npl + k) * 2], hi = lohi[(j * ctx->npl + k) * 2 + 1];
+      if (!(lo > 0) || !(hi > lo)) return fail(ctx, PMG_ERR_ARG, "bounds must satisfy 0 < lo < hi");
+      tmp[2 * j] = lo;
+      tmp[2 * j + 1] = hi;
+    }
+    CU(cudaMemcpy(h.pl[k].bounds64, tmp.data(), tmp.size() * sizeof(double), cudaMemcpyHostToDevice));
+    LK(1, launch_cast_d2f(h.pl[k].bounds64, h.pl[k].bounds32, tmp.size(), ctx->stream));
+  }
+  CU(cudaStreamSynchronize(ctx->stream));
+  return PMG_OK;
+}
+
+int pmg_gmg_vcycle(pmg_ctx* ctx, const double* b, double* x, void* stream) {
+  int st = check_level(ctx, ctx ? ctx->nlev - 1 : 0);
+  if (st) return st;
+  if (!b || !x) return fail(ctx, PMG_ERR_ARG, "null vector");
+  return precondition(ctx, b, x, (cudaStream_t)stream);
+}
+
+// One CG iteration body (captured into a CUDA graph): z = M r, rz = (r, z),
+// p = z + beta p, Ap = A p, alpha = rz / (p, Ap), x += alpha p, r -= alpha Ap,
+// rr = (r, r) copied to pinned host memory.
+static int cg_body(pmg_ctx* ctx, cudaStream_t s) {
+  HLevel& h = ctx->L.back();
+  const size_t n = h.nd;
+  int st = precondition(ctx, ctx->cg_r, ctx->cg_z, s);
+  if (st) return st;
+  LK(2, launch_dot(ctx->cg_r, ctx->cg_z, n, ctx->partial, ctx->scal, S_RZ, 1, s));
+  LK(1, launch_cg_update_p(ctx->cg_z, ctx->cg_p, ctx->scal, n, s));
+  LK(1 + (1 << ctx->dim), cell_apply<double>(ctx, ctx->p, ctx->cg_p, ctx->cg_Ap, h.pl[0].G64, h.N, s));
+  LK(2, launch_dot(ctx->cg_p, ctx->cg_Ap, n, ctx->partial, ctx->scal, S_PAP, 2, s));
+  LK(1, launch_cg_update_xr(ctx->cg_x, ctx->cg_r, ctx->cg_p, ctx->cg_Ap, ctx->scal, n, s));
+  LK(2, launch_dot(ctx->cg_r, ctx->cg_r, n, ctx->partial, ctx->scal, S_RR, 0, s));
+  CU(cudaMemcpyAsync(ctx->h_rr, ctx->scal + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s));
+  return PMG_OK;
+}
+
+int pmg_solve_cg(pmg_ctx* ctx, const double* b, double* u, double rtol, int maxit, int* iters, double* relres,
+                 void* stream) {
+  int st = check_level(ctx, ctx ? ctx->nlev - 1 : 0);
+  if (st) return st;
+  if (!b || !u || maxit < 0 || !(rtol >= 0)) return fail(ctx, PMG_ERR_ARG, "bad arguments");
+  cudaStream_t us = (cudaStream_t)stream;
+  cudaStream_t s = ctx->stream;
+  CU(cudaStreamSynchronize(us));
+  HLevel& h = ctx->L.back();
+  const size_t n = h.nd;
+  const int M = ctx->p * h.N + 1;
+  CU(cudaMemsetAsync(ctx->cg_x, 0, n * sizeof(double), s));
+  CU(cudaMemsetAsync(ctx->cg_p, 0, n * sizeof(double), s));
+  CU(cudaMemcpyAsync(ctx->cg_r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  LK(1, mask_boundary<double>(ctx, ctx->cg_r, M, s));
+  {
+    const double init[S_NSLOT] = {0.0, 1.0, 0.0, 0.0, 0.0, 0.0};
+    CU(cudaMemcpyAsync(ctx->scal, init, sizeof(init), cudaMemcpyHostToDevice, s));
+  }
+  LK(2, launch_dot(ctx->cg_r, ctx->cg_r, n, ctx->partial, ctx->scal, S_RR, 0, s));
+  CU(cudaMemcpyAsync(ctx->h_rr, ctx->scal + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  const double r0 = std::sqrt(*ctx->h_rr);
+  int it = 0;
+  double rel = 1.0;
+  int result = PMG_OK;
+  if (!std::isfinite(r0)) result = fail(ctx, PMG_ERR_NUMERIC, "non-finite right-hand side");
+  if (result == PMG_OK && r0 == 0.0) rel = 0.0;
+  if (result == PMG_OK && r0 > 0.0) {
+    if (!ctx->graph_exec) {
+      // warm-up outside capture (sets kernel attributes), then capture
+      cudaGraph_t g = nullptr;
+      const int64_t before = ctx->launches;
+      CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      st = cg_body(ctx, s);
+      ctx->graph_launches_per_iter = ctx->launches - before;
+      ctx->launches = before;
+      cudaError_t ce = cudaStreamEndCapture(s, &g);
+      if (st || ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        ctx->graph_exec = nullptr;
+      } else {
+        ctx->graph = g;
+        if (cudaGraphInstantiate(&ctx->graph_exec, g, 0) != cudaSuccess) {
+          cudaGetLastError();
+          ctx->graph_exec = nullptr;
+        }
+      }
+    }
+    while (it < maxit) {
+      ++it;
+      if (ctx->graph_exec) {
+        CU(cudaGraphLaunch(ctx->graph_exec, s));
+        ctx->launches += ctx->graph_launches_per_iter;
+      } else {
+        st = cg_body(ctx, s);
+        if (st) return st;
+      }
+      CU(cudaStreamSynchronize(s));
+      rel = std::sqrt(*ctx->h_rr) / r0;
+      if (!std::isfinite(rel)) {
+        result = fail(ctx, PMG_ERR_NUMERIC, "non-finite residual");
+        break;
+      }
+      if (rel <= rtol) break;
+    }
+    if (result == PMG_OK && rel > rtol) result = fail(ctx, PMG_ERR_NOT_CONVERGED, "maxit reached");
+  }
+  CU(cudaMemcpyAsync(u, ctx->cg_x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CU(cudaStreamSynchronize(s));
+  if (iters) *iters = it;
+  if (relres) *relres = rel;
+  return result;
+}
+
+int pmg_solve_cg_host(pmg_ctx* ctx, const double* b_host, double* u_host, double rtol, int maxit, int* iters,
+                      double* relres, void* stream) {
+  int st = check_level(ctx, ctx ? ctx->nlev - 1 : 0);
+  if (st) return st;
+  if (!b_host || !u_host) return fail(ctx, PMG_ERR_ARG, "null vector");
+  const size_t n = ctx->L.back().nd;
+  cudaStream_t s = ctx->stream;
+  CU(cudaMemcpyAsync(ctx->stage_b, b_host, n * sizeof(double), cudaMemcpyHostToDevice, s));
+  CU(cudaStreamSynchronize(s));
+  st = pmg_solve_cg(ctx, ctx->stage_b, ctx->stage_u, rtol, maxit, iters, relres, stream);
+  CU(cudaMemcpyAsync(u_host, ctx->stage_u, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  return st;
+}
+
+int pmg_rhs_manufactured(pmg_ctx* ctx, double* b, void* stream) {
+  int st = check_level(ctx, ctx ? ctx->nlev - 1 : 0);
+  if (st) return st;
+  if (!b) return fail(ctx, PMG_ERR_ARG, "null vector");
+  HLevel& h = ctx->L.back();
+  if (ctx->dim == 2) ST(launch_rhs_manufactured<2>(h.coords, h.N, ctx->p, b, (cudaStream_t)stream));
+  else ST(launch_rhs_manufactured<3>(h.coords, h.N, ctx->p, b, (cudaStream_t)stream));
+  return PMG_OK;
+}
+
+int pmg_get_colours(const pmg_ctx* ctx, int level, uint8_t* out) {
+  if (!ctx || !ctx->setup_ok || level < 0 || level >= ctx->nlev || !out) return PMG_ERR_ARG;
+  const HLevel& h = ctx->L[level];
+  std::memcpy(out, h.colours.data(), h.npatch);
+  return PMG_OK;
+}
+
+int pmg_get_patch_map(const pmg_ctx* ctx, int level, int64_t* out) {
+  if (!ctx || !ctx->setup_ok || level < 0 || level >= ctx->nlev || !out) return PMG_ERR_ARG;
+  const HLevel& h = ctx->L[level];
+  const int d = ctx->dim, Nl = h.N, Nv = Nl - 1;
+  const size_t Mg = (size_t)ctx->p * Nl + 1;
+  for (size_t j = 0; j < h.npatch; ++j) {
+    int v[3] = {0, 0, 0};
+    size_t rem = j;
+    for (int ax = 0; ax < d; ++ax) { v[ax] = 1 + (int)(rem % Nv); rem /= Nv; }
+    int64_t* o = out + j * ((1 << d) + 1);
+    for (int s2 = 0; s2 < (1 << d); ++s2) {
+      int64_t id = 0, mul = 1;
+      for (int ax = 0; ax < d; ++ax) { id += (v[ax] - 1 + ((s2 >> ax) & 1)) * mul; mul *= Nl; }
+      o[s2] = id;
+    }
+    int64_t g = 0, mul = 1;
+    for (int ax = 0; ax < d; ++ax) { g += (int64_t)ctx->p * (v[ax] - 1) * mul; mul *= (int64_t)Mg; }
+    o[1 << d] = g;
+  }
+  return PMG_OK;
+}
+
+int pmg_get_inv_diag(pmg_ctx* ctx, int level, int k, double* out, void* stream) {
+  int st = check_level(ctx, level);
+  if (st) return st;
+  if (k < 0 || k >= ctx->npl || !out) return fail(ctx, PMG_ERR_ARG, "bad p-level");
+  HLevel& h = ctx->L[level];
+  const size_t ndq = ipow_sz((size_t)h.pl[k].q * h.N + 1, ctx->dim);
+  CU(cudaMemcpyAsync(out, h.pl[k].dinv64, ndq * sizeof(double), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return PMG_OK;
+}
+
+double pmg_sweep_flops(const pmg_ctx* ctx, int level) {
+  if (!ctx || !ctx->mesh_ok || level < 0 || level >= ctx->nlev) return 0.0;
+  const int d = ctx->dim;
+  const int Nl = ctx->N >> (ctx->nlev - 1 - level);
+  const double npatch = (double)ipow_sz(Nl - 1, d);
+  auto fcell = [d](int n) { return 8.0 * d * std::pow(n, d + 1) + (2.0 * d * d - d) * std::pow(n, d); };
+  auto fpatch = [&](int q) { return (double)(1 << d) * fcell(q + 1); };
+  const int k = ctx->opt.cheb_degree;
+  const bool jac = ctx->opt.smoother == PMG_SMOOTHER_JACOBI;
+  double per = fpatch(ctx->p);   // Evaluate
+  for (int cyc = 0; cyc < ctx->opt.n_mg; ++cyc) {
+    for (int lv = 0; lv < ctx->npl; ++lv) {
+      const int q = ctx->plevels[lv];
+      if (q == 1) continue;
+      const bool zero = (lv > 0) || (cyc == 0);
+      const int pre = jac ? (zero ? 0 : 1) : (zero ? k - 1 : k);
+      const int post = jac ? 1 : k;
+      per += (pre + 1 + post) * fpatch(q);
+      const int qc = q / 2;
+      // restriction + prolongation: d sweeps per cell, each at most n_f^d * n_c FMAs
+      per += 2.0 * (1 << d) * 2.0 * d * std::pow(q + 1, d) * (qc + 1);
+    }
+  }
+  return per * npatch;
+}
+
+int pmg_launch_count(const pmg_ctx* ctx, int64_t* n) {
+  if (!ctx || !n) return PMG_ERR_ARG;
+  *n = ctx->launches;
+  return PMG_OK;
+}
+
+int pmg_fma_peak(pmg_ctx* ctx, int precision, double* flops) {
+  if (!ctx || !flops) return PMG_ERR_ARG;
+  CU(cudaSetDevice(ctx->device));
+  int nsm = 0;
+  CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+  const int block = 256, grid = nsm * 8;
+  cudaStream_t s = ctx->stream;
+  void* out = nullptr;
+  CU(cudaMalloc(&out, (size_t)grid * block * sizeof(double)));
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  double best = 0.0;
+  int iters = precision == PMG_PREC_FP64 ? 2000 : 20000;
+  for (int rep = 0; rep < 4; ++rep) {
+    CU(cudaEventRecord(e0, s));
+    if (precision == PMG_PREC_FP64) ST(launch_fma_chain<double>((double*)out, grid, block, iters, s));
+    else ST(launch_fma_chain<float>((float*)out, grid, block, iters, s));
+    CU(cudaEventRecord(e1, s));
+    CU(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, e0, e1));
+    const double f = 2.0 * 32.0 * iters * (double)grid * block / (ms * 1e-3);
+    best = std::max(best, f);
+    if (ms < 50.f) iters = (int)std::min<double>(iters * (60.0 / std::max(ms, 0.01f)), 2e8);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  *flops = best;
+  return PMG_OK;
+}
+
+}  // extern "C"

