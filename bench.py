@@ -201,6 +201,7 @@ def run_ours(args):
             ctx.solve_cg(b, x, 1e-8, 200)
         ms = []
         launches0 = ctx.launch_count()
+        torch.cuda.nvtx.range_push("timed_solves")
         for _ in range(nsteps):
             x.zero_()
             flush.zero_()
@@ -212,6 +213,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
             its.append((it, rel))
+        torch.cuda.nvtx.range_pop()
         return ms, its, ctx.launch_count() - launches0, x
 
     result = {}

@@ -15,7 +15,9 @@ The workloads follow the paper's test problems (Section 4: unit square/cube
 refined uniformly, interior vertices displaced; Section 3.3: coefficient
 jumps) with the sizes of the five benchmark configurations.  One
 ``numpy.random.default_rng(seed)`` stream draws, in this order: vertex
-perturbation, coefficient, right-hand side.
+perturbation, coefficient, right-hand side.  Vertices of cells with a
+non-positive corner volume are redrawn from a side stream seeded by
+(seed, attempt) until every corner is positive.
 """
 from __future__ import annotations
 
@@ -99,6 +101,49 @@ def perturbation(rng: np.random.Generator, dim: int, N: int, frac: float, law: s
     return disp
 
 
+def corner_volumes(x: np.ndarray, dim: int, N: int) -> np.ndarray:
+    """Signed corner volumes (N^dim cells x 2^dim corners): at each corner the
+    determinant of the dim cell edges leaving it along +x, +y(, +z) in the
+    cell's own index directions.  All positive <=> no inverted or non-convex
+    corner (the paper excludes such degenerate cells, Section 3.2)."""
+    X = x.reshape(*([N + 1] * dim), dim)                 # array axes [z][y][x] (or [y][x])
+    out = []
+    for v in range(2 ** dim):
+        cols = []
+        for k in range(dim):
+            lo = [((v >> a) & 1) if a != k else 0 for a in range(dim)]
+            hi = [((v >> a) & 1) if a != k else 1 for a in range(dim)]
+            sl_lo = tuple(slice(lo[dim - 1 - a], lo[dim - 1 - a] + N) for a in range(dim))
+            sl_hi = tuple(slice(hi[dim - 1 - a], hi[dim - 1 - a] + N) for a in range(dim))
+            cols.append(X[sl_hi] - X[sl_lo])
+        out.append(np.linalg.det(np.stack(cols, axis=-1)).reshape(-1))
+    return np.stack(out, axis=1)
+
+
+def valid_perturbation(rng, dim: int, N: int, frac: float, law: str, seed: int, max_attempts: int = 64):
+    """Perturbed vertices with every corner volume positive: vertices of cells
+    with a non-positive corner are redrawn (from a separate stream seeded by
+    (seed, attempt), so the main stream is consumed the same way every time)."""
+    x = grid_vertices(dim, N)
+    disp = perturbation(rng, dim, N, frac, law)
+    inner = interior_vertex_mask(dim, N)
+    for attempt in range(1, max_attempts + 1):
+        bad = corner_volumes(x + disp, dim, N).min(axis=1) <= 0.0
+        if not bad.any():
+            return x + disp
+        cells = np.nonzero(bad)[0]
+        verts = set()
+        for c in cells:
+            ci = [(c // N ** a) % N for a in range(dim)]
+            for v in range(2 ** dim):
+                verts.add(sum((ci[a] + ((v >> a) & 1)) * (N + 1) ** a for a in range(dim)))
+        verts = np.array(sorted(v for v in verts if inner[v]), dtype=np.int64)
+        sub = np.random.default_rng([seed, attempt])
+        fresh = perturbation(sub, dim, N, frac, law)
+        disp[verts] = fresh[verts]
+    raise RuntimeError("could not draw a valid perturbed mesh")
+
+
 def kappa_cells(rng: np.random.Generator, dim: int, N: int, spec: tuple) -> np.ndarray:
     nc = N ** dim
     if spec[0] == "const":
@@ -132,7 +177,7 @@ def make_problem(w: Workload) -> Problem:
     rng = np.random.default_rng(w.seed)
     x = grid_vertices(w.dim, w.N)
     if w.perturb > 0.0:
-        x = x + perturbation(rng, w.dim, w.N, w.perturb, w.law)
+        x = valid_perturbation(rng, w.dim, w.N, w.perturb, w.law, w.seed)
     kap = kappa_cells(rng, w.dim, w.N, w.kappa)
     b = rhs_uniform(rng, w.dim, w.p, w.N) if w.rhs == "uniform" else None
     return Problem(w, x, kap, b)
