@@ -263,7 +263,7 @@ def run_ours(args):
         err = float((x - torch.tensor(uh.numpy(), device=dev)).abs().max())
         result[name] = dict(ms=ms, its=its, launches=launches, t_sweep=t_sweep, sweep_flops=flops,
                             e2e_ms=e2e_ms, setup_s=t_setup, maxdiff_e2e=err,
-                            umax=float(x.abs().max()))
+                            umax=float(x.abs().max()), tuning=ctx.tuning())
         if name == "mixed":
             result["fma32"] = ctx.fma_peak(pmg.PREC_MIXED)
             result["fma64"] = ctx.fma_peak(pmg.PREC_FP64)
@@ -298,6 +298,9 @@ def run_ours(args):
             "rtol": 1e-8, "step": "one GMG-PCG solve from u = 0",
             "l2": "flushed (512 MB write) before every timed step",
             "replicas": world,
+            "patch_kernel_launch": {"variant": head["tuning"][0], "threads_per_cta": head["tuning"][1],
+                                    "patches_per_cta": head["tuning"][2],
+                                    "autotune_ms_per_variant": [round(x, 4) for x in head["tuning"][3]]},
         },
         "time_to_solution_ms": t_max,
         "cg_iterations": [i for i, _ in head["its"]],
@@ -309,7 +312,7 @@ def run_ours(args):
             "bound": "alu", "achieved": achieved / 1e12,
             "peak": FP32_PEAK_DERIVED / 1e12, "unit": "TFLOP/s",
             "frac": achieved / FP32_PEAK_DERIVED, "traffic": None,
-            "kernel": "k_patch<3,4,float,SWEEP> (finest-level patch sweep, 8 colour launches)",
+            "kernel": "k_patch<3,4,float,SWEEP,variant> (finest-level patch sweep, 8 colour launches)",
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
             "measured_fma_peak": result["fma32"] / 1e12,
             "frac_of_measured_fma": achieved / result["fma32"],

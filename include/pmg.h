@@ -66,12 +66,16 @@ typedef struct pmg_options {
   double fixed_lo, fixed_hi; /* interval used with PMG_BOUNDS_FIXED           */
   uint64_t seed;         /* seed of the Lanczos start vectors                  */
   int precision;         /* PMG_PREC_*                                         */
+  int autotune;          /* 1: pmg_setup times the launch-shape variants of the
+                            patch kernel on the finest level and keeps the
+                            fastest; 0: use `variant`                          */
+  int variant;           /* launch-shape variant when autotune = 0 (0 = default) */
 } pmg_options;
 
 typedef struct pmg_ctx pmg_ctx;
 
 /* Fill `opt` with the defaults: Chebyshev degree 3, N_MG = 1, Lanczos bounds
- * with 16 steps, safety 1.1, ratio 10, omega 0.5, seed 0, FP64. */
+ * with 16 steps, safety 1.1, ratio 10, omega 0.5, seed 0, FP64, autotune on. */
 void pmg_default_options(pmg_options* opt);
 
 /* Create a context on CUDA device `device`; `opt` may be NULL (defaults).
@@ -95,7 +99,8 @@ int pmg_mesh_structured(pmg_ctx* ctx, int dim, int N, int p, int n_levels,
 
 /* Build everything the solver needs (geometry tensors on every level and
  * p-level, level diagonals, patch and colour lists, Chebyshev bounds, coarse
- * Cholesky factor).  Returns PMG_ERR_DEGENERATE if a cell has det J <= 0 at
+ * Cholesky factor).  The coarsest level may have at most 16384 free DoFs
+ * (dense coarse solve), else PMG_ERR_UNSUPPORTED.  Returns PMG_ERR_DEGENERATE if a cell has det J <= 0 at
  * any Gauss point or vertex (Section 3.2 excludes such degenerate cells).
  * Synchronises the device. */
 int pmg_setup(pmg_ctx* ctx);
@@ -192,6 +197,14 @@ int pmg_get_inv_diag(pmg_ctx* ctx, int level, int k, double* out_dev, void* stre
  * sum-factorisation count 4d 1D sweeps + the quadrature-point product per
  * cell, plus the p-transfers). */
 double pmg_sweep_flops(const pmg_ctx* ctx, int level);
+
+/* Launch shape chosen for the patch-sweep kernel: variant index, threads per
+ * CTA, patches per CTA, and the set-up timings of the candidate variants
+ * (ms for one colour of the finest level, ms_per_variant[4], -1 where a
+ * variant does not exist or was not timed).  Any output may be NULL.
+ * Every variant computes bit-identical results. */
+int pmg_tuning(const pmg_ctx* ctx, int* variant, int* threads, int* patches_per_cta,
+               float* ms_per_variant);
 
 /* ---- measurement ----------------------------------------------------------
  * Number of kernels this context has launched so far (kernel nodes of a CUDA

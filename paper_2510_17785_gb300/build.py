@@ -51,10 +51,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
     srcs = _sources()
 
     hdr = hashlib.sha256()
-    for f in sorted(os.listdir(CSRC)):
-        if f.endswith((".h", ".cuh")):
-            with open(os.path.join(CSRC, f), "rb") as fh:
-                hdr.update(f.encode() + fh.read())
+    headers = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith((".h", ".cuh"))]
+    headers.append(os.path.join(os.path.dirname(HERE), "include", "pmg.h"))
+    for f in headers:
+        with open(f, "rb") as fh:
+            hdr.update(os.path.basename(f).encode() + fh.read())
     hdr.update(" ".join(ARCH + FLAGS).encode())
 
     def compile_one(src):

@@ -186,4 +186,19 @@ void h_restriction_band(int q, int Nc, std::vector<double>& W, std::vector<int>&
     }
 }
 
+static std::vector<TableUploader>& uploaders() {
+  static std::vector<TableUploader> v;
+  return v;
+}
+
+void register_table_uploader(TableUploader f) { uploaders().push_back(f); }
+
+int upload_all_tables(const Tables<double>& t64, const Tables<float>& t32, const Rules& r) {
+  for (TableUploader f : uploaders()) {
+    const int e = f(t64, t32, r);
+    if (e != 0) return e;
+  }
+  return 0;
+}
+
 }  // namespace pmg

@@ -1,5 +1,13 @@
 // Kernels for d = 3 in FP32, and the precision-generic FP32 helpers.
 #include "kernels_impl.cuh"
+PMG_EXTERN_PATCH(3, float, 1)
+PMG_EXTERN_PATCH(3, float, 2)
+PMG_EXTERN_PATCH(3, float, 3)
+PMG_EXTERN_PATCH(3, float, 4)
+PMG_EXTERN_PATCH(3, float, 5)
+PMG_EXTERN_PATCH(3, float, 6)
+PMG_EXTERN_PATCH(3, float, 7)
+PMG_EXTERN_PATCH(3, float, 8)
 PMG_INSTANTIATE_DIM_T(3, float)
 namespace pmg {
 template int launch_fma_chain<float>(float*, int, int, int, cudaStream_t);

@@ -1,6 +1,14 @@
 // Kernels for d = 3 in FP64, the precision-generic FP64 helpers, and the
 // FP64 CG vector operations.
 #include "kernels_impl.cuh"
+PMG_EXTERN_PATCH(3, double, 1)
+PMG_EXTERN_PATCH(3, double, 2)
+PMG_EXTERN_PATCH(3, double, 3)
+PMG_EXTERN_PATCH(3, double, 4)
+PMG_EXTERN_PATCH(3, double, 5)
+PMG_EXTERN_PATCH(3, double, 6)
+PMG_EXTERN_PATCH(3, double, 7)
+PMG_EXTERN_PATCH(3, double, 8)
 PMG_INSTANTIATE_DIM_T(3, double)
 namespace pmg {
 template int launch_fma_chain<double>(double*, int, int, int, cudaStream_t);

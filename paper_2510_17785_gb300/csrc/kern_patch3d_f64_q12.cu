@@ -1,0 +1,4 @@
+// Patch kernels for d = 3 in FP64, degree(s) 1, 2 (see kernels_impl.cuh).
+#include "kernels_impl.cuh"
+PMG_INSTANTIATE_PATCH(3, double, 1)
+PMG_INSTANTIATE_PATCH(3, double, 2)

@@ -19,15 +19,11 @@ inline int grid_for(size_t work, int threads) {
     if (cudaPeekAtLastError() != cudaSuccess) return ST_CUDA; \
   } while (0)
 
-template <int DIM, typename T>
-int upload_tables(const Tables<double>& h64, const Tables<float>& h32, const Rules& r) {
-  return upload_tables_tu(h64, h32, r) == cudaSuccess ? ST_OK : ST_CUDA;
-}
 
-template <int DIM, int P, typename T>
-int launch_patch_P(int mode, const PatchArgs<T>& a, cudaStream_t s) {
-  using C = Config<DIM, P, T>;
-  if constexpr (!C::fits) {
+template <int DIM, int P, typename T, int V>
+int launch_patch_PV(int mode, const PatchArgs<T>& a, cudaStream_t s) {
+  using C = Config<DIM, P, T, V>;
+  if constexpr (!C::fits || !C::distinct) {
     return ST_UNSUPPORTED;
   } else {
     if (a.n_items <= 0) return ST_OK;
@@ -35,61 +31,89 @@ int launch_patch_P(int mode, const PatchArgs<T>& a, cudaStream_t s) {
     if (mode == MODE_SWEEP) {
       static bool attr = false;
       if (!attr) {
-        if (cudaFuncSetAttribute(k_patch<DIM, P, T, MODE_SWEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(k_patch<DIM, P, T, MODE_SWEEP, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)C::smem) != cudaSuccess)
           return ST_CUDA;
         attr = true;
       }
-      k_patch<DIM, P, T, MODE_SWEEP><<<grid, C::NT, C::smem, s>>>(a);
+      k_patch<DIM, P, T, MODE_SWEEP, V><<<grid, C::NT, C::smem, s>>>(a);
     } else {
+      if constexpr (V != 0) return ST_UNSUPPORTED;
       static bool attr = false;
       if (!attr) {
-        if (cudaFuncSetAttribute(k_patch<DIM, P, T, MODE_LOCAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(k_patch<DIM, P, T, MODE_LOCAL, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)C::smem) != cudaSuccess)
           return ST_CUDA;
         attr = true;
       }
-      k_patch<DIM, P, T, MODE_LOCAL><<<grid, C::NT, C::smem, s>>>(a);
+      k_patch<DIM, P, T, MODE_LOCAL, V><<<grid, C::NT, C::smem, s>>>(a);
     }
     PMG_CHECK_LAUNCH();
     return ST_OK;
   }
 }
 
+// variants > 0 exist for 3D degrees 3..8 (sweep mode only)
+template <int DIM, int P, typename T>
+int launch_patch_P(int mode, int variant, const PatchArgs<T>& a, cudaStream_t s) {
+  if (variant == 0) return launch_patch_PV<DIM, P, T, 0>(mode, a, s);
+  if constexpr (DIM == 3 && P >= 3) {
+    switch (variant) {
+      case 1: return launch_patch_PV<DIM, P, T, 1>(mode, a, s);
+      case 2: return launch_patch_PV<DIM, P, T, 2>(mode, a, s);
+      case 3: return launch_patch_PV<DIM, P, T, 3>(mode, a, s);
+      default: return ST_UNSUPPORTED;
+    }
+  }
+  return ST_UNSUPPORTED;
+}
+
 template <int DIM, typename T>
-int launch_patch(int P, int mode, const PatchArgs<T>& a, cudaStream_t s) {
+int launch_patch(int P, int mode, int variant, const PatchArgs<T>& a, cudaStream_t s) {
   switch (P) {
-    case 1: return launch_patch_P<DIM, 1, T>(mode, a, s);
-    case 2: return launch_patch_P<DIM, 2, T>(mode, a, s);
-    case 3: return launch_patch_P<DIM, 3, T>(mode, a, s);
-    case 4: return launch_patch_P<DIM, 4, T>(mode, a, s);
-    case 5: return launch_patch_P<DIM, 5, T>(mode, a, s);
-    case 6: return launch_patch_P<DIM, 6, T>(mode, a, s);
-    case 7: return launch_patch_P<DIM, 7, T>(mode, a, s);
-    case 8: return launch_patch_P<DIM, 8, T>(mode, a, s);
+    case 1: return launch_patch_P<DIM, 1, T>(mode, variant, a, s);
+    case 2: return launch_patch_P<DIM, 2, T>(mode, variant, a, s);
+    case 3: return launch_patch_P<DIM, 3, T>(mode, variant, a, s);
+    case 4: return launch_patch_P<DIM, 4, T>(mode, variant, a, s);
+    case 5: return launch_patch_P<DIM, 5, T>(mode, variant, a, s);
+    case 6: return launch_patch_P<DIM, 6, T>(mode, variant, a, s);
+    case 7: return launch_patch_P<DIM, 7, T>(mode, variant, a, s);
+    case 8: return launch_patch_P<DIM, 8, T>(mode, variant, a, s);
     default: return ST_UNSUPPORTED;
   }
 }
 
+template <int DIM, int P, typename T, int V>
+void patch_config_PV(size_t* smem, int* ppb, int* nt) {
+  using C = Config<DIM, P, T, V>;
+  const bool ok = C::fits && C::distinct && (V == 0 || (DIM == 3 && P >= 3));
+  *smem = ok ? C::smem : 0;
+  *ppb = ok ? C::PPB : 0;
+  *nt = ok ? C::NT : 0;
+}
+
 template <int DIM, int P, typename T>
-void patch_config_P(size_t* smem, int* ppb, int* nt) {
-  using C = Config<DIM, P, T>;
-  *smem = C::fits ? C::smem : 0;
-  *ppb = C::fits ? C::PPB : 0;
-  *nt = C::NT;
+void patch_config_P(int variant, size_t* smem, int* ppb, int* nt) {
+  switch (variant) {
+    case 0: return patch_config_PV<DIM, P, T, 0>(smem, ppb, nt);
+    case 1: return patch_config_PV<DIM, P, T, 1>(smem, ppb, nt);
+    case 2: return patch_config_PV<DIM, P, T, 2>(smem, ppb, nt);
+    case 3: return patch_config_PV<DIM, P, T, 3>(smem, ppb, nt);
+    default: *smem = 0; *ppb = 0; *nt = 0;
+  }
 }
 
 template <int DIM, typename T>
-void patch_config(int P, size_t* smem, int* ppb, int* nt) {
+void patch_config(int P, int variant, size_t* smem, int* ppb, int* nt) {
   switch (P) {
-    case 1: return patch_config_P<DIM, 1, T>(smem, ppb, nt);
-    case 2: return patch_config_P<DIM, 2, T>(smem, ppb, nt);
-    case 3: return patch_config_P<DIM, 3, T>(smem, ppb, nt);
-    case 4: return patch_config_P<DIM, 4, T>(smem, ppb, nt);
-    case 5: return patch_config_P<DIM, 5, T>(smem, ppb, nt);
-    case 6: return patch_config_P<DIM, 6, T>(smem, ppb, nt);
-    case 7: return patch_config_P<DIM, 7, T>(smem, ppb, nt);
-    case 8: return patch_config_P<DIM, 8, T>(smem, ppb, nt);
+    case 1: return patch_config_P<DIM, 1, T>(variant, smem, ppb, nt);
+    case 2: return patch_config_P<DIM, 2, T>(variant, smem, ppb, nt);
+    case 3: return patch_config_P<DIM, 3, T>(variant, smem, ppb, nt);
+    case 4: return patch_config_P<DIM, 4, T>(variant, smem, ppb, nt);
+    case 5: return patch_config_P<DIM, 5, T>(variant, smem, ppb, nt);
+    case 6: return patch_config_P<DIM, 6, T>(variant, smem, ppb, nt);
+    case 7: return patch_config_P<DIM, 7, T>(variant, smem, ppb, nt);
+    case 8: return patch_config_P<DIM, 8, T>(variant, smem, ppb, nt);
     default: *smem = 0; *ppb = 0; *nt = 0;
   }
 }
@@ -261,11 +285,23 @@ int launch_fma_chain(T* out, int grid, int block, int iters, cudaStream_t s) {
 
 }  // namespace pmg
 
+// Explicit instantiation of the patch kernels of one degree (their own
+// translation unit each in 3D, so that they compile in parallel).
+#define PMG_INSTANTIATE_PATCH(DIM, T, P)                                                   \
+  namespace pmg {                                                                          \
+  template int launch_patch_P<DIM, P, T>(int, int, const PatchArgs<T>&, cudaStream_t);     \
+  }
+// ... and the declarations that keep other translation units from
+// instantiating them again.
+#define PMG_EXTERN_PATCH(DIM, T, P)                                                        \
+  namespace pmg {                                                                          \
+  extern template int launch_patch_P<DIM, P, T>(int, int, const PatchArgs<T>&, cudaStream_t); \
+  }
+
 #define PMG_INSTANTIATE_DIM_T(DIM, T)                                                                       \
   namespace pmg {                                                                                           \
-  template int upload_tables<DIM, T>(const Tables<double>&, const Tables<float>&, const Rules&);            \
-  template int launch_patch<DIM, T>(int, int, const PatchArgs<T>&, cudaStream_t);                           \
-  template void patch_config<DIM, T>(int, size_t*, int*, int*);                                             \
+  template int launch_patch<DIM, T>(int, int, int, const PatchArgs<T>&, cudaStream_t);                      \
+  template void patch_config<DIM, T>(int, int, size_t*, int*, int*);                                        \
   template int launch_lanczos<DIM, T>(int, const LanczosArgs<T>&, cudaStream_t);                            \
   template int launch_cell_apply<DIM, T>(int, const T*, T*, const T*, int, cudaStream_t);                   \
   template int launch_geometry<DIM, T>(const double*, const double*, int, int, T*, int*, cudaStream_t);     \

@@ -12,15 +12,16 @@ namespace pmg {
 // status codes (mirrors pmg.h)
 enum { ST_OK = 0, ST_ARG = 1, ST_CUDA = 2, ST_UNSUPPORTED = 7 };
 
-template <int DIM, typename T>
-int upload_tables(const Tables<double>& h64, const Tables<float>& h32, const Rules& r);
 
-// one launch of the patch kernel over a.n_items patches (MODE_SWEEP or MODE_LOCAL)
+// one launch of the patch kernel over a.n_items patches (MODE_SWEEP or
+// MODE_LOCAL) with launch-shape variant `variant` (0 = default; ST_UNSUPPORTED
+// if the variant does not exist for this degree)
 template <int DIM, typename T>
-int launch_patch(int P, int mode, const PatchArgs<T>& a, cudaStream_t s);
-// shared memory bytes per CTA and patches per CTA of the patch kernel (0 if unsupported)
+int launch_patch(int P, int mode, int variant, const PatchArgs<T>& a, cudaStream_t s);
+// shared memory bytes per CTA, patches per CTA and threads per CTA of a
+// variant of the patch kernel (all 0 if it does not exist)
 template <int DIM, typename T>
-void patch_config(int P, size_t* smem, int* ppb, int* nthreads);
+void patch_config(int P, int variant, size_t* smem, int* ppb, int* nthreads);
 
 template <int DIM, typename T>
 int launch_lanczos(int q, const LanczosArgs<T>& a, cudaStream_t s);

@@ -73,23 +73,32 @@ struct Layout {
   static constexpr int PS = (PS_RAW + 3) & ~3;    // per-patch stride in elements
 };
 
-template <int DIM, int P, typename T>
+// Launch shape of the patch kernel.  Variant 0 is the default; variants 1..3
+// (threads per CTA, patches per CTA) = (256, 2), (128, 1), (512, 4) are the
+// candidates the set-up autotuner times for 3D degrees 3..8.
+template <int DIM, int P, typename T, int V = 0>
 struct Config {
-  static constexpr int NT = (DIM == 3) ? 256 : 128;
+  static constexpr int NT0 = (DIM == 3) ? 256 : 128;
+  static constexpr int PPB0 = (DIM == 3) ? (P <= 2 ? 4 : 1) : (P <= 2 ? 8 : (P <= 4 ? 4 : 2));
+  static constexpr int NT = V == 0 ? NT0 : (V == 1 ? 256 : (V == 2 ? 128 : 512));
+  static constexpr int PPB_MAX = V == 0 ? PPB0 : (V == 1 ? 2 : (V == 2 ? 1 : 4));
   static constexpr size_t bytes_per_patch =
       sizeof(T) * Layout<DIM, P>::PS + sizeof(int) * ((1 << DIM) + 4);
-  static constexpr int PPB_MAX = (DIM == 3) ? (P <= 2 ? 4 : 1) : (P <= 2 ? 8 : (P <= 4 ? 4 : 2));
   static constexpr size_t SMEM_LIMIT = 227 * 1024;
   static constexpr int PPB_FIT = (int)(SMEM_LIMIT / bytes_per_patch);
   static constexpr int PPB = PPB_FIT < PPB_MAX ? (PPB_FIT < 1 ? 1 : PPB_FIT) : PPB_MAX;
   static constexpr size_t smem = bytes_per_patch * PPB;
   static constexpr bool fits = bytes_per_patch <= SMEM_LIMIT;
+  // a variant is distinct (worth instantiating) only if it differs from variant 0
+  static constexpr bool distinct = V == 0 || NT != Config<DIM, P, T, 0>::NT || PPB != Config<DIM, P, T, 0>::PPB;
 };
 
-template <int DIM, int P, typename T, int MODE>
+constexpr int NUM_VARIANTS = 4;
+
+template <int DIM, int P, typename T, int MODE, int V = 0>
 struct PatchKernel {
   using L = Layout<DIM, P>;
-  using C = Config<DIM, P, T>;
+  using C = Config<DIM, P, T, V>;
   static constexpr int NT = C::NT, PPB = C::PPB, NL = L::NL, PS = L::PS;
   static constexpr int NCELL = 1 << DIM;
 
@@ -475,10 +484,10 @@ struct PatchKernel {
   }
 };
 
-template <int DIM, int P, typename T, int MODE>
-__global__ void __launch_bounds__(Config<DIM, P, T>::NT) k_patch(const __grid_constant__ PatchArgs<T> args) {
+template <int DIM, int P, typename T, int MODE, int V = 0>
+__global__ void __launch_bounds__(Config<DIM, P, T, V>::NT) k_patch(const __grid_constant__ PatchArgs<T> args) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  using PK = PatchKernel<DIM, P, T, MODE>;
+  using PK = PatchKernel<DIM, P, T, MODE, V>;
   PK k;
   k.sm = reinterpret_cast<T*>(smem_raw);
   k.cells = reinterpret_cast<int*>(smem_raw + sizeof(T) * (size_t)PK::PS * PK::PPB);

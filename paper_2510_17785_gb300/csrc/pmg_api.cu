@@ -91,6 +91,10 @@ struct pmg_ctx {
   cudaGraphExec_t graph_exec = nullptr;
   int64_t graph_launches_per_iter = 0;   // kernels recorded in one CG iteration graph
   int64_t launches = 0;                  // kernels launched so far
+  int variant = 0;                       // launch shape of the patch-sweep kernel
+  float variant_ms[4] = {-1.f, -1.f, -1.f, -1.f};
+  double* lanczos_V = nullptr;           // Lanczos basis scratch, grown on demand, reused
+  size_t lanczos_V_n = 0;
   std::vector<void*> allocs;
 };
 
@@ -143,6 +147,9 @@ int dalloc(pmg_ctx* ctx, T** p, size_t n) {
     if (s_ != PMG_OK) return s_;              \
   } while (0)
 
+// largest coarsest level for the dense FP64 inverse (2 GB, O(nf^3) host work)
+constexpr int kMaxCoarseDofs = 16384;
+
 size_t ipow_sz(size_t b, int e) {
   size_t r = 1;
   for (int i = 0; i < e; ++i) r *= b;
@@ -152,7 +159,8 @@ size_t ipow_sz(size_t b, int e) {
 // ---- dispatch on dimension -------------------------------------------------
 template <typename T>
 int patch_launch(pmg_ctx* c, int mode, const PatchArgs<T>& a, cudaStream_t s) {
-  return c->dim == 2 ? launch_patch<2, T>(c->p, mode, a, s) : launch_patch<3, T>(c->p, mode, a, s);
+  const int v = mode == MODE_SWEEP ? c->variant : 0;
+  return c->dim == 2 ? launch_patch<2, T>(c->p, mode, v, a, s) : launch_patch<3, T>(c->p, mode, v, a, s);
 }
 template <typename T>
 int cell_apply(pmg_ctx* c, int q, const T* u, T* out, const T* G, int N, cudaStream_t s) {
@@ -371,6 +379,75 @@ bool cholesky_inverse(std::vector<double>& A, int n) {
   return true;
 }
 
+// Time every launch-shape variant of the patch-sweep kernel on colour 0 of
+// the finest level (zero vectors; results are discarded) and keep the fastest.
+template <typename T>
+int autotune_T(pmg_ctx* ctx, T* u, const T* b) {
+  const int lf = ctx->nlev - 1;
+  cudaStream_t s = ctx->stream;
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bestv = 0;
+  for (int v = 0; v < NUM_VARIANTS; ++v) {
+    size_t sm;
+    int ppb, nt;
+    if (ctx->dim == 2) patch_config<2, T>(ctx->p, v, &sm, &ppb, &nt);
+    else patch_config<3, T>(ctx->p, v, &sm, &ppb, &nt);
+    if (sm == 0) continue;
+    ctx->variant = v;
+    int st = sweep_colour<T>(ctx, lf, 0, b, u, s);     // warm-up (and kernel attribute)
+    if (st) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return st;
+    }
+    float ms = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      CU(cudaEventRecord(e0, s));
+      st = sweep_colour<T>(ctx, lf, 0, b, u, s);
+      if (st) return st;
+      CU(cudaEventRecord(e1, s));
+      CU(cudaEventSynchronize(e1));
+      float t = 0.f;
+      CU(cudaEventElapsedTime(&t, e0, e1));
+      ms = std::min(ms, t);
+    }
+    ctx->variant_ms[v] = ms;
+    if (ms < best) {
+      best = ms;
+      bestv = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->variant = bestv;
+  return PMG_OK;
+}
+
+int autotune(pmg_ctx* ctx) {
+  for (int v = 0; v < 4; ++v) ctx->variant_ms[v] = -1.f;
+  if (!ctx->opt.autotune) {
+    ctx->variant = ctx->opt.variant;
+    size_t sm;
+    int ppb, nt;
+    if (ctx->dim == 2) patch_config<2, double>(ctx->p, ctx->variant, &sm, &ppb, &nt);
+    else patch_config<3, double>(ctx->p, ctx->variant, &sm, &ppb, &nt);
+    if (sm == 0) return fail(ctx, PMG_ERR_UNSUPPORTED, "this launch-shape variant does not exist for this degree");
+    return PMG_OK;
+  }
+  HLevel& h = ctx->L.back();
+  if (ctx->opt.precision == PMG_PREC_MIXED) {
+    CU(cudaMemsetAsync(h.x32, 0, h.nd * sizeof(float), ctx->stream));
+    CU(cudaMemsetAsync(h.b32, 0, h.nd * sizeof(float), ctx->stream));
+    return autotune_T<float>(ctx, h.x32, h.b32);
+  }
+  CU(cudaMemsetAsync(h.x64, 0, h.nd * sizeof(double), ctx->stream));
+  CU(cudaMemsetAsync(h.b64, 0, h.nd * sizeof(double), ctx->stream));
+  return autotune_T<double>(ctx, h.x64, h.b64);
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -391,6 +468,8 @@ void pmg_default_options(pmg_options* o) {
   o->fixed_hi = 2.0;
   o->seed = 0;
   o->precision = PMG_PREC_FP64;
+  o->autotune = 1;
+  o->variant = 0;
 }
 
 int pmg_create(int device, const pmg_options* opt, pmg_ctx** out) {
@@ -403,7 +482,8 @@ int pmg_create(int device, const pmg_options* opt, pmg_ctx** out) {
   const pmg_options& o = ctx->opt;
   if (o.cheb_degree < 1 || o.cheb_degree > 8 || o.n_mg < 1 || o.lanczos_steps < 1 || o.lanczos_steps > 64 ||
       (o.smoother != 0 && o.smoother != 1) || (o.precision != 0 && o.precision != 1) || o.bounds < 0 ||
-      o.bounds > 2 || !(o.bound_safety > 0) || !(o.bound_ratio >= 1)) {
+      o.bounds > 2 || !(o.bound_safety > 0) || !(o.bound_ratio >= 1) || o.variant < 0 ||
+      o.variant >= NUM_VARIANTS) {
     delete ctx;
     return PMG_ERR_ARG;
   }
@@ -428,6 +508,7 @@ int pmg_destroy(pmg_ctx* ctx) {
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
   if (ctx->graph) cudaGraphDestroy(ctx->graph);
   for (void* p : ctx->allocs) cudaFree(p);
+  if (ctx->lanczos_V) cudaFree(ctx->lanczos_V);
   if (ctx->d_err) cudaFree(ctx->d_err);
   if (ctx->h_rr) cudaFreeHost(ctx->h_rr);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -448,11 +529,11 @@ int pmg_mesh_structured(pmg_ctx* ctx, int dim, int N, int p, int n_levels, const
   if (ctx->mesh_ok) return fail(ctx, PMG_ERR_ARG, "mesh already uploaded");
   size_t sz, pb;
   int ppb, nt;
-  if (dim == 2) patch_config<2, double>(p, &sz, &ppb, &nt);
-  else patch_config<3, double>(p, &sz, &ppb, &nt);
+  if (dim == 2) patch_config<2, double>(p, 0, &sz, &ppb, &nt);
+  else patch_config<3, double>(p, 0, &sz, &ppb, &nt);
   size_t sz32;
-  if (dim == 2) patch_config<2, float>(p, &sz32, &ppb, &nt);
-  else patch_config<3, float>(p, &sz32, &ppb, &nt);
+  if (dim == 2) patch_config<2, float>(p, 0, &sz32, &ppb, &nt);
+  else patch_config<3, float>(p, 0, &sz32, &ppb, &nt);
   (void)pb;
   if ((ctx->opt.precision == PMG_PREC_FP64 && sz == 0) || sz32 == 0)
     return fail(ctx, PMG_ERR_UNSUPPORTED, "patch working set of this degree does not fit in shared memory in this precision");
@@ -484,10 +565,8 @@ int pmg_setup(pmg_ctx* ctx) {
     Tables<float> t32;
     Rules r;
     build_tables(t64, t32, r);
-    ST(upload_tables<2, double>(t64, t32, r));
-    ST(upload_tables<3, double>(t64, t32, r));
-    ST(upload_tables<2, float>(t64, t32, r));
-    ST(upload_tables<3, float>(t64, t32, r));
+    const int e = upload_all_tables(t64, t32, r);
+    if (e != 0) return fail(ctx, PMG_ERR_CUDA, std::string("table upload: ") + cudaGetErrorString((cudaError_t)e));
   }
   const bool mixed = ctx->opt.precision == PMG_PREC_MIXED;
   // ---- levels: coordinates (even-index subsampling), kappa (mean of children)
@@ -650,6 +729,10 @@ int pmg_setup(pmg_ctx* ctx) {
       if (!bnd) fidx.push_back((int)i);
     }
     const int nf = (int)fidx.size();
+    if (nf > kMaxCoarseDofs)
+      return fail(ctx, PMG_ERR_UNSUPPORTED,
+                  "the coarsest level has " + std::to_string(nf) + " free DoFs; the dense coarse solver takes at most " +
+                      std::to_string(kMaxCoarseDofs) + ": use more h-levels");
     ctx->nf = nf;
     std::vector<double> A((size_t)nf * nf, 0.0), col(h.nd);
     for (int j = 0; j < nf; ++j) {
@@ -693,6 +776,11 @@ int pmg_setup(pmg_ctx* ctx) {
     ctx->setup_ok = false;
     return st;
   }
+  st = autotune(ctx);
+  if (st) {
+    ctx->setup_ok = false;
+    return st;
+  }
   // warm-up V-cycle on a zero vector: every kernel of the preconditioner runs
   // once (and gets its shared-memory attribute) before any graph capture
   CU(cudaMemsetAsync(ctx->cg_r, 0, ctx->L.back().nd * sizeof(double), s));
@@ -726,8 +814,15 @@ int pmg_compute_bounds(pmg_ctx* ctx, int source) {
       if (source != PMG_BOUNDS_LANCZOS) return fail(ctx, PMG_ERR_ARG, "unknown bounds source");
       const size_t ni = ipow_sz(2 * pl.q - 1, d);
       const size_t chunk = std::max<size_t>(1, std::min<size_t>(h.npatch, (size_t)(512u << 20) / (ctx->opt.lanczos_steps * ni * 8)));
-      double* V = nullptr;
-      DALLOC(V, chunk * ctx->opt.lanczos_steps * ni);
+      const size_t need = chunk * ctx->opt.lanczos_steps * ni;
+      if (ctx->lanczos_V_n < need) {
+        if (ctx->lanczos_V) CU(cudaFree(ctx->lanczos_V));
+        ctx->lanczos_V = nullptr;
+        ctx->lanczos_V_n = 0;
+        CU(cudaMalloc(&ctx->lanczos_V, need * sizeof(double)));
+        ctx->lanczos_V_n = need;
+      }
+      double* V = ctx->lanczos_V;
       for (size_t j0 = 0; j0 < h.npatch; j0 += chunk) {
         const int n = (int)std::min(chunk, h.npatch - j0);
         LanczosArgs<double> a;
@@ -1134,6 +1229,26 @@ double pmg_sweep_flops(const pmg_ctx* ctx, int level) {
   return per * npatch;
 }
 
+int pmg_tuning(const pmg_ctx* ctx, int* variant, int* threads, int* ppb_out, float* ms) {
+  if (!ctx || !ctx->setup_ok) return PMG_ERR_ARG;
+  size_t sm;
+  int ppb, nt;
+  const bool mixed = ctx->opt.precision == PMG_PREC_MIXED;
+  if (ctx->dim == 2) {
+    if (mixed) patch_config<2, float>(ctx->p, ctx->variant, &sm, &ppb, &nt);
+    else patch_config<2, double>(ctx->p, ctx->variant, &sm, &ppb, &nt);
+  } else {
+    if (mixed) patch_config<3, float>(ctx->p, ctx->variant, &sm, &ppb, &nt);
+    else patch_config<3, double>(ctx->p, ctx->variant, &sm, &ppb, &nt);
+  }
+  if (variant) *variant = ctx->variant;
+  if (threads) *threads = nt;
+  if (ppb_out) *ppb_out = ppb;
+  if (ms)
+    for (int v = 0; v < 4; ++v) ms[v] = ctx->variant_ms[v];
+  return PMG_OK;
+}
+
 int pmg_launch_count(const pmg_ctx* ctx, int64_t* n) {
   if (!ctx || !n) return PMG_ERR_ARG;
   *n = ctx->launches;
@@ -1174,3 +1289,4 @@ int pmg_fma_peak(pmg_ctx* ctx, int precision, double* flops) {
 }
 
 }  // extern "C"
+

@@ -93,6 +93,98 @@ struct SF {
     }
   }
 
+  // ---- forward interpolation along the last axis fused with the collocation
+  // derivative along it: writes the point values V and the derivative F.
+  template <bool INTIN>
+  __device__ __forceinline__ static void fwd_der_last_item(const T* __restrict__ in, T* __restrict__ V,
+                                                           T* __restrict__ F, int item) {
+    constexpr int AX = DIM - 1;
+    constexpr int L = INTIN ? Mi : M;
+    constexpr int I = ipow(QP, AX);
+    const int c = (NC == 2) ? (item & 1) : 0;
+    const int i = (NC == 2) ? (item >> 1) : item;
+    const T* src = in + i;
+    T v[n];
+#pragma unroll
+    for (int a = 0; a <= Q; ++a) {
+      const int k = c * Q + a;
+      if (INTIN) {
+        const bool ok = (k >= 1) && (k <= M - 2);
+        v[a] = ok ? src[(k - 1) * I] : T(0);
+      } else {
+        v[a] = src[k * I];
+      }
+    }
+    static_assert(L > 0, "");
+    T w[n];
+#pragma unroll
+    for (int g = 0; g < n; ++g) {
+      T s = T(0);
+#pragma unroll
+      for (int a = 0; a <= Q; ++a) s += tabB<T>(Q, g, a) * v[a];
+      w[g] = s;
+      V[(c * n + g) * I + i] = s;
+    }
+#pragma unroll
+    for (int g = 0; g < n; ++g) {
+      T s = T(0);
+#pragma unroll
+      for (int h = 0; h < n; ++h) s += tabD<T>(Q, g, h) * w[h];
+      F[(c * n + g) * I + i] = s;
+    }
+  }
+
+  // ---- transposed derivative along the last axis, added to the partial sums
+  // in Vp (the other directions), fused with the backward integration along
+  // that axis: one item per line (both cells), output [Lo][I].
+  __device__ __forceinline__ static void dert_bwd_last_item(const T* __restrict__ F, const T* __restrict__ Vp,
+                                                            T* __restrict__ out, int i) {
+    constexpr int AX = DIM - 1;
+    constexpr int I = ipow(QP, AX);
+    T w[NC][n];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      T f[n];
+#pragma unroll
+      for (int g = 0; g < n; ++g) f[g] = F[(c * n + g) * I + i];
+#pragma unroll
+      for (int h = 0; h < n; ++h) {
+        T s = Vp[(c * n + h) * I + i];
+#pragma unroll
+        for (int g = 0; g < n; ++g) s += tabD<T>(Q, g, h) * f[g];
+        w[c][h] = s;
+      }
+    }
+    if (NC == 1) {
+#pragma unroll
+      for (int a = 0; a <= Q; ++a) {
+        T s = T(0);
+#pragma unroll
+        for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, a) * w[0][g];
+        out[a * I + i] = s;
+      }
+    } else {
+#pragma unroll
+      for (int a = 1; a <= Q; ++a) {
+        T s = T(0);
+#pragma unroll
+        for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, a) * w[0][g];
+        if (a == Q) {
+#pragma unroll
+          for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, 0) * w[NC - 1][g];
+        }
+        out[(a - 1) * I + i] = s;
+      }
+#pragma unroll
+      for (int a = 1; a < Q; ++a) {
+        T s = T(0);
+#pragma unroll
+        for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, a) * w[NC - 1][g];
+        out[(Q + a - 1) * I + i] = s;
+      }
+    }
+  }
+
   // ---- collocation derivative along AX on [O][QP][I]
   template <int AX>
   __device__ __forceinline__ static void der_item(const T* __restrict__ in, T* __restrict__ out, int item) {
@@ -226,7 +318,8 @@ struct SF {
   template <bool INTIN, bool ACC, typename GF>
   __device__ static void apply(const T* in, int sin, T* out, int sout, T* scr, int sscr, const GF& gcell) {
     constexpr int L = INTIN ? Mi : M;
-    // scratch: V = scr[0..NQ), R = scr[NQ..)
+    constexpr int Lo = (NC == 2) ? Mi : M;
+    // scratch: V = scr[0..NQ), R = scr[NQ..); F_ax = R + ax*NQ
     auto Vp = [&](int pp) { return scr + pp * sscr; };
     auto Rp = [&](int pp) { return scr + pp * sscr + NQ; };
     if constexpr (DIM == 3) {
@@ -235,39 +328,14 @@ struct SF {
       __syncthreads();
       coop<NT, PPB, L * QP * NC>([&](int pp, int it) { fwd_item<1, INTIN>(Rp(pp), Rp(pp) + T1, it); });
       __syncthreads();
-      coop<NT, PPB, QP * QP * NC>([&](int pp, int it) { fwd_item<2, INTIN>(Rp(pp) + T1, Vp(pp), it); });
-      __syncthreads();
-      constexpr int ND = QP * QP * NC;
-      coop<NT, PPB, 3 * ND>([&](int pp, int it) {
-        const int ax = it / ND, r = it - ax * ND;
-        if (ax == 0) der_item<0>(Vp(pp), Rp(pp), r);
-        else if (ax == 1) der_item<1>(Vp(pp), Rp(pp) + NQ, r);
-        else der_item<2>(Vp(pp), Rp(pp) + 2 * NQ, r);
+      // z: interpolate to the Gauss points and differentiate along z in registers;
+      // T2 (R + T1) is read while F_2 (R + 2 NQ) is written: 2 NQ >= T1 + T2.
+      static_assert(2 * NQ >= L * L * QP + L * QP * QP, "F_2 overlaps the z input");
+      coop<NT, PPB, QP * QP * NC>([&](int pp, int it) {
+        fwd_der_last_item<INTIN>(Rp(pp) + T1, Vp(pp), Rp(pp) + 2 * NQ, it);
       });
       __syncthreads();
-      coop<NT, PPB, NQ>([&](int pp, int pt) { quad_item(Rp(pp), pt, gcell, pp); });
-      __syncthreads();
-      coop<NT, PPB, ND>([&](int pp, int it) { dert_item<0, false>(Rp(pp), Vp(pp), it); });
-      __syncthreads();
-      coop<NT, PPB, ND>([&](int pp, int it) { dert_item<1, true>(Rp(pp) + NQ, Vp(pp), it); });
-      __syncthreads();
-      coop<NT, PPB, ND>([&](int pp, int it) { dert_item<2, true>(Rp(pp) + 2 * NQ, Vp(pp), it); });
-      __syncthreads();
-      constexpr int Lo = (NC == 2) ? Mi : M;
-      constexpr int B1 = Lo * Lo * QP;       // [Lo][Lo][QP]
-      // V [QP][QP][QP] -> R+B1 [Lo][QP][QP] -> R [Lo][Lo][QP] -> out [Lo]^3
-      coop<NT, PPB, QP * QP * NC>([&](int pp, int it) { bwd_item<2, false>(Vp(pp), Rp(pp) + B1, it); });
-      __syncthreads();
-      coop<NT, PPB, Lo * QP * NC>([&](int pp, int it) { bwd_item<1, false>(Rp(pp) + B1, Rp(pp), it); });
-      __syncthreads();
-      coop<NT, PPB, Lo * Lo * NC>([&](int pp, int it) { bwd_item<0, ACC>(Rp(pp), out + pp * sout, it); });
-      __syncthreads();
-    } else {
-      coop<NT, PPB, L * NC>([&](int pp, int it) { fwd_item<0, INTIN>(in + pp * sin, Rp(pp), it); });
-      __syncthreads();
-      coop<NT, PPB, QP * NC>([&](int pp, int it) { fwd_item<1, INTIN>(Rp(pp), Vp(pp), it); });
-      __syncthreads();
-      constexpr int ND = QP * NC;
+      constexpr int ND = QP * QP * NC;
       coop<NT, PPB, 2 * ND>([&](int pp, int it) {
         const int ax = it / ND, r = it - ax * ND;
         if (ax == 0) der_item<0>(Vp(pp), Rp(pp), r);
@@ -280,8 +348,31 @@ struct SF {
       __syncthreads();
       coop<NT, PPB, ND>([&](int pp, int it) { dert_item<1, true>(Rp(pp) + NQ, Vp(pp), it); });
       __syncthreads();
-      constexpr int Lo = (NC == 2) ? Mi : M;
-      coop<NT, PPB, QP * NC>([&](int pp, int it) { bwd_item<1, false>(Vp(pp), Rp(pp), it); });
+      constexpr int B1 = Lo * Lo * QP;       // [Lo][Lo][QP]
+      // z: D^T F_2 + V -> B^T along z -> R + B1 [Lo][QP][QP]; R + B1 does not
+      // reach F_2 = R + 2 NQ because B1 + Lo QP^2 <= 2 NQ.
+      static_assert(B1 + Lo * QP * QP <= 2 * NQ, "z output overlaps F_2");
+      coop<NT, PPB, QP * QP>([&](int pp, int it) { dert_bwd_last_item(Rp(pp) + 2 * NQ, Vp(pp), Rp(pp) + B1, it); });
+      __syncthreads();
+      coop<NT, PPB, Lo * QP * NC>([&](int pp, int it) { bwd_item<1, false>(Rp(pp) + B1, Rp(pp), it); });
+      __syncthreads();
+      coop<NT, PPB, Lo * Lo * NC>([&](int pp, int it) { bwd_item<0, ACC>(Rp(pp), out + pp * sout, it); });
+      __syncthreads();
+    } else {
+      coop<NT, PPB, L * NC>([&](int pp, int it) { fwd_item<0, INTIN>(in + pp * sin, Rp(pp), it); });
+      __syncthreads();
+      // y: R [L][QP] -> V [QP][QP] and F_1 = R + NQ (R holds L*QP <= NQ values)
+      coop<NT, PPB, QP * NC>([&](int pp, int it) { fwd_der_last_item<INTIN>(Rp(pp), Vp(pp), Rp(pp) + NQ, it); });
+      __syncthreads();
+      constexpr int ND = QP * NC;
+      coop<NT, PPB, ND>([&](int pp, int it) { der_item<0>(Vp(pp), Rp(pp), it); });
+      __syncthreads();
+      coop<NT, PPB, NQ>([&](int pp, int pt) { quad_item(Rp(pp), pt, gcell, pp); });
+      __syncthreads();
+      coop<NT, PPB, ND>([&](int pp, int it) { dert_item<0, false>(Rp(pp), Vp(pp), it); });
+      __syncthreads();
+      // y: D^T F_1 + V -> B^T along y -> R [Lo][QP] (F_0 = R is dead)
+      coop<NT, PPB, QP>([&](int pp, int it) { dert_bwd_last_item(Rp(pp) + NQ, Vp(pp), Rp(pp), it); });
       __syncthreads();
       coop<NT, PPB, Lo * NC>([&](int pp, int it) { bwd_item<0, ACC>(Rp(pp), out + pp * sout, it); });
       __syncthreads();

@@ -21,4 +21,11 @@ struct Rules {
   double gw2[PMG_MAXQ + 1][PMG_MAXQ + 2];
 };
 
+using TableUploader = int (*)(const Tables<double>&, const Tables<float>&, const Rules&);
+// registry of the per-translation-unit uploaders (host code, basis.cpp)
+void register_table_uploader(TableUploader f);
+// upload the tables into every registered translation unit on the current
+// device; returns 0 or the first CUDA error code
+int upload_all_tables(const Tables<double>& t64, const Tables<float>& t32, const Rules& r);
+
 }  // namespace pmg

@@ -44,13 +44,22 @@ __device__ __forceinline__ double tabE<double>(int qf, int a, int b) { return c_
 template <>
 __device__ __forceinline__ float tabE<float>(int qf, int a, int b) { return c_tab_f32.E[qf][a][b]; }
 
-static inline cudaError_t upload_tables_tu(const Tables<double>& h64, const Tables<float>& h32,
-                                           const Rules& r) {
+static inline int upload_tables_tu(const Tables<double>& h64, const Tables<float>& h32, const Rules& r) {
   cudaError_t e = cudaMemcpyToSymbol(c_tab_f64, &h64, sizeof(h64));
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess) return (int)e;
   e = cudaMemcpyToSymbol(c_tab_f32, &h32, sizeof(h32));
-  if (e != cudaSuccess) return e;
-  return cudaMemcpyToSymbol(c_rules, &r, sizeof(r));
+  if (e != cudaSuccess) return (int)e;
+  return (int)cudaMemcpyToSymbol(c_rules, &r, sizeof(r));
 }
 
 }  // namespace pmg
+
+// Every translation unit that includes this header registers its uploader
+// when the library is loaded; upload_all_tables() (basis.cpp) calls them all
+// for the current device.
+namespace {
+struct PmgTableRegistrar {
+  PmgTableRegistrar() { pmg::register_table_uploader(&pmg::upload_tables_tu); }
+};
+static PmgTableRegistrar pmg_table_registrar;
+}  // namespace

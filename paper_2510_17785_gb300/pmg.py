@@ -30,6 +30,7 @@ SYMBOLS = (
     "pmg_local_vcycle", "pmg_get_bounds", "pmg_set_bounds", "pmg_compute_bounds", "pmg_get_ritz",
     "pmg_gmg_vcycle", "pmg_solve_cg", "pmg_solve_cg_host", "pmg_rhs_manufactured", "pmg_get_colours",
     "pmg_get_patch_map", "pmg_get_inv_diag", "pmg_sweep_flops", "pmg_launch_count", "pmg_fma_peak",
+    "pmg_tuning",
 )
 
 
@@ -38,7 +39,7 @@ class Options(C.Structure):
         ("smoother", C.c_int), ("cheb_degree", C.c_int), ("jacobi_omega", C.c_double), ("n_mg", C.c_int),
         ("bounds", C.c_int), ("lanczos_steps", C.c_int), ("bound_safety", C.c_double),
         ("bound_ratio", C.c_double), ("fixed_lo", C.c_double), ("fixed_hi", C.c_double),
-        ("seed", C.c_uint64), ("precision", C.c_int),
+        ("seed", C.c_uint64), ("precision", C.c_int), ("autotune", C.c_int), ("variant", C.c_int),
     ]
 
 
@@ -90,6 +91,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pmg_sweep_flops": (d, [vp, i]),
         "pmg_launch_count": (i, [vp, P(i64)]),
         "pmg_fma_peak": (i, [vp, i, P(d)]),
+        "pmg_tuning": (i, [vp, P(i), P(i), P(i), P(C.c_float)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -259,6 +261,13 @@ class Context:
 
     def sweep_flops(self, level) -> float:
         return self.lib.pmg_sweep_flops(self.h, level)
+
+    def tuning(self):
+        """(variant, threads per CTA, patches per CTA, [ms per candidate variant])"""
+        v, t, b = C.c_int(), C.c_int(), C.c_int()
+        ms = (C.c_float * 4)()
+        self._check(self.lib.pmg_tuning(self.h, C.byref(v), C.byref(t), C.byref(b), ms))
+        return v.value, t.value, b.value, list(ms)
 
     def launch_count(self) -> int:
         n = C.c_int64()

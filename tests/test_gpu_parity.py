@@ -301,3 +301,47 @@ def test_empty_local_batch_is_a_no_op():
     d = torch.zeros(1, dtype=torch.float64, device="cuda")
     ctx.local_vcycle(0, torch.zeros(0, dtype=torch.int64, device="cuda"), d, d, 1)
     ctx.close()
+
+
+def test_recomputing_bounds_reuses_scratch_and_is_reproducible():
+    from paper_2510_17785_gb300 import pmg
+    w = wl(3, 4, 4)
+    ctx, _ = gpu_ctx(w)
+    a = ctx.get_ritz(0)
+    for _ in range(3):
+        ctx.compute_bounds(pmg.BOUNDS_LANCZOS)
+    assert np.array_equal(ctx.get_ritz(0), a)
+    ctx.compute_bounds(pmg.BOUNDS_FIXED)
+    b = ctx.get_bounds(0)
+    assert np.all(b[:, 0, 0] == ctx.options.fixed_lo) and np.all(b[:, 0, 1] == ctx.options.fixed_hi)
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_launch_shape_variants_are_bit_identical(precision):
+    """Every launch-shape variant of the sweep kernel computes the same bits
+    (one owner thread per output, fixed summation order), so the set-up
+    autotuner may pick any of them."""
+    from paper_2510_17785_gb300 import pmg
+    prec = pmg.PREC_MIXED if precision == "mixed" else pmg.PREC_FP64
+    w = wl(3, 6, 4)
+    prob = inputs.make_problem(w)
+    u0 = inputs.random_vector(31, 3, 4, 6)
+    outs = []
+    for v in range(4):
+        ctx = pmg.Context(0, precision=prec, autotune=0, variant=v, **fixed())
+        ctx.mesh_structured(3, 6, 4, 2, prob.coords, prob.kappa)
+        try:
+            ctx.setup()
+        except pmg.PMGError as e:
+            assert e.code == 7            # variant does not exist for this configuration
+            ctx.close()
+            continue
+        u = dev(u0)
+        ctx.patch_smooth(1, dev(prob.rhs), u, 2, False)
+        torch.cuda.synchronize()
+        outs.append(u.cpu().numpy())
+        ctx.close()
+    assert len(outs) >= 2
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
