@@ -217,6 +217,31 @@ int pmg_launch_count(const pmg_ctx* ctx, int64_t* n);
  * (2 flops per FMA).  Synchronises the device. */
 int pmg_fma_peak(pmg_ctx* ctx, int precision, double* flops_per_s);
 
+/* ---- allocation-free bounds ----------------------------------------------
+ * No counterpart in the paper: an engineering entry point for callers that
+ * must not allocate device memory at this point (for instance while a CUDA
+ * graph is being captured, inside a framework that owns the device memory
+ * through its own allocator, or in a solver that refreshes its Chebyshev
+ * intervals mid-run and must not stall on cudaMalloc/cudaFree).
+ *
+ * Computes the same Lanczos estimates as pmg_compute_bounds (FP64, the
+ * context's Lanczos options) for patches first_patch .. first_patch +
+ * n_patches - 1 of mesh level `level` at p-level index k (degree p >> k, must
+ * be > 1) and writes n_patches x (theta_min, theta_max) to ritz_dev and
+ * n_patches x (lo, hi) to bounds_dev: caller-owned device FP64 arrays.  The
+ * context's own intervals are not changed.  Asynchronous on `stream`.
+ *
+ * Allocates no device memory: the Lanczos basis lives in one fixed 16 MiB
+ * device array inside the library (held by every GPU that loads it until the
+ * process exits).  Limit: n_patches * lanczos_steps * (2q-1)^d <= 2^21
+ * doubles, else PMG_ERR_ARG (split the range).  The first call on a device
+ * also uploads this entry point's tables and looks up the array's device
+ * address; make that first call before any stream capture.  All calls share
+ * the array: calls whose kernels overlap on the GPU race, so serialise them. */
+int pmg_lanczos_bounds_noalloc(pmg_ctx* ctx, int level, int k, int64_t first_patch,
+                               int64_t n_patches, double* ritz_dev, double* bounds_dev,
+                               void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,6 +14,7 @@
 
 #include "../../include/pmg.h"
 #include "basis.h"
+#include "lanczos_view.h"
 #include "launch.h"
 
 using namespace pmg;
@@ -1290,3 +1291,27 @@ int pmg_fma_peak(pmg_ctx* ctx, int precision, double* flops) {
 
 }  // extern "C"
 
+// ---------------------------------------------------------------------------
+// internal accessors (lanczos_view.h)
+namespace pmg {
+
+int lanczos_view(const pmg_ctx* ctx, int level, int k, LanczosView* v) {
+  if (!ctx || !v || !ctx->setup_ok || level < 0 || level >= ctx->nlev || k < 0 || k >= ctx->npl) return PMG_ERR_ARG;
+  const HLevel& h = ctx->L[level];
+  v->device = ctx->device;
+  v->dim = ctx->dim;
+  v->N = h.N;
+  v->q = h.pl[k].q;
+  v->ksteps = ctx->opt.lanczos_steps;
+  v->npatch = (int64_t)h.npatch;
+  v->G64 = h.pl[k].G64;
+  v->dinv64 = h.pl[k].dinv64;
+  v->seed = ctx->opt.seed;
+  v->safety = ctx->opt.bound_safety;
+  v->ratio = ctx->opt.bound_ratio;
+  return PMG_OK;
+}
+
+int set_last_error(pmg_ctx* ctx, int code, const char* msg) { return fail(ctx, code, msg); }
+
+}  // namespace pmg

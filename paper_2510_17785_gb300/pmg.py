@@ -30,7 +30,7 @@ SYMBOLS = (
     "pmg_local_vcycle", "pmg_get_bounds", "pmg_set_bounds", "pmg_compute_bounds", "pmg_get_ritz",
     "pmg_gmg_vcycle", "pmg_solve_cg", "pmg_solve_cg_host", "pmg_rhs_manufactured", "pmg_get_colours",
     "pmg_get_patch_map", "pmg_get_inv_diag", "pmg_sweep_flops", "pmg_launch_count", "pmg_fma_peak",
-    "pmg_tuning",
+    "pmg_lanczos_bounds_noalloc", "pmg_tuning",
 )
 
 
@@ -91,6 +91,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pmg_sweep_flops": (d, [vp, i]),
         "pmg_launch_count": (i, [vp, P(i64)]),
         "pmg_fma_peak": (i, [vp, i, P(d)]),
+        "pmg_lanczos_bounds_noalloc": (i, [vp, i, i, i64, i64, vp, vp, vp]),
         "pmg_tuning": (i, [vp, P(i), P(i), P(i), P(C.c_float)]),
     }
     for name, (res, args) in sig.items():
@@ -273,6 +274,13 @@ class Context:
         n = C.c_int64()
         self._check(self.lib.pmg_launch_count(self.h, C.byref(n)))
         return n.value
+
+    def lanczos_bounds_noalloc(self, level, k, first_patch, n_patches, ritz, bounds, stream=None):
+        """Lanczos intervals for a patch range without any device allocation
+        (see include/pmg.h); ritz and bounds are float64 CUDA tensors of
+        n_patches x 2 values."""
+        self._check(self.lib.pmg_lanczos_bounds_noalloc(self.h, level, k, first_patch, n_patches, _ptr(ritz),
+                                                        _ptr(bounds), _stream(stream)))
 
     def fma_peak(self, precision) -> float:
         f = C.c_double()
