@@ -48,7 +48,8 @@ enum {
 
 /* ---- options ----------------------------------------------------------- */
 enum { PMG_SMOOTHER_CHEBYSHEV = 0, PMG_SMOOTHER_JACOBI = 1 };
-enum { PMG_BOUNDS_LANCZOS = 0, PMG_BOUNDS_FIXED = 1, PMG_BOUNDS_USER = 2 };
+enum { PMG_BOUNDS_LANCZOS = 0, PMG_BOUNDS_FIXED = 1, PMG_BOUNDS_USER = 2,
+       PMG_BOUNDS_MLP = 3   /* learned intervals (pmg_set_mlp), see below      */ };
 enum { PMG_PREC_FP64 = 0,  /* everything in FP64                               */
        PMG_PREC_MIXED = 1  /* patch smoother, local p-MG and GMG levels in FP32;
                               outer CG, its residuals and dots, and the coarse
@@ -70,12 +71,17 @@ typedef struct pmg_options {
                             patch kernel on the finest level and keeps the
                             fastest; 0: use `variant`                          */
   int variant;           /* launch-shape variant when autotune = 0 (0 = default) */
+  double mlp_safety;     /* PMG_BOUNDS_MLP: hi = mlp_safety * predicted theta_max */
+  int coarse_kappa;      /* coefficient of a coarse cell from its 2^d children:
+                            PMG_KAPPA_ARITHMETIC, _GEOMETRIC or _HARMONIC mean  */
 } pmg_options;
+enum { PMG_KAPPA_ARITHMETIC = 0, PMG_KAPPA_GEOMETRIC = 1, PMG_KAPPA_HARMONIC = 2 };
 
 typedef struct pmg_ctx pmg_ctx;
 
 /* Fill `opt` with the defaults: Chebyshev degree 3, N_MG = 1, Lanczos bounds
- * with 16 steps, safety 1.1, ratio 10, omega 0.5, seed 0, FP64, autotune on. */
+ * with 16 steps, safety 1.1, ratio 10, omega 0.5, seed 0, FP64, autotune on,
+ * MLP safety 1.2. */
 void pmg_default_options(pmg_options* opt);
 
 /* Create a context on CUDA device `device`; `opt` may be NULL (defaults).
@@ -91,8 +97,9 @@ const char* pmg_last_error(const pmg_ctx* ctx);
  * 2^(n_levels-1)).  coords: ((N+1)^dim x dim) FP64 vertex coordinates in
  * lexicographic vertex order (x fastest); vertices of coarser levels are the
  * finest-level vertices with even indices.  kappa: N^dim FP64 cell values of
- * the coefficient (paper: mu); a coarse cell takes the arithmetic mean of its
- * 2^dim children.  Boundary vertices must lie on the boundary of the unit
+ * the coefficient (paper: mu); a coarse cell takes the mean of its
+ * 2^dim children (options.coarse_kappa: arithmetic, geometric or harmonic).
+ * Boundary vertices must lie on the boundary of the unit
  * square/cube for the Dirichlet data to mean what it says (not checked). */
 int pmg_mesh_structured(pmg_ctx* ctx, int dim, int N, int p, int n_levels,
                         const double* coords, const double* kappa);
@@ -200,11 +207,51 @@ double pmg_sweep_flops(const pmg_ctx* ctx, int level);
 
 /* Launch shape chosen for the patch-sweep kernel: variant index, threads per
  * CTA, patches per CTA, and the set-up timings of the candidate variants
- * (ms for one colour of the finest level, ms_per_variant[4], -1 where a
+ * (ms for one colour of the finest level, ms_per_variant[8], -1 where a
  * variant does not exist or was not timed).  Any output may be NULL.
  * Every variant computes bit-identical results. */
 int pmg_tuning(const pmg_ctx* ctx, int* variant, int* threads, int* patches_per_cta,
                float* ms_per_variant);
+
+/* ---- learned Chebyshev intervals ------------------------------------------
+ * No counterpart in the paper (its smoother is damped Jacobi).  A small MLP
+ * predicts (log theta_max, log theta_min) of the Lanczos run of a patch from
+ * 16 features of its cells' geometry and coefficient; Lanczos stays the
+ * judge.  Network 16 -> 64 -> 64 -> 2 with ReLU on standardised inputs and
+ * targets; PMG_MLP_NPARAM parameters (W1 64x16 row-major, b1, W2 64x64, b2,
+ * W3 2x64, b3) and PMG_MLP_NNORM normalisation floats (mean and std of the 16
+ * features, then mean and std of the 2 targets).  Training is FP32 (Adam),
+ * inference BF16 with FP32 accumulation.  Loss per sample: sum_o w_o (y_o -
+ * t_o)^2 / 2, w_0 = asym when theta_max is underestimated, averaged. */
+#define PMG_MLP_NPARAM 5378
+#define PMG_MLP_NNORM 36
+
+typedef struct pmg_train_opts {
+  int epochs;
+  int batch;
+  float lr, beta1, beta2, eps;
+  float asym;            /* weight of underestimated theta_max               */
+  uint64_t seed;         /* shuffling                                        */
+} pmg_train_opts;
+void pmg_default_train_options(pmg_train_opts* opt);
+
+/* Features of every patch of mesh level l at p-level index k: device float
+ * array of n_patches x 16 (layout and definitions in the implementation). */
+int pmg_features(pmg_ctx* ctx, int level, int k, float* X_dev, void* stream);
+/* Loss and gradient of the loss on n samples (X: n x 16 raw features, T:
+ * n x 2 raw targets; all device pointers; one batch of all n). */
+int pmg_mlp_grad(int device, const float* params_dev, const float* norm_dev, const float* X_dev,
+                 const float* T_dev, int n, float asym, float* loss_dev, float* grad_dev, void* stream);
+/* Train in place (params_dev: initial -> trained) on n samples; writes the
+ * mean batch loss of every epoch to loss_hist_host (may be NULL). */
+int pmg_mlp_train(int device, float* params_dev, const float* norm_dev, const float* X_dev,
+                  const float* T_dev, int64_t n, const pmg_train_opts* opt, float* loss_hist_host);
+/* Y (n x 2 device) = predicted (log theta_max, log theta_min); bf16 != 0
+ * rounds weights and activations to BF16 (FP32 accumulation). */
+int pmg_mlp_predict(int device, const float* params_dev, const float* norm_dev, const float* X_dev,
+                    int64_t n, int bf16, float* Y_dev, void* stream);
+/* Install a trained network (host arrays) for PMG_BOUNDS_MLP. */
+int pmg_set_mlp(pmg_ctx* ctx, const float* params_host, const float* norm_host);
 
 /* ---- measurement ----------------------------------------------------------
  * Number of kernels this context has launched so far (kernel nodes of a CUDA

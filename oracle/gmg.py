@@ -6,7 +6,8 @@ Test infrastructure only.
   square/cube with N_l = N_c * 2^(l-1) cells per direction.  The vertices of
   a coarser level are the fine-level vertices with even indices (topological
   nestedness; the coarse cells are the multilinear images of those vertices).
-  The coefficient of a coarse cell is the arithmetic mean of its 2^d children.
+  The coefficient of a coarse cell is the arithmetic (default), geometric or
+  harmonic mean of its 2^d children.
 * Transfers: prolongation is the embedding through the reference cells
   (a fine node's value is the coarse cell's function at the fine node's
   position in the coarse reference cell); restriction is its transpose
@@ -27,7 +28,7 @@ import scipy.sparse as sp
 from . import fem, patch as pt, rules
 
 
-def coarsen(mesh: fem.StructuredMesh) -> fem.StructuredMesh:
+def coarsen(mesh: fem.StructuredMesh, kappa_rule: str = "arithmetic") -> fem.StructuredMesh:
     d, N = mesh.dim, mesh.N
     assert N % 2 == 0
     Nc = N // 2
@@ -36,17 +37,19 @@ def coarsen(mesh: fem.StructuredMesh) -> fem.StructuredMesh:
     Xc = X[sl].reshape(-1, d)
     kap = mesh.kappa.reshape(*([N] * d))
     kc = np.zeros([Nc] * d)
+    f, finv = {"arithmetic": (lambda k: k, lambda m: m), "geometric": (np.log, np.exp),
+               "harmonic": (lambda k: 1.0 / k, lambda m: 1.0 / m)}[kappa_rule]
     for off in fem._lex(d, 2):
         idx = tuple(slice(off[d - 1 - a], None, 2) for a in range(d))   # array axes are reversed
-        kc += kap[idx]
-    kc /= 2 ** d
+        kc += f(kap[idx])
+    kc = finv(kc / 2 ** d)
     return fem.StructuredMesh(d, Nc, Xc, kc.reshape(-1))
 
 
-def hierarchy(mesh: fem.StructuredMesh, coarse_N: int):
+def hierarchy(mesh: fem.StructuredMesh, coarse_N: int, kappa_rule: str = "arithmetic"):
     out = [mesh]
     while out[-1].N > coarse_N:
-        out.append(coarsen(out[-1]))
+        out.append(coarsen(out[-1], kappa_rule))
     assert out[-1].N == coarse_N
     return out[::-1]                     # coarsest first
 
@@ -73,9 +76,10 @@ def prolongation(coarse: fem.StructuredMesh, fine: fem.StructuredMesh, q: int) -
 
 
 class GMG:
-    def __init__(self, fine: fem.StructuredMesh, p: int, coarse_N: int, smoother_args=None):
+    def __init__(self, fine: fem.StructuredMesh, p: int, coarse_N: int, smoother_args=None,
+                 kappa_rule: str = "arithmetic"):
         self.p = p
-        self.meshes = hierarchy(fine, coarse_N)
+        self.meshes = hierarchy(fine, coarse_N, kappa_rule)
         self.free = [m.free_mask(p) for m in self.meshes]
         self.A = []
         for m, f in zip(self.meshes, self.free):

@@ -11,6 +11,7 @@ PMG_EXTERN_PATCH(3, double, 7)
 PMG_EXTERN_PATCH(3, double, 8)
 PMG_INSTANTIATE_DIM_T(3, double)
 namespace pmg {
+template int launch_dense_patch<3>(int, const double*, int, int, int, double*, cudaStream_t);
 template int launch_fma_chain<double>(double*, int, int, int, cudaStream_t);
 template int launch_diag<3>(const double*, int, int, double*, double*, float*, cudaStream_t);
 template int launch_rhs_manufactured<3>(const double*, int, int, double*, cudaStream_t);

@@ -62,6 +62,10 @@ int launch_patch_P(int mode, int variant, const PatchArgs<T>& a, cudaStream_t s)
       case 1: return launch_patch_PV<DIM, P, T, 1>(mode, a, s);
       case 2: return launch_patch_PV<DIM, P, T, 2>(mode, a, s);
       case 3: return launch_patch_PV<DIM, P, T, 3>(mode, a, s);
+      case 4: return launch_patch_PV<DIM, P, T, 4>(mode, a, s);
+      case 5: return launch_patch_PV<DIM, P, T, 5>(mode, a, s);
+      case 6: return launch_patch_PV<DIM, P, T, 6>(mode, a, s);
+      case 7: return launch_patch_PV<DIM, P, T, 7>(mode, a, s);
       default: return ST_UNSUPPORTED;
     }
   }
@@ -99,6 +103,10 @@ void patch_config_P(int variant, size_t* smem, int* ppb, int* nt) {
     case 1: return patch_config_PV<DIM, P, T, 1>(smem, ppb, nt);
     case 2: return patch_config_PV<DIM, P, T, 2>(smem, ppb, nt);
     case 3: return patch_config_PV<DIM, P, T, 3>(smem, ppb, nt);
+    case 4: return patch_config_PV<DIM, P, T, 4>(smem, ppb, nt);
+    case 5: return patch_config_PV<DIM, P, T, 5>(smem, ppb, nt);
+    case 6: return patch_config_PV<DIM, P, T, 6>(smem, ppb, nt);
+    case 7: return patch_config_PV<DIM, P, T, 7>(smem, ppb, nt);
     default: *smem = 0; *ppb = 0; *nt = 0;
   }
 }
@@ -151,6 +159,23 @@ int launch_lanczos(int q, const LanczosArgs<T>& a, cudaStream_t s) {
     case 8: return launch_lanczos_Q<DIM, 8, T>(a, s);
     default: return ST_UNSUPPORTED;
   }
+}
+
+template <int DIM>
+int launch_dense_patch(int q, const double* G64, int N, int first, int n, double* A, cudaStream_t s) {
+  if (n <= 0) return ST_OK;
+  switch (q) {
+    case 2: k_dense_patch<DIM, 2><<<n, 128, 0, s>>>(G64, N, first, n, A); break;
+    case 3:
+      if constexpr (DIM == 2) { k_dense_patch<DIM, 3><<<n, 128, 0, s>>>(G64, N, first, n, A); break; }
+      return ST_UNSUPPORTED;
+    case 4:
+      if constexpr (DIM == 2) { k_dense_patch<DIM, 4><<<n, 128, 0, s>>>(G64, N, first, n, A); break; }
+      return ST_UNSUPPORTED;
+    default: return ST_UNSUPPORTED;
+  }
+  PMG_CHECK_LAUNCH();
+  return ST_OK;
 }
 
 template <int DIM, int Q, typename T>

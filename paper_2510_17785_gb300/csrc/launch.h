@@ -30,6 +30,10 @@ int launch_lanczos(int q, const LanczosArgs<T>& a, cudaStream_t s);
 template <int DIM, typename T>
 int launch_cell_apply(int q, const T* u, T* out, const T* G, int N, cudaStream_t s);
 
+// dense patch matrices [n][Ni][Ni] of patches first .. first+n-1 at degree q (FP64)
+template <int DIM>
+int launch_dense_patch(int q, const double* G64, int N, int first, int n, double* A, cudaStream_t s);
+
 template <int DIM, typename T>
 int launch_geometry(const double* coords, const double* kappa, int N, int q, T* G, int* err, cudaStream_t s);
 

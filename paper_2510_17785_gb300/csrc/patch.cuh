@@ -29,7 +29,14 @@ struct LevelArgs {
   const T* G;          // geometry tensors of degree q: [cells][ncomp][(q+1)^d]
   const T* dinv;       // 1 / diag(A_q) on the global degree-q grid, 0 on Dirichlet
   const T* bounds;     // [patches][2]: Chebyshev interval (lo, hi), q > 1
+  const T* dense;      // small levels: [patches][Ni][Ni] row-major patch matrix A_{j,q}
 };
+
+// Levels whose patch operator is small enough to be applied as a dense
+// matrix (Ni <= 64: q <= 2 in 3D, q <= 4 in 2D; never the p = 1 level).
+__host__ __device__ constexpr bool dense_level(int dim, int q) {
+  return q > 1 && (dim == 3 ? (2 * q - 1) * (2 * q - 1) * (2 * q - 1) : (2 * q - 1) * (2 * q - 1)) <= 64;
+}
 
 template <typename T>
 struct PatchArgs {
@@ -49,7 +56,7 @@ struct PatchArgs {
   int* err;                    // device error flag
 };
 
-template <int DIM, int P>
+template <int DIM, int P, bool LINE = false>
 struct Layout {
   static constexpr int NL = nlevels(P);
   __host__ __device__ static constexpr int q(int k) { return P >> k; }
@@ -63,42 +70,79 @@ struct Layout {
   __host__ __device__ static constexpr int DIR(int k) { return off(k) + 3 * ni(k); }
   __host__ __device__ static constexpr int AD(int k) { return q(k) == 1 ? off(k) + 3 : off(k) + 4 * ni(k); }
   __host__ __device__ static constexpr int DINV(int k) { return q(k) == 1 ? off(k) + 2 : off(k) + 5 * ni(k); }
-  static constexpr int CLOS = off(NL);
+  // dense patch matrices of the small levels, staged per patch
+  __host__ __device__ static constexpr int dsz(int k) { return dense_level(DIM, q(k)) ? ni(k) * ni(k) : 0; }
+  __host__ __device__ static constexpr int doff(int k) { return k == 0 ? off(NL) : doff(k - 1) + dsz(k - 1); }
+  __host__ __device__ static constexpr int DENSE(int k) { return doff(k); }
+  static constexpr int CLOS = doff(NL);
   static constexpr int NN0 = ipow(2 * P + 1, DIM);
   static constexpr int SCR = CLOS + NN0;
-  static constexpr int SCRATCH = Dims<DIM, 2, P>::SCRATCH;
+  static constexpr int SCRATCH = LINE ? Dims<DIM, 2, P>::SCRATCH_LINE : Dims<DIM, 2, P>::SCRATCH;
   static constexpr int COEF = SCR + SCRATCH;      // per level: 1/theta, c1[1..7], c2[1..7]
   static constexpr int NCOEF = 16;
   static constexpr int PS_RAW = COEF + NL * NCOEF;
   static constexpr int PS = (PS_RAW + 3) & ~3;    // per-patch stride in elements
 };
 
-// Launch shape of the patch kernel.  Variant 0 is the default; variants 1..3
-// (threads per CTA, patches per CTA) = (256, 2), (128, 1), (512, 4) are the
-// candidates the set-up autotuner times for 3D degrees 3..8.
+// Launch shape of the patch kernel.  Variant 0 is the default; for 3D degrees
+// 3..8 the set-up autotuner also times variants 1..7:
+//   variant:          1        2        3        4        5        6        7
+//   design:         stage    stage    stage    line     line     stage    stage
+//   threads / CTA:    256      128      512      256      128      256      128
+//   patches / CTA:      2        1        4        2        1        4        2
+// (patches per CTA are capped by shared memory).  "stage": every direction's
+// flux in shared memory; "line": one thread per line along the last
+// direction keeps that direction's gradient and flux in registers.
+constexpr int NUM_VARIANTS = 8;
+
 template <int DIM, int P, typename T, int V = 0>
 struct Config {
   static constexpr int NT0 = (DIM == 3) ? 256 : 128;
   static constexpr int PPB0 = (DIM == 3) ? (P <= 2 ? 4 : 1) : (P <= 2 ? 8 : (P <= 4 ? 4 : 2));
-  static constexpr int NT = V == 0 ? NT0 : (V == 1 ? 256 : (V == 2 ? 128 : 512));
-  static constexpr int PPB_MAX = V == 0 ? PPB0 : (V == 1 ? 2 : (V == 2 ? 1 : 4));
+  static constexpr int NTV[NUM_VARIANTS] = {NT0, 256, 128, 512, 256, 128, 256, 128};
+  static constexpr int PPBV[NUM_VARIANTS] = {PPB0, 2, 1, 4, 2, 1, 4, 2};
+  static constexpr bool LINEV[NUM_VARIANTS] = {false, false, false, false, true, true, false, false};
+  static constexpr int NT = NTV[V];
+  static constexpr int PPB_MAX = PPBV[V];
+  static constexpr bool LINE = LINEV[V];
   static constexpr size_t bytes_per_patch =
-      sizeof(T) * Layout<DIM, P>::PS + sizeof(int) * ((1 << DIM) + 4);
+      sizeof(T) * Layout<DIM, P, LINE>::PS + sizeof(int) * ((1 << DIM) + 4);
   static constexpr size_t SMEM_LIMIT = 227 * 1024;
   static constexpr int PPB_FIT = (int)(SMEM_LIMIT / bytes_per_patch);
   static constexpr int PPB = PPB_FIT < PPB_MAX ? (PPB_FIT < 1 ? 1 : PPB_FIT) : PPB_MAX;
   static constexpr size_t smem = bytes_per_patch * PPB;
   static constexpr bool fits = bytes_per_patch <= SMEM_LIMIT;
-  // a variant is distinct (worth instantiating) only if it differs from variant 0
-  static constexpr bool distinct = V == 0 || NT != Config<DIM, P, T, 0>::NT || PPB != Config<DIM, P, T, 0>::PPB;
+  // register budget per thread (launch bound): 64 for FP32 up to degree 5,
+  // 128 otherwise (FP64, or the larger line registers at high degree)
+  static constexpr int REG_TARGET = (sizeof(T) == 4 && P <= 5) ? 64 : 128;
+  static constexpr int MINB_RAW = 65536 / (NT * REG_TARGET);
+  static constexpr int MINB = MINB_RAW < 1 ? 1 : MINB_RAW;
+  // a variant exists (is worth instantiating) if it fits and differs from
+  // every lower-numbered variant
+  template <int W>
+  static constexpr bool same_as() {
+    return Config<DIM, P, T, W>::NT == NT && Config<DIM, P, T, W>::PPB == PPB && Config<DIM, P, T, W>::LINE == LINE;
+  }
+  static constexpr bool distinct_impl() {
+    if constexpr (V == 0) return true;
+    else if constexpr (V == 1) return !same_as<0>();
+    else if constexpr (V == 2) return !same_as<0>() && !same_as<1>();
+    else if constexpr (V == 3) return !same_as<0>() && !same_as<1>() && !same_as<2>();
+    else if constexpr (V == 4) return !same_as<0>() && !same_as<1>() && !same_as<2>() && !same_as<3>();
+    else if constexpr (V == 5) return !same_as<0>() && !same_as<1>() && !same_as<2>() && !same_as<3>() && !same_as<4>();
+    else if constexpr (V == 6)
+      return !same_as<0>() && !same_as<1>() && !same_as<2>() && !same_as<3>() && !same_as<4>() && !same_as<5>();
+    else
+      return !same_as<0>() && !same_as<1>() && !same_as<2>() && !same_as<3>() && !same_as<4>() && !same_as<5>() &&
+             !same_as<6>();
+  }
+  static constexpr bool distinct = distinct_impl();
 };
-
-constexpr int NUM_VARIANTS = 4;
 
 template <int DIM, int P, typename T, int MODE, int V = 0>
 struct PatchKernel {
-  using L = Layout<DIM, P>;
   using C = Config<DIM, P, T, V>;
+  using L = Layout<DIM, P, C::LINE>;
   static constexpr int NT = C::NT, PPB = C::PPB, NL = L::NL, PS = L::PS;
   static constexpr int NCELL = 1 << DIM;
 
@@ -117,21 +161,36 @@ struct PatchKernel {
     return [G, cl](int pp, int slot) { return G + (size_t)cl[pp * (NCELL + 4) + slot] * stride; };
   }
 
-  // out = A_q in on interior vectors of level K
+  // out = A_q in on interior vectors of level K (matrix-free, or the staged
+  // dense patch matrix on small levels)
   template <int K>
   __device__ void apply_int(int in_off, int out_off) {
     constexpr int q = P >> K;
-    SF<DIM, 2, q, T, NT, PPB>::template apply<true, false>(vec(0, in_off), PS, vec(0, out_off), PS,
-                                                          vec(0, L::SCR), PS, gfun<K>());
+    if constexpr (dense_level(DIM, q)) {
+      constexpr int NI = L::ni(K);
+      coop<NT, PPB, NI>([&](int pp, int r) {
+        const T* A = vec(pp, L::DENSE(K)) + r * NI;
+        const T* x = vec(pp, in_off);
+        T s = T(0);
+#pragma unroll
+        for (int c = 0; c < NI; ++c) s += A[c] * x[c];
+        vec(pp, out_off)[r] = s;
+      });
+      __syncthreads();
+    } else {
+      SF<DIM, 2, q, T, NT, PPB, C::LINE>::template apply<true, false>(vec(0, in_off), PS, vec(0, out_off), PS,
+                                                                     vec(0, L::SCR), PS, gfun<K>());
+    }
   }
 
   // ---- p-transfers between level K (degree qf) and K+1 (degree qc = qf/2)
   // Prolongation along axis AX on interior nodes: [O][Mc][I] -> [O][Mf][I]
   template <int K, int AX, bool ACC>
   __device__ static void prol_item(const T* __restrict__ in, T* __restrict__ out, int item, int Mc, int Mf,
-                                   int I) {
+                                   int I, int O) {
     constexpr int qf = P >> K, qc = qf >> 1;
-    const int c = item & 1, pi = item >> 1;
+    const int OI = O * I;
+    const int c = item >= OI, pi = item - c * OI;
     const int i = pi % I, o = pi / I;
     const T* src = in + o * Mc * I + i;
     T* dst = out + o * Mf * I + i;
@@ -157,9 +216,10 @@ struct PatchKernel {
   // Restriction (transpose) along axis AX: [O][Mf][I] -> [O][Mc][I]
   template <int K>
   __device__ static void rest_item(const T* __restrict__ in, T* __restrict__ out, int item, int Mc, int Mf,
-                                   int I) {
+                                   int I, int O) {
     constexpr int qf = P >> K, qc = qf >> 1;
-    const int c = item & 1, pi = item >> 1;
+    const int OI = O * I;
+    const int c = item >= OI, pi = item - c * OI;
     const int i = pi % I, o = pi / I;
     const T* src = in + o * Mf * I + i;
     T* dst = out + o * Mc * I + i;
@@ -204,22 +264,22 @@ struct PatchKernel {
     T* t = vec(0, L::SCR);
     if constexpr (DIM == 3) {
       coop<NT, PPB, Mf * Mf * 2>([&](int pp, int it) {
-        rest_item<K>(vec(pp, L::RES(K)), t + pp * PS, it, Mc, Mf, 1);
+        rest_item<K>(vec(pp, L::RES(K)), t + pp * PS, it, Mc, Mf, 1, Mf * Mf);
       });
       __syncthreads();
       coop<NT, PPB, Mf * Mc * 2>([&](int pp, int it) {
-        rest_item<K>(t + pp * PS, t + pp * PS + Mf * Mf * Mc, it, Mc, Mf, Mc);
+        rest_item<K>(t + pp * PS, t + pp * PS + Mf * Mf * Mc, it, Mc, Mf, Mc, Mf);
       });
       __syncthreads();
       coop<NT, PPB, Mc * Mc * 2>([&](int pp, int it) {
-        rest_item<K>(t + pp * PS + Mf * Mf * Mc, vec(pp, L::R_(K + 1)), it, Mc, Mf, Mc * Mc);
+        rest_item<K>(t + pp * PS + Mf * Mf * Mc, vec(pp, L::R_(K + 1)), it, Mc, Mf, Mc * Mc, 1);
       });
       __syncthreads();
     } else {
-      coop<NT, PPB, Mf * 2>([&](int pp, int it) { rest_item<K>(vec(pp, L::RES(K)), t + pp * PS, it, Mc, Mf, 1); });
+      coop<NT, PPB, Mf * 2>([&](int pp, int it) { rest_item<K>(vec(pp, L::RES(K)), t + pp * PS, it, Mc, Mf, 1, Mf); });
       __syncthreads();
       coop<NT, PPB, Mc * 2>([&](int pp, int it) {
-        rest_item<K>(t + pp * PS, vec(pp, L::R_(K + 1)), it, Mc, Mf, Mc);
+        rest_item<K>(t + pp * PS, vec(pp, L::R_(K + 1)), it, Mc, Mf, Mc, 1);
       });
       __syncthreads();
     }
@@ -233,24 +293,24 @@ struct PatchKernel {
     T* t = vec(0, L::SCR);
     if constexpr (DIM == 3) {
       coop<NT, PPB, Mc * Mc * 2>([&](int pp, int it) {
-        prol_item<K, 0, false>(vec(pp, L::D_(K + 1)), t + pp * PS, it, Mc, Mf, 1);
+        prol_item<K, 0, false>(vec(pp, L::D_(K + 1)), t + pp * PS, it, Mc, Mf, 1, Mc * Mc);
       });
       __syncthreads();
       coop<NT, PPB, Mc * Mf * 2>([&](int pp, int it) {
-        prol_item<K, 1, false>(t + pp * PS, t + pp * PS + Mc * Mc * Mf, it, Mc, Mf, Mf);
+        prol_item<K, 1, false>(t + pp * PS, t + pp * PS + Mc * Mc * Mf, it, Mc, Mf, Mf, Mc);
       });
       __syncthreads();
       coop<NT, PPB, Mf * Mf * 2>([&](int pp, int it) {
-        prol_item<K, 2, true>(t + pp * PS + Mc * Mc * Mf, vec(pp, L::D_(K)), it, Mc, Mf, Mf * Mf);
+        prol_item<K, 2, true>(t + pp * PS + Mc * Mc * Mf, vec(pp, L::D_(K)), it, Mc, Mf, Mf * Mf, 1);
       });
       __syncthreads();
     } else {
       coop<NT, PPB, Mc * 2>([&](int pp, int it) {
-        prol_item<K, 0, false>(vec(pp, L::D_(K + 1)), t + pp * PS, it, Mc, Mf, 1);
+        prol_item<K, 0, false>(vec(pp, L::D_(K + 1)), t + pp * PS, it, Mc, Mf, 1, Mc);
       });
       __syncthreads();
       coop<NT, PPB, Mf * 2>([&](int pp, int it) {
-        prol_item<K, 1, true>(t + pp * PS, vec(pp, L::D_(K)), it, Mc, Mf, Mf);
+        prol_item<K, 1, true>(t + pp * PS, vec(pp, L::D_(K)), it, Mc, Mf, Mf, 1);
       });
       __syncthreads();
     }
@@ -407,6 +467,13 @@ struct PatchKernel {
         const bool act = cells[pp * (NCELL + 4) + NCELL + 1];
         vec(pp, L::DINV(K))[i] = act ? a->lv[K].dinv[gindex_int<q>(pp, i)] : T(0);
       });
+      if constexpr (dense_level(DIM, q)) {
+        coop<NT, PPB, NI * NI>([&](int pp, int e) {
+          const bool act = cells[pp * (NCELL + 4) + NCELL + 1];
+          const int pid = cells[pp * (NCELL + 4) + NCELL];
+          vec(pp, L::DENSE(K))[e] = act ? a->lv[K].dense[(size_t)pid * NI * NI + e] : T(0);
+        });
+      }
       // Chebyshev coefficients (FP64 scalars, rounded to T)
       if (a->smoother == 0) {
         for (int pp = threadIdx.x; pp < PPB; pp += NT) {
@@ -450,13 +517,8 @@ struct PatchKernel {
       });
       __syncthreads();
       // Evaluate: r = b - A u on the patch interior
-      if constexpr (P > 1) {
-        SF<DIM, 2, P, T, NT, PPB>::template apply<false, false>(vec(0, L::CLOS), PS, vec(0, L::AD(0)), PS,
-                                                               vec(0, L::SCR), PS, gfun<0>());
-      } else {
-        SF<DIM, 2, 1, T, NT, PPB>::template apply<false, false>(vec(0, L::CLOS), PS, vec(0, L::AD(0)), PS,
-                                                               vec(0, L::SCR), PS, gfun<0>());
-      }
+      SF<DIM, 2, P, T, NT, PPB, C::LINE>::template apply<false, false>(vec(0, L::CLOS), PS, vec(0, L::AD(0)), PS,
+                                                                      vec(0, L::SCR), PS, gfun<0>());
       coop<NT, PPB, NI0>([&](int pp, int i) { vec(pp, L::R_(0))[i] -= vec(pp, L::AD(0))[i]; });
       __syncthreads();
     } else {
@@ -485,7 +547,8 @@ struct PatchKernel {
 };
 
 template <int DIM, int P, typename T, int MODE, int V = 0>
-__global__ void __launch_bounds__(Config<DIM, P, T, V>::NT) k_patch(const __grid_constant__ PatchArgs<T> args) {
+__global__ void __launch_bounds__(Config<DIM, P, T, V>::NT, Config<DIM, P, T, V>::MINB)
+    k_patch(const __grid_constant__ PatchArgs<T> args) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   using PK = PatchKernel<DIM, P, T, MODE, V>;
   PK k;
@@ -493,6 +556,44 @@ __global__ void __launch_bounds__(Config<DIM, P, T, V>::NT) k_patch(const __grid
   k.cells = reinterpret_cast<int*>(smem_raw + sizeof(T) * (size_t)PK::PS * PK::PPB);
   k.a = &args;
   k.run();
+}
+
+// ------------------------------------------------------------------------
+// Dense patch matrices of a small level (set-up): column i of A_{j,q} is the
+// matrix-free patch operator applied to the unit vector e_i.  One patch per
+// CTA; FP64.
+template <int DIM, int Q>
+__global__ void __launch_bounds__(128) k_dense_patch(const double* __restrict__ G, int N, int first_patch,
+                                                     int n_items, double* __restrict__ A) {
+  constexpr int NT = 128;
+  using Dm = Dims<DIM, 2, Q>;
+  constexpr int NI = Dm::NI;
+  constexpr int NCELL = 1 << DIM;
+  __shared__ double x[NI], y[NI], scr[Dm::SCRATCH];
+  __shared__ int cl[NCELL];
+  const int item = blockIdx.x;
+  if (item >= n_items) return;
+  const int pid = first_patch + item;
+  if (threadIdx.x < NCELL) {
+    const int Nv = N - 1;
+    int rem = pid, id = 0, mul = 1;
+    for (int ax = 0; ax < DIM; ++ax) {
+      const int v = 1 + rem % Nv;
+      rem /= Nv;
+      id += (v - 1 + ((threadIdx.x >> ax) & 1)) * mul;
+      mul *= N;
+    }
+    cl[threadIdx.x] = id;
+  }
+  const int* clp = cl;
+  auto gf = [G, clp](int, int slot) { return G + (size_t)clp[slot] * (Dm::NCOMP * Dm::NGC); };
+  for (int i = 0; i < NI; ++i) {
+    for (int r = threadIdx.x; r < NI; r += NT) x[r] = r == i ? 1.0 : 0.0;
+    __syncthreads();
+    SF<DIM, 2, Q, double, NT, 1>::template apply<true, false>(x, 0, y, 0, scr, 0, gf);
+    for (int r = threadIdx.x; r < NI; r += NT) A[((size_t)item * NI + r) * NI + i] = y[r];
+    __syncthreads();
+  }
 }
 
 // ------------------------------------------------------------------------

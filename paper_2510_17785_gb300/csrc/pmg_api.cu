@@ -16,6 +16,7 @@
 #include "basis.h"
 #include "lanczos_view.h"
 #include "launch.h"
+#include "mlp.h"
 
 using namespace pmg;
 
@@ -36,6 +37,8 @@ struct PLevel {
   double* bounds64 = nullptr;
   float* bounds32 = nullptr;
   double* ritz = nullptr;
+  double* dense64 = nullptr;   // small levels: dense patch matrices [patch][Ni][Ni]
+  float* dense32 = nullptr;
 };
 
 struct HLevel {
@@ -93,7 +96,9 @@ struct pmg_ctx {
   int64_t graph_launches_per_iter = 0;   // kernels recorded in one CG iteration graph
   int64_t launches = 0;                  // kernels launched so far
   int variant = 0;                       // launch shape of the patch-sweep kernel
-  float variant_ms[4] = {-1.f, -1.f, -1.f, -1.f};
+  float variant_ms[NUM_VARIANTS] = {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f};
+  float* mlp_params = nullptr;           // PMG_BOUNDS_MLP network and normalisation
+  float* mlp_norm = nullptr;
   double* lanczos_V = nullptr;           // Lanczos basis scratch, grown on demand, reused
   size_t lanczos_V_n = 0;
   std::vector<void*> allocs;
@@ -192,6 +197,13 @@ template <>
 const float* Boundsof<float>(const PLevel& pl) { return pl.bounds32; }
 
 template <typename T>
+const T* Denseof(const PLevel& pl);
+template <>
+const double* Denseof<double>(const PLevel& pl) { return pl.dense64; }
+template <>
+const float* Denseof<float>(const PLevel& pl) { return pl.dense32; }
+
+template <typename T>
 PatchArgs<T> patch_args(pmg_ctx* c, int level) {
   PatchArgs<T> a;
   std::memset(&a, 0, sizeof(a));
@@ -201,6 +213,7 @@ PatchArgs<T> patch_args(pmg_ctx* c, int level) {
     a.lv[k].G = Gof<T>(h.pl[k]);
     a.lv[k].dinv = Dinvof<T>(h.pl[k]);
     a.lv[k].bounds = Boundsof<T>(h.pl[k]);
+    a.lv[k].dense = Denseof<T>(h.pl[k]);
   }
   a.smoother = c->opt.smoother;
   a.cheb_degree = c->opt.cheb_degree;
@@ -428,7 +441,7 @@ int autotune_T(pmg_ctx* ctx, T* u, const T* b) {
 }
 
 int autotune(pmg_ctx* ctx) {
-  for (int v = 0; v < 4; ++v) ctx->variant_ms[v] = -1.f;
+  for (int v = 0; v < NUM_VARIANTS; ++v) ctx->variant_ms[v] = -1.f;
   if (!ctx->opt.autotune) {
     ctx->variant = ctx->opt.variant;
     size_t sm;
@@ -471,6 +484,8 @@ void pmg_default_options(pmg_options* o) {
   o->precision = PMG_PREC_FP64;
   o->autotune = 1;
   o->variant = 0;
+  o->mlp_safety = 1.2;
+  o->coarse_kappa = PMG_KAPPA_ARITHMETIC;
 }
 
 int pmg_create(int device, const pmg_options* opt, pmg_ctx** out) {
@@ -483,7 +498,7 @@ int pmg_create(int device, const pmg_options* opt, pmg_ctx** out) {
   const pmg_options& o = ctx->opt;
   if (o.cheb_degree < 1 || o.cheb_degree > 8 || o.n_mg < 1 || o.lanczos_steps < 1 || o.lanczos_steps > 64 ||
       (o.smoother != 0 && o.smoother != 1) || (o.precision != 0 && o.precision != 1) || o.bounds < 0 ||
-      o.bounds > 2 || !(o.bound_safety > 0) || !(o.bound_ratio >= 1) || o.variant < 0 ||
+      o.bounds > 3 || !(o.bound_safety > 0) || !(o.mlp_safety > 0) || o.coarse_kappa < 0 || o.coarse_kappa > 2 || !(o.bound_ratio >= 1) || o.variant < 0 ||
       o.variant >= NUM_VARIANTS) {
     delete ctx;
     return PMG_ERR_ARG;
@@ -595,12 +610,14 @@ int pmg_setup(pmg_ctx* ctx) {
         int ci[3] = {0, 0, 0};
         for (int ax = 0; ax < d; ++ax) { ci[ax] = (int)(rem % Nl); rem /= Nl; }
         double sum = 0.0;
+        const int rule = ctx->opt.coarse_kappa;
         for (int ch = 0; ch < (1 << d); ++ch) {
           size_t fid = 0, mul = 1;
           for (int ax = 0; ax < d; ++ax) { fid += (size_t)(2 * ci[ax] + ((ch >> ax) & 1)) * mul; mul *= Nf; }
-          sum += K[fid];
+          sum += rule == PMG_KAPPA_GEOMETRIC ? std::log(K[fid]) : (rule == PMG_KAPPA_HARMONIC ? 1.0 / K[fid] : K[fid]);
         }
-        Kc[c] = sum / (1 << d);
+        const double m = sum / (1 << d);
+        Kc[c] = rule == PMG_KAPPA_GEOMETRIC ? std::exp(m) : (rule == PMG_KAPPA_HARMONIC ? 1.0 / m : m);
       }
       X.swap(Xc);
       K.swap(Kc);
@@ -636,6 +653,16 @@ int pmg_setup(pmg_ctx* ctx) {
       }
       if (d == 2) ST(launch_diag<2>(pl.G64, h.N, q, diag, pl.dinv64, pl.dinv32, s));
       else ST(launch_diag<3>(pl.G64, h.N, q, diag, pl.dinv64, pl.dinv32, s));
+      if (dense_level(d, q) && h.npatch > 0) {
+        const size_t ni = ipow_sz(2 * q - 1, d);
+        DALLOC(pl.dense64, h.npatch * ni * ni);
+        if (d == 2) ST(launch_dense_patch<2>(q, pl.G64, h.N, 0, (int)h.npatch, pl.dense64, s));
+        else ST(launch_dense_patch<3>(q, pl.G64, h.N, 0, (int)h.npatch, pl.dense64, s));
+        if (mixed) {
+          DALLOC(pl.dense32, h.npatch * ni * ni);
+          ST(launch_cast_d2f(pl.dense64, pl.dense32, h.npatch * ni * ni, s));
+        }
+      }
       DALLOC(pl.bounds64, 2 * std::max<size_t>(h.npatch, 1));
       DALLOC(pl.bounds32, 2 * std::max<size_t>(h.npatch, 1));
       DALLOC(pl.ritz, 2 * std::max<size_t>(h.npatch, 1));
@@ -810,6 +837,20 @@ int pmg_compute_bounds(pmg_ctx* ctx, int source) {
         for (size_t j = 0; j < h.npatch; ++j) { v[2 * j] = ctx->opt.fixed_lo; v[2 * j + 1] = ctx->opt.fixed_hi; }
         CU(cudaMemcpy(pl.bounds64, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice));
         LK(1, launch_cast_d2f(pl.bounds64, pl.bounds32, v.size(), s));
+        continue;
+      }
+      if (source == PMG_BOUNDS_MLP) {
+        if (!ctx->mlp_params) return fail(ctx, PMG_ERR_ARG, "no network installed (pmg_set_mlp)");
+        float *X = nullptr, *Y = nullptr;
+        CU(cudaMalloc(&X, h.npatch * 16 * sizeof(float)));
+        CU(cudaMalloc(&Y, h.npatch * 2 * sizeof(float)));
+        ST(features_launch(d, h.coords, h.kappa, h.N, pl.q, ctx->npl - 1 - k, (int)h.npatch, X, s));
+        ST(mlp_infer_launch(ctx->mlp_params, ctx->mlp_norm, X, (int64_t)h.npatch, 1, Y, s));
+        ST(bounds_from_logs_launch(Y, (int64_t)h.npatch, ctx->opt.mlp_safety, ctx->opt.bound_ratio, pl.bounds32,
+                                   pl.bounds64, s));
+        CU(cudaStreamSynchronize(s));
+        cudaFree(X);
+        cudaFree(Y);
         continue;
       }
       if (source != PMG_BOUNDS_LANCZOS) return fail(ctx, PMG_ERR_ARG, "unknown bounds source");
@@ -1246,7 +1287,30 @@ int pmg_tuning(const pmg_ctx* ctx, int* variant, int* threads, int* ppb_out, flo
   if (threads) *threads = nt;
   if (ppb_out) *ppb_out = ppb;
   if (ms)
-    for (int v = 0; v < 4; ++v) ms[v] = ctx->variant_ms[v];
+    for (int v = 0; v < NUM_VARIANTS; ++v) ms[v] = ctx->variant_ms[v];
+  return PMG_OK;
+}
+
+int pmg_features(pmg_ctx* ctx, int level, int k, float* X, void* stream) {
+  int st = check_level(ctx, level);
+  if (st) return st;
+  if (k < 0 || k >= ctx->npl || !X) return fail(ctx, PMG_ERR_ARG, "bad p-level or null output");
+  HLevel& h = ctx->L[level];
+  ST(features_launch(ctx->dim, h.coords, h.kappa, h.N, h.pl[k].q, ctx->npl - 1 - k, (int)h.npatch, X,
+                     (cudaStream_t)stream));
+  return PMG_OK;
+}
+
+int pmg_set_mlp(pmg_ctx* ctx, const float* params, const float* norm) {
+  if (!ctx || !params || !norm) return PMG_ERR_ARG;
+  CU(cudaSetDevice(ctx->device));
+  if (!ctx->mlp_params) DALLOC(ctx->mlp_params, PMG_MLP_NPARAM);
+  if (!ctx->mlp_norm) DALLOC(ctx->mlp_norm, PMG_MLP_NNORM);
+  for (int i = 0; i < 16; ++i)
+    if (!(norm[16 + i] > 0)) return fail(ctx, PMG_ERR_ARG, "feature standard deviations must be positive");
+  if (!(norm[34] > 0) || !(norm[35] > 0)) return fail(ctx, PMG_ERR_ARG, "target standard deviations must be positive");
+  CU(cudaMemcpy(ctx->mlp_params, params, PMG_MLP_NPARAM * sizeof(float), cudaMemcpyHostToDevice));
+  CU(cudaMemcpy(ctx->mlp_norm, norm, PMG_MLP_NNORM * sizeof(float), cudaMemcpyHostToDevice));
   return PMG_OK;
 }
 

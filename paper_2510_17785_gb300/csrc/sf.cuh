@@ -18,7 +18,9 @@
 // points (collocation derivative D).  Each point multiplies the reference
 // gradient by the symmetric tensor G = w kappa det(J) J^-1 J^-T (stored per
 // cell as DIM*(DIM+1)/2 components).  Backward: D^T along each direction
-// summed, then B^T along z, y, x.
+// summed, then B^T along z, y, x.  Along the last direction one thread owns a
+// whole line for the interpolation, the point products and the transposed
+// sweeps, keeping that direction's gradient and flux in registers.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -44,8 +46,13 @@ struct Dims {
   // forward temporaries for the widest input (all nodes)
   static constexpr int T1 = ipow(M, DIM - 1) * QP;
   static constexpr int T2 = (DIM == 3) ? M * QP * QP : 0;
+  static constexpr int Lo = (NC == 2) ? Mi : M;
+  static constexpr int B = (DIM == 3) ? Lo * Lo * QP + Lo * QP * QP : Lo * QP;   // backward temporaries
+  // stage design: all DIM flux arrays in R; line design: DIM - 1 of them
   static constexpr int R = cmax(T1 + T2, DIM * NQ);
-  static constexpr int SCRATCH = NQ + R;          // V + R
+  static constexpr int R_LINE = cmax(cmax(T1 + T2, (DIM - 1) * NQ), B);
+  static constexpr int SCRATCH = NQ + R;          // V + R (stage design)
+  static constexpr int SCRATCH_LINE = NQ + R_LINE;
 };
 
 // A cooperative loop over PPB blocks x ITEMS work items.
@@ -58,7 +65,7 @@ __device__ __forceinline__ void coop(F&& f) {
   }
 }
 
-template <int DIM, int NC, int Q, typename T, int NT, int PPB>
+template <int DIM, int NC, int Q, typename T, int NT, int PPB, bool LINE = false>
 struct SF {
   using D = Dims<DIM, NC, Q>;
   static constexpr int n = D::n, M = D::M, Mi = D::Mi, QP = D::QP, NQ = D::NQ;
@@ -68,8 +75,9 @@ struct SF {
   __device__ __forceinline__ static void fwd_item(const T* __restrict__ in, T* __restrict__ out, int item) {
     constexpr int L = INTIN ? Mi : M;
     constexpr int I = ipow(QP, AX);
-    const int c = (NC == 2) ? (item & 1) : 0;
-    const int pi = (NC == 2) ? (item >> 1) : item;
+    constexpr int OI = ipow(L, DIM - 1 - AX) * I;     // items per cell
+    const int c = (NC == 2) ? (item >= OI) : 0;
+    const int pi = item - c * OI;
     const int i = pi % I, o = pi / I;
     const T* src = in + o * L * I + i;
     T* dst = out + o * QP * I + i;
@@ -101,8 +109,8 @@ struct SF {
     constexpr int AX = DIM - 1;
     constexpr int L = INTIN ? Mi : M;
     constexpr int I = ipow(QP, AX);
-    const int c = (NC == 2) ? (item & 1) : 0;
-    const int i = (NC == 2) ? (item >> 1) : item;
+    const int c = (NC == 2) ? (item >= I) : 0;
+    const int i = item - c * I;
     const T* src = in + i;
     T v[n];
 #pragma unroll
@@ -185,12 +193,186 @@ struct SF {
     }
   }
 
+  // ---- quadrature-point product: F_k <- sum_l G_kl F_l
+  // gcell(pp, slot) returns the G base pointer of cell `slot` of block pp.
+  template <typename GF>
+  __device__ __forceinline__ static void quad_item(T* __restrict__ F, int pt, const GF& gcell, int pp) {
+    constexpr int NGC = D::NGC;
+    int cslot = 0, lg = 0, rem = pt, mul = 1, cmul = 1;
+#pragma unroll
+    for (int ax = 0; ax < DIM; ++ax) {
+      const int qa = rem % QP;
+      rem /= QP;
+      const int ca = (NC == 2) ? (qa >= n) : 0;
+      const int ga = qa - ca * n;
+      cslot += ca * cmul;
+      lg += ga * mul;
+      cmul *= NC;
+      mul *= n;
+    }
+    const T* G = gcell(pp, cslot) + lg;
+    if (DIM == 3) {
+      const T g0 = F[pt], g1 = F[NQ + pt], g2 = F[2 * NQ + pt];
+      const T G00 = G[0], G01 = G[NGC], G02 = G[2 * NGC], G11 = G[3 * NGC], G12 = G[4 * NGC],
+              G22 = G[5 * NGC];
+      F[pt] = G00 * g0 + G01 * g1 + G02 * g2;
+      F[NQ + pt] = G01 * g0 + G11 * g1 + G12 * g2;
+      F[2 * NQ + pt] = G02 * g0 + G12 * g1 + G22 * g2;
+    } else {
+      const T g0 = F[pt], g1 = F[NQ + pt];
+      const T G00 = G[0], G01 = G[NGC], G11 = G[2 * NGC];
+      F[pt] = G00 * g0 + G01 * g1;
+      F[NQ + pt] = G01 * g0 + G11 * g1;
+    }
+  }
+
+  // ---- line-owner stages along the last axis (z in 3D, y in 2D).
+  // One thread owns one line (both cells, 2n points); the last-axis gradient
+  // and flux of the line stay in its registers between stages.
+  static constexpr int NLINE = ipow(QP, DIM - 1);          // lines per block
+  static constexpr int LPT = (PPB * NLINE + NT - 1) / NT;  // lines per thread
+
+  // forward interpolation along the last axis + collocation derivative:
+  // writes V (point values), keeps the last-axis gradient in gz
+  template <bool INTIN>
+  __device__ __forceinline__ static void line_fwd(const T* __restrict__ in, T* __restrict__ V, int i, T (&gz)[QP]) {
+    constexpr int L = INTIN ? Mi : M;
+    constexpr int I = NLINE;
+    static_assert(L > 0, "");
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      T v[n];
+#pragma unroll
+      for (int a = 0; a <= Q; ++a) {
+        const int k = c * Q + a;
+        if (INTIN) {
+          const bool ok = (k >= 1) && (k <= M - 2);
+          v[a] = ok ? in[(k - 1) * I + i] : T(0);
+        } else {
+          v[a] = in[k * I + i];
+        }
+      }
+      T w[n];
+#pragma unroll
+      for (int g = 0; g < n; ++g) {
+        T s = T(0);
+#pragma unroll
+        for (int a = 0; a <= Q; ++a) s += tabB<T>(Q, g, a) * v[a];
+        w[g] = s;
+        V[(c * n + g) * I + i] = s;
+      }
+#pragma unroll
+      for (int g = 0; g < n; ++g) {
+        T s = T(0);
+#pragma unroll
+        for (int h = 0; h < n; ++h) s += tabD<T>(Q, g, h) * w[h];
+        gz[c * n + g] = s;
+      }
+    }
+  }
+
+  // quadrature-point product along one line: F_0 .. F_{d-2} (other-direction
+  // gradients in shared memory) and gz (registers) -> fluxes in place / in fz
+  template <typename GF>
+  __device__ __forceinline__ static void line_quad(T* __restrict__ F, int i, const T (&gz)[QP], T (&fz)[QP],
+                                                   const GF& gcell, int pp) {
+    constexpr int NGC = D::NGC;
+    constexpr int I = NLINE;
+    // position of the line in the other directions
+    int cslot0 = 0, lg0 = 0;
+    {
+      int rem = i, mul = 1, cmul = 1;
+#pragma unroll
+      for (int ax = 0; ax < DIM - 1; ++ax) {
+        const int qa = rem % QP;
+        rem /= QP;
+        const int ca = (NC == 2) ? (qa >= n) : 0;
+        cslot0 += ca * cmul;
+        lg0 += (qa - ca * n) * mul;
+        cmul *= NC;
+        mul *= n;
+      }
+    }
+    constexpr int CSTRIDE = ipow(NC, DIM - 1);   // cell-slot step along the last axis
+    constexpr int GSTRIDE = ipow(n, DIM - 1);    // local point step along the last axis
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const T* Gc = gcell(pp, cslot0 + c * CSTRIDE) + lg0;
+#pragma unroll
+      for (int g = 0; g < n; ++g) {
+        const int pt = (c * n + g) * I + i;
+        const T* G = Gc + g * GSTRIDE;
+        if (DIM == 3) {
+          const T G00 = G[0], G01 = G[NGC], G02 = G[2 * NGC], G11 = G[3 * NGC], G12 = G[4 * NGC],
+                  G22 = G[5 * NGC];
+          const T g0 = F[pt], g1 = F[NQ + pt], g2 = gz[c * n + g];
+          F[pt] = G00 * g0 + G01 * g1 + G02 * g2;
+          F[NQ + pt] = G01 * g0 + G11 * g1 + G12 * g2;
+          fz[c * n + g] = G02 * g0 + G12 * g1 + G22 * g2;
+        } else {
+          const T G00 = G[0], G01 = G[NGC], G11 = G[2 * NGC];
+          const T g0 = F[pt], g1 = gz[c * n + g];
+          F[pt] = G00 * g0 + G01 * g1;
+          fz[c * n + g] = G01 * g0 + G11 * g1;
+        }
+      }
+    }
+  }
+
+  // transposed derivative along the last axis (fz in registers) added to the
+  // other directions' sums in Vp, then backward integration along that axis:
+  // output [Lo][I]
+  __device__ __forceinline__ static void line_bwd(const T (&fz)[QP], const T* __restrict__ Vp, T* __restrict__ out,
+                                                  int i) {
+    constexpr int I = NLINE;
+    T w[NC][n];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+#pragma unroll
+      for (int h = 0; h < n; ++h) {
+        T s = Vp[(c * n + h) * I + i];
+#pragma unroll
+        for (int g = 0; g < n; ++g) s += tabD<T>(Q, g, h) * fz[c * n + g];
+        w[c][h] = s;
+      }
+    }
+    if (NC == 1) {
+#pragma unroll
+      for (int a = 0; a <= Q; ++a) {
+        T s = T(0);
+#pragma unroll
+        for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, a) * w[0][g];
+        out[a * I + i] = s;
+      }
+    } else {
+#pragma unroll
+      for (int a = 1; a <= Q; ++a) {
+        T s = T(0);
+#pragma unroll
+        for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, a) * w[0][g];
+        if (a == Q) {
+#pragma unroll
+          for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, 0) * w[NC - 1][g];
+        }
+        out[(a - 1) * I + i] = s;
+      }
+#pragma unroll
+      for (int a = 1; a < Q; ++a) {
+        T s = T(0);
+#pragma unroll
+        for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, a) * w[NC - 1][g];
+        out[(Q + a - 1) * I + i] = s;
+      }
+    }
+  }
+
   // ---- collocation derivative along AX on [O][QP][I]
   template <int AX>
   __device__ __forceinline__ static void der_item(const T* __restrict__ in, T* __restrict__ out, int item) {
     constexpr int I = ipow(QP, AX);
-    const int c = (NC == 2) ? (item & 1) : 0;
-    const int pi = (NC == 2) ? (item >> 1) : item;
+    constexpr int OI = ipow(QP, DIM - 1 - AX) * I;    // items per cell
+    const int c = (NC == 2) ? (item >= OI) : 0;
+    const int pi = item - c * OI;
     const int i = pi % I, o = pi / I;
     const T* src = in + o * QP * I + c * n * I + i;
     T* dst = out + o * QP * I + c * n * I + i;
@@ -210,8 +392,9 @@ struct SF {
   template <int AX, bool ACC>
   __device__ __forceinline__ static void dert_item(const T* __restrict__ in, T* __restrict__ out, int item) {
     constexpr int I = ipow(QP, AX);
-    const int c = (NC == 2) ? (item & 1) : 0;
-    const int pi = (NC == 2) ? (item >> 1) : item;
+    constexpr int OI = ipow(QP, DIM - 1 - AX) * I;    // items per cell
+    const int c = (NC == 2) ? (item >= OI) : 0;
+    const int pi = item - c * OI;
     const int i = pi % I, o = pi / I;
     const T* src = in + o * QP * I + c * n * I + i;
     T* dst = out + o * QP * I + c * n * I + i;
@@ -234,8 +417,9 @@ struct SF {
   __device__ __forceinline__ static void bwd_item(const T* __restrict__ in, T* __restrict__ out, int item) {
     constexpr int I = ipow(QP, AX);
     constexpr int Lout = (NC == 2) ? Mi : M;
-    const int c = (NC == 2) ? (item & 1) : 0;
-    const int pi = (NC == 2) ? (item >> 1) : item;
+    constexpr int OI = ipow(Lout, DIM - 1 - AX) * I;  // items per cell
+    const int c = (NC == 2) ? (item >= OI) : 0;
+    const int pi = item - c * OI;
     const int i = pi % I, o = pi / I;
     const T* src = in + o * QP * I + i;
     T* dst = out + o * Lout * I + i;
@@ -278,45 +462,218 @@ struct SF {
     }
   }
 
-  // ---- quadrature-point product: F_k <- sum_l G_kl F_l
-  // gcell(pp, slot) returns the G base pointer of cell `slot` of block pp.
-  template <typename GF>
-  __device__ __forceinline__ static void quad_item(T* __restrict__ F, int pt, const GF& gcell, int pp) {
-    constexpr int NGC = D::NGC;
-    int cslot = 0, lg = 0, rem = pt, mul = 1, cmul = 1;
+  template <bool INTIN, bool ACC, typename GF>
+  __device__ __forceinline__ static void apply_line(const T* in, int sin, T* out, int sout, T* scr, int sscr,
+                                                    const GF& gcell) {
+    constexpr int L = INTIN ? Mi : M;
+    constexpr int Lo = (NC == 2) ? Mi : M;
+    // scratch: V = scr[0..NQ) (point values, later the transposed sums),
+    // R = scr[NQ..): forward temporaries, then F_0 (and F_1 in 3D).
+    auto Vp = [&](int pp) { return scr + pp * sscr; };
+    auto Rp = [&](int pp) { return scr + pp * sscr + NQ; };
+    T gz[LPT][QP], fz[LPT][QP];
+    if constexpr (DIM == 3) {
+      constexpr int T1 = L * L * QP;
+      coop<NT, PPB, L * L * NC>([&](int pp, int it) { fwd_item<0, INTIN>(in + pp * sin, Rp(pp), it); });
+      __syncthreads();
+      coop<NT, PPB, L * QP * NC>([&](int pp, int it) { fwd_item<1, INTIN>(Rp(pp), Rp(pp) + T1, it); });
+      __syncthreads();
 #pragma unroll
-    for (int ax = 0; ax < DIM; ++ax) {
-      const int qa = rem % QP;
-      rem /= QP;
-      const int ca = (NC == 2) ? (qa >= n) : 0;
-      const int ga = qa - ca * n;
-      cslot += ca * cmul;
-      lg += ga * mul;
-      cmul *= NC;
-      mul *= n;
-    }
-    const T* G = gcell(pp, cslot) + lg;
-    if (DIM == 3) {
-      const T g0 = F[pt], g1 = F[NQ + pt], g2 = F[2 * NQ + pt];
-      const T G00 = G[0], G01 = G[NGC], G02 = G[2 * NGC], G11 = G[3 * NGC], G12 = G[4 * NGC],
-              G22 = G[5 * NGC];
-      F[pt] = G00 * g0 + G01 * g1 + G02 * g2;
-      F[NQ + pt] = G01 * g0 + G11 * g1 + G12 * g2;
-      F[2 * NQ + pt] = G02 * g0 + G12 * g1 + G22 * g2;
+      for (int l = 0; l < LPT; ++l) {
+        const int it = threadIdx.x + l * NT;
+        if (it < PPB * NLINE) {
+          const int pp = it / NLINE;
+          line_fwd<INTIN>(Rp(pp) + T1, Vp(pp), it - pp * NLINE, gz[l]);
+        }
+      }
+      __syncthreads();
+      constexpr int ND = QP * QP * NC;
+      coop<NT, PPB, 2 * ND>([&](int pp, int it) {
+        const int ax = it / ND, r = it - ax * ND;
+        if (ax == 0) der_item<0>(Vp(pp), Rp(pp), r);
+        else der_item<1>(Vp(pp), Rp(pp) + NQ, r);
+      });
+      __syncthreads();
+#pragma unroll
+      for (int l = 0; l < LPT; ++l) {
+        const int it = threadIdx.x + l * NT;
+        if (it < PPB * NLINE) {
+          const int pp = it / NLINE;
+          line_quad(Rp(pp), it - pp * NLINE, gz[l], fz[l], gcell, pp);
+        }
+      }
+      __syncthreads();
+      coop<NT, PPB, ND>([&](int pp, int it) { dert_item<0, false>(Rp(pp), Vp(pp), it); });
+      __syncthreads();
+      coop<NT, PPB, ND>([&](int pp, int it) { dert_item<1, true>(Rp(pp) + NQ, Vp(pp), it); });
+      __syncthreads();
+      constexpr int B1 = Lo * Lo * QP;       // [Lo][Lo][QP]
+      static_assert(B1 + Lo * QP * QP <= Dims<DIM, NC, Q>::R_LINE, "backward temporaries exceed R");
+#pragma unroll
+      for (int l = 0; l < LPT; ++l) {
+        const int it = threadIdx.x + l * NT;
+        if (it < PPB * NLINE) {
+          const int pp = it / NLINE;
+          line_bwd(fz[l], Vp(pp), Rp(pp) + B1, it - pp * NLINE);
+        }
+      }
+      __syncthreads();
+      coop<NT, PPB, Lo * QP * NC>([&](int pp, int it) { bwd_item<1, false>(Rp(pp) + B1, Rp(pp), it); });
+      __syncthreads();
+      coop<NT, PPB, Lo * Lo * NC>([&](int pp, int it) { bwd_item<0, ACC>(Rp(pp), out + pp * sout, it); });
+      __syncthreads();
     } else {
-      const T g0 = F[pt], g1 = F[NQ + pt];
-      const T G00 = G[0], G01 = G[NGC], G11 = G[2 * NGC];
-      F[pt] = G00 * g0 + G01 * g1;
-      F[NQ + pt] = G01 * g0 + G11 * g1;
+      coop<NT, PPB, L * NC>([&](int pp, int it) { fwd_item<0, INTIN>(in + pp * sin, Rp(pp), it); });
+      __syncthreads();
+#pragma unroll
+      for (int l = 0; l < LPT; ++l) {
+        const int it = threadIdx.x + l * NT;
+        if (it < PPB * NLINE) {
+          const int pp = it / NLINE;
+          line_fwd<INTIN>(Rp(pp), Vp(pp), it - pp * NLINE, gz[l]);
+        }
+      }
+      __syncthreads();
+      constexpr int ND = QP * NC;
+      coop<NT, PPB, ND>([&](int pp, int it) { der_item<0>(Vp(pp), Rp(pp), it); });
+      __syncthreads();
+#pragma unroll
+      for (int l = 0; l < LPT; ++l) {
+        const int it = threadIdx.x + l * NT;
+        if (it < PPB * NLINE) {
+          const int pp = it / NLINE;
+          line_quad(Rp(pp), it - pp * NLINE, gz[l], fz[l], gcell, pp);
+        }
+      }
+      __syncthreads();
+      coop<NT, PPB, ND>([&](int pp, int it) { dert_item<0, false>(Rp(pp), Vp(pp), it); });
+      __syncthreads();
+      // R [Lo][QP] (F_0 is dead)
+#pragma unroll
+      for (int l = 0; l < LPT; ++l) {
+        const int it = threadIdx.x + l * NT;
+        if (it < PPB * NLINE) {
+          const int pp = it / NLINE;
+          line_bwd(fz[l], Vp(pp), Rp(pp), it - pp * NLINE);
+        }
+      }
+      __syncthreads();
+      coop<NT, PPB, Lo * NC>([&](int pp, int it) { bwd_item<0, ACC>(Rp(pp), out + pp * sout, it); });
+      __syncthreads();
+    }
+  }
+  // ---- batched stages: every thread takes U items per iteration and issues
+  // all their loads before any arithmetic, so the latencies of independent
+  // items overlap (one item per thread and iteration leaves them serial).
+  static constexpr int U = 2;
+
+  // quadrature-point products over all PPB * NQ points (stage design)
+  template <typename GF>
+  __device__ __forceinline__ static void quad_stage(T* scr, int sscr, const GF& gcell) {
+    constexpr int NGC = D::NGC;
+    constexpr int NCOMP = D::NCOMP;
+    constexpr int TOT = PPB * NQ;
+#pragma unroll 1
+    for (int base = threadIdx.x; base < TOT; base += U * NT) {
+      T g[U][DIM], G[U][NCOMP];
+      int off[U];
+      bool ok[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int it0 = base + u * NT;
+        ok[u] = it0 < TOT;
+        const int it = ok[u] ? it0 : base;
+        const int pp = it / NQ, pt = it - pp * NQ;
+        int cslot = 0, lg = 0, rem = pt, mul = 1, cmul = 1;
+#pragma unroll
+        for (int ax = 0; ax < DIM; ++ax) {
+          const int qa = rem % QP;
+          rem /= QP;
+          const int ca = (NC == 2) ? (qa >= n) : 0;
+          cslot += ca * cmul;
+          lg += (qa - ca * n) * mul;
+          cmul *= NC;
+          mul *= n;
+        }
+        const T* Gp = gcell(pp, cslot) + lg;
+        off[u] = pp * sscr + NQ + pt;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) g[u][d] = scr[off[u] + d * NQ];
+#pragma unroll
+        for (int k = 0; k < NCOMP; ++k) G[u][k] = Gp[k * NGC];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (!ok[u]) continue;
+        T* F = scr + off[u];
+        if (DIM == 3) {
+          F[0] = G[u][0] * g[u][0] + G[u][1] * g[u][1] + G[u][2] * g[u][2];
+          F[NQ] = G[u][1] * g[u][0] + G[u][3] * g[u][1] + G[u][4] * g[u][2];
+          F[2 * NQ] = G[u][2] * g[u][0] + G[u][4] * g[u][1] + G[u][5] * g[u][2];
+        } else {
+          F[0] = G[u][0] * g[u][0] + G[u][1] * g[u][1];
+          F[NQ] = G[u][1] * g[u][0] + G[u][2] * g[u][1];
+        }
+      }
     }
   }
 
-  // Full operator: out = A in for PPB blocks.  in/out/scr are per-block base
-  // pointers with strides; INTIN: input on interior nodes (Dirichlet zero on
-  // the block boundary) else on all nodes.  ACC: out += A in.
-  // Ends with __syncthreads().
+  // collocation derivative (TRANS = false: out[g] = sum_h D[g][h] v[h]) or its
+  // transpose (TRANS = true: out[h] (+)= sum_g D[g][h] v[g]) on n-point cell
+  // segments; map(item, src, dst, stride) locates item's segments.
+  template <bool TRANS, bool ACC, int TOT, typename Map>
+  __device__ __forceinline__ static void dseg_stage(const Map& map) {
+#pragma unroll 1
+    for (int base = threadIdx.x; base < TOT; base += U * NT) {
+      T v[U][n], a[U][n];
+      T* dst[U];
+      int str[U];
+      bool ok[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int it0 = base + u * NT;
+        ok[u] = it0 < TOT;
+        const T* src;
+        map(ok[u] ? it0 : base, src, dst[u], str[u]);
+#pragma unroll
+        for (int h = 0; h < n; ++h) v[u][h] = src[h * str[u]];
+        if (ACC) {
+#pragma unroll
+          for (int h = 0; h < n; ++h) a[u][h] = dst[u][h * str[u]];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (!ok[u]) continue;
+#pragma unroll
+        for (int g = 0; g < n; ++g) {
+          T s = ACC ? a[u][g] : T(0);
+#pragma unroll
+          for (int h = 0; h < n; ++h) s += (TRANS ? tabD<T>(Q, h, g) : tabD<T>(Q, g, h)) * v[u][h];
+          dst[u][g * str[u]] = s;
+        }
+      }
+    }
+  }
+
+  // item -> segment of direction AX (I = QP^AX) of block pp in arrays
+  // [O][QP][I] starting at in / out
+  template <int AX>
+  __device__ __forceinline__ static void seg(int r, const T* in, T* out, const T*& src, T*& dst, int& stride) {
+    constexpr int I = ipow(QP, AX);
+    constexpr int OI = ipow(QP, DIM - 1 - AX) * I;
+    const int c = (NC == 2) ? (r >= OI) : 0;
+    const int pi = r - c * OI;
+    const int i = pi % I, o = pi / I;
+    const int offs = o * QP * I + c * n * I + i;
+    src = in + offs;
+    dst = out + offs;
+    stride = I;
+  }
+
   template <bool INTIN, bool ACC, typename GF>
-  __device__ static void apply(const T* in, int sin, T* out, int sout, T* scr, int sscr, const GF& gcell) {
+  __device__ __forceinline__ static void apply_stage(const T* in, int sin, T* out, int sout, T* scr, int sscr,
+                                                     const GF& gcell) {
     constexpr int L = INTIN ? Mi : M;
     constexpr int Lo = (NC == 2) ? Mi : M;
     // scratch: V = scr[0..NQ), R = scr[NQ..); F_ax = R + ax*NQ
@@ -336,17 +693,28 @@ struct SF {
       });
       __syncthreads();
       constexpr int ND = QP * QP * NC;
-      coop<NT, PPB, 2 * ND>([&](int pp, int it) {
-        const int ax = it / ND, r = it - ax * ND;
-        if (ax == 0) der_item<0>(Vp(pp), Rp(pp), r);
-        else der_item<1>(Vp(pp), Rp(pp) + NQ, r);
+      dseg_stage<false, false, PPB * 2 * ND>([&](int it, const T*& src, T*& dst, int& st) {
+        const int pp = it / (2 * ND), r2 = it - pp * (2 * ND);
+        const int ax = r2 / ND, r = r2 - ax * ND;
+        if (ax == 0) seg<0>(r, Vp(pp), Rp(pp), src, dst, st);
+        else seg<1>(r, Vp(pp), Rp(pp) + NQ, src, dst, st);
       });
       __syncthreads();
-      coop<NT, PPB, NQ>([&](int pp, int pt) { quad_item(Rp(pp), pt, gcell, pp); });
+      quad_stage(scr, sscr, gcell);
       __syncthreads();
-      coop<NT, PPB, ND>([&](int pp, int it) { dert_item<0, false>(Rp(pp), Vp(pp), it); });
+      dseg_stage<true, false, PPB * ND>([&](int it, const T*& src, T*& dst, int& st) {
+        const int pp = it / ND;
+        const T* s0;
+        T* d0;
+        seg<0>(it - pp * ND, Rp(pp), Vp(pp), s0, d0, st);
+        src = s0;
+        dst = d0;
+      });
       __syncthreads();
-      coop<NT, PPB, ND>([&](int pp, int it) { dert_item<1, true>(Rp(pp) + NQ, Vp(pp), it); });
+      dseg_stage<true, true, PPB * ND>([&](int it, const T*& src, T*& dst, int& st) {
+        const int pp = it / ND;
+        seg<1>(it - pp * ND, Rp(pp) + NQ, Vp(pp), src, dst, st);
+      });
       __syncthreads();
       constexpr int B1 = Lo * Lo * QP;       // [Lo][Lo][QP]
       // z: D^T F_2 + V -> B^T along z -> R + B1 [Lo][QP][QP]; R + B1 does not
@@ -365,11 +733,17 @@ struct SF {
       coop<NT, PPB, QP * NC>([&](int pp, int it) { fwd_der_last_item<INTIN>(Rp(pp), Vp(pp), Rp(pp) + NQ, it); });
       __syncthreads();
       constexpr int ND = QP * NC;
-      coop<NT, PPB, ND>([&](int pp, int it) { der_item<0>(Vp(pp), Rp(pp), it); });
+      dseg_stage<false, false, PPB * ND>([&](int it, const T*& src, T*& dst, int& st) {
+        const int pp = it / ND;
+        seg<0>(it - pp * ND, Vp(pp), Rp(pp), src, dst, st);
+      });
       __syncthreads();
-      coop<NT, PPB, NQ>([&](int pp, int pt) { quad_item(Rp(pp), pt, gcell, pp); });
+      quad_stage(scr, sscr, gcell);
       __syncthreads();
-      coop<NT, PPB, ND>([&](int pp, int it) { dert_item<0, false>(Rp(pp), Vp(pp), it); });
+      dseg_stage<true, false, PPB * ND>([&](int it, const T*& src, T*& dst, int& st) {
+        const int pp = it / ND;
+        seg<0>(it - pp * ND, Rp(pp), Vp(pp), src, dst, st);
+      });
       __syncthreads();
       // y: D^T F_1 + V -> B^T along y -> R [Lo][QP] (F_0 = R is dead)
       coop<NT, PPB, QP>([&](int pp, int it) { dert_bwd_last_item(Rp(pp) + NQ, Vp(pp), Rp(pp), it); });
@@ -377,6 +751,20 @@ struct SF {
       coop<NT, PPB, Lo * NC>([&](int pp, int it) { bwd_item<0, ACC>(Rp(pp), out + pp * sout, it); });
       __syncthreads();
     }
+  }
+
+  // Full operator: out = A in (or out += A in) for PPB blocks; in/out/scr are
+  // per-block base pointers with strides; INTIN: input on interior nodes only.
+  // Not inlined: one copy per (level, input kind) is shared by all call
+  // sites, which keeps the patch kernel small for the instruction cache.
+  // LINE selects the design of the last direction: false = separate stages
+  // with all fluxes in shared memory, true = one thread per line with that
+  // direction's gradient and flux in registers.  Ends with __syncthreads().
+  template <bool INTIN, bool ACC, typename GF>
+  __device__ __noinline__ static void apply(const T* in, int sin, T* out, int sout, T* scr, int sscr,
+                                            const GF& gcell) {
+    if constexpr (LINE) apply_line<INTIN, ACC>(in, sin, out, sout, scr, sscr, gcell);
+    else apply_stage<INTIN, ACC>(in, sin, out, sout, scr, sscr, gcell);
   }
 };
 

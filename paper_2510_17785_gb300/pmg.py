@@ -20,8 +20,10 @@ PMG_OK = 0
 ERRORS = {1: "PMG_ERR_ARG", 2: "PMG_ERR_CUDA", 3: "PMG_ERR_DEGENERATE", 4: "PMG_ERR_NOT_CONVERGED",
           5: "PMG_ERR_NUMERIC", 6: "PMG_ERR_TIMEOUT", 7: "PMG_ERR_UNSUPPORTED"}
 SMOOTHER_CHEBYSHEV, SMOOTHER_JACOBI = 0, 1
-BOUNDS_LANCZOS, BOUNDS_FIXED, BOUNDS_USER = 0, 1, 2
+BOUNDS_LANCZOS, BOUNDS_FIXED, BOUNDS_USER, BOUNDS_MLP = 0, 1, 2, 3
+MLP_NPARAM, MLP_NNORM = 5378, 36
 PREC_FP64, PREC_MIXED = 0, 1
+KAPPA_ARITHMETIC, KAPPA_GEOMETRIC, KAPPA_HARMONIC = 0, 1, 2
 
 # every symbol include/pmg.h declares
 SYMBOLS = (
@@ -30,7 +32,8 @@ SYMBOLS = (
     "pmg_local_vcycle", "pmg_get_bounds", "pmg_set_bounds", "pmg_compute_bounds", "pmg_get_ritz",
     "pmg_gmg_vcycle", "pmg_solve_cg", "pmg_solve_cg_host", "pmg_rhs_manufactured", "pmg_get_colours",
     "pmg_get_patch_map", "pmg_get_inv_diag", "pmg_sweep_flops", "pmg_launch_count", "pmg_fma_peak",
-    "pmg_lanczos_bounds_noalloc", "pmg_tuning",
+    "pmg_lanczos_bounds_noalloc", "pmg_tuning", "pmg_default_train_options", "pmg_features", "pmg_mlp_grad",
+    "pmg_mlp_train", "pmg_mlp_predict", "pmg_set_mlp",
 )
 
 
@@ -40,7 +43,13 @@ class Options(C.Structure):
         ("bounds", C.c_int), ("lanczos_steps", C.c_int), ("bound_safety", C.c_double),
         ("bound_ratio", C.c_double), ("fixed_lo", C.c_double), ("fixed_hi", C.c_double),
         ("seed", C.c_uint64), ("precision", C.c_int), ("autotune", C.c_int), ("variant", C.c_int),
+        ("mlp_safety", C.c_double), ("coarse_kappa", C.c_int),
     ]
+
+
+class TrainOptions(C.Structure):
+    _fields_ = [("epochs", C.c_int), ("batch", C.c_int), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("asym", C.c_float), ("seed", C.c_uint64)]
 
 
 class PMGError(RuntimeError):
@@ -93,6 +102,12 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pmg_fma_peak": (i, [vp, i, P(d)]),
         "pmg_lanczos_bounds_noalloc": (i, [vp, i, i, i64, i64, vp, vp, vp]),
         "pmg_tuning": (i, [vp, P(i), P(i), P(i), P(C.c_float)]),
+        "pmg_default_train_options": (None, [P(TrainOptions)]),
+        "pmg_features": (i, [vp, i, i, vp, vp]),
+        "pmg_mlp_grad": (i, [i, vp, vp, vp, vp, i, C.c_float, vp, vp, vp]),
+        "pmg_mlp_train": (i, [i, vp, vp, vp, vp, i64, P(TrainOptions), vp]),
+        "pmg_mlp_predict": (i, [i, vp, vp, vp, i64, i, vp, vp]),
+        "pmg_set_mlp": (i, [vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -109,6 +124,52 @@ def default_options(**kw) -> Options:
     for k, v in kw.items():
         setattr(o, k, v)
     return o
+
+
+def train_options(**kw) -> TrainOptions:
+    lib = load()
+    o = TrainOptions()
+    lib.pmg_default_train_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _check_rc(rc, what):
+    if rc != PMG_OK:
+        raise PMGError(rc, what)
+
+
+def mlp_grad(params, norm, X, T, asym=4.0, device=0):
+    """(loss, grad) of the loss on all samples; float32 CUDA tensors."""
+    import torch
+    lib = load()
+    loss = torch.zeros(1, dtype=torch.float32, device=params.device)
+    g = torch.zeros_like(params)
+    _check_rc(lib.pmg_mlp_grad(device, _ptr(params), _ptr(norm), _ptr(X), _ptr(T), X.shape[0], asym, _ptr(loss),
+                               _ptr(g), _stream(None)), "pmg_mlp_grad")
+    return loss, g
+
+
+def mlp_train(params, norm, X, T, device=0, **opts):
+    """Train params (float32 CUDA tensor) in place; returns the per-epoch losses."""
+    lib = load()
+    o = train_options(**opts)
+    hist = np.zeros(max(o.epochs, 1), dtype=np.float32)
+    import torch
+    torch.cuda.synchronize()
+    _check_rc(lib.pmg_mlp_train(device, _ptr(params), _ptr(norm), _ptr(X), _ptr(T), X.shape[0], C.byref(o),
+                                hist.ctypes.data), "pmg_mlp_train")
+    return hist[: o.epochs]
+
+
+def mlp_predict(params, norm, X, bf16=True, device=0):
+    import torch
+    lib = load()
+    Y = torch.zeros((X.shape[0], 2), dtype=torch.float32, device=X.device)
+    _check_rc(lib.pmg_mlp_predict(device, _ptr(params), _ptr(norm), _ptr(X), X.shape[0], int(bf16), _ptr(Y),
+                                  _stream(None)), "pmg_mlp_predict")
+    return Y
 
 
 def _ptr(t) -> int:
@@ -266,9 +327,17 @@ class Context:
     def tuning(self):
         """(variant, threads per CTA, patches per CTA, [ms per candidate variant])"""
         v, t, b = C.c_int(), C.c_int(), C.c_int()
-        ms = (C.c_float * 4)()
+        ms = (C.c_float * 8)()
         self._check(self.lib.pmg_tuning(self.h, C.byref(v), C.byref(t), C.byref(b), ms))
         return v.value, t.value, b.value, list(ms)
+
+    def features(self, level, k, X, stream=None):
+        self._check(self.lib.pmg_features(self.h, level, k, _ptr(X), _stream(stream)))
+
+    def set_mlp(self, params: np.ndarray, norm: np.ndarray):
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        norm = np.ascontiguousarray(norm, dtype=np.float32)
+        self._check(self.lib.pmg_set_mlp(self.h, params.ctypes.data, norm.ctypes.data))
 
     def launch_count(self) -> int:
         n = C.c_int64()

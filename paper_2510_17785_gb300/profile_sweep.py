@@ -10,7 +10,6 @@ full capture saves and restores little memory.
 from __future__ import annotations
 
 import argparse
-import math
 import os
 import sys
 
@@ -26,8 +25,10 @@ def main():
     ap.add_argument("--sweeps", type=int, default=3)
     ap.add_argument("--levels", type=int, default=0, help="h-levels (default: down to 2 cells per direction)")
     args = ap.parse_args()
-    if args.levels <= 0:
-        args.levels = int(round(math.log2(args.N / 2))) + 1
+    if args.levels <= 0:                  # halve while the cell count stays even and >= 2
+        args.levels, n = 1, args.N
+        while n % 2 == 0 and n // 2 >= 2:
+            args.levels, n = args.levels + 1, n // 2
 
     import torch
     from paper_2510_17785_gb300 import inputs, pmg

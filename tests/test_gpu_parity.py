@@ -328,7 +328,7 @@ def test_launch_shape_variants_are_bit_identical(precision):
     prob = inputs.make_problem(w)
     u0 = inputs.random_vector(31, 3, 4, 6)
     outs = []
-    for v in range(4):
+    for v in range(8):
         ctx = pmg.Context(0, precision=prec, autotune=0, variant=v, **fixed())
         ctx.mesh_structured(3, 6, 4, 2, prob.coords, prob.kappa)
         try:
