@@ -160,6 +160,24 @@ def cpu_baseline(w, levels, iters, npatch=48, reps=4):
     }
 
 
+# ------------------------------------------------------------ multi-rank
+def aggregate(t_local_ms: float, n_free_local: int, dist: bool):
+    """Whole-job time and throughput: every rank solved its own problem, the
+    job took as long as the slowest rank (max over ranks), and the job's
+    throughput is all ranks' DoFs over that time."""
+    t_max, n_total = t_local_ms, n_free_local
+    if dist:
+        import torch
+        import torch.distributed as td
+        dev = torch.device("cuda", torch.cuda.current_device()) if td.get_backend() == "nccl" else torch.device("cpu")
+        tt = torch.tensor([t_local_ms], dtype=torch.float64, device=dev)
+        nn = torch.tensor([float(n_free_local)], dtype=torch.float64, device=dev)
+        td.all_reduce(tt, op=td.ReduceOp.MAX)
+        td.all_reduce(nn, op=td.ReduceOp.SUM)
+        t_max, n_total = float(tt.item()), int(nn.item())
+    return t_max, n_total / (t_max * 1e-3)
+
+
 # ------------------------------------------------------------------ ours
 def run_ours(args):
     import torch
@@ -271,12 +289,7 @@ def run_ours(args):
 
     head = result["mixed"]
     t_step = sum(head["ms"]) / len(head["ms"])
-    t_max = t_step
-    if dist:
-        tt = torch.tensor([t_step], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * w.n_free / (t_max * 1e-3)
+    t_max, value = aggregate(t_step, w.n_free, dist)
     achieved = head["sweep_flops"] / head["t_sweep"]
     out = {
         "metric": METRIC,

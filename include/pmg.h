@@ -74,6 +74,9 @@ typedef struct pmg_options {
   double mlp_safety;     /* PMG_BOUNDS_MLP: hi = mlp_safety * predicted theta_max */
   int coarse_kappa;      /* coefficient of a coarse cell from its 2^d children:
                             PMG_KAPPA_ARITHMETIC, _GEOMETRIC or _HARMONIC mean  */
+  int post_reverse;      /* 1: post-smoothing sweeps the colours in reverse
+                            order (symmetric V-cycle, for CG; default);
+                            0: same order as pre-smoothing (Section 4; GMRES) */
 } pmg_options;
 enum { PMG_KAPPA_ARITHMETIC = 0, PMG_KAPPA_GEOMETRIC = 1, PMG_KAPPA_HARMONIC = 2 };
 
@@ -177,6 +180,16 @@ int pmg_gmg_vcycle(pmg_ctx* ctx, const double* b_dev, double* x_dev, void* strea
  * Returns PMG_ERR_NOT_CONVERGED at maxit, PMG_ERR_NUMERIC on NaN/Inf. */
 int pmg_solve_cg(pmg_ctx* ctx, const double* b_dev, double* u_dev, double rtol, int maxit,
                  int* iters, double* relres, void* stream);
+
+/* Restarted GMRES(restart) on the finest level from u = 0 with the GMG V-cycle
+ * as preconditioner M (the paper's outer solver, Section 4), modified
+ * Gram-Schmidt Arnoldi, Givens rotations.  left = 0: right preconditioning,
+ * u = M y, stops when ||b - A u||_2 <= rtol ||b||_2; left = 1: the Krylov space
+ * of M A, stops when ||M (b - A u)||_2 <= rtol ||M b||_2.  Synchronises once per
+ * inner product (the Hessenberg least-squares problem lives on the host).
+ * Returns PMG_ERR_NOT_CONVERGED at maxit. */
+int pmg_solve_gmres(pmg_ctx* ctx, const double* b_dev, double* u_dev, double rtol, int maxit,
+                    int restart, int left, int* iters, double* relres, void* stream);
 
 /* Same solve with host vectors: copies b in, solves, copies u out. */
 int pmg_solve_cg_host(pmg_ctx* ctx, const double* b_host, double* u_host, double rtol,

@@ -14,10 +14,11 @@ Test infrastructure only.
   (Section 2).
 * V-cycle: one multiplicative patch-smoother sweep before (colours in
   increasing order) and one after (colours reversed, so that the V-cycle is
-  symmetric and can precondition CG), coarse problem solved by a dense
-  Cholesky factorisation.
-* Outer solver: preconditioned CG from u = 0, stopping when
-  ||r_k||_2 <= rtol ||r_0||_2.
+  symmetric and can precondition CG; or in the same order, the paper's
+  choice, Section 4), coarse problem solved by a dense Cholesky factorisation.
+* Outer solvers from u = 0, stopping when ||r_k||_2 <= rtol ||r_0||_2:
+  preconditioned CG, and restarted GMRES (the paper's, Section 4), right- or
+  left-preconditioned, with modified Gram-Schmidt Arnoldi and Givens rotations.
 """
 from __future__ import annotations
 
@@ -77,8 +78,9 @@ def prolongation(coarse: fem.StructuredMesh, fine: fem.StructuredMesh, q: int) -
 
 class GMG:
     def __init__(self, fine: fem.StructuredMesh, p: int, coarse_N: int, smoother_args=None,
-                 kappa_rule: str = "arithmetic"):
+                 kappa_rule: str = "arithmetic", post_reverse: bool = True):
         self.p = p
+        self.post_reverse = post_reverse
         self.meshes = hierarchy(fine, coarse_N, kappa_rule)
         self.free = [m.free_mask(p) for m in self.meshes]
         self.A = []
@@ -111,7 +113,7 @@ class GMG:
         r = b - self.A[l] @ x
         e = self.vcycle(self.P[l - 1].T @ r, l - 1)
         x = x + self.P[l - 1] @ e
-        x = S.sweep(x, b, reverse=True)
+        x = S.sweep(x, b, reverse=self.post_reverse)
         return x
 
 
@@ -140,3 +142,60 @@ def pcg(A, b, M, rtol=1e-8, maxit=200):
         p = z + (rz_new / rz) * p
         rz = rz_new
     return x, maxit, hist
+
+
+def gmres(A, b, M, rtol=1e-8, maxit=200, restart=50, left=False):
+    """Restarted GMRES(restart) from x = 0 with preconditioner M.
+
+    Right (default): x = M y with y from the Krylov space of A M; the residual
+    monitored is the true one, b - A x.  Left: the Krylov space of M A, the
+    residual monitored is the preconditioned one, M (b - A x).  Returns
+    (x, iterations, relres history)."""
+    n = len(b)
+    x = np.zeros_like(b)
+    r = M(b) if left else b.copy()
+    r0 = np.linalg.norm(r)
+    hist = [1.0]
+    if r0 == 0.0:
+        return x, 0, hist
+    it = 0
+    while it < maxit:
+        beta = np.linalg.norm(r)
+        V = np.zeros((restart + 1, n))
+        H = np.zeros((restart + 1, restart))
+        V[0] = r / beta
+        cs, sn = np.zeros(restart), np.zeros(restart)
+        g = np.zeros(restart + 1)
+        g[0] = beta
+        k = 0
+        for j in range(restart):
+            w = M(A @ V[j]) if left else A @ M(V[j])
+            for i in range(j + 1):                       # modified Gram-Schmidt
+                H[i, j] = w @ V[i]
+                w = w - H[i, j] * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            if H[j + 1, j] > 0.0:
+                V[j + 1] = w / H[j + 1, j]
+            for i in range(j):                           # previous rotations
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]
+                H[i, j] = t
+            den = np.hypot(H[j, j], H[j + 1, j])
+            cs[j], sn[j] = H[j, j] / den, H[j + 1, j] / den
+            H[j, j] = den
+            H[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            it += 1
+            k = j + 1
+            hist.append(abs(g[j + 1]) / r0)
+            if hist[-1] <= rtol or it >= maxit:
+                break
+        y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])
+        x = x + (V[:k].T @ y if left else M(V[:k].T @ y))
+        r = b - A @ x
+        if left:
+            r = M(r)
+        if hist[-1] <= rtol:
+            break
+    return x, it, hist

@@ -224,8 +224,9 @@ class PatchSmoother:
     """All interior-vertex patches of one mesh, with per-(patch, level) bounds."""
 
     def __init__(self, mesh: fem.StructuredMesh, p: int, levels=None, sm: Smoother | None = None,
-                 bounds_fn=None, n_cycles: int = 1):
+                 bounds_fn=None, n_cycles: int = 1, order: str = "colour"):
         self.mesh, self.p = mesh, p
+        self.order = order             # "colour": colour-major; "vertex": plain vertex order
         self.levels = levels_halving(p) if levels is None else levels
         self.sm = Smoother() if sm is None else sm
         self.n_cycles = n_cycles
@@ -259,8 +260,14 @@ class PatchSmoother:
     def sweep(self, u, b, reverse=False, colours=None, within="increasing"):
         """One multiplicative sweep (Algorithm 1, colour-major order).  `within`
         orders the patches of one colour ("increasing" or "decreasing" vertex
-        id)."""
+        id).  With order "vertex" the patches run in plain vertex order
+        (decreasing when reversed), one after the other."""
         u = u.copy()
+        if self.order == "vertex":
+            for v in (self.vertices[::-1] if reverse else self.vertices):
+                idx, d = self.update(v, u, b)
+                u[idx] += d
+            return u
         n_col = 2 ** self.mesh.dim
         order = list(range(n_col)) if colours is None else list(colours)
         if reverse:

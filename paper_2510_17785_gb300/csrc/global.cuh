@@ -404,6 +404,16 @@ static __global__ void k_cg_update_xr(double* __restrict__ x, double* __restrict
   }
 }
 
+// y += a x ; y = a x
+static __global__ void k_axpy(double a, const double* __restrict__ x, double* __restrict__ y, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] += a * x[i];
+}
+static __global__ void k_scale(double a, const double* __restrict__ x, double* __restrict__ y, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i];
+}
+
 // ---------------------------------------------------------------------------
 // Coarse solve: x_free = Ainv b_free (dense FP64 inverse of the coarsest
 // matrix, computed once at set-up).  One warp per row.

@@ -39,6 +39,16 @@ int launch_dot(const double* x, const double* y, size_t n, double* partial, doub
   PMG_CHECK_LAUNCH();
   return ST_OK;
 }
+int launch_axpy(double a, const double* x, double* y, size_t n, cudaStream_t s) {
+  k_axpy<<<grid_for(n, 256), 256, 0, s>>>(a, x, y, n);
+  PMG_CHECK_LAUNCH();
+  return ST_OK;
+}
+int launch_scale(double a, const double* x, double* y, size_t n, cudaStream_t s) {
+  k_scale<<<grid_for(n, 256), 256, 0, s>>>(a, x, y, n);
+  PMG_CHECK_LAUNCH();
+  return ST_OK;
+}
 int launch_cg_update_p(const double* z, double* p, const double* scal, size_t n, cudaStream_t s) {
   k_cg_update_p<<<grid_for(n, 256), 256, 0, s>>>(z, p, scal, n);
   PMG_CHECK_LAUNCH();

@@ -63,6 +63,8 @@ int launch_cast_d2f(const double* x, float* y, size_t n, cudaStream_t s);
 int launch_cast_f2d(const float* x, double* y, size_t n, cudaStream_t s);
 int launch_dot(const double* x, const double* y, size_t n, double* partial, double* scal, int slot, int op,
                cudaStream_t s);
+int launch_axpy(double a, const double* x, double* y, size_t n, cudaStream_t s);
+int launch_scale(double a, const double* x, double* y, size_t n, cudaStream_t s);
 int launch_cg_update_p(const double* z, double* p, const double* scal, size_t n, cudaStream_t s);
 int launch_cg_update_xr(double* x, double* r, const double* p, const double* Ap, const double* scal, size_t n,
                         cudaStream_t s);

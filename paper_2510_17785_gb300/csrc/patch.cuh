@@ -56,6 +56,44 @@ struct PatchArgs {
   int* err;                    // device error flag
 };
 
+// Epilogues of the patch operator applies: the smoother and residual updates
+// applied to each output value as it is produced (no extra pass over Ad).
+enum { EPI_STORE = 0, EPI_RESID, EPI_EVAL, EPI_CHEB0, EPI_CHEB, EPI_JAC };
+
+template <typename T>
+struct PatchEpi {
+  T* sm;
+  int PS;
+  int kind;
+  int r, d, res, dir, dinv, ad, coef, it;
+  T omega;
+  __device__ __forceinline__ void operator()(int pp, int i, T s) const {
+    T* b = sm + pp * PS;
+    switch (kind) {
+      case EPI_STORE: b[ad + i] = s; break;
+      case EPI_RESID: b[res + i] = b[r + i] - s; break;          // res = r - A d
+      case EPI_EVAL: b[r + i] -= s; break;                       // r = b - A u
+      case EPI_CHEB0: {                                          // first step from d != 0
+        const T rs = b[dinv + i] * (b[r + i] - s);
+        const T dr = rs * b[coef];
+        b[res + i] = rs;
+        b[dir + i] = dr;
+        b[d + i] += dr;
+        break;
+      }
+      case EPI_CHEB: {                                           // step it of the recurrence
+        const T rs = b[res + i] - b[dinv + i] * s;
+        const T dr = b[coef + it] * b[dir + i] + b[coef + 7 + it] * rs;
+        b[res + i] = rs;
+        b[dir + i] = dr;
+        b[d + i] += dr;
+        break;
+      }
+      default: b[d + i] += omega * b[dinv + i] * (b[r + i] - s);  // damped Jacobi
+    }
+  }
+};
+
 template <int DIM, int P, bool LINE = false>
 struct Layout {
   static constexpr int NL = nlevels(P);
@@ -161,12 +199,33 @@ struct PatchKernel {
     return [G, cl](int pp, int slot) { return G + (size_t)cl[pp * (NCELL + 4) + slot] * stride; };
   }
 
-  // out = A_q in on interior vectors of level K (matrix-free, or the staged
-  // dense patch matrix on small levels)
   template <int K>
-  __device__ void apply_int(int in_off, int out_off) {
+  __device__ PatchEpi<T> epi(int kind, int it = 0) const {
+    PatchEpi<T> e;
+    e.sm = sm;
+    e.PS = PS;
+    e.kind = kind;
+    e.r = L::R_(K);
+    e.d = L::D_(K);
+    e.res = L::RES(K);
+    e.dir = L::DIR(K);
+    e.dinv = L::DINV(K);
+    e.ad = L::AD(K);
+    e.coef = L::COEF + K * L::NCOEF;
+    e.it = it;
+    e.omega = T(a->omega);
+    return e;
+  }
+
+  // A_q x on the interior vector at in_off of level K, every output value
+  // passed through the epilogue `e` (matrix-free, or the staged dense patch
+  // matrix on small levels).  Ends with a barrier.
+  template <int K>
+  __device__ void apply_int(int in_off, const PatchEpi<T>& e) {
     constexpr int q = P >> K;
     if constexpr (dense_level(DIM, q)) {
+      // the epilogue may overwrite the input, which other rows still read:
+      // products first, epilogue after a barrier
       constexpr int NI = L::ni(K);
       coop<NT, PPB, NI>([&](int pp, int r) {
         const T* A = vec(pp, L::DENSE(K)) + r * NI;
@@ -174,12 +233,16 @@ struct PatchKernel {
         T s = T(0);
 #pragma unroll
         for (int c = 0; c < NI; ++c) s += A[c] * x[c];
-        vec(pp, out_off)[r] = s;
+        vec(pp, L::AD(K))[r] = s;
       });
       __syncthreads();
+      if (e.kind != EPI_STORE) {
+        coop<NT, PPB, NI>([&](int pp, int r) { e(pp, r, vec(pp, L::AD(K))[r]); });
+        __syncthreads();
+      }
     } else {
-      SF<DIM, 2, q, T, NT, PPB, C::LINE>::template apply<true, false>(vec(0, in_off), PS, vec(0, out_off), PS,
-                                                                     vec(0, L::SCR), PS, gfun<K>());
+      SF<DIM, 2, q, T, NT, PPB, C::LINE>::template apply_epi<true>(vec(0, in_off), PS, vec(0, L::SCR), PS,
+                                                                  gfun<K>(), e);
     }
   }
 
@@ -321,48 +384,32 @@ struct PatchKernel {
   __device__ void smooth(bool zero_start) {
     constexpr int NI = L::ni(K);
     if (a->smoother == 1) {   // damped Jacobi, d += omega D^-1 (r - A d)
-      const T om = T(a->omega);
       if (zero_start) {
+        const T om = T(a->omega);
         coop<NT, PPB, NI>([&](int pp, int i) { vec(pp, L::D_(K))[i] = om * vec(pp, L::DINV(K))[i] * vec(pp, L::R_(K))[i]; });
         __syncthreads();
       } else {
-        apply_int<K>(L::D_(K), L::AD(K));
-        coop<NT, PPB, NI>([&](int pp, int i) {
-          T* d = vec(pp, L::D_(K));
-          d[i] += om * vec(pp, L::DINV(K))[i] * (vec(pp, L::R_(K))[i] - vec(pp, L::AD(K))[i]);
-        });
-        __syncthreads();
+        apply_int<K>(L::D_(K), epi<K>(EPI_JAC));
       }
       return;
     }
     // Chebyshev iteration (three-term recurrence on D^-1 A over [lo, hi])
     const int deg = a->cheb_degree;
-    if (!zero_start) apply_int<K>(L::D_(K), L::AD(K));
-    coop<NT, PPB, NI>([&](int pp, int i) {
-      const T* cf = vec(pp, L::COEF + K * L::NCOEF);
-      const T rr = zero_start ? vec(pp, L::R_(K))[i] : vec(pp, L::R_(K))[i] - vec(pp, L::AD(K))[i];
-      const T res = vec(pp, L::DINV(K))[i] * rr;
-      const T dir = res * cf[0];
-      vec(pp, L::RES(K))[i] = res;
-      vec(pp, L::DIR(K))[i] = dir;
-      T* d = vec(pp, L::D_(K));
-      d[i] = zero_start ? dir : d[i] + dir;
-    });
-    __syncthreads();
-#pragma unroll 1
-    for (int it = 1; it < deg; ++it) {
-      apply_int<K>(L::DIR(K), L::AD(K));
+    if (zero_start) {
       coop<NT, PPB, NI>([&](int pp, int i) {
         const T* cf = vec(pp, L::COEF + K * L::NCOEF);
-        const T c1 = cf[it], c2 = cf[7 + it];
-        const T res = vec(pp, L::RES(K))[i] - vec(pp, L::DINV(K))[i] * vec(pp, L::AD(K))[i];
-        const T dir = c1 * vec(pp, L::DIR(K))[i] + c2 * res;
+        const T res = vec(pp, L::DINV(K))[i] * vec(pp, L::R_(K))[i];
+        const T dir = res * cf[0];
         vec(pp, L::RES(K))[i] = res;
         vec(pp, L::DIR(K))[i] = dir;
-        vec(pp, L::D_(K))[i] += dir;
+        vec(pp, L::D_(K))[i] = dir;
       });
       __syncthreads();
+    } else {
+      apply_int<K>(L::D_(K), epi<K>(EPI_CHEB0));
     }
+#pragma unroll 1
+    for (int it = 1; it < deg; ++it) apply_int<K>(L::DIR(K), epi<K>(EPI_CHEB, it));
   }
 
   // ---- Algorithm 2
@@ -375,9 +422,7 @@ struct PatchKernel {
     } else {
       constexpr int NI = L::ni(K);
       smooth<K>(zero_start);                                      // pre-smoothing
-      apply_int<K>(L::D_(K), L::AD(K));                           // residual
-      coop<NT, PPB, NI>([&](int pp, int i) { vec(pp, L::RES(K))[i] = vec(pp, L::R_(K))[i] - vec(pp, L::AD(K))[i]; });
-      __syncthreads();
+      apply_int<K>(L::D_(K), epi<K>(EPI_RESID));                  // residual
       restrict_res<K>();                                          // restriction
       vcycle<K + 1>(true);                                        // coarse correction
       prolong_add<K>();                                           // prolongation
@@ -517,10 +562,8 @@ struct PatchKernel {
       });
       __syncthreads();
       // Evaluate: r = b - A u on the patch interior
-      SF<DIM, 2, P, T, NT, PPB, C::LINE>::template apply<false, false>(vec(0, L::CLOS), PS, vec(0, L::AD(0)), PS,
-                                                                      vec(0, L::SCR), PS, gfun<0>());
-      coop<NT, PPB, NI0>([&](int pp, int i) { vec(pp, L::R_(0))[i] -= vec(pp, L::AD(0))[i]; });
-      __syncthreads();
+      SF<DIM, 2, P, T, NT, PPB, C::LINE>::template apply_epi<false>(vec(0, L::CLOS), PS, vec(0, L::SCR), PS,
+                                                                   gfun<0>(), epi<0>(EPI_EVAL));
     } else {
       coop<NT, PPB, NI0>([&](int pp, int i) {
         const bool act = cells[pp * (NCELL + 4) + NCELL + 1];

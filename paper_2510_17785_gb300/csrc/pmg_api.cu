@@ -99,6 +99,8 @@ struct pmg_ctx {
   float variant_ms[NUM_VARIANTS] = {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f};
   float* mlp_params = nullptr;           // PMG_BOUNDS_MLP network and normalisation
   float* mlp_norm = nullptr;
+  double* gm_V = nullptr;                // GMRES basis (restart + 1 vectors), grown on demand
+  int gm_m = 0;
   double* lanczos_V = nullptr;           // Lanczos basis scratch, grown on demand, reused
   size_t lanczos_V_n = 0;
   std::vector<void*> allocs;
@@ -335,7 +337,7 @@ int vcycle(pmg_ctx* ctx, int l, cudaStream_t s) {
   st = prolongate<T>(ctx, l, Xof<T>(hc), r, TA<T>(ctx), TB<T>(ctx), s);
   if (st) return st;
   LK(1, launch_add_to<T>(r, x, h.nd, s));
-  return sweep<T>(ctx, l, b, x, true, s);                         // post-smoothing
+  return sweep<T>(ctx, l, b, x, ctx->opt.post_reverse != 0, s);  // post-smoothing
 }
 
 // z = M r on the finest level (FP64 in and out)
@@ -486,6 +488,7 @@ void pmg_default_options(pmg_options* o) {
   o->variant = 0;
   o->mlp_safety = 1.2;
   o->coarse_kappa = PMG_KAPPA_ARITHMETIC;
+  o->post_reverse = 1;
 }
 
 int pmg_create(int device, const pmg_options* opt, pmg_ctx** out) {
@@ -525,6 +528,7 @@ int pmg_destroy(pmg_ctx* ctx) {
   if (ctx->graph) cudaGraphDestroy(ctx->graph);
   for (void* p : ctx->allocs) cudaFree(p);
   if (ctx->lanczos_V) cudaFree(ctx->lanczos_V);
+  if (ctx->gm_V) cudaFree(ctx->gm_V);
   if (ctx->d_err) cudaFree(ctx->d_err);
   if (ctx->h_rr) cudaFreeHost(ctx->h_rr);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -1175,6 +1179,138 @@ int pmg_solve_cg(pmg_ctx* ctx, const double* b, double* u, double rtol, int maxi
     if (result == PMG_OK && rel > rtol) result = fail(ctx, PMG_ERR_NOT_CONVERGED, "maxit reached");
   }
   CU(cudaMemcpyAsync(u, ctx->cg_x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CU(cudaStreamSynchronize(s));
+  if (iters) *iters = it;
+  if (relres) *relres = rel;
+  return result;
+}
+
+// (x, y) in FP64, deterministic, result on the host
+static int dot_host(pmg_ctx* ctx, const double* x, const double* y, size_t n, double* out, cudaStream_t s) {
+  LK(2, launch_dot(x, y, n, ctx->partial, ctx->scal, S_RR, 0, s));
+  CU(cudaMemcpyAsync(ctx->h_rr, ctx->scal + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  *out = *ctx->h_rr;
+  return PMG_OK;
+}
+
+int pmg_solve_gmres(pmg_ctx* ctx, const double* b, double* u, double rtol, int maxit, int restart, int left,
+                    int* iters, double* relres, void* stream) {
+  int st = check_level(ctx, ctx ? ctx->nlev - 1 : 0);
+  if (st) return st;
+  if (!b || !u || maxit < 0 || restart < 1 || restart > 1000 || !(rtol >= 0)) return fail(ctx, PMG_ERR_ARG, "bad arguments");
+  cudaStream_t us = (cudaStream_t)stream;
+  cudaStream_t s = ctx->stream;
+  CU(cudaStreamSynchronize(us));
+  HLevel& h = ctx->L.back();
+  const size_t n = h.nd;
+  const int M = ctx->p * h.N + 1;
+  if (ctx->gm_m < restart) {
+    if (ctx->gm_V) CU(cudaFree(ctx->gm_V));
+    ctx->gm_V = nullptr;
+    ctx->gm_m = 0;
+    CU(cudaMalloc(&ctx->gm_V, (size_t)(restart + 1) * n * sizeof(double)));
+    ctx->gm_m = restart;
+  }
+  double* V = ctx->gm_V;
+  double *x = ctx->cg_x, *r = ctx->cg_r, *w = ctx->cg_Ap, *z = ctx->cg_z, *t = ctx->cg_p;
+  CU(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+  CU(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  LK(1, mask_boundary<double>(ctx, r, M, s));
+  if (left) {                                                           // r = M b
+    st = precondition(ctx, r, z, s);
+    if (st) return st;
+    CU(cudaMemcpyAsync(r, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  double rr;
+  st = dot_host(ctx, r, r, n, &rr, s);
+  if (st) return st;
+  const double r0 = std::sqrt(rr);
+  int it = 0;
+  double rel = r0 > 0 ? 1.0 : 0.0;
+  int result = PMG_OK;
+  if (!std::isfinite(r0)) result = fail(ctx, PMG_ERR_NUMERIC, "non-finite right-hand side");
+  std::vector<double> H((size_t)(restart + 1) * restart), cs(restart), sn(restart), g(restart + 1), y(restart);
+  while (result == PMG_OK && r0 > 0 && rel > rtol && it < maxit) {
+    double beta;
+    st = dot_host(ctx, r, r, n, &beta, s);
+    if (st) return st;
+    beta = std::sqrt(beta);
+    LK(1, launch_scale(1.0 / beta, r, V, n, s));
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int k = 0;
+    for (int j = 0; j < restart && it < maxit; ++j) {
+      if (left) {                                                       // w = M A v_j
+        LK(1 + (1 << ctx->dim), cell_apply<double>(ctx, ctx->p, V + (size_t)j * n, z, h.pl[0].G64, h.N, s));
+        st = precondition(ctx, z, w, s);
+      } else {                                                          // w = A M v_j
+        st = precondition(ctx, V + (size_t)j * n, z, s);
+        if (!st) LK(1 + (1 << ctx->dim), cell_apply<double>(ctx, ctx->p, z, w, h.pl[0].G64, h.N, s));
+      }
+      if (st) return st;
+      for (int i = 0; i <= j; ++i) {                                    // modified Gram-Schmidt
+        double hij;
+        st = dot_host(ctx, w, V + (size_t)i * n, n, &hij, s);
+        if (st) return st;
+        H[(size_t)i * restart + j] = hij;
+        LK(1, launch_axpy(-hij, V + (size_t)i * n, w, n, s));
+      }
+      double hn;
+      st = dot_host(ctx, w, w, n, &hn, s);
+      if (st) return st;
+      hn = std::sqrt(hn);
+      H[(size_t)(j + 1) * restart + j] = hn;
+      if (hn > 0) LK(1, launch_scale(1.0 / hn, w, V + (size_t)(j + 1) * n, n, s));
+      for (int i = 0; i < j; ++i) {                                     // previous rotations
+        const double a = H[(size_t)i * restart + j], c = H[(size_t)(i + 1) * restart + j];
+        H[(size_t)i * restart + j] = cs[i] * a + sn[i] * c;
+        H[(size_t)(i + 1) * restart + j] = -sn[i] * a + cs[i] * c;
+      }
+      const double a = H[(size_t)j * restart + j], c = H[(size_t)(j + 1) * restart + j];
+      const double den = std::hypot(a, c);
+      cs[j] = a / den;
+      sn[j] = c / den;
+      H[(size_t)j * restart + j] = den;
+      H[(size_t)(j + 1) * restart + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++it;
+      k = j + 1;
+      rel = std::fabs(g[j + 1]) / r0;
+      if (!std::isfinite(rel)) {
+        result = fail(ctx, PMG_ERR_NUMERIC, "non-finite residual");
+        break;
+      }
+      if (rel <= rtol) break;
+    }
+    if (result != PMG_OK) break;
+    for (int i = k - 1; i >= 0; --i) {                                  // H y = g (upper triangular)
+      double v = g[i];
+      for (int c2 = i + 1; c2 < k; ++c2) v -= H[(size_t)i * restart + c2] * y[c2];
+      y[i] = v / H[(size_t)i * restart + i];
+    }
+    if (left) {                                                         // x += V y
+      for (int i = 0; i < k; ++i) LK(1, launch_axpy(y[i], V + (size_t)i * n, x, n, s));
+    } else {                                                            // x += M (V y)
+      CU(cudaMemsetAsync(t, 0, n * sizeof(double), s));
+      for (int i = 0; i < k; ++i) LK(1, launch_axpy(y[i], V + (size_t)i * n, t, n, s));
+      st = precondition(ctx, t, z, s);
+      if (st) return st;
+      LK(1, launch_axpy(1.0, z, x, n, s));
+    }
+    LK(1 + (1 << ctx->dim), cell_apply<double>(ctx, ctx->p, x, w, h.pl[0].G64, h.N, s));   // r = b - A x
+    CU(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    LK(1, mask_boundary<double>(ctx, r, M, s));
+    LK(1, launch_axpy(-1.0, w, r, n, s));
+    if (left) {                                                         // r = M (b - A x)
+      st = precondition(ctx, r, z, s);
+      if (st) return st;
+      CU(cudaMemcpyAsync(r, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+  }
+  if (result == PMG_OK && rel > rtol) result = fail(ctx, PMG_ERR_NOT_CONVERGED, "maxit reached");
+  CU(cudaMemcpyAsync(u, x, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   CU(cudaStreamSynchronize(s));
   if (iters) *iters = it;
   if (relres) *relres = rel;

@@ -410,6 +410,53 @@ struct SF {
     }
   }
 
+  // ---- final backward integration along x: like bwd_item<0, false> but every
+  // output value goes through put(pp, index, value) (the apply's epilogue)
+  template <typename PUT>
+  __device__ __forceinline__ static void bwd0_item(const T* __restrict__ in, int item, int pp, const PUT& put) {
+    constexpr int Lout = (NC == 2) ? Mi : M;
+    constexpr int OI = ipow(Lout, DIM - 1);      // items per cell
+    const int c = (NC == 2) ? (item >= OI) : 0;
+    const int o = item - c * OI;
+    const T* src = in + o * QP;
+    const int base = o * Lout;
+    T v[n];
+#pragma unroll
+    for (int g = 0; g < n; ++g) v[g] = src[c * n + g];
+    if (NC == 1) {
+#pragma unroll
+      for (int a = 0; a <= Q; ++a) {
+        T s = T(0);
+#pragma unroll
+        for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, a) * v[g];
+        put(pp, base + a, s);
+      }
+    } else if (c == 0) {
+      T w[n];
+#pragma unroll
+      for (int g = 0; g < n; ++g) w[g] = src[n + g];
+#pragma unroll
+      for (int a = 1; a <= Q; ++a) {
+        T s = T(0);
+#pragma unroll
+        for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, a) * v[g];
+        if (a == Q) {
+#pragma unroll
+          for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, 0) * w[g];
+        }
+        put(pp, base + a - 1, s);
+      }
+    } else {
+#pragma unroll
+      for (int a = 1; a < Q; ++a) {
+        T s = T(0);
+#pragma unroll
+        for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, a) * v[g];
+        put(pp, base + Q + a - 1, s);
+      }
+    }
+  }
+
   // ---- backward integration along AX: [O][QP][I] -> [O][Lout][I]
   // NC = 2: interior nodes only (Lout = Mi); NC = 1: all nodes (Lout = M).
   // ACC: add into the output instead of writing.
@@ -462,9 +509,9 @@ struct SF {
     }
   }
 
-  template <bool INTIN, bool ACC, typename GF>
-  __device__ __forceinline__ static void apply_line(const T* in, int sin, T* out, int sout, T* scr, int sscr,
-                                                    const GF& gcell) {
+  template <bool INTIN, typename GF, typename EPI>
+  __device__ __forceinline__ static void apply_line(const T* in, int sin, T* scr, int sscr, const GF& gcell,
+                                                    const EPI& epi) {
     constexpr int L = INTIN ? Mi : M;
     constexpr int Lo = (NC == 2) ? Mi : M;
     // scratch: V = scr[0..NQ) (point values, later the transposed sums),
@@ -520,7 +567,7 @@ struct SF {
       __syncthreads();
       coop<NT, PPB, Lo * QP * NC>([&](int pp, int it) { bwd_item<1, false>(Rp(pp) + B1, Rp(pp), it); });
       __syncthreads();
-      coop<NT, PPB, Lo * Lo * NC>([&](int pp, int it) { bwd_item<0, ACC>(Rp(pp), out + pp * sout, it); });
+      coop<NT, PPB, Lo * Lo * NC>([&](int pp, int it) { bwd0_item(Rp(pp), it, pp, epi); });
       __syncthreads();
     } else {
       coop<NT, PPB, L * NC>([&](int pp, int it) { fwd_item<0, INTIN>(in + pp * sin, Rp(pp), it); });
@@ -558,7 +605,7 @@ struct SF {
         }
       }
       __syncthreads();
-      coop<NT, PPB, Lo * NC>([&](int pp, int it) { bwd_item<0, ACC>(Rp(pp), out + pp * sout, it); });
+      coop<NT, PPB, Lo * NC>([&](int pp, int it) { bwd0_item(Rp(pp), it, pp, epi); });
       __syncthreads();
     }
   }
@@ -671,9 +718,9 @@ struct SF {
     stride = I;
   }
 
-  template <bool INTIN, bool ACC, typename GF>
-  __device__ __forceinline__ static void apply_stage(const T* in, int sin, T* out, int sout, T* scr, int sscr,
-                                                     const GF& gcell) {
+  template <bool INTIN, typename GF, typename EPI>
+  __device__ __forceinline__ static void apply_stage(const T* in, int sin, T* scr, int sscr, const GF& gcell,
+                                                     const EPI& epi) {
     constexpr int L = INTIN ? Mi : M;
     constexpr int Lo = (NC == 2) ? Mi : M;
     // scratch: V = scr[0..NQ), R = scr[NQ..); F_ax = R + ax*NQ
@@ -724,7 +771,7 @@ struct SF {
       __syncthreads();
       coop<NT, PPB, Lo * QP * NC>([&](int pp, int it) { bwd_item<1, false>(Rp(pp) + B1, Rp(pp), it); });
       __syncthreads();
-      coop<NT, PPB, Lo * Lo * NC>([&](int pp, int it) { bwd_item<0, ACC>(Rp(pp), out + pp * sout, it); });
+      coop<NT, PPB, Lo * Lo * NC>([&](int pp, int it) { bwd0_item(Rp(pp), it, pp, epi); });
       __syncthreads();
     } else {
       coop<NT, PPB, L * NC>([&](int pp, int it) { fwd_item<0, INTIN>(in + pp * sin, Rp(pp), it); });
@@ -748,23 +795,42 @@ struct SF {
       // y: D^T F_1 + V -> B^T along y -> R [Lo][QP] (F_0 = R is dead)
       coop<NT, PPB, QP>([&](int pp, int it) { dert_bwd_last_item(Rp(pp) + NQ, Vp(pp), Rp(pp), it); });
       __syncthreads();
-      coop<NT, PPB, Lo * NC>([&](int pp, int it) { bwd_item<0, ACC>(Rp(pp), out + pp * sout, it); });
+      coop<NT, PPB, Lo * NC>([&](int pp, int it) { bwd0_item(Rp(pp), it, pp, epi); });
       __syncthreads();
     }
   }
 
-  // Full operator: out = A in (or out += A in) for PPB blocks; in/out/scr are
-  // per-block base pointers with strides; INTIN: input on interior nodes only.
+  // Full operator A in for PPB blocks, every output value handed to the
+  // epilogue epi(pp, index, value) in the final stage (apply: stored, or
+  // added, to out); in/scr are per-block base pointers with strides; INTIN:
+  // input on interior nodes only.  The input is read in the first stage only,
+  // so an epilogue may overwrite it.
   // Not inlined: one copy per (level, input kind) is shared by all call
   // sites, which keeps the patch kernel small for the instruction cache.
   // LINE selects the design of the last direction: false = separate stages
   // with all fluxes in shared memory, true = one thread per line with that
   // direction's gradient and flux in registers.  Ends with __syncthreads().
+  template <bool INTIN, typename GF, typename EPI>
+  __device__ __noinline__ static void apply_epi(const T* in, int sin, T* scr, int sscr, const GF& gcell,
+                                                const EPI& epi) {
+    if constexpr (LINE) apply_line<INTIN>(in, sin, scr, sscr, gcell, epi);
+    else apply_stage<INTIN>(in, sin, scr, sscr, gcell, epi);
+  }
+
+  // plain result: out (+)= A in, per block pp at out + pp * sout
+  template <bool ACC>
+  struct Store {
+    T* out;
+    int sout;
+    __device__ void operator()(int pp, int i, T s) const {
+      T* p = out + pp * sout + i;
+      *p = ACC ? *p + s : s;
+    }
+  };
+
   template <bool INTIN, bool ACC, typename GF>
-  __device__ __noinline__ static void apply(const T* in, int sin, T* out, int sout, T* scr, int sscr,
-                                            const GF& gcell) {
-    if constexpr (LINE) apply_line<INTIN, ACC>(in, sin, out, sout, scr, sscr, gcell);
-    else apply_stage<INTIN, ACC>(in, sin, out, sout, scr, sscr, gcell);
+  __device__ static void apply(const T* in, int sin, T* out, int sout, T* scr, int sscr, const GF& gcell) {
+    apply_epi<INTIN>(in, sin, scr, sscr, gcell, Store<ACC>{out, sout});
   }
 };
 

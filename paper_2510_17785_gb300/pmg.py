@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libpmg.so")
 PMG_OK = 0
 ERRORS = {1: "PMG_ERR_ARG", 2: "PMG_ERR_CUDA", 3: "PMG_ERR_DEGENERATE", 4: "PMG_ERR_NOT_CONVERGED",
           5: "PMG_ERR_NUMERIC", 6: "PMG_ERR_TIMEOUT", 7: "PMG_ERR_UNSUPPORTED"}
+globals().update({name: code for code, name in ERRORS.items()})
 SMOOTHER_CHEBYSHEV, SMOOTHER_JACOBI = 0, 1
 BOUNDS_LANCZOS, BOUNDS_FIXED, BOUNDS_USER, BOUNDS_MLP = 0, 1, 2, 3
 MLP_NPARAM, MLP_NNORM = 5378, 36
@@ -33,7 +34,7 @@ SYMBOLS = (
     "pmg_gmg_vcycle", "pmg_solve_cg", "pmg_solve_cg_host", "pmg_rhs_manufactured", "pmg_get_colours",
     "pmg_get_patch_map", "pmg_get_inv_diag", "pmg_sweep_flops", "pmg_launch_count", "pmg_fma_peak",
     "pmg_lanczos_bounds_noalloc", "pmg_tuning", "pmg_default_train_options", "pmg_features", "pmg_mlp_grad",
-    "pmg_mlp_train", "pmg_mlp_predict", "pmg_set_mlp",
+    "pmg_mlp_train", "pmg_mlp_predict", "pmg_set_mlp", "pmg_solve_gmres",
 )
 
 
@@ -43,7 +44,7 @@ class Options(C.Structure):
         ("bounds", C.c_int), ("lanczos_steps", C.c_int), ("bound_safety", C.c_double),
         ("bound_ratio", C.c_double), ("fixed_lo", C.c_double), ("fixed_hi", C.c_double),
         ("seed", C.c_uint64), ("precision", C.c_int), ("autotune", C.c_int), ("variant", C.c_int),
-        ("mlp_safety", C.c_double), ("coarse_kappa", C.c_int),
+        ("mlp_safety", C.c_double), ("coarse_kappa", C.c_int), ("post_reverse", C.c_int),
     ]
 
 
@@ -108,6 +109,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pmg_mlp_train": (i, [i, vp, vp, vp, vp, i64, P(TrainOptions), vp]),
         "pmg_mlp_predict": (i, [i, vp, vp, vp, i64, i, vp, vp]),
         "pmg_set_mlp": (i, [vp, vp, vp]),
+        "pmg_solve_gmres": (i, [vp, vp, vp, d, i, i, i, P(i), P(d), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -269,6 +271,14 @@ class Context:
         it, rel = C.c_int(), C.c_double()
         rc = self.lib.pmg_solve_cg(self.h, _ptr(b), _ptr(u), rtol, maxit, C.byref(it), C.byref(rel),
                                    _stream(stream))
+        if check:
+            self._check(rc)
+        return it.value, rel.value, rc
+
+    def solve_gmres(self, b, u, rtol=1e-8, maxit=200, restart=50, left=False, stream=None, check=True):
+        it, rel = C.c_int(), C.c_double()
+        rc = self.lib.pmg_solve_gmres(self.h, _ptr(b), _ptr(u), rtol, maxit, restart, int(bool(left)), C.byref(it),
+                                      C.byref(rel), _stream(stream))
         if check:
             self._check(rc)
         return it.value, rel.value, rc

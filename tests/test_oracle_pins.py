@@ -14,6 +14,7 @@ import pytest
 import scipy.sparse.linalg as spla
 
 from oracle import fem, gmg, lanczos as lz, patch as pt, rules
+from oracle.gmg import gmres
 from paper_2510_17785_gb300 import inputs
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -478,3 +479,69 @@ def test_gmg_preconditioned_cg(kind):
     # the symmetric V-cycle is a symmetric operator
     y1, y2 = rng.uniform(-1, 1, len(b)) * free, rng.uniform(-1, 1, len(b)) * free
     assert abs(y1 @ G.vcycle(y2) - y2 @ G.vcycle(y1)) < 1e-12 * abs(y1 @ G.vcycle(y1))
+
+
+# ------------------------------------------------------------------ GMRES
+def test_gmres_minimises_the_residual_over_the_krylov_space():
+    """GMRES after k steps has the smallest residual ||b - A M y|| over the
+    Krylov space K_k(A M, b), checked by a dense least-squares solve."""
+    rng = np.random.default_rng(9)
+    n = 40
+    A = rng.standard_normal((n, n)) + 8 * np.eye(n)
+    Mi = np.diag(1.0 / np.diag(A)) + 0.01 * rng.standard_normal((n, n))     # non-symmetric preconditioner
+    b = rng.standard_normal(n)
+    AM = A @ Mi
+    for k in (1, 3, 6, 10):
+        x, it, hist = gmres(A, b, lambda v: Mi @ v, rtol=1e-30, maxit=k, restart=50)
+        K = np.column_stack([np.linalg.matrix_power(AM, i) @ b for i in range(k)])
+        y, *_ = np.linalg.lstsq(AM @ K, b, rcond=None)
+        best = np.linalg.norm(b - AM @ K @ y)
+        assert it == k
+        assert abs(np.linalg.norm(b - A @ x) - best) < 1e-10 * np.linalg.norm(b)
+        assert abs(hist[-1] * np.linalg.norm(b) - best) < 1e-10 * np.linalg.norm(b)
+
+
+def test_left_gmres_minimises_the_preconditioned_residual():
+    """Left preconditioning: after k steps ||M (b - A x)|| is the smallest over
+    x in K_k(M A, M b) (dense least squares), and the restart keeps it monotone."""
+    rng = np.random.default_rng(12)
+    n = 40
+    A = rng.standard_normal((n, n)) + 8 * np.eye(n)
+    Mi = np.diag(1.0 / np.diag(A)) + 0.01 * rng.standard_normal((n, n))
+    b = rng.standard_normal(n)
+    MA, Mb = Mi @ A, Mi @ b
+    for k in (1, 4, 9):
+        x, it, hist = gmres(A, b, lambda v: Mi @ v, rtol=1e-30, maxit=k, restart=50, left=True)
+        K = np.column_stack([np.linalg.matrix_power(MA, i) @ Mb for i in range(k)])
+        y, *_ = np.linalg.lstsq(MA @ K, Mb, rcond=None)
+        best = np.linalg.norm(Mb - MA @ K @ y)
+        assert it == k
+        assert abs(np.linalg.norm(Mi @ (b - A @ x)) - best) < 1e-10 * np.linalg.norm(Mb)
+        assert abs(hist[-1] * np.linalg.norm(Mb) - best) < 1e-10 * np.linalg.norm(Mb)
+    x, it, hist = gmres(A, b, lambda v: Mi @ v, rtol=1e-10, maxit=60, restart=4, left=True)
+    assert all(h1 <= h0 * (1 + 1e-12) for h0, h1 in zip(hist, hist[1:]))
+    assert abs(np.linalg.norm(Mi @ (b - A @ x)) - hist[-1] * np.linalg.norm(Mb)) <= 1e-10 * np.linalg.norm(Mb)
+
+
+def test_gmres_with_exact_preconditioner_takes_one_step():
+    rng = np.random.default_rng(10)
+    A = rng.standard_normal((30, 30)) + 6 * np.eye(30)
+    b = rng.standard_normal(30)
+    Ainv = np.linalg.inv(A)
+    for left in (False, True):
+        x, it, hist = gmres(A, b, lambda v: Ainv @ v, 1e-12, 20, left=left)
+        assert it == 1 and np.allclose(A @ x, b, atol=1e-10)
+
+
+def test_gmres_with_the_paper_smoother_on_a_small_mesh():
+    """Section 4 set-up in miniature: Jacobi p-MG patch smoother, same colour
+    order before and after the coarse correction (non-symmetric), GMRES."""
+    m = _mesh(2, 8, 0.25, 33)
+    p = 3
+    G = gmg.GMG(m, p, 2, smoother_args=dict(sm=pt.Smoother(kind="jacobi", omega=0.5)), post_reverse=False)
+    rng = np.random.default_rng(11)
+    free = G.free[-1]
+    b = rng.uniform(-1, 1, len(free)) * free
+    x, it, hist = gmres(G.A[-1], b, G.vcycle, 1e-8, 60)
+    assert hist[-1] <= 1e-8 and it <= 15
+    assert np.linalg.norm(G.A[-1] @ x - b) <= 1e-7 * np.linalg.norm(b)
