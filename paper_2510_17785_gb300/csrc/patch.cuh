@@ -125,41 +125,51 @@ struct Layout {
 // Launch shape of the patch kernel.  Variant 0 is the default; for 3D degrees
 // 3..8 the set-up autotuner also times variants 1..7:
 //   variant:          1        2        3        4        5        6        7
-//   design:         stage    stage    stage    line     line     stage    stage
-//   threads / CTA:    256      128      512      256      128      256      128
-//   patches / CTA:      2        1        4        2        1        4        2
+//   design:         stage    stage    line     line     line     line     line
+//   threads / CTA:    256      128       64      256      128       32      128
+//   patches / CTA:      2        1        1        2        1        1        2
+//   groups:                                                                 2
 // (patches per CTA are capped by shared memory).  "stage": every direction's
 // flux in shared memory; "line": one thread per line along the last
-// direction keeps that direction's gradient and flux in registers.
+// direction keeps that direction's gradient and flux in registers.  With
+// groups, each patch of the CTA has its own threads and barrier.
 constexpr int NUM_VARIANTS = 8;
 
 template <int DIM, int P, typename T, int V = 0>
 struct Config {
   static constexpr int NT0 = (DIM == 3) ? 256 : 128;
   static constexpr int PPB0 = (DIM == 3) ? (P <= 2 ? 4 : 1) : (P <= 2 ? 8 : (P <= 4 ? 4 : 2));
-  static constexpr int NTV[NUM_VARIANTS] = {NT0, 256, 128, 512, 256, 128, 256, 128};
-  static constexpr int PPBV[NUM_VARIANTS] = {PPB0, 2, 1, 4, 2, 1, 4, 2};
-  static constexpr bool LINEV[NUM_VARIANTS] = {false, false, false, false, true, true, false, false};
+  static constexpr int NTV[NUM_VARIANTS] = {NT0, 256, 128, 64, 256, 128, 32, 128};
+  static constexpr int PPBV[NUM_VARIANTS] = {PPB0, 2, 1, 1, 2, 1, 1, 2};
+  static constexpr bool LINEV[NUM_VARIANTS] = {false, false, false, true, true, true, true, true};
+  static constexpr bool GROUPV[NUM_VARIANTS] = {false, false, false, false, false, false, false, true};
   static constexpr int NT = NTV[V];
   static constexpr int PPB_MAX = PPBV[V];
   static constexpr bool LINE = LINEV[V];
   static constexpr size_t bytes_per_patch =
-      sizeof(T) * Layout<DIM, P, LINE>::PS + sizeof(int) * ((1 << DIM) + 4);
+      sizeof(T) * Layout<DIM, P, LINE>::PS + sizeof(int) * ((1 << DIM) + 6);
   static constexpr size_t SMEM_LIMIT = 227 * 1024;
   static constexpr int PPB_FIT = (int)(SMEM_LIMIT / bytes_per_patch);
   static constexpr int PPB = PPB_FIT < PPB_MAX ? (PPB_FIT < 1 ? 1 : PPB_FIT) : PPB_MAX;
   static constexpr size_t smem = bytes_per_patch * PPB;
   static constexpr bool fits = bytes_per_patch <= SMEM_LIMIT;
+  // grouped only when the CTA really holds several patches
+  static constexpr bool GROUPED = GROUPV[V] && PPB > 1 && NT % PPB == 0 && (NT / PPB) % 32 == 0;
   // register budget per thread (launch bound): 64 for FP32 up to degree 5,
   // 128 otherwise (FP64, or the larger line registers at high degree)
   static constexpr int REG_TARGET = (sizeof(T) == 4 && P <= 5) ? 64 : 128;
-  static constexpr int MINB_RAW = 65536 / (NT * REG_TARGET);
+  // resident CTAs per SM: by the register target, and at most what shared
+  // memory allows (small CTAs then get the registers shared memory leaves)
+  static constexpr int MINB_REG = 65536 / (NT * REG_TARGET);
+  static constexpr int MINB_SMEM = (int)((228 * 1024) / (smem + 1024));
+  static constexpr int MINB_RAW = MINB_REG < MINB_SMEM ? MINB_REG : MINB_SMEM;
   static constexpr int MINB = MINB_RAW < 1 ? 1 : MINB_RAW;
   // a variant exists (is worth instantiating) if it fits and differs from
   // every lower-numbered variant
   template <int W>
   static constexpr bool same_as() {
-    return Config<DIM, P, T, W>::NT == NT && Config<DIM, P, T, W>::PPB == PPB && Config<DIM, P, T, W>::LINE == LINE;
+    return Config<DIM, P, T, W>::NT == NT && Config<DIM, P, T, W>::PPB == PPB && Config<DIM, P, T, W>::LINE == LINE &&
+           Config<DIM, P, T, W>::GROUPED == GROUPED;
   }
   static constexpr bool distinct_impl() {
     if constexpr (V == 0) return true;
@@ -181,11 +191,13 @@ template <int DIM, int P, typename T, int MODE, int V = 0>
 struct PatchKernel {
   using C = Config<DIM, P, T, V>;
   using L = Layout<DIM, P, C::LINE>;
+  using TM = Team<C::NT, C::PPB, C::GROUPED>;
   static constexpr int NT = C::NT, PPB = C::PPB, NL = L::NL, PS = L::PS;
   static constexpr int NCELL = 1 << DIM;
 
   T* sm;           // per-patch arrays, stride PS
-  int* cells;      // [PPB][NCELL + 4]: global cell ids, then patch id, vertex index parts
+  int* cells;      // [PPB][CST]: global cell ids, patch id, active flag, vertex indices (v_x, v_y, v_z)
+  static constexpr int CST = NCELL + 6;
   const PatchArgs<T>* a;
 
   __device__ T* vec(int pp, int off) const { return sm + pp * PS + off; }
@@ -196,7 +208,7 @@ struct PatchKernel {
     constexpr int stride = Dims<DIM, 2, q>::NCOMP * ipow(q + 1, DIM);
     const T* G = a->lv[K].G;
     const int* cl = cells;
-    return [G, cl](int pp, int slot) { return G + (size_t)cl[pp * (NCELL + 4) + slot] * stride; };
+    return [G, cl](int pp, int slot) { return G + (size_t)cl[pp * CST + slot] * stride; };
   }
 
   template <int K>
@@ -227,7 +239,7 @@ struct PatchKernel {
       // the epilogue may overwrite the input, which other rows still read:
       // products first, epilogue after a barrier
       constexpr int NI = L::ni(K);
-      coop<NT, PPB, NI>([&](int pp, int r) {
+      TM::template loop<NI>([&](int pp, int r) {
         const T* A = vec(pp, L::DENSE(K)) + r * NI;
         const T* x = vec(pp, in_off);
         T s = T(0);
@@ -235,13 +247,13 @@ struct PatchKernel {
         for (int c = 0; c < NI; ++c) s += A[c] * x[c];
         vec(pp, L::AD(K))[r] = s;
       });
-      __syncthreads();
+      TM::sync();
       if (e.kind != EPI_STORE) {
-        coop<NT, PPB, NI>([&](int pp, int r) { e(pp, r, vec(pp, L::AD(K))[r]); });
-        __syncthreads();
+        TM::template loop<NI>([&](int pp, int r) { e(pp, r, vec(pp, L::AD(K))[r]); });
+        TM::sync();
       }
     } else {
-      SF<DIM, 2, q, T, NT, PPB, C::LINE>::template apply_epi<true>(vec(0, in_off), PS, vec(0, L::SCR), PS,
+      SF<DIM, 2, q, T, NT, PPB, C::LINE, C::GROUPED>::template apply_epi<true>(vec(0, in_off), PS, vec(0, L::SCR), PS,
                                                                   gfun<K>(), e);
     }
   }
@@ -326,25 +338,25 @@ struct PatchKernel {
     constexpr int Mf = 2 * qf - 1, Mc = (qc == 1) ? 1 : 2 * qc - 1;
     T* t = vec(0, L::SCR);
     if constexpr (DIM == 3) {
-      coop<NT, PPB, Mf * Mf * 2>([&](int pp, int it) {
+      TM::template loop<Mf * Mf * 2>([&](int pp, int it) {
         rest_item<K>(vec(pp, L::RES(K)), t + pp * PS, it, Mc, Mf, 1, Mf * Mf);
       });
-      __syncthreads();
-      coop<NT, PPB, Mf * Mc * 2>([&](int pp, int it) {
+      TM::sync();
+      TM::template loop<Mf * Mc * 2>([&](int pp, int it) {
         rest_item<K>(t + pp * PS, t + pp * PS + Mf * Mf * Mc, it, Mc, Mf, Mc, Mf);
       });
-      __syncthreads();
-      coop<NT, PPB, Mc * Mc * 2>([&](int pp, int it) {
+      TM::sync();
+      TM::template loop<Mc * Mc * 2>([&](int pp, int it) {
         rest_item<K>(t + pp * PS + Mf * Mf * Mc, vec(pp, L::R_(K + 1)), it, Mc, Mf, Mc * Mc, 1);
       });
-      __syncthreads();
+      TM::sync();
     } else {
-      coop<NT, PPB, Mf * 2>([&](int pp, int it) { rest_item<K>(vec(pp, L::RES(K)), t + pp * PS, it, Mc, Mf, 1, Mf); });
-      __syncthreads();
-      coop<NT, PPB, Mc * 2>([&](int pp, int it) {
+      TM::template loop<Mf * 2>([&](int pp, int it) { rest_item<K>(vec(pp, L::RES(K)), t + pp * PS, it, Mc, Mf, 1, Mf); });
+      TM::sync();
+      TM::template loop<Mc * 2>([&](int pp, int it) {
         rest_item<K>(t + pp * PS, vec(pp, L::R_(K + 1)), it, Mc, Mf, Mc, 1);
       });
-      __syncthreads();
+      TM::sync();
     }
   }
 
@@ -355,27 +367,27 @@ struct PatchKernel {
     constexpr int Mf = 2 * qf - 1, Mc = (qc == 1) ? 1 : 2 * qc - 1;
     T* t = vec(0, L::SCR);
     if constexpr (DIM == 3) {
-      coop<NT, PPB, Mc * Mc * 2>([&](int pp, int it) {
+      TM::template loop<Mc * Mc * 2>([&](int pp, int it) {
         prol_item<K, 0, false>(vec(pp, L::D_(K + 1)), t + pp * PS, it, Mc, Mf, 1, Mc * Mc);
       });
-      __syncthreads();
-      coop<NT, PPB, Mc * Mf * 2>([&](int pp, int it) {
+      TM::sync();
+      TM::template loop<Mc * Mf * 2>([&](int pp, int it) {
         prol_item<K, 1, false>(t + pp * PS, t + pp * PS + Mc * Mc * Mf, it, Mc, Mf, Mf, Mc);
       });
-      __syncthreads();
-      coop<NT, PPB, Mf * Mf * 2>([&](int pp, int it) {
+      TM::sync();
+      TM::template loop<Mf * Mf * 2>([&](int pp, int it) {
         prol_item<K, 2, true>(t + pp * PS + Mc * Mc * Mf, vec(pp, L::D_(K)), it, Mc, Mf, Mf * Mf, 1);
       });
-      __syncthreads();
+      TM::sync();
     } else {
-      coop<NT, PPB, Mc * 2>([&](int pp, int it) {
+      TM::template loop<Mc * 2>([&](int pp, int it) {
         prol_item<K, 0, false>(vec(pp, L::D_(K + 1)), t + pp * PS, it, Mc, Mf, 1, Mc);
       });
-      __syncthreads();
-      coop<NT, PPB, Mf * 2>([&](int pp, int it) {
+      TM::sync();
+      TM::template loop<Mf * 2>([&](int pp, int it) {
         prol_item<K, 1, true>(t + pp * PS, vec(pp, L::D_(K)), it, Mc, Mf, Mf, 1);
       });
-      __syncthreads();
+      TM::sync();
     }
   }
 
@@ -386,8 +398,8 @@ struct PatchKernel {
     if (a->smoother == 1) {   // damped Jacobi, d += omega D^-1 (r - A d)
       if (zero_start) {
         const T om = T(a->omega);
-        coop<NT, PPB, NI>([&](int pp, int i) { vec(pp, L::D_(K))[i] = om * vec(pp, L::DINV(K))[i] * vec(pp, L::R_(K))[i]; });
-        __syncthreads();
+        TM::template loop<NI>([&](int pp, int i) { vec(pp, L::D_(K))[i] = om * vec(pp, L::DINV(K))[i] * vec(pp, L::R_(K))[i]; });
+        TM::sync();
       } else {
         apply_int<K>(L::D_(K), epi<K>(EPI_JAC));
       }
@@ -396,7 +408,7 @@ struct PatchKernel {
     // Chebyshev iteration (three-term recurrence on D^-1 A over [lo, hi])
     const int deg = a->cheb_degree;
     if (zero_start) {
-      coop<NT, PPB, NI>([&](int pp, int i) {
+      TM::template loop<NI>([&](int pp, int i) {
         const T* cf = vec(pp, L::COEF + K * L::NCOEF);
         const T res = vec(pp, L::DINV(K))[i] * vec(pp, L::R_(K))[i];
         const T dir = res * cf[0];
@@ -404,7 +416,7 @@ struct PatchKernel {
         vec(pp, L::DIR(K))[i] = dir;
         vec(pp, L::D_(K))[i] = dir;
       });
-      __syncthreads();
+      TM::sync();
     } else {
       apply_int<K>(L::D_(K), epi<K>(EPI_CHEB0));
     }
@@ -417,8 +429,8 @@ struct PatchKernel {
   __device__ void vcycle(bool zero_start) {
     constexpr int q = P >> K;
     if constexpr (q == 1) {
-      coop<NT, PPB, 1>([&](int pp, int) { vec(pp, L::D_(K))[0] = vec(pp, L::R_(K))[0] * vec(pp, L::DINV(K))[0]; });
-      __syncthreads();
+      TM::template loop<1>([&](int pp, int) { vec(pp, L::D_(K))[0] = vec(pp, L::R_(K))[0] * vec(pp, L::DINV(K))[0]; });
+      TM::sync();
     } else {
       constexpr int NI = L::ni(K);
       smooth<K>(zero_start);                                      // pre-smoothing
@@ -441,7 +453,7 @@ struct PatchKernel {
     int v[3] = {1, 1, 1};
     int rem = pid;
     for (int ax = 0; ax < DIM; ++ax) { v[ax] = 1 + rem % Nv; rem /= Nv; }
-    int* cl = cells + pp * (NCELL + 4);
+    int* cl = cells + pp * CST;
     for (int s = 0; s < NCELL; ++s) {
       int id = 0, mul = 1;
       for (int ax = 0; ax < DIM; ++ax) { id += (v[ax] - 1 + ((s >> ax) & 1)) * mul; mul *= N; }
@@ -449,16 +461,10 @@ struct PatchKernel {
     }
     cl[NCELL] = pid;
     cl[NCELL + 1] = active ? 1 : 0;
-    cl[NCELL + 2] = v[0] + (N + 1) * (v[1] + (N + 1) * (DIM == 3 ? v[2] : 0));
+    for (int ax = 0; ax < 3; ++ax) cl[NCELL + 2 + ax] = v[ax];
   }
 
-  __device__ int patch_vertex(int pp, int ax) const {
-    const int* cl = cells + pp * (NCELL + 4);
-    const int N = a->N;
-    int vid = cl[NCELL + 2];
-    for (int k = 0; k < ax; ++k) vid /= (N + 1);
-    return vid % (N + 1);
-  }
+  __device__ int patch_vertex(int pp, int ax) const { return cells[pp * CST + NCELL + 2 + ax]; }
 
   // global index on the degree-q grid of patch-local node (k_x, k_y[, k_z]) in [0, 2q]
   template <int q>
@@ -499,8 +505,8 @@ struct PatchKernel {
   __device__ void load_level() {
     constexpr int q = P >> K;
     if constexpr (q == 1) {
-      coop<NT, PPB, 1>([&](int pp, int) {
-        const bool act = cells[pp * (NCELL + 4) + NCELL + 1];
+      TM::template loop<1>([&](int pp, int) {
+        const bool act = cells[pp * CST + NCELL + 1];
         const int N = a->N;
         size_t idx = 0, mul = 1;
         for (int ax = 0; ax < DIM; ++ax) { idx += (size_t)patch_vertex(pp, ax) * mul; mul *= (N + 1); }
@@ -508,22 +514,22 @@ struct PatchKernel {
       });
     } else {
       constexpr int NI = L::ni(K);
-      coop<NT, PPB, NI>([&](int pp, int i) {
-        const bool act = cells[pp * (NCELL + 4) + NCELL + 1];
+      TM::template loop<NI>([&](int pp, int i) {
+        const bool act = cells[pp * CST + NCELL + 1];
         vec(pp, L::DINV(K))[i] = act ? a->lv[K].dinv[gindex_int<q>(pp, i)] : T(0);
       });
       if constexpr (dense_level(DIM, q)) {
-        coop<NT, PPB, NI * NI>([&](int pp, int e) {
-          const bool act = cells[pp * (NCELL + 4) + NCELL + 1];
-          const int pid = cells[pp * (NCELL + 4) + NCELL];
+        TM::template loop<NI * NI>([&](int pp, int e) {
+          const bool act = cells[pp * CST + NCELL + 1];
+          const int pid = cells[pp * CST + NCELL];
           vec(pp, L::DENSE(K))[e] = act ? a->lv[K].dense[(size_t)pid * NI * NI + e] : T(0);
         });
       }
       // Chebyshev coefficients (FP64 scalars, rounded to T)
       if (a->smoother == 0) {
-        for (int pp = threadIdx.x; pp < PPB; pp += NT) {
-          const bool act = cells[pp * (NCELL + 4) + NCELL + 1];
-          const int pid = cells[pp * (NCELL + 4) + NCELL];
+        TM::per_block([&](int pp) {
+          const bool act = cells[pp * CST + NCELL + 1];
+          const int pid = cells[pp * CST + NCELL];
           double lo = 1.0, hi = 2.0;
           if (act) { lo = (double)a->lv[K].bounds[2 * (size_t)pid]; hi = (double)a->lv[K].bounds[2 * (size_t)pid + 1]; }
           const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
@@ -537,7 +543,7 @@ struct PatchKernel {
             cf[7 + i] = T((2.0 * rn) / delta);
             rho = rn;
           }
-        }
+        });
       }
     }
     if constexpr (K + 1 < NL) load_level<K + 1>();
@@ -545,44 +551,44 @@ struct PatchKernel {
 
   __device__ void run() {
     const int item0 = blockIdx.x * PPB;
-    for (int pp = threadIdx.x; pp < PPB; pp += NT) setup_patch(pp, item0 + pp, item0 + pp < a->n_items);
-    __syncthreads();
+    TM::per_block([&](int pp) { setup_patch(pp, item0 + pp, item0 + pp < a->n_items); });
+    TM::sync();
     load_level<0>();
     constexpr int NI0 = L::ni(0);
     if (MODE == MODE_SWEEP) {
       // Gather: closure of u, interior of b
       constexpr int NN0 = L::NN0;
-      coop<NT, PPB, NN0>([&](int pp, int i) {
-        const bool act = cells[pp * (NCELL + 4) + NCELL + 1];
+      TM::template loop<NN0>([&](int pp, int i) {
+        const bool act = cells[pp * CST + NCELL + 1];
         vec(pp, L::CLOS)[i] = act ? a->u[gindex<P>(pp, i)] : T(0);
       });
-      coop<NT, PPB, NI0>([&](int pp, int i) {
-        const bool act = cells[pp * (NCELL + 4) + NCELL + 1];
+      TM::template loop<NI0>([&](int pp, int i) {
+        const bool act = cells[pp * CST + NCELL + 1];
         vec(pp, L::R_(0))[i] = act ? a->b[gindex_int<P>(pp, i)] : T(0);
       });
-      __syncthreads();
+      TM::sync();
       // Evaluate: r = b - A u on the patch interior
-      SF<DIM, 2, P, T, NT, PPB, C::LINE>::template apply_epi<false>(vec(0, L::CLOS), PS, vec(0, L::SCR), PS,
+      SF<DIM, 2, P, T, NT, PPB, C::LINE, C::GROUPED>::template apply_epi<false>(vec(0, L::CLOS), PS, vec(0, L::SCR), PS,
                                                                    gfun<0>(), epi<0>(EPI_EVAL));
     } else {
-      coop<NT, PPB, NI0>([&](int pp, int i) {
-        const bool act = cells[pp * (NCELL + 4) + NCELL + 1];
+      TM::template loop<NI0>([&](int pp, int i) {
+        const bool act = cells[pp * CST + NCELL + 1];
         vec(pp, L::R_(0))[i] = act ? a->r_in[(size_t)(item0 + pp) * NI0 + i] : T(0);
       });
-      __syncthreads();
+      TM::sync();
     }
     // Solve: N_MG V-cycles, the first from d = 0
 #pragma unroll 1
     for (int cyc = 0; cyc < a->n_mg; ++cyc) vcycle<0>(cyc == 0);
     // Scatter
     if (MODE == MODE_SWEEP) {
-      coop<NT, PPB, NI0>([&](int pp, int i) {
-        const bool act = cells[pp * (NCELL + 4) + NCELL + 1];
+      TM::template loop<NI0>([&](int pp, int i) {
+        const bool act = cells[pp * CST + NCELL + 1];
         if (act) a->u[gindex_int<P>(pp, i)] += vec(pp, L::D_(0))[i];
       });
     } else {
-      coop<NT, PPB, NI0>([&](int pp, int i) {
-        const bool act = cells[pp * (NCELL + 4) + NCELL + 1];
+      TM::template loop<NI0>([&](int pp, int i) {
+        const bool act = cells[pp * CST + NCELL + 1];
         if (act) a->d_out[(size_t)(item0 + pp) * NI0 + i] = vec(pp, L::D_(0))[i];
       });
     }

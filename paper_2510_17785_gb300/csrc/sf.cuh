@@ -65,80 +65,180 @@ __device__ __forceinline__ void coop(F&& f) {
   }
 }
 
-template <int DIM, int NC, int Q, typename T, int NT, int PPB, bool LINE = false>
+// How the NT threads of a CTA share its PPB blocks.
+//  GROUPED = false: every thread works on every block; a stage ends with a
+//    CTA-wide barrier.
+//  GROUPED = true: the CTA is PPB independent groups of TPP = NT / PPB threads
+//    (a multiple of 32); group g works on block g only and synchronises with a
+//    barrier of its own (named barrier g + 1, or a warp barrier for one-warp
+//    groups), so no group waits for another group's block.
+template <int NT, int PPB, bool GROUPED>
+struct Team {
+  static_assert(!GROUPED || (NT % PPB == 0 && (NT / PPB) % 32 == 0 && PPB <= 15), "bad grouped team");
+  static constexpr int TPP = GROUPED ? NT / PPB : NT;      // threads sharing one item loop
+  static constexpr int SPAN = GROUPED ? 1 : PPB;           // blocks covered by one item loop
+  __device__ __forceinline__ static int group() { return GROUPED ? (int)threadIdx.x / TPP : 0; }
+  __device__ __forceinline__ static int lane() { return GROUPED ? (int)threadIdx.x % TPP : (int)threadIdx.x; }
+  __device__ __forceinline__ static void sync() {
+    if constexpr (!GROUPED || PPB == 1) {
+      __syncthreads();
+    } else if constexpr (TPP == 32) {
+      __syncwarp();
+    } else {
+      asm volatile("bar.sync %0, %1;" ::"r"(group() + 1), "n"(TPP) : "memory");
+    }
+  }
+  // f(pp, item) for item in [0, ITEMS) of every block this thread serves
+  template <int ITEMS, typename F>
+  __device__ __forceinline__ static void loop(F&& f) {
+    if constexpr (GROUPED) {
+      const int pp = group();
+#pragma unroll 1
+      for (int it = lane(); it < ITEMS; it += TPP) f(pp, it);
+    } else {
+      coop<NT, PPB, ITEMS>(f);
+    }
+  }
+  // the l-th (block, item) slot of this thread in a loop over ITEMS items
+  // per block: false when the thread has no l-th slot
+  template <int ITEMS>
+  __device__ __forceinline__ static bool slot(int l, int& pp, int& item) {
+    const int it = lane() + l * TPP;
+    if constexpr (GROUPED) {
+      pp = group();
+      item = it;
+    } else {
+      pp = it / ITEMS;
+      item = it - pp * ITEMS;
+    }
+    return it < SPAN * ITEMS;
+  }
+  // f(pp) once for every block, by one thread
+  template <typename F>
+  __device__ __forceinline__ static void per_block(F&& f) {
+    if constexpr (GROUPED) {
+      if (lane() == 0) f(group());
+    } else {
+      for (int pp = threadIdx.x; pp < PPB; pp += NT) f(pp);
+    }
+  }
+};
+
+template <int DIM, int NC, int Q, typename T, int NT, int PPB, bool LINE = false, bool GROUPED = false>
 struct SF {
   using D = Dims<DIM, NC, Q>;
+  using TM = Team<NT, PPB, GROUPED>;
   static constexpr int n = D::n, M = D::M, Mi = D::Mi, QP = D::QP, NQ = D::NQ;
 
-  // ---- forward interpolation along axis AX: [O][L][I] -> [O][QP][I]
+  // ---- line helpers: one item is a whole line of the block along an axis
+  // (all NC cells).  The node values of a line with the patch's Dirichlet
+  // ends (INTIN) are zero at both ends; those terms are skipped.
+  template <bool INTIN>
+  __device__ __forceinline__ static void load_line(const T* __restrict__ src, int stride, T (&v)[M]) {
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      if (INTIN && NC == 2) v[k] = (k == 0 || k == M - 1) ? T(0) : src[(k - 1) * stride];
+      else v[k] = src[k * stride];
+    }
+  }
+  // nodes -> Gauss points of every cell of the line
+  template <bool INTIN>
+  __device__ __forceinline__ static void interp_line(const T (&v)[M], T (&w)[QP]) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int a0 = (INTIN && NC == 2 && c == 0) ? 1 : 0;
+      const int a1 = (INTIN && NC == 2 && c == NC - 1) ? Q - 1 : Q;
+#pragma unroll
+      for (int g = 0; g < n; ++g) {
+        T s = T(0);
+#pragma unroll
+        for (int a = 0; a <= Q; ++a)
+          if (a >= a0 && a <= a1) s += tabB<T>(Q, g, a) * v[c * Q + a];
+        w[c * n + g] = s;
+      }
+    }
+  }
+  // Gauss points of every cell -> nodes (transposed interpolation); NC = 2:
+  // interior nodes 1..M-2 only, written to out[(k-1)*stride] (ACC: added);
+  // NC = 1: all nodes.  The node shared by the two cells sums cell 0's terms,
+  // then cell 1's.
+  template <bool ACC, typename PUT>
+  __device__ __forceinline__ static void integ_line(const T (&w)[QP], const PUT& put) {
+    if constexpr (NC == 1) {
+#pragma unroll
+      for (int a = 0; a <= Q; ++a) {
+        T s = put.init(a);
+#pragma unroll
+        for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, a) * w[g];
+        put(a, s);
+      }
+    } else {
+#pragma unroll
+      for (int k = 1; k <= M - 2; ++k) {
+        T s = put.init(k - 1);
+        if (k <= Q) {
+#pragma unroll
+          for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, k) * w[g];
+        }
+        if (k >= Q) {
+#pragma unroll
+          for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, k - Q) * w[n + g];
+        }
+        put(k - 1, s);
+      }
+    }
+  }
+  // output sinks for integ_line: strided store (ACC: add) / epilogue
+  template <bool ACC>
+  struct LineStore {
+    T* dst;
+    int stride;
+    __device__ __forceinline__ T init(int k) const { return ACC ? dst[k * stride] : T(0); }
+    __device__ __forceinline__ void operator()(int k, T s) const { dst[k * stride] = s; }
+  };
+  template <typename EPI>
+  struct LineEpi {
+    const EPI& epi;
+    int pp, base;
+    __device__ __forceinline__ T init(int) const { return T(0); }
+    __device__ __forceinline__ void operator()(int k, T s) const { epi(pp, base + k, s); }
+  };
+
+  // ---- forward interpolation along axis AX: [O][L][I] -> [O][QP][I], one line per item
   template <int AX, bool INTIN>
   __device__ __forceinline__ static void fwd_item(const T* __restrict__ in, T* __restrict__ out, int item) {
     constexpr int L = INTIN ? Mi : M;
     constexpr int I = ipow(QP, AX);
-    constexpr int OI = ipow(L, DIM - 1 - AX) * I;     // items per cell
-    const int c = (NC == 2) ? (item >= OI) : 0;
-    const int pi = item - c * OI;
-    const int i = pi % I, o = pi / I;
-    const T* src = in + o * L * I + i;
+    const int i = item % I, o = item / I;
+    T v[M], w[QP];
+    load_line<INTIN>(in + o * L * I + i, I, v);
+    interp_line<INTIN>(v, w);
     T* dst = out + o * QP * I + i;
-    T v[n];
 #pragma unroll
-    for (int a = 0; a <= Q; ++a) {
-      const int k = c * Q + a;
-      if (INTIN) {
-        const bool ok = (k >= 1) && (k <= M - 2);
-        v[a] = ok ? src[(k - 1) * I] : T(0);
-      } else {
-        v[a] = src[k * I];
-      }
-    }
-#pragma unroll
-    for (int g = 0; g < n; ++g) {
-      T s = T(0);
-#pragma unroll
-      for (int a = 0; a <= Q; ++a) s += tabB<T>(Q, g, a) * v[a];
-      dst[(c * n + g) * I] = s;
-    }
+    for (int g = 0; g < QP; ++g) dst[g * I] = w[g];
   }
 
   // ---- forward interpolation along the last axis fused with the collocation
   // derivative along it: writes the point values V and the derivative F.
   template <bool INTIN>
   __device__ __forceinline__ static void fwd_der_last_item(const T* __restrict__ in, T* __restrict__ V,
-                                                           T* __restrict__ F, int item) {
+                                                           T* __restrict__ F, int i) {
     constexpr int AX = DIM - 1;
-    constexpr int L = INTIN ? Mi : M;
     constexpr int I = ipow(QP, AX);
-    const int c = (NC == 2) ? (item >= I) : 0;
-    const int i = item - c * I;
-    const T* src = in + i;
-    T v[n];
+    T v[M], w[QP];
+    load_line<INTIN>(in + i, I, v);
+    interp_line<INTIN>(v, w);
 #pragma unroll
-    for (int a = 0; a <= Q; ++a) {
-      const int k = c * Q + a;
-      if (INTIN) {
-        const bool ok = (k >= 1) && (k <= M - 2);
-        v[a] = ok ? src[(k - 1) * I] : T(0);
-      } else {
-        v[a] = src[k * I];
+    for (int g = 0; g < QP; ++g) V[g * I + i] = w[g];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+#pragma unroll
+      for (int g = 0; g < n; ++g) {
+        T s = T(0);
+#pragma unroll
+        for (int h = 0; h < n; ++h) s += tabD<T>(Q, g, h) * w[c * n + h];
+        F[(c * n + g) * I + i] = s;
       }
-    }
-    static_assert(L > 0, "");
-    T w[n];
-#pragma unroll
-    for (int g = 0; g < n; ++g) {
-      T s = T(0);
-#pragma unroll
-      for (int a = 0; a <= Q; ++a) s += tabB<T>(Q, g, a) * v[a];
-      w[g] = s;
-      V[(c * n + g) * I + i] = s;
-    }
-#pragma unroll
-    for (int g = 0; g < n; ++g) {
-      T s = T(0);
-#pragma unroll
-      for (int h = 0; h < n; ++h) s += tabD<T>(Q, g, h) * w[h];
-      F[(c * n + g) * I + i] = s;
     }
   }
 
@@ -230,7 +330,7 @@ struct SF {
   // One thread owns one line (both cells, 2n points); the last-axis gradient
   // and flux of the line stay in its registers between stages.
   static constexpr int NLINE = ipow(QP, DIM - 1);          // lines per block
-  static constexpr int LPT = (PPB * NLINE + NT - 1) / NT;  // lines per thread
+  static constexpr int LPT = (TM::SPAN * NLINE + TM::TPP - 1) / TM::TPP;  // lines per thread
 
   // forward interpolation along the last axis + collocation derivative:
   // writes V (point values), keeps the last-axis gradient in gz
@@ -366,25 +466,25 @@ struct SF {
     }
   }
 
-  // ---- collocation derivative along AX on [O][QP][I]
+  // ---- collocation derivative along AX on [O][QP][I], one line per item
   template <int AX>
   __device__ __forceinline__ static void der_item(const T* __restrict__ in, T* __restrict__ out, int item) {
     constexpr int I = ipow(QP, AX);
-    constexpr int OI = ipow(QP, DIM - 1 - AX) * I;    // items per cell
-    const int c = (NC == 2) ? (item >= OI) : 0;
-    const int pi = item - c * OI;
-    const int i = pi % I, o = pi / I;
-    const T* src = in + o * QP * I + c * n * I + i;
-    T* dst = out + o * QP * I + c * n * I + i;
-    T v[n];
+    const int i = item % I, o = item / I;
+    const T* src = in + o * QP * I + i;
+    T* dst = out + o * QP * I + i;
+    T v[QP];
 #pragma unroll
-    for (int h = 0; h < n; ++h) v[h] = src[h * I];
+    for (int h = 0; h < QP; ++h) v[h] = src[h * I];
 #pragma unroll
-    for (int g = 0; g < n; ++g) {
-      T s = T(0);
+    for (int c = 0; c < NC; ++c) {
 #pragma unroll
-      for (int h = 0; h < n; ++h) s += tabD<T>(Q, g, h) * v[h];
-      dst[g * I] = s;
+      for (int g = 0; g < n; ++g) {
+        T s = T(0);
+#pragma unroll
+        for (int h = 0; h < n; ++h) s += tabD<T>(Q, g, h) * v[c * n + h];
+        dst[(c * n + g) * I] = s;
+      }
     }
   }
 
@@ -392,121 +492,53 @@ struct SF {
   template <int AX, bool ACC>
   __device__ __forceinline__ static void dert_item(const T* __restrict__ in, T* __restrict__ out, int item) {
     constexpr int I = ipow(QP, AX);
-    constexpr int OI = ipow(QP, DIM - 1 - AX) * I;    // items per cell
-    const int c = (NC == 2) ? (item >= OI) : 0;
-    const int pi = item - c * OI;
-    const int i = pi % I, o = pi / I;
-    const T* src = in + o * QP * I + c * n * I + i;
-    T* dst = out + o * QP * I + c * n * I + i;
-    T v[n];
+    const int i = item % I, o = item / I;
+    const T* src = in + o * QP * I + i;
+    T* dst = out + o * QP * I + i;
+    T v[QP], a[QP];
 #pragma unroll
-    for (int g = 0; g < n; ++g) v[g] = src[g * I];
+    for (int g = 0; g < QP; ++g) v[g] = src[g * I];
+    if (ACC) {
 #pragma unroll
-    for (int h = 0; h < n; ++h) {
-      T s = ACC ? dst[h * I] : T(0);
+      for (int g = 0; g < QP; ++g) a[g] = dst[g * I];
+    }
 #pragma unroll
-      for (int g = 0; g < n; ++g) s += tabD<T>(Q, g, h) * v[g];
-      dst[h * I] = s;
+    for (int c = 0; c < NC; ++c) {
+#pragma unroll
+      for (int h = 0; h < n; ++h) {
+        T s = ACC ? a[c * n + h] : T(0);
+#pragma unroll
+        for (int g = 0; g < n; ++g) s += tabD<T>(Q, g, h) * v[c * n + g];
+        dst[(c * n + h) * I] = s;
+      }
     }
   }
 
   // ---- final backward integration along x: like bwd_item<0, false> but every
   // output value goes through put(pp, index, value) (the apply's epilogue)
   template <typename PUT>
-  __device__ __forceinline__ static void bwd0_item(const T* __restrict__ in, int item, int pp, const PUT& put) {
+  __device__ __forceinline__ static void bwd0_item(const T* __restrict__ in, int o, int pp, const PUT& put) {
     constexpr int Lout = (NC == 2) ? Mi : M;
-    constexpr int OI = ipow(Lout, DIM - 1);      // items per cell
-    const int c = (NC == 2) ? (item >= OI) : 0;
-    const int o = item - c * OI;
     const T* src = in + o * QP;
-    const int base = o * Lout;
-    T v[n];
+    T w[QP];
 #pragma unroll
-    for (int g = 0; g < n; ++g) v[g] = src[c * n + g];
-    if (NC == 1) {
-#pragma unroll
-      for (int a = 0; a <= Q; ++a) {
-        T s = T(0);
-#pragma unroll
-        for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, a) * v[g];
-        put(pp, base + a, s);
-      }
-    } else if (c == 0) {
-      T w[n];
-#pragma unroll
-      for (int g = 0; g < n; ++g) w[g] = src[n + g];
-#pragma unroll
-      for (int a = 1; a <= Q; ++a) {
-        T s = T(0);
-#pragma unroll
-        for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, a) * v[g];
-        if (a == Q) {
-#pragma unroll
-          for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, 0) * w[g];
-        }
-        put(pp, base + a - 1, s);
-      }
-    } else {
-#pragma unroll
-      for (int a = 1; a < Q; ++a) {
-        T s = T(0);
-#pragma unroll
-        for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, a) * v[g];
-        put(pp, base + Q + a - 1, s);
-      }
-    }
+    for (int g = 0; g < QP; ++g) w[g] = src[g];
+    integ_line<false>(w, LineEpi<PUT>{put, pp, o * Lout});
   }
 
-  // ---- backward integration along AX: [O][QP][I] -> [O][Lout][I]
+  // ---- backward integration along AX: [O][QP][I] -> [O][Lout][I], one line per item
   // NC = 2: interior nodes only (Lout = Mi); NC = 1: all nodes (Lout = M).
   // ACC: add into the output instead of writing.
   template <int AX, bool ACC>
   __device__ __forceinline__ static void bwd_item(const T* __restrict__ in, T* __restrict__ out, int item) {
     constexpr int I = ipow(QP, AX);
     constexpr int Lout = (NC == 2) ? Mi : M;
-    constexpr int OI = ipow(Lout, DIM - 1 - AX) * I;  // items per cell
-    const int c = (NC == 2) ? (item >= OI) : 0;
-    const int pi = item - c * OI;
-    const int i = pi % I, o = pi / I;
+    const int i = item % I, o = item / I;
     const T* src = in + o * QP * I + i;
-    T* dst = out + o * Lout * I + i;
-    T v[n];
+    T w[QP];
 #pragma unroll
-    for (int g = 0; g < n; ++g) v[g] = src[(c * n + g) * I];
-    if (NC == 1) {
-#pragma unroll
-      for (int a = 0; a <= Q; ++a) {
-        T s = ACC ? dst[a * I] : T(0);
-#pragma unroll
-        for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, a) * v[g];
-        dst[a * I] = s;
-      }
-    } else if (c == 0) {
-      // nodes 1..Q (node Q is shared with cell 1)
-      T w[n];
-#pragma unroll
-      for (int g = 0; g < n; ++g) w[g] = src[(n + g) * I];
-#pragma unroll
-      for (int a = 1; a <= Q; ++a) {
-        T s = ACC ? dst[(a - 1) * I] : T(0);
-#pragma unroll
-        for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, a) * v[g];
-        if (a == Q) {
-#pragma unroll
-          for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, 0) * w[g];
-        }
-        dst[(a - 1) * I] = s;
-      }
-    } else {
-      // nodes Q+1 .. 2Q-1
-#pragma unroll
-      for (int a = 1; a < Q; ++a) {
-        T s = ACC ? dst[(Q + a - 1) * I] : T(0);
-#pragma unroll
-        for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, a) * v[g];
-        dst[(Q + a - 1) * I] = s;
-      }
-    }
+    for (int g = 0; g < QP; ++g) w[g] = src[g * I];
+    integ_line<ACC>(w, LineStore<ACC>{out + o * Lout * I + i, I});
   }
 
   template <bool INTIN, typename GF, typename EPI>
@@ -521,92 +553,86 @@ struct SF {
     T gz[LPT][QP], fz[LPT][QP];
     if constexpr (DIM == 3) {
       constexpr int T1 = L * L * QP;
-      coop<NT, PPB, L * L * NC>([&](int pp, int it) { fwd_item<0, INTIN>(in + pp * sin, Rp(pp), it); });
-      __syncthreads();
-      coop<NT, PPB, L * QP * NC>([&](int pp, int it) { fwd_item<1, INTIN>(Rp(pp), Rp(pp) + T1, it); });
-      __syncthreads();
+      TM::template loop<L * L>([&](int pp, int it) { fwd_item<0, INTIN>(in + pp * sin, Rp(pp), it); });
+      TM::sync();
+      TM::template loop<L * QP>([&](int pp, int it) { fwd_item<1, INTIN>(Rp(pp), Rp(pp) + T1, it); });
+      TM::sync();
 #pragma unroll
       for (int l = 0; l < LPT; ++l) {
-        const int it = threadIdx.x + l * NT;
-        if (it < PPB * NLINE) {
-          const int pp = it / NLINE;
-          line_fwd<INTIN>(Rp(pp) + T1, Vp(pp), it - pp * NLINE, gz[l]);
+        int pp, line;
+        if (TM::template slot<NLINE>(l, pp, line)) {
+          line_fwd<INTIN>(Rp(pp) + T1, Vp(pp), line, gz[l]);
         }
       }
-      __syncthreads();
-      constexpr int ND = QP * QP * NC;
-      coop<NT, PPB, 2 * ND>([&](int pp, int it) {
+      TM::sync();
+      constexpr int ND = QP * QP;           // lines per direction
+      TM::template loop<2 * ND>([&](int pp, int it) {
         const int ax = it / ND, r = it - ax * ND;
         if (ax == 0) der_item<0>(Vp(pp), Rp(pp), r);
         else der_item<1>(Vp(pp), Rp(pp) + NQ, r);
       });
-      __syncthreads();
+      TM::sync();
 #pragma unroll
       for (int l = 0; l < LPT; ++l) {
-        const int it = threadIdx.x + l * NT;
-        if (it < PPB * NLINE) {
-          const int pp = it / NLINE;
-          line_quad(Rp(pp), it - pp * NLINE, gz[l], fz[l], gcell, pp);
+        int pp, line;
+        if (TM::template slot<NLINE>(l, pp, line)) {
+          line_quad(Rp(pp), line, gz[l], fz[l], gcell, pp);
         }
       }
-      __syncthreads();
-      coop<NT, PPB, ND>([&](int pp, int it) { dert_item<0, false>(Rp(pp), Vp(pp), it); });
-      __syncthreads();
-      coop<NT, PPB, ND>([&](int pp, int it) { dert_item<1, true>(Rp(pp) + NQ, Vp(pp), it); });
-      __syncthreads();
+      TM::sync();
+      TM::template loop<ND>([&](int pp, int it) { dert_item<0, false>(Rp(pp), Vp(pp), it); });
+      TM::sync();
+      TM::template loop<ND>([&](int pp, int it) { dert_item<1, true>(Rp(pp) + NQ, Vp(pp), it); });
+      TM::sync();
       constexpr int B1 = Lo * Lo * QP;       // [Lo][Lo][QP]
       static_assert(B1 + Lo * QP * QP <= Dims<DIM, NC, Q>::R_LINE, "backward temporaries exceed R");
 #pragma unroll
       for (int l = 0; l < LPT; ++l) {
-        const int it = threadIdx.x + l * NT;
-        if (it < PPB * NLINE) {
-          const int pp = it / NLINE;
-          line_bwd(fz[l], Vp(pp), Rp(pp) + B1, it - pp * NLINE);
+        int pp, line;
+        if (TM::template slot<NLINE>(l, pp, line)) {
+          line_bwd(fz[l], Vp(pp), Rp(pp) + B1, line);
         }
       }
-      __syncthreads();
-      coop<NT, PPB, Lo * QP * NC>([&](int pp, int it) { bwd_item<1, false>(Rp(pp) + B1, Rp(pp), it); });
-      __syncthreads();
-      coop<NT, PPB, Lo * Lo * NC>([&](int pp, int it) { bwd0_item(Rp(pp), it, pp, epi); });
-      __syncthreads();
+      TM::sync();
+      TM::template loop<Lo * QP>([&](int pp, int it) { bwd_item<1, false>(Rp(pp) + B1, Rp(pp), it); });
+      TM::sync();
+      TM::template loop<Lo * Lo>([&](int pp, int it) { bwd0_item(Rp(pp), it, pp, epi); });
+      TM::sync();
     } else {
-      coop<NT, PPB, L * NC>([&](int pp, int it) { fwd_item<0, INTIN>(in + pp * sin, Rp(pp), it); });
-      __syncthreads();
+      TM::template loop<L>([&](int pp, int it) { fwd_item<0, INTIN>(in + pp * sin, Rp(pp), it); });
+      TM::sync();
 #pragma unroll
       for (int l = 0; l < LPT; ++l) {
-        const int it = threadIdx.x + l * NT;
-        if (it < PPB * NLINE) {
-          const int pp = it / NLINE;
-          line_fwd<INTIN>(Rp(pp), Vp(pp), it - pp * NLINE, gz[l]);
+        int pp, line;
+        if (TM::template slot<NLINE>(l, pp, line)) {
+          line_fwd<INTIN>(Rp(pp), Vp(pp), line, gz[l]);
         }
       }
-      __syncthreads();
-      constexpr int ND = QP * NC;
-      coop<NT, PPB, ND>([&](int pp, int it) { der_item<0>(Vp(pp), Rp(pp), it); });
-      __syncthreads();
+      TM::sync();
+      constexpr int ND = QP;                // lines per direction
+      TM::template loop<ND>([&](int pp, int it) { der_item<0>(Vp(pp), Rp(pp), it); });
+      TM::sync();
 #pragma unroll
       for (int l = 0; l < LPT; ++l) {
-        const int it = threadIdx.x + l * NT;
-        if (it < PPB * NLINE) {
-          const int pp = it / NLINE;
-          line_quad(Rp(pp), it - pp * NLINE, gz[l], fz[l], gcell, pp);
+        int pp, line;
+        if (TM::template slot<NLINE>(l, pp, line)) {
+          line_quad(Rp(pp), line, gz[l], fz[l], gcell, pp);
         }
       }
-      __syncthreads();
-      coop<NT, PPB, ND>([&](int pp, int it) { dert_item<0, false>(Rp(pp), Vp(pp), it); });
-      __syncthreads();
+      TM::sync();
+      TM::template loop<ND>([&](int pp, int it) { dert_item<0, false>(Rp(pp), Vp(pp), it); });
+      TM::sync();
       // R [Lo][QP] (F_0 is dead)
 #pragma unroll
       for (int l = 0; l < LPT; ++l) {
-        const int it = threadIdx.x + l * NT;
-        if (it < PPB * NLINE) {
-          const int pp = it / NLINE;
-          line_bwd(fz[l], Vp(pp), Rp(pp), it - pp * NLINE);
+        int pp, line;
+        if (TM::template slot<NLINE>(l, pp, line)) {
+          line_bwd(fz[l], Vp(pp), Rp(pp), line);
         }
       }
-      __syncthreads();
-      coop<NT, PPB, Lo * NC>([&](int pp, int it) { bwd0_item(Rp(pp), it, pp, epi); });
-      __syncthreads();
+      TM::sync();
+      TM::template loop<Lo>([&](int pp, int it) { bwd0_item(Rp(pp), it, pp, epi); });
+      TM::sync();
     }
   }
   // ---- batched stages: every thread takes U items per iteration and issues
@@ -614,23 +640,31 @@ struct SF {
   // items overlap (one item per thread and iteration leaves them serial).
   static constexpr int U = 2;
 
-  // quadrature-point products over all PPB * NQ points (stage design)
+  // quadrature-point products over all points of the served blocks (stage design)
   template <typename GF>
   __device__ __forceinline__ static void quad_stage(T* scr, int sscr, const GF& gcell) {
     constexpr int NGC = D::NGC;
     constexpr int NCOMP = D::NCOMP;
-    constexpr int TOT = PPB * NQ;
+    constexpr int TOT = TM::SPAN * NQ;
+    constexpr int STEP = TM::TPP;
 #pragma unroll 1
-    for (int base = threadIdx.x; base < TOT; base += U * NT) {
+    for (int base = TM::lane(); base < TOT; base += U * STEP) {
       T g[U][DIM], G[U][NCOMP];
       int off[U];
       bool ok[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int it0 = base + u * NT;
+        const int it0 = base + u * STEP;
         ok[u] = it0 < TOT;
         const int it = ok[u] ? it0 : base;
-        const int pp = it / NQ, pt = it - pp * NQ;
+        int pp, pt;
+        if constexpr (GROUPED) {
+          pp = TM::group();
+          pt = it;
+        } else {
+          pp = it / NQ;
+          pt = it - pp * NQ;
+        }
         int cslot = 0, lg = 0, rem = pt, mul = 1, cmul = 1;
 #pragma unroll
         for (int ax = 0; ax < DIM; ++ax) {
@@ -666,53 +700,66 @@ struct SF {
   }
 
   // collocation derivative (TRANS = false: out[g] = sum_h D[g][h] v[h]) or its
-  // transpose (TRANS = true: out[h] (+)= sum_g D[g][h] v[g]) on n-point cell
-  // segments; map(item, src, dst, stride) locates item's segments.
-  template <bool TRANS, bool ACC, int TOT, typename Map>
+  // transpose (TRANS = true: out[h] (+)= sum_g D[g][h] v[g]) on every cell of
+  // a line, ITEMS lines per block; map(pp, item, src, dst, stride) locates an
+  // item's line.
+  template <bool TRANS, bool ACC, int ITEMS, typename Map>
   __device__ __forceinline__ static void dseg_stage(const Map& map) {
+    constexpr int TOT = TM::SPAN * ITEMS;
+    constexpr int STEP = TM::TPP;
 #pragma unroll 1
-    for (int base = threadIdx.x; base < TOT; base += U * NT) {
-      T v[U][n], a[U][n];
+    for (int base = TM::lane(); base < TOT; base += U * STEP) {
+      T v[U][QP], a[U][QP];
       T* dst[U];
       int str[U];
       bool ok[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int it0 = base + u * NT;
+        const int it0 = base + u * STEP;
         ok[u] = it0 < TOT;
+        const int it = ok[u] ? it0 : base;
+        int pp, r;
+        if constexpr (GROUPED) {
+          pp = TM::group();
+          r = it;
+        } else {
+          pp = it / ITEMS;
+          r = it - pp * ITEMS;
+        }
         const T* src;
-        map(ok[u] ? it0 : base, src, dst[u], str[u]);
+        map(pp, r, src, dst[u], str[u]);
 #pragma unroll
-        for (int h = 0; h < n; ++h) v[u][h] = src[h * str[u]];
+        for (int h = 0; h < QP; ++h) v[u][h] = src[h * str[u]];
         if (ACC) {
 #pragma unroll
-          for (int h = 0; h < n; ++h) a[u][h] = dst[u][h * str[u]];
+          for (int h = 0; h < QP; ++h) a[u][h] = dst[u][h * str[u]];
         }
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         if (!ok[u]) continue;
 #pragma unroll
-        for (int g = 0; g < n; ++g) {
-          T s = ACC ? a[u][g] : T(0);
+        for (int c = 0; c < NC; ++c) {
 #pragma unroll
-          for (int h = 0; h < n; ++h) s += (TRANS ? tabD<T>(Q, h, g) : tabD<T>(Q, g, h)) * v[u][h];
-          dst[u][g * str[u]] = s;
+          for (int g = 0; g < n; ++g) {
+            T s = ACC ? a[u][c * n + g] : T(0);
+#pragma unroll
+            for (int h = 0; h < n; ++h)
+              s += (TRANS ? tabD<T>(Q, h, g) : tabD<T>(Q, g, h)) * v[u][c * n + h];
+            dst[u][(c * n + g) * str[u]] = s;
+          }
         }
       }
     }
   }
 
-  // item -> segment of direction AX (I = QP^AX) of block pp in arrays
-  // [O][QP][I] starting at in / out
+  // line r of direction AX (I = QP^AX) of a block in arrays [O][QP][I]
+  // starting at in / out
   template <int AX>
   __device__ __forceinline__ static void seg(int r, const T* in, T* out, const T*& src, T*& dst, int& stride) {
     constexpr int I = ipow(QP, AX);
-    constexpr int OI = ipow(QP, DIM - 1 - AX) * I;
-    const int c = (NC == 2) ? (r >= OI) : 0;
-    const int pi = r - c * OI;
-    const int i = pi % I, o = pi / I;
-    const int offs = o * QP * I + c * n * I + i;
+    const int i = r % I, o = r / I;
+    const int offs = o * QP * I + i;
     src = in + offs;
     dst = out + offs;
     stride = I;
@@ -728,75 +775,70 @@ struct SF {
     auto Rp = [&](int pp) { return scr + pp * sscr + NQ; };
     if constexpr (DIM == 3) {
       constexpr int T1 = L * L * QP;
-      coop<NT, PPB, L * L * NC>([&](int pp, int it) { fwd_item<0, INTIN>(in + pp * sin, Rp(pp), it); });
-      __syncthreads();
-      coop<NT, PPB, L * QP * NC>([&](int pp, int it) { fwd_item<1, INTIN>(Rp(pp), Rp(pp) + T1, it); });
-      __syncthreads();
+      TM::template loop<L * L>([&](int pp, int it) { fwd_item<0, INTIN>(in + pp * sin, Rp(pp), it); });
+      TM::sync();
+      TM::template loop<L * QP>([&](int pp, int it) { fwd_item<1, INTIN>(Rp(pp), Rp(pp) + T1, it); });
+      TM::sync();
       // z: interpolate to the Gauss points and differentiate along z in registers;
       // T2 (R + T1) is read while F_2 (R + 2 NQ) is written: 2 NQ >= T1 + T2.
       static_assert(2 * NQ >= L * L * QP + L * QP * QP, "F_2 overlaps the z input");
-      coop<NT, PPB, QP * QP * NC>([&](int pp, int it) {
+      TM::template loop<QP * QP>([&](int pp, int it) {
         fwd_der_last_item<INTIN>(Rp(pp) + T1, Vp(pp), Rp(pp) + 2 * NQ, it);
       });
-      __syncthreads();
-      constexpr int ND = QP * QP * NC;
-      dseg_stage<false, false, PPB * 2 * ND>([&](int it, const T*& src, T*& dst, int& st) {
-        const int pp = it / (2 * ND), r2 = it - pp * (2 * ND);
+      TM::sync();
+      constexpr int ND = QP * QP;           // lines per direction
+      dseg_stage<false, false, 2 * ND>([&](int pp, int r2, const T*& src, T*& dst, int& st) {
         const int ax = r2 / ND, r = r2 - ax * ND;
         if (ax == 0) seg<0>(r, Vp(pp), Rp(pp), src, dst, st);
         else seg<1>(r, Vp(pp), Rp(pp) + NQ, src, dst, st);
       });
-      __syncthreads();
+      TM::sync();
       quad_stage(scr, sscr, gcell);
-      __syncthreads();
-      dseg_stage<true, false, PPB * ND>([&](int it, const T*& src, T*& dst, int& st) {
-        const int pp = it / ND;
+      TM::sync();
+      dseg_stage<true, false, ND>([&](int pp, int r, const T*& src, T*& dst, int& st) {
         const T* s0;
         T* d0;
-        seg<0>(it - pp * ND, Rp(pp), Vp(pp), s0, d0, st);
+        seg<0>(r, Rp(pp), Vp(pp), s0, d0, st);
         src = s0;
         dst = d0;
       });
-      __syncthreads();
-      dseg_stage<true, true, PPB * ND>([&](int it, const T*& src, T*& dst, int& st) {
-        const int pp = it / ND;
-        seg<1>(it - pp * ND, Rp(pp) + NQ, Vp(pp), src, dst, st);
+      TM::sync();
+      dseg_stage<true, true, ND>([&](int pp, int r, const T*& src, T*& dst, int& st) {
+        seg<1>(r, Rp(pp) + NQ, Vp(pp), src, dst, st);
       });
-      __syncthreads();
+      TM::sync();
       constexpr int B1 = Lo * Lo * QP;       // [Lo][Lo][QP]
       // z: D^T F_2 + V -> B^T along z -> R + B1 [Lo][QP][QP]; R + B1 does not
       // reach F_2 = R + 2 NQ because B1 + Lo QP^2 <= 2 NQ.
       static_assert(B1 + Lo * QP * QP <= 2 * NQ, "z output overlaps F_2");
-      coop<NT, PPB, QP * QP>([&](int pp, int it) { dert_bwd_last_item(Rp(pp) + 2 * NQ, Vp(pp), Rp(pp) + B1, it); });
-      __syncthreads();
-      coop<NT, PPB, Lo * QP * NC>([&](int pp, int it) { bwd_item<1, false>(Rp(pp) + B1, Rp(pp), it); });
-      __syncthreads();
-      coop<NT, PPB, Lo * Lo * NC>([&](int pp, int it) { bwd0_item(Rp(pp), it, pp, epi); });
-      __syncthreads();
+      TM::template loop<QP * QP>([&](int pp, int it) { dert_bwd_last_item(Rp(pp) + 2 * NQ, Vp(pp), Rp(pp) + B1, it); });
+      TM::sync();
+      TM::template loop<Lo * QP>([&](int pp, int it) { bwd_item<1, false>(Rp(pp) + B1, Rp(pp), it); });
+      TM::sync();
+      TM::template loop<Lo * Lo>([&](int pp, int it) { bwd0_item(Rp(pp), it, pp, epi); });
+      TM::sync();
     } else {
-      coop<NT, PPB, L * NC>([&](int pp, int it) { fwd_item<0, INTIN>(in + pp * sin, Rp(pp), it); });
-      __syncthreads();
+      TM::template loop<L>([&](int pp, int it) { fwd_item<0, INTIN>(in + pp * sin, Rp(pp), it); });
+      TM::sync();
       // y: R [L][QP] -> V [QP][QP] and F_1 = R + NQ (R holds L*QP <= NQ values)
-      coop<NT, PPB, QP * NC>([&](int pp, int it) { fwd_der_last_item<INTIN>(Rp(pp), Vp(pp), Rp(pp) + NQ, it); });
-      __syncthreads();
-      constexpr int ND = QP * NC;
-      dseg_stage<false, false, PPB * ND>([&](int it, const T*& src, T*& dst, int& st) {
-        const int pp = it / ND;
-        seg<0>(it - pp * ND, Vp(pp), Rp(pp), src, dst, st);
+      TM::template loop<QP>([&](int pp, int it) { fwd_der_last_item<INTIN>(Rp(pp), Vp(pp), Rp(pp) + NQ, it); });
+      TM::sync();
+      constexpr int ND = QP;                // lines per direction
+      dseg_stage<false, false, ND>([&](int pp, int r, const T*& src, T*& dst, int& st) {
+        seg<0>(r, Vp(pp), Rp(pp), src, dst, st);
       });
-      __syncthreads();
+      TM::sync();
       quad_stage(scr, sscr, gcell);
-      __syncthreads();
-      dseg_stage<true, false, PPB * ND>([&](int it, const T*& src, T*& dst, int& st) {
-        const int pp = it / ND;
-        seg<0>(it - pp * ND, Rp(pp), Vp(pp), src, dst, st);
+      TM::sync();
+      dseg_stage<true, false, ND>([&](int pp, int r, const T*& src, T*& dst, int& st) {
+        seg<0>(r, Rp(pp), Vp(pp), src, dst, st);
       });
-      __syncthreads();
+      TM::sync();
       // y: D^T F_1 + V -> B^T along y -> R [Lo][QP] (F_0 = R is dead)
-      coop<NT, PPB, QP>([&](int pp, int it) { dert_bwd_last_item(Rp(pp) + NQ, Vp(pp), Rp(pp), it); });
-      __syncthreads();
-      coop<NT, PPB, Lo * NC>([&](int pp, int it) { bwd0_item(Rp(pp), it, pp, epi); });
-      __syncthreads();
+      TM::template loop<QP>([&](int pp, int it) { dert_bwd_last_item(Rp(pp) + NQ, Vp(pp), Rp(pp), it); });
+      TM::sync();
+      TM::template loop<Lo>([&](int pp, int it) { bwd0_item(Rp(pp), it, pp, epi); });
+      TM::sync();
     }
   }
 

@@ -3,7 +3,8 @@ finest-level patch sweeps and one operator apply, nothing else.
 
     python -m paper_2510_17785_gb300.profile_sweep --N 16 --p 4 --precision mixed --sweeps 3
 
-Meant for ``ncu -k regex:k_patch ...`` on a case far smaller than the
+Meant for ``ncu --nvtx --nvtx-include "sweeps/" -k regex:k_patch ...`` (the sweeps
+run inside the NVTX range "sweeps", so set-up launches are not captured) on a case far smaller than the
 benchmark (a few hundred MB on the device), so that every replay pass of a
 full capture saves and restores little memory.
 """
@@ -24,6 +25,8 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--sweeps", type=int, default=3)
     ap.add_argument("--levels", type=int, default=0, help="h-levels (default: down to 2 cells per direction)")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="launch-shape variant without set-up timing (default: time them all and keep the fastest)")
     args = ap.parse_args()
     if args.levels <= 0:                  # halve while the cell count stays even and >= 2
         args.levels, n = 1, args.N
@@ -37,18 +40,23 @@ def main():
                         ("const", 1.0), "uniform", 77)
     prob = inputs.make_problem(w)
     prec = pmg.PREC_MIXED if args.precision == "mixed" else pmg.PREC_FP64
-    ctx = pmg.Context(0, precision=prec)
+    tune = dict(autotune=0, variant=args.variant) if args.variant >= 0 else {}
+    ctx = pmg.Context(0, precision=prec, **tune)
     ctx.mesh_structured(w.dim, w.N, w.p, args.levels, prob.coords, prob.kappa)
     ctx.setup()
     b = torch.tensor(prob.rhs, device="cuda")
     u = torch.zeros_like(b)
     lf = args.levels - 1
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("sweeps")       # ncu --nvtx --nvtx-include "sweeps/" selects these launches
     for _ in range(args.sweeps):
         ctx.patch_smooth(lf, b, u, 1, False)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     Au = torch.zeros_like(b)
     ctx.apply(lf, u, Au)
     torch.cuda.synchronize()
-    print(f"ok: {w.name} sweeps={args.sweeps} |u|_inf={float(u.abs().max()):.6e}")
+    print(f"ok: {w.name} sweeps={args.sweeps} tuning={ctx.tuning()} |u|_inf={float(u.abs().max()):.6e}")
     ctx.close()
 
 

@@ -318,19 +318,20 @@ def test_recomputing_bounds_reuses_scratch_and_is_reproducible():
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
-def test_launch_shape_variants_are_bit_identical(precision):
+@pytest.mark.parametrize("p", [4, 6])
+def test_launch_shape_variants_are_bit_identical(precision, p):
     """Every launch-shape variant of the sweep kernel computes the same bits
     (one owner thread per output, fixed summation order), so the set-up
     autotuner may pick any of them."""
     from paper_2510_17785_gb300 import pmg
     prec = pmg.PREC_MIXED if precision == "mixed" else pmg.PREC_FP64
-    w = wl(3, 6, 4)
+    w = wl(3, 6, p)
     prob = inputs.make_problem(w)
-    u0 = inputs.random_vector(31, 3, 4, 6)
+    u0 = inputs.random_vector(31, 3, p, 6)
     outs = []
     for v in range(8):
         ctx = pmg.Context(0, precision=prec, autotune=0, variant=v, **fixed())
-        ctx.mesh_structured(3, 6, 4, 2, prob.coords, prob.kappa)
+        ctx.mesh_structured(3, 6, p, 2, prob.coords, prob.kappa)
         try:
             ctx.setup()
         except pmg.PMGError as e:
