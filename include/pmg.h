@@ -191,6 +191,24 @@ int pmg_solve_cg(pmg_ctx* ctx, const double* b_dev, double* u_dev, double rtol, 
 int pmg_solve_gmres(pmg_ctx* ctx, const double* b_dev, double* u_dev, double rtol, int maxit,
                     int restart, int left, int* iters, double* relres, void* stream);
 
+/* Several independent problems solved together (no counterpart in the paper;
+ * the batched-solve layer of this library).  Each context is set up on its own
+ * mesh, degree and options (degrees and sizes may differ); problem k solves
+ * A_k u_k = b_k by the GMG-preconditioned CG of pmg_solve_cg, with the same
+ * stopping rule and the same iterates as a call of pmg_solve_cg on that context
+ * alone.  One host thread interleaves the problems: every iteration of every
+ * unfinished problem is launched (a captured CUDA graph on the context's own
+ * stream) before any is waited for, so the problems run concurrently on the
+ * GPU and small ones fill the SMs that large ones leave idle.
+ * ctxs[n_problems]: distinct contexts after pmg_setup, on the same device.
+ * b[k], u[k]: device vectors of context k (layout of pmg_solve_cg).
+ * iters, relres, status: host arrays of n_problems entries, or NULL; status[k]
+ * is problem k's code.  Returns PMG_OK if every problem converged, else the
+ * first failing problem's code (messages in each context's pmg_last_error).
+ * Synchronises; every problem's work is finished on return. */
+int pmg_batch_solve_cg(pmg_ctx* const* ctxs, int n_problems, const double* const* b, double* const* u,
+                       double rtol, int maxit, int* iters, double* relres, int* status);
+
 /* Same solve with host vectors: copies b in, solves, copies u out. */
 int pmg_solve_cg_host(pmg_ctx* ctx, const double* b_host, double* u_host, double rtol,
                       int maxit, int* iters, double* relres, void* stream);

@@ -1109,6 +1109,62 @@ static int cg_body(pmg_ctx* ctx, cudaStream_t s) {
   return PMG_OK;
 }
 
+// ---- CG in three steps, so that several contexts can interleave their
+// iterations (pmg_batch_solve_cg): start (x = 0, r = b, (r, r) copied to the
+// host), graph (capture of one iteration body, once per context), step (one
+// iteration launched; (r, r) copied to the host at its end).  All are
+// asynchronous on the context's stream.
+static int cg_start(pmg_ctx* ctx, const double* b) {
+  cudaStream_t s = ctx->stream;
+  HLevel& h = ctx->L.back();
+  const size_t n = h.nd;
+  const int M = ctx->p * h.N + 1;
+  CU(cudaMemsetAsync(ctx->cg_x, 0, n * sizeof(double), s));
+  CU(cudaMemsetAsync(ctx->cg_p, 0, n * sizeof(double), s));
+  CU(cudaMemcpyAsync(ctx->cg_r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  LK(1, mask_boundary<double>(ctx, ctx->cg_r, M, s));
+  {
+    static const double init[S_NSLOT] = {0.0, 1.0, 0.0, 0.0, 0.0, 0.0};
+    CU(cudaMemcpyAsync(ctx->scal, init, sizeof(init), cudaMemcpyHostToDevice, s));
+  }
+  LK(2, launch_dot(ctx->cg_r, ctx->cg_r, n, ctx->partial, ctx->scal, S_RR, 0, s));
+  CU(cudaMemcpyAsync(ctx->h_rr, ctx->scal + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s));
+  return PMG_OK;
+}
+
+static int cg_graph(pmg_ctx* ctx) {
+  if (ctx->graph_exec) return PMG_OK;
+  cudaStream_t s = ctx->stream;
+  cudaGraph_t g = nullptr;
+  const int64_t before = ctx->launches;
+  CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  int st = cg_body(ctx, s);
+  ctx->graph_launches_per_iter = ctx->launches - before;
+  ctx->launches = before;
+  cudaError_t ce = cudaStreamEndCapture(s, &g);
+  if (st || ce != cudaSuccess) {           // no graph: iterations launch the body directly
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    ctx->graph_exec = nullptr;
+  } else {
+    ctx->graph = g;
+    if (cudaGraphInstantiate(&ctx->graph_exec, g, 0) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->graph_exec = nullptr;
+    }
+  }
+  return PMG_OK;
+}
+
+static int cg_step(pmg_ctx* ctx) {
+  if (ctx->graph_exec) {
+    CU(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
+    ctx->launches += ctx->graph_launches_per_iter;
+    return PMG_OK;
+  }
+  return cg_body(ctx, ctx->stream);
+}
+
 int pmg_solve_cg(pmg_ctx* ctx, const double* b, double* u, double rtol, int maxit, int* iters, double* relres,
                  void* stream) {
   int st = check_level(ctx, ctx ? ctx->nlev - 1 : 0);
@@ -1119,17 +1175,8 @@ int pmg_solve_cg(pmg_ctx* ctx, const double* b, double* u, double rtol, int maxi
   CU(cudaStreamSynchronize(us));
   HLevel& h = ctx->L.back();
   const size_t n = h.nd;
-  const int M = ctx->p * h.N + 1;
-  CU(cudaMemsetAsync(ctx->cg_x, 0, n * sizeof(double), s));
-  CU(cudaMemsetAsync(ctx->cg_p, 0, n * sizeof(double), s));
-  CU(cudaMemcpyAsync(ctx->cg_r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  LK(1, mask_boundary<double>(ctx, ctx->cg_r, M, s));
-  {
-    const double init[S_NSLOT] = {0.0, 1.0, 0.0, 0.0, 0.0, 0.0};
-    CU(cudaMemcpyAsync(ctx->scal, init, sizeof(init), cudaMemcpyHostToDevice, s));
-  }
-  LK(2, launch_dot(ctx->cg_r, ctx->cg_r, n, ctx->partial, ctx->scal, S_RR, 0, s));
-  CU(cudaMemcpyAsync(ctx->h_rr, ctx->scal + S_RR, sizeof(double), cudaMemcpyDeviceToHost, s));
+  st = cg_start(ctx, b);
+  if (st) return st;
   CU(cudaStreamSynchronize(s));
   const double r0 = std::sqrt(*ctx->h_rr);
   int it = 0;
@@ -1138,36 +1185,12 @@ int pmg_solve_cg(pmg_ctx* ctx, const double* b, double* u, double rtol, int maxi
   if (!std::isfinite(r0)) result = fail(ctx, PMG_ERR_NUMERIC, "non-finite right-hand side");
   if (result == PMG_OK && r0 == 0.0) rel = 0.0;
   if (result == PMG_OK && r0 > 0.0) {
-    if (!ctx->graph_exec) {
-      // warm-up outside capture (sets kernel attributes), then capture
-      cudaGraph_t g = nullptr;
-      const int64_t before = ctx->launches;
-      CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      st = cg_body(ctx, s);
-      ctx->graph_launches_per_iter = ctx->launches - before;
-      ctx->launches = before;
-      cudaError_t ce = cudaStreamEndCapture(s, &g);
-      if (st || ce != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
-        cudaGetLastError();
-        ctx->graph_exec = nullptr;
-      } else {
-        ctx->graph = g;
-        if (cudaGraphInstantiate(&ctx->graph_exec, g, 0) != cudaSuccess) {
-          cudaGetLastError();
-          ctx->graph_exec = nullptr;
-        }
-      }
-    }
+    st = cg_graph(ctx);
+    if (st) return st;
     while (it < maxit) {
       ++it;
-      if (ctx->graph_exec) {
-        CU(cudaGraphLaunch(ctx->graph_exec, s));
-        ctx->launches += ctx->graph_launches_per_iter;
-      } else {
-        st = cg_body(ctx, s);
-        if (st) return st;
-      }
+      st = cg_step(ctx);
+      if (st) return st;
       CU(cudaStreamSynchronize(s));
       rel = std::sqrt(*ctx->h_rr) / r0;
       if (!std::isfinite(rel)) {
@@ -1182,6 +1205,79 @@ int pmg_solve_cg(pmg_ctx* ctx, const double* b, double* u, double rtol, int maxi
   CU(cudaStreamSynchronize(s));
   if (iters) *iters = it;
   if (relres) *relres = rel;
+  return result;
+}
+
+int pmg_batch_solve_cg(pmg_ctx* const* ctxs, int n_problems, const double* const* b, double* const* u, double rtol,
+                       int maxit, int* iters, double* relres, int* status) {
+  if (n_problems < 0 || (n_problems > 0 && (!ctxs || !b || !u)) || maxit < 0 || !(rtol >= 0)) return PMG_ERR_ARG;
+  const int K = n_problems;
+  for (int k = 0; k < K; ++k) {
+    if (!ctxs[k] || !b[k] || !u[k]) return PMG_ERR_ARG;
+    for (int j = 0; j < k; ++j)
+      if (ctxs[j] == ctxs[k]) return fail(ctxs[k], PMG_ERR_ARG, "a context appears twice in the batch");
+    const int st = check_level(ctxs[k], ctxs[k]->nlev - 1);
+    if (st) return st;
+  }
+  std::vector<double> r0(K, 0.0), rel(K, 1.0);
+  std::vector<int> it(K, 0), res(K, PMG_OK);
+  std::vector<char> active(K, 0);
+  for (int k = 0; k < K; ++k) {                      // every start in flight before the first wait
+    const int st = cg_start(ctxs[k], b[k]);
+    if (st) return st;
+  }
+  for (int k = 0; k < K; ++k) {
+    pmg_ctx* ctx = ctxs[k];
+    CU(cudaStreamSynchronize(ctx->stream));
+    r0[k] = std::sqrt(*ctx->h_rr);
+    if (!std::isfinite(r0[k])) res[k] = fail(ctx, PMG_ERR_NUMERIC, "non-finite right-hand side");
+    else if (r0[k] == 0.0) rel[k] = 0.0;
+    else if (maxit > 0) active[k] = 1;
+    if (active[k]) {
+      const int st = cg_graph(ctx);
+      if (st) return st;
+    }
+  }
+  for (;;) {
+    bool any = false;
+    for (int k = 0; k < K; ++k) {                    // one iteration of every unfinished problem
+      if (!active[k]) continue;
+      any = true;
+      ++it[k];
+      const int st = cg_step(ctxs[k]);
+      if (st) return st;
+    }
+    if (!any) break;
+    for (int k = 0; k < K; ++k) {
+      if (!active[k]) continue;
+      pmg_ctx* ctx = ctxs[k];
+      CU(cudaStreamSynchronize(ctx->stream));
+      rel[k] = std::sqrt(*ctx->h_rr) / r0[k];
+      if (!std::isfinite(rel[k])) {
+        res[k] = fail(ctx, PMG_ERR_NUMERIC, "non-finite residual");
+        active[k] = 0;
+      } else if (rel[k] <= rtol) {
+        active[k] = 0;
+      } else if (it[k] >= maxit) {
+        res[k] = fail(ctx, PMG_ERR_NOT_CONVERGED, "maxit reached");
+        active[k] = 0;
+      }
+    }
+  }
+  for (int k = 0; k < K; ++k) {
+    pmg_ctx* ctx = ctxs[k];
+    if (res[k] == PMG_OK && rel[k] > rtol) res[k] = fail(ctx, PMG_ERR_NOT_CONVERGED, "maxit reached");
+    CU(cudaMemcpyAsync(u[k], ctx->cg_x, ctx->L.back().nd * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  int result = PMG_OK;
+  for (int k = 0; k < K; ++k) {
+    pmg_ctx* ctx = ctxs[k];
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (iters) iters[k] = it[k];
+    if (relres) relres[k] = rel[k];
+    if (status) status[k] = res[k];
+    if (res[k] != PMG_OK && result == PMG_OK) result = res[k];
+  }
   return result;
 }
 

@@ -34,7 +34,7 @@ SYMBOLS = (
     "pmg_gmg_vcycle", "pmg_solve_cg", "pmg_solve_cg_host", "pmg_rhs_manufactured", "pmg_get_colours",
     "pmg_get_patch_map", "pmg_get_inv_diag", "pmg_sweep_flops", "pmg_launch_count", "pmg_fma_peak",
     "pmg_lanczos_bounds_noalloc", "pmg_tuning", "pmg_default_train_options", "pmg_features", "pmg_mlp_grad",
-    "pmg_mlp_train", "pmg_mlp_predict", "pmg_set_mlp", "pmg_solve_gmres",
+    "pmg_mlp_train", "pmg_mlp_predict", "pmg_set_mlp", "pmg_solve_gmres", "pmg_batch_solve_cg",
 )
 
 
@@ -110,6 +110,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pmg_mlp_predict": (i, [i, vp, vp, vp, i64, i, vp, vp]),
         "pmg_set_mlp": (i, [vp, vp, vp]),
         "pmg_solve_gmres": (i, [vp, vp, vp, d, i, i, i, P(i), P(d), vp]),
+        "pmg_batch_solve_cg": (i, [vp, i, vp, vp, d, i, P(i), P(d), P(i)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -140,6 +141,26 @@ def train_options(**kw) -> TrainOptions:
 def _check_rc(rc, what):
     if rc != PMG_OK:
         raise PMGError(rc, what)
+
+
+def batch_solve_cg(ctxs, bs, us, rtol=1e-8, maxit=200, check=True):
+    """pmg_batch_solve_cg over Contexts ctxs with device vectors bs[k], us[k];
+    returns (iterations, relres, status) lists."""
+    K = len(ctxs)
+    if len(bs) != K or len(us) != K:
+        raise ValueError("one right-hand side and one solution vector per context")
+    lib = load()
+    hs = (C.c_void_p * K)(*[c.h for c in ctxs])
+    bp = (C.c_void_p * K)(*[_ptr(b) for b in bs])
+    up = (C.c_void_p * K)(*[_ptr(u) for u in us])
+    it, rel, st = (C.c_int * K)(), (C.c_double * K)(), (C.c_int * K)()
+    rc = lib.pmg_batch_solve_cg(hs, K, bp, up, rtol, maxit, it, rel, st)
+    if check and rc != PMG_OK:
+        bad = [k for k in range(K) if st[k] != PMG_OK]
+        k = bad[0] if bad else 0
+        msg = lib.pmg_last_error(ctxs[k].h) if ctxs else b""
+        raise PMGError(rc, f"problem {k}: " + (msg.decode() if msg else ""))
+    return list(it), list(rel), list(st)
 
 
 def mlp_grad(params, norm, X, T, asym=4.0, device=0):

@@ -51,6 +51,11 @@ def test_argument_validation_without_device(lib):
     assert lib.pmg_destroy(None) == 1
     assert lib.pmg_setup(None) == 1
     assert lib.pmg_sweep_flops(None, 0) == 0.0
+    assert lib.pmg_batch_solve_cg(None, -1, None, None, 1e-8, 10, None, None, None) == 1   # negative count
+    assert lib.pmg_batch_solve_cg(None, 2, None, None, 1e-8, 10, None, None, None) == 1    # null arrays
+    assert lib.pmg_batch_solve_cg(None, 0, None, None, 1e-8, 10, None, None, None) == 0    # empty batch
+    nul = (C.c_void_p * 1)(None)
+    assert lib.pmg_batch_solve_cg(nul, 1, nul, nul, 1e-8, 10, None, None, None) == 1       # null context
 
 
 def test_binding_fails_loudly_without_library(tmp_path):
