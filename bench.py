@@ -40,6 +40,9 @@ def parse():
     ap.add_argument("--workload", default="c2_3d_q4_n32_perturbed")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison arm")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-interval arm")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="instead: K independent problems (3D, 8^3 cells, degrees 2/4/6/8) solved together")
     return ap.parse_args()
 
 
@@ -179,6 +182,125 @@ def aggregate(t_local_ms: float, n_free_local: int, dist: bool):
 
 
 # ------------------------------------------------------------------ ours
+def learned_arm(w, levels, local, timed_solves, dev):
+    """Mixed precision with MLP-predicted Chebyshev intervals: train on the
+    Lanczos estimates of three small problems of the same degree, then time
+    the interval computation (MLP vs Lanczos) and the solve on the workload."""
+    import numpy as np
+    import torch
+    from paper_2510_17785_gb300 import inputs, pmg
+
+    t0 = time.perf_counter()
+    Xs, Ts = [], []
+    train = [(8, 0.25, ("const", 1.0)), (8, 0.15, ("loguniform", -1.0, 1.0)), (6, 0.3, ("loguniform", -2.0, 2.0))]
+    for i, (N, pert, kap) in enumerate(train):
+        wt = inputs.Workload(f"train{i}", w.dim, N, w.p, pert, "uniform", kap, "uniform", 9000 + i)
+        pt_ = inputs.make_problem(wt)
+        lv, n = 1, N
+        while n % 2 == 0 and n // 2 >= 2:
+            lv, n = lv + 1, n // 2
+        c = pmg.Context(local, precision=pmg.PREC_MIXED)
+        c.mesh_structured(wt.dim, N, wt.p, lv, pt_.coords, pt_.kappa)
+        c.setup()
+        X, T = pmg.mlp_training_data(c)
+        Xs.append(X)
+        Ts.append(T)
+        c.close()
+    X, T = np.concatenate(Xs), np.concatenate(Ts)
+    norm = np.concatenate([X.mean(0), X.std(0) + 1e-6, T.mean(0), T.std(0) + 1e-6]).astype(np.float32)
+    f32 = lambda a: torch.tensor(np.asarray(a), dtype=torch.float32, device=dev)
+    params = f32(pmg.mlp_init(11))
+    hist = pmg.mlp_train(params, f32(norm), f32(X), f32(T), epochs=150, batch=256, lr=2e-3, asym=4.0)
+    t_train = time.perf_counter() - t0
+
+    prob = inputs.make_problem(w)
+    ctx = pmg.Context(local, precision=pmg.PREC_MIXED, bounds=pmg.BOUNDS_FIXED)
+    ctx.mesh_structured(w.dim, w.N, w.p, levels, prob.coords, prob.kappa)
+    ctx.setup()
+    b = torch.zeros((w.p * w.N + 1) ** w.dim, dtype=torch.float64, device=dev)
+    ctx.rhs_manufactured(b)
+    out = {}
+    ctx.compute_bounds(pmg.BOUNDS_LANCZOS)                    # warm-up of both sources
+    ctx.set_mlp(params.cpu().numpy(), norm)
+    ctx.compute_bounds(pmg.BOUNDS_MLP)
+    for src, key in ((pmg.BOUNDS_LANCZOS, "lanczos"), (pmg.BOUNDS_MLP, "mlp")):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        ctx.compute_bounds(src)
+        torch.cuda.synchronize()
+        out["bounds_" + key] = time.perf_counter() - t
+        if key == "lanczos":
+            x = torch.zeros_like(b)
+            out["its_lanczos"], _, _ = ctx.solve_cg(b, x, 1e-8, 200)
+    ms, its, _, _ = timed_solves(ctx, b, 3, 1)
+    ctx.close()
+    out.update(ms=ms, its=its, train_s=t_train, samples=int(X.shape[0]), train_problems=len(train),
+               loss=[float(hist[0]), float(hist[-1])])
+    return out
+
+
+def run_batch(args):
+    """K independent problems (unit cube, 8^3 cells, degrees 2, 4, 6, 8 in
+    turn, log-uniform coefficients) solved together by pmg_batch_solve_cg,
+    against the same problems solved one after another."""
+    import torch
+    from paper_2510_17785_gb300 import inputs, pmg
+
+    K, N = args.batch, 8
+    ctxs, bs, n_free = [], [], 0
+    t0 = time.perf_counter()
+    for k in range(K):
+        p = (2, 4, 6, 8)[k % 4]
+        wk = inputs.Workload(f"batch{k}", 3, N, p, 0.2, "sphere", ("loguniform", -2.0, 2.0), "uniform", 4004 * 64 + k)
+        pr = inputs.make_problem(wk)
+        c = pmg.Context(0, precision=pmg.PREC_MIXED)
+        c.mesh_structured(3, N, p, 3, pr.coords, pr.kappa)
+        c.setup()
+        ctxs.append(c)
+        bs.append(torch.tensor(pr.rhs, device="cuda"))
+        n_free += wk.n_free
+    t_setup = time.perf_counter() - t0
+    us = [torch.zeros_like(b) for b in bs]
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), r
+
+    def batch():
+        return pmg.batch_solve_cg(ctxs, bs, us, 1e-8, 200)
+
+    def one_by_one():
+        return [c.solve_cg(b, u, 1e-8, 200)[0] for c, b, u in zip(ctxs, bs, us)]
+
+    for _ in range(args.warmup):
+        batch()
+    tb, ts, its = [], [], None
+    for _ in range(args.steps):
+        t, (its, _, _) = timed(batch)
+        tb.append(t)
+        t, its1 = timed(one_by_one)
+        ts.append(t)
+        assert its1 == its
+    mb, msq = statistics.mean(tb), statistics.mean(ts)
+    print(json.dumps({
+        "metric": "batched GMG-PCG to 1e-8: free DoFs of all problems / time, independent problems of mixed degree",
+        "value": n_free / (mb * 1e-3), "unit": "DoFs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": mb, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 local/GMG + f64 CG", "data": "synthetic",
+        "config": {"workload": f"{K} problems, unit cube 8^3 cells, degrees 2/4/6/8, kappa 10^U(-2,2)",
+                   "n_free_total": n_free, "setup_s": t_setup},
+        "one_by_one_ms": msq, "speedup_vs_one_by_one": msq / mb, "cg_iterations": its,
+    }))
+    for c in ctxs:
+        c.close()
+
+
 def run_ours(args):
     import torch
     from paper_2510_17785_gb300 import inputs, pmg
@@ -287,6 +409,9 @@ def run_ours(args):
             result["fma64"] = ctx.fma_peak(pmg.PREC_FP64)
         ctx.close()
 
+    if not args.no_learned:
+        result["learned"] = learned_arm(w, levels, local, timed_solves, dev)
+
     head = result["mixed"]
     t_step = sum(head["ms"]) / len(head["ms"])
     t_max, value = aggregate(t_step, w.n_free, dist)
@@ -350,6 +475,19 @@ def run_ours(args):
             "speedup_mixed_vs_fp64": t64 / t_max,
             "max_abs_diff_mixed_vs_fp64_solution": None,
         }
+    if "learned" in result:
+        L = result["learned"]
+        tl = sum(L["ms"]) / len(L["ms"])
+        out["learned"] = {
+            "value": world * w.n_free / (tl * 1e-3), "ms_per_step": tl,
+            "cg_iterations": [i for i, _ in L["its"]], "final_relres": max(r for _, r in L["its"]),
+            "bounds_s_mlp": L["bounds_mlp"], "bounds_s_lanczos": L["bounds_lanczos"],
+            "iterations_with_lanczos_bounds": L["its_lanczos"],
+            "train": {"problems": L["train_problems"], "samples": L["samples"], "s": L["train_s"],
+                      "loss_first_last": L["loss"]},
+            "note": "mixed precision; Chebyshev intervals from the BF16 MLP (16-64-64-2) trained in this run on "
+                    "Lanczos estimates of three small problems of the same degree",
+        }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         its = int(statistics.median(i for i, _ in head["its"]))
         out["cpu_baseline"] = cpu_baseline(w, levels, its)
@@ -393,5 +531,7 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.batch > 0:
+        run_batch(a)
     else:
         run_ours(a)

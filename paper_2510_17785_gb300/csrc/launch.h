@@ -1,6 +1,7 @@
 // Host-side launchers of the device kernels, explicitly instantiated per
 // (dimension, precision) in kern_<d>d_<prec>.cu.
 #pragma once
+#include <string>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -10,7 +11,7 @@
 namespace pmg {
 
 // status codes (mirrors pmg.h)
-enum { ST_OK = 0, ST_ARG = 1, ST_CUDA = 2, ST_UNSUPPORTED = 7 };
+enum { ST_OK = 0, ST_ARG = 1, ST_CUDA = 2, ST_NOT_SPD = 5, ST_UNSUPPORTED = 7 };
 
 
 // one launch of the patch kernel over a.n_items patches (MODE_SWEEP or
@@ -64,6 +65,10 @@ int launch_cast_f2d(const float* x, double* y, size_t n, cudaStream_t s);
 int launch_dot(const double* x, const double* y, size_t n, double* partial, double* scal, int slot, int op,
                cudaStream_t s);
 int launch_axpy(double a, const double* x, double* y, size_t n, cudaStream_t s);
+// dense coarse solver set-up (coarse.cu)
+int launch_unit(double* x, size_t idx, cudaStream_t s);
+int launch_gather_coarse(const double* cols, const int* fidx, int nf, size_t nd, double* A, cudaStream_t s);
+int coarse_inverse(double* A, int n, cudaStream_t s, std::string* msg);
 int launch_scale(double a, const double* x, double* y, size_t n, cudaStream_t s);
 int launch_cg_update_p(const double* z, double* p, const double* scal, size_t n, cudaStream_t s);
 int launch_cg_update_xr(double* x, double* r, const double* p, const double* Ap, const double* scal, size_t n,

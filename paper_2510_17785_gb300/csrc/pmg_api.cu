@@ -155,7 +155,8 @@ int dalloc(pmg_ctx* ctx, T** p, size_t n) {
     if (s_ != PMG_OK) return s_;              \
   } while (0)
 
-// largest coarsest level for the dense FP64 inverse (2 GB, O(nf^3) host work)
+// largest coarsest level for the dense FP64 inverse (2 GB matrix; its assembly
+// holds nf columns of the coarsest vector, about 2 GB more, during set-up)
 constexpr int kMaxCoarseDofs = 16384;
 
 size_t ipow_sz(size_t b, int e) {
@@ -356,43 +357,6 @@ int precondition(pmg_ctx* ctx, const double* r, double* z, cudaStream_t s) {
     CU(cudaMemcpyAsync(z, h.x64, h.nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
   }
   return PMG_OK;
-}
-
-// ---- host dense Cholesky and inverse of the coarse matrix -------------------
-bool cholesky_inverse(std::vector<double>& A, int n) {
-  // A (n x n, row-major, SPD) -> lower factor L in place
-  for (int j = 0; j < n; ++j) {
-    double d = A[(size_t)j * n + j];
-    for (int k = 0; k < j; ++k) d -= A[(size_t)j * n + k] * A[(size_t)j * n + k];
-    if (!(d > 0.0)) return false;
-    d = std::sqrt(d);
-    A[(size_t)j * n + j] = d;
-#pragma omp parallel for schedule(static)
-    for (int i = j + 1; i < n; ++i) {
-      double s = A[(size_t)i * n + j];
-      for (int k = 0; k < j; ++k) s -= A[(size_t)i * n + k] * A[(size_t)j * n + k];
-      A[(size_t)i * n + j] = s / d;
-    }
-  }
-  // inverse: solve L L^T X = I column by column
-  std::vector<double> X((size_t)n * n, 0.0);
-#pragma omp parallel for schedule(dynamic)
-  for (int c = 0; c < n; ++c) {
-    std::vector<double> y(n, 0.0);
-    for (int i = 0; i < n; ++i) {
-      double s = (i == c) ? 1.0 : 0.0;
-      for (int k = 0; k < i; ++k) s -= A[(size_t)i * n + k] * y[k];
-      y[i] = s / A[(size_t)i * n + i];
-    }
-    for (int i = n - 1; i >= 0; --i) {
-      double s = y[i];
-      for (int k = i + 1; k < n; ++k) s -= A[(size_t)k * n + i] * y[k];
-      y[i] = s / A[(size_t)i * n + i];
-    }
-    for (int i = 0; i < n; ++i) X[(size_t)i * n + c] = y[i];
-  }
-  A.swap(X);
-  return true;
 }
 
 // Time every launch-shape variant of the patch-sweep kernel on colour 0 of
@@ -766,27 +730,33 @@ int pmg_setup(pmg_ctx* ctx) {
                   "the coarsest level has " + std::to_string(nf) + " free DoFs; the dense coarse solver takes at most " +
                       std::to_string(kMaxCoarseDofs) + ": use more h-levels");
     ctx->nf = nf;
-    std::vector<double> A((size_t)nf * nf, 0.0), col(h.nd);
-    for (int j = 0; j < nf; ++j) {
-      CU(cudaMemsetAsync(h.x64, 0, h.nd * sizeof(double), s));
-      const double one = 1.0;
-      CU(cudaMemcpyAsync(h.x64 + fidx[j], &one, sizeof(double), cudaMemcpyHostToDevice, s));
-      LK(1 + (1 << ctx->dim), cell_apply<double>(ctx, p, h.x64, h.r64, h.pl[0].G64, h.N, s));
-      CU(cudaMemcpyAsync(col.data(), h.r64, h.nd * sizeof(double), cudaMemcpyDeviceToHost, s));
-      CU(cudaStreamSynchronize(s));
-      for (int i = 0; i < nf; ++i) A[(size_t)i * nf + j] = col[fidx[i]];
-    }
-    // symmetrise the rounding
-    for (int i = 0; i < nf; ++i)
-      for (int j = 0; j < i; ++j) {
-        const double v = 0.5 * (A[(size_t)i * nf + j] + A[(size_t)j * nf + i]);
-        A[(size_t)i * nf + j] = A[(size_t)j * nf + i] = v;
-      }
-    if (!cholesky_inverse(A, nf)) return fail(ctx, PMG_ERR_NUMERIC, "coarse matrix is not positive definite");
-    DALLOC(ctx->Ainv, A.size());
+    DALLOC(ctx->Ainv, (size_t)nf * nf);
     DALLOC(ctx->freeidx, fidx.size());
-    CU(cudaMemcpy(ctx->Ainv, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice));
     CU(cudaMemcpy(ctx->freeidx, fidx.data(), fidx.size() * sizeof(int), cudaMemcpyHostToDevice));
+    // all columns of the operator at once (nf unit vectors), then the free rows
+    double* cols = nullptr;
+    CU(cudaMalloc(&cols, (size_t)nf * h.nd * sizeof(double)));
+    int st = PMG_OK;
+    for (int j = 0; j < nf && st == PMG_OK; ++j) {
+      if (cudaMemsetAsync(h.x64, 0, h.nd * sizeof(double), s) != cudaSuccess ||
+          launch_unit(h.x64, (size_t)fidx[j], s) != ST_OK) {
+        st = fail(ctx, PMG_ERR_CUDA, "coarse matrix assembly failed");
+        break;
+      }
+      ctx->launches += 1;
+      if (cell_apply<double>(ctx, p, h.x64, cols + (size_t)j * h.nd, h.pl[0].G64, h.N, s) != ST_OK)
+        st = fail(ctx, PMG_ERR_CUDA, "coarse matrix assembly failed");
+      ctx->launches += 1 + (1 << ctx->dim);
+    }
+    if (st == PMG_OK && launch_gather_coarse(cols, ctx->freeidx, nf, h.nd, ctx->Ainv, s) != ST_OK)
+      st = fail(ctx, PMG_ERR_CUDA, "coarse matrix gather failed");
+    if (st == PMG_OK && cudaStreamSynchronize(s) != cudaSuccess) st = fail(ctx, PMG_ERR_CUDA, "coarse matrix assembly failed");
+    cudaFree(cols);
+    if (st) return st;
+    std::string msg;
+    const int ci = coarse_inverse(ctx->Ainv, nf, s, &msg);
+    if (ci == ST_NOT_SPD) return fail(ctx, PMG_ERR_NUMERIC, msg);
+    if (ci != ST_OK) return fail(ctx, PMG_ERR_CUDA, msg);
   }
   // ---- CG vectors
   {

@@ -163,6 +163,40 @@ def batch_solve_cg(ctxs, bs, us, rtol=1e-8, maxit=200, check=True):
     return list(it), list(rel), list(st)
 
 
+def mlp_init(seed: int = 0) -> np.ndarray:
+    """Initial MLP parameters in the library's layout (W1 [64][16], b1 [64],
+    W2 [64][64], b2 [64], W3 [2][64], b3 [2], row-major, concatenated):
+    weights uniform in +-sqrt(6 / fan_in), biases zero; FP32."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for rows, cols in ((64, 16), (64, 64), (2, 64)):
+        lim = np.sqrt(6.0 / cols)
+        parts.append(rng.uniform(-lim, lim, size=rows * cols))
+        parts.append(np.zeros(rows))
+    theta = np.concatenate(parts).astype(np.float32)
+    assert theta.size == MLP_NPARAM
+    return theta
+
+
+def mlp_training_data(ctx, dtype=None):
+    """(features [n, 16], targets [n, 2] = (log theta_max, log theta_min)) of every
+    patch, mesh level and p-level q > 1 of a set-up context with Lanczos
+    intervals: the training set of the interval network."""
+    import torch
+    Xs, Ts = [], []
+    for lv in range(ctx.n_levels):
+        npatch, _ = ctx.num_patches(lv)
+        ritz = ctx.get_ritz(lv)
+        for k, q in enumerate(ctx.p_levels()):
+            if q == 1:
+                continue
+            X = torch.zeros((npatch, 16), dtype=torch.float32, device="cuda")
+            ctx.features(lv, k, X)
+            Xs.append(X.cpu().numpy())
+            Ts.append(np.log(ritz[:, k, ::-1]))
+    return np.concatenate(Xs), np.ascontiguousarray(np.concatenate(Ts))
+
+
 def mlp_grad(params, norm, X, T, asym=4.0, device=0):
     """(loss, grad) of the loss on all samples; float32 CUDA tensors."""
     import torch
