@@ -28,6 +28,9 @@ sys.path.insert(0, ROOT)
 
 FP32_PEAK_DERIVED = 152 * 128 * 2 * 2.070e9      # SMs x FP32 lanes x 2 flops x max SM clock
 FP64_PEAK_NOMINAL = 1.25e12                      # GB300 FP64 rate (nominal)
+# DRAM bytes (read + write) of one finest-level colour launch of the FP32 patch kernel on the 3D Q4 32^3
+# workload (colour 0, 3,375 patches), from one ncu capture of the current kernel
+PATCH_LAUNCH_TRAFFIC = 112.328448e6 + 36.908288e6
 METRIC = "patch-smoother DoFs/s and CG time-to-1e-8 residual: mixed/learned vs plain FP64, 1 GB300"
 
 
@@ -449,7 +452,9 @@ def run_ours(args):
         "roofline": {
             "bound": "alu", "achieved": achieved / 1e12,
             "peak": FP32_PEAK_DERIVED / 1e12, "unit": "TFLOP/s",
-            "frac": achieved / FP32_PEAK_DERIVED, "traffic": None,
+            "frac": achieved / FP32_PEAK_DERIVED,
+            "traffic": PATCH_LAUNCH_TRAFFIC if w.name == "c2_3d_q4_n32_perturbed" else None,
+            "traffic_note": "DRAM bytes of one colour launch (colour 0, 3,375 patches) from an ncu capture",
             "kernel": "k_patch<3,4,float,SWEEP,variant> (finest-level patch sweep, 8 colour launches)",
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
             "measured_fma_peak": result["fma32"] / 1e12,
