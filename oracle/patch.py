@@ -83,6 +83,7 @@ class PatchLevel:
     A_ic: np.ndarray        # interior x closure
     A: np.ndarray           # interior x interior
     diag: np.ndarray
+    dim: int = 0
 
 
 class Patch:
@@ -113,7 +114,7 @@ class Patch:
         ii = [pos[n] for n in interior]
         A_ic = Acl[ii, :]
         A = A_ic[:, ii]
-        return PatchLevel(q, np.array(closure), np.array(interior), A_ic, A, np.diag(A).copy())
+        return PatchLevel(q, np.array(closure), np.array(interior), A_ic, A, np.diag(A).copy(), m.dim)
 
     def _prolongation(self, qc: int, qf: int) -> np.ndarray:
         """Embedding V_{j,qc} -> V_{j,qf} on interior DoFs: entry (k, i) is the
@@ -147,9 +148,9 @@ class Patch:
 
 @dataclasses.dataclass
 class Smoother:
-    kind: str = "chebyshev"      # or "jacobi"
+    kind: str = "chebyshev"      # "chebyshev", "jacobi" or "fdm" (Cartesian-reinforced)
     degree: int = 3              # Chebyshev degree
-    omega: float = 0.5           # Jacobi damping
+    omega: float = 0.5           # damping of the Jacobi and Cartesian-reinforced steps
     steps: int = 1               # smoothing steps (pre and post each)
 
 
@@ -180,9 +181,40 @@ def chebyshev(A, diag, r, d, lo, hi, degree, zero_start=False):
     return d
 
 
+_REFERENCE = {}
+
+
+def reference_patch_matrix(dim: int, q: int) -> np.ndarray:
+    """A_{b,q}: the interior matrix of the undeformed Cartesian patch (2^d
+    square/cube cells, kappa = 1) at degree q (Section 3.1, Cartesian-reinforced
+    smoother), assembled like any patch matrix."""
+    key = (dim, q)
+    if key not in _REFERENCE:
+        g = np.linspace(0.0, 1.0, 3)
+        axes = np.meshgrid(*([g] * dim), indexing="ij")
+        X = np.stack([a.T.reshape(-1) for a in axes], axis=1)    # x fastest
+        m = fem.StructuredMesh(dim, 2, X, np.ones(2 ** dim))
+        _REFERENCE[key] = Patch(m, (1,) * dim, [q]).lv[q].A
+    return _REFERENCE[key]
+
+
+def cartesian_reinforced(lv: PatchLevel, r, d, omega, steps):
+    """Damped Richardson steps d <- d + omega P^-1 (r - A d) with the
+    Cartesian-reinforced preconditioner of Section 3.1: the reference patch
+    inverse A_b^-1, rescaled by diag(A_b) and the inverse diagonal of the
+    actual patch matrix, P^-1 = diag(A_j)^-1 diag(A_b) A_b^-1."""
+    Ab = reference_patch_matrix(lv.dim, lv.q)
+    scale = np.diag(Ab) / lv.diag
+    for _ in range(steps):
+        d = d + omega * scale * np.linalg.solve(Ab, r - lv.A @ d)
+    return d
+
+
 def smooth(lv: PatchLevel, r, d, sm: Smoother, bounds, zero_start):
     if sm.kind == "jacobi":
         return jacobi(lv.A, lv.diag, r, d, sm.omega, sm.steps)
+    if sm.kind == "fdm":
+        return cartesian_reinforced(lv, r, d, sm.omega, sm.steps)
     lo, hi = bounds
     for s in range(sm.steps):
         d = chebyshev(lv.A, lv.diag, r, d, lo, hi, sm.degree, zero_start and s == 0)
