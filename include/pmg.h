@@ -47,7 +47,7 @@ enum {
 };
 
 /* ---- options ----------------------------------------------------------- */
-enum { PMG_SMOOTHER_CHEBYSHEV = 0, PMG_SMOOTHER_JACOBI = 1 };
+enum { PMG_SMOOTHER_CHEBYSHEV = 0, PMG_SMOOTHER_JACOBI = 1, PMG_SMOOTHER_CARTESIAN = 2 };
 enum { PMG_BOUNDS_LANCZOS = 0, PMG_BOUNDS_FIXED = 1, PMG_BOUNDS_USER = 2,
        PMG_BOUNDS_MLP = 3   /* learned intervals (pmg_set_mlp), see below      */ };
 enum { PMG_PREC_FP64 = 0,  /* everything in FP64                               */
@@ -56,9 +56,15 @@ enum { PMG_PREC_FP64 = 0,  /* everything in FP64                               *
                               solve in FP64                                   */ };
 
 typedef struct pmg_options {
-  int smoother;          /* PMG_SMOOTHER_*: smoother on every local p-level    */
+  int smoother;          /* PMG_SMOOTHER_*: smoother on every local p-level:
+                            Chebyshev iteration on D^-1 A; damped Jacobi
+                            d += omega D^-1 (r - A d); Cartesian-reinforced
+                            d += omega D^-1 diag(A_b) A_b^-1 (r - A d), A_b the
+                            reference Cartesian patch operator inverted by fast
+                            diagonalisation (Section 3.1)                    */
   int cheb_degree;       /* Chebyshev polynomial degree (k), >= 1              */
-  double jacobi_omega;   /* damping of the Jacobi smoother (paper: 1/2)        */
+  double jacobi_omega;   /* damping omega of the Jacobi and Cartesian-reinforced
+                            steps (paper: 1/2)                                 */
   int n_mg;              /* local V-cycles per patch solve (N_MG, >= 1)        */
   int bounds;            /* PMG_BOUNDS_*: source of the Chebyshev intervals    */
   int lanczos_steps;     /* Lanczos steps per (patch, p-level)                 */

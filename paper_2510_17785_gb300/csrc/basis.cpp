@@ -201,4 +201,118 @@ int upload_all_tables(const Tables<double>& t64, const Tables<float>& t32, const
   return 0;
 }
 
+
+
+// ---- fast diagonalisation of the reference Cartesian patch ------------------
+// 1D stiffness K and mass M of the degree-q basis on two unit cells, restricted
+// to the 2q-1 interior nodes (Gauss rule with q+1 points per cell, exact for
+// these polynomial products).  The generalised eigenproblem K s = lambda M s is
+// reduced with the Cholesky factor of M (M = L L^T, C = L^-1 K L^-T) and C is
+// diagonalised by cyclic Jacobi rotations; S = L^-T Q then satisfies
+// S^T M S = I and S^T K S = diag(lambda), so the d-dimensional reference
+// operator K(x)M(x)M + M(x)K(x)M + M(x)M(x)K has the inverse
+// (S(x)S(x)S) diag(1 / (lambda_i + lambda_j + lambda_k)) (S(x)S(x)S)^T.
+std::vector<double> fdm_table(int q) {
+  const int n = q + 1, mi = 2 * q - 1;
+  std::vector<double> gx, gw;
+  gauss_rule(n, gx, gw);
+  const std::vector<double> gl = gauss_lobatto(q);
+  const auto B = lagrange_matrix(gl, gx);     // [g][a]
+  const auto Dg = diff_matrix(gx);            // [g][h]
+  std::vector<std::vector<double>> Bd(n, std::vector<double>(n, 0.0));
+  for (int g = 0; g < n; ++g)
+    for (int a = 0; a < n; ++a)
+      for (int h = 0; h < n; ++h) Bd[g][a] += Dg[g][h] * B[h][a];
+  std::vector<double> K((size_t)mi * mi, 0.0), M((size_t)mi * mi, 0.0);
+  for (int c = 0; c < 2; ++c)
+    for (int a = 0; a <= q; ++a)
+      for (int b = 0; b <= q; ++b) {
+        const int i = c * q + a - 1, j = c * q + b - 1;        // interior index, -1 / mi: boundary
+        if (i < 0 || j < 0 || i >= mi || j >= mi) continue;
+        double k = 0.0, m = 0.0;
+        for (int g = 0; g < n; ++g) {
+          k += gw[g] * Bd[g][a] * Bd[g][b];
+          m += gw[g] * B[g][a] * B[g][b];
+        }
+        K[(size_t)i * mi + j] += k;
+        M[(size_t)i * mi + j] += m;
+      }
+  // M = L L^T
+  std::vector<double> L((size_t)mi * mi, 0.0);
+  for (int j = 0; j < mi; ++j) {
+    double d = M[(size_t)j * mi + j];
+    for (int k = 0; k < j; ++k) d -= L[(size_t)j * mi + k] * L[(size_t)j * mi + k];
+    d = std::sqrt(d);
+    L[(size_t)j * mi + j] = d;
+    for (int i = j + 1; i < mi; ++i) {
+      double v = M[(size_t)i * mi + j];
+      for (int k = 0; k < j; ++k) v -= L[(size_t)i * mi + k] * L[(size_t)j * mi + k];
+      L[(size_t)i * mi + j] = v / d;
+    }
+  }
+  // Li = L^-1 (lower triangular)
+  std::vector<double> Li((size_t)mi * mi, 0.0);
+  for (int c = 0; c < mi; ++c)
+    for (int i = 0; i < mi; ++i) {
+      double v = (i == c) ? 1.0 : 0.0;
+      for (int k = 0; k < i; ++k) v -= L[(size_t)i * mi + k] * Li[(size_t)k * mi + c];
+      Li[(size_t)i * mi + c] = v / L[(size_t)i * mi + i];
+    }
+  // C = Li K Li^T
+  std::vector<double> T((size_t)mi * mi, 0.0), C((size_t)mi * mi, 0.0);
+  for (int i = 0; i < mi; ++i)
+    for (int j = 0; j < mi; ++j)
+      for (int k = 0; k < mi; ++k) T[(size_t)i * mi + j] += Li[(size_t)i * mi + k] * K[(size_t)k * mi + j];
+  for (int i = 0; i < mi; ++i)
+    for (int j = 0; j < mi; ++j)
+      for (int k = 0; k < mi; ++k) C[(size_t)i * mi + j] += T[(size_t)i * mi + k] * Li[(size_t)j * mi + k];
+  // cyclic Jacobi: C = Q diag Q^T
+  std::vector<double> Q((size_t)mi * mi, 0.0);
+  for (int i = 0; i < mi; ++i) Q[(size_t)i * mi + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < mi; ++i)
+      for (int j = i + 1; j < mi; ++j) off += C[(size_t)i * mi + j] * C[(size_t)i * mi + j];
+    if (off < 1e-30) break;
+    for (int p = 0; p < mi; ++p)
+      for (int r = p + 1; r < mi; ++r) {
+        const double apr = C[(size_t)p * mi + r];
+        if (std::fabs(apr) < 1e-300) continue;
+        const double app = C[(size_t)p * mi + p], arr = C[(size_t)r * mi + r];
+        const double tau = (arr - app) / (2.0 * apr);
+        const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+        const double cs = 1.0 / std::sqrt(1.0 + t * t), sn = t * cs;
+        for (int k = 0; k < mi; ++k) {            // C <- J^T C J
+          const double ckp = C[(size_t)k * mi + p], ckr = C[(size_t)k * mi + r];
+          C[(size_t)k * mi + p] = cs * ckp - sn * ckr;
+          C[(size_t)k * mi + r] = sn * ckp + cs * ckr;
+        }
+        for (int k = 0; k < mi; ++k) {
+          const double cpk = C[(size_t)p * mi + k], crk = C[(size_t)r * mi + k];
+          C[(size_t)p * mi + k] = cs * cpk - sn * crk;
+          C[(size_t)r * mi + k] = sn * cpk + cs * crk;
+        }
+        for (int k = 0; k < mi; ++k) {            // Q <- Q J
+          const double qkp = Q[(size_t)k * mi + p], qkr = Q[(size_t)k * mi + r];
+          Q[(size_t)k * mi + p] = cs * qkp - sn * qkr;
+          Q[(size_t)k * mi + r] = sn * qkp + cs * qkr;
+        }
+      }
+  }
+  // S = Li^T Q; output [S (row i: node, column k: mode)][lambda][diag K][diag M]
+  std::vector<double> out((size_t)mi * mi + 3 * mi, 0.0);
+  for (int i = 0; i < mi; ++i)
+    for (int k = 0; k < mi; ++k) {
+      double v = 0.0;
+      for (int j = 0; j < mi; ++j) v += Li[(size_t)j * mi + i] * Q[(size_t)j * mi + k];
+      out[(size_t)i * mi + k] = v;
+    }
+  for (int k = 0; k < mi; ++k) {
+    out[(size_t)mi * mi + k] = C[(size_t)k * mi + k];
+    out[(size_t)mi * mi + mi + k] = K[(size_t)k * mi + k];
+    out[(size_t)mi * mi + 2 * mi + k] = M[(size_t)k * mi + k];
+  }
+  return out;
+}
+
 }  // namespace pmg

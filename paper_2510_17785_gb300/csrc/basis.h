@@ -30,4 +30,10 @@ void h_prolongation_band(int q, int Nc, std::vector<double>& W, std::vector<int>
 // its transpose as a band of width 4q+1 (start may be negative)
 void h_restriction_band(int q, int Nc, std::vector<double>& W, std::vector<int>& start, int& width);
 
+// Fast-diagonalisation table of the reference Cartesian patch at degree q
+// (Section 3.1, Cartesian-reinforced smoother), mi = 2q - 1 interior nodes:
+// [S: mi x mi row-major, S^T M S = I, S^T K S = diag(lambda)][lambda: mi]
+// [diag K: mi][diag M: mi] for the 1D stiffness K and mass M on two unit cells.
+std::vector<double> fdm_table(int q);
+
 }  // namespace pmg

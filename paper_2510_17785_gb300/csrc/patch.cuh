@@ -30,6 +30,8 @@ struct LevelArgs {
   const T* dinv;       // 1 / diag(A_q) on the global degree-q grid, 0 on Dirichlet
   const T* bounds;     // [patches][2]: Chebyshev interval (lo, hi), q > 1
   const T* dense;      // small levels: [patches][Ni][Ni] row-major patch matrix A_{j,q}
+  const T* fdm;        // Cartesian-reinforced smoother: reference-patch fast-diagonalisation table of
+                       // degree q, [S: Mi x Mi][lambda: Mi][diag K: Mi][diag M: Mi], Mi = 2q - 1
 };
 
 // Levels whose patch operator is small enough to be applied as a dense
@@ -49,7 +51,7 @@ struct PatchArgs {
   const T* b;                  // MODE_SWEEP: right-hand side
   const T* r_in;               // MODE_LOCAL: [n_items][Ni]
   T* d_out;                    // MODE_LOCAL: [n_items][Ni]
-  int smoother;                // 0 Chebyshev, 1 Jacobi
+  int smoother;                // 0 Chebyshev, 1 Jacobi, 2 Cartesian-reinforced
   int cheb_degree;
   double omega;
   int n_mg;
@@ -118,7 +120,12 @@ struct Layout {
   static constexpr int SCRATCH = LINE ? Dims<DIM, 2, P>::SCRATCH_LINE : Dims<DIM, 2, P>::SCRATCH;
   static constexpr int COEF = SCR + SCRATCH;      // per level: 1/theta, c1[1..7], c2[1..7]
   static constexpr int NCOEF = 16;
-  static constexpr int PS_RAW = COEF + NL * NCOEF;
+  // fast-diagonalisation tables of the Cartesian-reinforced smoother, per level q > 1
+  __host__ __device__ static constexpr int mi(int k) { return 2 * q(k) - 1; }
+  __host__ __device__ static constexpr int fsz(int k) { return q(k) > 1 ? mi(k) * mi(k) + 3 * mi(k) : 0; }
+  __host__ __device__ static constexpr int foff(int k) { return k == 0 ? COEF + NL * NCOEF : foff(k - 1) + fsz(k - 1); }
+  __host__ __device__ static constexpr int FDM(int k) { return foff(k); }
+  static constexpr int PS_RAW = foff(NL);
   static constexpr int PS = (PS_RAW + 3) & ~3;    // per-patch stride in elements
 };
 
@@ -391,10 +398,127 @@ struct PatchKernel {
     }
   }
 
+  // ---- Cartesian-reinforced step (Section 3.1):
+  // d <- d + omega diag(A_j)^-1 diag(A_b) A_b^-1 (r - A_j d), with the reference
+  // Cartesian patch operator A_b = sum over axes of K (x) M (x) M (permuted)
+  // inverted by fast diagonalisation: with S^T M S = I and S^T K S = Lambda,
+  // A_b^-1 = (S (x) S (x) S) (Lambda_x + Lambda_y + Lambda_z)^-1 (S (x) S (x) S)^T.
+  // Stages: S^T along x, y; along z S^T, the eigenvalue scaling and S in one
+  // thread per line; S along y; S along x with the update of d.
+  template <int K, int AX, bool BACK>
+  __device__ static void fdm_line(const T* __restrict__ Sm, const T* __restrict__ in, T* __restrict__ out, int line) {
+    constexpr int Mi = L::mi(K);
+    constexpr int I = ipow(Mi, AX);
+    const int i0 = line % I, o = line / I;
+    const T* src = in + o * Mi * I + i0;
+    T* dst = out + o * Mi * I + i0;
+    T v[Mi];
+#pragma unroll
+    for (int i = 0; i < Mi; ++i) v[i] = src[i * I];
+#pragma unroll
+    for (int k = 0; k < Mi; ++k) {
+      T t = T(0);
+#pragma unroll
+      for (int i = 0; i < Mi; ++i) t += (BACK ? Sm[k * Mi + i] : Sm[i * Mi + k]) * v[i];
+      dst[k * I] = t;
+    }
+  }
+
+  template <int K>
+  __device__ void fdm_step(bool zero_start) {
+    constexpr int q = P >> K, Mi = L::mi(K), NI = L::ni(K);
+    constexpr int NLINE = NI / Mi;                     // lines along one axis
+    static_assert(2 * NI <= L::SCRATCH, "the fast-diagonalisation buffers exceed the scratch region");
+    int src = L::R_(K);
+    if (!zero_start) {                                 // res = r - A d
+      apply_int<K>(L::D_(K), epi<K>(EPI_RESID));
+      src = L::RES(K);
+    }
+    auto X = [&](int pp) { return vec(pp, L::SCR); };
+    auto Y = [&](int pp) { return vec(pp, L::SCR) + NI; };
+    auto Sm = [&](int pp) { return vec(pp, L::FDM(K)); };
+    auto lam = [&](int pp) { return vec(pp, L::FDM(K)) + Mi * Mi; };
+    TM::template loop<NLINE>([&](int pp, int l) { fdm_line<K, 0, false>(Sm(pp), vec(pp, src), X(pp), l); });
+    TM::sync();
+    if constexpr (DIM == 3) {
+      TM::template loop<NLINE>([&](int pp, int l) { fdm_line<K, 1, false>(Sm(pp), X(pp), Y(pp), l); });
+      TM::sync();
+    }
+    // last axis: forward, 1 / (lambda_x + lambda_y [+ lambda_z]), backward, in place
+    TM::template loop<NLINE>([&](int pp, int l) {
+      T* buf = (DIM == 3) ? Y(pp) : X(pp);
+      const T* S = Sm(pp);
+      const T* lm = lam(pp);
+      const T lsum = (DIM == 3) ? lm[l % Mi] + lm[l / Mi] : lm[l];
+      T v[Mi], w[Mi];
+#pragma unroll
+      for (int i = 0; i < Mi; ++i) v[i] = buf[i * NLINE + l];
+#pragma unroll
+      for (int k = 0; k < Mi; ++k) {
+        T t = T(0);
+#pragma unroll
+        for (int i = 0; i < Mi; ++i) t += S[i * Mi + k] * v[i];
+        w[k] = t / (lsum + lm[k]);
+      }
+#pragma unroll
+      for (int i = 0; i < Mi; ++i) {
+        T t = T(0);
+#pragma unroll
+        for (int k = 0; k < Mi; ++k) t += S[i * Mi + k] * w[k];
+        buf[i * NLINE + l] = t;
+      }
+    });
+    TM::sync();
+    if constexpr (DIM == 3) {
+      TM::template loop<NLINE>([&](int pp, int l) { fdm_line<K, 1, true>(Sm(pp), Y(pp), X(pp), l); });
+      TM::sync();
+    }
+    // x: S, then d (+)= omega dinv diag(A_b) z, diag(A_b) from the 1D diagonals
+    const T om = T(a->omega);
+    TM::template loop<NLINE>([&](int pp, int l) {
+      const T* S = Sm(pp);
+      const T* Kd = vec(pp, L::FDM(K)) + Mi * Mi + Mi;
+      const T* Md = Kd + Mi;
+      const T* in = X(pp) + l * Mi;
+      T v[Mi];
+#pragma unroll
+      for (int k = 0; k < Mi; ++k) v[k] = in[k];
+      int jy, jz;
+      if constexpr (DIM == 3) {
+        jy = l % Mi;
+        jz = l / Mi;
+      } else {
+        jy = l;
+        jz = 0;
+      }
+      T* d = vec(pp, L::D_(K)) + l * Mi;
+      const T* dv = vec(pp, L::DINV(K)) + l * Mi;
+#pragma unroll
+      for (int i = 0; i < Mi; ++i) {
+        T t = T(0);
+#pragma unroll
+        for (int k = 0; k < Mi; ++k) t += S[i * Mi + k] * v[k];
+        T dg;
+        if constexpr (DIM == 3)
+          dg = Kd[i] * Md[jy] * Md[jz] + Md[i] * Kd[jy] * Md[jz] + Md[i] * Md[jy] * Kd[jz];
+        else
+          dg = Kd[i] * Md[jy] + Md[i] * Kd[jy];
+        const T upd = om * dv[i] * dg * t;
+        d[i] = zero_start ? upd : d[i] + upd;
+      }
+    });
+    TM::sync();
+    (void)q;
+  }
+
   // ---- smoother on level K: d <- S(d; r), zero_start => d = 0 on entry
   template <int K>
   __device__ void smooth(bool zero_start) {
     constexpr int NI = L::ni(K);
+    if (a->smoother == 2) {
+      fdm_step<K>(zero_start);
+      return;
+    }
     if (a->smoother == 1) {   // damped Jacobi, d += omega D^-1 (r - A d)
       if (zero_start) {
         const T om = T(a->omega);
@@ -524,6 +648,11 @@ struct PatchKernel {
           const int pid = cells[pp * CST + NCELL];
           vec(pp, L::DENSE(K))[e] = act ? a->lv[K].dense[(size_t)pid * NI * NI + e] : T(0);
         });
+      }
+      // reference-patch fast-diagonalisation table (Cartesian-reinforced smoother)
+      if (a->smoother == 2) {
+        constexpr int FS = L::fsz(K);
+        TM::template loop<FS>([&](int pp, int e) { vec(pp, L::FDM(K))[e] = a->lv[K].fdm[e]; });
       }
       // Chebyshev coefficients (FP64 scalars, rounded to T)
       if (a->smoother == 0) {

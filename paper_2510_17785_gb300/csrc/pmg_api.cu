@@ -101,6 +101,8 @@ struct pmg_ctx {
   float* mlp_norm = nullptr;
   double* gm_V = nullptr;                // GMRES basis (restart + 1 vectors), grown on demand
   int gm_m = 0;
+  double* fdm64[PMG_MAXQ + 1] = {nullptr};   // Cartesian-reinforced tables per degree q (device)
+  float* fdm32[PMG_MAXQ + 1] = {nullptr};
   double* lanczos_V = nullptr;           // Lanczos basis scratch, grown on demand, reused
   size_t lanczos_V_n = 0;
   std::vector<void*> allocs;
@@ -207,12 +209,20 @@ template <>
 const float* Denseof<float>(const PLevel& pl) { return pl.dense32; }
 
 template <typename T>
+const T* Fdmof(const pmg_ctx* c, int q);
+template <>
+const double* Fdmof<double>(const pmg_ctx* c, int q) { return c->fdm64[q]; }
+template <>
+const float* Fdmof<float>(const pmg_ctx* c, int q) { return c->fdm32[q]; }
+
+template <typename T>
 PatchArgs<T> patch_args(pmg_ctx* c, int level) {
   PatchArgs<T> a;
   std::memset(&a, 0, sizeof(a));
   HLevel& h = c->L[level];
   a.N = h.N;
   for (int k = 0; k < c->npl; ++k) {
+    a.lv[k].fdm = Fdmof<T>(c, c->plevels[k]);
     a.lv[k].G = Gof<T>(h.pl[k]);
     a.lv[k].dinv = Dinvof<T>(h.pl[k]);
     a.lv[k].bounds = Boundsof<T>(h.pl[k]);
@@ -464,7 +474,7 @@ int pmg_create(int device, const pmg_options* opt, pmg_ctx** out) {
   else pmg_default_options(&ctx->opt);
   const pmg_options& o = ctx->opt;
   if (o.cheb_degree < 1 || o.cheb_degree > 8 || o.n_mg < 1 || o.lanczos_steps < 1 || o.lanczos_steps > 64 ||
-      (o.smoother != 0 && o.smoother != 1) || (o.precision != 0 && o.precision != 1) || o.bounds < 0 ||
+      (o.smoother < 0 || o.smoother > 2) || (o.precision != 0 && o.precision != 1) || o.bounds < 0 ||
       o.bounds > 3 || !(o.bound_safety > 0) || !(o.mlp_safety > 0) || o.coarse_kappa < 0 || o.coarse_kappa > 2 || !(o.bound_ratio >= 1) || o.variant < 0 ||
       o.variant >= NUM_VARIANTS) {
     delete ctx;
@@ -708,6 +718,17 @@ int pmg_setup(pmg_ctx* ctx) {
       nloc = std::max(nloc, ctx->L[l].npatch * ipow_sz(2 * p - 1, d));
     DALLOC(ctx->s32a, std::max(nfin, nloc));
     DALLOC(ctx->s32b, std::max(nfin, nloc));
+  }
+  // ---- Cartesian-reinforced smoother: reference-patch fast-diagonalisation tables
+  for (int k = 0; k < ctx->npl; ++k) {
+    const int q = ctx->plevels[k];
+    if (q < 2 || ctx->fdm64[q]) continue;
+    const std::vector<double> t = fdm_table(q);
+    const std::vector<float> t32(t.begin(), t.end());
+    DALLOC(ctx->fdm64[q], t.size());
+    DALLOC(ctx->fdm32[q], t.size());
+    CU(cudaMemcpy(ctx->fdm64[q], t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(ctx->fdm32[q], t32.data(), t32.size() * sizeof(float), cudaMemcpyHostToDevice));
   }
   // ---- coarse matrix by applying the coarsest operator to unit vectors
   {
@@ -1455,7 +1476,8 @@ double pmg_sweep_flops(const pmg_ctx* ctx, int level) {
   auto fcell = [d](int n) { return 8.0 * d * std::pow(n, d + 1) + (2.0 * d * d - d) * std::pow(n, d); };
   auto fpatch = [&](int q) { return (double)(1 << d) * fcell(q + 1); };
   const int k = ctx->opt.cheb_degree;
-  const bool jac = ctx->opt.smoother == PMG_SMOOTHER_JACOBI;
+  const bool jac = ctx->opt.smoother == PMG_SMOOTHER_JACOBI || ctx->opt.smoother == PMG_SMOOTHER_CARTESIAN;
+  const bool fdm = ctx->opt.smoother == PMG_SMOOTHER_CARTESIAN;
   double per = fpatch(ctx->p);   // Evaluate
   for (int cyc = 0; cyc < ctx->opt.n_mg; ++cyc) {
     for (int lv = 0; lv < ctx->npl; ++lv) {
@@ -1465,6 +1487,8 @@ double pmg_sweep_flops(const pmg_ctx* ctx, int level) {
       const int pre = jac ? (zero ? 0 : 1) : (zero ? k - 1 : k);
       const int post = jac ? 1 : k;
       per += (pre + 1 + post) * fpatch(q);
+      if (fdm)   // pre and post: 2d one-dimensional contractions of (2q-1)^(d+1) FMAs each
+        per += 2.0 * 2.0 * (2.0 * d) * std::pow(2 * q - 1, d + 1);
       const int qc = q / 2;
       // restriction + prolongation: d sweeps per cell, each at most n_f^d * n_c FMAs
       per += 2.0 * (1 << d) * 2.0 * d * std::pow(q + 1, d) * (qc + 1);

@@ -20,7 +20,7 @@ PMG_OK = 0
 ERRORS = {1: "PMG_ERR_ARG", 2: "PMG_ERR_CUDA", 3: "PMG_ERR_DEGENERATE", 4: "PMG_ERR_NOT_CONVERGED",
           5: "PMG_ERR_NUMERIC", 6: "PMG_ERR_TIMEOUT", 7: "PMG_ERR_UNSUPPORTED"}
 globals().update({name: code for code, name in ERRORS.items()})
-SMOOTHER_CHEBYSHEV, SMOOTHER_JACOBI = 0, 1
+SMOOTHER_CHEBYSHEV, SMOOTHER_JACOBI, SMOOTHER_CARTESIAN = 0, 1, 2
 BOUNDS_LANCZOS, BOUNDS_FIXED, BOUNDS_USER, BOUNDS_MLP = 0, 1, 2, 3
 MLP_NPARAM, MLP_NNORM = 5378, 36
 PREC_FP64, PREC_MIXED = 0, 1

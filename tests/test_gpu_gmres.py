@@ -101,9 +101,9 @@ def _golden(name):
     return rows
 
 
-def _paper_cases():
+def _paper_cases(name="gmres_iterations_jacobi.txt"):
     cases = {}
-    for dim, p, nmg, delta, it in _golden("gmres_iterations_jacobi.txt"):
+    for dim, p, nmg, delta, it in _golden(name):
         cases.setdefault((int(dim), int(p)), []).append((int(nmg), float(delta), int(it)))
     return sorted(cases.items())
 
@@ -143,3 +143,27 @@ def test_paper_jacobi_iteration_counts(key, cases):
         assert by[(1, delta)] >= by[(2, delta)] >= by[(25, delta)], got
     for nmg in (1, 2, 25):
         assert by[(nmg, deltas[-1])] >= by[(nmg, deltas[0])], got
+
+
+@pytest.mark.parametrize("key,cases", _paper_cases("gmres_iterations_cartesian.txt"),
+                         ids=lambda v: f"{v[0]}d_p{v[1]}" if isinstance(v, tuple) else "")
+def test_paper_cartesian_reinforced_iteration_counts(key, cases):
+    """The paper's table of GMRES iterations with the Cartesian-reinforced local
+    smoother (damped, omega = 1/2), left-preconditioned GMRES; printed and
+    measured counts are listed on failure."""
+    from paper_2510_17785_gb300 import pmg
+    dim, p = key
+    N, levels = {2: (32, 5), 3: (8, 3)}[dim]
+    got = []
+    for nmg, delta, paper in cases:
+        w = inputs.Workload("paper", dim, N, p, delta, "sphere", ("const", 1.0), "uniform", 11)
+        prec = pmg.PREC_MIXED if (dim == 3 and p >= 7) else pmg.PREC_FP64
+        ctx, prob = _setup(w, levels, smoother=pmg.SMOOTHER_CARTESIAN, jacobi_omega=0.5, n_mg=nmg, post_reverse=0,
+                           precision=prec)
+        x = torch.zeros(len(prob.rhs), dtype=torch.float64, device="cuda")
+        it, rel, _ = ctx.solve_gmres(dev(prob.rhs), x, 1e-8, 100, 100, left=True)
+        ctx.close()
+        got.append((nmg, delta, it, paper))
+    print(dim, p, got)
+    for nmg, delta, it, paper in got:
+        assert abs(it - paper) <= 2, got

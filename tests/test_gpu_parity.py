@@ -118,10 +118,11 @@ def test_manufactured_load_vector(dim, N, p):
 @pytest.mark.parametrize("dim,N,p,kind,ncyc", [
     (2, 6, 4, "chebyshev", 1), (2, 6, 4, "jacobi", 1), (2, 5, 7, "chebyshev", 2), (2, 4, 2, "chebyshev", 1),
     (2, 4, 1, "chebyshev", 1), (3, 4, 4, "chebyshev", 1), (3, 3, 3, "jacobi", 2), (3, 3, 2, "chebyshev", 3),
-    (3, 2, 6, "chebyshev", 1), (3, 2, 5, "jacobi", 1)])
+    (3, 2, 6, "chebyshev", 1), (3, 2, 5, "jacobi", 1),
+    (2, 6, 4, "fdm", 1), (2, 4, 7, "fdm", 2), (3, 3, 4, "fdm", 1), (3, 2, 2, "fdm", 2), (3, 2, 6, "fdm", 1)])
 def test_local_vcycle(dim, N, p, kind, ncyc):
     from paper_2510_17785_gb300 import pmg
-    sm = pmg.SMOOTHER_JACOBI if kind == "jacobi" else pmg.SMOOTHER_CHEBYSHEV
+    sm = {"jacobi": pmg.SMOOTHER_JACOBI, "fdm": pmg.SMOOTHER_CARTESIAN}.get(kind, pmg.SMOOTHER_CHEBYSHEV)
     w = wl(dim, N, p)
     ctx, prob = gpu_ctx(w, **fixed(smoother=sm))
     m = omesh(prob)
@@ -171,10 +172,10 @@ def test_lanczos_bounds(dim, N, p):
     (2, 16, 4, "chebyshev", False),      # the 2D Q4 16x16 workload
     (2, 7, 3, "jacobi", True), (2, 5, 6, "chebyshev", True), (2, 2, 2, "chebyshev", False),
     (2, 3, 1, "chebyshev", False), (3, 4, 4, "chebyshev", False), (3, 3, 2, "jacobi", True),
-    (3, 2, 3, "chebyshev", False)])
+    (3, 2, 3, "chebyshev", False), (2, 6, 5, "fdm", False), (3, 3, 4, "fdm", True)])
 def test_sweep_matches_sequential_oracle(dim, N, p, kind, reverse):
     from paper_2510_17785_gb300 import pmg
-    sm = pmg.SMOOTHER_JACOBI if kind == "jacobi" else pmg.SMOOTHER_CHEBYSHEV
+    sm = {"jacobi": pmg.SMOOTHER_JACOBI, "fdm": pmg.SMOOTHER_CARTESIAN}.get(kind, pmg.SMOOTHER_CHEBYSHEV)
     w = wl(dim, N, p, perturb=0.25 if N > 2 else 0.0)
     ctx, prob = gpu_ctx(w, **fixed(smoother=sm))
     m = omesh(prob)
