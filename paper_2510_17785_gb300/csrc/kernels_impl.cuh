@@ -23,7 +23,7 @@ inline int grid_for(size_t work, int threads) {
 template <int DIM, int P, typename T, int V>
 int launch_patch_PV(int mode, const PatchArgs<T>& a, cudaStream_t s) {
   using C = Config<DIM, P, T, V>;
-  if constexpr (!C::fits || !C::distinct) {
+  if constexpr (!C::exists) {
     return ST_UNSUPPORTED;
   } else {
     if (a.n_items <= 0) return ST_OK;
@@ -90,7 +90,7 @@ int launch_patch(int P, int mode, int variant, const PatchArgs<T>& a, cudaStream
 template <int DIM, int P, typename T, int V>
 void patch_config_PV(size_t* smem, int* ppb, int* nt) {
   using C = Config<DIM, P, T, V>;
-  const bool ok = C::fits && C::distinct && (V == 0 || (DIM == 3 && P >= 3));
+  const bool ok = C::exists && (V == 0 || (DIM == 3 && P >= 3));
   *smem = ok ? C::smem : 0;
   *ppb = ok ? C::PPB : 0;
   *nt = ok ? C::NT : 0;

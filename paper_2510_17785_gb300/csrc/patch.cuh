@@ -101,22 +101,29 @@ struct Layout {
   static constexpr int NL = nlevels(P);
   __host__ __device__ static constexpr int q(int k) { return P >> k; }
   __host__ __device__ static constexpr int ni(int k) { return q(k) == 1 ? 1 : ipow(2 * q(k) - 1, DIM); }
-  __host__ __device__ static constexpr int lb(int k) { return q(k) == 1 ? 4 : 6 * ni(k); }
+  // per-level vectors r, d, res, dir, [A x: dense levels only], 1/diag
+  __host__ __device__ static constexpr bool dn(int k) { return dense_level(DIM, q(k)); }
+  __host__ __device__ static constexpr int lb(int k) { return q(k) == 1 ? 4 : (dn(k) ? 6 : 5) * ni(k); }
   __host__ __device__ static constexpr int off(int k) { return k == 0 ? 0 : off(k - 1) + lb(k - 1); }
-  // per-level vectors
   __host__ __device__ static constexpr int R_(int k) { return off(k); }
   __host__ __device__ static constexpr int D_(int k) { return off(k) + ni(k); }
   __host__ __device__ static constexpr int RES(int k) { return off(k) + 2 * ni(k); }
   __host__ __device__ static constexpr int DIR(int k) { return off(k) + 3 * ni(k); }
+  // A x of a dense level (the matrix-free levels hand every value to an epilogue instead)
   __host__ __device__ static constexpr int AD(int k) { return q(k) == 1 ? off(k) + 3 : off(k) + 4 * ni(k); }
-  __host__ __device__ static constexpr int DINV(int k) { return q(k) == 1 ? off(k) + 2 : off(k) + 5 * ni(k); }
+  __host__ __device__ static constexpr int DINV(int k) {
+    return q(k) == 1 ? off(k) + 2 : off(k) + (dn(k) ? 5 : 4) * ni(k);
+  }
   // dense patch matrices of the small levels, staged per patch
   __host__ __device__ static constexpr int dsz(int k) { return dense_level(DIM, q(k)) ? ni(k) * ni(k) : 0; }
   __host__ __device__ static constexpr int doff(int k) { return k == 0 ? off(NL) : doff(k - 1) + dsz(k - 1); }
   __host__ __device__ static constexpr int DENSE(int k) { return doff(k); }
-  static constexpr int CLOS = doff(NL);
+  // closure of u for Evaluate: it is read before d, res and dir of the top
+  // level are first written, so it shares their storage when it fits there
   static constexpr int NN0 = ipow(2 * P + 1, DIM);
-  static constexpr int SCR = CLOS + NN0;
+  static constexpr bool CLOS_SHARED = q(0) > 1 && !dn(0) && NN0 <= 3 * ni(0);
+  static constexpr int CLOS = CLOS_SHARED ? D_(0) : doff(NL);
+  static constexpr int SCR = CLOS_SHARED ? doff(NL) : doff(NL) + NN0;
   static constexpr int SCRATCH = LINE ? Dims<DIM, 2, P>::SCRATCH_LINE : Dims<DIM, 2, P>::SCRATCH;
   static constexpr int COEF = SCR + SCRATCH;      // per level: 1/theta, c1[1..7], c2[1..7]
   static constexpr int NCOEF = 16;
@@ -192,6 +199,17 @@ struct Config {
              !same_as<6>();
   }
   static constexpr bool distinct = distinct_impl();
+  // worth compiling: a line variant keeps at most two lines' gradients and
+  // fluxes per thread in registers (more spills and bloats the build); FP64,
+  // bound by the FP64 FMA rate, keeps variants 0, 2 and 4, and only 0 from
+  // degree 7 on
+  static constexpr int QPL = 2 * (P + 1);
+  static constexpr int TPP_ = GROUPED ? NT / PPB : NT;
+  static constexpr int SPAN_ = GROUPED ? 1 : PPB;
+  static constexpr int LPT_ = (SPAN_ * ipow(QPL, DIM - 1) + TPP_ - 1) / TPP_;
+  static constexpr bool worth = (!LINE || LPT_ <= 2) &&
+                                (sizeof(T) == 4 || V == 0 || ((V == 2 || V == 4) && P <= 6));
+  static constexpr bool exists = fits && distinct && worth;
 };
 
 template <int DIM, int P, typename T, int MODE, int V = 0>

@@ -891,7 +891,13 @@ int pmg_compute_bounds(pmg_ctx* ctx, int source) {
           b.ratio = a.ratio;
           b.ritz = pl.ritz;
           b.bounds = pl.bounds32;
-          if (!pl.G32) return fail(ctx, PMG_ERR_UNSUPPORTED, "Lanczos at this degree needs the FP32 geometry (mixed precision)");
+          if (!pl.G32) {   // FP64 contexts: an FP32 copy of the geometry for the interval estimates only
+            const size_t ng = h.ncells * (size_t)(d * (d + 1) / 2) * ipow_sz(pl.q + 1, d);
+            DALLOC(pl.G32, ng);
+            if (d == 2) ST(launch_geometry<2, float>(h.coords, h.kappa, h.N, pl.q, pl.G32, ctx->d_err, s));
+            else ST(launch_geometry<3, float>(h.coords, h.kappa, h.N, pl.q, pl.G32, ctx->d_err, s));
+            b.G = pl.G32;
+          }
           ST(d == 2 ? launch_lanczos<2, float>(pl.q, b, s) : launch_lanczos<3, float>(pl.q, b, s));
           LK(1, launch_cast_f2d(pl.bounds32, pl.bounds64, 2 * h.npatch, s));
         } else {

@@ -119,7 +119,8 @@ def test_manufactured_load_vector(dim, N, p):
     (2, 6, 4, "chebyshev", 1), (2, 6, 4, "jacobi", 1), (2, 5, 7, "chebyshev", 2), (2, 4, 2, "chebyshev", 1),
     (2, 4, 1, "chebyshev", 1), (3, 4, 4, "chebyshev", 1), (3, 3, 3, "jacobi", 2), (3, 3, 2, "chebyshev", 3),
     (3, 2, 6, "chebyshev", 1), (3, 2, 5, "jacobi", 1),
-    (2, 6, 4, "fdm", 1), (2, 4, 7, "fdm", 2), (3, 3, 4, "fdm", 1), (3, 2, 2, "fdm", 2), (3, 2, 6, "fdm", 1)])
+    (2, 6, 4, "fdm", 1), (2, 4, 7, "fdm", 2), (3, 3, 4, "fdm", 1), (3, 2, 2, "fdm", 2), (3, 2, 6, "fdm", 1),
+    (3, 2, 7, "chebyshev", 1), (3, 2, 7, "fdm", 1)])
 def test_local_vcycle(dim, N, p, kind, ncyc):
     from paper_2510_17785_gb300 import pmg
     sm = {"jacobi": pmg.SMOOTHER_JACOBI, "fdm": pmg.SMOOTHER_CARTESIAN}.get(kind, pmg.SMOOTHER_CHEBYSHEV)
