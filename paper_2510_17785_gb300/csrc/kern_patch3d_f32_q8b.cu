@@ -1,0 +1,7 @@
+// Patch kernels for d = 3 in FP32, degree 8: launch-shape variants 4-7
+// (see kern_patch3d_f32_q8.cu).
+#include "kernels_impl.cuh"
+PMG_INSTANTIATE_PATCH_V(3, float, 8, 4)
+PMG_INSTANTIATE_PATCH_V(3, float, 8, 5)
+PMG_INSTANTIATE_PATCH_V(3, float, 8, 6)
+PMG_INSTANTIATE_PATCH_V(3, float, 8, 7)

@@ -316,6 +316,17 @@ int launch_fma_chain(T* out, int grid, int block, int iters, cudaStream_t s) {
   namespace pmg {                                                                          \
   template int launch_patch_P<DIM, P, T>(int, int, const PatchArgs<T>&, cudaStream_t);     \
   }
+// One launch-shape variant of a degree in a translation unit of its own (the
+// heaviest degrees are split so that the build runs them in parallel), and
+// the declaration that keeps the dispatcher's unit from instantiating it.
+#define PMG_INSTANTIATE_PATCH_V(DIM, T, P, V)                                              \
+  namespace pmg {                                                                          \
+  template int launch_patch_PV<DIM, P, T, V>(int, const PatchArgs<T>&, cudaStream_t);      \
+  }
+#define PMG_EXTERN_PATCH_V(DIM, T, P, V)                                                   \
+  namespace pmg {                                                                          \
+  extern template int launch_patch_PV<DIM, P, T, V>(int, const PatchArgs<T>&, cudaStream_t); \
+  }
 // ... and the declarations that keep other translation units from
 // instantiating them again.
 #define PMG_EXTERN_PATCH(DIM, T, P)                                                        \
