@@ -61,7 +61,9 @@ typedef struct pmg_options {
                             d += omega D^-1 (r - A d); Cartesian-reinforced
                             d += omega D^-1 diag(A_b) A_b^-1 (r - A d), A_b the
                             reference Cartesian patch operator inverted by fast
-                            diagonalisation (Section 3.1)                    */
+                            diagonalisation (Section 3.1).  The last is not a
+                            symmetric step: precondition GMRES with it, as the
+                            paper does, not CG                              */
   int cheb_degree;       /* Chebyshev polynomial degree (k), >= 1              */
   double jacobi_omega;   /* damping omega of the Jacobi and Cartesian-reinforced
                             steps (paper: 1/2)                                 */
