@@ -347,4 +347,4 @@ def test_launch_shape_variants_are_bit_identical(precision, p):
         ctx.close()
     assert len(outs) >= 2
     for o in outs[1:]:
-        assert np.array_equal(o, outs[0])
+        assert np.array_equal(o, outs[0]), relerr(o, outs[0])
