@@ -256,9 +256,12 @@ class PatchSmoother:
     """All interior-vertex patches of one mesh, with per-(patch, level) bounds."""
 
     def __init__(self, mesh: fem.StructuredMesh, p: int, levels=None, sm: Smoother | None = None,
-                 bounds_fn=None, n_cycles: int = 1, order: str = "colour"):
+                 bounds_fn=None, n_cycles: int = 1, order: str = "colour", additive: bool = False,
+                 theta: float = 1.0):
         self.mesh, self.p = mesh, p
         self.order = order             # "colour": colour-major; "vertex": plain vertex order
+        self.additive, self.theta = additive, theta
+        self._mult = None
         self.levels = levels_halving(p) if levels is None else levels
         self.sm = Smoother() if sm is None else sm
         self.n_cycles = n_cycles
@@ -289,7 +292,38 @@ class PatchSmoother:
         d = local_solve(P, r, self.sm, self.bounds(v), self.n_cycles)
         return P.lv[self.levels[0]].interior, d
 
+    def multiplicity(self) -> np.ndarray:
+        """Number of patches whose interior holds each global DoF (0 off every
+        patch), counted patch by patch."""
+        if self._mult is None:
+            m = np.zeros(self.mesh.n_nodes(self.p))
+            for v in self.vertices:
+                m[self.patch(v).lv[self.levels[0]].interior] += 1
+            self._mult = m
+        return self._mult
+
+    def sweep_additive(self, u, b, reverse=False):
+        """Weighted additive sweep: every patch solves with the residual of the
+        same u, the corrections are summed, u += theta W sum_j Pi_j^T d_j with
+        W = diag(1 / multiplicity).  reverse: the transpose, W applied to the
+        residual instead (u += theta sum_j Pi_j^T B_j Pi_j W (b - A u)), so that
+        a V-cycle with the forward sweep before and the reverse one after the
+        coarse correction is symmetric."""
+        mult = self.multiplicity()
+        w = np.divide(1.0, mult, out=np.zeros_like(mult), where=mult > 0)
+        corr = np.zeros_like(u)
+        for v in self.vertices:
+            P = self.patch(v)
+            idx = P.lv[self.levels[0]].interior
+            r = P.residual(u, b)
+            if reverse:
+                r = w[idx] * r
+            corr[idx] += local_solve(P, r, self.sm, self.bounds(v), self.n_cycles)
+        return u + self.theta * (corr if reverse else w * corr)
+
     def sweep(self, u, b, reverse=False, colours=None, within="increasing"):
+        if self.additive:
+            return self.sweep_additive(u, b, reverse)
         """One multiplicative sweep (Algorithm 1, colour-major order).  `within`
         orders the patches of one colour ("increasing" or "decreasing" vertex
         id).  With order "vertex" the patches run in plain vertex order

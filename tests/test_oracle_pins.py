@@ -576,3 +576,48 @@ def test_cartesian_reinforced_contracts_on_a_distorted_patch():
     rho_fdm = np.abs(np.linalg.eigvals(E)).max()
     rho_jac = np.abs(np.linalg.eigvals(J)).max()
     assert rho_fdm < 0.9 and rho_fdm < rho_jac
+
+
+# ------------------------------------------------------ weighted additive sweep
+def test_multiplicity_is_the_patch_count_per_dof():
+    """Each DoF is interior to the patches of the vertices of the cells holding
+    it that are interior vertices: a vertex DoF to 1, an edge/face/cell DoF to
+    2, 4, 8 in 3D away from the boundary."""
+    m = _mesh(3, 4, 0.2, 51)
+    S = pt.PatchSmoother(m, 2, additive=True, sm=pt.Smoother(kind="jacobi"))
+    mult = S.multiplicity()
+    assert set(np.unique(mult)) <= {0, 1, 2, 4, 8}
+    free = m.free_mask(2)
+    assert np.all(mult[free] >= 1) and np.all(mult[~free] == 0)
+    node = m.node_index(2, [3, 3, 3])              # the middle of the cell (1,1,1): 8 patches
+    assert mult[node] == 8
+    node = m.node_index(2, [2, 2, 2])              # vertex (1,1,1): its own patch only
+    assert mult[node] == 1
+
+
+def test_additive_vcycle_is_symmetric():
+    """Forward weighted sweep before, transposed sweep after the coarse
+    correction: a symmetric preconditioner (usable in CG)."""
+    m = _mesh(2, 8, 0.25, 52, ("loguniform", -1, 1))
+    p = 2
+    G = gmg.GMG(m, p, 2, smoother_args=dict(bounds_fn=lz.fixed_bounds_fn(0.3, 2.0), additive=True, theta=0.7))
+    rng = np.random.default_rng(53)
+    free = G.free[-1]
+    y1, y2 = rng.uniform(-1, 1, len(free)) * free, rng.uniform(-1, 1, len(free)) * free
+    a, c = y1 @ G.vcycle(y2), y2 @ G.vcycle(y1)
+    assert abs(a - c) < 1e-12 * abs(y1 @ G.vcycle(y1))
+
+
+def test_additive_sweep_with_exact_local_solves_on_one_patch():
+    """2x2 mesh, one patch covering every free DoF with weight 1: the weighted
+    additive sweep with an exact local solve is the exact solve (theta = 1)."""
+    m = _mesh(2, 2, 0.2, 54)
+    p = 3
+    S = pt.PatchSmoother(m, p, additive=True, theta=1.0, sm=pt.Smoother(kind="jacobi"), n_cycles=60)
+    A = m.assemble(p).toarray()
+    free = m.free_mask(p)
+    rng = np.random.default_rng(55)
+    b = rng.uniform(-1, 1, len(free)) * free
+    u = S.sweep(np.zeros_like(b), b)
+    Af = A[np.ix_(free, free)]
+    assert np.allclose(u[free], np.linalg.solve(Af, b[free]), rtol=0, atol=1e-9 * np.abs(u).max())
