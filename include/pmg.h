@@ -85,6 +85,14 @@ typedef struct pmg_options {
   int post_reverse;      /* 1: post-smoothing sweeps the colours in reverse
                             order (symmetric V-cycle, for CG; default);
                             0: same order as pre-smoothing (Section 4; GMRES) */
+  int additive;          /* 0: multiplicative sweep (Algorithm 1, default);
+                            1: weighted additive sweep: every patch solves with
+                            the residual of the same u and
+                            u += theta W sum_j Pi_j^T d_j, W = diag(1/m), m the
+                            number of patches whose interior holds the DoF; a
+                            reversed sweep (post-smoothing) applies W to the
+                            residual instead, so the V-cycle stays symmetric  */
+  double additive_theta; /* theta of the additive sweep (default 1)          */
 } pmg_options;
 enum { PMG_KAPPA_ARITHMETIC = 0, PMG_KAPPA_GEOMETRIC = 1, PMG_KAPPA_HARMONIC = 2 };
 

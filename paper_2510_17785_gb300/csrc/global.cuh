@@ -404,6 +404,28 @@ static __global__ void k_cg_update_xr(double* __restrict__ x, double* __restrict
   }
 }
 
+// additive sweep: u += theta (W) corr on free DoFs, W = 1 / patch multiplicity
+template <int DIM, typename T>
+__global__ void k_additive_update(T* __restrict__ u, const T* __restrict__ corr, T theta, int weighted, int q,
+                                  int N) {
+  const int M = q * N + 1;
+  size_t nd = 1;
+  for (int ax = 0; ax < DIM; ++ax) nd *= M;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nd; i += (size_t)gridDim.x * blockDim.x) {
+    size_t rem = i;
+    int m = 1;
+    bool bnd = false;
+    for (int ax = 0; ax < DIM; ++ax) {
+      const int g = (int)(rem % M);
+      rem /= M;
+      bnd = bnd || g == 0 || g == M - 1;
+      m *= bnd ? 1 : patch_multiplicity_1d(g, q, N);
+    }
+    if (bnd) continue;
+    u[i] += weighted ? theta * corr[i] / T(m) : theta * corr[i];
+  }
+}
+
 // y += a x ; y = a x
 static __global__ void k_axpy(double a, const double* __restrict__ x, double* __restrict__ y, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)

@@ -227,6 +227,15 @@ int launch_geometry(const double* coords, const double* kappa, int N, int q, T* 
   return ST_OK;
 }
 
+template <int DIM, typename T>
+int launch_additive_update(T* u, const T* corr, double theta, int weighted, int q, int N, cudaStream_t s) {
+  size_t nd = 1;
+  for (int ax = 0; ax < DIM; ++ax) nd *= (size_t)q * N + 1;
+  k_additive_update<DIM, T><<<grid_for(nd, 256), 256, 0, s>>>(u, corr, T(theta), weighted, q, N);
+  PMG_CHECK_LAUNCH();
+  return ST_OK;
+}
+
 template <int DIM>
 int launch_diag(const double* G64, int N, int q, double* diag, double* dinv64, float* dinv32, cudaStream_t s) {
   const size_t M = (size_t)q * N + 1;
@@ -341,5 +350,6 @@ int launch_fma_chain(T* out, int grid, int block, int iters, cudaStream_t s) {
   template int launch_lanczos<DIM, T>(int, const LanczosArgs<T>&, cudaStream_t);                            \
   template int launch_cell_apply<DIM, T>(int, const T*, T*, const T*, int, cudaStream_t);                   \
   template int launch_geometry<DIM, T>(const double*, const double*, int, int, T*, int*, cudaStream_t);     \
+  template int launch_additive_update<DIM, T>(T*, const T*, double, int, int, int, cudaStream_t);            \
   template int launch_mask_boundary<DIM, T>(T*, int, cudaStream_t);                                         \
   }

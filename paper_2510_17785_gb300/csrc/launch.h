@@ -37,6 +37,9 @@ int launch_dense_patch(int q, const double* G64, int N, int first, int n, double
 
 template <int DIM, typename T>
 int launch_geometry(const double* coords, const double* kappa, int N, int q, T* G, int* err, cudaStream_t s);
+// additive sweep: u += theta (W) corr on free DoFs (W = 1 / patch multiplicity)
+template <int DIM, typename T>
+int launch_additive_update(T* u, const T* corr, double theta, int weighted, int q, int N, cudaStream_t s);
 
 // FP64 only
 template <int DIM>

@@ -56,7 +56,10 @@ struct PatchArgs {
   double omega;
   int n_mg;
   int* err;                    // device error flag
+  T* corr;                     // additive sweep: corrections are added here instead of to u, or NULL
+  int weight_residual;         // additive sweep, transposed form: residual scaled by 1 / multiplicity
 };
+
 
 // Epilogues of the patch operator applies: the smoother and residual updates
 // applied to each output value as it is produced (no extra pass over Ad).
@@ -717,6 +720,20 @@ struct PatchKernel {
       // Evaluate: r = b - A u on the patch interior
       SF<DIM, 2, P, T, NT, PPB, C::LINE, C::GROUPED>::template apply_epi<false>(vec(0, L::CLOS), PS, vec(0, L::SCR), PS,
                                                                    gfun<0>(), epi<0>(EPI_EVAL));
+      if (a->weight_residual) {               // transposed additive sweep: r <- W r
+        TM::template loop<NI0>([&](int pp, int i) {
+          constexpr int Mi = 2 * P - 1;
+          int rem = i, m = 1;
+#pragma unroll
+          for (int ax = 0; ax < DIM; ++ax) {
+            const int k = rem % Mi;
+            rem /= Mi;
+            m *= patch_multiplicity_1d(P * (patch_vertex(pp, ax) - 1) + 1 + k, P, a->N);
+          }
+          vec(pp, L::R_(0))[i] /= T(m);
+        });
+        TM::sync();
+      }
     } else {
       TM::template loop<NI0>([&](int pp, int i) {
         const bool act = cells[pp * CST + NCELL + 1];
@@ -729,9 +746,10 @@ struct PatchKernel {
     for (int cyc = 0; cyc < a->n_mg; ++cyc) vcycle<0>(cyc == 0);
     // Scatter
     if (MODE == MODE_SWEEP) {
+      T* dst = a->corr ? a->corr : a->u;      // additive: corrections collected apart from u
       TM::template loop<NI0>([&](int pp, int i) {
         const bool act = cells[pp * CST + NCELL + 1];
-        if (act) a->u[gindex_int<P>(pp, i)] += vec(pp, L::D_(0))[i];
+        if (act) dst[gindex_int<P>(pp, i)] += vec(pp, L::D_(0))[i];
       });
     } else {
       TM::template loop<NI0>([&](int pp, int i) {

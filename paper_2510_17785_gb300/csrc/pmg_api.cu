@@ -99,6 +99,8 @@ struct pmg_ctx {
   float variant_ms[NUM_VARIANTS] = {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f};
   float* mlp_params = nullptr;           // PMG_BOUNDS_MLP network and normalisation
   float* mlp_norm = nullptr;
+  double* add64 = nullptr;               // additive sweeps: correction sums (finest-level size)
+  float* add32 = nullptr;
   double* gm_V = nullptr;                // GMRES basis (restart + 1 vectors), grown on demand
   int gm_m = 0;
   double* fdm64[PMG_MAXQ + 1] = {nullptr};   // Cartesian-reinforced tables per degree q (device)
@@ -249,8 +251,37 @@ int sweep_colour(pmg_ctx* ctx, int level, int colour, const T* b, T* u, cudaStre
 }
 
 template <typename T>
+T* additive_buffer(pmg_ctx* ctx);
+template <>
+double* additive_buffer<double>(pmg_ctx* ctx) { return ctx->add64; }
+template <>
+float* additive_buffer<float>(pmg_ctx* ctx) { return ctx->add32; }
+
+template <typename T>
 int sweep(pmg_ctx* ctx, int level, const T* b, T* u, bool reverse, cudaStream_t s) {
   const int nc = 1 << ctx->dim;
+  if (ctx->opt.additive) {
+    // weighted additive sweep: every colour adds its corrections to `corr`
+    // (patches of one colour have disjoint interiors; colours in a fixed
+    // order, so the sum is deterministic), all from the residual of the same u
+    HLevel& h = ctx->L[level];
+    T* corr = additive_buffer<T>(ctx);
+    CU(cudaMemsetAsync(corr, 0, h.nd * sizeof(T), s));
+    for (int c = 0; c < nc; ++c) {
+      PatchArgs<T> a = patch_args<T>(ctx, level);
+      a.list = h.colour_list[c];
+      a.n_items = h.ncolour[c];
+      a.u = u;
+      a.b = b;
+      a.corr = corr;
+      a.weight_residual = reverse ? 1 : 0;
+      LK(1, patch_launch<T>(ctx, MODE_SWEEP, a, s));
+    }
+    const int w = reverse ? 0 : 1;
+    LK(1, ctx->dim == 2 ? launch_additive_update<2, T>(u, corr, ctx->opt.additive_theta, w, ctx->p, h.N, s)
+                        : launch_additive_update<3, T>(u, corr, ctx->opt.additive_theta, w, ctx->p, h.N, s));
+    return PMG_OK;
+  }
   for (int i = 0; i < nc; ++i) {
     const int c = reverse ? nc - 1 - i : i;
     int st = sweep_colour<T>(ctx, level, c, b, u, s);
@@ -463,6 +494,8 @@ void pmg_default_options(pmg_options* o) {
   o->mlp_safety = 1.2;
   o->coarse_kappa = PMG_KAPPA_ARITHMETIC;
   o->post_reverse = 1;
+  o->additive = 0;
+  o->additive_theta = 1.0;
 }
 
 int pmg_create(int device, const pmg_options* opt, pmg_ctx** out) {
@@ -475,8 +508,9 @@ int pmg_create(int device, const pmg_options* opt, pmg_ctx** out) {
   const pmg_options& o = ctx->opt;
   if (o.cheb_degree < 1 || o.cheb_degree > 8 || o.n_mg < 1 || o.lanczos_steps < 1 || o.lanczos_steps > 64 ||
       (o.smoother < 0 || o.smoother > 2) || (o.precision != 0 && o.precision != 1) || o.bounds < 0 ||
+      (o.additive != 0 && o.additive != 1) || !(o.additive_theta > 0) ||
       o.bounds > 3 || !(o.bound_safety > 0) || !(o.mlp_safety > 0) || o.coarse_kappa < 0 || o.coarse_kappa > 2 || !(o.bound_ratio >= 1) || o.variant < 0 ||
-      o.variant >= NUM_VARIANTS) {
+      o.variant >= NUM_VARIANTS || (o.additive != 0 && o.additive != 1) || !(o.additive_theta > 0)) {
     delete ctx;
     return PMG_ERR_ARG;
   }
@@ -783,6 +817,10 @@ int pmg_setup(pmg_ctx* ctx) {
   {
     const size_t n = ctx->L.back().nd;
     DALLOC(ctx->cg_x, n);
+    if (ctx->opt.additive) {
+      DALLOC(ctx->add64, n);
+      if (mixed) DALLOC(ctx->add32, n);
+    }
     DALLOC(ctx->cg_r, n);
     DALLOC(ctx->cg_z, n);
     DALLOC(ctx->cg_p, n);
@@ -957,6 +995,7 @@ int pmg_patch_smooth_colour(pmg_ctx* ctx, int level, int colour, const double* b
   if (st) return st;
   if (colour < 0 || colour >= (1 << ctx->dim)) return fail(ctx, PMG_ERR_ARG, "colour out of range");
   if (!b || !u) return fail(ctx, PMG_ERR_ARG, "null vector");
+  if (ctx->opt.additive) return fail(ctx, PMG_ERR_UNSUPPORTED, "an additive sweep runs all colours (pmg_patch_smooth)");
   cudaStream_t s = (cudaStream_t)stream;
   HLevel& h = ctx->L[level];
   if (ctx->opt.precision == PMG_PREC_MIXED) {

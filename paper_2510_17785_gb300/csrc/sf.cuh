@@ -55,6 +55,16 @@ struct Dims {
   static constexpr int SCRATCH_LINE = NQ + R_LINE;
 };
 
+// Number of vertex patches whose interior holds the node with per-axis index
+// g (degree q, N cells per direction, interior vertices 1..N-1): a node on a
+// vertex line lies in that vertex's patches only, any other node in the
+// patches of both end vertices of its cell that are interior.
+__host__ __device__ inline int patch_multiplicity_1d(int g, int q, int N) {
+  if (g % q == 0) return 1;
+  const int c = g / q;
+  return (c >= 1 && c <= N - 1) + (c + 1 >= 1 && c + 1 <= N - 1);
+}
+
 // A cooperative loop over PPB blocks x ITEMS work items.
 template <int NT, int PPB, int ITEMS, typename F>
 __device__ __forceinline__ void coop(F&& f) {

@@ -45,6 +45,7 @@ class Options(C.Structure):
         ("bound_ratio", C.c_double), ("fixed_lo", C.c_double), ("fixed_hi", C.c_double),
         ("seed", C.c_uint64), ("precision", C.c_int), ("autotune", C.c_int), ("variant", C.c_int),
         ("mlp_safety", C.c_double), ("coarse_kappa", C.c_int), ("post_reverse", C.c_int),
+        ("additive", C.c_int), ("additive_theta", C.c_double),
     ]
 
 

@@ -348,3 +348,37 @@ def test_launch_shape_variants_are_bit_identical(precision, p):
     assert len(outs) >= 2
     for o in outs[1:]:
         assert np.array_equal(o, outs[0]), relerr(o, outs[0])
+
+
+# ------------------------------------------------ weighted additive sweep
+@pytest.mark.parametrize("dim,N,p,reverse,theta", [(2, 6, 3, False, 1.0), (2, 6, 3, True, 0.7), (3, 4, 2, False, 0.5),
+                                                   (3, 3, 4, True, 1.0)])
+def test_additive_sweep_matches_oracle(dim, N, p, reverse, theta):
+    w = wl(dim, N, p)
+    ctx, prob = gpu_ctx(w, **fixed(additive=1, additive_theta=theta))
+    m = omesh(prob)
+    u0 = inputs.random_vector(9, dim, p, N)
+    b = prob.rhs
+    u = dev(u0)
+    ctx.patch_smooth(0, dev(b), u, 1, reverse)
+    torch.cuda.synchronize()
+    S = pt.PatchSmoother(m, p, bounds_fn=lz.fixed_bounds_fn(FIX_LO, FIX_HI), additive=True, theta=theta)
+    ref = S.sweep(u0, b, reverse=reverse)
+    assert relerr(u.cpu().numpy(), ref) < TOL
+    ctx.close()
+
+
+def test_additive_gmg_cg_matches_oracle():
+    dim, N, p, levels = 2, 8, 3, 3
+    w = wl(dim, N, p)
+    ctx, prob = gpu_ctx(w, n_levels=levels, **fixed(additive=1, additive_theta=0.6))
+    G = gmg.GMG(omesh(prob), p, N >> (levels - 1),
+                smoother_args=dict(bounds_fn=lz.fixed_bounds_fn(FIX_LO, FIX_HI), additive=True, theta=0.6))
+    b = prob.rhs
+    xr, it_ref, hist = gmg.pcg(G.A[-1], b, G.vcycle, 1e-8, 200)
+    x = torch.zeros(len(b), dtype=torch.float64, device="cuda")
+    it, rel, _ = ctx.solve_cg(dev(b), x, 1e-8, 200)
+    assert rel <= 1e-8 and hist[-1] <= 1e-8
+    assert abs(it - it_ref) <= 1, (it, it_ref)
+    assert relerr(x.cpu().numpy(), xr) < 1e-9
+    ctx.close()
