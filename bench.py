@@ -511,7 +511,7 @@ def run_reference(args):
     from paper_2510_17785_gb300 import inputs
     w = inputs.WORKLOADS[args.workload]
     levels = int(round(math.log2(w.N // w.coarse_N))) + 1
-    iters = 8          # CG iterations the GPU solver needs on this workload (both precisions)
+    iters = 7          # CG iterations the GPU solver needs on this workload (both precisions, measured)
     vals = []
     for i in range(args.warmup + args.steps):
         t = oracle_patch_times(w.name, 12, 2)
