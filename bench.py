@@ -406,7 +406,8 @@ def run_ours(args):
         err = float((x - torch.tensor(uh.numpy(), device=dev)).abs().max())
         result[name] = dict(ms=ms, its=its, launches=launches, t_sweep=t_sweep, sweep_flops=flops,
                             e2e_ms=e2e_ms, setup_s=t_setup, maxdiff_e2e=err,
-                            umax=float(x.abs().max()), tuning=ctx.tuning())
+                            umax=float(x.abs().max()), tuning=ctx.tuning(),
+                            level_variants=[ctx.tuning_level(lv)[0] for lv in range(levels)])
         if name == "mixed":
             result["fma32"] = ctx.fma_peak(pmg.PREC_MIXED)
             result["fma64"] = ctx.fma_peak(pmg.PREC_FP64)
@@ -441,7 +442,8 @@ def run_ours(args):
             "replicas": world,
             "patch_kernel_launch": {"variant": head["tuning"][0], "threads_per_cta": head["tuning"][1],
                                     "patches_per_cta": head["tuning"][2],
-                                    "autotune_ms_per_variant": [round(x, 4) for x in head["tuning"][3]]},
+                                    "autotune_ms_per_variant": [round(x, 4) for x in head["tuning"][3]],
+                                    "variant_per_mesh_level": head["level_variants"]},
         },
         "time_to_solution_ms": t_max,
         "cg_iterations": [i for i, _ in head["its"]],

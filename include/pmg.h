@@ -259,6 +259,11 @@ double pmg_sweep_flops(const pmg_ctx* ctx, int level);
  * Every variant computes bit-identical results. */
 int pmg_tuning(const pmg_ctx* ctx, int* variant, int* threads, int* patches_per_cta,
                float* ms_per_variant);
+/* Launch shape used on mesh level `level` (the set-up autotuner times every
+ * variant on one colour of every level: large launches favour occupancy, the
+ * small launches of coarse levels the latency of one patch) and its timings
+ * (ms_per_variant[8], -1 where not timed).  Either output may be NULL. */
+int pmg_tuning_level(const pmg_ctx* ctx, int level, int* variant, float* ms_per_variant);
 
 /* ---- learned Chebyshev intervals ------------------------------------------
  * No counterpart in the paper (its smoother is damped Jacobi).  A small MLP

@@ -99,7 +99,7 @@ struct PatchEpi {
   }
 };
 
-template <int DIM, int P, bool LINE = false>
+template <int DIM, int P, bool LINE = false, bool GSMEM = false>
 struct Layout {
   static constexpr int NL = nlevels(P);
   __host__ __device__ static constexpr int q(int k) { return P >> k; }
@@ -135,36 +135,46 @@ struct Layout {
   __host__ __device__ static constexpr int fsz(int k) { return q(k) > 1 ? mi(k) * mi(k) + 3 * mi(k) : 0; }
   __host__ __device__ static constexpr int foff(int k) { return k == 0 ? COEF + NL * NCOEF : foff(k - 1) + fsz(k - 1); }
   __host__ __device__ static constexpr int FDM(int k) { return foff(k); }
-  static constexpr int PS_RAW = foff(NL);
+  // geometry tensors of the patch's 2^d cells at the top degree, staged once
+  // per patch (latency-oriented launch shapes): [cell slot][ncomp][(p+1)^d]
+  static constexpr int GCELL = (DIM * (DIM + 1) / 2) * ipow(P + 1, DIM);
+  static constexpr int GS = (foff(NL) + 3) & ~3;
+  static constexpr int PS_RAW = GSMEM ? GS + (1 << DIM) * GCELL : foff(NL);
   static constexpr int PS = (PS_RAW + 3) & ~3;    // per-patch stride in elements
 };
 
 // Launch shape of the patch kernel.  Variant 0 is the default; for 3D degrees
 // 3..8 the set-up autotuner also times variants 1..7:
 //   variant:          1        2        3        4        5        6        7
-//   design:         stage    stage    line     line     line     line     line
-//   threads / CTA:    256      128       64      256      128       32      128
+//   design:         stage    stage    stage    line     line     line     line
+//   threads / CTA:    256      128      512      256      128      512      128
 //   patches / CTA:      2        1        1        2        1        1        2
+//   geometry:                          staged                     staged
 //   groups:                                                                 2
 // (patches per CTA are capped by shared memory).  "stage": every direction's
 // flux in shared memory; "line": one thread per line along the last
 // direction keeps that direction's gradient and flux in registers.  With
-// groups, each patch of the CTA has its own threads and barrier.
+// groups, each patch of the CTA has its own threads and barrier.  "staged":
+// latency-oriented shapes for small launches (coarse mesh levels), one patch
+// per 512 threads, the top level's geometry tensors copied to shared memory
+// once per patch instead of read from L2 by every apply.
 constexpr int NUM_VARIANTS = 8;
 
 template <int DIM, int P, typename T, int V = 0>
 struct Config {
   static constexpr int NT0 = (DIM == 3) ? 256 : 128;
   static constexpr int PPB0 = (DIM == 3) ? (P <= 2 ? 4 : 1) : (P <= 2 ? 8 : (P <= 4 ? 4 : 2));
-  static constexpr int NTV[NUM_VARIANTS] = {NT0, 256, 128, 64, 256, 128, 32, 128};
+  static constexpr int NTV[NUM_VARIANTS] = {NT0, 256, 128, 512, 256, 128, 512, 128};
   static constexpr int PPBV[NUM_VARIANTS] = {PPB0, 2, 1, 1, 2, 1, 1, 2};
-  static constexpr bool LINEV[NUM_VARIANTS] = {false, false, false, true, true, true, true, true};
+  static constexpr bool LINEV[NUM_VARIANTS] = {false, false, false, false, true, true, true, true};
   static constexpr bool GROUPV[NUM_VARIANTS] = {false, false, false, false, false, false, false, true};
+  static constexpr bool GSMEMV[NUM_VARIANTS] = {false, false, false, true, false, false, true, false};
   static constexpr int NT = NTV[V];
   static constexpr int PPB_MAX = PPBV[V];
   static constexpr bool LINE = LINEV[V];
+  static constexpr bool GSMEM = GSMEMV[V];
   static constexpr size_t bytes_per_patch =
-      sizeof(T) * Layout<DIM, P, LINE>::PS + sizeof(int) * ((1 << DIM) + 6);
+      sizeof(T) * Layout<DIM, P, LINE, GSMEM>::PS + sizeof(int) * ((1 << DIM) + 6);
   static constexpr size_t SMEM_LIMIT = 227 * 1024;
   static constexpr int PPB_FIT = (int)(SMEM_LIMIT / bytes_per_patch);
   static constexpr int PPB = PPB_FIT < PPB_MAX ? (PPB_FIT < 1 ? 1 : PPB_FIT) : PPB_MAX;
@@ -174,7 +184,7 @@ struct Config {
   static constexpr bool GROUPED = GROUPV[V] && PPB > 1 && NT % PPB == 0 && (NT / PPB) % 32 == 0;
   // register budget per thread (launch bound): 64 for FP32 up to degree 5,
   // 128 otherwise (FP64, or the larger line registers at high degree)
-  static constexpr int REG_TARGET = (sizeof(T) == 4 && P <= 5) ? 64 : 128;
+  static constexpr int REG_TARGET = (sizeof(T) == 4 && P <= 5 && !GSMEMV[V]) ? 64 : 128;
   // resident CTAs per SM: by the register target, and at most what shared
   // memory allows (small CTAs then get the registers shared memory leaves)
   static constexpr int MINB_REG = 65536 / (NT * REG_TARGET);
@@ -186,7 +196,7 @@ struct Config {
   template <int W>
   static constexpr bool same_as() {
     return Config<DIM, P, T, W>::NT == NT && Config<DIM, P, T, W>::PPB == PPB && Config<DIM, P, T, W>::LINE == LINE &&
-           Config<DIM, P, T, W>::GROUPED == GROUPED;
+           Config<DIM, P, T, W>::GROUPED == GROUPED && Config<DIM, P, T, W>::GSMEM == GSMEM;
   }
   static constexpr bool distinct_impl() {
     if constexpr (V == 0) return true;
@@ -204,21 +214,21 @@ struct Config {
   static constexpr bool distinct = distinct_impl();
   // worth compiling: a line variant keeps at most two lines' gradients and
   // fluxes per thread in registers (more spills and bloats the build); FP64,
-  // bound by the FP64 FMA rate, keeps variants 0, 2 and 4, and only 0 from
+  // bound by the FP64 FMA rate, keeps variants 0, 2, 4 and 6, and only 0 from
   // degree 7 on
   static constexpr int QPL = 2 * (P + 1);
   static constexpr int TPP_ = GROUPED ? NT / PPB : NT;
   static constexpr int SPAN_ = GROUPED ? 1 : PPB;
   static constexpr int LPT_ = (SPAN_ * ipow(QPL, DIM - 1) + TPP_ - 1) / TPP_;
   static constexpr bool worth = (!LINE || LPT_ <= 2) &&
-                                (sizeof(T) == 4 || V == 0 || ((V == 2 || V == 4) && P <= 6));
+                                (sizeof(T) == 4 || V == 0 || ((V == 2 || V == 4 || V == 6) && P <= 6));
   static constexpr bool exists = fits && distinct && worth;
 };
 
 template <int DIM, int P, typename T, int MODE, int V = 0>
 struct PatchKernel {
   using C = Config<DIM, P, T, V>;
-  using L = Layout<DIM, P, C::LINE>;
+  using L = Layout<DIM, P, C::LINE, C::GSMEM>;
   using TM = Team<C::NT, C::PPB, C::GROUPED>;
   static constexpr int NT = C::NT, PPB = C::PPB, NL = L::NL, PS = L::PS;
   static constexpr int NCELL = 1 << DIM;
@@ -234,9 +244,14 @@ struct PatchKernel {
   __device__ auto gfun() const {
     constexpr int q = P >> K;
     constexpr int stride = Dims<DIM, 2, q>::NCOMP * ipow(q + 1, DIM);
-    const T* G = a->lv[K].G;
-    const int* cl = cells;
-    return [G, cl](int pp, int slot) { return G + (size_t)cl[pp * CST + slot] * stride; };
+    if constexpr (C::GSMEM && K == 0) {                 // staged in shared memory by load_level
+      const T* gs = sm + L::GS;
+      return [gs](int pp, int slot) { return gs + pp * PS + slot * stride; };
+    } else {
+      const T* G = a->lv[K].G;
+      const int* cl = cells;
+      return [G, cl](int pp, int slot) { return G + (size_t)cl[pp * CST + slot] * stride; };
+    }
   }
 
   template <int K>
@@ -668,6 +683,14 @@ struct PatchKernel {
           const bool act = cells[pp * CST + NCELL + 1];
           const int pid = cells[pp * CST + NCELL];
           vec(pp, L::DENSE(K))[e] = act ? a->lv[K].dense[(size_t)pid * NI * NI + e] : T(0);
+        });
+      }
+      if constexpr (C::GSMEM && K == 0) {                // the cells' geometry tensors, once per patch
+        constexpr int GC = L::GCELL;
+        TM::template loop<NCELL * GC>([&](int pp, int e) {
+          const bool act = cells[pp * CST + NCELL + 1];
+          const int slot = e / GC;
+          vec(pp, L::GS)[e] = act ? a->lv[K].G[(size_t)cells[pp * CST + slot] * GC + (e - slot * GC)] : T(0);
         });
       }
       // reference-patch fast-diagonalisation table (Cartesian-reinforced smoother)

@@ -97,6 +97,8 @@ struct pmg_ctx {
   int64_t launches = 0;                  // kernels launched so far
   int variant = 0;                       // launch shape of the patch-sweep kernel
   float variant_ms[NUM_VARIANTS] = {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f};
+  int level_variant[16] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};  // per mesh level
+  float level_ms[16][NUM_VARIANTS] = {};  // set-up timings per mesh level (-1: not timed)
   float* mlp_params = nullptr;           // PMG_BOUNDS_MLP network and normalisation
   float* mlp_norm = nullptr;
   double* add64 = nullptr;               // additive sweeps: correction sums (finest-level size)
@@ -170,9 +172,12 @@ size_t ipow_sz(size_t b, int e) {
 }
 
 // ---- dispatch on dimension -------------------------------------------------
+// launch shape: the one tuned for the mesh level (sweeps), else the context's
 template <typename T>
-int patch_launch(pmg_ctx* c, int mode, const PatchArgs<T>& a, cudaStream_t s) {
-  const int v = mode == MODE_SWEEP ? c->variant : 0;
+int patch_launch(pmg_ctx* c, int mode, const PatchArgs<T>& a, cudaStream_t s, int level = -1) {
+  int v = 0;
+  if (mode == MODE_SWEEP)
+    v = (level >= 0 && level < 16 && c->level_variant[level] >= 0) ? c->level_variant[level] : c->variant;
   return c->dim == 2 ? launch_patch<2, T>(c->p, mode, v, a, s) : launch_patch<3, T>(c->p, mode, v, a, s);
 }
 template <typename T>
@@ -246,7 +251,7 @@ int sweep_colour(pmg_ctx* ctx, int level, int colour, const T* b, T* u, cudaStre
   a.n_items = h.ncolour[colour];
   a.u = u;
   a.b = b;
-  LK(1, patch_launch<T>(ctx, MODE_SWEEP, a, s));
+  LK(1, patch_launch<T>(ctx, MODE_SWEEP, a, s, level));
   return PMG_OK;
 }
 
@@ -275,7 +280,7 @@ int sweep(pmg_ctx* ctx, int level, const T* b, T* u, bool reverse, cudaStream_t 
       a.b = b;
       a.corr = corr;
       a.weight_residual = reverse ? 1 : 0;
-      LK(1, patch_launch<T>(ctx, MODE_SWEEP, a, s));
+      LK(1, patch_launch<T>(ctx, MODE_SWEEP, a, s, level));
     }
     const int w = reverse ? 0 : 1;
     LK(1, ctx->dim == 2 ? launch_additive_update<2, T>(u, corr, ctx->opt.additive_theta, w, ctx->p, h.N, s)
@@ -401,50 +406,61 @@ int precondition(pmg_ctx* ctx, const double* r, double* z, cudaStream_t s) {
 }
 
 // Time every launch-shape variant of the patch-sweep kernel on colour 0 of
-// the finest level (zero vectors; results are discarded) and keep the fastest.
+// every mesh level (zero vectors; results are discarded) and keep the fastest
+// per level: large launches favour occupancy, the small launches of coarse
+// levels the latency of one patch.  The finest level's timings are reported.
 template <typename T>
-int autotune_T(pmg_ctx* ctx, T* u, const T* b) {
-  const int lf = ctx->nlev - 1;
+int autotune_T(pmg_ctx* ctx) {
   cudaStream_t s = ctx->stream;
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
-  float best = 1e30f;
-  int bestv = 0;
-  for (int v = 0; v < NUM_VARIANTS; ++v) {
-    size_t sm;
-    int ppb, nt;
-    if (ctx->dim == 2) patch_config<2, T>(ctx->p, v, &sm, &ppb, &nt);
-    else patch_config<3, T>(ctx->p, v, &sm, &ppb, &nt);
-    if (sm == 0) continue;
-    ctx->variant = v;
-    int st = sweep_colour<T>(ctx, lf, 0, b, u, s);     // warm-up (and kernel attribute)
-    if (st) {
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      return st;
+  int st = PMG_OK;
+  for (int l = 0; l < 16; ++l)
+    for (int v = 0; v < NUM_VARIANTS; ++v) ctx->level_ms[l][v] = -1.f;
+  for (int l = ctx->nlev - 1; l >= 0 && st == PMG_OK; --l) {
+    HLevel& h = ctx->L[l];
+    if (h.npatch == 0 || l >= 16) continue;
+    T* u = Xof<T>(h);
+    T* b = Bof<T>(h);
+    if (cudaMemsetAsync(u, 0, h.nd * sizeof(T), s) != cudaSuccess ||
+        cudaMemsetAsync(b, 0, h.nd * sizeof(T), s) != cudaSuccess) {
+      st = fail(ctx, PMG_ERR_CUDA, "autotune: memset failed");
+      break;
     }
-    float ms = 1e30f;
-    for (int rep = 0; rep < 3; ++rep) {
-      CU(cudaEventRecord(e0, s));
-      st = sweep_colour<T>(ctx, lf, 0, b, u, s);
-      if (st) return st;
-      CU(cudaEventRecord(e1, s));
-      CU(cudaEventSynchronize(e1));
-      float t = 0.f;
-      CU(cudaEventElapsedTime(&t, e0, e1));
-      ms = std::min(ms, t);
+    float best = 1e30f;
+    int bestv = 0;
+    for (int v = 0; v < NUM_VARIANTS && st == PMG_OK; ++v) {
+      size_t sm;
+      int ppb, nt;
+      if (ctx->dim == 2) patch_config<2, T>(ctx->p, v, &sm, &ppb, &nt);
+      else patch_config<3, T>(ctx->p, v, &sm, &ppb, &nt);
+      if (sm == 0) continue;
+      ctx->level_variant[l] = v;
+      st = sweep_colour<T>(ctx, l, 0, b, u, s);          // warm-up (and kernel attribute)
+      float ms = 1e30f;
+      for (int rep = 0; rep < 3 && st == PMG_OK; ++rep) {
+        float t = 0.f;
+        if (cudaEventRecord(e0, s) != cudaSuccess) st = fail(ctx, PMG_ERR_CUDA, "autotune: event");
+        if (st == PMG_OK) st = sweep_colour<T>(ctx, l, 0, b, u, s);
+        if (st == PMG_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                             cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+          st = fail(ctx, PMG_ERR_CUDA, "autotune: event");
+        ms = std::min(ms, t);
+      }
+      if (l == ctx->nlev - 1) ctx->variant_ms[v] = ms;
+      ctx->level_ms[l][v] = ms;
+      if (ms < best) {
+        best = ms;
+        bestv = v;
+      }
     }
-    ctx->variant_ms[v] = ms;
-    if (ms < best) {
-      best = ms;
-      bestv = v;
-    }
+    ctx->level_variant[l] = bestv;
+    if (l == ctx->nlev - 1) ctx->variant = bestv;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  ctx->variant = bestv;
-  return PMG_OK;
+  return st;
 }
 
 int autotune(pmg_ctx* ctx) {
@@ -458,15 +474,8 @@ int autotune(pmg_ctx* ctx) {
     if (sm == 0) return fail(ctx, PMG_ERR_UNSUPPORTED, "this launch-shape variant does not exist for this degree");
     return PMG_OK;
   }
-  HLevel& h = ctx->L.back();
-  if (ctx->opt.precision == PMG_PREC_MIXED) {
-    CU(cudaMemsetAsync(h.x32, 0, h.nd * sizeof(float), ctx->stream));
-    CU(cudaMemsetAsync(h.b32, 0, h.nd * sizeof(float), ctx->stream));
-    return autotune_T<float>(ctx, h.x32, h.b32);
-  }
-  CU(cudaMemsetAsync(h.x64, 0, h.nd * sizeof(double), ctx->stream));
-  CU(cudaMemsetAsync(h.b64, 0, h.nd * sizeof(double), ctx->stream));
-  return autotune_T<double>(ctx, h.x64, h.b64);
+  if (ctx->opt.precision == PMG_PREC_MIXED) return autotune_T<float>(ctx);
+  return autotune_T<double>(ctx);
 }
 
 }  // namespace
@@ -1540,6 +1549,15 @@ double pmg_sweep_flops(const pmg_ctx* ctx, int level) {
     }
   }
   return per * npatch;
+}
+
+int pmg_tuning_level(const pmg_ctx* ctx, int level, int* variant, float* ms_per_variant) {
+  if (!ctx || !ctx->setup_ok || level < 0 || level >= ctx->nlev) return PMG_ERR_ARG;
+  const int v = (level < 16 && ctx->level_variant[level] >= 0) ? ctx->level_variant[level] : ctx->variant;
+  if (variant) *variant = v;
+  if (ms_per_variant)
+    for (int k = 0; k < NUM_VARIANTS; ++k) ms_per_variant[k] = level < 16 ? ctx->level_ms[level][k] : -1.f;
+  return PMG_OK;
 }
 
 int pmg_tuning(const pmg_ctx* ctx, int* variant, int* threads, int* ppb_out, float* ms) {

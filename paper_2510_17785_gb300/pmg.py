@@ -35,6 +35,7 @@ SYMBOLS = (
     "pmg_get_patch_map", "pmg_get_inv_diag", "pmg_sweep_flops", "pmg_launch_count", "pmg_fma_peak",
     "pmg_lanczos_bounds_noalloc", "pmg_tuning", "pmg_default_train_options", "pmg_features", "pmg_mlp_grad",
     "pmg_mlp_train", "pmg_mlp_predict", "pmg_set_mlp", "pmg_solve_gmres", "pmg_batch_solve_cg",
+    "pmg_tuning_level",
 )
 
 
@@ -112,6 +113,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pmg_set_mlp": (i, [vp, vp, vp]),
         "pmg_solve_gmres": (i, [vp, vp, vp, d, i, i, i, P(i), P(d), vp]),
         "pmg_batch_solve_cg": (i, [vp, i, vp, vp, d, i, P(i), P(d), P(i)]),
+        "pmg_tuning_level": (i, [vp, i, P(i), P(C.c_float)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -396,6 +398,13 @@ class Context:
         ms = (C.c_float * 8)()
         self._check(self.lib.pmg_tuning(self.h, C.byref(v), C.byref(t), C.byref(b), ms))
         return v.value, t.value, b.value, list(ms)
+
+    def tuning_level(self, level):
+        """(variant used on mesh level `level`, [set-up ms per candidate variant])"""
+        v = C.c_int()
+        ms = (C.c_float * 8)()
+        self._check(self.lib.pmg_tuning_level(self.h, level, C.byref(v), ms))
+        return v.value, list(ms)
 
     def features(self, level, k, X, stream=None):
         self._check(self.lib.pmg_features(self.h, level, k, _ptr(X), _stream(stream)))

@@ -57,6 +57,9 @@ def main():
     ctx.apply(lf, u, Au)
     torch.cuda.synchronize()
     print(f"ok: {w.name} sweeps={args.sweeps} tuning={ctx.tuning()} |u|_inf={float(u.abs().max()):.6e}")
+    for lv in range(args.levels):
+        v, ms = ctx.tuning_level(lv)
+        print(f"  level {lv}: variant {v}, ms per variant {[round(x, 4) for x in ms]}")
     ctx.close()
 
 

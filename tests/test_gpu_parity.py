@@ -322,6 +322,7 @@ def test_recomputing_bounds_reuses_scratch_and_is_reproducible():
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 @pytest.mark.parametrize("p", [4, 6])
 def test_launch_shape_variants_are_bit_identical(precision, p):
+    """(also: the per-level tuning query reports an existing variant on every level)"""
     """Every launch-shape variant of the sweep kernel computes the same bits
     (one owner thread per output, fixed summation order), so the set-up
     autotuner may pick any of them."""
