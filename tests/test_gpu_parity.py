@@ -322,7 +322,6 @@ def test_recomputing_bounds_reuses_scratch_and_is_reproducible():
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 @pytest.mark.parametrize("p", [4, 6])
 def test_launch_shape_variants_are_bit_identical(precision, p):
-    """(also: the per-level tuning query reports an existing variant on every level)"""
     """Every launch-shape variant of the sweep kernel computes the same bits
     (one owner thread per output, fixed summation order), so the set-up
     autotuner may pick any of them."""
@@ -341,6 +340,7 @@ def test_launch_shape_variants_are_bit_identical(precision, p):
             assert e.code == 7            # variant does not exist for this configuration
             ctx.close()
             continue
+        assert all(ctx.tuning_level(lv)[0] == v for lv in range(2))   # without autotuning: the chosen variant
         u = dev(u0)
         ctx.patch_smooth(1, dev(prob.rhs), u, 2, False)
         torch.cuda.synchronize()
@@ -382,4 +382,14 @@ def test_additive_gmg_cg_matches_oracle():
     assert rel <= 1e-8 and hist[-1] <= 1e-8
     assert abs(it - it_ref) <= 1, (it, it_ref)
     assert relerr(x.cpu().numpy(), xr) < 1e-9
+    ctx.close()
+
+
+def test_autotuner_picks_a_variant_per_level():
+    """With autotuning every mesh level gets an existing variant, timed."""
+    w = wl(3, 8, 4)
+    ctx, prob = gpu_ctx(w, n_levels=3, **fixed())
+    for lv in range(1, 3):
+        v, ms = ctx.tuning_level(lv)
+        assert 0 <= v < 8 and ms[v] > 0 and all(m < 0 or m >= ms[v] for m in ms)
     ctx.close()
