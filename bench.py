@@ -256,7 +256,7 @@ def run_batch(args):
         p = (2, 4, 6, 8)[k % 4]
         wk = inputs.Workload(f"batch{k}", 3, N, p, 0.2, "sphere", ("loguniform", -2.0, 2.0), "uniform", 4004 * 64 + k)
         pr = inputs.make_problem(wk)
-        c = pmg.Context(0, precision=pmg.PREC_MIXED)
+        c = pmg.Context(0, precision=pmg.PREC_MIXED, autotune=2)   # shapes for a shared GPU
         c.mesh_structured(3, N, p, 3, pr.coords, pr.kappa)
         c.setup()
         ctxs.append(c)

@@ -76,8 +76,11 @@ typedef struct pmg_options {
   uint64_t seed;         /* seed of the Lanczos start vectors                  */
   int precision;         /* PMG_PREC_*                                         */
   int autotune;          /* 1: pmg_setup times the launch-shape variants of the
-                            patch kernel on the finest level and keeps the
-                            fastest; 0: use `variant`                          */
+                            patch sweep on one colour of every mesh level and
+                            keeps the fastest per level; 2: the same without
+                            the latency-oriented shapes (variants 3 and 6),
+                            for problems that share the GPU (batched solves);
+                            0: use `variant` everywhere                       */
   int variant;           /* launch-shape variant when autotune = 0 (0 = default) */
   double mlp_safety;     /* PMG_BOUNDS_MLP: hi = mlp_safety * predicted theta_max */
   int coarse_kappa;      /* coefficient of a coarse cell from its 2^d children:

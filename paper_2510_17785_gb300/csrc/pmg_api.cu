@@ -436,6 +436,7 @@ int autotune_T(pmg_ctx* ctx) {
       if (ctx->dim == 2) patch_config<2, T>(ctx->p, v, &sm, &ppb, &nt);
       else patch_config<3, T>(ctx->p, v, &sm, &ppb, &nt);
       if (sm == 0) continue;
+      if (ctx->opt.autotune == 2 && (v == 3 || v == 6)) continue;   // throughput mode: no latency shapes
       ctx->level_variant[l] = v;
       st = sweep_colour<T>(ctx, l, 0, b, u, s);          // warm-up (and kernel attribute)
       float ms = 1e30f;
