@@ -7,6 +7,13 @@
 
 namespace pmg {
 
+// index of the current device for per-device caches (-1 on failure)
+inline int current_device() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
+  return dev;
+}
+
 inline int grid_for(size_t work, int threads) {
   size_t g = (work + threads - 1) / threads;
   if (g > 152 * 32) g = 152 * 32;
@@ -28,23 +35,25 @@ int launch_patch_PV(int mode, const PatchArgs<T>& a, cudaStream_t s) {
   } else {
     if (a.n_items <= 0) return ST_OK;
     const int grid = (a.n_items + C::PPB - 1) / C::PPB;
+    const int dev = current_device();
+    if (dev < 0) return ST_CUDA;
     if (mode == MODE_SWEEP) {
-      static bool attr = false;
-      if (!attr) {
+      static bool attr[64] = {};                 // the attribute is per device
+      if (!attr[dev]) {
         if (cudaFuncSetAttribute(k_patch<DIM, P, T, MODE_SWEEP, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)C::smem) != cudaSuccess)
           return ST_CUDA;
-        attr = true;
+        attr[dev] = true;
       }
       k_patch<DIM, P, T, MODE_SWEEP, V><<<grid, C::NT, C::smem, s>>>(a);
     } else {
       if constexpr (V != 0) return ST_UNSUPPORTED;
-      static bool attr = false;
-      if (!attr) {
+      static bool attr[64] = {};
+      if (!attr[dev]) {
         if (cudaFuncSetAttribute(k_patch<DIM, P, T, MODE_LOCAL, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)C::smem) != cudaSuccess)
           return ST_CUDA;
-        attr = true;
+        attr[dev] = true;
       }
       k_patch<DIM, P, T, MODE_LOCAL, V><<<grid, C::NT, C::smem, s>>>(a);
     }
@@ -134,12 +143,14 @@ int launch_lanczos_Q(const LanczosArgs<T>& a, cudaStream_t s) {
   } else {
     if (a.n_items <= 0) return ST_OK;
     if (a.ksteps > 64) return ST_ARG;
-    static bool attr = false;
-    if (!attr) {
+    static bool attr[64] = {};                   // the attribute is per device
+    const int dev = current_device();
+    if (dev < 0) return ST_CUDA;
+    if (!attr[dev]) {
       if (cudaFuncSetAttribute(k_lanczos<DIM, Q, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
           cudaSuccess)
         return ST_CUDA;
-      attr = true;
+      attr[dev] = true;
     }
     k_lanczos<DIM, Q, T><<<a.n_items, 256, smem, s>>>(a);
     PMG_CHECK_LAUNCH();
@@ -183,12 +194,14 @@ int launch_cell_apply_Q(const T* u, T* out, const T* G, int N, cudaStream_t s) {
   constexpr int NT = DIM == 3 ? 128 : 64;
   constexpr int CPB = DIM == 3 ? (Q <= 2 ? 4 : (Q <= 5 ? 2 : 1)) : (Q <= 4 ? 8 : 4);
   using CA = CellApply<DIM, Q, T, NT, CPB>;
-  static bool attr = false;
-  if (!attr) {
+  static bool attr[64] = {};                     // the attribute is per device
+  const int dev = current_device();
+  if (dev < 0) return ST_CUDA;
+  if (!attr[dev]) {
     if (cudaFuncSetAttribute(k_cell_apply<DIM, Q, T, NT, CPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)CA::smem) != cudaSuccess)
       return ST_CUDA;
-    attr = true;
+    attr[dev] = true;
   }
   size_t M = (size_t)Q * N + 1, total = 1;
   for (int ax = 0; ax < DIM; ++ax) total *= M;
