@@ -30,7 +30,7 @@ FP32_PEAK_DERIVED = 152 * 128 * 2 * 2.070e9      # SMs x FP32 lanes x 2 flops x 
 FP64_PEAK_NOMINAL = 1.25e12                      # GB300 FP64 rate (nominal)
 # DRAM bytes (read + write) of one finest-level colour launch of the FP32 patch kernel on the 3D Q4 32^3
 # workload (colour 0, 3,375 patches), from one ncu capture of the current kernel
-PATCH_LAUNCH_TRAFFIC = 114.140416e6 + 77.756160e6
+PATCH_LAUNCH_TRAFFIC = 114.047488e6 + 78.020608e6
 METRIC = "patch-smoother DoFs/s and CG time-to-1e-8 residual: mixed/learned vs plain FP64, 1 GB300"
 
 

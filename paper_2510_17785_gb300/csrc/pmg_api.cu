@@ -466,6 +466,8 @@ int autotune_T(pmg_ctx* ctx) {
 
 int autotune(pmg_ctx* ctx) {
   for (int v = 0; v < NUM_VARIANTS; ++v) ctx->variant_ms[v] = -1.f;
+  for (int l = 0; l < 16; ++l)
+    for (int v = 0; v < NUM_VARIANTS; ++v) ctx->level_ms[l][v] = -1.f;
   if (!ctx->opt.autotune) {
     ctx->variant = ctx->opt.variant;
     size_t sm;
