@@ -272,7 +272,7 @@ int pmg_tuning_level(const pmg_ctx* ctx, int level, int* variant, float* ms_per_
  * No counterpart in the paper (its smoother is damped Jacobi).  A small MLP
  * predicts (log theta_max, log theta_min) of the Lanczos run of a patch from
  * 16 features of its cells' geometry and coefficient; Lanczos stays the
- * judge.  Network 16 -> 64 -> 64 -> 2 with ReLU on standardised inputs and
+ * reference estimate.  Network 16 -> 64 -> 64 -> 2 with ReLU on standardised inputs and
  * targets; PMG_MLP_NPARAM parameters (W1 64x16 row-major, b1, W2 64x64, b2,
  * W3 2x64, b3) and PMG_MLP_NNORM normalisation floats (mean and std of the 16
  * features, then mean and std of the 2 targets).  Training is FP32 (Adam),

@@ -4,7 +4,7 @@ Test infrastructure only.  The paper has no learned component: the
 Chebyshev smoother needs an interval for the spectrum of D^-1 A_{j,q} on every
 patch j and p-level q, which Lanczos provides (oracle/lanczos.py); the MLP
 predicts (log theta_max, log theta_min) from cheap per-patch features instead,
-and Lanczos stays the judge.
+and the Lanczos estimate stays the reference it is checked against.
 
 Features (16) of patch j at degree q, from its 2^d cells; for each cell c,
 J_c is the Jacobian of its multilinear map at the cell centre, s_c its

@@ -6,7 +6,8 @@
 // spectrum of D^-1 A_{j,q}.  A 16-step Lanczos run per (patch, level) gives it
 // (k_lanczos); the MLP predicts (log theta_max, log theta_min) of that run from
 // geometric and coefficient features at a tiny fraction of the cost, and
-// Lanczos remains the judge (tests) and the fallback.
+// Lanczos remains the reference the predictions are checked against (tests)
+// and the fallback.
 //
 // Features of patch j at degree q, from its 2^d cells, with J_c the Jacobian
 // of cell c at its centre, s_c its singular values, d_c = det J_c,
