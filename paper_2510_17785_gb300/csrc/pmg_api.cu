@@ -1270,9 +1270,14 @@ int pmg_batch_solve_cg(pmg_ctx* const* ctxs, int n_problems, const double* const
   std::vector<double> r0(K, 0.0), rel(K, 1.0);
   std::vector<int> it(K, 0), res(K, PMG_OK);
   std::vector<char> active(K, 0);
+  // on an error, no problem's work may still be running when we return
+  auto drain = [&](int code) {
+    for (int k = 0; k < K; ++k) cudaStreamSynchronize(ctxs[k]->stream);
+    return code;
+  };
   for (int k = 0; k < K; ++k) {                      // every start in flight before the first wait
     const int st = cg_start(ctxs[k], b[k]);
-    if (st) return st;
+    if (st) return drain(st);
   }
   for (int k = 0; k < K; ++k) {
     pmg_ctx* ctx = ctxs[k];
@@ -1283,7 +1288,7 @@ int pmg_batch_solve_cg(pmg_ctx* const* ctxs, int n_problems, const double* const
     else if (maxit > 0) active[k] = 1;
     if (active[k]) {
       const int st = cg_graph(ctx);
-      if (st) return st;
+      if (st) return drain(st);
     }
   }
   for (;;) {
@@ -1293,7 +1298,7 @@ int pmg_batch_solve_cg(pmg_ctx* const* ctxs, int n_problems, const double* const
       any = true;
       ++it[k];
       const int st = cg_step(ctxs[k]);
-      if (st) return st;
+      if (st) return drain(st);
     }
     if (!any) break;
     for (int k = 0; k < K; ++k) {
