@@ -348,6 +348,36 @@ def test_sweep_single_patch_brute_force():
     assert np.allclose(S.sweep(u, b), ref, atol=1e-13)
 
 
+@pytest.mark.parametrize("order,reverse", [("colour", False), ("colour", True), ("vertex", False), ("vertex", True)])
+def test_sweep_several_patches_brute_force(order, reverse):
+    """3x3 mesh, four overlapping patches: the sweep applies
+    u <- u + Pi_j^T B_j (b - A u)_j patch after patch in the stated order
+    (colour-major, or plain vertex order; reversed for post-smoothing), with
+    B_j each patch's V-cycle operator and A the assembled global matrix."""
+    m = _mesh(2, 3, 0.2, 61, ("loguniform", -1, 1))
+    p = 3
+    S = pt.PatchSmoother(m, p, bounds_fn=lz.exact_bounds_fn(), order=order)
+    Ag = m.assemble(p).toarray()
+    rng = np.random.default_rng(62)
+    free = m.free_mask(p)
+    u = rng.uniform(-1, 1, m.n_nodes(p)) * free
+    b = rng.uniform(-1, 1, m.n_nodes(p)) * free
+    verts = pt.interior_vertices(2, 3)
+    if order == "colour":
+        seq = sorted(verts, key=lambda v: (pt.colour_of(v), verts.index(v)))
+    else:
+        seq = list(verts)
+    if reverse:
+        seq = seq[::-1] if order == "vertex" else sorted(verts, key=lambda v: (-pt.colour_of(v), verts.index(v)))
+    ref = u.copy()
+    for v in seq:
+        P = S.patch(v)
+        I = P.lv[p].interior
+        B = pt.vcycle_matrix(P, S.sm, S.bounds(v))
+        ref[I] += B @ (b - Ag @ ref)[I]
+    assert np.allclose(S.sweep(u, b, reverse=reverse), ref, atol=1e-12)
+
+
 def test_sweep_patches_of_one_colour_commute():
     m = _mesh(2, 6, 0.2, 12)
     p = 2
