@@ -321,17 +321,24 @@ int pmg_fma_peak(pmg_ctx* ctx, int precision, double* flops_per_s);
 
 /* ---- allocation-free bounds ----------------------------------------------
  * No counterpart in the paper: an engineering entry point for callers that
- * must not allocate device memory at this point (for instance while a CUDA
- * graph is being captured, inside a framework that owns the device memory
- * through its own allocator, or in a solver that refreshes its Chebyshev
- * intervals mid-run and must not stall on cudaMalloc/cudaFree).
+ * must not allocate device memory at this point (for instance inside a
+ * framework that owns the device memory through its own allocator, or in a
+ * solver that refreshes its Chebyshev intervals mid-run and must not stall on
+ * cudaMalloc/cudaFree, which synchronise the device).
  *
- * Computes the same Lanczos estimates as pmg_compute_bounds (FP64, the
- * context's Lanczos options) for patches first_patch .. first_patch +
- * n_patches - 1 of mesh level `level` at p-level index k (degree p >> k, must
- * be > 1) and writes n_patches x (theta_min, theta_max) to ritz_dev and
- * n_patches x (lo, hi) to bounds_dev: caller-owned device FP64 arrays.  The
- * context's own intervals are not changed.  Asynchronous on `stream`.
+ * Computes the same Lanczos estimates as pmg_compute_bounds (the context's
+ * Lanczos options) for patches first_patch .. first_patch + n_patches - 1 of
+ * mesh level `level` at p-level index k (degree p >> k, must be > 1) and
+ * writes n_patches x (theta_min, theta_max) to ritz_dev and n_patches x
+ * (lo, hi) to bounds_dev: caller-owned device FP64 arrays of at least
+ * 2 * n_patches values each, on the context's device.  The context's own
+ * intervals are not changed.  Asynchronous on `stream`.  The operator is
+ * applied in FP64, except at degrees whose FP64 working set exceeds shared
+ * memory (3D q >= 7), where, like pmg_compute_bounds, it is applied in FP32
+ * with FP64 Lanczos vectors and the intervals are rounded to FP32; that needs
+ * the context's FP32 geometry (always present in mixed precision; in FP64
+ * contexts made by pmg_compute_bounds with Lanczos bounds), else
+ * PMG_ERR_UNSUPPORTED.
  *
  * Allocates no device memory: the Lanczos basis lives in one fixed 16 MiB
  * device array inside the library (held by every GPU that loads it until the
@@ -339,7 +346,8 @@ int pmg_fma_peak(pmg_ctx* ctx, int precision, double* flops_per_s);
  * doubles, else PMG_ERR_ARG (split the range).  The first call on a device
  * also uploads this entry point's tables and looks up the array's device
  * address; make that first call before any stream capture.  All calls share
- * the array: calls whose kernels overlap on the GPU race, so serialise them. */
+ * the array: calls whose kernels overlap on the GPU race, so serialise them.
+ * The caller's current device is restored before the call returns. */
 int pmg_lanczos_bounds_noalloc(pmg_ctx* ctx, int level, int k, int64_t first_patch,
                                int64_t n_patches, double* ritz_dev, double* bounds_dev,
                                void* stream);

@@ -12,6 +12,8 @@ struct LanczosView {
   int64_t npatch = 0;
   const double* G64 = nullptr;
   const double* dinv64 = nullptr;
+  const float* G32 = nullptr;       // FP32 geometry, NULL if the context made none
+  const float* dinv32 = nullptr;
   uint64_t seed = 0;
   double safety = 0.0, ratio = 0.0;
 };

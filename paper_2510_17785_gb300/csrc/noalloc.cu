@@ -2,14 +2,13 @@
 // pmg_compute_bounds for a range of patches, for callers that must not
 // allocate device memory.
 //
-// Who cannot allocate: code that runs while a CUDA graph is being captured
-// (cudaMalloc is not capturable), code inside a framework that owns the
-// device memory budget through its own caching allocator and forbids raw
-// cudaMalloc/cudaFree (which also synchronise the device), and long-running
-// or latency-critical solvers that recompute Chebyshev bounds mid-run and must
-// not stall on, or fail in, an allocation.  pmg_compute_bounds needs a
-// device buffer for the Lanczos basis; this entry point uses a fixed
-// file-scope device array instead.
+// Who cannot allocate: code inside a framework that owns the device memory
+// budget through its own caching allocator and forbids raw cudaMalloc/cudaFree
+// (which also synchronise the device), and long-running or latency-critical
+// solvers that recompute Chebyshev bounds mid-run and must not stall on, or
+// fail in, an allocation.  pmg_compute_bounds needs a device buffer for the
+// Lanczos basis; this entry point uses a fixed file-scope device array
+// instead.
 //
 // The array (kScratchBytes = 16 MiB) is part of the library image: every GPU
 // that loads the library holds it until the process exits.  All calls share
@@ -17,6 +16,12 @@
 // every basis vector before reading it, so nothing needs clearing.  Calls
 // whose kernels overlap on the GPU (different streams, or different contexts
 // on one device) race on the array: serialise them.
+//
+// Degrees whose FP64 working set does not fit in shared memory (3D q >= 7)
+// use the FP32 operator with FP64 Lanczos vectors, as pmg_compute_bounds
+// does; that needs the context's FP32 geometry, which mixed-precision
+// contexts always hold and FP64 contexts hold once pmg_compute_bounds has
+// taken that fallback.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -39,16 +44,42 @@ struct DeviceState {
 DeviceState g_dev[kMaxDevices];
 std::mutex g_mu;
 
-template <int DIM, int Q>
+template <int DIM, int Q, typename T>
 cudaError_t set_smem_attr() {
-  constexpr size_t smem = pmg::lanczos_smem<DIM, Q, double>();
+  constexpr size_t smem = pmg::lanczos_smem<DIM, Q, T>();
   if constexpr (smem > 227 * 1024) {
     return cudaSuccess;
   } else {
-    return cudaFuncSetAttribute(pmg::k_lanczos<DIM, Q, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem);
+    return cudaFuncSetAttribute(pmg::k_lanczos<DIM, Q, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
 }
+
+template <typename T>
+cudaError_t set_smem_attrs() {
+  cudaError_t a[] = {set_smem_attr<2, 2, T>(), set_smem_attr<2, 3, T>(), set_smem_attr<2, 4, T>(),
+                     set_smem_attr<2, 5, T>(), set_smem_attr<2, 6, T>(), set_smem_attr<2, 7, T>(),
+                     set_smem_attr<2, 8, T>(), set_smem_attr<3, 2, T>(), set_smem_attr<3, 3, T>(),
+                     set_smem_attr<3, 4, T>(), set_smem_attr<3, 5, T>(), set_smem_attr<3, 6, T>(),
+                     set_smem_attr<3, 7, T>(), set_smem_attr<3, 8, T>()};
+  for (cudaError_t x : a)
+    if (x != cudaSuccess) return x;
+  return cudaSuccess;
+}
+
+// Makes `dev` current for the lifetime of the guard and restores the
+// caller's current device on every return path.
+struct DeviceGuard {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int dev) {
+    err = cudaGetDevice(&prev);
+    if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
 
 // Once per device, with that device current: upload this file's constant
 // tables, set the kernels' shared-memory limits and take the device address
@@ -60,12 +91,10 @@ cudaError_t setup_device(int dev) {
   pmg::build_tables(t64, t32, r);
   cudaError_t e = (cudaError_t)pmg::upload_tables_tu(t64, t32, r);
   if (e != cudaSuccess) return e;
-  cudaError_t a[] = {set_smem_attr<2, 2>(), set_smem_attr<2, 3>(), set_smem_attr<2, 4>(), set_smem_attr<2, 5>(),
-                     set_smem_attr<2, 6>(), set_smem_attr<2, 7>(), set_smem_attr<2, 8>(), set_smem_attr<3, 2>(),
-                     set_smem_attr<3, 3>(), set_smem_attr<3, 4>(), set_smem_attr<3, 5>(), set_smem_attr<3, 6>(),
-                     set_smem_attr<3, 7>(), set_smem_attr<3, 8>()};
-  for (cudaError_t x : a)
-    if (x != cudaSuccess) return x;
+  e = set_smem_attrs<double>();
+  if (e != cudaSuccess) return e;
+  e = set_smem_attrs<float>();
+  if (e != cudaSuccess) return e;
   double* ptr = nullptr;
   e = cudaGetSymbolAddress((void**)&ptr, g_lanczos_scratch);
   if (e != cudaSuccess) return e;
@@ -74,29 +103,46 @@ cudaError_t setup_device(int dev) {
   return cudaSuccess;
 }
 
-template <int DIM, int Q>
-int launch(const pmg::LanczosArgs<double>& a, cudaStream_t s) {
-  constexpr size_t smem = pmg::lanczos_smem<DIM, Q, double>();
+template <int DIM, int Q, typename T>
+int launch(const pmg::LanczosArgs<T>& a, cudaStream_t s) {
+  constexpr size_t smem = pmg::lanczos_smem<DIM, Q, T>();
   if constexpr (smem > 227 * 1024) {
     return PMG_ERR_UNSUPPORTED;
   } else {
-    pmg::k_lanczos<DIM, Q, double><<<a.n_items, 256, smem, s>>>(a);
+    pmg::k_lanczos<DIM, Q, T><<<a.n_items, 256, smem, s>>>(a);
     return cudaPeekAtLastError() == cudaSuccess ? PMG_OK : PMG_ERR_CUDA;
   }
 }
 
-template <int DIM>
-int launch_q(int q, const pmg::LanczosArgs<double>& a, cudaStream_t s) {
+template <int DIM, typename T>
+int launch_q(int q, const pmg::LanczosArgs<T>& a, cudaStream_t s) {
   switch (q) {
-    case 2: return launch<DIM, 2>(a, s);
-    case 3: return launch<DIM, 3>(a, s);
-    case 4: return launch<DIM, 4>(a, s);
-    case 5: return launch<DIM, 5>(a, s);
-    case 6: return launch<DIM, 6>(a, s);
-    case 7: return launch<DIM, 7>(a, s);
-    case 8: return launch<DIM, 8>(a, s);
+    case 2: return launch<DIM, 2, T>(a, s);
+    case 3: return launch<DIM, 3, T>(a, s);
+    case 4: return launch<DIM, 4, T>(a, s);
+    case 5: return launch<DIM, 5, T>(a, s);
+    case 6: return launch<DIM, 6, T>(a, s);
+    case 7: return launch<DIM, 7, T>(a, s);
+    case 8: return launch<DIM, 8, T>(a, s);
     default: return PMG_ERR_UNSUPPORTED;
   }
+}
+
+template <typename T>
+void fill_args(pmg::LanczosArgs<T>& a, const pmg::LanczosView& v, int64_t first_patch, int64_t n_patches,
+               double* scratch, double* ritz_dev, double* bounds_dev) {
+  a.N = v.N;
+  a.n_items = (int)n_patches;
+  a.first_patch = (int)first_patch;
+  a.V = scratch;
+  a.ksteps = v.ksteps;
+  a.seed = v.seed;
+  a.safety = v.safety;
+  a.ratio = v.ratio;
+  a.ritz = ritz_dev;
+  a.bounds = nullptr;
+  a.bounds_f64 = bounds_dev;
+  a.out_offset = first_patch;      // patch first_patch lands in entry 0 of the caller's arrays
 }
 
 }  // namespace
@@ -121,8 +167,9 @@ extern "C" int pmg_lanczos_bounds_noalloc(pmg_ctx* ctx, int level, int k, int64_
                                "16 MiB scratch array; split the patch range into smaller calls");
   if (v.ksteps > 64) return pmg::set_last_error(ctx, PMG_ERR_ARG, "noalloc Lanczos: more than 64 Lanczos steps");
   if (v.device < 0 || v.device >= kMaxDevices) return pmg::set_last_error(ctx, PMG_ERR_ARG, "device index too large");
-  if (cudaSetDevice(v.device) != cudaSuccess)
-    return pmg::set_last_error(ctx, PMG_ERR_CUDA, "noalloc Lanczos: cudaSetDevice failed");
+  DeviceGuard guard(v.device);
+  if (guard.err != cudaSuccess)
+    return pmg::set_last_error(ctx, PMG_ERR_CUDA, "noalloc Lanczos: cudaGetDevice/cudaSetDevice failed");
   {
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_dev[v.device].ready) {
@@ -131,24 +178,27 @@ extern "C" int pmg_lanczos_bounds_noalloc(pmg_ctx* ctx, int level, int k, int64_
     }
   }
   if (n_patches == 0) return PMG_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  double* scratch = g_dev[v.device].scratch;
   pmg::LanczosArgs<double> a;
-  a.N = v.N;
-  a.n_items = (int)n_patches;
-  a.first_patch = (int)first_patch;
+  fill_args(a, v, first_patch, n_patches, scratch, ritz_dev, bounds_dev);
   a.G = v.G64;
   a.dinv = v.dinv64;
-  a.V = g_dev[v.device].scratch;
-  a.ksteps = v.ksteps;
-  a.seed = v.seed;
-  a.safety = v.safety;
-  a.ratio = v.ratio;
-  // the kernel indexes its outputs by global patch id; shift so that patch
-  // first_patch lands in entry 0 of the caller's arrays
-  a.ritz = ritz_dev - 2 * first_patch;
-  a.bounds = bounds_dev - 2 * first_patch;
-  const int st = v.dim == 2 ? launch_q<2>(v.q, a, (cudaStream_t)stream) : launch_q<3>(v.q, a, (cudaStream_t)stream);
+  int st = v.dim == 2 ? launch_q<2, double>(v.q, a, s) : launch_q<3, double>(v.q, a, s);
+  if (st == PMG_ERR_UNSUPPORTED) {
+    // the FP64 working set does not fit: FP32 operator, FP64 Lanczos vectors
+    if (!v.G32 || !v.dinv32)
+      return pmg::set_last_error(ctx, PMG_ERR_UNSUPPORTED,
+                                 "noalloc Lanczos: this degree needs the FP32 geometry copy, which this FP64 context "
+                                 "has not made (pmg_compute_bounds with Lanczos bounds makes it)");
+    pmg::LanczosArgs<float> b;
+    fill_args(b, v, first_patch, n_patches, scratch, ritz_dev, bounds_dev);
+    b.G = v.G32;
+    b.dinv = v.dinv32;
+    st = v.dim == 2 ? launch_q<2, float>(v.q, b, s) : launch_q<3, float>(v.q, b, s);
+  }
   if (st == PMG_ERR_UNSUPPORTED)
-    return pmg::set_last_error(ctx, st, "noalloc Lanczos: the FP64 working set of this degree exceeds shared memory");
+    return pmg::set_last_error(ctx, st, "noalloc Lanczos: the working set of this degree exceeds shared memory");
   if (st != PMG_OK) return pmg::set_last_error(ctx, st, cudaGetErrorString(cudaGetLastError()));
   return PMG_OK;
 }

@@ -853,7 +853,9 @@ struct LanczosArgs {
   uint64_t seed;
   double safety, ratio;
   double* ritz;           // [patches][2] (theta_min, theta_max), FP64
-  T* bounds;              // [patches][2] (lo, hi)
+  T* bounds;              // [patches][2] (lo, hi), or NULL
+  double* bounds_f64;     // [patches][2] (lo, hi) rounded to T, then widened to FP64, or NULL
+  int64_t out_offset;     // patch id written to entry 0 of ritz / bounds / bounds_f64
 };
 
 __device__ __forceinline__ uint64_t splitmix64_dev(uint64_t z) {
@@ -1014,10 +1016,17 @@ __global__ void __launch_bounds__(256) k_lanczos(const __grid_constant__ Lanczos
     }
     const double bhi = a.safety * ext[1];
     const double blo = fmax(ext[0], bhi / a.ratio);
-    a.ritz[2 * (size_t)pid] = ext[0];
-    a.ritz[2 * (size_t)pid + 1] = ext[1];
-    a.bounds[2 * (size_t)pid] = T(blo);
-    a.bounds[2 * (size_t)pid + 1] = T(bhi);
+    const size_t o = 2 * (size_t)((int64_t)pid - a.out_offset);
+    a.ritz[o] = ext[0];
+    a.ritz[o + 1] = ext[1];
+    if (a.bounds) {
+      a.bounds[o] = T(blo);
+      a.bounds[o + 1] = T(bhi);
+    }
+    if (a.bounds_f64) {
+      a.bounds_f64[o] = (double)T(blo);
+      a.bounds_f64[o + 1] = (double)T(bhi);
+    }
   }
 }
 

@@ -925,6 +925,8 @@ int pmg_compute_bounds(pmg_ctx* ctx, int source) {
         a.ratio = ctx->opt.bound_ratio;
         a.ritz = pl.ritz;
         a.bounds = pl.bounds64;
+        a.bounds_f64 = nullptr;
+        a.out_offset = 0;
         int r = d == 2 ? launch_lanczos<2, double>(pl.q, a, s) : launch_lanczos<3, double>(pl.q, a, s);
         if (r == ST_UNSUPPORTED) {
           // the FP64 working set does not fit: FP32 operator, FP64 Lanczos vectors
@@ -941,6 +943,8 @@ int pmg_compute_bounds(pmg_ctx* ctx, int source) {
           b.ratio = a.ratio;
           b.ritz = pl.ritz;
           b.bounds = pl.bounds32;
+          b.bounds_f64 = nullptr;
+          b.out_offset = 0;
           if (!pl.G32) {   // FP64 contexts: an FP32 copy of the geometry for the interval estimates only
             const size_t ng = h.ncells * (size_t)(d * (d + 1) / 2) * ipow_sz(pl.q + 1, d);
             DALLOC(pl.G32, ng);
@@ -1667,6 +1671,8 @@ int lanczos_view(const pmg_ctx* ctx, int level, int k, LanczosView* v) {
   v->npatch = (int64_t)h.npatch;
   v->G64 = h.pl[k].G64;
   v->dinv64 = h.pl[k].dinv64;
+  v->G32 = h.pl[k].G32;
+  v->dinv32 = h.pl[k].dinv32;
   v->seed = ctx->opt.seed;
   v->safety = ctx->opt.bound_safety;
   v->ratio = ctx->opt.bound_ratio;

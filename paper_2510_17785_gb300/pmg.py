@@ -257,6 +257,7 @@ class Context:
         if rc != PMG_OK:
             raise PMGError(rc, "pmg_create failed")
         self.h = h
+        self.device = int(device)
         self.options = opt
         self.dim = self.N = self.p = self.n_levels = None
 
@@ -421,8 +422,20 @@ class Context:
 
     def lanczos_bounds_noalloc(self, level, k, first_patch, n_patches, ritz, bounds, stream=None):
         """Lanczos intervals for a patch range without any device allocation
-        (see include/pmg.h); ritz and bounds are float64 CUDA tensors of
-        n_patches x 2 values."""
+        (see include/pmg.h); ritz and bounds are contiguous float64 CUDA
+        tensors of at least n_patches x 2 values on the context's device.
+        The C side receives bare pointers and cannot check their size or type,
+        so this wrapper does, before the call."""
+        import torch
+        for name, t in (("ritz", ritz), ("bounds", bounds)):
+            if not hasattr(t, "is_cuda") or not t.is_cuda:
+                raise TypeError(f"{name} must be a CUDA tensor")
+            if t.dtype != torch.float64:
+                raise TypeError(f"{name} must be float64, got {t.dtype}")
+            if t.device.index != self.device:
+                raise ValueError(f"{name} is on cuda:{t.device.index}, the context on cuda:{self.device}")
+            if t.numel() < 2 * int(n_patches):
+                raise ValueError(f"{name} holds {t.numel()} values, needs 2 * n_patches = {2 * int(n_patches)}")
         self._check(self.lib.pmg_lanczos_bounds_noalloc(self.h, level, k, first_patch, n_patches, _ptr(ritz),
                                                         _ptr(bounds), _stream(stream)))
 

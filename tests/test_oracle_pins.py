@@ -312,21 +312,75 @@ def test_vcycle_symmetric_contractive_and_exact_limit(dim, p, kind):
     assert anorm(x - d) < 1e-6 * anorm(x)
 
 
-def test_single_patch_iterations_loose_paper_pin():
+def test_paper_level_sequence():
+    """Section 3.2 ("Baseline Performance"): p-levels come from the nested
+    sequence 1, 3, 7, 15, ... (p_{k+1} = 2 p_k + 1) with p itself on top; the
+    text prints {1, 3, 7, 8} for p = 8."""
+    assert pt.levels_paper(8) == [8, 7, 3, 1]
+    assert pt.levels_paper(7) == [7, 3, 1]
+    assert pt.levels_paper(15) == [15, 7, 3, 1]
+    assert pt.levels_paper(3) == [3, 1]
+    assert pt.levels_paper(4) == [4, 3, 1]
+
+
+def _single_patch_cg_iterations(dim, p):
+    m = _mesh(dim, 2, 0.0, 0)
+    P = pt.Patch(m, (1,) * dim, pt.levels_paper(p))
+    sm = pt.Smoother(kind="jacobi", omega=0.5)
+    b = np.random.default_rng(0).uniform(-1, 1, len(P.lv[p].diag))
+    _, it, _ = gmg.pcg(P.lv[p].A, b, lambda r: pt.local_solve(P, r, sm, {}), 1e-8, 100)
+    return it
+
+
+def test_single_patch_iterations_paper_pin():
     """Section 3.2 (text of fig:iter_vs_p_Jacobi_cartesian): CG with one Jacobi
-    p-MG V-cycle on an undeformed 2D Cartesian patch takes about 10 iterations
-    at p = 3.  A loose check: within +-3 of the printed value."""
-    rows = _read_golden("single_patch_iterations.txt")
-    for dim, p, approx in rows:
-        dim, p, approx = int(dim), int(p), int(approx)
-        if p > 7:
-            continue          # p = 15 is covered by the slow test below
-        m = _mesh(dim, 2, 0.0, 0)
-        P = pt.Patch(m, (1,) * dim, pt.levels_paper(p))
-        sm = pt.Smoother(kind="jacobi", omega=0.5)
-        b = np.random.default_rng(0).uniform(-1, 1, len(P.lv[p].diag))
-        _, it, _ = gmg.pcg(P.lv[p].A, b, lambda r: pt.local_solve(P, r, sm, {}), 1e-8, 100)
-        assert abs(it - approx) <= 3, (p, it)
+    (omega = 1/2) p-MG V-cycle on an undeformed 2D Cartesian patch takes
+    "about 10" iterations at p = 3 and "about 23" at p = 15.  The paper prints
+    only these two approximate values, so each is checked within 20% (at least
+    3 iterations), and the growth between them, the figure's main claim,
+    within 2.3 +- 0.4.  The oracle measures 12 and 27 (ratio 2.25)."""
+    rows = {int(p): int(a) for d, p, a in _read_golden("single_patch_iterations.txt") if int(d) == 2}
+    its = {p: _single_patch_cg_iterations(2, p) for p in rows}
+    for p, approx in rows.items():
+        assert abs(its[p] - approx) <= max(3, 0.2 * approx), (p, its[p], approx)
+    ratio = its[15] / its[3]
+    assert abs(ratio - rows[15] / rows[3]) <= 0.4, (its, ratio)
+
+
+# ------------------------------------------------------------ coarse kappa
+def test_coarse_kappa_rules_hand_computed():
+    """The coefficient of a coarse cell is the arithmetic (default),
+    geometric or harmonic mean of the coefficients of its 2^d children (the
+    paper does not say which; the children of coarse cell (I, J[, K]) are the
+    fine cells (2I + a, 2J + b[, 2K + c])).  Checked against hand-written
+    loops over distinct per-cell values, and against the closed forms of a
+    2 x 2 -> 1 case."""
+    one = _mesh(2, 2, 0.0, 0)
+    one.kappa[:] = [1.0, 2.0, 3.0, 10.0]
+    assert gmg.coarsen(one).kappa[0] == pytest.approx(4.0, rel=1e-15)
+    assert gmg.coarsen(one, "geometric").kappa[0] == pytest.approx(60.0 ** 0.25, rel=1e-14)
+    assert gmg.coarsen(one, "harmonic").kappa[0] == pytest.approx(4.0 / (1 + 1 / 2 + 1 / 3 + 1 / 10), rel=1e-14)
+    for dim, N in ((2, 4), (3, 4)):
+        m = _mesh(dim, N, 0.2, 5)
+        m.kappa[:] = 1.0 + np.arange(N ** dim) ** 1.5      # distinct values, cell id = x + N y (+ N^2 z)
+        Nc = N // 2
+        for rule, mean in (("arithmetic", lambda v: sum(v) / len(v)),
+                           ("geometric", lambda v: math.exp(sum(math.log(t) for t in v) / len(v))),
+                           ("harmonic", lambda v: len(v) / sum(1.0 / t for t in v))):
+            c = gmg.coarsen(m, rule)
+            for cc in range(Nc ** dim):
+                I = [(cc // Nc ** k) % Nc for k in range(dim)]
+                kids = []
+                for s in range(2 ** dim):
+                    f = [2 * I[k] + ((s >> k) & 1) for k in range(dim)]
+                    kids.append(m.kappa[sum(f[k] * N ** k for k in range(dim))])
+                assert c.kappa[cc] == pytest.approx(mean(kids), rel=1e-13), (dim, rule, cc)
+        # coarse vertices are the even-index fine vertices
+        c = gmg.coarsen(m)
+        for vc in range((Nc + 1) ** dim):
+            V = [(vc // (Nc + 1) ** k) % (Nc + 1) for k in range(dim)]
+            vf = sum(2 * V[k] * (N + 1) ** k for k in range(dim))
+            assert np.array_equal(c.coords[vc], m.coords[vf])
 
 
 # ------------------------------------------------------------------- sweeps
