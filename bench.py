@@ -29,8 +29,9 @@ sys.path.insert(0, ROOT)
 FP32_PEAK_DERIVED = 152 * 128 * 2 * 2.070e9      # SMs x FP32 lanes x 2 flops x max SM clock
 FP64_PEAK_NOMINAL = 1.25e12                      # GB300 FP64 rate (nominal)
 # DRAM bytes (read + write) of one finest-level colour launch of the FP32 patch kernel on the 3D Q4 32^3
-# workload (colour 0, 3,375 patches), from one ncu capture of the current kernel
-PATCH_LAUNCH_TRAFFIC = 114.047488e6 + 78.020608e6
+# workload (colour 0, 3,375 patches), from the ncu capture summarised in profiles/k_patch_q4_f32_sweep.md;
+# None while the kernel has changed since that capture
+PATCH_LAUNCH_TRAFFIC = None
 METRIC = "patch-smoother DoFs/s and CG time-to-1e-8 residual: mixed/learned vs plain FP64, 1 GB300"
 
 
@@ -46,6 +47,17 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-interval arm")
     ap.add_argument("--batch", type=int, default=0,
                     help="instead: K independent problems (3D, 8^3 cells, degrees 2/4/6/8) solved together")
+    ap.add_argument("--no-c3", action="store_true", help="skip the 48^3 Q7 sub-record (workloads.c3)")
+    ap.add_argument("--sweep-only", action="store_true",
+                    help="instead: set up one problem and run a few finest-level patch sweeps inside the NVTX "
+                         "range 'sweeps' (a small driver for kernel captures)")
+    ap.add_argument("--N", type=int, default=16, help="--sweep-only: cells per direction")
+    ap.add_argument("--p", type=int, default=4, help="--sweep-only: degree")
+    ap.add_argument("--dim", type=int, default=3, help="--sweep-only: dimension")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"], help="--sweep-only")
+    ap.add_argument("--sweeps", type=int, default=3, help="--sweep-only: sweeps inside the range")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="--sweep-only: launch-shape variant without set-up timing (default: autotuned)")
     return ap.parse_args()
 
 
@@ -100,68 +112,142 @@ class Clocks:
 
 
 # ---------------------------------------------------------- CPU baseline
-CPU_SCRIPT = r"""
-import json, sys, time
-import numpy as np
-sys.path.insert(0, {root!r})
-from oracle import fem, lanczos as lz, patch as pt
-from paper_2510_17785_gb300 import inputs
-w = inputs.WORKLOADS[{workload!r}]
-prob = inputs.make_problem(w)
-m = fem.StructuredMesh(w.dim, w.N, prob.coords, prob.kappa)
-verts = pt.interior_vertices(w.dim, w.N)
-rng = np.random.default_rng(1234)
-pick = [verts[i] for i in rng.choice(len(verts), {npatch}, replace=False)]
-u = inputs.random_vector(5, w.dim, w.p, w.N)
-b = inputs.random_vector(6, w.dim, w.p, w.N)
-t0 = time.perf_counter()
-patches = []
-for v in pick:
-    P = pt.Patch(m, v, pt.levels_halving(w.p))
-    patches.append((P, lz.lanczos_bounds_fn(seed=0)(P, pt.patch_id(w.dim, w.N, v))))
-t_build = (time.perf_counter() - t0) / len(pick)
-sm = pt.Smoother()
-t0 = time.perf_counter()
-for rep in range({reps}):
-    for P, bd in patches:
-        d = pt.local_solve(P, P.residual(u, b), sm, bd, 1)
-t_visit = (time.perf_counter() - t0) / ({reps} * len(pick))
-print(json.dumps(dict(t_build=t_build, t_visit=t_visit, npatch=len(pick), reps={reps})))
-"""
+# The oracle (plain FP64 numpy, dense patch matrices) timed on the host cores
+# of the GPU machine.  It runs in a child process with no GPU visible, which
+# spreads a bounded sample of finest-level patches over a spawn pool with one
+# single-threaded worker per core: every worker builds its patches' dense
+# level matrices and Lanczos intervals (set-up, timed apart), then times
+# Evaluate + one local V-cycle per visit.  All workers run at once, so the
+# aggregate visit rate includes their contention for memory bandwidth.
 
-
-def oracle_patch_times(workload: str, npatch: int, reps: int):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    code = CPU_SCRIPT.format(root=ROOT, workload=workload, npatch=npatch, reps=reps)
+def _oracle_sample_worker(task):
+    """One worker: (workload name, vertex indices, visits per patch) ->
+    timings.  Imports the oracle only here, in the spawned process."""
+    import numpy as np
+    from oracle import fem, lanczos as lz, patch as pt
+    from paper_2510_17785_gb300 import inputs
+    wname, vids, reps, dims = task
+    w = inputs.WORKLOADS[wname] if wname in inputs.WORKLOADS else inputs.Workload(wname, *dims)
+    prob = inputs.make_problem(w)
+    m = fem.StructuredMesh(w.dim, w.N, prob.coords, prob.kappa)
+    verts = pt.interior_vertices(w.dim, w.N)
+    u = inputs.random_vector(5, w.dim, w.p, w.N)
+    b = inputs.random_vector(6, w.dim, w.p, w.N)
     t0 = time.perf_counter()
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
-    if r.returncode != 0:
-        raise RuntimeError(r.stderr[-2000:])
-    out = json.loads(r.stdout.strip().splitlines()[-1])
-    out["wall_s"] = time.perf_counter() - t0
+    patches = []
+    for vi in vids:
+        P = pt.Patch(m, verts[vi], pt.levels_halving(w.p))
+        patches.append((P, lz.lanczos_bounds_fn(seed=0)(P, pt.patch_id(w.dim, w.N, verts[vi]))))
+    t_build = time.perf_counter() - t0
+    sm = pt.Smoother()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        for P, bd in patches:
+            pt.local_solve(P, P.residual(u, b), sm, bd, 1)
+    return {"t_build": t_build, "t_visits": time.perf_counter() - t0, "visits": reps * len(vids),
+            "patches": len(vids)}
+
+
+def _oracle_iterations_worker(task):
+    """The oracle's own GMG-preconditioned CG iteration count on a small
+    problem of the workload's kind (same degree, perturbation law,
+    coefficient and right-hand-side kind)."""
+    import numpy as np
+    from oracle import fem, gmg, lanczos as lz, patch as pt
+    from paper_2510_17785_gb300 import inputs
+    wname, N = task
+    w = inputs.WORKLOADS[wname].with_(name=f"{wname}_small", N=N, seed=inputs.WORKLOADS[wname].seed + 17)
+    prob = inputs.make_problem(w)
+    m = fem.StructuredMesh(w.dim, N, prob.coords, prob.kappa)
+    G = gmg.GMG(m, w.p, w.coarse_N, smoother_args=dict(sm=pt.Smoother(), bounds_fn=lz.lanczos_bounds_fn(seed=0)))
+    free = G.free[-1]
+    if w.rhs == "manufactured":
+        f = lambda X: w.dim * np.pi ** 2 * np.prod(np.sin(np.pi * X), axis=1)
+        b = m.load_vector(f, w.p, w.p + 2) * free
+    else:
+        b = prob.rhs * free
+    _, it, hist = gmg.pcg(G.A[-1], b, G.vcycle, 1e-8, 200)
+    return {"iterations": it, "relres": hist[-1], "N": N}
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _cpu_child(spec: dict) -> dict:
+    """Runs in the GPU-less child: the parallel sample (and, if asked, the
+    oracle's iteration count first)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import numpy as np
+    from oracle import patch as pt
+    from paper_2510_17785_gb300 import inputs
+    cores = os.cpu_count() or 1
+    w = inputs.WORKLOADS[spec["workload"]]
+    nv = len(pt.interior_vertices(w.dim, w.N))
+    rng = np.random.default_rng(1234 + spec.get("seed", 0))
+    per = spec["patches_per_core"]
+    pick = rng.choice(nv, size=min(nv, cores * per), replace=False)
+    tasks = [(w.name, [int(v) for v in pick[i::cores]], spec["reps"], None) for i in range(cores)]
+    out = {"cores": cores, "cpu": cpu_model()}
+    ctx = mp.get_context("spawn")
+    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=ctx) as ex:
+        if spec.get("iterations_N"):
+            out["oracle_cg"] = ex.submit(_oracle_iterations_worker, (w.name, spec["iterations_N"])).result()
+        t0 = time.perf_counter()
+        res = list(ex.map(_oracle_sample_worker, [t for t in tasks if t[1]]))
+        out["wall_s"] = time.perf_counter() - t0
+    out["visit_rate"] = sum(r["visits"] / r["t_visits"] for r in res)          # visits / s, all cores together
+    out["t_visit_core"] = sum(r["t_visits"] for r in res) / sum(r["visits"] for r in res)
+    out["t_build_core"] = sum(r["t_build"] for r in res) / sum(r["patches"] for r in res)
+    out["patches"] = sum(r["patches"] for r in res)
+    out["visits"] = sum(r["visits"] for r in res)
     return out
 
 
-def oracle_solve_estimate(w, levels: int, iters: int, t_visit: float) -> float:
-    """Patch work of one solve: every V-cycle visits every patch of every
-    smoothed level twice (forward and reverse sweep)."""
+def oracle_cpu_sample(workload: str, patches_per_core: int, reps: int, iterations_N: int = 0, seed: int = 0):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    spec = dict(workload=workload, patches_per_core=patches_per_core, reps=reps, iterations_N=iterations_N,
+                seed=seed)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-child", json.dumps(spec)],
+                       capture_output=True, text=True, env=env, timeout=1200)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def solve_visits(w, levels: int) -> int:
+    """Patch visits of one GMG-PCG iteration: every V-cycle sweeps every
+    smoothed mesh level twice (forward and reverse)."""
     visits = 0
     for l in range(1, levels):
         Nl = w.N >> (levels - 1 - l)
         visits += 2 * (Nl - 1) ** w.dim
-    return iters * visits * t_visit
+    return visits
 
 
-def cpu_baseline(w, levels, iters, npatch=48, reps=4):
-    t = oracle_patch_times(w.name, npatch, reps)
-    t_solve = oracle_solve_estimate(w, levels, iters, t["t_visit"])
+def cpu_baseline(w, levels, iters, patches_per_core=2, reps=20):
+    t = oracle_cpu_sample(w.name, patches_per_core, reps)
+    t_solve = iters * solve_visits(w, levels) / t["visit_rate"]
     return {
-        "value": w.n_free / t_solve, "unit": "DoFs/s", "cores": 1, "kind": "oracle",
-        "sample": (f"{t['npatch']} seeded patches of the finest level, {t['reps']} Evaluate+V-cycle visits each "
-                   f"(dense FP64 patch matrices built once, {t['t_build']*1e3:.1f} ms/patch, not counted); "
-                   f"{t['t_visit']*1e3:.3f} ms per visit x {iters} CG iterations x 2 sweeps x all patches of "
-                   f"levels 1..{levels-1}: patch work only, extrapolated ({t['wall_s']:.1f} s of CPU work)"),
+        "value": w.n_free / t_solve, "unit": "DoFs/s", "cores": t["cores"], "kind": "oracle", "cpu": t["cpu"],
+        "sample": (f"{t['patches']} seeded finest-level patches on {t['cores']} cores (one single-threaded "
+                   f"worker each, all at once), {reps} Evaluate + V-cycle visits per patch: "
+                   f"{t['visit_rate']:.0f} visits/s together ({t['t_visit_core'] * 1e3:.3f} ms per visit per "
+                   f"core); extrapolated to {iters} CG iterations x 2 sweeps x all patches of levels 1..{levels - 1} "
+                   f"(patch work only: the oracle's global matrix-vector products are not counted; building the "
+                   f"dense patch matrices is set-up, {t['t_build_core'] * 1e3:.0f} ms per patch per core, not "
+                   f"counted); {t['wall_s']:.1f} s wall"),
+        "extrapolated": True,
         "t_solve_extrapolated_s": t_solve,
     }
 
@@ -182,6 +268,45 @@ def aggregate(t_local_ms: float, n_free_local: int, dist: bool):
         td.all_reduce(nn, op=td.ReduceOp.SUM)
         t_max, n_total = float(tt.item()), int(nn.item())
     return t_max, n_total / (t_max * 1e-3)
+
+
+# ------------------------------------------------------------ sweep only
+def run_sweep_only(args):
+    """Set up one problem (unit cube/square, N cells per direction, degree p,
+    U(-0.25h, 0.25h) vertex perturbation, kappa = 1) and run `sweeps`
+    finest-level patch sweeps inside the NVTX range "sweeps", then one
+    operator apply.  For kernel captures on cases far smaller than the
+    benchmark:  ncu --nvtx --nvtx-include "sweeps/" -k regex:k_patch ..."""
+    import torch
+    from paper_2510_17785_gb300 import inputs, pmg
+
+    levels, n = 1, args.N
+    while n % 2 == 0 and n // 2 >= 2:
+        levels, n = levels + 1, n // 2
+    w = inputs.Workload(f"sweep_{args.dim}d_q{args.p}_n{args.N}", args.dim, args.N, args.p, 0.25, "uniform",
+                        ("const", 1.0), "uniform", 77)
+    prob = inputs.make_problem(w)
+    prec = pmg.PREC_MIXED if args.precision == "mixed" else pmg.PREC_FP64
+    tune = dict(autotune=0, variant=args.variant) if args.variant >= 0 else {}
+    ctx = pmg.Context(0, precision=prec, **tune)
+    ctx.mesh_structured(w.dim, w.N, w.p, levels, prob.coords, prob.kappa)
+    ctx.setup()
+    b = torch.tensor(prob.rhs, device="cuda")
+    u = torch.zeros_like(b)
+    lf = levels - 1
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("sweeps")
+    for _ in range(args.sweeps):
+        ctx.patch_smooth(lf, b, u, 1, False)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    Au = torch.zeros_like(b)
+    ctx.apply(lf, u, Au)
+    torch.cuda.synchronize()
+    print(json.dumps({"sweep_only": w.name, "sweeps": args.sweeps, "tuning": ctx.tuning(),
+                      "level_tuning": [ctx.tuning_level(lv) for lv in range(levels)],
+                      "u_max": float(u.abs().max())}))
+    ctx.close()
 
 
 # ------------------------------------------------------------------ ours
@@ -239,6 +364,67 @@ def learned_arm(w, levels, local, timed_solves, dev):
     ctx.close()
     out.update(ms=ms, its=its, train_s=t_train, samples=int(X.shape[0]), train_problems=len(train),
                loss=[float(hist[0]), float(hist[-1])])
+    return out
+
+
+def c3_record(local, dev, flush, stream, fma32):
+    """The 3D Q7 48^3 workload (kappa = 10^U(-3,3) per cell, random
+    right-hand side, GMG 48 -> 3): set-up, the finest-level FP32 sweep and its
+    roofline fraction, one mixed-precision GMG-PCG solve to 1e-8, and the
+    difference between one FP32 and one FP64 sweep from the same state."""
+    import torch
+    from paper_2510_17785_gb300 import inputs, pmg
+
+    w = inputs.C3
+    levels = int(round(math.log2(w.N // w.coarse_N))) + 1
+    prob = inputs.make_problem(w)
+    out = {"workload": w.name, "dim": w.dim, "cells_per_dir": w.N, "p": w.p, "n_free": w.n_free,
+           "h_levels": levels}
+
+    def ev_time(fn):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), r
+
+    b = torch.tensor(prob.rhs, device=dev)
+    u_sw = {}
+    for name, prec in (("mixed", pmg.PREC_MIXED), ("fp64", pmg.PREC_FP64)):
+        ctx = pmg.Context(local, precision=prec)
+        ctx.mesh_structured(w.dim, w.N, w.p, levels, prob.coords, prob.kappa)
+        t0 = time.perf_counter()
+        ctx.setup()
+        t_setup = time.perf_counter() - t0
+        lf = levels - 1
+        u = torch.zeros_like(b)
+        ctx.patch_smooth(lf, b, u, 1, False)             # one sweep from u = 0, kept for the comparison
+        torch.cuda.synchronize()
+        u_sw[name] = u.clone()
+        nsw = 3 if name == "mixed" else 1
+        ms, _ = ev_time(lambda: ctx.patch_smooth(lf, b, u, nsw, False))
+        t_sweep = ms / nsw * 1e-3
+        flops = ctx.sweep_flops(lf)
+        rec = {"setup_s": t_setup, "sweep_ms": t_sweep * 1e3, "sweep_dofs_per_s": w.n_free / t_sweep,
+               "sweep_flops": flops}
+        if name == "mixed":
+            rec["roofline"] = {"bound": "alu", "achieved": flops / t_sweep / 1e12, "unit": "TFLOP/s",
+                               "peak": FP32_PEAK_DERIVED / 1e12, "frac": flops / t_sweep / FP32_PEAK_DERIVED,
+                               "frac_of_measured_fma": flops / t_sweep / fma32,
+                               "kernel": "k_patch<3,7,float,SWEEP,variant> (finest-level sweep, 8 colour launches)"}
+            x = torch.zeros_like(b)
+            ctx.solve_cg(b, x, 1e-8, 300)                 # warm-up (captures the iteration graph)
+            x.zero_()
+            ms, (it, rel, _) = ev_time(lambda: ctx.solve_cg(b, x, 1e-8, 300))
+            rec.update(solve_ms=ms, cg_iterations=it, final_relres=rel, dofs_per_s=w.n_free / (ms * 1e-3),
+                       tuning_level_variants=[ctx.tuning_level(lv)[0] for lv in range(levels)])
+        out[name] = rec
+        ctx.close()
+    ref = u_sw["fp64"]
+    out["mixed_vs_fp64_one_sweep_rel_max_err"] = float((u_sw["mixed"] - ref).abs().max() / ref.abs().max())
     return out
 
 
@@ -415,6 +601,8 @@ def run_ours(args):
 
     if not args.no_learned:
         result["learned"] = learned_arm(w, levels, local, timed_solves, dev)
+    if not args.no_c3 and world == 1:
+        result["c3"] = c3_record(local, dev, flush, stream, result["fma32"])
 
     head = result["mixed"]
     t_step = sum(head["ms"]) / len(head["ms"])
@@ -456,7 +644,8 @@ def run_ours(args):
             "peak": FP32_PEAK_DERIVED / 1e12, "unit": "TFLOP/s",
             "frac": achieved / FP32_PEAK_DERIVED,
             "traffic": PATCH_LAUNCH_TRAFFIC if w.name == "c2_3d_q4_n32_perturbed" else None,
-            "traffic_note": "DRAM bytes of one colour launch (colour 0, 3,375 patches) from an ncu capture",
+            "traffic_note": ("DRAM bytes of one colour launch (colour 0, 3,375 patches) from the ncu capture of "
+                             "profiles/k_patch_q4_f32_sweep.md (null: kernel changed since)"),
             "kernel": "k_patch<3,4,float,SWEEP,variant> (finest-level patch sweep, 8 colour launches)",
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
             "measured_fma_peak": result["fma32"] / 1e12,
@@ -495,6 +684,8 @@ def run_ours(args):
             "note": "mixed precision; Chebyshev intervals from the BF16 MLP (16-64-64-2) trained in this run on "
                     "Lanczos estimates of three small problems of the same degree",
         }
+    if "c3" in result:
+        out["workloads"] = {"c3": result["c3"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         its = int(statistics.median(i for i, _ in head["its"]))
         out["cpu_baseline"] = cpu_baseline(w, levels, its)
@@ -507,37 +698,54 @@ def run_ours(args):
 
 # -------------------------------------------------------------- reference
 def run_reference(args):
+    """The oracle on the host cores, on the workload of our arm.  Its CG
+    iteration count is the oracle's own (GMG-PCG on the same kind of problem
+    at twice the coarsest mesh size: the GPU path is never consulted); every step
+    times a bounded sample of patch visits on all cores and extrapolates the
+    solve's patch work from it (labelled)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from paper_2510_17785_gb300 import inputs
     w = inputs.WORKLOADS[args.workload]
     levels = int(round(math.log2(w.N // w.coarse_N))) + 1
-    iters = 7          # CG iterations the GPU solver needs on this workload (both precisions, measured)
+    first = oracle_cpu_sample(w.name, 1, 40, iterations_N=2 * w.coarse_N)
+    iters = first["oracle_cg"]["iterations"]
     vals = []
     for i in range(args.warmup + args.steps):
-        t = oracle_patch_times(w.name, 12, 2)
-        v = w.n_free / oracle_solve_estimate(w, levels, iters, t["t_visit"])
+        t = oracle_cpu_sample(w.name, 1, 40, seed=i + 1)
+        v = w.n_free / (iters * solve_visits(w, levels) / t["visit_rate"])
         if i >= args.warmup:
             vals.append((v, t))
     v = statistics.mean(x for x, _ in vals)
+    t = vals[-1][1]
     ms = w.n_free / v * 1e3
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "DoFs/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "dim": w.dim, "cells_per_dir": w.N, "p": w.p, "n_free": w.n_free},
-        "cpu_baseline": {"value": v, "unit": "DoFs/s", "cores": 1, "kind": "oracle",
-                         "sample": "12 seeded finest-level patches x 2 Evaluate+V-cycle visits per step; "
-                                   f"extrapolated to {iters} CG iterations x 2 sweeps x all patches"},
+        "cpu_baseline": {"value": v, "unit": "DoFs/s", "cores": t["cores"], "kind": "oracle", "cpu": t["cpu"],
+                         "sample": (f"per step: {t['patches']} seeded finest-level patches on {t['cores']} cores, "
+                                    f"40 Evaluate + V-cycle visits each; extrapolated (labelled) to {iters} CG "
+                                    f"iterations x 2 sweeps x all patches of levels 1..{levels - 1}, patch work only; "
+                                    f"the iteration count is the oracle's own GMG-PCG on the same kind of problem "
+                                    f"with {first['oracle_cg']['N']} cells per direction (relres "
+                                    f"{first['oracle_cg']['relres']:.1e})"),
+                         "extrapolated": True},
         "e2e": {"value": v, "unit": "DoFs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
 
 if __name__ == "__main__":
+    if len(sys.argv) == 3 and sys.argv[1] == "--cpu-child":
+        print(json.dumps(_cpu_child(json.loads(sys.argv[2]))))
+        sys.exit(0)
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.sweep_only:
+        run_sweep_only(a)
     elif a.batch > 0:
         run_batch(a)
     else:

@@ -46,6 +46,9 @@ enum {
   PMG_ERR_UNSUPPORTED = 7    /* e.g. p > 8, or a precision/degree combination  */
 };
 
+/* Number of launch-shape variants of the patch-sweep kernel (pmg_tuning). */
+#define PMG_NUM_VARIANTS 10
+
 /* ---- options ----------------------------------------------------------- */
 enum { PMG_SMOOTHER_CHEBYSHEV = 0, PMG_SMOOTHER_JACOBI = 1, PMG_SMOOTHER_CARTESIAN = 2 };
 enum { PMG_BOUNDS_LANCZOS = 0, PMG_BOUNDS_FIXED = 1, PMG_BOUNDS_USER = 2,
@@ -257,7 +260,7 @@ double pmg_sweep_flops(const pmg_ctx* ctx, int level);
 
 /* Launch shape chosen for the patch-sweep kernel: variant index, threads per
  * CTA, patches per CTA, and the set-up timings of the candidate variants
- * (ms for one colour of the finest level, ms_per_variant[8], -1 where a
+ * (ms for one colour of the finest level, ms_per_variant[PMG_NUM_VARIANTS], -1 where a
  * variant does not exist or was not timed).  Any output may be NULL.
  * Every variant computes bit-identical results. */
 int pmg_tuning(const pmg_ctx* ctx, int* variant, int* threads, int* patches_per_cta,
@@ -265,7 +268,7 @@ int pmg_tuning(const pmg_ctx* ctx, int* variant, int* threads, int* patches_per_
 /* Launch shape used on mesh level `level` (the set-up autotuner times every
  * variant on one colour of every level: large launches favour occupancy, the
  * small launches of coarse levels the latency of one patch) and its timings
- * (ms_per_variant[8], -1 where not timed).  Either output may be NULL. */
+ * (ms_per_variant[PMG_NUM_VARIANTS], -1 where not timed).  Either output may be NULL. */
 int pmg_tuning_level(const pmg_ctx* ctx, int level, int* variant, float* ms_per_variant);
 
 /* ---- learned Chebyshev intervals ------------------------------------------

@@ -65,10 +65,11 @@ def prolongation(coarse: fem.StructuredMesh, fine: fem.StructuredMesh, q: int) -
         fc = [min(m[a] // q, fine.N - 1) for a in range(d)]          # a fine cell holding the node
         cc = [fc[a] // 2 for a in range(d)]                           # its parent
         xi = [(fc[a] % 2 + gl[m[a] - q * fc[a]]) / 2.0 for a in range(d)]
+        lx = [rules.lagrange(gl, xi[a])[0] for a in range(d)]     # coarse basis along each axis at the node
         for loc in fem._lex(d, q + 1):
             val = 1.0
             for a in range(d):
-                val *= rules.lagrange(gl, xi[a])[0, loc[a]]
+                val *= lx[a][loc[a]]
             if abs(val) > 0.0:
                 rows.append(nf)
                 cols.append(coarse.node_index(q, [q * cc[a] + loc[a] for a in range(d)]))

@@ -262,9 +262,8 @@ __global__ void __launch_bounds__(NT) k_cell_apply(const T* __restrict__ u, T* _
     sm[cp * PS + i] = v;
   });
   __syncthreads();
-  const int* clp = cl;
-  auto gf = [G, clp](int cp, int) {
-    const int c = clp[2 * cp];
+  auto gf = [G](int cp, int) {
+    const int c = reinterpret_cast<const int*>(pmg_smem + sizeof(T) * PS * CPB)[2 * cp];
     return G + (size_t)(c < 0 ? 0 : c) * (Dm::NCOMP * Dm::NGC);
   };
   SF<DIM, 1, Q, T, NT, CPB>::template apply<false, false>(sm, PS, sm + NN, PS, sm + 2 * NN, PS, gf);

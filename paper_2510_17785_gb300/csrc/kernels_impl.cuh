@@ -75,6 +75,8 @@ int launch_patch_P(int mode, int variant, const PatchArgs<T>& a, cudaStream_t s)
       case 5: return launch_patch_PV<DIM, P, T, 5>(mode, a, s);
       case 6: return launch_patch_PV<DIM, P, T, 6>(mode, a, s);
       case 7: return launch_patch_PV<DIM, P, T, 7>(mode, a, s);
+      case 8: return launch_patch_PV<DIM, P, T, 8>(mode, a, s);
+      case 9: return launch_patch_PV<DIM, P, T, 9>(mode, a, s);
       default: return ST_UNSUPPORTED;
     }
   }
@@ -116,6 +118,8 @@ void patch_config_P(int variant, size_t* smem, int* ppb, int* nt) {
     case 5: return patch_config_PV<DIM, P, T, 5>(smem, ppb, nt);
     case 6: return patch_config_PV<DIM, P, T, 6>(smem, ppb, nt);
     case 7: return patch_config_PV<DIM, P, T, 7>(smem, ppb, nt);
+    case 8: return patch_config_PV<DIM, P, T, 8>(smem, ppb, nt);
+    case 9: return patch_config_PV<DIM, P, T, 9>(smem, ppb, nt);
     default: *smem = 0; *ppb = 0; *nt = 0;
   }
 }
@@ -176,12 +180,12 @@ template <int DIM>
 int launch_dense_patch(int q, const double* G64, int N, int first, int n, double* A, cudaStream_t s) {
   if (n <= 0) return ST_OK;
   switch (q) {
-    case 2: k_dense_patch<DIM, 2><<<n, 128, 0, s>>>(G64, N, first, n, A); break;
+    case 2: k_dense_patch<DIM, 2><<<n, 128, dense_patch_smem<DIM, 2>(), s>>>(G64, N, first, n, A); break;
     case 3:
-      if constexpr (DIM == 2) { k_dense_patch<DIM, 3><<<n, 128, 0, s>>>(G64, N, first, n, A); break; }
+      if constexpr (DIM == 2) { k_dense_patch<DIM, 3><<<n, 128, dense_patch_smem<DIM, 3>(), s>>>(G64, N, first, n, A); break; }
       return ST_UNSUPPORTED;
     case 4:
-      if constexpr (DIM == 2) { k_dense_patch<DIM, 4><<<n, 128, 0, s>>>(G64, N, first, n, A); break; }
+      if constexpr (DIM == 2) { k_dense_patch<DIM, 4><<<n, 128, dense_patch_smem<DIM, 4>(), s>>>(G64, N, first, n, A); break; }
       return ST_UNSUPPORTED;
     default: return ST_UNSUPPORTED;
   }

@@ -16,6 +16,7 @@
 // the 2^d-cell patch, with the per-point geometry tensors G read from global
 // memory (L1/L2 resident across the applies of one patch).
 #pragma once
+#include "../../include/pmg.h"
 #include "sf.cuh"
 
 namespace pmg {
@@ -72,6 +73,12 @@ struct PatchEpi {
   int kind;
   int r, d, res, dir, dinv, ad, coef, it;
   T omega;
+  // the patch arrays start at the kernel's dynamic shared memory
+  __device__ __forceinline__ PatchEpi rebase() const {
+    PatchEpi e = *this;
+    e.sm = reinterpret_cast<T*>(pmg_smem);
+    return e;
+  }
   __device__ __forceinline__ void operator()(int pp, int i, T s) const {
     T* b = sm + pp * PS;
     switch (kind) {
@@ -144,31 +151,33 @@ struct Layout {
 };
 
 // Launch shape of the patch kernel.  Variant 0 is the default; for 3D degrees
-// 3..8 the set-up autotuner also times variants 1..7:
-//   variant:          1        2        3        4        5        6        7
-//   design:         stage    stage    stage    line     line     line     line
-//   threads / CTA:    256      128      512      256      128      512      128
-//   patches / CTA:      2        1        1        2        1        1        2
-//   geometry:                          staged                     staged
-//   groups:                                                                 2
+// 3..8 the set-up autotuner also times variants 1..9:
+//   variant:          1      2      3      4      5      6      7      8      9
+//   design:         stage  stage  stage  line   line   line   line   line   stage
+//   threads / CTA:    256    128    512    256    128    512    128    256    256
+//   patches / CTA:      2      1      1      2      1      1      2      2      2
+//   geometry:                    staged                staged        staged staged
+//   groups:                                                   2
 // (patches per CTA are capped by shared memory).  "stage": every direction's
 // flux in shared memory; "line": one thread per line along the last
 // direction keeps that direction's gradient and flux in registers.  With
 // groups, each patch of the CTA has its own threads and barrier.  "staged":
-// latency-oriented shapes for small launches (coarse mesh levels), one patch
-// per 512 threads, the top level's geometry tensors copied to shared memory
-// once per patch instead of read from L2 by every apply.
-constexpr int NUM_VARIANTS = 8;
+// the top level's geometry tensors are copied to shared memory once per
+// patch instead of read from L2 by every apply; variants 3 and 6 are
+// latency-oriented shapes for small launches (coarse mesh levels, one patch
+// per 512 threads), 8 and 9 throughput shapes (two patches per 256 threads,
+// a 128-register budget, two CTAs per SM).
+constexpr int NUM_VARIANTS = PMG_NUM_VARIANTS;
 
 template <int DIM, int P, typename T, int V = 0>
 struct Config {
   static constexpr int NT0 = (DIM == 3) ? 256 : 128;
   static constexpr int PPB0 = (DIM == 3) ? (P <= 2 ? 4 : 1) : (P <= 2 ? 8 : (P <= 4 ? 4 : 2));
-  static constexpr int NTV[NUM_VARIANTS] = {NT0, 256, 128, 512, 256, 128, 512, 128};
-  static constexpr int PPBV[NUM_VARIANTS] = {PPB0, 2, 1, 1, 2, 1, 1, 2};
-  static constexpr bool LINEV[NUM_VARIANTS] = {false, false, false, false, true, true, true, true};
-  static constexpr bool GROUPV[NUM_VARIANTS] = {false, false, false, false, false, false, false, true};
-  static constexpr bool GSMEMV[NUM_VARIANTS] = {false, false, false, true, false, false, true, false};
+  static constexpr int NTV[NUM_VARIANTS] = {NT0, 256, 128, 512, 256, 128, 512, 128, 256, 256};
+  static constexpr int PPBV[NUM_VARIANTS] = {PPB0, 2, 1, 1, 2, 1, 1, 2, 2, 2};
+  static constexpr bool LINEV[NUM_VARIANTS] = {false, false, false, false, true, true, true, true, true, false};
+  static constexpr bool GROUPV[NUM_VARIANTS] = {false, false, false, false, false, false, false, true, false, false};
+  static constexpr bool GSMEMV[NUM_VARIANTS] = {false, false, false, true, false, false, true, false, true, true};
   static constexpr int NT = NTV[V];
   static constexpr int PPB_MAX = PPBV[V];
   static constexpr bool LINE = LINEV[V];
@@ -198,19 +207,12 @@ struct Config {
     return Config<DIM, P, T, W>::NT == NT && Config<DIM, P, T, W>::PPB == PPB && Config<DIM, P, T, W>::LINE == LINE &&
            Config<DIM, P, T, W>::GROUPED == GROUPED && Config<DIM, P, T, W>::GSMEM == GSMEM;
   }
-  static constexpr bool distinct_impl() {
-    if constexpr (V == 0) return true;
-    else if constexpr (V == 1) return !same_as<0>();
-    else if constexpr (V == 2) return !same_as<0>() && !same_as<1>();
-    else if constexpr (V == 3) return !same_as<0>() && !same_as<1>() && !same_as<2>();
-    else if constexpr (V == 4) return !same_as<0>() && !same_as<1>() && !same_as<2>() && !same_as<3>();
-    else if constexpr (V == 5) return !same_as<0>() && !same_as<1>() && !same_as<2>() && !same_as<3>() && !same_as<4>();
-    else if constexpr (V == 6)
-      return !same_as<0>() && !same_as<1>() && !same_as<2>() && !same_as<3>() && !same_as<4>() && !same_as<5>();
-    else
-      return !same_as<0>() && !same_as<1>() && !same_as<2>() && !same_as<3>() && !same_as<4>() && !same_as<5>() &&
-             !same_as<6>();
+  template <int W>
+  static constexpr bool distinct_from_lower() {
+    if constexpr (W >= V) return true;
+    else return !same_as<W>() && distinct_from_lower<W + 1>();
   }
+  static constexpr bool distinct_impl() { return distinct_from_lower<0>(); }
   static constexpr bool distinct = distinct_impl();
   // worth compiling: a line variant keeps at most two lines' gradients and
   // fluxes per thread in registers (more spills and bloats the build); FP64,
@@ -221,7 +223,8 @@ struct Config {
   static constexpr int SPAN_ = GROUPED ? 1 : PPB;
   static constexpr int LPT_ = (SPAN_ * ipow(QPL, DIM - 1) + TPP_ - 1) / TPP_;
   static constexpr bool worth = (!LINE || LPT_ <= 2) &&
-                                (sizeof(T) == 4 || V == 0 || ((V == 2 || V == 4 || V == 6) && P <= 6));
+                                (sizeof(T) == 4 || V == 0 || ((V == 2 || V == 4 || V == 6) && P <= 6)) &&
+                                (V < 8 || (DIM == 3 && P >= 3));
   static constexpr bool exists = fits && distinct && worth;
 };
 
@@ -245,12 +248,14 @@ struct PatchKernel {
     constexpr int q = P >> K;
     constexpr int stride = Dims<DIM, 2, q>::NCOMP * ipow(q + 1, DIM);
     if constexpr (C::GSMEM && K == 0) {                 // staged in shared memory by load_level
-      const T* gs = sm + L::GS;
-      return [gs](int pp, int slot) { return gs + pp * PS + slot * stride; };
+      return [](int pp, int slot) { return reinterpret_cast<const T*>(pmg_smem) + L::GS + pp * PS + slot * stride; };
     } else {
       const T* G = a->lv[K].G;
-      const int* cl = cells;
-      return [G, cl](int pp, int slot) { return G + (size_t)cl[pp * CST + slot] * stride; };
+      // the cell list follows the PPB patch arrays in dynamic shared memory
+      return [G](int pp, int slot) {
+        const int* cl = reinterpret_cast<const int*>(pmg_smem + sizeof(T) * (size_t)PS * PPB);
+        return G + (size_t)cl[pp * CST + slot] * stride;
+      };
     }
   }
 
@@ -806,8 +811,10 @@ __global__ void __launch_bounds__(128) k_dense_patch(const double* __restrict__ 
   using Dm = Dims<DIM, 2, Q>;
   constexpr int NI = Dm::NI;
   constexpr int NCELL = 1 << DIM;
-  __shared__ double x[NI], y[NI], scr[Dm::SCRATCH];
-  __shared__ int cl[NCELL];
+  double* x = reinterpret_cast<double*>(pmg_smem);
+  double* y = x + NI;
+  double* scr = y + NI;
+  int* cl = reinterpret_cast<int*>(scr + Dm::SCRATCH);
   const int item = blockIdx.x;
   if (item >= n_items) return;
   const int pid = first_patch + item;
@@ -822,8 +829,10 @@ __global__ void __launch_bounds__(128) k_dense_patch(const double* __restrict__ 
     }
     cl[threadIdx.x] = id;
   }
-  const int* clp = cl;
-  auto gf = [G, clp](int, int slot) { return G + (size_t)clp[slot] * (Dm::NCOMP * Dm::NGC); };
+  auto gf = [G](int, int slot) {
+    const int* clp = reinterpret_cast<const int*>(pmg_smem + sizeof(double) * (2 * NI + Dm::SCRATCH));
+    return G + (size_t)clp[slot] * (Dm::NCOMP * Dm::NGC);
+  };
   for (int i = 0; i < NI; ++i) {
     for (int r = threadIdx.x; r < NI; r += NT) x[r] = r == i ? 1.0 : 0.0;
     __syncthreads();
@@ -831,6 +840,12 @@ __global__ void __launch_bounds__(128) k_dense_patch(const double* __restrict__ 
     for (int r = threadIdx.x; r < NI; r += NT) A[((size_t)item * NI + r) * NI + i] = y[r];
     __syncthreads();
   }
+}
+
+template <int DIM, int Q>
+constexpr size_t dense_patch_smem() {
+  using Dm = Dims<DIM, 2, Q>;
+  return sizeof(double) * (2 * Dm::NI + Dm::SCRATCH) + sizeof(int) * (1 << DIM);
 }
 
 // ------------------------------------------------------------------------
@@ -911,6 +926,7 @@ __global__ void __launch_bounds__(256) k_lanczos(const __grid_constant__ Lanczos
   double* be = al + 64;                              // beta[ksteps]
   double* cf = be + 64;                              // CGS coefficients[ksteps]
   int* cl = reinterpret_cast<int*>(cf + 64);
+  const size_t cl_byte = reinterpret_cast<unsigned char*>(cl) - smem_raw;
 
   const int item = blockIdx.x;
   if (item >= a.n_items) return;
@@ -951,9 +967,10 @@ __global__ void __launch_bounds__(256) k_lanczos(const __grid_constant__ Lanczos
     for (int i = threadIdx.x; i < NI; i += NT) dv[i] /= nrm;
     __syncthreads();
   }
-  const int* clp = cl;
   const T* G = a.G;
-  auto gf = [G, clp](int, int slot) { return G + (size_t)clp[slot] * (Dm::NCOMP * Dm::NGC); };
+  auto gf = [G, cl_byte](int, int slot) {
+    return G + (size_t)reinterpret_cast<const int*>(pmg_smem + cl_byte)[slot] * (Dm::NCOMP * Dm::NGC);
+  };
   int nal = 0;
   for (int j = 0; j < k; ++j) {
     for (int i = threadIdx.x; i < NI; i += NT) {

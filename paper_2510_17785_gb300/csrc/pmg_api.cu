@@ -96,7 +96,7 @@ struct pmg_ctx {
   int64_t graph_launches_per_iter = 0;   // kernels recorded in one CG iteration graph
   int64_t launches = 0;                  // kernels launched so far
   int variant = 0;                       // launch shape of the patch-sweep kernel
-  float variant_ms[NUM_VARIANTS] = {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f};
+  float variant_ms[NUM_VARIANTS] = {};   // set-up timings of the finest level (-1: not timed)
   int level_variant[16] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};  // per mesh level
   float level_ms[16][NUM_VARIANTS] = {};  // set-up timings per mesh level (-1: not timed)
   float* mlp_params = nullptr;           // PMG_BOUNDS_MLP network and normalisation

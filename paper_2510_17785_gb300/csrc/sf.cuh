@@ -30,6 +30,20 @@
 namespace pmg {
 
 __host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+// Dynamic shared memory of the launching kernel: every kernel that applies
+// the operator keeps its vectors and scratch there.  A pointer into it that
+// crosses a non-inlined call is only a generic address to the callee, whose
+// loads and stores then go through the generic path; smem_ptr() re-derives
+// the same address from this __shared__ array so that they stay shared-memory
+// accesses.
+extern __shared__ __align__(16) unsigned char pmg_smem[];
+
+template <typename T>
+__device__ __forceinline__ T* smem_ptr(T* p) {
+  const unsigned off = (unsigned)(__cvta_generic_to_shared((const void*)p) - __cvta_generic_to_shared(pmg_smem));
+  return reinterpret_cast<T*>(pmg_smem + off);
+}
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
 template <int DIM, int NC, int Q>
@@ -255,8 +269,9 @@ struct SF {
   // ---- transposed derivative along the last axis, added to the partial sums
   // in Vp (the other directions), fused with the backward integration along
   // that axis: one item per line (both cells), output [Lo][I].
+  // (3D: the partial sums are the two arrays Vp + Vq)
   __device__ __forceinline__ static void dert_bwd_last_item(const T* __restrict__ F, const T* __restrict__ Vp,
-                                                            T* __restrict__ out, int i) {
+                                                            const T* __restrict__ Vq, T* __restrict__ out, int i) {
     constexpr int AX = DIM - 1;
     constexpr int I = ipow(QP, AX);
     T w[NC][n];
@@ -268,6 +283,7 @@ struct SF {
 #pragma unroll
       for (int h = 0; h < n; ++h) {
         T s = Vp[(c * n + h) * I + i];
+        if (DIM == 3) s += Vq[(c * n + h) * I + i];
 #pragma unroll
         for (int g = 0; g < n; ++g) s += tabD<T>(Q, g, h) * f[g];
         w[c][h] = s;
@@ -432,8 +448,10 @@ struct SF {
   // transposed derivative along the last axis (fz in registers) added to the
   // other directions' sums in Vp, then backward integration along that axis:
   // output [Lo][I]
-  __device__ __forceinline__ static void line_bwd(const T (&fz)[QP], const T* __restrict__ Vp, T* __restrict__ out,
-                                                  int i) {
+  // Vq: a second array of partial sums added to Vp (3D: the x and y
+  // directions' transposed derivatives), or NULL
+  __device__ __forceinline__ static void line_bwd(const T (&fz)[QP], const T* __restrict__ Vp,
+                                                  const T* __restrict__ Vq, T* __restrict__ out, int i) {
     constexpr int I = NLINE;
     T w[NC][n];
 #pragma unroll
@@ -441,6 +459,7 @@ struct SF {
 #pragma unroll
       for (int h = 0; h < n; ++h) {
         T s = Vp[(c * n + h) * I + i];
+        if (DIM == 3) s += Vq[(c * n + h) * I + i];
 #pragma unroll
         for (int g = 0; g < n; ++g) s += tabD<T>(Q, g, h) * fz[c * n + g];
         w[c][h] = s;
@@ -524,6 +543,28 @@ struct SF {
     }
   }
 
+  // ---- transposed derivative along AX in place: the thread reads its whole
+  // line before writing it back
+  template <int AX>
+  __device__ __forceinline__ static void dert_inplace_item(T* __restrict__ F, int item) {
+    constexpr int I = ipow(QP, AX);
+    const int i = item % I, o = item / I;
+    T* p = F + o * QP * I + i;
+    T v[QP];
+#pragma unroll
+    for (int g = 0; g < QP; ++g) v[g] = p[g * I];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+#pragma unroll
+      for (int h = 0; h < n; ++h) {
+        T s = T(0);
+#pragma unroll
+        for (int g = 0; g < n; ++g) s += tabD<T>(Q, g, h) * v[c * n + g];
+        p[(c * n + h) * I] = s;
+      }
+    }
+  }
+
   // ---- final backward integration along x: like bwd_item<0, false> but every
   // output value goes through put(pp, index, value) (the apply's epilogue)
   template <typename PUT>
@@ -590,21 +631,24 @@ struct SF {
         }
       }
       TM::sync();
-      TM::template loop<ND>([&](int pp, int it) { dert_item<0, false>(Rp(pp), Vp(pp), it); });
+      // transposed derivatives along x and y, each in place on its flux array
+      TM::template loop<2 * ND>([&](int pp, int it) {
+        const int ax = it / ND, r = it - ax * ND;
+        if (ax == 0) dert_inplace_item<0>(Rp(pp), r);
+        else dert_inplace_item<1>(Rp(pp) + NQ, r);
+      });
       TM::sync();
-      TM::template loop<ND>([&](int pp, int it) { dert_item<1, true>(Rp(pp) + NQ, Vp(pp), it); });
-      TM::sync();
-      constexpr int B1 = Lo * Lo * QP;       // [Lo][Lo][QP]
-      static_assert(B1 + Lo * QP * QP <= Dims<DIM, NC, Q>::R_LINE, "backward temporaries exceed R");
+      // z: their sum + D^T of the z flux, integrated along z into V [Lo][QP][QP]
+      static_assert(Lo * QP * QP <= NQ, "z output exceeds V");
 #pragma unroll
       for (int l = 0; l < LPT; ++l) {
         int pp, line;
         if (TM::template slot<NLINE>(l, pp, line)) {
-          line_bwd(fz[l], Vp(pp), Rp(pp) + B1, line);
+          line_bwd(fz[l], Rp(pp), Rp(pp) + NQ, Vp(pp), line);
         }
       }
       TM::sync();
-      TM::template loop<Lo * QP>([&](int pp, int it) { bwd_item<1, false>(Rp(pp) + B1, Rp(pp), it); });
+      TM::template loop<Lo * QP>([&](int pp, int it) { bwd_item<1, false>(Vp(pp), Rp(pp), it); });
       TM::sync();
       TM::template loop<Lo * Lo>([&](int pp, int it) { bwd0_item(Rp(pp), it, pp, epi); });
       TM::sync();
@@ -637,7 +681,7 @@ struct SF {
       for (int l = 0; l < LPT; ++l) {
         int pp, line;
         if (TM::template slot<NLINE>(l, pp, line)) {
-          line_bwd(fz[l], Vp(pp), Rp(pp), line);
+          line_bwd(fz[l], Vp(pp), nullptr, Rp(pp), line);
         }
       }
       TM::sync();
@@ -805,25 +849,20 @@ struct SF {
       TM::sync();
       quad_stage(scr, sscr, gcell);
       TM::sync();
-      dseg_stage<true, false, ND>([&](int pp, int r, const T*& src, T*& dst, int& st) {
-        const T* s0;
-        T* d0;
-        seg<0>(r, Rp(pp), Vp(pp), s0, d0, st);
-        src = s0;
-        dst = d0;
+      // transposed derivatives along x and y, each in place on its flux array
+      dseg_stage<true, false, 2 * ND>([&](int pp, int r2, const T*& src, T*& dst, int& st) {
+        const int ax = r2 / ND, r = r2 - ax * ND;
+        if (ax == 0) seg<0>(r, Rp(pp), Rp(pp), src, dst, st);
+        else seg<1>(r, Rp(pp) + NQ, Rp(pp) + NQ, src, dst, st);
       });
       TM::sync();
-      dseg_stage<true, true, ND>([&](int pp, int r, const T*& src, T*& dst, int& st) {
-        seg<1>(r, Rp(pp) + NQ, Vp(pp), src, dst, st);
+      // z: F_0 + F_1 + D^T F_2 -> B^T along z -> V [Lo][QP][QP]
+      static_assert(Lo * QP * QP <= NQ, "z output exceeds V");
+      TM::template loop<QP * QP>([&](int pp, int it) {
+        dert_bwd_last_item(Rp(pp) + 2 * NQ, Rp(pp), Rp(pp) + NQ, Vp(pp), it);
       });
       TM::sync();
-      constexpr int B1 = Lo * Lo * QP;       // [Lo][Lo][QP]
-      // z: D^T F_2 + V -> B^T along z -> R + B1 [Lo][QP][QP]; R + B1 does not
-      // reach F_2 = R + 2 NQ because B1 + Lo QP^2 <= 2 NQ.
-      static_assert(B1 + Lo * QP * QP <= 2 * NQ, "z output overlaps F_2");
-      TM::template loop<QP * QP>([&](int pp, int it) { dert_bwd_last_item(Rp(pp) + 2 * NQ, Vp(pp), Rp(pp) + B1, it); });
-      TM::sync();
-      TM::template loop<Lo * QP>([&](int pp, int it) { bwd_item<1, false>(Rp(pp) + B1, Rp(pp), it); });
+      TM::template loop<Lo * QP>([&](int pp, int it) { bwd_item<1, false>(Vp(pp), Rp(pp), it); });
       TM::sync();
       TM::template loop<Lo * Lo>([&](int pp, int it) { bwd0_item(Rp(pp), it, pp, epi); });
       TM::sync();
@@ -845,7 +884,7 @@ struct SF {
       });
       TM::sync();
       // y: D^T F_1 + V -> B^T along y -> R [Lo][QP] (F_0 = R is dead)
-      TM::template loop<QP>([&](int pp, int it) { dert_bwd_last_item(Rp(pp) + NQ, Vp(pp), Rp(pp), it); });
+      TM::template loop<QP>([&](int pp, int it) { dert_bwd_last_item(Rp(pp) + NQ, Vp(pp), nullptr, Rp(pp), it); });
       TM::sync();
       TM::template loop<Lo>([&](int pp, int it) { bwd0_item(Rp(pp), it, pp, epi); });
       TM::sync();
@@ -862,18 +901,25 @@ struct SF {
   // LINE selects the design of the last direction: false = separate stages
   // with all fluxes in shared memory, true = one thread per line with that
   // direction's gradient and flux in registers.  Ends with __syncthreads().
+  // The functors are passed by value and the vectors are re-derived as
+  // shared-memory pointers (smem_ptr) on entry, so that nothing of the call
+  // goes through local memory or generic addressing.
   template <bool INTIN, typename GF, typename EPI>
-  __device__ __noinline__ static void apply_epi(const T* in, int sin, T* scr, int sscr, const GF& gcell,
-                                                const EPI& epi) {
-    if constexpr (LINE) apply_line<INTIN>(in, sin, scr, sscr, gcell, epi);
-    else apply_stage<INTIN>(in, sin, scr, sscr, gcell, epi);
+  __device__ __noinline__ static void apply_epi(const T* in, int sin, T* scr, int sscr, const GF gcell,
+                                                const EPI epi) {
+    const T* in_s = smem_ptr(in);
+    T* scr_s = smem_ptr(scr);
+    const EPI e = epi.rebase();
+    if constexpr (LINE) apply_line<INTIN>(in_s, sin, scr_s, sscr, gcell, e);
+    else apply_stage<INTIN>(in_s, sin, scr_s, sscr, gcell, e);
   }
 
-  // plain result: out (+)= A in, per block pp at out + pp * sout
+  // plain result: out (+)= A in, per block pp at out + pp * sout (shared memory)
   template <bool ACC>
   struct Store {
     T* out;
     int sout;
+    __device__ __forceinline__ Store rebase() const { return Store{smem_ptr(out), sout}; }
     __device__ void operator()(int pp, int i, T s) const {
       T* p = out + pp * sout + i;
       *p = ACC ? *p + s : s;

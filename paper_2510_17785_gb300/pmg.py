@@ -24,6 +24,7 @@ SMOOTHER_CHEBYSHEV, SMOOTHER_JACOBI, SMOOTHER_CARTESIAN = 0, 1, 2
 BOUNDS_LANCZOS, BOUNDS_FIXED, BOUNDS_USER, BOUNDS_MLP = 0, 1, 2, 3
 MLP_NPARAM, MLP_NNORM = 5378, 36
 PREC_FP64, PREC_MIXED = 0, 1
+NUM_VARIANTS = 10              # PMG_NUM_VARIANTS of include/pmg.h
 KAPPA_ARITHMETIC, KAPPA_GEOMETRIC, KAPPA_HARMONIC = 0, 1, 2
 
 # every symbol include/pmg.h declares
@@ -396,14 +397,14 @@ class Context:
     def tuning(self):
         """(variant, threads per CTA, patches per CTA, [ms per candidate variant])"""
         v, t, b = C.c_int(), C.c_int(), C.c_int()
-        ms = (C.c_float * 8)()
+        ms = (C.c_float * NUM_VARIANTS)()
         self._check(self.lib.pmg_tuning(self.h, C.byref(v), C.byref(t), C.byref(b), ms))
         return v.value, t.value, b.value, list(ms)
 
     def tuning_level(self, level):
         """(variant used on mesh level `level`, [set-up ms per candidate variant])"""
         v = C.c_int()
-        ms = (C.c_float * 8)()
+        ms = (C.c_float * NUM_VARIANTS)()
         self._check(self.lib.pmg_tuning_level(self.h, level, C.byref(v), ms))
         return v.value, list(ms)
 
