@@ -334,11 +334,11 @@ def learned_arm(w, levels, local, timed_solves, dev):
         Xs.append(X)
         Ts.append(T)
         c.close()
-    X, T = np.concatenate(Xs), np.concatenate(Ts)
-    norm = np.concatenate([X.mean(0), X.std(0) + 1e-6, T.mean(0), T.std(0) + 1e-6]).astype(np.float32)
+    X, T = torch.cat(Xs), torch.cat(Ts)
+    norm = pmg.mlp_norm(X, T, device=local)
     f32 = lambda a: torch.tensor(np.asarray(a), dtype=torch.float32, device=dev)
     params = f32(pmg.mlp_init(11))
-    hist = pmg.mlp_train(params, f32(norm), f32(X), f32(T), epochs=150, batch=256, lr=2e-3, asym=4.0)
+    hist = pmg.mlp_train(params, f32(norm), X, T, device=local, epochs=150, batch=256, lr=2e-3, asym=4.0)
     t_train = time.perf_counter() - t0
 
     prob = inputs.make_problem(w)

@@ -47,7 +47,7 @@ enum {
 };
 
 /* Number of launch-shape variants of the patch-sweep kernel (pmg_tuning). */
-#define PMG_NUM_VARIANTS 10
+#define PMG_NUM_VARIANTS 13
 
 /* ---- options ----------------------------------------------------------- */
 enum { PMG_SMOOTHER_CHEBYSHEV = 0, PMG_SMOOTHER_JACOBI = 1, PMG_SMOOTHER_CARTESIAN = 2 };
@@ -129,6 +129,17 @@ const char* pmg_last_error(const pmg_ctx* ctx);
 int pmg_mesh_structured(pmg_ctx* ctx, int dim, int N, int p, int n_levels,
                         const double* coords, const double* kappa);
 
+/* Coefficient of every cell of mesh level `level` (0 = coarsest; host array
+ * of N_l^d doubles, cell index lexicographic with x fastest, copied), in
+ * place of the one the set-up derives from the finer level with the
+ * `coarse_kappa` rule (Section 2 defines kappa on the domain only; a coarse
+ * level's coefficient is the user's choice).  On the finest level it
+ * replaces the mesh's coefficient; a coarser level not uploaded is derived
+ * from the level above it, uploaded or not.  Call after the mesh upload and
+ * before pmg_setup; PMG_ERR_ARG otherwise or if a value is not positive and
+ * finite. */
+int pmg_coeff_upload(pmg_ctx* ctx, int level, const double* kappa_host);
+
 /* Build everything the solver needs (geometry tensors on every level and
  * p-level, level diagonals, patch and colour lists, Chebyshev bounds, coarse
  * Cholesky factor).  The coarsest level may have at most 16384 free DoFs
@@ -198,7 +209,10 @@ int pmg_gmg_vcycle(pmg_ctx* ctx, const double* b_dev, double* x_dev, void* strea
 
 /* Preconditioned CG on the finest level from u = 0 until
  * ||r_k||_2 <= rtol ||b||_2 or maxit iterations.  Writes *iters and *relres
- * (host).  Synchronises `stream` once per iteration (one 8-byte read).
+ * (host).  The solve runs on the context's own stream, ordered after the work
+ * already queued on `stream` (an event wait: `stream` itself is not
+ * synchronised); the host reads one 8-byte residual per iteration, and the
+ * call returns when the solve, including the write of u_dev, has finished.
  * Returns PMG_ERR_NOT_CONVERGED at maxit, PMG_ERR_NUMERIC on NaN/Inf. */
 int pmg_solve_cg(pmg_ctx* ctx, const double* b_dev, double* u_dev, double rtol, int maxit,
                  int* iters, double* relres, void* stream);
@@ -207,8 +221,10 @@ int pmg_solve_cg(pmg_ctx* ctx, const double* b_dev, double* u_dev, double rtol, 
  * as preconditioner M (the paper's outer solver, Section 4), modified
  * Gram-Schmidt Arnoldi, Givens rotations.  left = 0: right preconditioning,
  * u = M y, stops when ||b - A u||_2 <= rtol ||b||_2; left = 1: the Krylov space
- * of M A, stops when ||M (b - A u)||_2 <= rtol ||M b||_2.  Synchronises once per
- * inner product (the Hessenberg least-squares problem lives on the host).
+ * of M A, stops when ||M (b - A u)||_2 <= rtol ||M b||_2.  Runs on the
+ * context's own stream after the work queued on `stream` (event wait), and
+ * synchronises that internal stream once per inner product (the Hessenberg
+ * least-squares problem lives on the host); returns when finished.
  * Returns PMG_ERR_NOT_CONVERGED at maxit. */
 int pmg_solve_gmres(pmg_ctx* ctx, const double* b_dev, double* u_dev, double rtol, int maxit,
                     int restart, int left, int* iters, double* relres, void* stream);
@@ -310,6 +326,22 @@ int pmg_mlp_predict(int device, const float* params_dev, const float* norm_dev, 
                     int64_t n, int bf16, float* Y_dev, void* stream);
 /* Install a trained network (host arrays) for PMG_BOUNDS_MLP. */
 int pmg_set_mlp(pmg_ctx* ctx, const float* params_host, const float* norm_host);
+/* Initial parameters (host array of PMG_MLP_NPARAM floats): weights uniform in
+ * +-sqrt(6 / fan_in) from the SplitMix64 counter stream of `seed`, biases 0. */
+void pmg_mlp_init(uint64_t seed, float* params_host);
+/* Training targets of mesh level `level`, p-level index k (degree > 1): the
+ * context's Lanczos estimates as T_dev (n_patches x 2 device floats) =
+ * (log theta_max, log theta_min).  Asynchronous on `stream`. */
+int pmg_mlp_targets(pmg_ctx* ctx, int level, int k, float* T_dev, void* stream);
+/* Normalisation of a training set (X_dev n x 16 features, T_dev n x 2 targets,
+ * device): the PMG_MLP_NNORM floats (column means, then population standard
+ * deviations + 1e-6, of X and then of T) to norm_host.  Synchronises. */
+int pmg_mlp_norm(int device, const float* X_dev, const float* T_dev, int64_t n, float* norm_host);
+/* Write the installed network (parameters and normalisation) to a file, or
+ * read one written by pmg_mlp_save and install it (as pmg_set_mlp).  File:
+ * 8-byte magic, two uint32 counts, the floats; PMG_ERR_ARG on any mismatch. */
+int pmg_mlp_save(pmg_ctx* ctx, const char* path);
+int pmg_mlp_load(pmg_ctx* ctx, const char* path);
 
 /* ---- measurement ----------------------------------------------------------
  * Number of kernels this context has launched so far (kernel nodes of a CUDA

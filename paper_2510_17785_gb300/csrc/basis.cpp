@@ -142,13 +142,46 @@ void build_tables(Tables<double>& t64, Tables<float>& t32, Rules& r) {
       for (int a = 0; a <= q; ++a) r.Bg[q][g][a] = B2[g][a];
     }
   }
-  for (int q = 0; q <= PMG_MAXQ; ++q)
+  // even/odd parts of B, B^T, D, D^T (see table_types.h); M is first made
+  // exactly (anti)symmetric by averaging M[i][j] with S M[n-1-i][n-1-j]
+  for (int q = 1; q <= PMG_MAXQ; ++q) {
+    const int n = q + 1, h = n / 2;
+    for (int k = 0; k < 4; ++k) {
+      const double S = (k == EO_D || k == EO_DT) ? -1.0 : 1.0;
+      auto raw = [&](int i, int j) {
+        switch (k) {
+          case EO_B: return t64.B[q][i][j];
+          case EO_BT: return t64.B[q][j][i];
+          case EO_D: return t64.D[q][i][j];
+          default: return t64.D[q][j][i];
+        }
+      };
+      auto M = [&](int i, int j) { return 0.5 * (raw(i, j) + S * raw(n - 1 - i, n - 1 - j)); };
+      for (int i = 0; i <= h && i < n; ++i) {
+        for (int j = 0; j < h; ++j) {
+          t64.Ee[k][q][i][j] = 0.5 * (M(i, j) + M(i, n - 1 - j));
+          t64.Eo[k][q][i][j] = 0.5 * (M(i, j) - M(i, n - 1 - j));
+        }
+        t64.Em[k][q][i] = (n % 2 == 1) ? M(i, h) : 0.0;
+      }
+    }
+  }
+  for (int q = 0; q <= PMG_MAXQ; ++q) {
     for (int i = 0; i <= PMG_MAXQ; ++i)
       for (int j = 0; j <= PMG_MAXQ; ++j) {
         t32.B[q][i][j] = (float)t64.B[q][i][j];
         t32.D[q][i][j] = (float)t64.D[q][i][j];
         t32.E[q][i][j] = (float)t64.E[q][i][j];
       }
+    for (int k = 0; k < 4; ++k)
+      for (int i = 0; i < PMG_EOR; ++i) {
+        t32.Em[k][q][i] = (float)t64.Em[k][q][i];
+        for (int j = 0; j < PMG_EOC; ++j) {
+          t32.Ee[k][q][i][j] = (float)t64.Ee[k][q][i][j];
+          t32.Eo[k][q][i][j] = (float)t64.Eo[k][q][i][j];
+        }
+      }
+  }
 }
 
 void h_prolongation_band(int q, int Nc, std::vector<double>& W, std::vector<int>& start) {

@@ -77,6 +77,9 @@ int launch_patch_P(int mode, int variant, const PatchArgs<T>& a, cudaStream_t s)
       case 7: return launch_patch_PV<DIM, P, T, 7>(mode, a, s);
       case 8: return launch_patch_PV<DIM, P, T, 8>(mode, a, s);
       case 9: return launch_patch_PV<DIM, P, T, 9>(mode, a, s);
+      case 10: return launch_patch_PV<DIM, P, T, 10>(mode, a, s);
+      case 11: return launch_patch_PV<DIM, P, T, 11>(mode, a, s);
+      case 12: return launch_patch_PV<DIM, P, T, 12>(mode, a, s);
       default: return ST_UNSUPPORTED;
     }
   }
@@ -120,6 +123,9 @@ void patch_config_P(int variant, size_t* smem, int* ppb, int* nt) {
     case 7: return patch_config_PV<DIM, P, T, 7>(smem, ppb, nt);
     case 8: return patch_config_PV<DIM, P, T, 8>(smem, ppb, nt);
     case 9: return patch_config_PV<DIM, P, T, 9>(smem, ppb, nt);
+    case 10: return patch_config_PV<DIM, P, T, 10>(smem, ppb, nt);
+    case 11: return patch_config_PV<DIM, P, T, 11>(smem, ppb, nt);
+    case 12: return patch_config_PV<DIM, P, T, 12>(smem, ppb, nt);
     default: *smem = 0; *ppb = 0; *nt = 0;
   }
 }

@@ -35,6 +35,7 @@
 #include <vector>
 
 #include "../../include/pmg.h"
+#include "device_guard.h"
 #include "mlp.h"
 
 namespace pmg {
@@ -425,11 +426,93 @@ int bounds_from_logs_launch(const float* Y, int64_t n, double safety, double rat
   return cudaPeekAtLastError() == cudaSuccess ? PMG_OK : PMG_ERR_CUDA;
 }
 
+// ---- training targets and normalisation ------------------------------------
+// T[i] = (log theta_max, log theta_min) of patch i from its Ritz pair
+// (theta_min, theta_max)
+__global__ void k_log_targets(const double* __restrict__ ritz, int64_t n, float* __restrict__ T) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    T[2 * i] = (float)log(ritz[2 * i + 1]);
+    T[2 * i + 1] = (float)log(ritz[2 * i]);
+  }
+}
+
+// column c of an n x cols row-major matrix: out[c] = mean, out[cols + c] =
+// population standard deviation + 1e-6 (two passes in FP64, one block per
+// column, fixed reduction order: deterministic)
+__global__ void __launch_bounds__(256) k_col_stats(const float* __restrict__ A, int64_t n, int cols,
+                                                   float* __restrict__ out) {
+  __shared__ double red[256];
+  const int c = blockIdx.x;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += 256) s += (double)A[i * cols + c];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double mean = red[0] / (double)n;
+  __syncthreads();
+  double v = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += 256) {
+    const double d = (double)A[i * cols + c] - mean;
+    v += d * d;
+  }
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[c] = (float)mean;
+    out[cols + c] = (float)(sqrt(red[0] / (double)n) + 1e-6);
+  }
+}
+
+int targets_launch(const double* ritz, int64_t n, float* T, cudaStream_t s) {
+  if (n <= 0) return PMG_OK;
+  k_log_targets<<<grid_for((size_t)n, 256), 256, 0, s>>>(ritz, n, T);
+  return cudaPeekAtLastError() == cudaSuccess ? PMG_OK : PMG_ERR_CUDA;
+}
+
 }  // namespace pmg
 
 using namespace pmg;
 
 extern "C" {
+
+void pmg_mlp_init(uint64_t seed, float* params) {
+  if (!params) return;
+  // SplitMix64 counter stream (Steele, Lea and Flood 2014): u_i in [0, 1)
+  auto u01 = [seed](uint64_t i) {
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * 0x1.0p-53;
+  };
+  const int rows[3] = {NH, NH, NO}, cols[3] = {NF, NH, NH}, woff[3] = {OW1, OW2, OW3}, boff[3] = {OB1, OB2, OB3};
+  uint64_t ctr = 0;
+  for (int l = 0; l < 3; ++l) {
+    const double lim = std::sqrt(6.0 / cols[l]);
+    for (int i = 0; i < rows[l] * cols[l]; ++i) params[woff[l] + i] = (float)((2.0 * u01(ctr++) - 1.0) * lim);
+    for (int i = 0; i < rows[l]; ++i) params[boff[l] + i] = 0.f;
+  }
+}
+
+int pmg_mlp_norm(int device, const float* X, const float* T, int64_t n, float* norm_host) {
+  if (!X || !T || !norm_host || n <= 0) return PMG_ERR_ARG;
+  pmg::DeviceGuard guard(device);
+  if (guard.err != cudaSuccess) return PMG_ERR_CUDA;
+  float* out = nullptr;
+  if (cudaMalloc(&out, PMG_MLP_NNORM * sizeof(float)) != cudaSuccess) return PMG_ERR_CUDA;
+  k_col_stats<<<NF, 256>>>(X, n, NF, out);
+  k_col_stats<<<NO, 256>>>(T, n, NO, out + 2 * NF);
+  cudaError_t e = cudaMemcpy(norm_host, out, PMG_MLP_NNORM * sizeof(float), cudaMemcpyDeviceToHost);
+  cudaFree(out);
+  return e == cudaSuccess ? PMG_OK : PMG_ERR_CUDA;
+}
 
 void pmg_default_train_options(pmg_train_opts* o) {
   if (!o) return;
@@ -446,7 +529,8 @@ void pmg_default_train_options(pmg_train_opts* o) {
 int pmg_mlp_grad(int device, const float* params, const float* norm, const float* X, const float* T, int n,
                  float asym, float* loss, float* grad, void* stream) {
   if (!params || !norm || !X || !T || !grad || n <= 0) return PMG_ERR_ARG;
-  if (cudaSetDevice(device) != cudaSuccess) return PMG_ERR_CUDA;
+  pmg::DeviceGuard guard(device);
+  if (guard.err != cudaSuccess) return PMG_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
   Work w;
   if (alloc_work(w, n) != PMG_OK) return PMG_ERR_CUDA;
@@ -470,7 +554,8 @@ int pmg_mlp_train(int device, float* params, const float* norm, const float* X, 
   if (opt_in) o = *opt_in;
   else pmg_default_train_options(&o);
   if (!params || !norm || !X || !T || n <= 0 || o.batch <= 0 || o.epochs < 0) return PMG_ERR_ARG;
-  if (cudaSetDevice(device) != cudaSuccess) return PMG_ERR_CUDA;
+  pmg::DeviceGuard guard(device);
+  if (guard.err != cudaSuccess) return PMG_ERR_CUDA;
   cudaStream_t s = nullptr;
   const int b = (int)std::min<int64_t>(o.batch, n);
   Work w;
@@ -517,7 +602,8 @@ int pmg_mlp_train(int device, float* params, const float* norm, const float* X, 
 int pmg_mlp_predict(int device, const float* params, const float* norm, const float* X, int64_t n, int bf16,
                     float* Y, void* stream) {
   if (!params || !norm || !X || !Y || n < 0) return PMG_ERR_ARG;
-  if (cudaSetDevice(device) != cudaSuccess) return PMG_ERR_CUDA;
+  pmg::DeviceGuard guard(device);
+  if (guard.err != cudaSuccess) return PMG_ERR_CUDA;
   return mlp_infer_launch(params, norm, X, n, bf16, Y, (cudaStream_t)stream);
 }
 

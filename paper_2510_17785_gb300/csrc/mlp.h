@@ -15,4 +15,7 @@ int mlp_infer_launch(const float* params, const float* norm, const float* X, int
 int bounds_from_logs_launch(const float* Y, int64_t n, double safety, double ratio, float* b32, double* b64,
                             cudaStream_t s);
 
+// T (n x 2) = (log theta_max, log theta_min) from Ritz pairs (theta_min, theta_max)
+int targets_launch(const double* ritz, int64_t n, float* T, cudaStream_t s);
+
 }  // namespace pmg

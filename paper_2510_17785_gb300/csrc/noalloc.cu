@@ -28,6 +28,7 @@
 
 #include "../../include/pmg.h"
 #include "basis.h"
+#include "device_guard.h"
 #include "lanczos_view.h"
 #include "patch.cuh"
 
@@ -65,21 +66,6 @@ cudaError_t set_smem_attrs() {
     if (x != cudaSuccess) return x;
   return cudaSuccess;
 }
-
-// Makes `dev` current for the lifetime of the guard and restores the
-// caller's current device on every return path.
-struct DeviceGuard {
-  int prev = -1;
-  cudaError_t err = cudaSuccess;
-  explicit DeviceGuard(int dev) {
-    err = cudaGetDevice(&prev);
-    if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
 
 // Once per device, with that device current: upload this file's constant
 // tables, set the kernels' shared-memory limits and take the device address
@@ -167,7 +153,7 @@ extern "C" int pmg_lanczos_bounds_noalloc(pmg_ctx* ctx, int level, int k, int64_
                                "16 MiB scratch array; split the patch range into smaller calls");
   if (v.ksteps > 64) return pmg::set_last_error(ctx, PMG_ERR_ARG, "noalloc Lanczos: more than 64 Lanczos steps");
   if (v.device < 0 || v.device >= kMaxDevices) return pmg::set_last_error(ctx, PMG_ERR_ARG, "device index too large");
-  DeviceGuard guard(v.device);
+  pmg::DeviceGuard guard(v.device);
   if (guard.err != cudaSuccess)
     return pmg::set_last_error(ctx, PMG_ERR_CUDA, "noalloc Lanczos: cudaGetDevice/cudaSetDevice failed");
   {

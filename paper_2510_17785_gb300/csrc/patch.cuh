@@ -152,10 +152,10 @@ struct Layout {
 
 // Launch shape of the patch kernel.  Variant 0 is the default; for 3D degrees
 // 3..8 the set-up autotuner also times variants 1..9:
-//   variant:          1      2      3      4      5      6      7      8      9
-//   design:         stage  stage  stage  line   line   line   line   line   stage
-//   threads / CTA:    256    128    512    256    128    512    128    256    256
-//   patches / CTA:      2      1      1      2      1      1      2      2      2
+//   variant:          1      2      3      4      5      6      7      8      9     10     11     12
+//   design:         stage  stage  stage  line   line   line   line   line   stage  line   line   line
+//   threads / CTA:    256    128    512    256    128    512    128    256    256    224    320    416
+//   patches / CTA:      2      1      1      2      1      1      2      2      2      2      3      4
 //   geometry:                    staged                staged        staged staged
 //   groups:                                                   2
 // (patches per CTA are capped by shared memory).  "stage": every direction's
@@ -166,18 +166,23 @@ struct Layout {
 // patch instead of read from L2 by every apply; variants 3 and 6 are
 // latency-oriented shapes for small launches (coarse mesh levels, one patch
 // per 512 threads), 8 and 9 throughput shapes (two patches per 256 threads,
-// a 128-register budget, two CTAs per SM).
+// a 128-register budget, two CTAs per SM).  Variants 10-12 size the CTA to
+// about 100 threads per patch, the number of lines along the last direction
+// at degree 4 (fewer idle threads at each barrier).
 constexpr int NUM_VARIANTS = PMG_NUM_VARIANTS;
 
 template <int DIM, int P, typename T, int V = 0>
 struct Config {
   static constexpr int NT0 = (DIM == 3) ? 256 : 128;
   static constexpr int PPB0 = (DIM == 3) ? (P <= 2 ? 4 : 1) : (P <= 2 ? 8 : (P <= 4 ? 4 : 2));
-  static constexpr int NTV[NUM_VARIANTS] = {NT0, 256, 128, 512, 256, 128, 512, 128, 256, 256};
-  static constexpr int PPBV[NUM_VARIANTS] = {PPB0, 2, 1, 1, 2, 1, 1, 2, 2, 2};
-  static constexpr bool LINEV[NUM_VARIANTS] = {false, false, false, false, true, true, true, true, true, false};
-  static constexpr bool GROUPV[NUM_VARIANTS] = {false, false, false, false, false, false, false, true, false, false};
-  static constexpr bool GSMEMV[NUM_VARIANTS] = {false, false, false, true, false, false, true, false, true, true};
+  static constexpr int NTV[NUM_VARIANTS] = {NT0, 256, 128, 512, 256, 128, 512, 128, 256, 256, 224, 320, 416};
+  static constexpr int PPBV[NUM_VARIANTS] = {PPB0, 2, 1, 1, 2, 1, 1, 2, 2, 2, 2, 3, 4};
+  static constexpr bool LINEV[NUM_VARIANTS] = {false, false, false, false, true, true, true, true, true, false,
+                                               true, true, true};
+  static constexpr bool GROUPV[NUM_VARIANTS] = {false, false, false, false, false, false, false, true, false, false,
+                                                false, false, false};
+  static constexpr bool GSMEMV[NUM_VARIANTS] = {false, false, false, true, false, false, true, false, true, true,
+                                                false, false, false};
   static constexpr int NT = NTV[V];
   static constexpr int PPB_MAX = PPBV[V];
   static constexpr bool LINE = LINEV[V];
@@ -196,7 +201,8 @@ struct Config {
   static constexpr int REG_TARGET = (sizeof(T) == 4 && P <= 5 && !GSMEMV[V]) ? 64 : 128;
   // resident CTAs per SM: by the register target, and at most what shared
   // memory allows (small CTAs then get the registers shared memory leaves)
-  static constexpr int MINB_REG = 65536 / (NT * REG_TARGET);
+  static constexpr int MINB_REG_RAW = 65536 / (NT * REG_TARGET);
+  static constexpr int MINB_REG = MINB_REG_RAW < 1 ? 1 : MINB_REG_RAW;
   static constexpr int MINB_SMEM = (int)((228 * 1024) / (smem + 1024));
   static constexpr int MINB_RAW = MINB_REG < MINB_SMEM ? MINB_REG : MINB_SMEM;
   static constexpr int MINB = MINB_RAW < 1 ? 1 : MINB_RAW;
@@ -224,7 +230,7 @@ struct Config {
   static constexpr int LPT_ = (SPAN_ * ipow(QPL, DIM - 1) + TPP_ - 1) / TPP_;
   static constexpr bool worth = (!LINE || LPT_ <= 2) &&
                                 (sizeof(T) == 4 || V == 0 || ((V == 2 || V == 4 || V == 6) && P <= 6)) &&
-                                (V < 8 || (DIM == 3 && P >= 3));
+                                (V < 8 || (DIM == 3 && P >= 3)) && (V < 10 || (sizeof(T) == 4 && P <= 5));
   static constexpr bool exists = fits && distinct && worth;
 };
 
@@ -243,12 +249,21 @@ struct PatchKernel {
 
   __device__ T* vec(int pp, int off) const { return sm + pp * PS + off; }
 
+  // geometry of cell `slot` of patch pp staged in shared memory (GSMEM variants)
+  template <int stride>
+  struct SharedGeom {
+    static constexpr bool kShared = true;
+    __device__ const T* operator()(int pp, int slot) const {
+      return reinterpret_cast<const T*>(pmg_smem) + L::GS + pp * PS + slot * stride;
+    }
+  };
+
   template <int K>
   __device__ auto gfun() const {
     constexpr int q = P >> K;
     constexpr int stride = Dims<DIM, 2, q>::NCOMP * ipow(q + 1, DIM);
     if constexpr (C::GSMEM && K == 0) {                 // staged in shared memory by load_level
-      return [](int pp, int slot) { return reinterpret_cast<const T*>(pmg_smem) + L::GS + pp * PS + slot * stride; };
+      return SharedGeom<stride>{};
     } else {
       const T* G = a->lv[K].G;
       // the cell list follows the PPB patch arrays in dynamic shared memory
@@ -703,24 +718,35 @@ struct PatchKernel {
         constexpr int FS = L::fsz(K);
         TM::template loop<FS>([&](int pp, int e) { vec(pp, L::FDM(K))[e] = a->lv[K].fdm[e]; });
       }
-      // Chebyshev coefficients (FP64 scalars, rounded to T)
+      // Chebyshev coefficients of the three-term recurrence (Saad, Algorithm
+      // 12.1): with sigma = theta / delta the recurrence rho_1 = 1 / sigma,
+      // rho_{i+1} = 1 / (2 sigma - rho_i) has the closed form
+      // rho_i = C_{i-1}(sigma) / C_i(sigma) (C_k: Chebyshev polynomials of the
+      // first kind), so coefficient i is computed by thread i on its own, in
+      // the kernel's precision: cf[i] = rho_{i+1} rho_i = C_{i-1} / C_{i+1},
+      // cf[7 + i] = 2 rho_{i+1} / delta = 2 C_i / (delta C_{i+1}).
       if (a->smoother == 0) {
-        TM::per_block([&](int pp) {
+        TM::template loop<8>([&](int pp, int i) {
           const bool act = cells[pp * CST + NCELL + 1];
           const int pid = cells[pp * CST + NCELL];
-          double lo = 1.0, hi = 2.0;
-          if (act) { lo = (double)a->lv[K].bounds[2 * (size_t)pid]; hi = (double)a->lv[K].bounds[2 * (size_t)pid + 1]; }
-          const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
-          const double sigma = theta / delta;
-          double rho = 1.0 / sigma;
+          T lo = T(1), hi = T(2);
+          if (act) { lo = a->lv[K].bounds[2 * (size_t)pid]; hi = a->lv[K].bounds[2 * (size_t)pid + 1]; }
+          const T theta = T(0.5) * (hi + lo), delta = T(0.5) * (hi - lo);
           T* cf = vec(pp, L::COEF + K * L::NCOEF);
-          cf[0] = T(1.0 / theta);
-          for (int i = 1; i < 8; ++i) {
-            const double rn = 1.0 / (2.0 * sigma - rho);
-            cf[i] = T(rn * rho);
-            cf[7 + i] = T((2.0 * rn) / delta);
-            rho = rn;
+          if (i == 0) {
+            cf[0] = T(1) / theta;
+            return;
           }
+          const T sigma = theta / delta;
+          T cm = T(1), c0 = sigma;                       // C_{k-1}, C_k at k = 1
+          for (int k = 1; k < i; ++k) {
+            const T cn = T(2) * sigma * c0 - cm;
+            cm = c0;
+            c0 = cn;
+          }
+          const T cp = T(2) * sigma * c0 - cm;           // C_{i+1}
+          cf[i] = cm / cp;
+          cf[7 + i] = (T(2) * c0) / (delta * cp);
         });
       }
     }

@@ -14,6 +14,7 @@
 
 #include "../../include/pmg.h"
 #include "basis.h"
+#include "device_guard.h"
 #include "lanczos_view.h"
 #include "launch.h"
 #include "mlp.h"
@@ -73,6 +74,7 @@ struct pmg_ctx {
   int npl = 0;
   int plevels[8] = {0};
   std::vector<double> h_coords, h_kappa;
+  std::vector<std::vector<double>> kappa_level;   // per-level coefficients from pmg_coeff_upload (empty: derived)
   std::vector<HLevel> L;
   bool mesh_ok = false, setup_ok = false;
   int* d_err = nullptr;
@@ -91,6 +93,7 @@ struct pmg_ctx {
   double* h_rr = nullptr;   // pinned
   double *stage_b = nullptr, *stage_u = nullptr;   // device staging for the host-vector solve
   cudaStream_t stream = nullptr;
+  cudaEvent_t ev_caller = nullptr;       // orders the solvers' internal stream after the caller's
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   int64_t graph_launches_per_iter = 0;   // kernels recorded in one CG iteration graph
@@ -484,6 +487,13 @@ int autotune(pmg_ctx* ctx) {
 }  // namespace
 
 // ===========================================================================
+// Every entry point that touches the device makes the context's device
+// current and restores the caller's on return.
+#define PMG_GUARD_DEV(dev)                          \
+  pmg::DeviceGuard pmg_device_guard_(dev);          \
+  if (pmg_device_guard_.err != cudaSuccess) return PMG_ERR_CUDA
+#define PMG_GUARD_CTX(ctx) PMG_GUARD_DEV((ctx)->device)
+
 extern "C" {
 
 void pmg_default_options(pmg_options* o) {
@@ -526,13 +536,15 @@ int pmg_create(int device, const pmg_options* opt, pmg_ctx** out) {
     delete ctx;
     return PMG_ERR_ARG;
   }
-  if (cudaSetDevice(device) != cudaSuccess) {
+  pmg::DeviceGuard guard(device);
+  if (guard.err != cudaSuccess) {
     delete ctx;
     return PMG_ERR_CUDA;
   }
   if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess || cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess ||
-      cudaMallocHost(&ctx->h_rr, sizeof(double)) != cudaSuccess) {
+      cudaMallocHost(&ctx->h_rr, sizeof(double)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_caller, cudaEventDisableTiming) != cudaSuccess) {
     delete ctx;
     return PMG_ERR_CUDA;
   }
@@ -542,7 +554,7 @@ int pmg_create(int device, const pmg_options* opt, pmg_ctx** out) {
 
 int pmg_destroy(pmg_ctx* ctx) {
   if (!ctx) return PMG_ERR_ARG;
-  cudaSetDevice(ctx->device);
+  pmg::DeviceGuard guard(ctx->device);
   cudaDeviceSynchronize();
   if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
   if (ctx->graph) cudaGraphDestroy(ctx->graph);
@@ -552,6 +564,7 @@ int pmg_destroy(pmg_ctx* ctx) {
   if (ctx->d_err) cudaFree(ctx->d_err);
   if (ctx->h_rr) cudaFreeHost(ctx->h_rr);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  if (ctx->ev_caller) cudaEventDestroy(ctx->ev_caller);
   delete ctx;
   return PMG_OK;
 }
@@ -594,10 +607,23 @@ int pmg_mesh_structured(pmg_ctx* ctx, int dim, int N, int p, int n_levels, const
   return PMG_OK;
 }
 
+int pmg_coeff_upload(pmg_ctx* ctx, int level, const double* kappa) {
+  if (!ctx) return PMG_ERR_ARG;
+  if (!ctx->mesh_ok) return fail(ctx, PMG_ERR_ARG, "upload a mesh first");
+  if (ctx->setup_ok) return fail(ctx, PMG_ERR_ARG, "coefficients must be uploaded before pmg_setup");
+  if (level < 0 || level >= ctx->nlev || !kappa) return fail(ctx, PMG_ERR_ARG, "bad level or null array");
+  const size_t nc = ipow_sz(ctx->N >> (ctx->nlev - 1 - level), ctx->dim);
+  for (size_t i = 0; i < nc; ++i)
+    if (!std::isfinite(kappa[i]) || !(kappa[i] > 0)) return fail(ctx, PMG_ERR_ARG, "kappa must be positive and finite");
+  if ((int)ctx->kappa_level.size() < ctx->nlev) ctx->kappa_level.resize(ctx->nlev);
+  ctx->kappa_level[level].assign(kappa, kappa + nc);
+  return PMG_OK;
+}
+
 int pmg_setup(pmg_ctx* ctx) {
   if (!ctx || !ctx->mesh_ok) return fail(ctx, PMG_ERR_ARG, "upload a mesh first");
   if (ctx->setup_ok) return fail(ctx, PMG_ERR_ARG, "already set up");
-  CU(cudaSetDevice(ctx->device));
+  PMG_GUARD_CTX(ctx);
   const int d = ctx->dim, p = ctx->p;
   cudaStream_t s = ctx->stream;
   {
@@ -646,6 +672,7 @@ int pmg_setup(pmg_ctx* ctx) {
       X.swap(Xc);
       K.swap(Kc);
     }
+    if (l < (int)ctx->kappa_level.size() && !ctx->kappa_level[l].empty()) K = ctx->kappa_level[l];
     h.nd = ipow_sz((size_t)p * Nl + 1, d);
     h.ncells = ipow_sz(Nl, d);
     h.npatch = ipow_sz(Nl - 1, d);
@@ -868,6 +895,7 @@ int pmg_setup(pmg_ctx* ctx) {
 
 int pmg_compute_bounds(pmg_ctx* ctx, int source) {
   if (!ctx || !ctx->setup_ok) return fail(ctx, PMG_ERR_ARG, "not set up");
+  PMG_GUARD_CTX(ctx);
   cudaStream_t s = ctx->stream;
   const int d = ctx->dim;
   if (source == PMG_BOUNDS_USER) return PMG_OK;
@@ -1000,6 +1028,7 @@ static int check_level(pmg_ctx* ctx, int level) {
 int pmg_apply(pmg_ctx* ctx, int level, const double* u, double* Au, void* stream) {
   int st = check_level(ctx, level);
   if (st) return st;
+  PMG_GUARD_CTX(ctx);
   if (!u || !Au) return fail(ctx, PMG_ERR_ARG, "null vector");
   HLevel& h = ctx->L[level];
   LK(1 + (1 << ctx->dim), cell_apply<double>(ctx, ctx->p, u, Au, h.pl[0].G64, h.N, (cudaStream_t)stream));
@@ -1009,6 +1038,7 @@ int pmg_apply(pmg_ctx* ctx, int level, const double* u, double* Au, void* stream
 int pmg_patch_smooth_colour(pmg_ctx* ctx, int level, int colour, const double* b, double* u, void* stream) {
   int st = check_level(ctx, level);
   if (st) return st;
+  PMG_GUARD_CTX(ctx);
   if (colour < 0 || colour >= (1 << ctx->dim)) return fail(ctx, PMG_ERR_ARG, "colour out of range");
   if (!b || !u) return fail(ctx, PMG_ERR_ARG, "null vector");
   if (ctx->opt.additive) return fail(ctx, PMG_ERR_UNSUPPORTED, "an additive sweep runs all colours (pmg_patch_smooth)");
@@ -1028,6 +1058,7 @@ int pmg_patch_smooth_colour(pmg_ctx* ctx, int level, int colour, const double* b
 int pmg_patch_smooth(pmg_ctx* ctx, int level, const double* b, double* u, int n_sweeps, int reverse, void* stream) {
   int st = check_level(ctx, level);
   if (st) return st;
+  PMG_GUARD_CTX(ctx);
   if (!b || !u || n_sweeps < 0) return fail(ctx, PMG_ERR_ARG, "bad arguments");
   cudaStream_t s = (cudaStream_t)stream;
   HLevel& h = ctx->L[level];
@@ -1052,6 +1083,7 @@ int pmg_local_vcycle(pmg_ctx* ctx, int level, int64_t n, const int64_t* ids, con
                      int n_cycles, void* stream) {
   int st = check_level(ctx, level);
   if (st) return st;
+  PMG_GUARD_CTX(ctx);
   if (n < 0 || (n > 0 && (!ids || !r || !dout)) || n_cycles < 1) return fail(ctx, PMG_ERR_ARG, "bad arguments");
   if (n == 0) return PMG_OK;
   HLevel& h = ctx->L[level];
@@ -1083,6 +1115,7 @@ int pmg_local_vcycle(pmg_ctx* ctx, int level, int64_t n, const int64_t* ids, con
 int pmg_get_bounds(pmg_ctx* ctx, int level, double* lohi) {
   int st = check_level(ctx, level);
   if (st) return st;
+  PMG_GUARD_CTX(ctx);
   HLevel& h = ctx->L[level];
   std::vector<double> out(2 * h.npatch * ctx->npl, 0.0), tmp(2 * h.npatch);
   CU(cudaStreamSynchronize(ctx->stream));
@@ -1101,6 +1134,7 @@ int pmg_get_bounds(pmg_ctx* ctx, int level, double* lohi) {
 int pmg_get_ritz(pmg_ctx* ctx, int level, double* tm) {
   int st = check_level(ctx, level);
   if (st) return st;
+  PMG_GUARD_CTX(ctx);
   HLevel& h = ctx->L[level];
   std::vector<double> out(2 * h.npatch * ctx->npl, 0.0), tmp(2 * h.npatch);
   CU(cudaStreamSynchronize(ctx->stream));
@@ -1119,6 +1153,7 @@ int pmg_get_ritz(pmg_ctx* ctx, int level, double* tm) {
 int pmg_set_bounds(pmg_ctx* ctx, int level, const double* lohi) {
   int st = check_level(ctx, level);
   if (st) return st;
+  PMG_GUARD_CTX(ctx);
   HLevel& h = ctx->L[level];
   std::vector<double> tmp(2 * h.npatch);
   for (int k = 0; k < ctx->npl; ++k) {
@@ -1139,6 +1174,7 @@ int pmg_set_bounds(pmg_ctx* ctx, int level, const double* lohi) {
 int pmg_gmg_vcycle(pmg_ctx* ctx, const double* b, double* x, void* stream) {
   int st = check_level(ctx, ctx ? ctx->nlev - 1 : 0);
   if (st) return st;
+  PMG_GUARD_CTX(ctx);
   if (!b || !x) return fail(ctx, PMG_ERR_ARG, "null vector");
   return precondition(ctx, b, x, (cudaStream_t)stream);
 }
@@ -1221,10 +1257,14 @@ int pmg_solve_cg(pmg_ctx* ctx, const double* b, double* u, double rtol, int maxi
                  void* stream) {
   int st = check_level(ctx, ctx ? ctx->nlev - 1 : 0);
   if (st) return st;
+  PMG_GUARD_CTX(ctx);
   if (!b || !u || maxit < 0 || !(rtol >= 0)) return fail(ctx, PMG_ERR_ARG, "bad arguments");
   cudaStream_t us = (cudaStream_t)stream;
   cudaStream_t s = ctx->stream;
-  CU(cudaStreamSynchronize(us));
+  // the solve runs on the context's stream, after the work already queued
+  // on the caller's stream (an event wait; the caller's stream is not synchronised)
+  CU(cudaEventRecord(ctx->ev_caller, us));
+  CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_caller, 0));
   HLevel& h = ctx->L.back();
   const size_t n = h.nd;
   st = cg_start(ctx, b);
@@ -1270,7 +1310,11 @@ int pmg_batch_solve_cg(pmg_ctx* const* ctxs, int n_problems, const double* const
       if (ctxs[j] == ctxs[k]) return fail(ctxs[k], PMG_ERR_ARG, "a context appears twice in the batch");
     const int st = check_level(ctxs[k], ctxs[k]->nlev - 1);
     if (st) return st;
+    if (ctxs[k]->device != ctxs[0]->device)
+      return fail(ctxs[k], PMG_ERR_ARG, "all problems of a batch must be on one device");
   }
+  if (K == 0) return PMG_OK;
+  PMG_GUARD_DEV(ctxs[0]->device);
   std::vector<double> r0(K, 0.0), rel(K, 1.0);
   std::vector<int> it(K, 0), res(K, PMG_OK);
   std::vector<char> active(K, 0);
@@ -1351,10 +1395,14 @@ int pmg_solve_gmres(pmg_ctx* ctx, const double* b, double* u, double rtol, int m
                     int* iters, double* relres, void* stream) {
   int st = check_level(ctx, ctx ? ctx->nlev - 1 : 0);
   if (st) return st;
+  PMG_GUARD_CTX(ctx);
   if (!b || !u || maxit < 0 || restart < 1 || restart > 1000 || !(rtol >= 0)) return fail(ctx, PMG_ERR_ARG, "bad arguments");
   cudaStream_t us = (cudaStream_t)stream;
   cudaStream_t s = ctx->stream;
-  CU(cudaStreamSynchronize(us));
+  // the solve runs on the context's stream, after the work already queued
+  // on the caller's stream (an event wait; the caller's stream is not synchronised)
+  CU(cudaEventRecord(ctx->ev_caller, us));
+  CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_caller, 0));
   HLevel& h = ctx->L.back();
   const size_t n = h.nd;
   const int M = ctx->p * h.N + 1;
@@ -1474,6 +1522,7 @@ int pmg_solve_cg_host(pmg_ctx* ctx, const double* b_host, double* u_host, double
                       double* relres, void* stream) {
   int st = check_level(ctx, ctx ? ctx->nlev - 1 : 0);
   if (st) return st;
+  PMG_GUARD_CTX(ctx);
   if (!b_host || !u_host) return fail(ctx, PMG_ERR_ARG, "null vector");
   const size_t n = ctx->L.back().nd;
   cudaStream_t s = ctx->stream;
@@ -1488,6 +1537,7 @@ int pmg_solve_cg_host(pmg_ctx* ctx, const double* b_host, double* u_host, double
 int pmg_rhs_manufactured(pmg_ctx* ctx, double* b, void* stream) {
   int st = check_level(ctx, ctx ? ctx->nlev - 1 : 0);
   if (st) return st;
+  PMG_GUARD_CTX(ctx);
   if (!b) return fail(ctx, PMG_ERR_ARG, "null vector");
   HLevel& h = ctx->L.back();
   if (ctx->dim == 2) ST(launch_rhs_manufactured<2>(h.coords, h.N, ctx->p, b, (cudaStream_t)stream));
@@ -1527,6 +1577,7 @@ int pmg_get_patch_map(const pmg_ctx* ctx, int level, int64_t* out) {
 int pmg_get_inv_diag(pmg_ctx* ctx, int level, int k, double* out, void* stream) {
   int st = check_level(ctx, level);
   if (st) return st;
+  PMG_GUARD_CTX(ctx);
   if (k < 0 || k >= ctx->npl || !out) return fail(ctx, PMG_ERR_ARG, "bad p-level");
   HLevel& h = ctx->L[level];
   const size_t ndq = ipow_sz((size_t)h.pl[k].q * h.N + 1, ctx->dim);
@@ -1595,6 +1646,7 @@ int pmg_tuning(const pmg_ctx* ctx, int* variant, int* threads, int* ppb_out, flo
 int pmg_features(pmg_ctx* ctx, int level, int k, float* X, void* stream) {
   int st = check_level(ctx, level);
   if (st) return st;
+  PMG_GUARD_CTX(ctx);
   if (k < 0 || k >= ctx->npl || !X) return fail(ctx, PMG_ERR_ARG, "bad p-level or null output");
   HLevel& h = ctx->L[level];
   ST(features_launch(ctx->dim, h.coords, h.kappa, h.N, h.pl[k].q, ctx->npl - 1 - k, (int)h.npatch, X,
@@ -1604,7 +1656,7 @@ int pmg_features(pmg_ctx* ctx, int level, int k, float* X, void* stream) {
 
 int pmg_set_mlp(pmg_ctx* ctx, const float* params, const float* norm) {
   if (!ctx || !params || !norm) return PMG_ERR_ARG;
-  CU(cudaSetDevice(ctx->device));
+  PMG_GUARD_CTX(ctx);
   if (!ctx->mlp_params) DALLOC(ctx->mlp_params, PMG_MLP_NPARAM);
   if (!ctx->mlp_norm) DALLOC(ctx->mlp_norm, PMG_MLP_NNORM);
   for (int i = 0; i < 16; ++i)
@@ -1615,6 +1667,54 @@ int pmg_set_mlp(pmg_ctx* ctx, const float* params, const float* norm) {
   return PMG_OK;
 }
 
+int pmg_mlp_targets(pmg_ctx* ctx, int level, int k, float* T, void* stream) {
+  int st = check_level(ctx, level);
+  if (st) return st;
+  PMG_GUARD_CTX(ctx);
+  if (k < 0 || k >= ctx->npl || !T) return fail(ctx, PMG_ERR_ARG, "bad p-level or null output");
+  const HLevel& h = ctx->L[level];
+  if (h.pl[k].q < 2) return fail(ctx, PMG_ERR_ARG, "the p = 1 level has no Lanczos estimates");
+  ST(targets_launch(h.pl[k].ritz, (int64_t)h.npatch, T, (cudaStream_t)stream));
+  return PMG_OK;
+}
+
+// file layout: 8-byte magic "PMGMLP1", uint32 parameter count, uint32
+// normalisation count, the parameters, the normalisation floats (host byte order)
+static const char kMlpMagic[8] = {'P', 'M', 'G', 'M', 'L', 'P', '1', 0};
+
+int pmg_mlp_save(pmg_ctx* ctx, const char* path) {
+  if (!ctx || !path) return PMG_ERR_ARG;
+  if (!ctx->mlp_params) return fail(ctx, PMG_ERR_ARG, "no network installed (pmg_set_mlp or pmg_mlp_load)");
+  PMG_GUARD_CTX(ctx);
+  std::vector<float> prm(PMG_MLP_NPARAM), nrm(PMG_MLP_NNORM);
+  CU(cudaMemcpy(prm.data(), ctx->mlp_params, prm.size() * sizeof(float), cudaMemcpyDeviceToHost));
+  CU(cudaMemcpy(nrm.data(), ctx->mlp_norm, nrm.size() * sizeof(float), cudaMemcpyDeviceToHost));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(ctx, PMG_ERR_ARG, "cannot open the file for writing");
+  const uint32_t counts[2] = {PMG_MLP_NPARAM, PMG_MLP_NNORM};
+  bool ok = std::fwrite(kMlpMagic, 1, 8, f) == 8 && std::fwrite(counts, sizeof(uint32_t), 2, f) == 2 &&
+            std::fwrite(prm.data(), sizeof(float), prm.size(), f) == prm.size() &&
+            std::fwrite(nrm.data(), sizeof(float), nrm.size(), f) == nrm.size();
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? PMG_OK : fail(ctx, PMG_ERR_ARG, "short write");
+}
+
+int pmg_mlp_load(pmg_ctx* ctx, const char* path) {
+  if (!ctx || !path) return PMG_ERR_ARG;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(ctx, PMG_ERR_ARG, "cannot open the file");
+  char magic[8] = {};
+  uint32_t counts[2] = {0, 0};
+  std::vector<float> prm(PMG_MLP_NPARAM), nrm(PMG_MLP_NNORM);
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMlpMagic, 8) == 0 &&
+            std::fread(counts, sizeof(uint32_t), 2, f) == 2 && counts[0] == PMG_MLP_NPARAM &&
+            counts[1] == PMG_MLP_NNORM && std::fread(prm.data(), sizeof(float), prm.size(), f) == prm.size() &&
+            std::fread(nrm.data(), sizeof(float), nrm.size(), f) == nrm.size();
+  std::fclose(f);
+  if (!ok) return fail(ctx, PMG_ERR_ARG, "not a network file of this library (magic, sizes or length)");
+  return pmg_set_mlp(ctx, prm.data(), nrm.data());
+}
+
 int pmg_launch_count(const pmg_ctx* ctx, int64_t* n) {
   if (!ctx || !n) return PMG_ERR_ARG;
   *n = ctx->launches;
@@ -1623,7 +1723,7 @@ int pmg_launch_count(const pmg_ctx* ctx, int64_t* n) {
 
 int pmg_fma_peak(pmg_ctx* ctx, int precision, double* flops) {
   if (!ctx || !flops) return PMG_ERR_ARG;
-  CU(cudaSetDevice(ctx->device));
+  PMG_GUARD_CTX(ctx);
   int nsm = 0;
   CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
   const int block = 256, grid = nsm * 8;

@@ -39,6 +39,25 @@ __host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * i
 // accesses.
 extern __shared__ __align__(16) unsigned char pmg_smem[];
 
+// Geometry functors (gcell) return the G base pointer of a cell; a functor
+// type that declares `static constexpr bool kShared = true` serves G from
+// shared memory, every other one from global memory, where it is read
+// through the read-only data path (ld.global.nc), since G does not change
+// during a launch.
+template <typename GF, typename = void>
+struct GeomInShared {
+  static constexpr bool value = false;
+};
+template <typename GF>
+struct GeomInShared<GF, decltype((void)GF::kShared)> {
+  static constexpr bool value = GF::kShared;
+};
+template <typename GF, typename T>
+__device__ __forceinline__ T gload(const T* p) {
+  if constexpr (GeomInShared<GF>::value) return *p;
+  else return __ldg(p);
+}
+
 template <typename T>
 __device__ __forceinline__ T* smem_ptr(T* p) {
   const unsigned off = (unsigned)(__cvta_generic_to_shared((const void*)p) - __cvta_generic_to_shared(pmg_smem));
@@ -165,22 +184,64 @@ struct SF {
       else v[k] = src[k * stride];
     }
   }
-  // nodes -> Gauss points of every cell of the line
+  // ---- y = M x for the n x n matrix KIND (EO_B, EO_BT, EO_D, EO_DT) of
+  // degree Q, from the even and odd parts of x: with h = n / 2 and
+  // M[n-1-i][n-1-j] = S M[i][j], the outputs i and n-1-i are E_i + O_i and
+  // S (E_i - O_i), E_i = sum_j Ee[i][j] (x_j + x_{n-1-j}) (+ Em[i] x_h for odd n),
+  // O_i = sum_j Eo[i][j] (x_j - x_{n-1-j}); about half the multiplications of
+  // the plain product (12-13 instead of 25 at n = 5, 41 instead of 81 at n = 9).
+  template <int KIND>
+  __device__ __forceinline__ static void eo_apply(const T (&x)[n], T (&y)[n]) {
+    constexpr int h = n / 2;
+    constexpr bool odd = (n & 1) != 0;
+    constexpr bool anti = (KIND == EO_D || KIND == EO_DT);
+    T xe[h > 0 ? h : 1], xo[h > 0 ? h : 1];
+#pragma unroll
+    for (int j = 0; j < h; ++j) {
+      xe[j] = x[j] + x[n - 1 - j];
+      xo[j] = x[j] - x[n - 1 - j];
+    }
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      T e = odd ? tabEm<T>(KIND, Q, i) * x[h] : T(0);
+#pragma unroll
+      for (int j = 0; j < h; ++j) e += tabEe<T>(KIND, Q, i, j) * xe[j];
+      T o = T(0);
+#pragma unroll
+      for (int j = 0; j < h; ++j) o += tabEo<T>(KIND, Q, i, j) * xo[j];
+      y[i] = e + o;
+      y[n - 1 - i] = anti ? o - e : e - o;
+    }
+    if constexpr (odd) {
+      T m = T(0);
+      if constexpr (anti) {
+#pragma unroll
+        for (int j = 0; j < h; ++j) m += tabEo<T>(KIND, Q, h, j) * xo[j];
+      } else {
+        m = tabEm<T>(KIND, Q, h) * x[h];
+#pragma unroll
+        for (int j = 0; j < h; ++j) m += tabEe<T>(KIND, Q, h, j) * xe[j];
+      }
+      y[h] = m;
+    }
+  }
+  // the same on cell c of a line: x = in[c * step .. c * step + n), y to out[c * n ..)
+  template <int KIND, int LIN, int LOUT>
+  __device__ __forceinline__ static void eo_cell(const T (&in)[LIN], int base_in, T (&out)[LOUT], int base_out) {
+    T x[n], y[n];
+#pragma unroll
+    for (int a = 0; a < n; ++a) x[a] = in[base_in + a];
+    eo_apply<KIND>(x, y);
+#pragma unroll
+    for (int a = 0; a < n; ++a) out[base_out + a] = y[a];
+  }
+
+  // nodes -> Gauss points of every cell of the line (the patch's Dirichlet
+  // end values are zero in v)
   template <bool INTIN>
   __device__ __forceinline__ static void interp_line(const T (&v)[M], T (&w)[QP]) {
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const int a0 = (INTIN && NC == 2 && c == 0) ? 1 : 0;
-      const int a1 = (INTIN && NC == 2 && c == NC - 1) ? Q - 1 : Q;
-#pragma unroll
-      for (int g = 0; g < n; ++g) {
-        T s = T(0);
-#pragma unroll
-        for (int a = 0; a <= Q; ++a)
-          if (a >= a0 && a <= a1) s += tabB<T>(Q, g, a) * v[c * Q + a];
-        w[c * n + g] = s;
-      }
-    }
+    for (int c = 0; c < NC; ++c) eo_cell<EO_B>(v, c * Q, w, c * n);
   }
   // Gauss points of every cell -> nodes (transposed interpolation); NC = 2:
   // interior nodes 1..M-2 only, written to out[(k-1)*stride] (ACC: added);
@@ -188,27 +249,17 @@ struct SF {
   // then cell 1's.
   template <bool ACC, typename PUT>
   __device__ __forceinline__ static void integ_line(const T (&w)[QP], const PUT& put) {
+    T y[QP];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) eo_cell<EO_BT>(w, c * n, y, c * n);
     if constexpr (NC == 1) {
 #pragma unroll
-      for (int a = 0; a <= Q; ++a) {
-        T s = put.init(a);
-#pragma unroll
-        for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, a) * w[g];
-        put(a, s);
-      }
+      for (int a = 0; a <= Q; ++a) put(a, ACC ? put.init(a) + y[a] : y[a]);
     } else {
 #pragma unroll
       for (int k = 1; k <= M - 2; ++k) {
-        T s = put.init(k - 1);
-        if (k <= Q) {
-#pragma unroll
-          for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, k) * w[g];
-        }
-        if (k >= Q) {
-#pragma unroll
-          for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, k - Q) * w[n + g];
-        }
-        put(k - 1, s);
+        const T t = (k < Q) ? y[k] : (k == Q ? y[Q] + y[n] : y[n + k - Q]);
+        put(k - 1, ACC ? put.init(k - 1) + t : t);
       }
     }
   }
@@ -249,20 +300,36 @@ struct SF {
                                                            T* __restrict__ F, int i) {
     constexpr int AX = DIM - 1;
     constexpr int I = ipow(QP, AX);
-    T v[M], w[QP];
+    T v[M], w[QP], f[QP];
     load_line<INTIN>(in + i, I, v);
     interp_line<INTIN>(v, w);
 #pragma unroll
     for (int g = 0; g < QP; ++g) V[g * I + i] = w[g];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
+    for (int c = 0; c < NC; ++c) eo_cell<EO_D>(w, c * n, f, c * n);
 #pragma unroll
-      for (int g = 0; g < n; ++g) {
-        T s = T(0);
+    for (int g = 0; g < QP; ++g) F[g * I + i] = f[g];
+  }
+
+  // ---- backward along the last axis for one line: w = (partial sums of the
+  // other directions) + D^T f per cell, then B^T per cell; out[(k - 1) * I]
+  // receives interior node k (NC = 2) or node k (NC = 1).
+  __device__ __forceinline__ static void last_bwd(const T (&part)[QP], const T (&f)[QP], T* __restrict__ out,
+                                                  int I) {
+    T t[QP], w[QP], y[QP];
 #pragma unroll
-        for (int h = 0; h < n; ++h) s += tabD<T>(Q, g, h) * w[c * n + h];
-        F[(c * n + g) * I + i] = s;
-      }
+    for (int c = 0; c < NC; ++c) eo_cell<EO_DT>(f, c * n, t, c * n);
+#pragma unroll
+    for (int g = 0; g < QP; ++g) w[g] = part[g] + t[g];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) eo_cell<EO_BT>(w, c * n, y, c * n);
+    if constexpr (NC == 1) {
+#pragma unroll
+      for (int a = 0; a <= Q; ++a) out[a * I] = y[a];
+    } else {
+#pragma unroll
+      for (int k = 1; k <= M - 2; ++k)
+        out[(k - 1) * I] = (k < Q) ? y[k] : (k == Q ? y[Q] + y[n] : y[n + k - Q]);
     }
   }
 
@@ -274,49 +341,14 @@ struct SF {
                                                             const T* __restrict__ Vq, T* __restrict__ out, int i) {
     constexpr int AX = DIM - 1;
     constexpr int I = ipow(QP, AX);
-    T w[NC][n];
+    T f[QP], part[QP];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      T f[n];
-#pragma unroll
-      for (int g = 0; g < n; ++g) f[g] = F[(c * n + g) * I + i];
-#pragma unroll
-      for (int h = 0; h < n; ++h) {
-        T s = Vp[(c * n + h) * I + i];
-        if (DIM == 3) s += Vq[(c * n + h) * I + i];
-#pragma unroll
-        for (int g = 0; g < n; ++g) s += tabD<T>(Q, g, h) * f[g];
-        w[c][h] = s;
-      }
+    for (int g = 0; g < QP; ++g) {
+      f[g] = F[g * I + i];
+      part[g] = Vp[g * I + i];
+      if (DIM == 3) part[g] += Vq[g * I + i];
     }
-    if (NC == 1) {
-#pragma unroll
-      for (int a = 0; a <= Q; ++a) {
-        T s = T(0);
-#pragma unroll
-        for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, a) * w[0][g];
-        out[a * I + i] = s;
-      }
-    } else {
-#pragma unroll
-      for (int a = 1; a <= Q; ++a) {
-        T s = T(0);
-#pragma unroll
-        for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, a) * w[0][g];
-        if (a == Q) {
-#pragma unroll
-          for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, 0) * w[NC - 1][g];
-        }
-        out[(a - 1) * I + i] = s;
-      }
-#pragma unroll
-      for (int a = 1; a < Q; ++a) {
-        T s = T(0);
-#pragma unroll
-        for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, a) * w[NC - 1][g];
-        out[(Q + a - 1) * I + i] = s;
-      }
-    }
+    last_bwd(part, f, out + i, I);
   }
 
   // ---- quadrature-point product: F_k <- sum_l G_kl F_l
@@ -339,14 +371,14 @@ struct SF {
     const T* G = gcell(pp, cslot) + lg;
     if (DIM == 3) {
       const T g0 = F[pt], g1 = F[NQ + pt], g2 = F[2 * NQ + pt];
-      const T G00 = G[0], G01 = G[NGC], G02 = G[2 * NGC], G11 = G[3 * NGC], G12 = G[4 * NGC],
-              G22 = G[5 * NGC];
+      const T G00 = gload<GF>(G), G01 = gload<GF>(G + NGC), G02 = gload<GF>(G + 2 * NGC),
+              G11 = gload<GF>(G + 3 * NGC), G12 = gload<GF>(G + 4 * NGC), G22 = gload<GF>(G + 5 * NGC);
       F[pt] = G00 * g0 + G01 * g1 + G02 * g2;
       F[NQ + pt] = G01 * g0 + G11 * g1 + G12 * g2;
       F[2 * NQ + pt] = G02 * g0 + G12 * g1 + G22 * g2;
     } else {
       const T g0 = F[pt], g1 = F[NQ + pt];
-      const T G00 = G[0], G01 = G[NGC], G11 = G[2 * NGC];
+      const T G00 = gload<GF>(G), G01 = gload<GF>(G + NGC), G11 = gload<GF>(G + 2 * NGC);
       F[pt] = G00 * g0 + G01 * g1;
       F[NQ + pt] = G01 * g0 + G11 * g1;
     }
@@ -365,36 +397,17 @@ struct SF {
     constexpr int L = INTIN ? Mi : M;
     constexpr int I = NLINE;
     static_assert(L > 0, "");
+    T v[M], w[QP];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      T v[n];
-#pragma unroll
-      for (int a = 0; a <= Q; ++a) {
-        const int k = c * Q + a;
-        if (INTIN) {
-          const bool ok = (k >= 1) && (k <= M - 2);
-          v[a] = ok ? in[(k - 1) * I + i] : T(0);
-        } else {
-          v[a] = in[k * I + i];
-        }
-      }
-      T w[n];
-#pragma unroll
-      for (int g = 0; g < n; ++g) {
-        T s = T(0);
-#pragma unroll
-        for (int a = 0; a <= Q; ++a) s += tabB<T>(Q, g, a) * v[a];
-        w[g] = s;
-        V[(c * n + g) * I + i] = s;
-      }
-#pragma unroll
-      for (int g = 0; g < n; ++g) {
-        T s = T(0);
-#pragma unroll
-        for (int h = 0; h < n; ++h) s += tabD<T>(Q, g, h) * w[h];
-        gz[c * n + g] = s;
-      }
+    for (int k = 0; k < M; ++k) {
+      if (INTIN) v[k] = (k >= 1 && k <= M - 2) ? in[(k - 1) * I + i] : T(0);
+      else v[k] = in[k * I + i];
     }
+    interp_line<INTIN>(v, w);
+#pragma unroll
+    for (int g = 0; g < QP; ++g) V[g * I + i] = w[g];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) eo_cell<EO_D>(w, c * n, gz, c * n);
   }
 
   // quadrature-point product along one line: F_0 .. F_{d-2} (other-direction
@@ -429,14 +442,14 @@ struct SF {
         const int pt = (c * n + g) * I + i;
         const T* G = Gc + g * GSTRIDE;
         if (DIM == 3) {
-          const T G00 = G[0], G01 = G[NGC], G02 = G[2 * NGC], G11 = G[3 * NGC], G12 = G[4 * NGC],
-                  G22 = G[5 * NGC];
+          const T G00 = gload<GF>(G), G01 = gload<GF>(G + NGC), G02 = gload<GF>(G + 2 * NGC),
+                  G11 = gload<GF>(G + 3 * NGC), G12 = gload<GF>(G + 4 * NGC), G22 = gload<GF>(G + 5 * NGC);
           const T g0 = F[pt], g1 = F[NQ + pt], g2 = gz[c * n + g];
           F[pt] = G00 * g0 + G01 * g1 + G02 * g2;
           F[NQ + pt] = G01 * g0 + G11 * g1 + G12 * g2;
           fz[c * n + g] = G02 * g0 + G12 * g1 + G22 * g2;
         } else {
-          const T G00 = G[0], G01 = G[NGC], G11 = G[2 * NGC];
+          const T G00 = gload<GF>(G), G01 = gload<GF>(G + NGC), G11 = gload<GF>(G + 2 * NGC);
           const T g0 = F[pt], g1 = gz[c * n + g];
           F[pt] = G00 * g0 + G01 * g1;
           fz[c * n + g] = G01 * g0 + G11 * g1;
@@ -446,53 +459,18 @@ struct SF {
   }
 
   // transposed derivative along the last axis (fz in registers) added to the
-  // other directions' sums in Vp, then backward integration along that axis:
-  // output [Lo][I]
-  // Vq: a second array of partial sums added to Vp (3D: the x and y
-  // directions' transposed derivatives), or NULL
+  // other directions' sums (Vp, and Vq in 3D), then backward integration
+  // along that axis: output [Lo][I]
   __device__ __forceinline__ static void line_bwd(const T (&fz)[QP], const T* __restrict__ Vp,
                                                   const T* __restrict__ Vq, T* __restrict__ out, int i) {
     constexpr int I = NLINE;
-    T w[NC][n];
+    T part[QP];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-#pragma unroll
-      for (int h = 0; h < n; ++h) {
-        T s = Vp[(c * n + h) * I + i];
-        if (DIM == 3) s += Vq[(c * n + h) * I + i];
-#pragma unroll
-        for (int g = 0; g < n; ++g) s += tabD<T>(Q, g, h) * fz[c * n + g];
-        w[c][h] = s;
-      }
+    for (int g = 0; g < QP; ++g) {
+      part[g] = Vp[g * I + i];
+      if (DIM == 3) part[g] += Vq[g * I + i];
     }
-    if (NC == 1) {
-#pragma unroll
-      for (int a = 0; a <= Q; ++a) {
-        T s = T(0);
-#pragma unroll
-        for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, a) * w[0][g];
-        out[a * I + i] = s;
-      }
-    } else {
-#pragma unroll
-      for (int a = 1; a <= Q; ++a) {
-        T s = T(0);
-#pragma unroll
-        for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, a) * w[0][g];
-        if (a == Q) {
-#pragma unroll
-          for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, 0) * w[NC - 1][g];
-        }
-        out[(a - 1) * I + i] = s;
-      }
-#pragma unroll
-      for (int a = 1; a < Q; ++a) {
-        T s = T(0);
-#pragma unroll
-        for (int g = 0; g < n; ++g) s += tabB<T>(Q, g, a) * w[NC - 1][g];
-        out[(Q + a - 1) * I + i] = s;
-      }
-    }
+    last_bwd(part, fz, out + i, I);
   }
 
   // ---- collocation derivative along AX on [O][QP][I], one line per item
@@ -502,19 +480,13 @@ struct SF {
     const int i = item % I, o = item / I;
     const T* src = in + o * QP * I + i;
     T* dst = out + o * QP * I + i;
-    T v[QP];
+    T v[QP], y[QP];
 #pragma unroll
     for (int h = 0; h < QP; ++h) v[h] = src[h * I];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
+    for (int c = 0; c < NC; ++c) eo_cell<EO_D>(v, c * n, y, c * n);
 #pragma unroll
-      for (int g = 0; g < n; ++g) {
-        T s = T(0);
-#pragma unroll
-        for (int h = 0; h < n; ++h) s += tabD<T>(Q, g, h) * v[c * n + h];
-        dst[(c * n + g) * I] = s;
-      }
-    }
+    for (int g = 0; g < QP; ++g) dst[g * I] = y[g];
   }
 
   // ---- transposed derivative along AX, written (ACC = false) or added
@@ -524,23 +496,13 @@ struct SF {
     const int i = item % I, o = item / I;
     const T* src = in + o * QP * I + i;
     T* dst = out + o * QP * I + i;
-    T v[QP], a[QP];
+    T v[QP], y[QP];
 #pragma unroll
     for (int g = 0; g < QP; ++g) v[g] = src[g * I];
-    if (ACC) {
 #pragma unroll
-      for (int g = 0; g < QP; ++g) a[g] = dst[g * I];
-    }
+    for (int c = 0; c < NC; ++c) eo_cell<EO_DT>(v, c * n, y, c * n);
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-#pragma unroll
-      for (int h = 0; h < n; ++h) {
-        T s = ACC ? a[c * n + h] : T(0);
-#pragma unroll
-        for (int g = 0; g < n; ++g) s += tabD<T>(Q, g, h) * v[c * n + g];
-        dst[(c * n + h) * I] = s;
-      }
-    }
+    for (int g = 0; g < QP; ++g) dst[g * I] = ACC ? dst[g * I] + y[g] : y[g];
   }
 
   // ---- transposed derivative along AX in place: the thread reads its whole
@@ -550,19 +512,13 @@ struct SF {
     constexpr int I = ipow(QP, AX);
     const int i = item % I, o = item / I;
     T* p = F + o * QP * I + i;
-    T v[QP];
+    T v[QP], y[QP];
 #pragma unroll
     for (int g = 0; g < QP; ++g) v[g] = p[g * I];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
+    for (int c = 0; c < NC; ++c) eo_cell<EO_DT>(v, c * n, y, c * n);
 #pragma unroll
-      for (int h = 0; h < n; ++h) {
-        T s = T(0);
-#pragma unroll
-        for (int g = 0; g < n; ++g) s += tabD<T>(Q, g, h) * v[c * n + g];
-        p[(c * n + h) * I] = s;
-      }
-    }
+    for (int g = 0; g < QP; ++g) p[g * I] = y[g];
   }
 
   // ---- final backward integration along x: like bwd_item<0, false> but every
@@ -735,7 +691,7 @@ struct SF {
 #pragma unroll
         for (int d = 0; d < DIM; ++d) g[u][d] = scr[off[u] + d * NQ];
 #pragma unroll
-        for (int k = 0; k < NCOMP; ++k) G[u][k] = Gp[k * NGC];
+        for (int k = 0; k < NCOMP; ++k) G[u][k] = gload<GF>(Gp + k * NGC);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -792,17 +748,11 @@ struct SF {
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         if (!ok[u]) continue;
+        T y[QP];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
+        for (int c = 0; c < NC; ++c) eo_cell<TRANS ? EO_DT : EO_D>(v[u], c * n, y, c * n);
 #pragma unroll
-          for (int g = 0; g < n; ++g) {
-            T s = ACC ? a[u][c * n + g] : T(0);
-#pragma unroll
-            for (int h = 0; h < n; ++h)
-              s += (TRANS ? tabD<T>(Q, h, g) : tabD<T>(Q, g, h)) * v[u][c * n + h];
-            dst[u][(c * n + g) * str[u]] = s;
-          }
-        }
+        for (int g = 0; g < QP; ++g) dst[u][g * str[u]] = ACC ? a[u][g] + y[g] : y[g];
       }
     }
   }

@@ -5,11 +5,26 @@
 
 namespace pmg {
 
+// Even/odd parts of the n x n (n = q + 1) one-dimensional matrices M with
+// M[n-1-i][n-1-j] = S M[i][j]: the interpolation B and its transpose (S = +1;
+// Gauss points and Gauss-Lobatto nodes are symmetric about 1/2) and the
+// collocation derivative D and its transpose (S = -1).  With h = n / 2,
+//   Ee[i][j] = (M[i][j] + M[i][n-1-j]) / 2,  Eo[i][j] = (M[i][j] - M[i][n-1-j]) / 2  (j < h),
+//   Em[i]    = M[i][h] (n odd),
+// for rows i <= h; y = M x then follows from the even and odd parts of x
+// (sf.cuh, eo_apply).
+#define PMG_EOR (PMG_MAXQ / 2 + 1)       // rows i = 0 .. h (h <= 4 for n <= 9)
+#define PMG_EOC ((PMG_MAXQ + 1) / 2)     // columns j < h
+enum { EO_B = 0, EO_BT = 1, EO_D = 2, EO_DT = 3 };
+
 template <typename T>
 struct Tables {
   T B[PMG_MAXQ + 1][PMG_MAXQ + 1][PMG_MAXQ + 1];
   T D[PMG_MAXQ + 1][PMG_MAXQ + 1][PMG_MAXQ + 1];
   T E[PMG_MAXQ + 1][PMG_MAXQ + 1][PMG_MAXQ + 1];
+  T Ee[4][PMG_MAXQ + 1][PMG_EOR][PMG_EOC];
+  T Eo[4][PMG_MAXQ + 1][PMG_EOR][PMG_EOC];
+  T Em[4][PMG_MAXQ + 1][PMG_EOR];
 };
 
 struct Rules {

@@ -44,6 +44,26 @@ __device__ __forceinline__ double tabE<double>(int qf, int a, int b) { return c_
 template <>
 __device__ __forceinline__ float tabE<float>(int qf, int a, int b) { return c_tab_f32.E[qf][a][b]; }
 
+// even/odd parts of B, B^T, D, D^T (table_types.h)
+template <typename T>
+__device__ __forceinline__ T tabEe(int k, int q, int i, int j);
+template <>
+__device__ __forceinline__ double tabEe<double>(int k, int q, int i, int j) { return c_tab_f64.Ee[k][q][i][j]; }
+template <>
+__device__ __forceinline__ float tabEe<float>(int k, int q, int i, int j) { return c_tab_f32.Ee[k][q][i][j]; }
+template <typename T>
+__device__ __forceinline__ T tabEo(int k, int q, int i, int j);
+template <>
+__device__ __forceinline__ double tabEo<double>(int k, int q, int i, int j) { return c_tab_f64.Eo[k][q][i][j]; }
+template <>
+__device__ __forceinline__ float tabEo<float>(int k, int q, int i, int j) { return c_tab_f32.Eo[k][q][i][j]; }
+template <typename T>
+__device__ __forceinline__ T tabEm(int k, int q, int i);
+template <>
+__device__ __forceinline__ double tabEm<double>(int k, int q, int i) { return c_tab_f64.Em[k][q][i]; }
+template <>
+__device__ __forceinline__ float tabEm<float>(int k, int q, int i) { return c_tab_f32.Em[k][q][i]; }
+
 static inline int upload_tables_tu(const Tables<double>& h64, const Tables<float>& h32, const Rules& r) {
   cudaError_t e = cudaMemcpyToSymbol(c_tab_f64, &h64, sizeof(h64));
   if (e != cudaSuccess) return (int)e;

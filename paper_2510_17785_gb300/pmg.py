@@ -24,7 +24,7 @@ SMOOTHER_CHEBYSHEV, SMOOTHER_JACOBI, SMOOTHER_CARTESIAN = 0, 1, 2
 BOUNDS_LANCZOS, BOUNDS_FIXED, BOUNDS_USER, BOUNDS_MLP = 0, 1, 2, 3
 MLP_NPARAM, MLP_NNORM = 5378, 36
 PREC_FP64, PREC_MIXED = 0, 1
-NUM_VARIANTS = 10              # PMG_NUM_VARIANTS of include/pmg.h
+NUM_VARIANTS = 13              # PMG_NUM_VARIANTS of include/pmg.h
 KAPPA_ARITHMETIC, KAPPA_GEOMETRIC, KAPPA_HARMONIC = 0, 1, 2
 
 # every symbol include/pmg.h declares
@@ -36,7 +36,8 @@ SYMBOLS = (
     "pmg_get_patch_map", "pmg_get_inv_diag", "pmg_sweep_flops", "pmg_launch_count", "pmg_fma_peak",
     "pmg_lanczos_bounds_noalloc", "pmg_tuning", "pmg_default_train_options", "pmg_features", "pmg_mlp_grad",
     "pmg_mlp_train", "pmg_mlp_predict", "pmg_set_mlp", "pmg_solve_gmres", "pmg_batch_solve_cg",
-    "pmg_tuning_level",
+    "pmg_tuning_level", "pmg_coeff_upload", "pmg_mlp_init", "pmg_mlp_targets", "pmg_mlp_norm", "pmg_mlp_save",
+    "pmg_mlp_load",
 )
 
 
@@ -115,6 +116,12 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pmg_solve_gmres": (i, [vp, vp, vp, d, i, i, i, P(i), P(d), vp]),
         "pmg_batch_solve_cg": (i, [vp, i, vp, vp, d, i, P(i), P(d), P(i)]),
         "pmg_tuning_level": (i, [vp, i, P(i), P(C.c_float)]),
+        "pmg_coeff_upload": (i, [vp, i, vp]),
+        "pmg_mlp_init": (None, [C.c_uint64, vp]),
+        "pmg_mlp_targets": (i, [vp, i, i, vp, vp]),
+        "pmg_mlp_norm": (i, [i, vp, vp, i64, vp]),
+        "pmg_mlp_save": (i, [vp, C.c_char_p]),
+        "pmg_mlp_load": (i, [vp, C.c_char_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -168,37 +175,38 @@ def batch_solve_cg(ctxs, bs, us, rtol=1e-8, maxit=200, check=True):
 
 
 def mlp_init(seed: int = 0) -> np.ndarray:
-    """Initial MLP parameters in the library's layout (W1 [64][16], b1 [64],
-    W2 [64][64], b2 [64], W3 [2][64], b3 [2], row-major, concatenated):
-    weights uniform in +-sqrt(6 / fan_in), biases zero; FP32."""
-    rng = np.random.default_rng(seed)
-    parts = []
-    for rows, cols in ((64, 16), (64, 64), (2, 64)):
-        lim = np.sqrt(6.0 / cols)
-        parts.append(rng.uniform(-lim, lim, size=rows * cols))
-        parts.append(np.zeros(rows))
-    theta = np.concatenate(parts).astype(np.float32)
-    assert theta.size == MLP_NPARAM
+    """Initial MLP parameters from the library (pmg_mlp_init): float32 array of
+    MLP_NPARAM values in the library's layout."""
+    theta = np.zeros(MLP_NPARAM, dtype=np.float32)
+    load().pmg_mlp_init(seed, theta.ctypes.data)
     return theta
 
 
-def mlp_training_data(ctx, dtype=None):
-    """(features [n, 16], targets [n, 2] = (log theta_max, log theta_min)) of every
+def mlp_training_data(ctx):
+    """(features X [n, 16], targets T [n, 2]) as float32 CUDA tensors: every
     patch, mesh level and p-level q > 1 of a set-up context with Lanczos
-    intervals: the training set of the interval network."""
+    intervals (pmg_features and pmg_mlp_targets), stacked."""
     import torch
     Xs, Ts = [], []
     for lv in range(ctx.n_levels):
         npatch, _ = ctx.num_patches(lv)
-        ritz = ctx.get_ritz(lv)
         for k, q in enumerate(ctx.p_levels()):
             if q == 1:
                 continue
             X = torch.zeros((npatch, 16), dtype=torch.float32, device="cuda")
+            T = torch.zeros((npatch, 2), dtype=torch.float32, device="cuda")
             ctx.features(lv, k, X)
-            Xs.append(X.cpu().numpy())
-            Ts.append(np.log(ritz[:, k, ::-1]))
-    return np.concatenate(Xs), np.ascontiguousarray(np.concatenate(Ts))
+            ctx.mlp_targets(lv, k, T)
+            Xs.append(X)
+            Ts.append(T)
+    return torch.cat(Xs), torch.cat(Ts)
+
+
+def mlp_norm(X, T, device=0) -> np.ndarray:
+    """The MLP_NNORM normalisation floats of a training set (pmg_mlp_norm)."""
+    norm = np.zeros(MLP_NNORM, dtype=np.float32)
+    _check_rc(load().pmg_mlp_norm(device, _ptr(X), _ptr(T), X.shape[0], norm.ctypes.data), "pmg_mlp_norm")
+    return norm
 
 
 def mlp_grad(params, norm, X, T, asym=4.0, device=0):
@@ -410,6 +418,19 @@ class Context:
 
     def features(self, level, k, X, stream=None):
         self._check(self.lib.pmg_features(self.h, level, k, _ptr(X), _stream(stream)))
+
+    def mlp_targets(self, level, k, T, stream=None):
+        self._check(self.lib.pmg_mlp_targets(self.h, level, k, _ptr(T), _stream(stream)))
+
+    def mlp_save(self, path: str):
+        self._check(self.lib.pmg_mlp_save(self.h, os.fsencode(path)))
+
+    def mlp_load(self, path: str):
+        self._check(self.lib.pmg_mlp_load(self.h, os.fsencode(path)))
+
+    def coeff_upload(self, level: int, kappa: np.ndarray):
+        kappa = np.ascontiguousarray(kappa, dtype=np.float64)
+        self._check(self.lib.pmg_coeff_upload(self.h, level, kappa.ctypes.data))
 
     def set_mlp(self, params: np.ndarray, norm: np.ndarray):
         params = np.ascontiguousarray(params, dtype=np.float32)

@@ -6,8 +6,10 @@ computation), and the GMG-preconditioned CG solve to 1e-8."""
 import numpy as np
 import pytest
 
-from oracle import fem, lanczos as lz, patch as pt
+from oracle import patch as pt
 from paper_2510_17785_gb300 import inputs
+
+import oracle_pool
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -36,24 +38,17 @@ def test_colour0_sweep_sampled_patches(c2):
     ctx.patch_smooth_colour(lf, 0, torch.tensor(b, device="cuda"), u)
     torch.cuda.synchronize()
     u1 = u.cpu().numpy()
-    m = fem.StructuredMesh(w.dim, w.N, prob.coords, prob.kappa)
     verts = [v for v in pt.interior_vertices(w.dim, w.N) if pt.colour_of(v) == 0]
     rng = np.random.default_rng(23)
     pick = [verts[i] for i in rng.choice(len(verts), 12, replace=False)]
     pick.append(verts[0])
     pick.append(verts[-1])
-    changed = np.zeros(len(u0), dtype=bool)
-    for v in pick:
-        P = pt.Patch(m, v, pt.levels_halving(w.p))
-        j = pt.patch_id(w.dim, w.N, v)
-        d = pt.local_solve(P, P.residual(u0, b), pt.Smoother(), lz.lanczos_bounds_fn(seed=0)(P, j), 1)
-        idx = P.lv[w.p].interior
+    for v, (j, idx, d, _) in zip(pick, oracle_pool.patch_updates(w.name, pick, u0, b)):
         got = u1[idx] - u0[idx]
         assert np.abs(got - d).max() < 1e-12 * np.abs(d).max(), v
-        changed[idx] = True
-    # DoFs outside every colour-0 patch interior are untouched
-    P0 = [pt.Patch(m, v, [1]) for v in verts[:1]]
-    assert P0
+    # DoFs outside every colour-0 patch interior are untouched, bit for bit
+    outside = ~oracle_pool.interior_union_mask(w.dim, w.p, w.N, 0)
+    assert outside.sum() > 0 and np.array_equal(u1[outside], u0[outside])
 
 
 def test_cg_to_1e8(c2):
@@ -95,33 +90,26 @@ def test_sweep_sampled_patches_large_degree(name, precision):
     ctx.mesh_structured(w.dim, w.N, w.p, levels, prob.coords, prob.kappa)
     ctx.setup()
     lf = levels - 1
-    m = fem.StructuredMesh(w.dim, w.N, prob.coords, prob.kappa)
     verts = [v for v in pt.interior_vertices(w.dim, w.N) if pt.colour_of(v) == 0]
     rng = np.random.default_rng(24)
-    pick = [verts[i] for i in rng.choice(len(verts), 2, replace=False)]
+    pick = [verts[i] for i in rng.choice(len(verts), 8, replace=False)]
+    u0 = inputs.random_vector(25, w.dim, w.p, w.N)
+    b = inputs.random_vector(26, w.dim, w.p, w.N)
+    # oracle first (one pool pass): each sampled patch's update and its Lanczos intervals
+    upd = oracle_pool.patch_updates(w.name, pick, u0, b)
     qs = ctx.p_levels()
     lohi = ctx.get_bounds(lf)
-    patches, bounds = [], []
-    for v in pick:
-        P = pt.Patch(m, v, pt.levels_halving(w.p))
-        j = pt.patch_id(w.dim, w.N, v)
-        bd = lz.lanczos_bounds_fn(seed=0)(P, j)
+    for j, _, _, bd in upd:
         for k, q in enumerate(qs):
             if q > 1:
                 lohi[j, k] = bd[q]
-        patches.append((P, j))
-        bounds.append(bd)
     ctx.set_bounds(lf, lohi)
-    u0 = inputs.random_vector(25, w.dim, w.p, w.N)
-    b = inputs.random_vector(26, w.dim, w.p, w.N)
     u = torch.tensor(u0, device="cuda")
     ctx.patch_smooth_colour(lf, 0, torch.tensor(b, device="cuda"), u)
     torch.cuda.synchronize()
     u1 = u.cpu().numpy()
     errs = []
-    for (P, j), bd in zip(patches, bounds):
-        d = pt.local_solve(P, P.residual(u0, b), pt.Smoother(), bd, 1)
-        idx = P.lv[w.p].interior
+    for j, idx, d, _ in upd:
         errs.append(np.abs((u1[idx] - u0[idx]) - d).max() / np.abs(d).max())
     print(name, precision, "relative error of the patch updates:", errs)
     assert max(errs) < tol, errs

@@ -123,7 +123,7 @@ def test_paper_jacobi_iteration_counts(key, cases):
     got = []
     for nmg, delta, paper in cases:
         w = inputs.Workload("paper", dim, N, p, delta, "sphere", ("const", 1.0), "uniform", 11)
-        prec = pmg.PREC_MIXED if (dim == 3 and p >= 7) else pmg.PREC_FP64   # FP64 3D patch of degree 7 exceeds shared memory
+        prec = pmg.PREC_FP64
         ctx, prob = _setup(w, levels, smoother=pmg.SMOOTHER_JACOBI, jacobi_omega=0.5, n_mg=nmg, post_reverse=0,
                            precision=prec)
         x = torch.zeros(len(prob.rhs), dtype=torch.float64, device="cuda")
@@ -157,7 +157,7 @@ def test_paper_cartesian_reinforced_iteration_counts(key, cases):
     got = []
     for nmg, delta, paper in cases:
         w = inputs.Workload("paper", dim, N, p, delta, "sphere", ("const", 1.0), "uniform", 11)
-        prec = pmg.PREC_MIXED if (dim == 3 and p >= 7) else pmg.PREC_FP64
+        prec = pmg.PREC_FP64
         ctx, prob = _setup(w, levels, smoother=pmg.SMOOTHER_CARTESIAN, jacobi_omega=0.5, n_mg=nmg, post_reverse=0,
                            precision=prec)
         x = torch.zeros(len(prob.rhs), dtype=torch.float64, device="cuda")

@@ -102,23 +102,6 @@ def test_training_reduces_the_loss():
     assert hist[-1] < 0.1 * hist[0]
 
 
-def _collect(ctxs):
-    """(features, log ritz) of every patch, mesh level and p-level > 1."""
-    Xs, Ts = [], []
-    for ctx in ctxs:
-        for lv in range(ctx.n_levels):
-            npatch, _ = ctx.num_patches(lv)
-            ritz = ctx.get_ritz(lv)
-            for k, q in enumerate(ctx.p_levels()):
-                if q == 1:
-                    continue
-                X = torch.zeros((npatch, 16), dtype=torch.float32, device="cuda")
-                ctx.features(lv, k, X)
-                Xs.append(X.cpu().numpy())
-                Ts.append(np.log(ritz[:, k, ::-1]))     # (log theta_max, log theta_min)
-    return np.concatenate(Xs), np.ascontiguousarray(np.concatenate(Ts))
-
-
 def test_learned_bounds_against_lanczos():
     """Train on Lanczos estimates of several problems, predict the intervals of
     a held-out one: the CG iteration count stays within one of the Lanczos
@@ -128,12 +111,13 @@ def test_learned_bounds_against_lanczos():
     for seed, (dim, N, p) in enumerate([(3, 8, 4), (3, 8, 2), (3, 6, 3), (3, 4, 6), (3, 8, 4), (3, 6, 5)]):
         ctx, _ = _ctx(dim, N, p, 100 + seed, perturb=0.1 + 0.03 * seed, kappa=("loguniform", -1.5, 1.5))
         train.append(ctx)
-    X, T = _collect(train)
+    data = [pmg.mlp_training_data(c) for c in train]      # features and log Lanczos estimates, on the device
     for c in train:
         c.close()
-    norm = _norm(X, T)
-    params = _f32(mlp.init_params(11))
-    hist = pmg.mlp_train(params, _f32(norm), _f32(X), _f32(T), epochs=150, batch=256, lr=2e-3, asym=4.0)
+    X, T = torch.cat([x for x, _ in data]), torch.cat([t for _, t in data])
+    norm = pmg.mlp_norm(X, T)
+    params = _f32(pmg.mlp_init(11))
+    hist = pmg.mlp_train(params, _f32(norm), X, T, epochs=150, batch=256, lr=2e-3, asym=4.0)
     assert hist[-1] < 0.2 * hist[0]
     # held-out problem, GMG-preconditioned CG with both interval sources
     w = inputs.Workload("held", 3, 8, 4, 0.2, "uniform", ("loguniform", -1.5, 1.5), "uniform", 999)
@@ -165,3 +149,57 @@ def test_learned_bounds_against_lanczos():
     assert t_mlp < t_lan
     ctxL.close()
     ctxM.close()
+
+
+def test_library_training_helpers():
+    """pmg_mlp_init: deterministic, weights within +-sqrt(6 / fan_in), zero
+    biases; pmg_mlp_targets: (log theta_max, log theta_min) of the context's
+    Lanczos estimates; pmg_mlp_norm: column means and population standard
+    deviations (+1e-6), checked against numpy."""
+    from paper_2510_17785_gb300 import pmg
+    a, b = pmg.mlp_init(3), pmg.mlp_init(3)
+    assert np.array_equal(a, b) and not np.array_equal(a, pmg.mlp_init(4))
+    o = 0
+    for rows, cols in ((64, 16), (64, 64), (2, 64)):
+        W = a[o:o + rows * cols]
+        assert np.abs(W).max() <= np.sqrt(6.0 / cols) and np.abs(W).max() > 0.9 * np.sqrt(6.0 / cols)
+        assert abs(W.mean()) < 0.1 * np.sqrt(6.0 / cols)
+        o += rows * cols
+        assert np.all(a[o:o + rows] == 0)
+        o += rows
+    assert o == pmg.MLP_NPARAM
+    ctx, _ = _ctx(3, 4, 4, 8)
+    X, T = pmg.mlp_training_data(ctx)
+    ritz = np.concatenate([ctx.get_ritz(lv)[:, k, :] for lv in range(ctx.n_levels)
+                           for k, q in enumerate(ctx.p_levels()) if q > 1])
+    assert np.allclose(T.cpu().numpy(), np.log(ritz[:, ::-1]), rtol=1e-6, atol=1e-6)
+    norm = pmg.mlp_norm(X, T)
+    Xn, Tn = X.cpu().numpy().astype(np.float64), T.cpu().numpy().astype(np.float64)
+    ref = np.concatenate([Xn.mean(0), Xn.std(0) + 1e-6, Tn.mean(0), Tn.std(0) + 1e-6])
+    assert np.allclose(norm, ref, rtol=1e-5, atol=1e-6)
+    ctx.close()
+
+
+def test_network_save_and_load_round_trip(tmp_path):
+    """A network written by pmg_mlp_save and read by pmg_mlp_load gives the
+    same learned intervals; a file of another kind is rejected."""
+    from paper_2510_17785_gb300 import pmg
+    X, T = _data(256, 9)
+    norm = _norm(X, T).astype(np.float32)
+    params = pmg.mlp_init(21)
+    c1, _ = _ctx(3, 4, 4, 12, bounds=pmg.BOUNDS_FIXED)
+    c1.set_mlp(params, norm)
+    c1.compute_bounds(pmg.BOUNDS_MLP)
+    path = str(tmp_path / "net.bin")
+    c1.mlp_save(path)
+    c2, _ = _ctx(3, 4, 4, 12, bounds=pmg.BOUNDS_FIXED)
+    c2.mlp_load(path)
+    c2.compute_bounds(pmg.BOUNDS_MLP)
+    for lv in range(c1.n_levels):
+        assert np.array_equal(c1.get_bounds(lv), c2.get_bounds(lv))
+    bad = tmp_path / "bad.bin"
+    bad.write_bytes(b"not a network file")
+    with pytest.raises(pmg.PMGError):
+        c2.mlp_load(str(bad))
+    c1.close()
+    c2.close()

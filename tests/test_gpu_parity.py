@@ -331,7 +331,7 @@ def test_launch_shape_variants_are_bit_identical(precision, p):
     prob = inputs.make_problem(w)
     u0 = inputs.random_vector(31, 3, p, 6)
     outs = []
-    for v in range(8):
+    for v in range(pmg.NUM_VARIANTS):
         ctx = pmg.Context(0, precision=prec, autotune=0, variant=v, **fixed())
         ctx.mesh_structured(3, 6, p, 2, prob.coords, prob.kappa)
         try:
@@ -393,3 +393,47 @@ def test_autotuner_picks_a_variant_per_level():
         v, ms = ctx.tuning_level(lv)
         assert 0 <= v < 8 and ms[v] > 0 and all(m < 0 or m >= ms[v] for m in ms)
     ctx.close()
+
+
+def test_coefficient_upload_per_level():
+    """pmg_coeff_upload replaces a level's coefficients: uploading the harmonic
+    mean of the children on the coarse level gives the operator of the
+    harmonic coarse rule, uploading 2 kappa on the finest level doubles its
+    operator, and an upload after set-up is rejected."""
+    from paper_2510_17785_gb300 import pmg
+    w = wl(3, 4, 2, kappa=("loguniform", -1, 1))
+    prob = inputs.make_problem(w)
+    kap = prob.kappa.reshape(4, 4, 4)
+    harm = np.zeros((2, 2, 2))
+    for c in range(8):
+        off = [(c >> k) & 1 for k in range(3)]
+        harm += 1.0 / kap[off[2]::2, off[1]::2, off[0]::2]
+    harm = 8.0 / harm
+
+    def apply(ctx, level):
+        n, _ = ctx.num_dofs(level)
+        u = dev(inputs.random_vector(41 + level, 3, 2, 4 >> (1 - level)))
+        out = torch.zeros_like(u)
+        ctx.apply(level, u, out)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+    ref = pmg.Context(0, coarse_kappa=pmg.KAPPA_HARMONIC, **fixed())
+    ref.mesh_structured(3, 4, 2, 2, prob.coords, prob.kappa)
+    ref.setup()
+    up = pmg.Context(0, **fixed())
+    up.mesh_structured(3, 4, 2, 2, prob.coords, prob.kappa)
+    up.coeff_upload(0, harm.reshape(-1))
+    up.setup()
+    a, b = apply(ref, 0), apply(up, 0)
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
+    two = pmg.Context(0, **fixed())
+    two.mesh_structured(3, 4, 2, 2, prob.coords, prob.kappa)
+    two.coeff_upload(1, 2.0 * prob.kappa)
+    two.setup()
+    a, b = apply(ref, 1), apply(two, 1)
+    assert np.abs(2.0 * a - b).max() <= 1e-12 * np.abs(b).max()
+    with pytest.raises(pmg.PMGError):
+        two.coeff_upload(0, harm.reshape(-1))
+    for c in (ref, up, two):
+        c.close()
