@@ -36,7 +36,8 @@ class Workload:
     p: int                 # polynomial degree
     perturb: float         # vertex displacement as a fraction of h = 1/N
     law: str               # "uniform": each component U(-perturb*h, perturb*h);
-                           # "sphere": length perturb*h, direction uniform on S^{d-1}
+                           # "sphere": length perturb*h, direction uniform on S^{d-1};
+                           # "kershaw": Kershaw-type mesh with parameter eps = perturb
     kappa: tuple           # ("const", value) or ("loguniform", log10_lo, log10_hi)
     rhs: str               # "uniform" (U[-1,1] on free DoFs) or "manufactured"
     seed: int
@@ -144,6 +145,39 @@ def valid_perturbation(rng, dim: int, N: int, frac: float, law: str, seed: int, 
     raise RuntimeError("could not draw a valid perturbed mesh")
 
 
+def kershaw_squeeze(t: np.ndarray, eps: float) -> np.ndarray:
+    """A piecewise-linear bijection of [0, 1] with a kink at 1/2: the left half
+    is stretched onto [0, 1 - eps/2], the right half squeezed onto
+    [1 - eps/2, 1] (eps in (0, 1]; eps = 1 is the identity)."""
+    return np.where(t <= 0.5, (2.0 - eps) * t, 1.0 - eps * (1.0 - t))
+
+
+def kershaw_vertices(dim: int, N: int, eps: float = 0.3) -> np.ndarray:
+    """Vertices of a Kershaw-type mesh of the unit square/cube (Kershaw 1981,
+    "Differencing of the diffusion equation in Lagrangian hydrodynamic codes":
+    a logically Cartesian grid whose mesh lines zig-zag).  x is kept; y is
+    mapped by a blend, linear in x, between the left-fine map
+    l(t) = 1 - s(1 - t) and the right-fine map r(t) = s(t) (s =
+    kershaw_squeeze): l -> r on x in [0, 1/3], r -> l on [1/3, 2/3] and
+    l -> r on [2/3, 1]; in 3D z is mapped the same way in the opposite phase.
+    Every map is monotone in its own coordinate and the x-faces stay planes
+    x = const, so every cell has det J > 0.  N must be a multiple of 3 (the
+    kinks of the blend lie on mesh lines)."""
+    if N % 3 != 0:
+        raise ValueError("a Kershaw-type mesh needs N divisible by 3")
+    x = grid_vertices(dim, N)
+    s = lambda t: kershaw_squeeze(t, eps)
+    left = lambda t: 1.0 - s(1.0 - t)
+    seg = np.minimum((x[:, 0] * 3.0).astype(int), 2)        # x segment 0, 1, 2
+    lam = x[:, 0] * 3.0 - seg                                 # position inside the segment
+    lam = np.where(seg == 1, 1.0 - lam, lam)                  # r -> l on the middle segment
+    out = x.copy()
+    out[:, 1] = (1.0 - lam) * left(x[:, 1]) + lam * s(x[:, 1])
+    if dim == 3:
+        out[:, 2] = lam * left(x[:, 2]) + (1.0 - lam) * s(x[:, 2])
+    return out
+
+
 def kappa_cells(rng: np.random.Generator, dim: int, N: int, spec: tuple) -> np.ndarray:
     nc = N ** dim
     if spec[0] == "const":
@@ -176,7 +210,9 @@ class Problem:
 def make_problem(w: Workload) -> Problem:
     rng = np.random.default_rng(w.seed)
     x = grid_vertices(w.dim, w.N)
-    if w.perturb > 0.0:
+    if w.law == "kershaw":
+        x = kershaw_vertices(w.dim, w.N, w.perturb)       # perturb holds the Kershaw parameter eps
+    elif w.perturb > 0.0:
         x = valid_perturbation(rng, w.dim, w.N, w.perturb, w.law, w.seed)
     kap = kappa_cells(rng, w.dim, w.N, w.kappa)
     b = rhs_uniform(rng, w.dim, w.p, w.N) if w.rhs == "uniform" else None
@@ -207,3 +243,118 @@ def single_patch_vertices(dim: int, delta: float, direction: np.ndarray) -> np.n
     u = np.asarray(direction, dtype=np.float64)
     x[c] += delta * 2.0 * u / np.linalg.norm(u)
     return x
+
+
+# ---------------------------------------------------------------------------
+# Unstructured quadrilateral / hexahedral meshes.  A cell is its 2^d vertex
+# ids in lexicographic corner order (corner c at the reference point whose
+# k-th coordinate is bit k of c).
+def triangulated_square(n: int, seed: int, perturb: float = 0.2):
+    """A seeded triangulation of the unit square: n x n squares, each cut along
+    a random diagonal, interior vertices moved by U(-perturb h, perturb h) per
+    component (h = 1/n).  Returns (points, triangles), triangles
+    counter-clockwise."""
+    rng = np.random.default_rng(seed)
+    pts = grid_vertices(2, n)
+    inner = interior_vertex_mask(2, n)
+    pts[inner] += rng.uniform(-perturb / n, perturb / n, size=(int(inner.sum()), 2))
+    tris = []
+    for j in range(n):
+        for i in range(n):
+            a, b = j * (n + 1) + i, j * (n + 1) + i + 1
+            c, d = a + (n + 1), b + (n + 1)
+            if rng.integers(2):
+                tris += [(a, b, d), (a, d, c)]
+            else:
+                tris += [(a, b, c), (b, d, c)]
+    return pts, np.array(tris, dtype=np.int64)
+
+
+def triangles_to_quads(points: np.ndarray, tris: np.ndarray):
+    """Each triangle split into 3 quadrilaterals through its edge midpoints and
+    centroid (the centroid has valence 3, an edge midpoint 4 in the interior,
+    an original vertex as many as its triangles).  Returns (coords, cells)."""
+    pts = [tuple(p) for p in points]
+    coords = list(map(np.array, pts))
+    mid = {}
+
+    def midpoint(a, b):
+        key = (min(a, b), max(a, b))
+        if key not in mid:
+            mid[key] = len(coords)
+            coords.append(0.5 * (points[a] + points[b]))
+        return mid[key]
+
+    cells = []
+    for a, b, c in tris:
+        mab, mbc, mca = midpoint(a, b), midpoint(b, c), midpoint(c, a)
+        g = len(coords)
+        coords.append((points[a] + points[b] + points[c]) / 3.0)
+        for p0, p1, p2, p3 in ((a, mab, g, mca), (b, mbc, g, mab), (c, mca, g, mbc)):
+            cells.append((p0, p1, p3, p2))            # cyclic (counter-clockwise) -> lexicographic
+    return np.array(coords), np.array(cells, dtype=np.int64)
+
+
+def extrude(coords2: np.ndarray, quads: np.ndarray, nz: int):
+    """Quadrilateral mesh of the unit square x nz layers of [0, 1]: hexahedra
+    with the quad's corners at the bottom (bit 2 = 0) and top (bit 2 = 1)."""
+    nv2 = len(coords2)
+    z = np.arange(nz + 1, dtype=np.float64) / nz
+    coords = np.concatenate([np.column_stack([coords2, np.full(nv2, zk)]) for zk in z])
+    cells = [tuple(list(q + k * nv2) + list(q + (k + 1) * nv2)) for k in range(nz) for q in quads]
+    return coords, np.array(cells, dtype=np.int64)
+
+
+def cube_tetrahedra(n: int, seed: int, perturb: float = 0.15):
+    """n^3 cubes of the unit cube, each cut into 6 tetrahedra around its main
+    diagonal (consistent across faces), interior vertices moved by
+    U(-perturb h, perturb h) per component.  Returns (points, tets), each tet
+    positively oriented."""
+    rng = np.random.default_rng(seed)
+    pts = grid_vertices(3, n)
+    inner = interior_vertex_mask(3, n)
+    pts[inner] += rng.uniform(-perturb / n, perturb / n, size=(int(inner.sum()), 3))
+    vid = lambda i, j, k: (k * (n + 1) + j) * (n + 1) + i
+    tets = []
+    for k in range(n):
+        for j in range(n):
+            for i in range(n):
+                v = [vid(i + (c & 1), j + ((c >> 1) & 1), k + ((c >> 2) & 1)) for c in range(8)]
+                for path in ((1, 3), (1, 5), (2, 3), (2, 6), (4, 5), (4, 6)):
+                    t = [v[0], v[path[0]], v[path[1]], v[7]]
+                    x = pts[t]
+                    if np.linalg.det(np.array([x[1] - x[0], x[2] - x[0], x[3] - x[0]])) < 0:
+                        t[1], t[2] = t[2], t[1]
+                    tets.append(tuple(t))
+    return pts, np.array(tets, dtype=np.int64)
+
+
+def tetrahedra_to_hexes(points: np.ndarray, tets: np.ndarray):
+    """Each tetrahedron split into 4 hexahedra through its edge midpoints, face
+    centroids and centroid (valence 4 at the centroid, 6 at an interior face
+    centroid).  Returns (coords, cells)."""
+    coords = [np.array(p) for p in points]
+    cache = {}
+
+    def point(key, fn):
+        if key not in cache:
+            cache[key] = len(coords)
+            coords.append(fn())
+        return cache[key]
+
+    cells = []
+    for t in tets:
+        t = [int(x) for x in t]
+        g = len(coords)
+        coords.append(points[t].mean(axis=0))
+        for ia in range(4):
+            a = t[ia]
+            o = [t[j] for j in range(4) if j != ia]
+            b, c, d = o
+            if ia % 2 == 1:                            # keep (b - a, c - a, d - a) right-handed
+                b, c = c, b
+            m = lambda x, y: point(("e", min(x, y), max(x, y)), lambda: 0.5 * (points[x] + points[y]))
+            f = lambda x, y, z: point(("f",) + tuple(sorted((x, y, z))),
+                                      lambda: (points[x] + points[y] + points[z]) / 3.0)
+            cells.append((a, m(a, b), m(a, c), f(a, b, c), m(a, d), f(a, b, d), f(a, c, d), g))
+    return np.array(coords), np.array(cells, dtype=np.int64)

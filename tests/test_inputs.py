@@ -39,3 +39,30 @@ def test_different_seeds_differ():
     a = inputs.make_problem(w)
     b = inputs.make_problem(w.with_(seed=w.seed + 1))
     assert not np.array_equal(a.coords, b.coords)
+
+
+def test_kershaw_type_mesh():
+    """The Kershaw-type generator keeps the boundary on itself, is the uniform
+    grid at eps = 1, has positive corner volumes at eps = 0.3 (cell sizes in a
+    ratio of (2 - eps) / eps along y), and needs N divisible by 3."""
+    import numpy as np
+    for dim in (2, 3):
+        N = 12
+        g = inputs.grid_vertices(dim, N)
+        assert np.allclose(inputs.kershaw_vertices(dim, N, 1.0), g, atol=1e-15)
+        x = inputs.kershaw_vertices(dim, N, 0.3)
+        bnd = ~inputs.interior_vertex_mask(dim, N)
+        on_bnd = np.any((x[bnd] < 1e-14) | (x[bnd] > 1 - 1e-14), axis=1)
+        assert on_bnd.all()
+        assert inputs.corner_volumes(x, dim, N).min() > 0
+        col = x[:N + 1, :]                                 # the first x-row: y = 0 edge (x varies)
+        assert np.allclose(col[:, 0], g[:N + 1, 0])
+        ys = np.sort(np.unique(np.round(x[x[:, 0] == 0.0][:, 1], 14)))
+        h = np.diff(ys)
+        assert abs(h.max() / h.min() - (2 - 0.3) / 0.3) < 1e-9
+    try:
+        inputs.kershaw_vertices(2, 8, 0.3)
+    except ValueError:
+        pass
+    else:
+        raise AssertionError("N = 8 accepted")
