@@ -47,7 +47,7 @@ enum {
 };
 
 /* Number of launch-shape variants of the patch-sweep kernel (pmg_tuning). */
-#define PMG_NUM_VARIANTS 13
+#define PMG_NUM_VARIANTS 16
 
 /* ---- options ----------------------------------------------------------- */
 enum { PMG_SMOOTHER_CHEBYSHEV = 0, PMG_SMOOTHER_JACOBI = 1, PMG_SMOOTHER_CARTESIAN = 2 };

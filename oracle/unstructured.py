@@ -390,3 +390,62 @@ class PatchSmoother:
                 d = pt.local_solve(P, P.residual(u, b), self.sm, self.bounds(v), 1)
                 u[P.lv[self.levels[0]].interior] += d
         return u
+
+
+# ------------------------------------------------------------ global solver
+def q1_prolongation(mesh: Mesh, q: int) -> sp.csr_matrix:
+    """Embedding of the Q1 space into the degree-q space of the same mesh:
+    entry (k, v) is vertex function v at DoF k, evaluated in a cell holding k."""
+    d = mesh.dim
+    gl = rules.gauss_lobatto_nodes(q)
+    cd = mesh.cell_dofs(q)
+    rows, cols, vals = [], [], []
+    done = set()
+    for c in range(mesh.nc):
+        for li, m in enumerate(_lex(d, q + 1)):
+            g = int(cd[c, li])
+            if g in done:
+                continue
+            done.add(g)
+            for v in range(2 ** d):
+                val = 1.0
+                for k in range(d):
+                    val *= gl[m[k]] if (v >> k) & 1 else 1.0 - gl[m[k]]
+                if val != 0.0:
+                    rows.append(g)
+                    cols.append(int(mesh.cells[c, v]))
+                    vals.append(val)
+    return sp.coo_matrix((vals, (rows, cols)), shape=(mesh.n_dofs(q), mesh.nv)).tocsr()
+
+
+class TwoLevel:
+    """Two-level preconditioner on an unstructured mesh: one multiplicative
+    patch sweep (colours increasing), the residual restricted to the Q1 space
+    of the same mesh (re-discretised with its own 2-point Gauss rule, the
+    reading of Section 3.1 "Level operators" carried to the global coarse
+    level), solved by a dense Cholesky factorisation, prolongated by the
+    embedding, then one sweep with the colours reversed: a symmetric
+    preconditioner for CG."""
+
+    def __init__(self, mesh: Mesh, p: int, smoother: PatchSmoother):
+        import scipy.linalg as sla
+        self.mesh, self.p, self.S = mesh, p, smoother
+        self.free = ~mesh.boundary_dofs(p)
+        self.A = fem.operator_with_dirichlet(mesh.assemble(p), self.free)
+        free1 = ~mesh.boundary_dofs(1)
+        self.free1 = free1
+        A1 = mesh.assemble(1).toarray()[np.ix_(free1, free1)]
+        self.chol = sla.cho_factor(A1, lower=True)
+        Df = sp.diags(self.free.astype(float))
+        D1 = sp.diags(free1.astype(float))
+        self.P = (Df @ q1_prolongation(mesh, p) @ D1).tocsr()
+
+    def vcycle(self, b):
+        import scipy.linalg as sla
+        x = self.S.sweep(np.zeros_like(b), b, reverse=False)
+        r = b - self.A @ x
+        r1 = self.P.T @ r
+        e1 = np.zeros(self.mesh.nv)
+        e1[self.free1] = sla.cho_solve(self.chol, r1[self.free1])
+        x = x + self.P @ e1
+        return self.S.sweep(x, b, reverse=True)

@@ -44,6 +44,72 @@ __device__ inline void cell_vertices(const double* coords, int N, int cell, doub
   }
 }
 
+// G = w kappa det(J) J^-1 J^-T at Gauss point g (index in the (q+1)^d rule)
+// of the cell with vertices X (2^d x d, lexicographic corners), written to
+// out[comp * ngc]; err gets bit 0 when det J <= 0 at the point or, for g = 0,
+// at a vertex of the cell (an inverted or non-convex corner).
+template <int DIM, typename T>
+__device__ void geometry_point(const double* X, double kappa, int q, int g, T* out, int ngc, int* err) {
+  const int n = q + 1;
+  double xi[3];
+  double w = 1.0;
+  int rem = g;
+  for (int ax = 0; ax < DIM; ++ax) {
+    const int ga = rem % n;
+    rem /= n;
+    xi[ax] = c_rules.gx[q][ga];
+    w *= c_rules.gw[q][ga];
+  }
+  double J[3][3];
+  q1_jacobian<DIM>(X, xi, J);
+  double det, Ji[3][3];
+  if (DIM == 3) {
+    const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+    const double id = 1.0 / det;
+    Ji[0][0] = c00 * id;
+    Ji[1][0] = c01 * id;
+    Ji[2][0] = c02 * id;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
+  } else {
+    det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    const double id = 1.0 / det;
+    Ji[0][0] = J[1][1] * id;
+    Ji[0][1] = -J[0][1] * id;
+    Ji[1][0] = -J[1][0] * id;
+    Ji[1][1] = J[0][0] * id;
+  }
+  if (!(det > 0.0)) atomicOr(err, 1);
+  if (g == 0) {
+    for (int v = 0; v < (1 << DIM); ++v) {
+      double xv[3], Jv[3][3];
+      for (int k = 0; k < DIM; ++k) xv[k] = (v >> k) & 1;
+      q1_jacobian<DIM>(X, xv, Jv);
+      const double dv = DIM == 3 ? Jv[0][0] * (Jv[1][1] * Jv[2][2] - Jv[1][2] * Jv[2][1]) -
+                                       Jv[0][1] * (Jv[1][0] * Jv[2][2] - Jv[1][2] * Jv[2][0]) +
+                                       Jv[0][2] * (Jv[1][0] * Jv[2][1] - Jv[1][1] * Jv[2][0])
+                                 : Jv[0][0] * Jv[1][1] - Jv[0][1] * Jv[1][0];
+      if (!(dv > 0.0)) atomicOr(err, 1);
+    }
+  }
+  const double s = w * kappa * det;
+  int comp = 0;
+  for (int k = 0; k < DIM; ++k)
+    for (int l = k; l < DIM; ++l) {
+      double v = 0.0;
+      for (int m = 0; m < DIM; ++m) v += Ji[k][m] * Ji[l][m];
+      out[(size_t)comp * ngc] = T(s * v);
+      ++comp;
+    }
+}
+
 template <int DIM, typename T>
 __global__ void k_geometry(const double* __restrict__ coords, const double* __restrict__ kappa, int N, int q,
                            T* __restrict__ G, int* err) {
@@ -57,67 +123,38 @@ __global__ void k_geometry(const double* __restrict__ coords, const double* __re
     const int g = (int)(t - (size_t)cell * ngc);
     double X[8 * 3];
     cell_vertices<DIM>(coords, N, cell, X);
-    double xi[3];
-    double w = 1.0;
-    int rem = g;
-    for (int ax = 0; ax < DIM; ++ax) {
-      const int ga = rem % n;
-      rem /= n;
-      xi[ax] = c_rules.gx[q][ga];
-      w *= c_rules.gw[q][ga];
+    geometry_point<DIM, T>(X, kappa[cell], q, g, G + (size_t)cell * NCOMP * ngc + g, ngc, err);
+  }
+}
+
+// diagonal entry of node a of a cell's degree-q operator:
+// sum_g sum_kl G_kl(g) d_k phi_a(g) d_l phi_a(g), G of the cell at Gc
+template <int DIM>
+__device__ double cell_diag_entry(const double* __restrict__ Gc, int q, int a) {
+  const int n = q + 1;
+  const int ngc = DIM == 3 ? n * n * n : n * n;
+  int aa[3] = {0, 0, 0}, rem = a;
+  for (int ax = 0; ax < DIM; ++ax) { aa[ax] = rem % n; rem /= n; }
+  double s = 0.0;
+  for (int g = 0; g < ngc; ++g) {
+    int gg[3] = {0, 0, 0}, r2 = g;
+    for (int ax = 0; ax < DIM; ++ax) { gg[ax] = r2 % n; r2 /= n; }
+    double grad[3];
+    for (int k = 0; k < DIM; ++k) {
+      double f = 1.0;
+      for (int ax = 0; ax < DIM; ++ax)
+        f *= (ax == k) ? c_rules.Bd[q][gg[ax]][aa[ax]] : c_tab_f64.B[q][gg[ax]][aa[ax]];
+      grad[k] = f;
     }
-    double J[3][3];
-    q1_jacobian<DIM>(X, xi, J);
-    double det, Ji[3][3];
-    if (DIM == 3) {
-      const double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-      const double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-      const double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-      det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
-      const double id = 1.0 / det;
-      Ji[0][0] = c00 * id;
-      Ji[1][0] = c01 * id;
-      Ji[2][0] = c02 * id;
-      Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
-      Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
-      Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
-      Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
-      Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
-      Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
-    } else {
-      det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-      const double id = 1.0 / det;
-      Ji[0][0] = J[1][1] * id;
-      Ji[0][1] = -J[0][1] * id;
-      Ji[1][0] = -J[1][0] * id;
-      Ji[1][1] = J[0][0] * id;
-    }
-    if (!(det > 0.0)) atomicOr(err, 1);
-    if (g == 0) {
-      // a cell is also degenerate when det J <= 0 at a vertex (a non-convex
-      // or inverted corner), even if every Gauss point is still positive
-      for (int v = 0; v < (1 << DIM); ++v) {
-        double xv[3], Jv[3][3];
-        for (int k = 0; k < DIM; ++k) xv[k] = (v >> k) & 1;
-        q1_jacobian<DIM>(X, xv, Jv);
-        const double dv = DIM == 3 ? Jv[0][0] * (Jv[1][1] * Jv[2][2] - Jv[1][2] * Jv[2][1]) -
-                                         Jv[0][1] * (Jv[1][0] * Jv[2][2] - Jv[1][2] * Jv[2][0]) +
-                                         Jv[0][2] * (Jv[1][0] * Jv[2][1] - Jv[1][1] * Jv[2][0])
-                                   : Jv[0][0] * Jv[1][1] - Jv[0][1] * Jv[1][0];
-        if (!(dv > 0.0)) atomicOr(err, 1);
-      }
-    }
-    const double s = w * kappa[cell] * det;
-    T* out = G + (size_t)cell * NCOMP * ngc + g;
     int comp = 0;
     for (int k = 0; k < DIM; ++k)
       for (int l = k; l < DIM; ++l) {
-        double v = 0.0;
-        for (int m = 0; m < DIM; ++m) v += Ji[k][m] * Ji[l][m];
-        out[(size_t)comp * ngc] = T(s * v);
+        const double gkl = Gc[(size_t)comp * ngc + g];
+        s += (k == l ? 1.0 : 2.0) * gkl * grad[k] * grad[l];
         ++comp;
       }
   }
+  return s;
 }
 
 // ---------------------------------------------------------------------------
@@ -149,26 +186,7 @@ __global__ void k_diag(const double* __restrict__ G, int N, int q, int parity, d
     int aa[3] = {0, 0, 0};
     rem = a;
     for (int ax = 0; ax < DIM; ++ax) { aa[ax] = rem % n; rem /= n; }
-    const double* Gc = G + (size_t)cell * NCOMP * ngc;
-    double s = 0.0;
-    for (int g = 0; g < ngc; ++g) {
-      int gg[3] = {0, 0, 0}, r2 = g;
-      for (int ax = 0; ax < DIM; ++ax) { gg[ax] = r2 % n; r2 /= n; }
-      double grad[3];
-      for (int k = 0; k < DIM; ++k) {
-        double f = 1.0;
-        for (int ax = 0; ax < DIM; ++ax)
-          f *= (ax == k) ? c_rules.Bd[q][gg[ax]][aa[ax]] : c_tab_f64.B[q][gg[ax]][aa[ax]];
-        grad[k] = f;
-      }
-      int comp = 0;
-      for (int k = 0; k < DIM; ++k)
-        for (int l = k; l < DIM; ++l) {
-          const double gkl = Gc[(size_t)comp * ngc + g];
-          s += (k == l ? 1.0 : 2.0) * gkl * grad[k] * grad[l];
-          ++comp;
-        }
-    }
+    const double s = cell_diag_entry<DIM>(G + (size_t)cell * NCOMP * ngc, q, a);
     size_t idx = 0, m2 = 1;
     for (int ax = 0; ax < DIM; ++ax) { idx += (size_t)(q * c[ax] + aa[ax]) * m2; m2 *= Mg; }
     diag[idx] += s;

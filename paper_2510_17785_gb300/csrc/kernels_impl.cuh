@@ -80,6 +80,9 @@ int launch_patch_P(int mode, int variant, const PatchArgs<T>& a, cudaStream_t s)
       case 10: return launch_patch_PV<DIM, P, T, 10>(mode, a, s);
       case 11: return launch_patch_PV<DIM, P, T, 11>(mode, a, s);
       case 12: return launch_patch_PV<DIM, P, T, 12>(mode, a, s);
+      case 13: return launch_patch_PV<DIM, P, T, 13>(mode, a, s);
+      case 14: return launch_patch_PV<DIM, P, T, 14>(mode, a, s);
+      case 15: return launch_patch_PV<DIM, P, T, 15>(mode, a, s);
       default: return ST_UNSUPPORTED;
     }
   }
@@ -126,6 +129,9 @@ void patch_config_P(int variant, size_t* smem, int* ppb, int* nt) {
     case 10: return patch_config_PV<DIM, P, T, 10>(smem, ppb, nt);
     case 11: return patch_config_PV<DIM, P, T, 11>(smem, ppb, nt);
     case 12: return patch_config_PV<DIM, P, T, 12>(smem, ppb, nt);
+    case 13: return patch_config_PV<DIM, P, T, 13>(smem, ppb, nt);
+    case 14: return patch_config_PV<DIM, P, T, 14>(smem, ppb, nt);
+    case 15: return patch_config_PV<DIM, P, T, 15>(smem, ppb, nt);
     default: *smem = 0; *ppb = 0; *nt = 0;
   }
 }

@@ -152,12 +152,12 @@ struct Layout {
 
 // Launch shape of the patch kernel.  Variant 0 is the default; for 3D degrees
 // 3..8 the set-up autotuner also times variants 1..9:
-//   variant:          1      2      3      4      5      6      7      8      9     10     11     12
-//   design:         stage  stage  stage  line   line   line   line   line   stage  line   line   line
-//   threads / CTA:    256    128    512    256    128    512    128    256    256    224    320    416
-//   patches / CTA:      2      1      1      2      1      1      2      2      2      2      3      4
-//   geometry:                    staged                staged        staged staged
-//   groups:                                                   2
+//   variant:          1     2     3     4     5     6     7     8     9    10    11    12    13    14    15
+//   design:         stage stage stage line  line  line  line  line  stage line  line  line  line  line  line
+//   threads / CTA:    256   128   512   256   128   512   128   256   256   224   320   416   192   256   128
+//   patches / CTA:      2     1     1     2     1     1     2     2     2     2     3     4     3     4     4
+//   geometry:                  staged            staged       staged staged
+//   groups:                                               2                             3     4     4
 // (patches per CTA are capped by shared memory).  "stage": every direction's
 // flux in shared memory; "line": one thread per line along the last
 // direction keeps that direction's gradient and flux in registers.  With
@@ -168,21 +168,25 @@ struct Layout {
 // per 512 threads), 8 and 9 throughput shapes (two patches per 256 threads,
 // a 128-register budget, two CTAs per SM).  Variants 10-12 size the CTA to
 // about 100 threads per patch, the number of lines along the last direction
-// at degree 4 (fewer idle threads at each barrier).
+// at degree 4 (fewer idle threads at each barrier).  Variants 13-15 give each
+// patch its own team of 64 or 32 threads (one or two warps) with its own
+// barrier and several lines per thread (more independent work per thread,
+// no waiting on the other patches of the CTA).
 constexpr int NUM_VARIANTS = PMG_NUM_VARIANTS;
 
 template <int DIM, int P, typename T, int V = 0>
 struct Config {
   static constexpr int NT0 = (DIM == 3) ? 256 : 128;
   static constexpr int PPB0 = (DIM == 3) ? (P <= 2 ? 4 : 1) : (P <= 2 ? 8 : (P <= 4 ? 4 : 2));
-  static constexpr int NTV[NUM_VARIANTS] = {NT0, 256, 128, 512, 256, 128, 512, 128, 256, 256, 224, 320, 416};
-  static constexpr int PPBV[NUM_VARIANTS] = {PPB0, 2, 1, 1, 2, 1, 1, 2, 2, 2, 2, 3, 4};
+  static constexpr int NTV[NUM_VARIANTS] = {NT0, 256, 128, 512, 256, 128, 512, 128, 256, 256, 224, 320, 416,
+                                            192, 256, 128};
+  static constexpr int PPBV[NUM_VARIANTS] = {PPB0, 2, 1, 1, 2, 1, 1, 2, 2, 2, 2, 3, 4, 3, 4, 4};
   static constexpr bool LINEV[NUM_VARIANTS] = {false, false, false, false, true, true, true, true, true, false,
-                                               true, true, true};
+                                               true, true, true, true, true, true};
   static constexpr bool GROUPV[NUM_VARIANTS] = {false, false, false, false, false, false, false, true, false, false,
-                                                false, false, false};
+                                                false, false, false, true, true, true};
   static constexpr bool GSMEMV[NUM_VARIANTS] = {false, false, false, true, false, false, true, false, true, true,
-                                                false, false, false};
+                                                false, false, false, false, false, false};
   static constexpr int NT = NTV[V];
   static constexpr int PPB_MAX = PPBV[V];
   static constexpr bool LINE = LINEV[V];
@@ -228,9 +232,9 @@ struct Config {
   static constexpr int TPP_ = GROUPED ? NT / PPB : NT;
   static constexpr int SPAN_ = GROUPED ? 1 : PPB;
   static constexpr int LPT_ = (SPAN_ * ipow(QPL, DIM - 1) + TPP_ - 1) / TPP_;
-  static constexpr bool worth = (!LINE || LPT_ <= 2) &&
+  static constexpr bool worth = (!LINE || LPT_ <= (GROUPED ? 4 : 2)) &&
                                 (sizeof(T) == 4 || V == 0 || ((V == 2 || V == 4 || V == 6) && P <= 6)) &&
-                                (V < 8 || (DIM == 3 && P >= 3)) && (V < 10 || (sizeof(T) == 4 && P <= 5));
+                                (V < 8 || (DIM == 3 && P >= 3)) && (V < 10 || (sizeof(T) == 4 && (V >= 13 || P <= 5)));
   static constexpr bool exists = fits && distinct && worth;
 };
 
@@ -248,6 +252,36 @@ struct PatchKernel {
   const PatchArgs<T>* a;
 
   __device__ T* vec(int pp, int off) const { return sm + pp * PS + off; }
+
+  // Shared-memory staging of global data: every thread issues the loads of
+  // U items before it stores any of them, so U loads are in flight per thread
+  // (one at a time, each staging pass is a chain of memory round trips).
+  // ld(pp, item) loads, st(pp, item, value) stores.
+  template <int ITEMS, typename LD, typename STF>
+  __device__ __forceinline__ void stage(LD&& ld, STF&& st) const {
+    constexpr int U = 8;
+    constexpr int TOT = TM::SPAN * ITEMS;
+#pragma unroll 1
+    for (int base = TM::lane(); base < TOT; base += U * TM::TPP) {
+      T v[U];
+      int pp[U], e[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int it = base + u * TM::TPP;
+        if constexpr (C::GROUPED) {
+          pp[u] = TM::group();
+          e[u] = it;
+        } else {
+          pp[u] = it / ITEMS;
+          e[u] = it - pp[u] * ITEMS;
+        }
+        v[u] = it < TOT ? ld(pp[u], e[u]) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (base + u * TM::TPP < TOT) st(pp[u], e[u], v[u]);
+    }
+  }
 
   // geometry of cell `slot` of patch pp staged in shared memory (GSMEM variants)
   template <int stride>
@@ -694,24 +728,27 @@ struct PatchKernel {
       });
     } else {
       constexpr int NI = L::ni(K);
-      TM::template loop<NI>([&](int pp, int i) {
+      const T* dinv = a->lv[K].dinv;
+      stage<NI>([&](int pp, int i) {
         const bool act = cells[pp * CST + NCELL + 1];
-        vec(pp, L::DINV(K))[i] = act ? a->lv[K].dinv[gindex_int<q>(pp, i)] : T(0);
-      });
+        return act ? __ldg(dinv + gindex_int<q>(pp, i)) : T(0);
+      }, [&](int pp, int i, T v) { vec(pp, L::DINV(K))[i] = v; });
       if constexpr (dense_level(DIM, q)) {
-        TM::template loop<NI * NI>([&](int pp, int e) {
+        const T* dense = a->lv[K].dense;
+        stage<NI * NI>([&](int pp, int e) {
           const bool act = cells[pp * CST + NCELL + 1];
           const int pid = cells[pp * CST + NCELL];
-          vec(pp, L::DENSE(K))[e] = act ? a->lv[K].dense[(size_t)pid * NI * NI + e] : T(0);
-        });
+          return act ? __ldg(dense + (size_t)pid * NI * NI + e) : T(0);
+        }, [&](int pp, int e, T v) { vec(pp, L::DENSE(K))[e] = v; });
       }
       if constexpr (C::GSMEM && K == 0) {                // the cells' geometry tensors, once per patch
         constexpr int GC = L::GCELL;
-        TM::template loop<NCELL * GC>([&](int pp, int e) {
+        const T* G = a->lv[K].G;
+        stage<NCELL * GC>([&](int pp, int e) {
           const bool act = cells[pp * CST + NCELL + 1];
           const int slot = e / GC;
-          vec(pp, L::GS)[e] = act ? a->lv[K].G[(size_t)cells[pp * CST + slot] * GC + (e - slot * GC)] : T(0);
-        });
+          return act ? __ldg(G + (size_t)cells[pp * CST + slot] * GC + (e - slot * GC)) : T(0);
+        }, [&](int pp, int e, T v) { vec(pp, L::GS)[e] = v; });
       }
       // reference-patch fast-diagonalisation table (Cartesian-reinforced smoother)
       if (a->smoother == 2) {
@@ -761,15 +798,19 @@ struct PatchKernel {
     constexpr int NI0 = L::ni(0);
     if (MODE == MODE_SWEEP) {
       // Gather: closure of u, interior of b
+      // (u is not written by any patch of this launch that another patch
+      // reads: patches of one colour share no cell)
       constexpr int NN0 = L::NN0;
-      TM::template loop<NN0>([&](int pp, int i) {
+      const T* ug = a->u;
+      const T* bg = a->b;
+      stage<NN0>([&](int pp, int i) {
         const bool act = cells[pp * CST + NCELL + 1];
-        vec(pp, L::CLOS)[i] = act ? a->u[gindex<P>(pp, i)] : T(0);
-      });
-      TM::template loop<NI0>([&](int pp, int i) {
+        return act ? __ldg(ug + gindex<P>(pp, i)) : T(0);
+      }, [&](int pp, int i, T v) { vec(pp, L::CLOS)[i] = v; });
+      stage<NI0>([&](int pp, int i) {
         const bool act = cells[pp * CST + NCELL + 1];
-        vec(pp, L::R_(0))[i] = act ? a->b[gindex_int<P>(pp, i)] : T(0);
-      });
+        return act ? __ldg(bg + gindex_int<P>(pp, i)) : T(0);
+      }, [&](int pp, int i, T v) { vec(pp, L::R_(0))[i] = v; });
       TM::sync();
       // Evaluate: r = b - A u on the patch interior
       SF<DIM, 2, P, T, NT, PPB, C::LINE, C::GROUPED>::template apply_epi<false>(vec(0, L::CLOS), PS, vec(0, L::SCR), PS,

@@ -24,7 +24,7 @@ SMOOTHER_CHEBYSHEV, SMOOTHER_JACOBI, SMOOTHER_CARTESIAN = 0, 1, 2
 BOUNDS_LANCZOS, BOUNDS_FIXED, BOUNDS_USER, BOUNDS_MLP = 0, 1, 2, 3
 MLP_NPARAM, MLP_NNORM = 5378, 36
 PREC_FP64, PREC_MIXED = 0, 1
-NUM_VARIANTS = 13              # PMG_NUM_VARIANTS of include/pmg.h
+NUM_VARIANTS = 16              # PMG_NUM_VARIANTS of include/pmg.h
 KAPPA_ARITHMETIC, KAPPA_GEOMETRIC, KAPPA_HARMONIC = 0, 1, 2
 
 # every symbol include/pmg.h declares

@@ -191,3 +191,30 @@ def test_sweep_brute_force_on_an_unstructured_mesh():
             B = pt.vcycle_matrix(P, S.sm, S.bounds(v))
             ref[I] += B @ (b - A @ ref)[I]
     assert np.allclose(S.sweep(u, b), ref, atol=1e-12)
+
+
+def test_q1_embedding_and_two_level_cg():
+    """The Q1 embedding reproduces linear functions exactly at every DoF; the
+    two-level preconditioner (patch sweeps, Q1 coarse space) is symmetric and
+    CG with it reaches 1e-8 and agrees with a sparse direct solve."""
+    import scipy.sparse.linalg as spla
+    from oracle import gmg
+    for name, m in _meshes():
+        q = 2
+        P = us.q1_prolongation(m, q)
+        a = np.array([0.3, -1.1, 0.7][: m.dim])
+        lin1 = m.coords @ a + 0.2
+        linq = m.node_coords(q) @ a + 0.2
+        assert np.abs(P @ lin1 - linq).max() < 1e-13
+        S = us.PatchSmoother(m, q, bounds_fn=lz.lanczos_bounds_fn(seed=0))
+        T = us.TwoLevel(m, q, S)
+        free = T.free
+        rng = np.random.default_rng(5)
+        b = rng.uniform(-1, 1, len(free)) * free
+        y1, y2 = rng.uniform(-1, 1, len(b)) * free, rng.uniform(-1, 1, len(b)) * free
+        assert abs(y1 @ T.vcycle(y2) - y2 @ T.vcycle(y1)) < 1e-11 * abs(y1 @ T.vcycle(y1)), name
+        x, it, hist = gmg.pcg(T.A, b, T.vcycle, 1e-8, 60)
+        assert hist[-1] <= 1e-8 and it <= 30, (name, it)
+        ref = np.zeros_like(b)
+        ref[free] = spla.spsolve(T.A.tocsr()[free][:, free].tocsc(), b[free])
+        assert np.linalg.norm(x - ref) < 1e-6 * np.linalg.norm(ref), name
