@@ -46,6 +46,10 @@ enum {
   PMG_ERR_UNSUPPORTED = 7    /* e.g. p > 8, or a precision/degree combination  */
 };
 
+/* Largest number of cells around a vertex (the valence of a vertex patch)
+ * that the unstructured-mesh kernels accept. */
+#define PMG_UMAXC 32
+
 /* Number of launch-shape variants of the patch-sweep kernel (pmg_tuning). */
 #define PMG_NUM_VARIANTS 16
 
@@ -129,6 +133,47 @@ const char* pmg_last_error(const pmg_ctx* ctx);
 int pmg_mesh_structured(pmg_ctx* ctx, int dim, int N, int p, int n_levels,
                         const double* coords, const double* kappa);
 
+/* ---- unstructured meshes ---------------------------------------------------
+ * Quadrilateral (dim 2) or hexahedral (dim 3) meshes of any topology, the
+ * setting of Section 2 without the Cartesian structure (the paper's vertex
+ * patches on general meshes and its simplicial patches of 3 quadrilaterals /
+ * 4 hexahedra, Section 3.2).  One mesh level: the patch smoother and the local
+ * p-multigrid of Sections 2.1 and 3 act on degree p; the preconditioner of
+ * pmg_solve_cg / pmg_solve_gmres / pmg_gmg_vcycle is two-level: a patch sweep,
+ * the Q1 space of the same mesh as coarse space (operator re-evaluated with
+ * the 2-point Gauss rule, dense Cholesky, at most 16384 free vertices), a
+ * reverse sweep.
+ *
+ * coords: n_vertices x dim doubles.  cell_vertices: n_cells x 2^dim vertex
+ * ids, lexicographic corner order (corner c at the reference point whose k-th
+ * coordinate is bit k of c), every cell positively oriented.
+ * vertex_on_boundary: n_vertices flags or NULL (derived: the vertices of the
+ * facets that belong to one cell).  level must be 0 and parent_cell,
+ * child_index NULL (PMG_ERR_UNSUPPORTED otherwise).  Host arrays are copied.
+ * Call pmg_set_degree before pmg_setup; kappa by pmg_coeff_upload (level 0,
+ * default 1).  DoF numbering (pmg_get_dof_map): vertices by id; edges sorted
+ * by (smaller id, larger id), q - 1 nodes each from the smaller-id end; faces
+ * sorted by their sorted vertex ids, (q - 1)^2 nodes in the frame of the
+ * face's smallest-id corner (first axis toward its smaller-id face neighbour,
+ * fastest); cell interiors by cell, x fastest.  Patches: the interior vertices
+ * in increasing id, each with its cells; colours: greedy in decreasing
+ * (splitmix64(id ^ seed), id), the smallest colour not used by a patch that
+ * shares a cell.  Chebyshev intervals: PMG_BOUNDS_FIXED or USER
+ * (pmg_set_bounds); the smoother Chebyshev or Jacobi; multiplicative sweeps.
+ * Local vectors of pmg_local_vcycle: one row of pmg_local_size values per patch
+ * (its interior DoFs in increasing global id, zero padded). */
+int pmg_mesh_upload(pmg_ctx* ctx, int level, int dim, int64_t n_vertices, const double* coords,
+                    int64_t n_cells, const int64_t* cell_vertices, const uint8_t* vertex_on_boundary,
+                    const int64_t* parent_cell, const uint8_t* child_index);
+/* Polynomial degree p (1..8) of an unstructured mesh (p-levels p, p/2, ..., 1). */
+int pmg_set_degree(pmg_ctx* ctx, int p);
+/* [n_cells][(q+1)^dim] global DoF ids of every cell's nodes at p-level index k
+ * (local order lexicographic, x fastest); unstructured meshes, after set-up. */
+int pmg_get_dof_map(pmg_ctx* ctx, int k, int32_t* out_host);
+/* Row length of the local vectors of pmg_local_vcycle on a level: (2p-1)^d on
+ * structured meshes, the largest patch interior on unstructured ones. */
+int pmg_local_size(const pmg_ctx* ctx, int level, int64_t* n);
+
 /* Coefficient of every cell of mesh level `level` (0 = coarsest; host array
  * of N_l^d doubles, cell index lexicographic with x fastest, copied), in
  * place of the one the set-up derives from the finer level with the
@@ -182,7 +227,9 @@ int pmg_patch_smooth_colour(pmg_ctx* ctx, int level, int colour, const double* b
  * numbering lexicographic over interior vertices, x fastest), apply n_cycles
  * V-cycles (the first from d = 0) to the local right-hand sides r_dev and
  * write the corrections d_dev.  r_dev and d_dev are device FP64 arrays of
- * n x (2p-1)^d values, patch-interior DoFs in lexicographic order (x fastest). */
+ * n x (2p-1)^d values, patch-interior DoFs in lexicographic order (x fastest)
+ * (unstructured meshes: n x pmg_local_size values, each row the patch's
+ * interior DoFs in increasing global id, zero padded). */
 int pmg_local_vcycle(pmg_ctx* ctx, int level, int64_t n, const int64_t* patch_ids_dev,
                      const double* r_dev, double* d_dev, int n_cycles, void* stream);
 
@@ -261,7 +308,9 @@ int pmg_rhs_manufactured(pmg_ctx* ctx, double* b_dev, void* stream);
 int pmg_get_colours(const pmg_ctx* ctx, int level, uint8_t* colours_host);
 /* Patch map of level l: for each patch its 2^d cells (int64, cell order
  * lexicographic inside the patch, x fastest) followed by the global DoF id of
- * its closure origin (lowest corner node). Writes n_patches x (2^d + 1). */
+ * its closure origin (lowest corner node). Writes n_patches x (2^d + 1).
+ * Unstructured meshes: n_patches x (1 + PMG_UMAXC): the patch's vertex id,
+ * then its cells in increasing id, -1 padded. */
 int pmg_get_patch_map(const pmg_ctx* ctx, int level, int64_t* map_host);
 
 /* Inverse level diagonal 1/diag(A_{l,q}) of mesh level l at p-level index k

@@ -113,6 +113,7 @@ void build_tables(Tables<double>& t64, Tables<float>& t32, Rules& r) {
     const std::vector<double> gl = gauss_lobatto(q);
     const auto B = lagrange_matrix(gl, gx);     // [g][a]
     const auto D = diff_matrix(gx);             // [g][h]
+    for (int a = 0; a < n; ++a) r.gll[q][a] = gl[a];
     for (int g = 0; g < n; ++g) {
       r.gx[q][g] = gx[g];
       r.gw[q][g] = gw[g];

@@ -11,7 +11,7 @@
 namespace pmg {
 
 // status codes (mirrors pmg.h)
-enum { ST_OK = 0, ST_ARG = 1, ST_CUDA = 2, ST_NOT_SPD = 5, ST_UNSUPPORTED = 7 };
+enum { ST_OK = 0, ST_ARG = 1, ST_CUDA = 2, ST_DEGENERATE = 3, ST_NOT_SPD = 5, ST_UNSUPPORTED = 7 };
 
 
 // one launch of the patch kernel over a.n_items patches (MODE_SWEEP or

@@ -16,6 +16,7 @@
 #include "basis.h"
 #include "device_guard.h"
 #include "lanczos_view.h"
+#include "umesh.h"
 #include "launch.h"
 #include "mlp.h"
 
@@ -75,6 +76,7 @@ struct pmg_ctx {
   int plevels[8] = {0};
   std::vector<double> h_coords, h_kappa;
   std::vector<std::vector<double>> kappa_level;   // per-level coefficients from pmg_coeff_upload (empty: derived)
+  UMesh* um = nullptr;                             // unstructured mesh (pmg_mesh_upload), else NULL
   std::vector<HLevel> L;
   bool mesh_ok = false, setup_ok = false;
   int* d_err = nullptr;
@@ -392,6 +394,7 @@ int vcycle(pmg_ctx* ctx, int l, cudaStream_t s) {
 
 // z = M r on the finest level (FP64 in and out)
 int precondition(pmg_ctx* ctx, const double* r, double* z, cudaStream_t s) {
+  if (ctx->um) return umesh_precondition(ctx->um, r, z, s) ? fail(ctx, PMG_ERR_CUDA, "unstructured V-cycle failed") : PMG_OK;
   const int lf = ctx->nlev - 1;
   HLevel& h = ctx->L[lf];
   if (ctx->opt.precision == PMG_PREC_MIXED) {
@@ -565,6 +568,7 @@ int pmg_destroy(pmg_ctx* ctx) {
   if (ctx->h_rr) cudaFreeHost(ctx->h_rr);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   if (ctx->ev_caller) cudaEventDestroy(ctx->ev_caller);
+  if (ctx->um) umesh_destroy(ctx->um);
   delete ctx;
   return PMG_OK;
 }
@@ -607,11 +611,65 @@ int pmg_mesh_structured(pmg_ctx* ctx, int dim, int N, int p, int n_levels, const
   return PMG_OK;
 }
 
+int pmg_set_degree(pmg_ctx* ctx, int p) {
+  if (!ctx) return PMG_ERR_ARG;
+  if (ctx->setup_ok) return fail(ctx, PMG_ERR_ARG, "already set up");
+  if (ctx->mesh_ok && !ctx->um) return fail(ctx, PMG_ERR_ARG, "a structured mesh carries its own degree");
+  if (p < 1 || p > 8) return fail(ctx, PMG_ERR_UNSUPPORTED, "degree must be in 1..8");
+  ctx->p = p;
+  ctx->npl = 0;
+  for (int q = p; q >= 1; q >>= 1) ctx->plevels[ctx->npl++] = q;
+  return PMG_OK;
+}
+
+int pmg_mesh_upload(pmg_ctx* ctx, int level, int dim, int64_t n_vertices, const double* coords, int64_t n_cells,
+                    const int64_t* cell_vertices, const uint8_t* vertex_on_boundary, const int64_t* parent_cell,
+                    const uint8_t* child_index) {
+  if (!ctx) return PMG_ERR_ARG;
+  if (ctx->mesh_ok) return fail(ctx, PMG_ERR_ARG, "mesh already uploaded");
+  if (level != 0 || parent_cell || child_index)
+    return fail(ctx, PMG_ERR_UNSUPPORTED,
+                "unstructured meshes: one mesh level (level 0, no parent cells); the coarse space is the Q1 space "
+                "of the same mesh");
+  if ((dim != 2 && dim != 3) || n_vertices < 1 || n_cells < 1 || !coords || !cell_vertices)
+    return fail(ctx, PMG_ERR_ARG, "bad mesh arguments");
+  if (n_vertices > INT32_MAX || n_cells > INT32_MAX) return fail(ctx, PMG_ERR_UNSUPPORTED, "mesh too large");
+  if (ctx->opt.additive || ctx->opt.smoother == PMG_SMOOTHER_CARTESIAN)
+    return fail(ctx, PMG_ERR_UNSUPPORTED,
+                "unstructured meshes: multiplicative sweeps with the Chebyshev or Jacobi local smoother");
+  std::string msg;
+  UMesh* m = umesh_create(dim, n_vertices, coords, n_cells, cell_vertices, vertex_on_boundary, &msg);
+  if (!m) return fail(ctx, PMG_ERR_ARG, msg);
+  ctx->um = m;
+  ctx->dim = dim;
+  ctx->nlev = 1;
+  ctx->N = 0;
+  ctx->mesh_ok = true;
+  return PMG_OK;
+}
+
+int pmg_get_dof_map(pmg_ctx* ctx, int k, int32_t* out) {
+  if (!ctx || !out) return PMG_ERR_ARG;
+  if (!ctx->um || !ctx->setup_ok) return fail(ctx, PMG_ERR_ARG, "an unstructured mesh after pmg_setup");
+  if (umesh_cell_dofs(ctx->um, k, out)) return fail(ctx, PMG_ERR_ARG, "p-level out of range");
+  return PMG_OK;
+}
+
+int pmg_local_size(const pmg_ctx* ctx, int level, int64_t* n) {
+  if (!ctx || !n || !ctx->setup_ok || level < 0 || level >= ctx->nlev) return PMG_ERR_ARG;
+  *n = ctx->um ? umesh_interior_max(ctx->um) : (int64_t)ipow_sz(2 * ctx->p - 1, ctx->dim);
+  return PMG_OK;
+}
+
 int pmg_coeff_upload(pmg_ctx* ctx, int level, const double* kappa) {
   if (!ctx) return PMG_ERR_ARG;
   if (!ctx->mesh_ok) return fail(ctx, PMG_ERR_ARG, "upload a mesh first");
   if (ctx->setup_ok) return fail(ctx, PMG_ERR_ARG, "coefficients must be uploaded before pmg_setup");
   if (level < 0 || level >= ctx->nlev || !kappa) return fail(ctx, PMG_ERR_ARG, "bad level or null array");
+  if (ctx->um) {
+    if (umesh_set_kappa(ctx->um, kappa)) return fail(ctx, PMG_ERR_ARG, "kappa must be positive and finite");
+    return PMG_OK;
+  }
   const size_t nc = ipow_sz(ctx->N >> (ctx->nlev - 1 - level), ctx->dim);
   for (size_t i = 0; i < nc; ++i)
     if (!std::isfinite(kappa[i]) || !(kappa[i] > 0)) return fail(ctx, PMG_ERR_ARG, "kappa must be positive and finite");
@@ -635,6 +693,40 @@ int pmg_setup(pmg_ctx* ctx) {
     if (e != 0) return fail(ctx, PMG_ERR_CUDA, std::string("table upload: ") + cudaGetErrorString((cudaError_t)e));
   }
   const bool mixed = ctx->opt.precision == PMG_PREC_MIXED;
+  if (ctx->um) {
+    if (ctx->p < 1) return fail(ctx, PMG_ERR_ARG, "set the degree first (pmg_set_degree)");
+    if (ctx->opt.bounds != PMG_BOUNDS_FIXED && ctx->opt.bounds != PMG_BOUNDS_USER)
+      return fail(ctx, PMG_ERR_UNSUPPORTED,
+                  "unstructured meshes: fixed or user-given Chebyshev intervals (pmg_set_bounds)");
+    UOptions o;
+    o.precision = ctx->opt.precision;
+    o.smoother = ctx->opt.smoother;
+    o.cheb_degree = ctx->opt.cheb_degree;
+    o.omega = ctx->opt.jacobi_omega;
+    o.n_mg = ctx->opt.n_mg;
+    o.fixed_lo = ctx->opt.fixed_lo;
+    o.fixed_hi = ctx->opt.fixed_hi;
+    o.seed = ctx->opt.seed;
+    CU(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s));
+    std::string msg;
+    const int ust = umesh_setup(ctx->um, ctx->p, o, s, ctx->d_err, &msg);
+    if (ust == ST_DEGENERATE) return fail(ctx, PMG_ERR_DEGENERATE, msg);
+    if (ust == ST_UNSUPPORTED) return fail(ctx, PMG_ERR_UNSUPPORTED, msg);
+    if (ust) return fail(ctx, PMG_ERR_CUDA, msg.empty() ? "unstructured set-up failed" : msg);
+    const size_t n = (size_t)umesh_ndofs(ctx->um);
+    DALLOC(ctx->cg_x, n);
+    DALLOC(ctx->cg_r, n);
+    DALLOC(ctx->cg_z, n);
+    DALLOC(ctx->cg_p, n);
+    DALLOC(ctx->cg_Ap, n);
+    DALLOC(ctx->stage_b, n);
+    DALLOC(ctx->stage_u, n);
+    DALLOC(ctx->partial, DOT_BLOCKS);
+    DALLOC(ctx->scal, S_NSLOT);
+    ctx->setup_ok = true;
+    CU(cudaStreamSynchronize(s));
+    return PMG_OK;
+  }
   // ---- levels: coordinates (even-index subsampling), kappa (mean of children)
   ctx->L.assign(ctx->nlev, HLevel());
   std::vector<double> X = ctx->h_coords, K = ctx->h_kappa;
@@ -896,6 +988,17 @@ int pmg_setup(pmg_ctx* ctx) {
 int pmg_compute_bounds(pmg_ctx* ctx, int source) {
   if (!ctx || !ctx->setup_ok) return fail(ctx, PMG_ERR_ARG, "not set up");
   PMG_GUARD_CTX(ctx);
+  if (ctx->um) {
+    if (source == PMG_BOUNDS_USER) return PMG_OK;
+    if (source != PMG_BOUNDS_FIXED)
+      return fail(ctx, PMG_ERR_UNSUPPORTED, "unstructured meshes: fixed or user-given Chebyshev intervals");
+    const size_t np = (size_t)umesh_npatch(ctx->um);
+    std::vector<double> v(2 * np);
+    for (size_t j = 0; j < np; ++j) { v[2 * j] = ctx->opt.fixed_lo; v[2 * j + 1] = ctx->opt.fixed_hi; }
+    for (int k = 0; k < ctx->npl; ++k)
+      if (ctx->plevels[k] > 1 && umesh_set_bounds(ctx->um, k, v.data())) return fail(ctx, PMG_ERR_CUDA, "bounds");
+    return PMG_OK;
+  }
   cudaStream_t s = ctx->stream;
   const int d = ctx->dim;
   if (source == PMG_BOUNDS_USER) return PMG_OK;
@@ -996,6 +1099,12 @@ int pmg_compute_bounds(pmg_ctx* ctx, int source) {
 
 int pmg_num_dofs(const pmg_ctx* ctx, int level, int64_t* total, int64_t* n_free) {
   if (!ctx || !ctx->mesh_ok || level < 0 || level >= ctx->nlev) return PMG_ERR_ARG;
+  if (ctx->um) {
+    if (!ctx->setup_ok) return PMG_ERR_ARG;
+    if (total) *total = umesh_ndofs(ctx->um);
+    if (n_free) *n_free = umesh_nfree(ctx->um);
+    return PMG_OK;
+  }
   const int Nl = ctx->N >> (ctx->nlev - 1 - level);
   if (total) *total = (int64_t)ipow_sz((size_t)ctx->p * Nl + 1, ctx->dim);
   if (n_free) *n_free = (int64_t)ipow_sz((size_t)ctx->p * Nl - 1, ctx->dim);
@@ -1004,6 +1113,12 @@ int pmg_num_dofs(const pmg_ctx* ctx, int level, int64_t* total, int64_t* n_free)
 
 int pmg_num_patches(const pmg_ctx* ctx, int level, int64_t* n_patches, int* n_colours) {
   if (!ctx || !ctx->mesh_ok || level < 0 || level >= ctx->nlev) return PMG_ERR_ARG;
+  if (ctx->um) {
+    if (!ctx->setup_ok) return PMG_ERR_ARG;
+    if (n_patches) *n_patches = umesh_npatch(ctx->um);
+    if (n_colours) *n_colours = umesh_ncolours(ctx->um);
+    return PMG_OK;
+  }
   const int Nl = ctx->N >> (ctx->nlev - 1 - level);
   if (n_patches) *n_patches = (int64_t)ipow_sz(Nl - 1, ctx->dim);
   if (n_colours) *n_colours = 1 << ctx->dim;
@@ -1030,6 +1145,7 @@ int pmg_apply(pmg_ctx* ctx, int level, const double* u, double* Au, void* stream
   if (st) return st;
   PMG_GUARD_CTX(ctx);
   if (!u || !Au) return fail(ctx, PMG_ERR_ARG, "null vector");
+  if (ctx->um) return umesh_apply(ctx->um, u, Au, (cudaStream_t)stream) ? fail(ctx, PMG_ERR_CUDA, "apply failed") : PMG_OK;
   HLevel& h = ctx->L[level];
   LK(1 + (1 << ctx->dim), cell_apply<double>(ctx, ctx->p, u, Au, h.pl[0].G64, h.N, (cudaStream_t)stream));
   return PMG_OK;
@@ -1039,8 +1155,13 @@ int pmg_patch_smooth_colour(pmg_ctx* ctx, int level, int colour, const double* b
   int st = check_level(ctx, level);
   if (st) return st;
   PMG_GUARD_CTX(ctx);
-  if (colour < 0 || colour >= (1 << ctx->dim)) return fail(ctx, PMG_ERR_ARG, "colour out of range");
   if (!b || !u) return fail(ctx, PMG_ERR_ARG, "null vector");
+  if (ctx->um) {
+    if (colour < 0 || colour >= umesh_ncolours(ctx->um)) return fail(ctx, PMG_ERR_ARG, "colour out of range");
+    return umesh_sweep_colour(ctx->um, colour, b, u, (cudaStream_t)stream) ? fail(ctx, PMG_ERR_CUDA, "sweep failed")
+                                                                           : PMG_OK;
+  }
+  if (colour < 0 || colour >= (1 << ctx->dim)) return fail(ctx, PMG_ERR_ARG, "colour out of range");
   if (ctx->opt.additive) return fail(ctx, PMG_ERR_UNSUPPORTED, "an additive sweep runs all colours (pmg_patch_smooth)");
   cudaStream_t s = (cudaStream_t)stream;
   HLevel& h = ctx->L[level];
@@ -1061,6 +1182,8 @@ int pmg_patch_smooth(pmg_ctx* ctx, int level, const double* b, double* u, int n_
   PMG_GUARD_CTX(ctx);
   if (!b || !u || n_sweeps < 0) return fail(ctx, PMG_ERR_ARG, "bad arguments");
   cudaStream_t s = (cudaStream_t)stream;
+  if (ctx->um)
+    return umesh_sweep(ctx->um, b, u, n_sweeps, reverse != 0, s) ? fail(ctx, PMG_ERR_CUDA, "sweep failed") : PMG_OK;
   HLevel& h = ctx->L[level];
   if (ctx->opt.precision == PMG_PREC_MIXED) {
     LK(1, launch_cast_d2f(b, ctx->s32a, h.nd, s));
@@ -1086,6 +1209,11 @@ int pmg_local_vcycle(pmg_ctx* ctx, int level, int64_t n, const int64_t* ids, con
   PMG_GUARD_CTX(ctx);
   if (n < 0 || (n > 0 && (!ids || !r || !dout)) || n_cycles < 1) return fail(ctx, PMG_ERR_ARG, "bad arguments");
   if (n == 0) return PMG_OK;
+  if (ctx->um) {
+    if (n > umesh_npatch(ctx->um)) return fail(ctx, PMG_ERR_ARG, "more patches than the level has");
+    return umesh_local(ctx->um, n, ids, r, dout, n_cycles, (cudaStream_t)stream) ? fail(ctx, PMG_ERR_CUDA, "local solve failed")
+                                                                                 : PMG_OK;
+  }
   HLevel& h = ctx->L[level];
   if ((size_t)n > h.npatch) return fail(ctx, PMG_ERR_ARG, "more patches than the level has");
   cudaStream_t s = (cudaStream_t)stream;
@@ -1116,6 +1244,21 @@ int pmg_get_bounds(pmg_ctx* ctx, int level, double* lohi) {
   int st = check_level(ctx, level);
   if (st) return st;
   PMG_GUARD_CTX(ctx);
+  if (ctx->um) {
+    const size_t np = (size_t)umesh_npatch(ctx->um);
+    std::vector<double> out(2 * np * ctx->npl, 0.0), tmp(2 * np);
+    CU(cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < ctx->npl; ++k) {
+      if (ctx->plevels[k] == 1 || np == 0) continue;
+      if (umesh_get_bounds(ctx->um, k, tmp.data())) return fail(ctx, PMG_ERR_CUDA, "bounds copy failed");
+      for (size_t j = 0; j < np; ++j) {
+        out[(j * ctx->npl + k) * 2] = tmp[2 * j];
+        out[(j * ctx->npl + k) * 2 + 1] = tmp[2 * j + 1];
+      }
+    }
+    std::memcpy(lohi, out.data(), out.size() * sizeof(double));
+    return PMG_OK;
+  }
   HLevel& h = ctx->L[level];
   std::vector<double> out(2 * h.npatch * ctx->npl, 0.0), tmp(2 * h.npatch);
   CU(cudaStreamSynchronize(ctx->stream));
@@ -1135,6 +1278,7 @@ int pmg_get_ritz(pmg_ctx* ctx, int level, double* tm) {
   int st = check_level(ctx, level);
   if (st) return st;
   PMG_GUARD_CTX(ctx);
+  if (ctx->um) return fail(ctx, PMG_ERR_UNSUPPORTED, "not available on unstructured meshes");
   HLevel& h = ctx->L[level];
   std::vector<double> out(2 * h.npatch * ctx->npl, 0.0), tmp(2 * h.npatch);
   CU(cudaStreamSynchronize(ctx->stream));
@@ -1154,6 +1298,22 @@ int pmg_set_bounds(pmg_ctx* ctx, int level, const double* lohi) {
   int st = check_level(ctx, level);
   if (st) return st;
   PMG_GUARD_CTX(ctx);
+  if (ctx->um) {
+    const size_t np = (size_t)umesh_npatch(ctx->um);
+    std::vector<double> tmp(2 * np);
+    CU(cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < ctx->npl; ++k) {
+      if (ctx->plevels[k] == 1 || np == 0) continue;
+      for (size_t j = 0; j < np; ++j) {
+        const double lo = lohi[(j * ctx->npl + k) * 2], hi = lohi[(j * ctx->npl + k) * 2 + 1];
+        if (!(lo > 0) || !(hi > lo)) return fail(ctx, PMG_ERR_ARG, "bounds must satisfy 0 < lo < hi");
+        tmp[2 * j] = lo;
+        tmp[2 * j + 1] = hi;
+      }
+      if (umesh_set_bounds(ctx->um, k, tmp.data())) return fail(ctx, PMG_ERR_CUDA, "bounds copy failed");
+    }
+    return PMG_OK;
+  }
   HLevel& h = ctx->L[level];
   std::vector<double> tmp(2 * h.npatch);
   for (int k = 0; k < ctx->npl; ++k) {
@@ -1182,14 +1342,31 @@ int pmg_gmg_vcycle(pmg_ctx* ctx, const double* b, double* x, void* stream) {
 // One CG iteration body (captured into a CUDA graph): z = M r, rz = (r, z),
 // p = z + beta p, Ap = A p, alpha = rz / (p, Ap), x += alpha p, r -= alpha Ap,
 // rr = (r, r) copied to pinned host memory.
-static int cg_body(pmg_ctx* ctx, cudaStream_t s) {
+// vector length of the finest level
+static size_t fine_n(const pmg_ctx* ctx) { return ctx->um ? (size_t)umesh_ndofs(ctx->um) : ctx->L.back().nd; }
+
+// Ax = A x on the finest level (FP64)
+static int fine_apply(pmg_ctx* ctx, const double* x, double* Ax, cudaStream_t s) {
+  if (ctx->um) return umesh_apply(ctx->um, x, Ax, s) ? fail(ctx, PMG_ERR_CUDA, "apply failed") : PMG_OK;
   HLevel& h = ctx->L.back();
-  const size_t n = h.nd;
+  LK(1 + (1 << ctx->dim), cell_apply<double>(ctx, ctx->p, x, Ax, h.pl[0].G64, h.N, s));
+  return PMG_OK;
+}
+
+static int fine_mask(pmg_ctx* ctx, double* x, cudaStream_t s) {
+  if (ctx->um) return umesh_mask(ctx->um, x, s) ? fail(ctx, PMG_ERR_CUDA, "mask failed") : PMG_OK;
+  LK(1, mask_boundary<double>(ctx, x, ctx->p * ctx->L.back().N + 1, s));
+  return PMG_OK;
+}
+
+static int cg_body(pmg_ctx* ctx, cudaStream_t s) {
+  const size_t n = fine_n(ctx);
   int st = precondition(ctx, ctx->cg_r, ctx->cg_z, s);
   if (st) return st;
   LK(2, launch_dot(ctx->cg_r, ctx->cg_z, n, ctx->partial, ctx->scal, S_RZ, 1, s));
   LK(1, launch_cg_update_p(ctx->cg_z, ctx->cg_p, ctx->scal, n, s));
-  LK(1 + (1 << ctx->dim), cell_apply<double>(ctx, ctx->p, ctx->cg_p, ctx->cg_Ap, h.pl[0].G64, h.N, s));
+  st = fine_apply(ctx, ctx->cg_p, ctx->cg_Ap, s);
+  if (st) return st;
   LK(2, launch_dot(ctx->cg_p, ctx->cg_Ap, n, ctx->partial, ctx->scal, S_PAP, 2, s));
   LK(1, launch_cg_update_xr(ctx->cg_x, ctx->cg_r, ctx->cg_p, ctx->cg_Ap, ctx->scal, n, s));
   LK(2, launch_dot(ctx->cg_r, ctx->cg_r, n, ctx->partial, ctx->scal, S_RR, 0, s));
@@ -1204,13 +1381,12 @@ static int cg_body(pmg_ctx* ctx, cudaStream_t s) {
 // asynchronous on the context's stream.
 static int cg_start(pmg_ctx* ctx, const double* b) {
   cudaStream_t s = ctx->stream;
-  HLevel& h = ctx->L.back();
-  const size_t n = h.nd;
-  const int M = ctx->p * h.N + 1;
+  const size_t n = fine_n(ctx);
   CU(cudaMemsetAsync(ctx->cg_x, 0, n * sizeof(double), s));
   CU(cudaMemsetAsync(ctx->cg_p, 0, n * sizeof(double), s));
   CU(cudaMemcpyAsync(ctx->cg_r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  LK(1, mask_boundary<double>(ctx, ctx->cg_r, M, s));
+  const int stm = fine_mask(ctx, ctx->cg_r, s);
+  if (stm) return stm;
   {
     static const double init[S_NSLOT] = {0.0, 1.0, 0.0, 0.0, 0.0, 0.0};
     CU(cudaMemcpyAsync(ctx->scal, init, sizeof(init), cudaMemcpyHostToDevice, s));
@@ -1265,8 +1441,7 @@ int pmg_solve_cg(pmg_ctx* ctx, const double* b, double* u, double rtol, int maxi
   // on the caller's stream (an event wait; the caller's stream is not synchronised)
   CU(cudaEventRecord(ctx->ev_caller, us));
   CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_caller, 0));
-  HLevel& h = ctx->L.back();
-  const size_t n = h.nd;
+  const size_t n = fine_n(ctx);
   st = cg_start(ctx, b);
   if (st) return st;
   CU(cudaStreamSynchronize(s));
@@ -1403,9 +1578,7 @@ int pmg_solve_gmres(pmg_ctx* ctx, const double* b, double* u, double rtol, int m
   // on the caller's stream (an event wait; the caller's stream is not synchronised)
   CU(cudaEventRecord(ctx->ev_caller, us));
   CU(cudaStreamWaitEvent(ctx->stream, ctx->ev_caller, 0));
-  HLevel& h = ctx->L.back();
-  const size_t n = h.nd;
-  const int M = ctx->p * h.N + 1;
+  const size_t n = fine_n(ctx);
   if (ctx->gm_m < restart) {
     if (ctx->gm_V) CU(cudaFree(ctx->gm_V));
     ctx->gm_V = nullptr;
@@ -1417,7 +1590,8 @@ int pmg_solve_gmres(pmg_ctx* ctx, const double* b, double* u, double rtol, int m
   double *x = ctx->cg_x, *r = ctx->cg_r, *w = ctx->cg_Ap, *z = ctx->cg_z, *t = ctx->cg_p;
   CU(cudaMemsetAsync(x, 0, n * sizeof(double), s));
   CU(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  LK(1, mask_boundary<double>(ctx, r, M, s));
+  st = fine_mask(ctx, r, s);
+  if (st) return st;
   if (left) {                                                           // r = M b
     st = precondition(ctx, r, z, s);
     if (st) return st;
@@ -1443,11 +1617,12 @@ int pmg_solve_gmres(pmg_ctx* ctx, const double* b, double* u, double rtol, int m
     int k = 0;
     for (int j = 0; j < restart && it < maxit; ++j) {
       if (left) {                                                       // w = M A v_j
-        LK(1 + (1 << ctx->dim), cell_apply<double>(ctx, ctx->p, V + (size_t)j * n, z, h.pl[0].G64, h.N, s));
+        st = fine_apply(ctx, V + (size_t)j * n, z, s);
+        if (st) break;
         st = precondition(ctx, z, w, s);
       } else {                                                          // w = A M v_j
         st = precondition(ctx, V + (size_t)j * n, z, s);
-        if (!st) LK(1 + (1 << ctx->dim), cell_apply<double>(ctx, ctx->p, z, w, h.pl[0].G64, h.N, s));
+        if (!st) st = fine_apply(ctx, z, w, s);
       }
       if (st) return st;
       for (int i = 0; i <= j; ++i) {                                    // modified Gram-Schmidt
@@ -1500,9 +1675,11 @@ int pmg_solve_gmres(pmg_ctx* ctx, const double* b, double* u, double rtol, int m
       if (st) return st;
       LK(1, launch_axpy(1.0, z, x, n, s));
     }
-    LK(1 + (1 << ctx->dim), cell_apply<double>(ctx, ctx->p, x, w, h.pl[0].G64, h.N, s));   // r = b - A x
+    st = fine_apply(ctx, x, w, s);   // r = b - A x
+    if (st) return st;
     CU(cudaMemcpyAsync(r, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    LK(1, mask_boundary<double>(ctx, r, M, s));
+    st = fine_mask(ctx, r, s);
+    if (st) return st;
     LK(1, launch_axpy(-1.0, w, r, n, s));
     if (left) {                                                         // r = M (b - A x)
       st = precondition(ctx, r, z, s);
@@ -1524,7 +1701,7 @@ int pmg_solve_cg_host(pmg_ctx* ctx, const double* b_host, double* u_host, double
   if (st) return st;
   PMG_GUARD_CTX(ctx);
   if (!b_host || !u_host) return fail(ctx, PMG_ERR_ARG, "null vector");
-  const size_t n = ctx->L.back().nd;
+  const size_t n = fine_n(ctx);
   cudaStream_t s = ctx->stream;
   CU(cudaMemcpyAsync(ctx->stage_b, b_host, n * sizeof(double), cudaMemcpyHostToDevice, s));
   CU(cudaStreamSynchronize(s));
@@ -1538,6 +1715,7 @@ int pmg_rhs_manufactured(pmg_ctx* ctx, double* b, void* stream) {
   int st = check_level(ctx, ctx ? ctx->nlev - 1 : 0);
   if (st) return st;
   PMG_GUARD_CTX(ctx);
+  if (ctx->um) return fail(ctx, PMG_ERR_UNSUPPORTED, "not available on unstructured meshes");
   if (!b) return fail(ctx, PMG_ERR_ARG, "null vector");
   HLevel& h = ctx->L.back();
   if (ctx->dim == 2) ST(launch_rhs_manufactured<2>(h.coords, h.N, ctx->p, b, (cudaStream_t)stream));
@@ -1547,6 +1725,7 @@ int pmg_rhs_manufactured(pmg_ctx* ctx, double* b, void* stream) {
 
 int pmg_get_colours(const pmg_ctx* ctx, int level, uint8_t* out) {
   if (!ctx || !ctx->setup_ok || level < 0 || level >= ctx->nlev || !out) return PMG_ERR_ARG;
+  if (ctx->um) return umesh_colours(ctx->um, out) ? PMG_ERR_ARG : PMG_OK;
   const HLevel& h = ctx->L[level];
   std::memcpy(out, h.colours.data(), h.npatch);
   return PMG_OK;
@@ -1554,6 +1733,7 @@ int pmg_get_colours(const pmg_ctx* ctx, int level, uint8_t* out) {
 
 int pmg_get_patch_map(const pmg_ctx* ctx, int level, int64_t* out) {
   if (!ctx || !ctx->setup_ok || level < 0 || level >= ctx->nlev || !out) return PMG_ERR_ARG;
+  if (ctx->um) return umesh_patches(ctx->um, out, 1 + PMG_UMAXC) ? PMG_ERR_ARG : PMG_OK;
   const HLevel& h = ctx->L[level];
   const int d = ctx->dim, Nl = h.N, Nv = Nl - 1;
   const size_t Mg = (size_t)ctx->p * Nl + 1;
@@ -1578,6 +1758,7 @@ int pmg_get_inv_diag(pmg_ctx* ctx, int level, int k, double* out, void* stream) 
   int st = check_level(ctx, level);
   if (st) return st;
   PMG_GUARD_CTX(ctx);
+  if (ctx->um) return fail(ctx, PMG_ERR_UNSUPPORTED, "not available on unstructured meshes");
   if (k < 0 || k >= ctx->npl || !out) return fail(ctx, PMG_ERR_ARG, "bad p-level");
   HLevel& h = ctx->L[level];
   const size_t ndq = ipow_sz((size_t)h.pl[k].q * h.N + 1, ctx->dim);
@@ -1586,7 +1767,7 @@ int pmg_get_inv_diag(pmg_ctx* ctx, int level, int k, double* out, void* stream) 
 }
 
 double pmg_sweep_flops(const pmg_ctx* ctx, int level) {
-  if (!ctx || !ctx->mesh_ok || level < 0 || level >= ctx->nlev) return 0.0;
+  if (!ctx || !ctx->mesh_ok || level < 0 || level >= ctx->nlev || ctx->um) return 0.0;
   const int d = ctx->dim;
   const int Nl = ctx->N >> (ctx->nlev - 1 - level);
   const double npatch = (double)ipow_sz(Nl - 1, d);
@@ -1647,6 +1828,7 @@ int pmg_features(pmg_ctx* ctx, int level, int k, float* X, void* stream) {
   int st = check_level(ctx, level);
   if (st) return st;
   PMG_GUARD_CTX(ctx);
+  if (ctx->um) return fail(ctx, PMG_ERR_UNSUPPORTED, "not available on unstructured meshes");
   if (k < 0 || k >= ctx->npl || !X) return fail(ctx, PMG_ERR_ARG, "bad p-level or null output");
   HLevel& h = ctx->L[level];
   ST(features_launch(ctx->dim, h.coords, h.kappa, h.N, h.pl[k].q, ctx->npl - 1 - k, (int)h.npatch, X,
@@ -1671,6 +1853,7 @@ int pmg_mlp_targets(pmg_ctx* ctx, int level, int k, float* T, void* stream) {
   int st = check_level(ctx, level);
   if (st) return st;
   PMG_GUARD_CTX(ctx);
+  if (ctx->um) return fail(ctx, PMG_ERR_UNSUPPORTED, "not available on unstructured meshes");
   if (k < 0 || k >= ctx->npl || !T) return fail(ctx, PMG_ERR_ARG, "bad p-level or null output");
   const HLevel& h = ctx->L[level];
   if (h.pl[k].q < 2) return fail(ctx, PMG_ERR_ARG, "the p = 1 level has no Lanczos estimates");
@@ -1717,7 +1900,7 @@ int pmg_mlp_load(pmg_ctx* ctx, const char* path) {
 
 int pmg_launch_count(const pmg_ctx* ctx, int64_t* n) {
   if (!ctx || !n) return PMG_ERR_ARG;
-  *n = ctx->launches;
+  *n = ctx->launches + (ctx->um ? umesh_kernel_launches(ctx->um) : 0);
   return PMG_OK;
 }
 

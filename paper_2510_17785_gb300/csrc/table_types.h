@@ -34,6 +34,7 @@ struct Rules {
   double Bg[PMG_MAXQ + 1][PMG_MAXQ + 2][PMG_MAXQ + 1];   // basis at the (q+2)-point rule
   double gx2[PMG_MAXQ + 1][PMG_MAXQ + 2];                 // (q+2)-point Gauss rule
   double gw2[PMG_MAXQ + 1][PMG_MAXQ + 2];
+  double gll[PMG_MAXQ + 1][PMG_MAXQ + 1];                 // Gauss-Lobatto nodes on [0, 1]
 };
 
 using TableUploader = int (*)(const Tables<double>&, const Tables<float>&, const Rules&);

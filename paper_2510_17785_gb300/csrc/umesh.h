@@ -1,0 +1,62 @@
+// Internal interface of the unstructured-mesh path (umesh.cu): the vertex-
+// patch smoother with the local p-multigrid solver on quadrilateral /
+// hexahedral meshes of arbitrary topology, the global operator, and a
+// two-level preconditioner (patch sweeps on Q_p, the Q1 space of the same
+// mesh as coarse space, dense Cholesky) for CG.  Not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace pmg {
+
+struct UMesh;
+
+struct UOptions {
+  int precision;         // PMG_PREC_*
+  int smoother;          // 0 Chebyshev, 1 Jacobi
+  int cheb_degree;
+  double omega;
+  int n_mg;
+  double fixed_lo, fixed_hi;
+  uint64_t seed;         // colouring priority
+};
+
+// host mesh (copied); kappa may be empty (1 everywhere)
+UMesh* umesh_create(int dim, int64_t nv, const double* coords, int64_t nc, const int64_t* cells,
+                    const uint8_t* vertex_on_boundary, std::string* msg);
+void umesh_destroy(UMesh* m);
+int umesh_set_kappa(UMesh* m, const double* kappa);     // nc values
+// build everything for degree p (p-levels p, p/2, ..., 1); ST_* codes, msg on error
+int umesh_setup(UMesh* m, int p, const UOptions& o, cudaStream_t s, int* err_dev, std::string* msg);
+
+int64_t umesh_ndofs(const UMesh* m);
+int64_t umesh_nfree(const UMesh* m);
+int64_t umesh_npatch(const UMesh* m);
+int umesh_ncolours(const UMesh* m);
+int umesh_nplevels(const UMesh* m, int* q);
+int64_t umesh_kernel_launches(const UMesh* m);
+// host copies of the integer structures
+int umesh_cell_dofs(const UMesh* m, int k, int32_t* out);             // [nc][(q+1)^d]
+int umesh_patches(const UMesh* m, int64_t* out, int width);           // [npatch][width]: vertex, cells (-1)
+int umesh_colours(const UMesh* m, uint8_t* out);
+int umesh_get_bounds(const UMesh* m, int k, double* out);             // [npatch][2]
+int umesh_set_bounds(UMesh* m, int k, const double* lohi);            // [npatch][2]
+int umesh_max_valence(const UMesh* m);
+
+// FP64 vectors of length umesh_ndofs (caller's device memory)
+int umesh_apply(UMesh* m, const double* u, double* Au, cudaStream_t s);
+int umesh_sweep(UMesh* m, const double* b, double* u, int n_sweeps, bool reverse, cudaStream_t s);
+int umesh_sweep_colour(UMesh* m, int colour, const double* b, double* u, cudaStream_t s);
+// local solves of patches ids[0..n): r, d are [n][n_interior_max] (rows padded)
+int umesh_local(UMesh* m, int64_t n, const int64_t* ids_dev, const double* r, double* d, int n_cycles,
+                cudaStream_t s);
+int64_t umesh_interior_max(const UMesh* m);
+// z = M r (two-level V-cycle), FP64 in and out
+int umesh_precondition(UMesh* m, const double* r, double* z, cudaStream_t s);
+// zero the Dirichlet DoFs of x
+int umesh_mask(UMesh* m, double* x, cudaStream_t s);
+
+}  // namespace pmg

@@ -25,6 +25,7 @@ BOUNDS_LANCZOS, BOUNDS_FIXED, BOUNDS_USER, BOUNDS_MLP = 0, 1, 2, 3
 MLP_NPARAM, MLP_NNORM = 5378, 36
 PREC_FP64, PREC_MIXED = 0, 1
 NUM_VARIANTS = 16              # PMG_NUM_VARIANTS of include/pmg.h
+UMAXC = 32                     # PMG_UMAXC: most cells of an unstructured patch
 KAPPA_ARITHMETIC, KAPPA_GEOMETRIC, KAPPA_HARMONIC = 0, 1, 2
 
 # every symbol include/pmg.h declares
@@ -37,7 +38,7 @@ SYMBOLS = (
     "pmg_lanczos_bounds_noalloc", "pmg_tuning", "pmg_default_train_options", "pmg_features", "pmg_mlp_grad",
     "pmg_mlp_train", "pmg_mlp_predict", "pmg_set_mlp", "pmg_solve_gmres", "pmg_batch_solve_cg",
     "pmg_tuning_level", "pmg_coeff_upload", "pmg_mlp_init", "pmg_mlp_targets", "pmg_mlp_norm", "pmg_mlp_save",
-    "pmg_mlp_load",
+    "pmg_mlp_load", "pmg_mesh_upload", "pmg_set_degree", "pmg_get_dof_map", "pmg_local_size",
 )
 
 
@@ -122,6 +123,10 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pmg_mlp_norm": (i, [i, vp, vp, i64, vp]),
         "pmg_mlp_save": (i, [vp, C.c_char_p]),
         "pmg_mlp_load": (i, [vp, C.c_char_p]),
+        "pmg_mesh_upload": (i, [vp, i, i, i64, vp, i64, vp, vp, vp, vp]),
+        "pmg_set_degree": (i, [vp, i]),
+        "pmg_get_dof_map": (i, [vp, i, vp]),
+        "pmg_local_size": (i, [vp, i, P(i64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -297,6 +302,43 @@ class Context:
                                                  kappa.ctypes.data))
         self.dim, self.N, self.p, self.n_levels = dim, N, p, n_levels
 
+    def mesh_upload(self, dim: int, coords: np.ndarray, cells: np.ndarray, p: int,
+                    vertex_on_boundary: Optional[np.ndarray] = None, kappa: Optional[np.ndarray] = None):
+        """Unstructured quadrilateral / hexahedral mesh: coords [n_v][dim],
+        cells [n_c][2^dim] vertex ids (lexicographic corner order); degree p."""
+        coords = np.ascontiguousarray(coords, dtype=np.float64)
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        nv, nc = coords.shape[0], cells.shape[0]
+        if coords.shape != (nv, dim) or cells.shape != (nc, 2 ** dim):
+            raise ValueError("coords must be [n_v][dim] and cells [n_c][2^dim]")
+        vob = None
+        if vertex_on_boundary is not None:
+            vob = np.ascontiguousarray(vertex_on_boundary, dtype=np.uint8)
+            if vob.shape != (nv,):
+                raise ValueError("vertex_on_boundary must hold n_v flags")
+        self._check(self.lib.pmg_mesh_upload(self.h, 0, dim, nv, coords.ctypes.data, nc, cells.ctypes.data,
+                                             None if vob is None else vob.ctypes.data, None, None))
+        self._check(self.lib.pmg_set_degree(self.h, p))
+        if kappa is not None:
+            self.coeff_upload(0, kappa)
+        self.dim, self.N, self.p, self.n_levels = dim, None, p, 1
+        self.n_cells = nc
+
+    def set_degree(self, p: int):
+        self._check(self.lib.pmg_set_degree(self.h, p))
+        self.p = p
+
+    def get_dof_map(self, k: int = 0):
+        q = self.p_levels()[k]
+        out = np.zeros((self.n_cells, (q + 1) ** self.dim), dtype=np.int32)
+        self._check(self.lib.pmg_get_dof_map(self.h, k, out.ctypes.data))
+        return out
+
+    def local_size(self, level: int) -> int:
+        n = C.c_int64()
+        self._check(self.lib.pmg_local_size(self.h, level, C.byref(n)))
+        return n.value
+
     def setup(self):
         self._check(self.lib.pmg_setup(self.h))
 
@@ -392,7 +434,8 @@ class Context:
 
     def get_patch_map(self, level):
         n, _ = self.num_patches(level)
-        out = np.zeros((n, 2 ** self.dim + 1), dtype=np.int64)
+        width = 2 ** self.dim + 1 if self.N is not None else 1 + UMAXC
+        out = np.zeros((n, width), dtype=np.int64)
         self._check(self.lib.pmg_get_patch_map(self.h, level, out.ctypes.data))
         return out
 
