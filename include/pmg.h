@@ -158,8 +158,10 @@ int pmg_mesh_structured(pmg_ctx* ctx, int dim, int N, int p, int n_levels,
  * fastest); cell interiors by cell, x fastest.  Patches: the interior vertices
  * in increasing id, each with its cells; colours: greedy in decreasing
  * (splitmix64(id ^ seed), id), the smallest colour not used by a patch that
- * shares a cell.  Chebyshev intervals: PMG_BOUNDS_FIXED or USER
- * (pmg_set_bounds); the smoother Chebyshev or Jacobi; multiplicative sweeps.
+ * shares a cell.  Chebyshev intervals: PMG_BOUNDS_LANCZOS (FP64 operator in
+ * both precisions; start-vector counter (vertex id << 20) | (q << 16) | i),
+ * FIXED or USER (pmg_set_bounds); the smoother Chebyshev or Jacobi;
+ * multiplicative sweeps.
  * Local vectors of pmg_local_vcycle: one row of pmg_local_size values per patch
  * (its interior DoFs in increasing global id, zero padded). */
 int pmg_mesh_upload(pmg_ctx* ctx, int level, int dim, int64_t n_vertices, const double* coords,
@@ -229,7 +231,8 @@ int pmg_patch_smooth_colour(pmg_ctx* ctx, int level, int colour, const double* b
  * write the corrections d_dev.  r_dev and d_dev are device FP64 arrays of
  * n x (2p-1)^d values, patch-interior DoFs in lexicographic order (x fastest)
  * (unstructured meshes: n x pmg_local_size values, each row the patch's
- * interior DoFs in increasing global id, zero padded). */
+ * interior DoFs in increasing global id, zero padded).  An id outside
+ * 0 .. n_patches - 1 gives a row of zeros (the call stays asynchronous). */
 int pmg_local_vcycle(pmg_ctx* ctx, int level, int64_t n, const int64_t* patch_ids_dev,
                      const double* r_dev, double* d_dev, int n_cycles, void* stream);
 

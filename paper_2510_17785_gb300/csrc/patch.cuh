@@ -659,11 +659,18 @@ struct PatchKernel {
   // ---- per-patch set-up: ids, cell list, level diagonals, Chebyshev coefficients
   __device__ void setup_patch(int pp, int item, bool active) {
     int pid = 0;
-    if (active) {
-      if (MODE == MODE_SWEEP) pid = a->list[item];
-      else pid = (int)a->ids64[item];
-    }
     const int N = a->N, Nv = N - 1;
+    if (active) {
+      if (MODE == MODE_SWEEP) {
+        pid = a->list[item];
+      } else {
+        const int64_t raw = a->ids64[item];
+        int64_t np = 1;
+        for (int ax = 0; ax < DIM; ++ax) np *= Nv;
+        if (raw >= 0 && raw < np) pid = (int)raw;
+        else active = false;                            // not a patch: a zero row
+      }
+    }
     int v[3] = {1, 1, 1};
     int rem = pid;
     for (int ax = 0; ax < DIM; ++ax) { v[ax] = 1 + rem % Nv; rem /= Nv; }
@@ -849,7 +856,7 @@ struct PatchKernel {
     } else {
       TM::template loop<NI0>([&](int pp, int i) {
         const bool act = cells[pp * CST + NCELL + 1];
-        if (act) a->d_out[(size_t)(item0 + pp) * NI0 + i] = vec(pp, L::D_(0))[i];
+        if (item0 + pp < a->n_items) a->d_out[(size_t)(item0 + pp) * NI0 + i] = act ? vec(pp, L::D_(0))[i] : T(0);
       });
     }
   }

@@ -695,9 +695,11 @@ int pmg_setup(pmg_ctx* ctx) {
   const bool mixed = ctx->opt.precision == PMG_PREC_MIXED;
   if (ctx->um) {
     if (ctx->p < 1) return fail(ctx, PMG_ERR_ARG, "set the degree first (pmg_set_degree)");
-    if (ctx->opt.bounds != PMG_BOUNDS_FIXED && ctx->opt.bounds != PMG_BOUNDS_USER)
+    if (ctx->opt.bounds == PMG_BOUNDS_MLP)
       return fail(ctx, PMG_ERR_UNSUPPORTED,
-                  "unstructured meshes: fixed or user-given Chebyshev intervals (pmg_set_bounds)");
+                  "unstructured meshes: Lanczos, fixed or user-given Chebyshev intervals (pmg_set_bounds)");
+    if (ctx->opt.bounds == PMG_BOUNDS_LANCZOS && (ctx->opt.lanczos_steps < 1 || ctx->opt.lanczos_steps > 64))
+      return fail(ctx, PMG_ERR_ARG, "lanczos_steps must be in 1..64");
     UOptions o;
     o.precision = ctx->opt.precision;
     o.smoother = ctx->opt.smoother;
@@ -723,6 +725,9 @@ int pmg_setup(pmg_ctx* ctx) {
     DALLOC(ctx->stage_u, n);
     DALLOC(ctx->partial, DOT_BLOCKS);
     DALLOC(ctx->scal, S_NSLOT);
+    if (ctx->opt.bounds == PMG_BOUNDS_LANCZOS &&
+        umesh_lanczos(ctx->um, ctx->opt.lanczos_steps, ctx->opt.seed, ctx->opt.bound_safety, ctx->opt.bound_ratio, s))
+      return fail(ctx, PMG_ERR_CUDA, "unstructured Lanczos intervals failed");
     ctx->setup_ok = true;
     CU(cudaStreamSynchronize(s));
     return PMG_OK;
@@ -990,8 +995,16 @@ int pmg_compute_bounds(pmg_ctx* ctx, int source) {
   PMG_GUARD_CTX(ctx);
   if (ctx->um) {
     if (source == PMG_BOUNDS_USER) return PMG_OK;
+    if (source == PMG_BOUNDS_LANCZOS) {
+      if (ctx->opt.lanczos_steps < 1 || ctx->opt.lanczos_steps > 64)
+        return fail(ctx, PMG_ERR_ARG, "lanczos_steps must be in 1..64");
+      return umesh_lanczos(ctx->um, ctx->opt.lanczos_steps, ctx->opt.seed, ctx->opt.bound_safety,
+                           ctx->opt.bound_ratio, ctx->stream)
+                 ? fail(ctx, PMG_ERR_CUDA, "unstructured Lanczos intervals failed")
+                 : PMG_OK;
+    }
     if (source != PMG_BOUNDS_FIXED)
-      return fail(ctx, PMG_ERR_UNSUPPORTED, "unstructured meshes: fixed or user-given Chebyshev intervals");
+      return fail(ctx, PMG_ERR_UNSUPPORTED, "unstructured meshes: Lanczos, fixed or user-given Chebyshev intervals");
     const size_t np = (size_t)umesh_npatch(ctx->um);
     std::vector<double> v(2 * np);
     for (size_t j = 0; j < np; ++j) { v[2 * j] = ctx->opt.fixed_lo; v[2 * j + 1] = ctx->opt.fixed_hi; }
@@ -1278,7 +1291,21 @@ int pmg_get_ritz(pmg_ctx* ctx, int level, double* tm) {
   int st = check_level(ctx, level);
   if (st) return st;
   PMG_GUARD_CTX(ctx);
-  if (ctx->um) return fail(ctx, PMG_ERR_UNSUPPORTED, "not available on unstructured meshes");
+  if (ctx->um) {
+    const size_t np = (size_t)umesh_npatch(ctx->um);
+    std::vector<double> out(2 * np * ctx->npl, 0.0), tmp(2 * np);
+    CU(cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < ctx->npl; ++k) {
+      if (ctx->plevels[k] == 1 || np == 0) continue;
+      if (umesh_get_ritz(ctx->um, k, tmp.data())) return fail(ctx, PMG_ERR_CUDA, "copy failed");
+      for (size_t j = 0; j < np; ++j) {
+        out[(j * ctx->npl + k) * 2] = tmp[2 * j];
+        out[(j * ctx->npl + k) * 2 + 1] = tmp[2 * j + 1];
+      }
+    }
+    std::memcpy(tm, out.data(), out.size() * sizeof(double));
+    return PMG_OK;
+  }
   HLevel& h = ctx->L[level];
   std::vector<double> out(2 * h.npatch * ctx->npl, 0.0), tmp(2 * h.npatch);
   CU(cudaStreamSynchronize(ctx->stream));

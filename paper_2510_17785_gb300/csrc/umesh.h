@@ -45,6 +45,9 @@ int umesh_colours(const UMesh* m, uint8_t* out);
 int umesh_get_bounds(const UMesh* m, int k, double* out);             // [npatch][2]
 int umesh_set_bounds(UMesh* m, int k, const double* lohi);            // [npatch][2]
 int umesh_max_valence(const UMesh* m);
+// Lanczos intervals of every p-level q > 1 (FP64 operator; synchronises s)
+int umesh_lanczos(UMesh* m, int ksteps, uint64_t seed, double safety, double ratio, cudaStream_t s);
+int umesh_get_ritz(const UMesh* m, int k, double* out);              // [npatch][2] (theta_min, theta_max)
 
 // FP64 vectors of length umesh_ndofs (caller's device memory)
 int umesh_apply(UMesh* m, const double* u, double* Au, cudaStream_t s);

@@ -93,6 +93,7 @@ std::string utopo_build(int dim, int64_t nv, int64_t nc, const int64_t* cells, c
   for (auto& vc : t->vertex_cells) {
     std::sort(vc.begin(), vc.end());
     vc.erase(std::unique(vc.begin(), vc.end()), vc.end());
+    if (vc.empty()) return "a vertex belongs to no cell";
   }
   // boundary: facets of one cell
   t->edge_on_boundary.assign(t->edges.size(), 0);

@@ -358,3 +358,124 @@ def tetrahedra_to_hexes(points: np.ndarray, tets: np.ndarray):
                                       lambda: (points[x] + points[y] + points[z]) / 3.0)
             cells.append((a, m(a, b), m(a, c), f(a, b, c), m(a, d), f(a, b, d), f(a, c, d), g))
     return np.array(coords), np.array(cells, dtype=np.int64)
+
+
+def boundary_vertices(dim: int, nv: int, cells: np.ndarray) -> np.ndarray:
+    """Vertices on a facet (edge in 2D, face in 3D) that belongs to one cell only."""
+    count = {}
+    for cv in cells:
+        for a in range(dim):
+            for side in (0, 1):
+                f = tuple(sorted(int(cv[c]) for c in range(2 ** dim) if ((c >> a) & 1) == side))
+                count[f] = count.get(f, 0) + 1
+    out = np.zeros(nv, dtype=bool)
+    for f, k in count.items():
+        if k == 1:
+            out[list(f)] = True
+    return out
+
+
+def corner_dets(coords: np.ndarray, cells: np.ndarray) -> np.ndarray:
+    """[n_cells][2^d] determinant of the edge vectors at every corner, each edge
+    oriented along its reference axis (positive for a cell that is not inverted
+    at that corner)."""
+    dim = coords.shape[1]
+    X = coords[cells]                                   # [nc][2^d][d]
+    out = np.zeros(cells.shape)
+    for c in range(2 ** dim):
+        J = np.stack([(X[:, c ^ (1 << k)] - X[:, c]) * (1.0 if ((c >> k) & 1) == 0 else -1.0)
+                      for k in range(dim)], axis=-1)
+        out[:, c] = np.linalg.det(J)
+    return out
+
+
+def perturb_unstructured(coords: np.ndarray, cells: np.ndarray, frac: float, rng: np.random.Generator):
+    """Interior vertices moved by frac * h_v in a direction uniform on the
+    sphere, h_v the shortest edge at the vertex.  Vertices of a cell that
+    comes out with a non-positive corner determinant go back to their place,
+    repeated until every corner is positive."""
+    dim = coords.shape[1]
+    nv = len(coords)
+    bnd = boundary_vertices(dim, nv, cells)
+    h = np.full(nv, np.inf)
+    for c in range(2 ** dim):
+        for k in range(dim):
+            if (c >> k) & 1:
+                continue
+            a, b = cells[:, c], cells[:, c | (1 << k)]
+            L = np.linalg.norm(coords[a] - coords[b], axis=1)
+            np.minimum.at(h, a, L)
+            np.minimum.at(h, b, L)
+    g = rng.normal(size=(nv, dim))
+    g /= np.linalg.norm(g, axis=1, keepdims=True)
+    move = frac * h[:, None] * g
+    move[bnd] = 0.0
+    out = coords + move
+    for _ in range(64):
+        bad = (corner_dets(out, cells) <= 0).any(axis=1)
+        if not bad.any():
+            return out, bnd
+        vs = np.unique(cells[bad])
+        out[vs] = coords[vs]
+    raise ValueError("could not perturb the mesh without inverting a cell")
+
+
+def unstructured_mesh(kind: str, size: int, seed: int, perturb: float = 0.2):
+    """Seeded unstructured meshes of the unit square / cube.
+
+    kind "trisplit2d": a size x size triangulated square, each triangle split
+    into 3 quadrilaterals (interior valences 3 to 8); "extruded": that mesh
+    (size x size) extruded into size // 2 layers (hexahedra, valences 6 to
+    16); "tetsplit": a size^3 cube of tetrahedra (6 per cube), each split into
+    4 hexahedra (valences 4, 6, 8, 12 and 24).  Interior vertices are then
+    moved by ``perturb`` times their shortest edge in a random direction.
+    Returns (coords, cells, vertex_on_boundary)."""
+    rng = np.random.default_rng(seed)
+    if kind in ("trisplit2d", "extruded"):
+        P, T = triangulated_square(size, int(rng.integers(1 << 31)))
+        X, C = triangles_to_quads(P, T)
+        if kind == "extruded":
+            X, C = extrude(X, C, max(1, size // 2))
+    elif kind == "tetsplit":
+        P, T = cube_tetrahedra(size, int(rng.integers(1 << 31)))
+        X, C = tetrahedra_to_hexes(P, T)
+    else:
+        raise ValueError(kind)
+    X, bnd = perturb_unstructured(X, C, perturb, rng)
+    return X, C, bnd
+
+
+@dataclasses.dataclass(frozen=True)
+class UProblem:
+    """One problem of the batched unstructured workload."""
+    name: str
+    kind: str
+    size: int
+    p: int
+    seed: int
+
+
+C4_KINDS = (("extruded", 12), ("tetsplit", 6), ("trisplit2d", 30))
+
+
+def c4_problems(n: int = 64):
+    """The batched unstructured workload: n independent problems, degree
+    2, 4, 6, 8 in turn, the mesh kind changing every four problems (extruded
+    triangulations, split tetrahedralisations, 2D split triangulations, each
+    about 5,000 cells), kappa 10^U(-2, 2) per cell and a U[-1, 1] right-hand
+    side on the free DoFs from seed 1004 * 64 + i."""
+    out = []
+    for i in range(n):
+        kind, size = C4_KINDS[(i // 4) % len(C4_KINDS)]
+        out.append(UProblem(f"c4_{i}_{kind}_q{(2, 4, 6, 8)[i % 4]}", kind, size, (2, 4, 6, 8)[i % 4], 1004 * 64 + i))
+    return out
+
+
+def make_unstructured_problem(u: UProblem):
+    """(coords, cells, vertex_on_boundary, kappa) of one batched problem: the
+    mesh from the kind's own seed (shared by every problem of that kind), the
+    coefficient from the problem's seed."""
+    X, C, bnd = unstructured_mesh(u.kind, u.size, 4004 + [k for k, _ in C4_KINDS].index(u.kind))
+    rng = np.random.default_rng(u.seed)
+    kappa = 10.0 ** rng.uniform(-2.0, 2.0, len(C))
+    return X, C, bnd, kappa

@@ -146,6 +146,22 @@ def test_local_vcycle(dim, N, p, kind, ncyc):
     ctx.close()
 
 
+def test_local_vcycle_ids_out_of_range_give_zero_rows():
+    dim, N, p = 2, 5, 3
+    ctx, prob = gpu_ctx(wl(dim, N, p), **fixed())
+    npatch = (N - 1) ** dim
+    ni = (2 * p - 1) ** dim
+    ids = np.array([0, npatch, -1, npatch - 1, -(2 ** 40)], dtype=np.int64)
+    r = np.random.default_rng(5).uniform(-1, 1, (len(ids), ni))
+    d = torch.full((len(ids) * ni,), 7.0, dtype=torch.float64, device="cuda")
+    ctx.local_vcycle(0, torch.tensor(ids, device="cuda"), dev(r.reshape(-1)), d, 1)
+    torch.cuda.synchronize()
+    d = d.cpu().numpy().reshape(len(ids), ni)
+    assert np.all(d[[1, 2, 4]] == 0.0)
+    assert np.abs(d[0]).max() > 0 and np.abs(d[3]).max() > 0
+    ctx.close()
+
+
 @pytest.mark.parametrize("dim,N,p", [(2, 5, 4), (2, 3, 8), (3, 3, 4), (3, 2, 6)])
 def test_lanczos_bounds(dim, N, p):
     w = wl(dim, N, p)

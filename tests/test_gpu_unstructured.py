@@ -213,11 +213,12 @@ def test_two_level_vcycle_and_cg(name, p):
 
 @pytest.mark.parametrize("name,p", [("2d_trisplit", 6), ("3d_tetsplit", 3)])
 def test_mixed_precision(name, p):
-    """FP32 patch solves: a sweep within FP32 rounding of the FP64 one, CG
-    (FP64 outer iteration) within one iteration of the FP64 preconditioner."""
+    """FP32 patch solves (Lanczos intervals, computed with the FP64 operator
+    in both modes): a sweep within FP32 rounding of the FP64 one, CG (FP64
+    outer iteration) within one iteration of the FP64 preconditioner."""
     from paper_2510_17785_gb300 import pmg
-    c64, m = ctx_for(name, p)
-    c32, _ = ctx_for(name, p, precision=pmg.PREC_MIXED)
+    c64, m = ctx_for(name, p, bounds=pmg.BOUNDS_LANCZOS)
+    c32, _ = ctx_for(name, p, bounds=pmg.BOUNDS_LANCZOS, precision=pmg.PREC_MIXED)
     free = ~m.boundary_dofs(p)
     rng = np.random.default_rng(10)
     u0 = rng.uniform(-1, 1, m.n_dofs(p)) * free
@@ -283,4 +284,69 @@ def test_rejections():
         with pytest.raises(pmg.PMGError) as e:
             call()
         assert e.value.code == pmg.PMG_ERR_UNSUPPORTED
+    ctx.close()
+
+
+def test_local_vcycle_ids_out_of_range_give_zero_rows():
+    ctx, m = ctx_for("2d_trisplit", 3)
+    npatch = ctx.num_patches(0)[0]
+    ni = ctx.local_size(0)
+    ids = np.array([0, npatch, -1, npatch - 1], dtype=np.int64)
+    r = np.random.default_rng(5).uniform(-1, 1, (len(ids), ni))
+    d = torch.full((len(ids) * ni,), 7.0, dtype=torch.float64, device="cuda")
+    ctx.local_vcycle(0, torch.tensor(ids, device="cuda"), dev(r.reshape(-1)), d, 1)
+    torch.cuda.synchronize()
+    d = d.cpu().numpy().reshape(len(ids), ni)
+    assert np.all(d[1] == 0.0) and np.all(d[2] == 0.0)
+    assert np.abs(d[0]).max() > 0 and np.abs(d[3]).max() > 0
+    ctx.close()
+
+
+@pytest.mark.parametrize("name,p", [("2d_trisplit", 4), ("2d_trisplit", 8), ("3d_extruded", 3),
+                                    ("3d_tetsplit", 2), ("3d_tetsplit_small", 6)])
+def test_lanczos_intervals(name, p):
+    """PMG_BOUNDS_LANCZOS on unstructured patches: Ritz values and intervals
+    of every patch and p-level q > 1 against the oracle's Lanczos (start
+    vector counter from the patch's vertex id), and a sweep with those
+    intervals on both sides."""
+    from paper_2510_17785_gb300 import pmg
+    ctx, m = ctx_for(name, p, bounds=pmg.BOUNDS_LANCZOS, seed=3)
+    verts = m.interior_vertices()
+    levels = pt.levels_halving(p)
+    ritz, bd = ctx.get_ritz(0), ctx.get_bounds(0)
+    for j, v in enumerate(verts):
+        P = us.Patch(m, v, levels)
+        for k, q in enumerate(levels):
+            if q == 1:
+                continue
+            lv = P.lv[q]
+            lo, hi, tmin, tmax = lz.patch_bounds(lv.A, lv.diag, 3, v, q)
+            assert abs(ritz[j, k, 0] - tmin) <= 1e-9 * tmax and abs(ritz[j, k, 1] - tmax) <= 1e-9 * tmax, (v, q)
+            assert abs(bd[j, k, 0] - lo) <= 1e-9 * hi and abs(bd[j, k, 1] - hi) <= 1e-9 * hi, (v, q)
+    free = ~m.boundary_dofs(p)
+    rng = np.random.default_rng(12)
+    u0 = rng.uniform(-1, 1, m.n_dofs(p)) * free
+    b = rng.uniform(-1, 1, m.n_dofs(p)) * free
+    u = dev(u0)
+    ctx.patch_smooth(0, dev(b), u, 1, False)
+    torch.cuda.synchronize()
+    S = us.PatchSmoother(m, p, bounds_fn=lz.lanczos_bounds_fn(seed=3))
+    assert relerr(u.cpu().numpy(), S.sweep(u0, b)) < 1e-10
+    ctx.close()
+
+
+def test_lanczos_two_level_cg_high_degree():
+    """2D degree 8: with Lanczos intervals the two-level CG converges and
+    matches the oracle's iteration count within one."""
+    from paper_2510_17785_gb300 import pmg
+    p = 8
+    ctx, m = ctx_for("2d_trisplit", p, bounds=pmg.BOUNDS_LANCZOS)
+    S = us.PatchSmoother(m, p, bounds_fn=lz.lanczos_bounds_fn(seed=0))
+    TL = us.TwoLevel(m, p, S)
+    b = np.random.default_rng(9).uniform(-1, 1, m.n_dofs(p)) * ~m.boundary_dofs(p)
+    _, it_ref, _ = gmg.pcg(TL.A, b, TL.vcycle, 1e-8, 100)
+    x = torch.zeros(len(b), dtype=torch.float64, device="cuda")
+    it, rel, _ = ctx.solve_cg(dev(b), x, 1e-8, 100)
+    assert rel <= 1e-8 and it_ref < 100
+    assert abs(it - it_ref) <= 1, (it, it_ref)
     ctx.close()
