@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison arm")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-interval arm")
+    ap.add_argument("--batch-structured", action="store_true",
+                    help="--batch: structured 8^3 cubes instead of the unstructured meshes")
     ap.add_argument("--batch", type=int, default=0,
                     help="instead: K independent problems (3D, 8^3 cells, degrees 2/4/6/8) solved together")
     ap.add_argument("--no-c3", action="store_true", help="skip the 48^3 Q7 sub-record (workloads.c3)")
@@ -437,25 +439,54 @@ def c3_record(local, dev, flush, stream, fma32):
 
 
 def run_batch(args):
-    """K independent problems (unit cube, 8^3 cells, degrees 2, 4, 6, 8 in
-    turn, log-uniform coefficients) solved together by pmg_batch_solve_cg,
-    against the same problems solved one after another."""
+    """K independent problems solved together by pmg_batch_solve_cg, against
+    the same problems solved one after another.  Default: the unstructured
+    batch (inputs.c4_problems: extruded and split-tetrahedron hexahedral
+    meshes and split-triangle quadrilateral meshes of about 5,000 cells,
+    degrees 2, 4, 6, 8 in turn, kappa 10^U(-2, 2), Lanczos intervals, the
+    two-level preconditioner with the Q1 coarse space).  --batch-structured:
+    unit cubes of 8^3 cells with the same degrees and coefficients."""
+    import numpy as np
     import torch
     from paper_2510_17785_gb300 import inputs, pmg
 
-    K, N = args.batch, 8
-    ctxs, bs, n_free = [], [], 0
+    K = args.batch
+    ctxs, bs, n_free, desc, kinds = [], [], 0, [], {}
     t0 = time.perf_counter()
-    for k in range(K):
-        p = (2, 4, 6, 8)[k % 4]
-        wk = inputs.Workload(f"batch{k}", 3, N, p, 0.2, "sphere", ("loguniform", -2.0, 2.0), "uniform", 4004 * 64 + k)
-        pr = inputs.make_problem(wk)
-        c = pmg.Context(0, precision=pmg.PREC_MIXED, autotune=2)   # shapes for a shared GPU
-        c.mesh_structured(3, N, p, 3, pr.coords, pr.kappa)
-        c.setup()
-        ctxs.append(c)
-        bs.append(torch.tensor(pr.rhs, device="cuda"))
-        n_free += wk.n_free
+    if args.batch_structured:
+        N = 8
+        for k in range(K):
+            p = (2, 4, 6, 8)[k % 4]
+            wk = inputs.Workload(f"batch{k}", 3, N, p, 0.2, "sphere", ("loguniform", -2.0, 2.0), "uniform",
+                                 4004 * 64 + k)
+            pr = inputs.make_problem(wk)
+            c = pmg.Context(0, precision=pmg.PREC_MIXED, autotune=2)   # shapes for a shared GPU
+            c.mesh_structured(3, N, p, 3, pr.coords, pr.kappa)
+            c.setup()
+            ctxs.append(c)
+            bs.append(torch.tensor(pr.rhs, device="cuda"))
+            n_free += wk.n_free
+        workload = f"{K} problems, unit cube 8^3 cells, degrees 2/4/6/8, kappa 10^U(-2,2)"
+    else:
+        meshes = {}
+        for u in inputs.c4_problems(K):
+            X, C, bnd, kappa = inputs.make_unstructured_problem(u)
+            c = pmg.Context(0, precision=pmg.PREC_MIXED, bounds=pmg.BOUNDS_LANCZOS)
+            c.mesh_upload(X.shape[1], X, C, u.p, vertex_on_boundary=bnd, kappa=kappa)
+            c.setup()
+            total, free = c.num_dofs(0)
+            rhs = np.random.default_rng(u.seed + 1).uniform(-1.0, 1.0, total)
+            ctxs.append(c)
+            bs.append(torch.tensor(rhs, device="cuda"))
+            n_free += free
+            kinds.setdefault(u.kind, {"cells": len(C), "problems": 0, "valences": None})
+            kinds[u.kind]["problems"] += 1
+            if kinds[u.kind]["valences"] is None:
+                pm = c.get_patch_map(0)
+                kinds[u.kind]["valences"] = sorted({int(v) for v in (pm[:, 1:] >= 0).sum(axis=1)})
+        workload = (f"{K} unstructured problems (extruded / split-tetrahedron hexahedral and split-triangle "
+                    f"quadrilateral meshes, ~5k cells each), degrees 2/4/6/8, kappa 10^U(-2,2), Lanczos intervals, "
+                    f"two-level preconditioner with the Q1 coarse space")
     t_setup = time.perf_counter() - t0
     us = [torch.zeros_like(b) for b in bs]
     stream = torch.cuda.current_stream()
@@ -479,7 +510,9 @@ def run_batch(args):
         batch()
     tb, ts, its = [], [], None
     for _ in range(args.steps):
+        l0 = sum(c.launch_count() for c in ctxs)
         t, (its, _, _) = timed(batch)
+        launches = sum(c.launch_count() for c in ctxs) - l0
         tb.append(t)
         t, its1 = timed(one_by_one)
         ts.append(t)
@@ -490,9 +523,9 @@ def run_batch(args):
         "value": n_free / (mb * 1e-3), "unit": "DoFs/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": mb, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 local/GMG + f64 CG", "data": "synthetic",
-        "config": {"workload": f"{K} problems, unit cube 8^3 cells, degrees 2/4/6/8, kappa 10^U(-2,2)",
-                   "n_free_total": n_free, "setup_s": t_setup},
+        "config": {"workload": workload, "n_free_total": n_free, "setup_s": t_setup, "meshes": kinds or None},
         "one_by_one_ms": msq, "speedup_vs_one_by_one": msq / mb, "cg_iterations": its,
+        "gpu_launches": launches,
     }))
     for c in ctxs:
         c.close()

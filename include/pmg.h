@@ -103,6 +103,20 @@ typedef struct pmg_options {
                             reversed sweep (post-smoothing) applies W to the
                             residual instead, so the V-cycle stays symmetric  */
   double additive_theta; /* theta of the additive sweep (default 1)          */
+  int persistent;        /* multiplicative sweeps of a mesh level as ONE
+                            cooperative launch over all its colours, CTAs
+                            meeting at a grid barrier between colours:
+                            1 (default): pmg_setup times it against the
+                            per-colour launches on every level with at most
+                            4096 patches and keeps the faster (not with
+                            autotune = 2, whose problems share the GPU);
+                            2: on every level; 0: never                     */
+  long long sync_budget; /* clock64 cycles a CTA waits at one grid barrier of
+                            a persistent sweep before it gives up: the sweep
+                            stops and the call that synchronises next
+                            (pmg_solve_cg, pmg_solve_cg_host, pmg_solve_gmres,
+                            pmg_batch_solve_cg, pmg_patch_smooth) returns
+                            PMG_ERR_TIMEOUT; 0 = 2^31                         */
 } pmg_options;
 enum { PMG_KAPPA_ARITHMETIC = 0, PMG_KAPPA_GEOMETRIC = 1, PMG_KAPPA_HARMONIC = 2 };
 
@@ -110,7 +124,7 @@ typedef struct pmg_ctx pmg_ctx;
 
 /* Fill `opt` with the defaults: Chebyshev degree 3, N_MG = 1, Lanczos bounds
  * with 16 steps, safety 1.1, ratio 10, omega 0.5, seed 0, FP64, autotune on,
- * MLP safety 1.2. */
+ * MLP safety 1.2, persistent sweeps where faster, wait budget 2^31 cycles. */
 void pmg_default_options(pmg_options* opt);
 
 /* Create a context on CUDA device `device`; `opt` may be NULL (defaults).
@@ -217,7 +231,10 @@ int pmg_apply(pmg_ctx* ctx, int level, const double* u_dev, double* Au_dev, void
  *   Scatter   u += Pi_j^T d_j                          (eq. scatter)
  * Patches of one colour share no cell, so they run concurrently and the
  * result equals the sequential sweep in colour-major order.  u_dev is
- * updated in place; n_sweeps sweeps are applied. */
+ * updated in place; n_sweeps sweeps are applied.  Asynchronous on `stream`,
+ * except on a level swept by the persistent launch (pmg_level_persistent):
+ * there the call waits for the stream and returns PMG_ERR_TIMEOUT if a grid
+ * barrier ran out of its budget. */
 int pmg_patch_smooth(pmg_ctx* ctx, int level, const double* b_dev, double* u_dev,
                      int n_sweeps, int reverse, void* stream);
 /* One colour of the sweep above (colour in 0..2^d-1). */
@@ -338,6 +355,10 @@ int pmg_tuning(const pmg_ctx* ctx, int* variant, int* threads, int* patches_per_
  * small launches of coarse levels the latency of one patch) and its timings
  * (ms_per_variant[PMG_NUM_VARIANTS], -1 where not timed).  Either output may be NULL. */
 int pmg_tuning_level(const pmg_ctx* ctx, int level, int* variant, float* ms_per_variant);
+/* Persistent sweeps of mesh level `level`: *on = 1 if its sweeps run as one
+ * cooperative launch; the set-up's timings of one full sweep with per-colour
+ * launches and with the persistent launch (ms; -1 if not timed). */
+int pmg_level_persistent(const pmg_ctx* ctx, int level, int* on, float* ms_per_colour, float* ms_persistent);
 
 /* ---- learned Chebyshev intervals ------------------------------------------
  * No counterpart in the paper (its smoother is damped Jacobi).  A small MLP

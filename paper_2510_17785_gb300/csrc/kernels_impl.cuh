@@ -89,6 +89,73 @@ int launch_patch_P(int mode, int variant, const PatchArgs<T>& a, cudaStream_t s)
   return ST_UNSUPPORTED;
 }
 
+// Launch shape of the persistent sweep: the one-patch-per-CTA shape with
+// geometry staged in shared memory where it exists (3D, FP32, degree >= 3),
+// else the default shape.
+template <int DIM, int P, typename T>
+constexpr int persist_variant() {
+  if constexpr (DIM == 3 && P >= 3 && sizeof(T) == 4) {
+    if constexpr (Config<DIM, P, T, 3>::exists) return 3;
+  }
+  return 0;
+}
+
+template <int DIM, int P, typename T>
+int launch_patch_persist_P(const PersistArgs<T>& pa, int* grid_out, cudaStream_t s) {
+  constexpr int V = persist_variant<DIM, P, T>();
+  using C = Config<DIM, P, T, V>;
+  if constexpr (!C::exists) {
+    return ST_UNSUPPORTED;
+  } else {
+    const int dev = current_device();
+    if (dev < 0) return ST_CUDA;
+    static int cap[64] = {};                     // co-resident CTAs of this kernel on the device
+    if (!cap[dev]) {
+      if (cudaFuncSetAttribute(k_patch_persist<DIM, P, T, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)C::smem) != cudaSuccess)
+        return ST_CUDA;
+      int per_sm = 0, nsm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_patch_persist<DIM, P, T, V>, C::NT, C::smem) !=
+              cudaSuccess ||
+          cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return ST_CUDA;
+      if (per_sm * nsm <= 0) return ST_UNSUPPORTED;
+      cap[dev] = per_sm * nsm;
+    }
+    int need = 1;
+    for (int c = 0; c < pa.n_colours; ++c) need = std::max(need, (pa.counts[c] + C::PPB - 1) / C::PPB);
+    const int grid = std::min(need, cap[dev]);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(C::NT);
+    cfg.dynamicSmemBytes = C::smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, k_patch_persist<DIM, P, T, V>, pa) != cudaSuccess) return ST_CUDA;
+    if (grid_out) *grid_out = grid;
+    return ST_OK;
+  }
+}
+
+template <int DIM, typename T>
+int launch_patch_persist(int P, const PersistArgs<T>& pa, int* grid_out, cudaStream_t s) {
+  switch (P) {
+    case 1: return launch_patch_persist_P<DIM, 1, T>(pa, grid_out, s);
+    case 2: return launch_patch_persist_P<DIM, 2, T>(pa, grid_out, s);
+    case 3: return launch_patch_persist_P<DIM, 3, T>(pa, grid_out, s);
+    case 4: return launch_patch_persist_P<DIM, 4, T>(pa, grid_out, s);
+    case 5: return launch_patch_persist_P<DIM, 5, T>(pa, grid_out, s);
+    case 6: return launch_patch_persist_P<DIM, 6, T>(pa, grid_out, s);
+    case 7: return launch_patch_persist_P<DIM, 7, T>(pa, grid_out, s);
+    case 8: return launch_patch_persist_P<DIM, 8, T>(pa, grid_out, s);
+    default: return ST_UNSUPPORTED;
+  }
+}
+
 template <int DIM, typename T>
 int launch_patch(int P, int mode, int variant, const PatchArgs<T>& a, cudaStream_t s) {
   switch (P) {
@@ -353,6 +420,7 @@ int launch_fma_chain(T* out, int grid, int block, int iters, cudaStream_t s) {
 #define PMG_INSTANTIATE_PATCH(DIM, T, P)                                                   \
   namespace pmg {                                                                          \
   template int launch_patch_P<DIM, P, T>(int, int, const PatchArgs<T>&, cudaStream_t);     \
+  template int launch_patch_persist_P<DIM, P, T>(const PersistArgs<T>&, int*, cudaStream_t); \
   }
 // One launch-shape variant of a degree in a translation unit of its own (the
 // heaviest degrees are split so that the build runs them in parallel), and
@@ -370,11 +438,13 @@ int launch_fma_chain(T* out, int grid, int block, int iters, cudaStream_t s) {
 #define PMG_EXTERN_PATCH(DIM, T, P)                                                        \
   namespace pmg {                                                                          \
   extern template int launch_patch_P<DIM, P, T>(int, int, const PatchArgs<T>&, cudaStream_t); \
+  extern template int launch_patch_persist_P<DIM, P, T>(const PersistArgs<T>&, int*, cudaStream_t); \
   }
 
 #define PMG_INSTANTIATE_DIM_T(DIM, T)                                                                       \
   namespace pmg {                                                                                           \
   template int launch_patch<DIM, T>(int, int, int, const PatchArgs<T>&, cudaStream_t);                      \
+  template int launch_patch_persist<DIM, T>(int, const PersistArgs<T>&, int*, cudaStream_t);               \
   template void patch_config<DIM, T>(int, int, size_t*, int*, int*);                                        \
   template int launch_lanczos<DIM, T>(int, const LanczosArgs<T>&, cudaStream_t);                            \
   template int launch_cell_apply<DIM, T>(int, const T*, T*, const T*, int, cudaStream_t);                   \

@@ -19,6 +19,10 @@ enum { ST_OK = 0, ST_ARG = 1, ST_CUDA = 2, ST_DEGENERATE = 3, ST_NOT_SPD = 5, ST
 // if the variant does not exist for this degree)
 template <int DIM, typename T>
 int launch_patch(int P, int mode, int variant, const PatchArgs<T>& a, cudaStream_t s);
+// one persistent cooperative launch sweeping every colour of a level
+// (pa.n_colours lists, grid barrier between colours); *grid_out = CTAs used
+template <int DIM, typename T>
+int launch_patch_persist(int P, const PersistArgs<T>& pa, int* grid_out, cudaStream_t s);
 // shared memory bytes per CTA, patches per CTA and threads per CTA of a
 // variant of the patch kernel (all 0 if it does not exist)
 template <int DIM, typename T>

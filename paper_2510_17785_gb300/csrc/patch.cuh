@@ -250,6 +250,9 @@ struct PatchKernel {
   int* cells;      // [PPB][CST]: global cell ids, patch id, active flag, vertex indices (v_x, v_y, v_z)
   static constexpr int CST = NCELL + 6;
   const PatchArgs<T>* a;
+  const int32_t* list;   // patch ids of the colour being swept (MODE_SWEEP)
+  int n_items;           // patches of this launch (or of the colour, persistent launches)
+  int blk;               // batch of PPB patches this CTA works on
 
   __device__ T* vec(int pp, int off) const { return sm + pp * PS + off; }
 
@@ -662,7 +665,7 @@ struct PatchKernel {
     const int N = a->N, Nv = N - 1;
     if (active) {
       if (MODE == MODE_SWEEP) {
-        pid = a->list[item];
+        pid = list[item];
       } else {
         const int64_t raw = a->ids64[item];
         int64_t np = 1;
@@ -798,8 +801,8 @@ struct PatchKernel {
   }
 
   __device__ void run() {
-    const int item0 = blockIdx.x * PPB;
-    TM::per_block([&](int pp) { setup_patch(pp, item0 + pp, item0 + pp < a->n_items); });
+    const int item0 = blk * PPB;
+    TM::per_block([&](int pp) { setup_patch(pp, item0 + pp, item0 + pp < n_items); });
     TM::sync();
     load_level<0>();
     constexpr int NI0 = L::ni(0);
@@ -856,7 +859,7 @@ struct PatchKernel {
     } else {
       TM::template loop<NI0>([&](int pp, int i) {
         const bool act = cells[pp * CST + NCELL + 1];
-        if (item0 + pp < a->n_items) a->d_out[(size_t)(item0 + pp) * NI0 + i] = act ? vec(pp, L::D_(0))[i] : T(0);
+        if (item0 + pp < n_items) a->d_out[(size_t)(item0 + pp) * NI0 + i] = act ? vec(pp, L::D_(0))[i] : T(0);
       });
     }
   }
@@ -871,7 +874,98 @@ __global__ void __launch_bounds__(Config<DIM, P, T, V>::NT, Config<DIM, P, T, V>
   k.sm = reinterpret_cast<T*>(smem_raw);
   k.cells = reinterpret_cast<int*>(smem_raw + sizeof(T) * (size_t)PK::PS * PK::PPB);
   k.a = &args;
+  k.list = args.list;
+  k.n_items = args.n_items;
+  k.blk = blockIdx.x;
   k.run();
+}
+
+// ------------------------------------------------------------------------
+// Persistent sweep of one mesh level: one co-resident (cooperative) launch
+// visits every colour in turn (Algorithm 1), the CTAs striding over the
+// colour's patch batches, with a grid-wide barrier between colours.  The
+// barrier is an arrival counter and a generation word in global memory; a
+// CTA waits for the generation to move with a bounded spin (clock64 budget).
+// When a wait runs out, the CTA sets the status word and returns, and every
+// other CTA returns at its next barrier or wait: no CTA waits without limit,
+// and the host reads the status (PMG_ERR_TIMEOUT).  The CTA that times out
+// leaves the counter behind; the host zeroes counter and status before it
+// reports the timeout.
+struct GridSync {
+  unsigned int* count;    // arrivals at the current barrier
+  unsigned int* gen;      // barrier generation
+  int* status;            // 0, or 1 after a wait ran out of budget
+  long long budget;       // clock64 cycles one CTA waits at one barrier
+};
+
+__device__ inline bool grid_sync(const GridSync& g) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (*(volatile int*)g.status != 0) {
+      ok = 0;
+    } else {
+      const unsigned int my = *(volatile unsigned int*)g.gen;   // before arriving
+      __threadfence();                                          // this CTA's writes before its arrival
+      if (atomicAdd(g.count, 1u) == gridDim.x - 1) {
+        atomicExch(g.count, 0u);
+        __threadfence();
+        atomicAdd(g.gen, 1u);
+      } else {
+        const long long t0 = clock64();
+        while (*(volatile unsigned int*)g.gen == my) {
+          if (*(volatile int*)g.status != 0) {
+            ok = 0;
+            break;
+          }
+          if (clock64() - t0 > g.budget) {
+            atomicExch(g.status, 1);
+            ok = 0;
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+      __threadfence();                                          // the others' writes before ours reads
+    }
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+template <typename T>
+struct PersistArgs {
+  PatchArgs<T> base;              // list and n_items unused
+  const int32_t* lists[8];        // patch ids of every colour
+  int counts[8];
+  int n_colours;
+  int reverse;                    // visit the colours in reverse order
+  GridSync sync;
+};
+
+template <int DIM, int P, typename T, int V>
+__global__ void __launch_bounds__(Config<DIM, P, T, V>::NT, Config<DIM, P, T, V>::MINB)
+    k_patch_persist(const __grid_constant__ PersistArgs<T> pa) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  using PK = PatchKernel<DIM, P, T, MODE_SWEEP, V>;
+  PK k;
+  k.sm = reinterpret_cast<T*>(smem_raw);
+  k.cells = reinterpret_cast<int*>(smem_raw + sizeof(T) * (size_t)PK::PS * PK::PPB);
+  k.a = &pa.base;
+  for (int i = 0; i < pa.n_colours; ++i) {
+    const int c = pa.reverse ? pa.n_colours - 1 - i : i;
+    k.list = pa.lists[c];
+    k.n_items = pa.counts[c];
+    const int nblk = (k.n_items + PK::PPB - 1) / PK::PPB;
+    for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+      k.blk = b;
+      k.run();
+      __syncthreads();                 // shared memory is reused by the next batch
+    }
+    if (i + 1 < pa.n_colours && !grid_sync(pa.sync)) return;
+  }
 }
 
 // ------------------------------------------------------------------------

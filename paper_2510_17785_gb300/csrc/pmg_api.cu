@@ -104,6 +104,10 @@ struct pmg_ctx {
   float variant_ms[NUM_VARIANTS] = {};   // set-up timings of the finest level (-1: not timed)
   int level_variant[16] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};  // per mesh level
   float level_ms[16][NUM_VARIANTS] = {};  // set-up timings per mesh level (-1: not timed)
+  bool level_persist[16] = {};           // sweeps of the level as one persistent launch
+  float persist_ms[16][2] = {};          // set-up: full sweep per-colour / persistent (-1: not timed)
+  bool any_persist = false;
+  unsigned int* d_sync = nullptr;        // grid barrier: count, generation, status
   float* mlp_params = nullptr;           // PMG_BOUNDS_MLP network and normalisation
   float* mlp_norm = nullptr;
   double* add64 = nullptr;               // additive sweeps: correction sums (finest-level size)
@@ -260,6 +264,50 @@ int sweep_colour(pmg_ctx* ctx, int level, int colour, const T* b, T* u, cudaStre
   return PMG_OK;
 }
 
+GridSync grid_sync_of(pmg_ctx* ctx) {
+  GridSync g;
+  g.count = ctx->d_sync;
+  g.gen = ctx->d_sync + 1;
+  g.status = reinterpret_cast<int*>(ctx->d_sync + 2);
+  g.budget = ctx->opt.sync_budget > 0 ? ctx->opt.sync_budget : (1LL << 31);
+  return g;
+}
+
+// every colour of the level in one cooperative launch (grid barrier between colours)
+template <typename T>
+int sweep_persist(pmg_ctx* ctx, int level, const T* b, T* u, bool reverse, cudaStream_t s) {
+  HLevel& h = ctx->L[level];
+  PersistArgs<T> pa;
+  std::memset(&pa, 0, sizeof(pa));
+  pa.base = patch_args<T>(ctx, level);
+  pa.base.u = u;
+  pa.base.b = b;
+  const int nc = 1 << ctx->dim;
+  for (int c = 0; c < nc; ++c) {
+    pa.lists[c] = h.colour_list[c];
+    pa.counts[c] = h.ncolour[c];
+  }
+  pa.n_colours = nc;
+  pa.reverse = reverse ? 1 : 0;
+  pa.sync = grid_sync_of(ctx);
+  int grid = 0;
+  LK(1, ctx->dim == 2 ? launch_patch_persist<2, T>(ctx->p, pa, &grid, s)
+                      : launch_patch_persist<3, T>(ctx->p, pa, &grid, s));
+  return PMG_OK;
+}
+
+// after a synchronisation: a persistent sweep whose barrier wait ran out
+int check_sync(pmg_ctx* ctx) {
+  if (!ctx->any_persist) return PMG_OK;
+  int st = 0;
+  CU(cudaMemcpy(&st, ctx->d_sync + 2, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st != 0) {
+    CU(cudaMemset(ctx->d_sync, 0, 3 * sizeof(unsigned int)));
+    return fail(ctx, PMG_ERR_TIMEOUT, "a grid barrier of a persistent sweep ran out of its wait budget");
+  }
+  return PMG_OK;
+}
+
 template <typename T>
 T* additive_buffer(pmg_ctx* ctx);
 template <>
@@ -292,6 +340,7 @@ int sweep(pmg_ctx* ctx, int level, const T* b, T* u, bool reverse, cudaStream_t 
                         : launch_additive_update<3, T>(u, corr, ctx->opt.additive_theta, w, ctx->p, h.N, s));
     return PMG_OK;
   }
+  if (level < 16 && ctx->level_persist[level]) return sweep_persist<T>(ctx, level, b, u, reverse, s);
   for (int i = 0; i < nc; ++i) {
     const int c = reverse ? nc - 1 - i : i;
     int st = sweep_colour<T>(ctx, level, c, b, u, s);
@@ -465,6 +514,44 @@ int autotune_T(pmg_ctx* ctx) {
     ctx->level_variant[l] = bestv;
     if (l == ctx->nlev - 1) ctx->variant = bestv;
   }
+  // persistent sweeps: one full sweep each way, the faster kept
+  for (int l = ctx->nlev - 1; l >= 0 && st == PMG_OK; --l) {
+    HLevel& h = ctx->L[l];
+    ctx->persist_ms[l][0] = ctx->persist_ms[l][1] = -1.f;
+    if (h.npatch == 0 || l >= 16 || ctx->opt.persistent == 0 || ctx->opt.additive) continue;
+    if (ctx->opt.persistent == 1 && (h.npatch > 4096 || ctx->opt.autotune == 2)) continue;
+    T* u = Xof<T>(h);
+    T* b = Bof<T>(h);
+    float ms[2] = {1e30f, 1e30f};
+    bool ok = true;
+    for (int mode = 0; mode < 2 && st == PMG_OK && ok; ++mode) {
+      ctx->level_persist[l] = mode == 1;
+      ctx->any_persist = ctx->any_persist || mode == 1;
+      int r = sweep<T>(ctx, l, b, u, false, s);                // warm-up
+      if (r != PMG_OK) {
+        if (mode == 1) {                                       // no co-resident grid: per-colour launches
+          cudaGetLastError();
+          ok = false;
+          break;
+        }
+        st = r;
+        break;
+      }
+      for (int rep = 0; rep < 3 && st == PMG_OK; ++rep) {
+        float t = 0.f;
+        if (cudaEventRecord(e0, s) != cudaSuccess) st = fail(ctx, PMG_ERR_CUDA, "autotune: event");
+        if (st == PMG_OK) st = sweep<T>(ctx, l, b, u, false, s);
+        if (st == PMG_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                             cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+          st = fail(ctx, PMG_ERR_CUDA, "autotune: event");
+        ms[mode] = std::min(ms[mode], t);
+      }
+    }
+    if (st == PMG_OK && ok) st = check_sync(ctx);
+    ctx->persist_ms[l][0] = ms[0];
+    ctx->persist_ms[l][1] = ok ? ms[1] : -1.f;
+    ctx->level_persist[l] = ok && (ctx->opt.persistent == 2 || ms[1] < ms[0]);
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return st;
@@ -474,7 +561,12 @@ int autotune(pmg_ctx* ctx) {
   for (int v = 0; v < NUM_VARIANTS; ++v) ctx->variant_ms[v] = -1.f;
   for (int l = 0; l < 16; ++l)
     for (int v = 0; v < NUM_VARIANTS; ++v) ctx->level_ms[l][v] = -1.f;
+  for (int l = 0; l < 16; ++l) ctx->persist_ms[l][0] = ctx->persist_ms[l][1] = -1.f;
   if (!ctx->opt.autotune) {
+    if (ctx->opt.persistent == 2 && !ctx->opt.additive) {
+      for (int l = 0; l < ctx->nlev && l < 16; ++l) ctx->level_persist[l] = ctx->L[l].npatch > 0;
+      ctx->any_persist = true;
+    }
     ctx->variant = ctx->opt.variant;
     size_t sm;
     int ppb, nt;
@@ -521,6 +613,8 @@ void pmg_default_options(pmg_options* o) {
   o->post_reverse = 1;
   o->additive = 0;
   o->additive_theta = 1.0;
+  o->persistent = 1;
+  o->sync_budget = 0;
 }
 
 int pmg_create(int device, const pmg_options* opt, pmg_ctx** out) {
@@ -535,7 +629,8 @@ int pmg_create(int device, const pmg_options* opt, pmg_ctx** out) {
       (o.smoother < 0 || o.smoother > 2) || (o.precision != 0 && o.precision != 1) || o.bounds < 0 ||
       (o.additive != 0 && o.additive != 1) || !(o.additive_theta > 0) ||
       o.bounds > 3 || !(o.bound_safety > 0) || !(o.mlp_safety > 0) || o.coarse_kappa < 0 || o.coarse_kappa > 2 || !(o.bound_ratio >= 1) || o.variant < 0 ||
-      o.variant >= NUM_VARIANTS || (o.additive != 0 && o.additive != 1) || !(o.additive_theta > 0)) {
+      o.variant >= NUM_VARIANTS || (o.additive != 0 && o.additive != 1) || !(o.additive_theta > 0) ||
+      o.persistent < 0 || o.persistent > 2 || o.sync_budget < 0) {
     delete ctx;
     return PMG_ERR_ARG;
   }
@@ -546,6 +641,8 @@ int pmg_create(int device, const pmg_options* opt, pmg_ctx** out) {
   }
   if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess || cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_sync, 3 * sizeof(unsigned int)) != cudaSuccess ||
+      cudaMemset(ctx->d_sync, 0, 3 * sizeof(unsigned int)) != cudaSuccess ||
       cudaMallocHost(&ctx->h_rr, sizeof(double)) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_caller, cudaEventDisableTiming) != cudaSuccess) {
     delete ctx;
@@ -565,6 +662,7 @@ int pmg_destroy(pmg_ctx* ctx) {
   if (ctx->lanczos_V) cudaFree(ctx->lanczos_V);
   if (ctx->gm_V) cudaFree(ctx->gm_V);
   if (ctx->d_err) cudaFree(ctx->d_err);
+  if (ctx->d_sync) cudaFree(ctx->d_sync);
   if (ctx->h_rr) cudaFreeHost(ctx->h_rr);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   if (ctx->ev_caller) cudaEventDestroy(ctx->ev_caller);
@@ -1198,6 +1296,8 @@ int pmg_patch_smooth(pmg_ctx* ctx, int level, const double* b, double* u, int n_
   if (ctx->um)
     return umesh_sweep(ctx->um, b, u, n_sweeps, reverse != 0, s) ? fail(ctx, PMG_ERR_CUDA, "sweep failed") : PMG_OK;
   HLevel& h = ctx->L[level];
+  // a persistent level's barrier status is read here, so the call waits for its stream
+  const bool wait = level < 16 && ctx->level_persist[level] && n_sweeps > 0;
   if (ctx->opt.precision == PMG_PREC_MIXED) {
     LK(1, launch_cast_d2f(b, ctx->s32a, h.nd, s));
     LK(1, launch_cast_d2f(u, ctx->s32b, h.nd, s));
@@ -1206,11 +1306,15 @@ int pmg_patch_smooth(pmg_ctx* ctx, int level, const double* b, double* u, int n_
       if (st) return st;
     }
     LK(1, launch_cast_f2d(ctx->s32b, u, h.nd, s));
-    return PMG_OK;
+  } else {
+    for (int i = 0; i < n_sweeps; ++i) {
+      st = sweep<double>(ctx, level, b, u, reverse != 0, s);
+      if (st) return st;
+    }
   }
-  for (int i = 0; i < n_sweeps; ++i) {
-    st = sweep<double>(ctx, level, b, u, reverse != 0, s);
-    if (st) return st;
+  if (wait) {
+    CU(cudaStreamSynchronize(s));
+    return check_sync(ctx);
   }
   return PMG_OK;
 }
@@ -1428,10 +1532,13 @@ static int cg_graph(pmg_ctx* ctx) {
   cudaStream_t s = ctx->stream;
   cudaGraph_t g = nullptr;
   const int64_t before = ctx->launches;
+  const int64_t ubefore = ctx->um ? umesh_kernel_launches(ctx->um) : 0;
   CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   int st = cg_body(ctx, s);
-  ctx->graph_launches_per_iter = ctx->launches - before;
-  ctx->launches = before;
+  // the capture launched nothing: what the body counted is one replay's launches
+  const int64_t ucount = ctx->um ? umesh_kernel_launches(ctx->um) - ubefore : 0;
+  ctx->graph_launches_per_iter = ctx->launches - before + ucount;
+  ctx->launches = before - ucount;
   cudaError_t ce = cudaStreamEndCapture(s, &g);
   if (st || ce != cudaSuccess) {           // no graph: iterations launch the body directly
     if (g) cudaGraphDestroy(g);
@@ -1486,6 +1593,7 @@ int pmg_solve_cg(pmg_ctx* ctx, const double* b, double* u, double rtol, int maxi
       st = cg_step(ctx);
       if (st) return st;
       CU(cudaStreamSynchronize(s));
+      if ((result = check_sync(ctx)) != PMG_OK) break;
       rel = std::sqrt(*ctx->h_rr) / r0;
       if (!std::isfinite(rel)) {
         result = fail(ctx, PMG_ERR_NUMERIC, "non-finite residual");
@@ -1556,7 +1664,11 @@ int pmg_batch_solve_cg(pmg_ctx* const* ctxs, int n_problems, const double* const
       pmg_ctx* ctx = ctxs[k];
       CU(cudaStreamSynchronize(ctx->stream));
       rel[k] = std::sqrt(*ctx->h_rr) / r0[k];
-      if (!std::isfinite(rel[k])) {
+      const int sy = check_sync(ctx);
+      if (sy != PMG_OK) {
+        res[k] = sy;
+        active[k] = 0;
+      } else if (!std::isfinite(rel[k])) {
         res[k] = fail(ctx, PMG_ERR_NUMERIC, "non-finite residual");
         active[k] = 0;
       } else if (rel[k] <= rtol) {
@@ -1570,7 +1682,7 @@ int pmg_batch_solve_cg(pmg_ctx* const* ctxs, int n_problems, const double* const
   for (int k = 0; k < K; ++k) {
     pmg_ctx* ctx = ctxs[k];
     if (res[k] == PMG_OK && rel[k] > rtol) res[k] = fail(ctx, PMG_ERR_NOT_CONVERGED, "maxit reached");
-    CU(cudaMemcpyAsync(u[k], ctx->cg_x, ctx->L.back().nd * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(u[k], ctx->cg_x, fine_n(ctx) * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
   }
   int result = PMG_OK;
   for (int k = 0; k < K; ++k) {
@@ -1719,7 +1831,8 @@ int pmg_solve_gmres(pmg_ctx* ctx, const double* b, double* u, double rtol, int m
   CU(cudaStreamSynchronize(s));
   if (iters) *iters = it;
   if (relres) *relres = rel;
-  return result;
+  const int sy = check_sync(ctx);
+  return sy != PMG_OK ? sy : result;
 }
 
 int pmg_solve_cg_host(pmg_ctx* ctx, const double* b_host, double* u_host, double rtol, int maxit, int* iters,
@@ -1828,6 +1941,15 @@ int pmg_tuning_level(const pmg_ctx* ctx, int level, int* variant, float* ms_per_
   if (variant) *variant = v;
   if (ms_per_variant)
     for (int k = 0; k < NUM_VARIANTS; ++k) ms_per_variant[k] = level < 16 ? ctx->level_ms[level][k] : -1.f;
+  return PMG_OK;
+}
+
+int pmg_level_persistent(const pmg_ctx* ctx, int level, int* on, float* ms_per_colour, float* ms_persistent) {
+  if (!ctx || !ctx->setup_ok || level < 0 || level >= ctx->nlev) return PMG_ERR_ARG;
+  const bool in = level < 16 && !ctx->um;
+  if (on) *on = in && ctx->level_persist[level] ? 1 : 0;
+  if (ms_per_colour) *ms_per_colour = in ? ctx->persist_ms[level][0] : -1.f;
+  if (ms_persistent) *ms_persistent = in ? ctx->persist_ms[level][1] : -1.f;
   return PMG_OK;
 }
 

@@ -38,6 +38,8 @@ class Workload:
     law: str               # "uniform": each component U(-perturb*h, perturb*h);
                            # "sphere": length perturb*h, direction uniform on S^{d-1};
                            # "kershaw": Kershaw-type mesh with parameter eps = perturb
+                           # (three blended segments); "kershaw6": the six-layer
+                           # Kershaw mesh, eps = perturb
     kappa: tuple           # ("const", value) or ("loguniform", log10_lo, log10_hi)
     rhs: str               # "uniform" (U[-1,1] on free DoFs) or "manufactured"
     seed: int
@@ -178,6 +180,31 @@ def kershaw_vertices(dim: int, N: int, eps: float = 0.3) -> np.ndarray:
     return out
 
 
+def kershaw6_vertices(dim: int, N: int, eps: float = 0.3) -> np.ndarray:
+    """Vertices of the six-layer Kershaw mesh of the unit square/cube (the
+    construction of the high-order benchmark literature, e.g. Fischer et al.,
+    "Scalability of high-performance PDE solvers", 2020): x is kept and cut
+    into six layers of width 1/6; y (and z, in the same phase) is mapped by
+    the left-fine profile l(t) = 1 - s(1 - t) on layer 0 and the right-fine
+    profile r(t) = s(t) on layer 5 (s = kershaw_squeeze), by a blend linear in
+    x from l to r across layer 1 and across layer 4, and from r back to l
+    across layers 2 and 3 together.  N must be a multiple of 6 (layer
+    boundaries on mesh lines)."""
+    if N % 6 != 0:
+        raise ValueError("the six-layer Kershaw mesh needs N divisible by 6")
+    x = grid_vertices(dim, N)
+    s = lambda t: kershaw_squeeze(t, eps)
+    left = lambda t: 1.0 - s(1.0 - t)
+    layer = np.minimum((x[:, 0] * 6.0 + 1e-12).astype(int), 5)
+    t = x[:, 0] * 6.0 - layer                                  # position inside the layer
+    lam = np.select([layer == 0, layer == 1, layer == 2, layer == 3, layer == 4],
+                    [np.zeros_like(t), t, 1.0 - 0.5 * t, 0.5 - 0.5 * t, t], default=np.ones_like(t))
+    out = x.copy()
+    for k in range(1, dim):
+        out[:, k] = (1.0 - lam) * left(x[:, k]) + lam * s(x[:, k])
+    return out
+
+
 def kappa_cells(rng: np.random.Generator, dim: int, N: int, spec: tuple) -> np.ndarray:
     nc = N ** dim
     if spec[0] == "const":
@@ -212,6 +239,8 @@ def make_problem(w: Workload) -> Problem:
     x = grid_vertices(w.dim, w.N)
     if w.law == "kershaw":
         x = kershaw_vertices(w.dim, w.N, w.perturb)       # perturb holds the Kershaw parameter eps
+    elif w.law == "kershaw6":
+        x = kershaw6_vertices(w.dim, w.N, w.perturb)
     elif w.perturb > 0.0:
         x = valid_perturbation(rng, w.dim, w.N, w.perturb, w.law, w.seed)
     kap = kappa_cells(rng, w.dim, w.N, w.kappa)
