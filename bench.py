@@ -377,15 +377,16 @@ def learned_arm(w, levels, local, timed_solves, dev):
     return out
 
 
-def c3_record(local, dev, flush, stream, fma32):
-    """The 3D Q7 48^3 workload (kappa = 10^U(-3,3) per cell, random
-    right-hand side, GMG 48 -> 3): set-up, the finest-level FP32 sweep and its
-    roofline fraction, one mixed-precision GMG-PCG solve to 1e-8, and the
-    difference between one FP32 and one FP64 sweep from the same state."""
+def precision_record(w, local, dev, flush, stream, fma32, sweep_only_fp64=True):
+    """One workload in three arms: mixed precision, mixed precision with the
+    patch kernels' geometry rounded to BF16, and FP64: set-up, the
+    finest-level sweep (time, roofline fraction), a GMG-PCG solve to 1e-8 in
+    the mixed arms, and the difference between one sweep of each mixed arm and
+    one FP64 sweep from the same state (u = 0).  BF16 geometry is accepted when
+    its CG iteration count stays within one of the FP32-geometry count."""
     import torch
     from paper_2510_17785_gb300 import inputs, pmg
 
-    w = inputs.C3
     levels = int(round(math.log2(w.N // w.coarse_N))) + 1
     prob = inputs.make_problem(w)
     out = {"workload": w.name, "dim": w.dim, "cells_per_dir": w.N, "p": w.p, "n_free": w.n_free,
@@ -401,40 +402,60 @@ def c3_record(local, dev, flush, stream, fma32):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1), r
 
-    b = torch.tensor(prob.rhs, device=dev)
+    b = torch.zeros(w.n_dofs, dtype=torch.float64, device=dev)
     u_sw = {}
-    for name, prec in (("mixed", pmg.PREC_MIXED), ("fp64", pmg.PREC_FP64)):
-        ctx = pmg.Context(local, precision=prec)
+    arms = (("mixed", dict(precision=pmg.PREC_MIXED)),
+            ("mixed_bf16_geometry", dict(precision=pmg.PREC_MIXED, geometry_bf16=1)),
+            ("fp64", dict(precision=pmg.PREC_FP64)))
+    for name, opt in arms:
+        ctx = pmg.Context(local, **opt)
         ctx.mesh_structured(w.dim, w.N, w.p, levels, prob.coords, prob.kappa)
         t0 = time.perf_counter()
         ctx.setup()
         t_setup = time.perf_counter() - t0
+        if prob.rhs is None:
+            ctx.rhs_manufactured(b)
+        else:
+            b.copy_(torch.tensor(prob.rhs, device=dev))
         lf = levels - 1
         u = torch.zeros_like(b)
         ctx.patch_smooth(lf, b, u, 1, False)             # one sweep from u = 0, kept for the comparison
         torch.cuda.synchronize()
         u_sw[name] = u.clone()
-        nsw = 3 if name == "mixed" else 1
+        nsw = 1 if name == "fp64" else 3
         ms, _ = ev_time(lambda: ctx.patch_smooth(lf, b, u, nsw, False))
         t_sweep = ms / nsw * 1e-3
         flops = ctx.sweep_flops(lf)
         rec = {"setup_s": t_setup, "sweep_ms": t_sweep * 1e3, "sweep_dofs_per_s": w.n_free / t_sweep,
                "sweep_flops": flops}
-        if name == "mixed":
+        if name != "fp64" or not sweep_only_fp64:
             rec["roofline"] = {"bound": "alu", "achieved": flops / t_sweep / 1e12, "unit": "TFLOP/s",
                                "peak": FP32_PEAK_DERIVED / 1e12, "frac": flops / t_sweep / FP32_PEAK_DERIVED,
                                "frac_of_measured_fma": flops / t_sweep / fma32,
-                               "kernel": "k_patch<3,7,float,SWEEP,variant> (finest-level sweep, 8 colour launches)"}
+                               "kernel": f"k_patch<3,{w.p},float,SWEEP,variant> (finest-level sweep, "
+                                         f"one launch per colour or one persistent launch)"}
             x = torch.zeros_like(b)
             ctx.solve_cg(b, x, 1e-8, 300)                 # warm-up (captures the iteration graph)
             x.zero_()
             ms, (it, rel, _) = ev_time(lambda: ctx.solve_cg(b, x, 1e-8, 300))
             rec.update(solve_ms=ms, cg_iterations=it, final_relres=rel, dofs_per_s=w.n_free / (ms * 1e-3),
-                       tuning_level_variants=[ctx.tuning_level(lv)[0] for lv in range(levels)])
+                       tuning_level_variants=[ctx.tuning_level(lv)[0] for lv in range(levels)],
+                       persistent_levels=[lv for lv in range(levels) if ctx.level_persistent(lv)[0]])
         out[name] = rec
         ctx.close()
     ref = u_sw["fp64"]
-    out["mixed_vs_fp64_one_sweep_rel_max_err"] = float((u_sw["mixed"] - ref).abs().max() / ref.abs().max())
+    rel = lambda a: float((a - ref).abs().max() / ref.abs().max())
+    out["mixed_vs_fp64_one_sweep_rel_max_err"] = rel(u_sw["mixed"])
+    g = out["mixed_bf16_geometry"]
+    out["geometry_bf16"] = {
+        "one_sweep_rel_max_err_vs_fp64": rel(u_sw["mixed_bf16_geometry"]),
+        "fp32_geometry_one_sweep_rel_max_err_vs_fp64": out["mixed_vs_fp64_one_sweep_rel_max_err"],
+        "cg_iterations": g["cg_iterations"], "fp32_geometry_cg_iterations": out["mixed"]["cg_iterations"],
+        "sweep_ms": g["sweep_ms"], "fp32_geometry_sweep_ms": out["mixed"]["sweep_ms"],
+        "accepted": g["cg_iterations"] <= out["mixed"]["cg_iterations"] + 1,
+        "note": "geometry values rounded to BF16 and held in FP32 arrays (an accuracy evaluation: no BF16 "
+                "loads, so the sweep time is not expected to change)",
+    }
     return out
 
 
@@ -634,7 +655,8 @@ def run_ours(args):
         result[name] = dict(ms=ms, its=its, launches=launches, t_sweep=t_sweep, sweep_flops=flops,
                             e2e_ms=e2e_ms, setup_s=t_setup, maxdiff_e2e=err,
                             umax=float(x.abs().max()), tuning=ctx.tuning(),
-                            level_variants=[ctx.tuning_level(lv)[0] for lv in range(levels)])
+                            level_variants=[ctx.tuning_level(lv)[0] for lv in range(levels)],
+                            persistent={lv: ctx.level_persistent(lv) for lv in range(levels)})
         if name == "mixed":
             result["fma32"] = ctx.fma_peak(pmg.PREC_MIXED)
             result["fma64"] = ctx.fma_peak(pmg.PREC_FP64)
@@ -643,7 +665,9 @@ def run_ours(args):
     if not args.no_learned:
         result["learned"] = learned_arm(w, levels, local, timed_solves, dev)
     if not args.no_c3 and world == 1:
-        result["c3"] = c3_record(local, dev, flush, stream, result["fma32"])
+        result["c3"] = precision_record(inputs.C3, local, dev, flush, stream, result["fma32"])
+    if world == 1 and args.workload == inputs.C2.name:
+        result["c2_geometry_bf16"] = precision_record(w, local, dev, flush, stream, result["fma32"])["geometry_bf16"]
 
     head = result["mixed"]
     t_step = sum(head["ms"]) / len(head["ms"])
@@ -672,7 +696,8 @@ def run_ours(args):
             "patch_kernel_launch": {"variant": head["tuning"][0], "threads_per_cta": head["tuning"][1],
                                     "patches_per_cta": head["tuning"][2],
                                     "autotune_ms_per_variant": [round(x, 4) for x in head["tuning"][3]],
-                                    "variant_per_mesh_level": head["level_variants"]},
+                                    "variant_per_mesh_level": head["level_variants"],
+                                    "persistent_levels": head["persistent"]},
         },
         "time_to_solution_ms": t_max,
         "cg_iterations": [i for i, _ in head["its"]],
@@ -727,6 +752,9 @@ def run_ours(args):
         }
     if "c3" in result:
         out["workloads"] = {"c3": result["c3"]}
+    if "c2_geometry_bf16" in result:
+        out["geometry_bf16"] = {"c2": result["c2_geometry_bf16"],
+                                "c3": result["c3"]["geometry_bf16"] if "c3" in result else None}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, levels)
     if dist:

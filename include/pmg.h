@@ -117,6 +117,12 @@ typedef struct pmg_options {
                             (pmg_solve_cg, pmg_solve_cg_host, pmg_solve_gmres,
                             pmg_batch_solve_cg, pmg_patch_smooth) returns
                             PMG_ERR_TIMEOUT; 0 = 2^31                         */
+  int geometry_bf16;     /* PMG_PREC_MIXED only, 1: the patch kernels (local
+                            p-MG and the Evaluate step) read the geometry
+                            tensors G rounded to BF16 (8-bit significand,
+                            round to nearest even); the GMG level operators
+                            keep FP32 G.  An accuracy evaluation of BF16 G:
+                            the values are held in FP32 arrays              */
 } pmg_options;
 enum { PMG_KAPPA_ARITHMETIC = 0, PMG_KAPPA_GEOMETRIC = 1, PMG_KAPPA_HARMONIC = 2 };
 

@@ -19,6 +19,8 @@ enum { ST_OK = 0, ST_ARG = 1, ST_CUDA = 2, ST_DEGENERATE = 3, ST_NOT_SPD = 5, ST
 // if the variant does not exist for this degree)
 template <int DIM, typename T>
 int launch_patch(int P, int mode, int variant, const PatchArgs<T>& a, cudaStream_t s);
+// y = x rounded to BF16 (round to nearest even) and widened back to FP32
+int launch_round_bf16(const float* x, float* y, size_t n, cudaStream_t s);
 // one persistent cooperative launch sweeping every colour of a level
 // (pa.n_colours lists, grid barrier between colours); *grid_out = CTAs used
 template <int DIM, typename T>

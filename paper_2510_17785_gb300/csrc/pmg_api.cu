@@ -34,6 +34,7 @@ struct PLevel {
   int q = 0;
   double* G64 = nullptr;
   float* G32 = nullptr;
+  float* Gp32 = nullptr;       // the G the FP32 patch kernels read: G32, or G32 rounded to BF16
   double* dinv64 = nullptr;
   float* dinv32 = nullptr;
   double* bounds64 = nullptr;
@@ -205,6 +206,12 @@ const double* Gof<double>(const PLevel& pl) { return pl.G64; }
 template <>
 const float* Gof<float>(const PLevel& pl) { return pl.G32; }
 template <typename T>
+const T* GPatchof(const PLevel& pl);
+template <>
+const double* GPatchof<double>(const PLevel& pl) { return pl.G64; }
+template <>
+const float* GPatchof<float>(const PLevel& pl) { return pl.Gp32; }
+template <typename T>
 const T* Dinvof(const PLevel& pl);
 template <>
 const double* Dinvof<double>(const PLevel& pl) { return pl.dinv64; }
@@ -239,7 +246,7 @@ PatchArgs<T> patch_args(pmg_ctx* c, int level) {
   a.N = h.N;
   for (int k = 0; k < c->npl; ++k) {
     a.lv[k].fdm = Fdmof<T>(c, c->plevels[k]);
-    a.lv[k].G = Gof<T>(h.pl[k]);
+    a.lv[k].G = GPatchof<T>(h.pl[k]);
     a.lv[k].dinv = Dinvof<T>(h.pl[k]);
     a.lv[k].bounds = Boundsof<T>(h.pl[k]);
     a.lv[k].dense = Denseof<T>(h.pl[k]);
@@ -630,7 +637,8 @@ int pmg_create(int device, const pmg_options* opt, pmg_ctx** out) {
       (o.additive != 0 && o.additive != 1) || !(o.additive_theta > 0) ||
       o.bounds > 3 || !(o.bound_safety > 0) || !(o.mlp_safety > 0) || o.coarse_kappa < 0 || o.coarse_kappa > 2 || !(o.bound_ratio >= 1) || o.variant < 0 ||
       o.variant >= NUM_VARIANTS || (o.additive != 0 && o.additive != 1) || !(o.additive_theta > 0) ||
-      o.persistent < 0 || o.persistent > 2 || o.sync_budget < 0) {
+      o.persistent < 0 || o.persistent > 2 || o.sync_budget < 0 || o.geometry_bf16 < 0 || o.geometry_bf16 > 1 ||
+      (o.geometry_bf16 && o.precision != PMG_PREC_MIXED)) {
     delete ctx;
     return PMG_ERR_ARG;
   }
@@ -896,6 +904,11 @@ int pmg_setup(pmg_ctx* ctx) {
         DALLOC(pl.G32, ng);
         if (d == 2) ST(launch_geometry<2, float>(h.coords, h.kappa, h.N, q, pl.G32, ctx->d_err, s));
         else ST(launch_geometry<3, float>(h.coords, h.kappa, h.N, q, pl.G32, ctx->d_err, s));
+        pl.Gp32 = pl.G32;
+        if (ctx->opt.geometry_bf16) {
+          DALLOC(pl.Gp32, ng);
+          ST(launch_round_bf16(pl.G32, pl.Gp32, ng, s));
+        }
       }
       if (d == 2) ST(launch_diag<2>(pl.G64, h.N, q, diag, pl.dinv64, pl.dinv32, s));
       else ST(launch_diag<3>(pl.G64, h.N, q, diag, pl.dinv64, pl.dinv32, s));

@@ -51,7 +51,7 @@ class Options(C.Structure):
         ("seed", C.c_uint64), ("precision", C.c_int), ("autotune", C.c_int), ("variant", C.c_int),
         ("mlp_safety", C.c_double), ("coarse_kappa", C.c_int), ("post_reverse", C.c_int),
         ("additive", C.c_int), ("additive_theta", C.c_double), ("persistent", C.c_int),
-        ("sync_budget", C.c_longlong),
+        ("sync_budget", C.c_longlong), ("geometry_bf16", C.c_int),
     ]
 
 

@@ -236,6 +236,8 @@ def test_paper_hp_comparison_iteration_counts(key, cases):
         assert rel <= 1e-8
         got.append((L, it, paper))
     print(dim, p, mesh, got)
+    if not got:
+        pytest.skip("every case of this row is outside the dense coarse solver's range")
     if mesh == "kershaw":
         if any(abs(it - paper) > 5 for _, it, paper in got) or got[-1][1] > got[0][1] + 2:
             pytest.xfail(f"Kershaw mesh (L, ours, paper): {got}")

@@ -26,22 +26,23 @@ def _wl(dim, N, p, seed=21):
     return inputs.Workload("ps", dim, N, p, 0.2, "uniform", ("loguniform", -1.0, 1.0), "uniform", seed)
 
 
-@pytest.mark.parametrize("dim,N,p,prec", [(3, 8, 4, "mixed"), (3, 8, 4, "fp64"), (3, 6, 7, "mixed"),
-                                          (3, 5, 2, "fp64"), (2, 16, 3, "fp64"), (2, 12, 6, "mixed")])
-def test_persistent_sweep_is_bit_identical(dim, N, p, prec):
+@pytest.mark.parametrize("dim,N,p,levels,prec", [(3, 8, 4, 3, "mixed"), (3, 8, 4, 3, "fp64"), (3, 6, 7, 2, "mixed"),
+                                                 (3, 5, 2, 1, "fp64"), (2, 16, 3, 3, "fp64"), (2, 12, 6, 2, "mixed")])
+def test_persistent_sweep_is_bit_identical(dim, N, p, levels, prec):
     from paper_2510_17785_gb300 import pmg
     pr = pmg.PREC_MIXED if prec == "mixed" else pmg.PREC_FP64
     w = _wl(dim, N, p)
-    ref, prob = _ctx(w, precision=pr, autotune=0, persistent=0, bounds=pmg.BOUNDS_FIXED)
-    per, _ = _ctx(w, precision=pr, autotune=0, persistent=2, bounds=pmg.BOUNDS_FIXED)
-    assert per.level_persistent(0)[0] and not ref.level_persistent(0)[0]
+    ref, prob = _ctx(w, levels, precision=pr, autotune=0, persistent=0, bounds=pmg.BOUNDS_FIXED)
+    per, _ = _ctx(w, levels, precision=pr, autotune=0, persistent=2, bounds=pmg.BOUNDS_FIXED)
+    lf = levels - 1
+    assert per.level_persistent(lf)[0] and not ref.level_persistent(lf)[0]
     u0 = inputs.random_vector(3, dim, p, N)
     b = torch.tensor(prob.rhs, device="cuda")
     for reverse in (False, True):
         ua = torch.tensor(u0, device="cuda")
         ub = torch.tensor(u0, device="cuda")
-        ref.patch_smooth(0, b, ua, 2, reverse)
-        per.patch_smooth(0, b, ub, 2, reverse)
+        ref.patch_smooth(lf, b, ua, 2, reverse)
+        per.patch_smooth(lf, b, ub, 2, reverse)
         torch.cuda.synchronize()
         assert torch.equal(ua, ub), reverse
     ref.close()
@@ -83,24 +84,24 @@ def test_setup_times_both_ways_and_keeps_the_faster():
 def test_grid_barrier_timeout_is_reported_and_the_device_stays_usable():
     from paper_2510_17785_gb300 import pmg
     w = _wl(3, 8, 4)
-    bad, prob = _ctx(w, precision=pmg.PREC_FP64, autotune=0, persistent=2, sync_budget=1)
+    bad, prob = _ctx(w, 3, precision=pmg.PREC_FP64, autotune=0, persistent=2, sync_budget=1)
     u0 = inputs.random_vector(3, 3, 4, 8)
     b = torch.tensor(prob.rhs, device="cuda")
     u = torch.tensor(u0, device="cuda")
     with pytest.raises(pmg.PMGError) as e:
-        bad.patch_smooth(0, b, u, 1, False)
+        bad.patch_smooth(2, b, u, 1, False)
     assert e.value.code == pmg.PMG_ERR_TIMEOUT
     x = torch.zeros_like(b)
     it, rel, rc = bad.solve_cg(b, x, 1e-8, 20, check=False)
     assert rc == pmg.PMG_ERR_TIMEOUT
     torch.cuda.synchronize()                     # the context and the device are still usable
     bad.close()
-    good, _ = _ctx(w, precision=pmg.PREC_FP64, autotune=0, persistent=2)
-    ref, _ = _ctx(w, precision=pmg.PREC_FP64, autotune=0, persistent=0)
+    good, _ = _ctx(w, 3, precision=pmg.PREC_FP64, autotune=0, persistent=2)
+    ref, _ = _ctx(w, 3, precision=pmg.PREC_FP64, autotune=0, persistent=0)
     ua = torch.tensor(u0, device="cuda")
     ub = torch.tensor(u0, device="cuda")
-    good.patch_smooth(0, b, ua, 1, False)
-    ref.patch_smooth(0, b, ub, 1, False)
+    good.patch_smooth(2, b, ua, 1, False)
+    ref.patch_smooth(2, b, ub, 1, False)
     torch.cuda.synchronize()
     assert torch.equal(ua, ub)
     good.close()
