@@ -577,8 +577,14 @@ int autotune(pmg_ctx* ctx) {
     ctx->variant = ctx->opt.variant;
     size_t sm;
     int ppb, nt;
-    if (ctx->dim == 2) patch_config<2, double>(ctx->p, ctx->variant, &sm, &ppb, &nt);
-    else patch_config<3, double>(ctx->p, ctx->variant, &sm, &ppb, &nt);
+    const bool mixed = ctx->opt.precision == PMG_PREC_MIXED;     // the sweeps' precision decides
+    if (ctx->dim == 2) {
+      if (mixed) patch_config<2, float>(ctx->p, ctx->variant, &sm, &ppb, &nt);
+      else patch_config<2, double>(ctx->p, ctx->variant, &sm, &ppb, &nt);
+    } else {
+      if (mixed) patch_config<3, float>(ctx->p, ctx->variant, &sm, &ppb, &nt);
+      else patch_config<3, double>(ctx->p, ctx->variant, &sm, &ppb, &nt);
+    }
     if (sm == 0) return fail(ctx, PMG_ERR_UNSUPPORTED, "this launch-shape variant does not exist for this degree");
     return PMG_OK;
   }
