@@ -123,6 +123,17 @@ typedef struct pmg_options {
                             round to nearest even); the GMG level operators
                             keep FP32 G.  An accuracy evaluation of BF16 G:
                             the values are held in FP32 arrays              */
+  int dense_local;       /* tabulated local solves: the local solve of a patch
+                            (N_MG V-cycles from zero with fixed intervals) is
+                            a fixed linear map, tabulated at set-up by
+                            applying it to unit vectors; a sweep then does
+                            one dense matrix-vector product per patch instead
+                            of the V-cycles.  1 (default): pmg_setup times it
+                            against the matrix-free V-cycles on every level
+                            whose table takes at most 2 GiB and keeps the
+                            faster; 2: on every such level; 0: never.  The
+                            result equals the V-cycles' up to rounding;
+                            pmg_local_vcycle always runs the V-cycles       */
 } pmg_options;
 enum { PMG_KAPPA_ARITHMETIC = 0, PMG_KAPPA_GEOMETRIC = 1, PMG_KAPPA_HARMONIC = 2 };
 
@@ -365,6 +376,10 @@ int pmg_tuning_level(const pmg_ctx* ctx, int level, int* variant, float* ms_per_
  * cooperative launch; the set-up's timings of one full sweep with per-colour
  * launches and with the persistent launch (ms; -1 if not timed). */
 int pmg_level_persistent(const pmg_ctx* ctx, int level, int* on, float* ms_per_colour, float* ms_persistent);
+/* Tabulated local solves on mesh level `level`: *on = 1 if its sweeps use
+ * them; the set-up's timings of one full sweep with the matrix-free V-cycles
+ * and with the tables (ms; -1 if not timed). */
+int pmg_level_dense_local(const pmg_ctx* ctx, int level, int* on, float* ms_matrix_free, float* ms_tabulated);
 
 /* ---- learned Chebyshev intervals ------------------------------------------
  * No counterpart in the paper (its smoother is damped Jacobi).  A small MLP

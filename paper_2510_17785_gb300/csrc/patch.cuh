@@ -59,6 +59,8 @@ struct PatchArgs {
   int* err;                    // device error flag
   T* corr;                     // additive sweep: corrections are added here instead of to u, or NULL
   int weight_residual;         // additive sweep, transposed form: residual scaled by 1 / multiplicity
+  const T* solveop;            // tabulated local solve: [patches][Ni][Ni], entry (m, k) = (B_j e_m)_k, or NULL
+  int unit_rhs;                // MODE_LOCAL: item i solves patch i / Ni with right-hand side e_(i mod Ni)
 };
 
 
@@ -667,7 +669,7 @@ struct PatchKernel {
       if (MODE == MODE_SWEEP) {
         pid = list[item];
       } else {
-        const int64_t raw = a->ids64[item];
+        const int64_t raw = a->unit_rhs ? (int64_t)(item / L::ni(0)) : a->ids64[item];
         int64_t np = 1;
         for (int ax = 0; ax < DIM; ++ax) np *= Nv;
         if (raw >= 0 && raw < np) pid = (int)raw;
@@ -842,13 +844,30 @@ struct PatchKernel {
     } else {
       TM::template loop<NI0>([&](int pp, int i) {
         const bool act = cells[pp * CST + NCELL + 1];
-        vec(pp, L::R_(0))[i] = act ? a->r_in[(size_t)(item0 + pp) * NI0 + i] : T(0);
+        const int it = item0 + pp;
+        vec(pp, L::R_(0))[i] = !act ? T(0) : a->unit_rhs ? T(i == it % NI0 ? 1 : 0) : a->r_in[(size_t)it * NI0 + i];
       });
       TM::sync();
     }
-    // Solve: N_MG V-cycles, the first from d = 0
+    // Solve: N_MG V-cycles, the first from d = 0 (or their tabulated operator)
+    if (MODE == MODE_SWEEP && a->solveop) {
+      // tabulated local solve: d = B_j r, one owner per output, fixed order over m
+      TM::template loop<NI0>([&](int pp, int k) {
+        const bool act = cells[pp * CST + NCELL + 1];
+        T s = T(0);
+        if (act) {
+          const T* B = a->solveop + (size_t)cells[pp * CST + NCELL] * NI0 * NI0 + k;
+          const T* r = vec(pp, L::R_(0));
+#pragma unroll 8
+          for (int m = 0; m < NI0; ++m) s += __ldg(B + (size_t)m * NI0) * r[m];
+        }
+        vec(pp, L::D_(0))[k] = s;
+      });
+      TM::sync();
+    } else {
 #pragma unroll 1
-    for (int cyc = 0; cyc < a->n_mg; ++cyc) vcycle<0>(cyc == 0);
+      for (int cyc = 0; cyc < a->n_mg; ++cyc) vcycle<0>(cyc == 0);
+    }
     // Scatter
     if (MODE == MODE_SWEEP) {
       T* dst = a->corr ? a->corr : a->u;      // additive: corrections collected apart from u

@@ -44,6 +44,13 @@ struct PLevel {
   float* dense32 = nullptr;
 };
 
+// tabulated local solve of a mesh level (top p-level): [patch][Ni][Ni], (m, k) = (B_j e_m)_k
+struct SolveTable {
+  double* t64 = nullptr;
+  float* t32 = nullptr;
+  bool on = false;
+};
+
 struct HLevel {
   int N = 0;
   size_t nd = 0;        // (pN+1)^d
@@ -106,6 +113,8 @@ struct pmg_ctx {
   int level_variant[16] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};  // per mesh level
   float level_ms[16][NUM_VARIANTS] = {};  // set-up timings per mesh level (-1: not timed)
   bool level_persist[16] = {};           // sweeps of the level as one persistent launch
+  SolveTable solve_table[16];            // tabulated local solves per mesh level
+  float dense_ms[16][2] = {};            // set-up: full sweep matrix-free / tabulated (-1: not timed)
   float persist_ms[16][2] = {};          // set-up: full sweep per-colour / persistent (-1: not timed)
   bool any_persist = false;
   unsigned int* d_sync = nullptr;        // grid barrier: count, generation, status
@@ -239,6 +248,13 @@ template <>
 const float* Fdmof<float>(const pmg_ctx* c, int q) { return c->fdm32[q]; }
 
 template <typename T>
+const T* SolveTableof(const SolveTable& t);
+template <>
+const double* SolveTableof<double>(const SolveTable& t) { return t.t64; }
+template <>
+const float* SolveTableof<float>(const SolveTable& t) { return t.t32; }
+
+template <typename T>
 PatchArgs<T> patch_args(pmg_ctx* c, int level) {
   PatchArgs<T> a;
   std::memset(&a, 0, sizeof(a));
@@ -251,6 +267,7 @@ PatchArgs<T> patch_args(pmg_ctx* c, int level) {
     a.lv[k].bounds = Boundsof<T>(h.pl[k]);
     a.lv[k].dense = Denseof<T>(h.pl[k]);
   }
+  if (level < 16 && c->solve_table[level].on) a.solveop = SolveTableof<T>(c->solve_table[level]);
   a.smoother = c->opt.smoother;
   a.cheb_degree = c->opt.cheb_degree;
   a.omega = c->opt.jacobi_omega;
@@ -301,6 +318,43 @@ int sweep_persist(pmg_ctx* ctx, int level, const T* b, T* u, bool reverse, cudaS
   LK(1, ctx->dim == 2 ? launch_patch_persist<2, T>(ctx->p, pa, &grid, s)
                       : launch_patch_persist<3, T>(ctx->p, pa, &grid, s));
   return PMG_OK;
+}
+
+// bytes of the tabulated local solves of a mesh level
+size_t solve_table_bytes(const pmg_ctx* ctx, int level, size_t elem) {
+  const size_t ni = ipow_sz(2 * ctx->p - 1, ctx->dim);
+  return ctx->L[level].npatch * ni * ni * elem;
+}
+
+// tabulate the local solves of a mesh level: one local launch over
+// (patch, unit right-hand side) items, whose outputs are the table's rows
+template <typename T>
+int build_solve_table(pmg_ctx* ctx, int level, T** out) {
+  HLevel& h = ctx->L[level];
+  const size_t ni = ipow_sz(2 * ctx->p - 1, ctx->dim);
+  const size_t items = h.npatch * ni;
+  if (items > (size_t)INT32_MAX) return fail(ctx, PMG_ERR_UNSUPPORTED, "local-solve table too large");
+  T* B = nullptr;
+  CU(cudaMalloc(&B, std::max<size_t>(items * ni, 1) * sizeof(T)));
+  PatchArgs<T> a = patch_args<T>(ctx, level);
+  a.solveop = nullptr;
+  a.unit_rhs = 1;
+  a.n_items = (int)items;
+  a.d_out = B;
+  const int st = patch_launch<T>(ctx, MODE_LOCAL, a, ctx->stream);
+  ctx->launches += 1;
+  if (st) {
+    cudaFree(B);
+    return fail(ctx, st == ST_UNSUPPORTED ? PMG_ERR_UNSUPPORTED : PMG_ERR_CUDA, "local-solve table launch failed");
+  }
+  *out = B;
+  return PMG_OK;
+}
+
+void free_solve_table(SolveTable& t) {
+  if (t.t64) cudaFree(t.t64);
+  if (t.t32) cudaFree(t.t32);
+  t = SolveTable();
 }
 
 // after a synchronisation: a persistent sweep whose barrier wait ran out
@@ -559,6 +613,41 @@ int autotune_T(pmg_ctx* ctx) {
     ctx->persist_ms[l][1] = ok ? ms[1] : -1.f;
     ctx->level_persist[l] = ok && (ctx->opt.persistent == 2 || ms[1] < ms[0]);
   }
+  // tabulated local solves: one full sweep each way, the faster kept
+  for (int l = ctx->nlev - 1; l >= 0 && st == PMG_OK; --l) {
+    HLevel& h = ctx->L[l];
+    if (l >= 16) continue;
+    ctx->dense_ms[l][0] = ctx->dense_ms[l][1] = -1.f;
+    if (h.npatch == 0 || ctx->opt.dense_local == 0 || solve_table_bytes(ctx, l, sizeof(T)) > (size_t(2) << 30))
+      continue;
+    T* tab = nullptr;
+    st = build_solve_table<T>(ctx, l, &tab);
+    if (st) break;
+    SolveTable& t = ctx->solve_table[l];
+    if constexpr (sizeof(T) == 8) t.t64 = reinterpret_cast<double*>(tab);
+    else t.t32 = reinterpret_cast<float*>(tab);
+    T* u = Xof<T>(h);
+    T* b = Bof<T>(h);
+    float ms[2] = {1e30f, 1e30f};
+    for (int mode = 0; mode < 2 && st == PMG_OK; ++mode) {
+      t.on = mode == 1;
+      st = sweep<T>(ctx, l, b, u, false, s);                 // warm-up
+      for (int rep = 0; rep < 3 && st == PMG_OK; ++rep) {
+        float tm = 0.f;
+        if (cudaEventRecord(e0, s) != cudaSuccess) st = fail(ctx, PMG_ERR_CUDA, "autotune: event");
+        if (st == PMG_OK) st = sweep<T>(ctx, l, b, u, false, s);
+        if (st == PMG_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                             cudaEventElapsedTime(&tm, e0, e1) != cudaSuccess))
+          st = fail(ctx, PMG_ERR_CUDA, "autotune: event");
+        ms[mode] = std::min(ms[mode], tm);
+      }
+    }
+    if (st == PMG_OK) st = check_sync(ctx);
+    ctx->dense_ms[l][0] = ms[0];
+    ctx->dense_ms[l][1] = ms[1];
+    t.on = ctx->opt.dense_local == 2 || ms[1] < ms[0];
+    if (!t.on) free_solve_table(t);
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return st;
@@ -569,10 +658,21 @@ int autotune(pmg_ctx* ctx) {
   for (int l = 0; l < 16; ++l)
     for (int v = 0; v < NUM_VARIANTS; ++v) ctx->level_ms[l][v] = -1.f;
   for (int l = 0; l < 16; ++l) ctx->persist_ms[l][0] = ctx->persist_ms[l][1] = -1.f;
+  for (int l = 0; l < 16; ++l) ctx->dense_ms[l][0] = ctx->dense_ms[l][1] = -1.f;
   if (!ctx->opt.autotune) {
     if (ctx->opt.persistent == 2 && !ctx->opt.additive) {
       for (int l = 0; l < ctx->nlev && l < 16; ++l) ctx->level_persist[l] = ctx->L[l].npatch > 0;
       ctx->any_persist = true;
+    }
+    if (ctx->opt.dense_local == 2) {
+      const bool mixed = ctx->opt.precision == PMG_PREC_MIXED;
+      for (int l = 0; l < ctx->nlev && l < 16; ++l) {
+        if (ctx->L[l].npatch == 0 || solve_table_bytes(ctx, l, mixed ? 4 : 8) > (size_t(2) << 30)) continue;
+        SolveTable& t = ctx->solve_table[l];
+        const int st = mixed ? build_solve_table<float>(ctx, l, &t.t32) : build_solve_table<double>(ctx, l, &t.t64);
+        if (st) return st;
+        t.on = true;
+      }
     }
     ctx->variant = ctx->opt.variant;
     size_t sm;
@@ -628,6 +728,8 @@ void pmg_default_options(pmg_options* o) {
   o->additive_theta = 1.0;
   o->persistent = 1;
   o->sync_budget = 0;
+  o->geometry_bf16 = 0;
+  o->dense_local = 1;
 }
 
 int pmg_create(int device, const pmg_options* opt, pmg_ctx** out) {
@@ -644,7 +746,7 @@ int pmg_create(int device, const pmg_options* opt, pmg_ctx** out) {
       o.bounds > 3 || !(o.bound_safety > 0) || !(o.mlp_safety > 0) || o.coarse_kappa < 0 || o.coarse_kappa > 2 || !(o.bound_ratio >= 1) || o.variant < 0 ||
       o.variant >= NUM_VARIANTS || (o.additive != 0 && o.additive != 1) || !(o.additive_theta > 0) ||
       o.persistent < 0 || o.persistent > 2 || o.sync_budget < 0 || o.geometry_bf16 < 0 || o.geometry_bf16 > 1 ||
-      (o.geometry_bf16 && o.precision != PMG_PREC_MIXED)) {
+      (o.geometry_bf16 && o.precision != PMG_PREC_MIXED) || o.dense_local < 0 || o.dense_local > 2) {
     delete ctx;
     return PMG_ERR_ARG;
   }
@@ -677,6 +779,7 @@ int pmg_destroy(pmg_ctx* ctx) {
   if (ctx->gm_V) cudaFree(ctx->gm_V);
   if (ctx->d_err) cudaFree(ctx->d_err);
   if (ctx->d_sync) cudaFree(ctx->d_sync);
+  for (auto& t : ctx->solve_table) free_solve_table(t);
   if (ctx->h_rr) cudaFreeHost(ctx->h_rr);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   if (ctx->ev_caller) cudaEventDestroy(ctx->ev_caller);
@@ -1969,6 +2072,15 @@ int pmg_level_persistent(const pmg_ctx* ctx, int level, int* on, float* ms_per_c
   if (on) *on = in && ctx->level_persist[level] ? 1 : 0;
   if (ms_per_colour) *ms_per_colour = in ? ctx->persist_ms[level][0] : -1.f;
   if (ms_persistent) *ms_persistent = in ? ctx->persist_ms[level][1] : -1.f;
+  return PMG_OK;
+}
+
+int pmg_level_dense_local(const pmg_ctx* ctx, int level, int* on, float* ms_matrix_free, float* ms_tabulated) {
+  if (!ctx || !ctx->setup_ok || level < 0 || level >= ctx->nlev) return PMG_ERR_ARG;
+  const bool in = level < 16 && !ctx->um;
+  if (on) *on = in && ctx->solve_table[level].on ? 1 : 0;
+  if (ms_matrix_free) *ms_matrix_free = in ? ctx->dense_ms[level][0] : -1.f;
+  if (ms_tabulated) *ms_tabulated = in ? ctx->dense_ms[level][1] : -1.f;
   return PMG_OK;
 }
 

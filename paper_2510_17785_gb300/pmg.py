@@ -39,7 +39,7 @@ SYMBOLS = (
     "pmg_mlp_train", "pmg_mlp_predict", "pmg_set_mlp", "pmg_solve_gmres", "pmg_batch_solve_cg",
     "pmg_tuning_level", "pmg_coeff_upload", "pmg_mlp_init", "pmg_mlp_targets", "pmg_mlp_norm", "pmg_mlp_save",
     "pmg_mlp_load", "pmg_mesh_upload", "pmg_set_degree", "pmg_get_dof_map", "pmg_local_size",
-    "pmg_level_persistent",
+    "pmg_level_persistent", "pmg_level_dense_local",
 )
 
 
@@ -51,7 +51,7 @@ class Options(C.Structure):
         ("seed", C.c_uint64), ("precision", C.c_int), ("autotune", C.c_int), ("variant", C.c_int),
         ("mlp_safety", C.c_double), ("coarse_kappa", C.c_int), ("post_reverse", C.c_int),
         ("additive", C.c_int), ("additive_theta", C.c_double), ("persistent", C.c_int),
-        ("sync_budget", C.c_longlong), ("geometry_bf16", C.c_int),
+        ("sync_budget", C.c_longlong), ("geometry_bf16", C.c_int), ("dense_local", C.c_int),
     ]
 
 
@@ -130,6 +130,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "pmg_get_dof_map": (i, [vp, i, vp]),
         "pmg_local_size": (i, [vp, i, P(i64)]),
         "pmg_level_persistent": (i, [vp, i, P(i), P(C.c_float), P(C.c_float)]),
+        "pmg_level_dense_local": (i, [vp, i, P(i), P(C.c_float), P(C.c_float)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -459,6 +460,12 @@ class Context:
         """(persistent sweeps on mesh level `level`?, set-up ms per-colour, ms persistent)"""
         on, a, b = C.c_int(), C.c_float(), C.c_float()
         self._check(self.lib.pmg_level_persistent(self.h, level, C.byref(on), C.byref(a), C.byref(b)))
+        return bool(on.value), a.value, b.value
+
+    def level_dense_local(self, level):
+        """(tabulated local solves on mesh level `level`?, set-up ms matrix-free, ms tabulated)"""
+        on, a, b = C.c_int(), C.c_float(), C.c_float()
+        self._check(self.lib.pmg_level_dense_local(self.h, level, C.byref(on), C.byref(a), C.byref(b)))
         return bool(on.value), a.value, b.value
 
     def tuning_level(self, level):
