@@ -37,6 +37,10 @@ def test_default_options(lib):
     assert o.smoother == pmg.SMOOTHER_CHEBYSHEV and o.cheb_degree == 3 and o.n_mg == 1
     assert o.lanczos_steps == 16 and o.bound_safety == 1.1 and o.bound_ratio == 10.0
     assert o.jacobi_omega == 0.5 and o.precision == pmg.PREC_FP64
+    # the trailing fields: the ctypes layout matches the C struct to its end
+    assert o.additive_theta == 1.0 and o.persistent == 1 and o.sync_budget == 0
+    assert o.geometry_bf16 == 0 and o.dense_local == 1
+    assert pmg.Options.dense_local.offset + 4 <= C.sizeof(pmg.Options)
 
 
 def test_argument_validation_without_device(lib):
@@ -48,6 +52,9 @@ def test_argument_validation_without_device(lib):
     assert lib.pmg_create(0, C.byref(bad), C.byref(h)) == 1
     bad = pmg.default_options(lanczos_steps=65)
     assert lib.pmg_create(0, C.byref(bad), C.byref(h)) == 1
+    for kw in (dict(persistent=3), dict(sync_budget=-1), dict(geometry_bf16=1), dict(dense_local=3)):
+        bad = pmg.default_options(**kw)                              # geometry_bf16 needs mixed precision
+        assert lib.pmg_create(0, C.byref(bad), C.byref(h)) == 1, kw
     assert lib.pmg_destroy(None) == 1
     assert lib.pmg_setup(None) == 1
     assert lib.pmg_sweep_flops(None, 0) == 0.0
