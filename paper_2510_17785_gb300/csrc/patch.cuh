@@ -255,6 +255,7 @@ struct PatchKernel {
   const int32_t* list;   // patch ids of the colour being swept (MODE_SWEEP)
   int n_items;           // patches of this launch (or of the colour, persistent launches)
   int blk;               // batch of PPB patches this CTA works on
+  bool coherent = false; // u changes during the launch (persistent sweeps): read it through L2
 
   __device__ T* vec(int pp, int off) const { return sm + pp * PS + off; }
 
@@ -817,7 +818,9 @@ struct PatchKernel {
       const T* bg = a->b;
       stage<NN0>([&](int pp, int i) {
         const bool act = cells[pp * CST + NCELL + 1];
-        return act ? __ldg(ug + gindex<P>(pp, i)) : T(0);
+        if (!act) return T(0);
+        const T* q = ug + gindex<P>(pp, i);
+        return coherent ? __ldcg(q) : __ldg(q);
       }, [&](int pp, int i, T v) { vec(pp, L::CLOS)[i] = v; });
       stage<NI0>([&](int pp, int i) {
         const bool act = cells[pp * CST + NCELL + 1];
@@ -873,7 +876,10 @@ struct PatchKernel {
       T* dst = a->corr ? a->corr : a->u;      // additive: corrections collected apart from u
       TM::template loop<NI0>([&](int pp, int i) {
         const bool act = cells[pp * CST + NCELL + 1];
-        if (act) dst[gindex_int<P>(pp, i)] += vec(pp, L::D_(0))[i];
+        if (act) {
+          T* q = dst + gindex_int<P>(pp, i);
+          *q = (coherent ? __ldcg(q) : *q) + vec(pp, L::D_(0))[i];
+        }
       });
     } else {
       TM::template loop<NI0>([&](int pp, int i) {
@@ -973,6 +979,7 @@ __global__ void __launch_bounds__(Config<DIM, P, T, V>::NT, Config<DIM, P, T, V>
   k.sm = reinterpret_cast<T*>(smem_raw);
   k.cells = reinterpret_cast<int*>(smem_raw + sizeof(T) * (size_t)PK::PS * PK::PPB);
   k.a = &pa.base;
+  k.coherent = true;                   // colours after the first read what earlier colours wrote
   for (int i = 0; i < pa.n_colours; ++i) {
     const int c = pa.reverse ? pa.n_colours - 1 - i : i;
     k.list = pa.lists[c];
