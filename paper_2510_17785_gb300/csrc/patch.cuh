@@ -139,16 +139,15 @@ struct Layout {
   static constexpr int SCRATCH = LINE ? Dims<DIM, 2, P>::SCRATCH_LINE : Dims<DIM, 2, P>::SCRATCH;
   static constexpr int COEF = SCR + SCRATCH;      // per level: 1/theta, c1[1..7], c2[1..7]
   static constexpr int NCOEF = 16;
-  // fast-diagonalisation tables of the Cartesian-reinforced smoother, per level q > 1
+  // (the fast-diagonalisation tables of the Cartesian-reinforced smoother are
+  // the same for every patch and are read from global memory)
   __host__ __device__ static constexpr int mi(int k) { return 2 * q(k) - 1; }
-  __host__ __device__ static constexpr int fsz(int k) { return q(k) > 1 ? mi(k) * mi(k) + 3 * mi(k) : 0; }
-  __host__ __device__ static constexpr int foff(int k) { return k == 0 ? COEF + NL * NCOEF : foff(k - 1) + fsz(k - 1); }
-  __host__ __device__ static constexpr int FDM(int k) { return foff(k); }
+  static constexpr int END = COEF + NL * NCOEF;
   // geometry tensors of the patch's 2^d cells at the top degree, staged once
   // per patch (latency-oriented launch shapes): [cell slot][ncomp][(p+1)^d]
   static constexpr int GCELL = (DIM * (DIM + 1) / 2) * ipow(P + 1, DIM);
-  static constexpr int GS = (foff(NL) + 3) & ~3;
-  static constexpr int PS_RAW = GSMEM ? GS + (1 << DIM) * GCELL : foff(NL);
+  static constexpr int GS = (END + 3) & ~3;
+  static constexpr int PS_RAW = GSMEM ? GS + (1 << DIM) * GCELL : END;
   static constexpr int PS = (PS_RAW + 3) & ~3;    // per-patch stride in elements
 };
 
@@ -532,8 +531,10 @@ struct PatchKernel {
     }
     auto X = [&](int pp) { return vec(pp, L::SCR); };
     auto Y = [&](int pp) { return vec(pp, L::SCR) + NI; };
-    auto Sm = [&](int pp) { return vec(pp, L::FDM(K)); };
-    auto lam = [&](int pp) { return vec(pp, L::FDM(K)) + Mi * Mi; };
+    // reference-patch table of level K: [S: Mi x Mi][lambda: Mi][diag K: Mi][diag M: Mi]
+    const T* const tab = a->lv[K].fdm;
+    auto Sm = [&](int) { return tab; };
+    auto lam = [&](int) { return tab + Mi * Mi; };
     TM::template loop<NLINE>([&](int pp, int l) { fdm_line<K, 0, false>(Sm(pp), vec(pp, src), X(pp), l); });
     TM::sync();
     if constexpr (DIM == 3) {
@@ -573,7 +574,7 @@ struct PatchKernel {
     const T om = T(a->omega);
     TM::template loop<NLINE>([&](int pp, int l) {
       const T* S = Sm(pp);
-      const T* Kd = vec(pp, L::FDM(K)) + Mi * Mi + Mi;
+      const T* Kd = tab + Mi * Mi + Mi;
       const T* Md = Kd + Mi;
       const T* in = X(pp) + l * Mi;
       T v[Mi];
@@ -762,11 +763,6 @@ struct PatchKernel {
           const int slot = e / GC;
           return act ? __ldg(G + (size_t)cells[pp * CST + slot] * GC + (e - slot * GC)) : T(0);
         }, [&](int pp, int e, T v) { vec(pp, L::GS)[e] = v; });
-      }
-      // reference-patch fast-diagonalisation table (Cartesian-reinforced smoother)
-      if (a->smoother == 2) {
-        constexpr int FS = L::fsz(K);
-        TM::template loop<FS>([&](int pp, int e) { vec(pp, L::FDM(K))[e] = a->lv[K].fdm[e]; });
       }
       // Chebyshev coefficients of the three-term recurrence (Saad, Algorithm
       // 12.1): with sigma = theta / delta the recurrence rho_1 = 1 / sigma,
