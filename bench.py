@@ -656,7 +656,8 @@ def run_ours(args):
                             e2e_ms=e2e_ms, setup_s=t_setup, maxdiff_e2e=err,
                             umax=float(x.abs().max()), tuning=ctx.tuning(),
                             level_variants=[ctx.tuning_level(lv)[0] for lv in range(levels)],
-                            persistent={lv: ctx.level_persistent(lv) for lv in range(levels)})
+                            persistent={lv: ctx.level_persistent(lv) for lv in range(levels)},
+                            dense_local={lv: ctx.level_dense_local(lv) for lv in range(levels)})
         if name == "mixed":
             result["fma32"] = ctx.fma_peak(pmg.PREC_MIXED)
             result["fma64"] = ctx.fma_peak(pmg.PREC_FP64)
@@ -697,7 +698,8 @@ def run_ours(args):
                                     "patches_per_cta": head["tuning"][2],
                                     "autotune_ms_per_variant": [round(x, 4) for x in head["tuning"][3]],
                                     "variant_per_mesh_level": head["level_variants"],
-                                    "persistent_levels": head["persistent"]},
+                                    "persistent_levels": head["persistent"],
+                                    "tabulated_local_solve_levels": head["dense_local"]},
         },
         "time_to_solution_ms": t_max,
         "cg_iterations": [i for i, _ in head["its"]],

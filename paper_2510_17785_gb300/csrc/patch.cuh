@@ -855,10 +855,21 @@ struct PatchKernel {
         const bool act = cells[pp * CST + NCELL + 1];
         T s = T(0);
         if (act) {
+          // 32 loads in flight per thread before their FMAs (the order over m is kept)
           const T* B = a->solveop + (size_t)cells[pp * CST + NCELL] * NI0 * NI0 + k;
           const T* r = vec(pp, L::R_(0));
-#pragma unroll 8
-          for (int m = 0; m < NI0; ++m) s += __ldg(B + (size_t)m * NI0) * r[m];
+          constexpr int W = 32;
+          int m = 0;
+#pragma unroll 1
+          for (; m + W <= NI0; m += W) {
+            T bv[W];
+#pragma unroll
+            for (int j = 0; j < W; ++j) bv[j] = __ldg(B + (size_t)(m + j) * NI0);
+#pragma unroll
+            for (int j = 0; j < W; ++j) s += bv[j] * r[m + j];
+          }
+#pragma unroll 1
+          for (; m < NI0; ++m) s += __ldg(B + (size_t)m * NI0) * r[m];
         }
         vec(pp, L::D_(0))[k] = s;
       });
