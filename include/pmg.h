@@ -134,6 +134,13 @@ typedef struct pmg_options {
                             faster; 2: on every such level; 0: never.  The
                             result equals the V-cycles' up to rounding;
                             pmg_local_vcycle always runs the V-cycles       */
+  int level_rule;        /* p-levels of the local V-cycle (Section 3.1):
+                            0 (default): p, p/2, ..., 1; 1: the paper's
+                            nested sequence 1, 3, 7, 15, ... below p with p
+                            on top (p = 8: 8, 7, 3, 1; they differ for
+                            p = 4, 5 and 8).  Rule 1 runs one launch shape
+                            (no autotuned shapes, no persistent sweeps);
+                            structured meshes only                          */
 } pmg_options;
 enum { PMG_KAPPA_ARITHMETIC = 0, PMG_KAPPA_GEOMETRIC = 1, PMG_KAPPA_HARMONIC = 2 };
 

@@ -125,13 +125,14 @@ void build_tables(Tables<double>& t64, Tables<float>& t32, Rules& r) {
         r.Bd[q][g][a] = bd;
       }
     }
-    // prolongation from degree q/2 to q
-    const int qc = q / 2;
-    if (qc >= 1) {
+    // prolongation from degree q/2 to q, and from the paper rule's coarse degree
+    for (int rule = 0; rule < 2; ++rule) {
+      const int qc = coarse_degree(q, rule);
+      if (qc < 1) continue;
       const std::vector<double> glc = gauss_lobatto(qc);
       const auto E = lagrange_matrix(glc, gl);   // [a][b]
       for (int a = 0; a <= q; ++a)
-        for (int b = 0; b <= qc; ++b) t64.E[q][a][b] = E[a][b];
+        for (int b = 0; b <= qc; ++b) (rule == 0 ? t64.E : t64.EP)[q][a][b] = E[a][b];
     }
     // (q+2)-point rule for load vectors
     std::vector<double> gx2, gw2;
@@ -173,6 +174,7 @@ void build_tables(Tables<double>& t64, Tables<float>& t32, Rules& r) {
         t32.B[q][i][j] = (float)t64.B[q][i][j];
         t32.D[q][i][j] = (float)t64.D[q][i][j];
         t32.E[q][i][j] = (float)t64.E[q][i][j];
+        t32.EP[q][i][j] = (float)t64.EP[q][i][j];
       }
     for (int k = 0; k < 4; ++k)
       for (int i = 0; i < PMG_EOR; ++i) {

@@ -47,7 +47,7 @@ int launch_patch_PV(int mode, const PatchArgs<T>& a, cudaStream_t s) {
       }
       k_patch<DIM, P, T, MODE_SWEEP, V><<<grid, C::NT, C::smem, s>>>(a);
     } else {
-      if constexpr (V != 0) return ST_UNSUPPORTED;
+      if constexpr (V != 0 && V != VARIANT_PAPER_LEVELS) return ST_UNSUPPORTED;
       static bool attr[64] = {};
       if (!attr[dev]) {
         if (cudaFuncSetAttribute(k_patch<DIM, P, T, MODE_LOCAL, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -66,6 +66,7 @@ int launch_patch_PV(int mode, const PatchArgs<T>& a, cudaStream_t s) {
 template <int DIM, int P, typename T>
 int launch_patch_P(int mode, int variant, const PatchArgs<T>& a, cudaStream_t s) {
   if (variant == 0) return launch_patch_PV<DIM, P, T, 0>(mode, a, s);
+  if (variant == VARIANT_PAPER_LEVELS) return launch_patch_PV<DIM, P, T, VARIANT_PAPER_LEVELS>(mode, a, s);
   if constexpr (DIM == 3 && P >= 3) {
     switch (variant) {
       case 1: return launch_patch_PV<DIM, P, T, 1>(mode, a, s);
@@ -174,7 +175,7 @@ int launch_patch(int P, int mode, int variant, const PatchArgs<T>& a, cudaStream
 template <int DIM, int P, typename T, int V>
 void patch_config_PV(size_t* smem, int* ppb, int* nt) {
   using C = Config<DIM, P, T, V>;
-  const bool ok = C::exists && (V == 0 || (DIM == 3 && P >= 3));
+  const bool ok = C::exists && (V == 0 || V == VARIANT_PAPER_LEVELS || (DIM == 3 && P >= 3));
   *smem = ok ? C::smem : 0;
   *ppb = ok ? C::PPB : 0;
   *nt = ok ? C::NT : 0;
@@ -182,6 +183,7 @@ void patch_config_PV(size_t* smem, int* ppb, int* nt) {
 
 template <int DIM, int P, typename T>
 void patch_config_P(int variant, size_t* smem, int* ppb, int* nt) {
+  if (variant == VARIANT_PAPER_LEVELS) return patch_config_PV<DIM, P, T, VARIANT_PAPER_LEVELS>(smem, ppb, nt);
   switch (variant) {
     case 0: return patch_config_PV<DIM, P, T, 0>(smem, ppb, nt);
     case 1: return patch_config_PV<DIM, P, T, 1>(smem, ppb, nt);

@@ -108,10 +108,10 @@ struct PatchEpi {
   }
 };
 
-template <int DIM, int P, bool LINE = false, bool GSMEM = false>
+template <int DIM, int P, bool LINE = false, bool GSMEM = false, int LR = 0>
 struct Layout {
-  static constexpr int NL = nlevels(P);
-  __host__ __device__ static constexpr int q(int k) { return P >> k; }
+  static constexpr int NL = nlevels_rule(P, LR);
+  __host__ __device__ static constexpr int q(int k) { return level_degree(P, LR, k); }
   __host__ __device__ static constexpr int ni(int k) { return q(k) == 1 ? 1 : ipow(2 * q(k) - 1, DIM); }
   // per-level vectors r, d, res, dir, [A x: dense levels only], 1/diag
   __host__ __device__ static constexpr bool dn(int k) { return dense_level(DIM, q(k)); }
@@ -174,6 +174,9 @@ struct Layout {
 // barrier and several lines per thread (more independent work per thread,
 // no waiting on the other patches of the CTA).
 constexpr int NUM_VARIANTS = PMG_NUM_VARIANTS;
+// the default launch shape with the paper's p-level rule (options.level_rule =
+// 1); never chosen by the autotuner, which times launch shapes only
+constexpr int VARIANT_PAPER_LEVELS = NUM_VARIANTS;
 
 template <int DIM, int P, typename T, int V = 0>
 struct Config {
@@ -188,22 +191,25 @@ struct Config {
                                                 false, false, false, true, true, true};
   static constexpr bool GSMEMV[NUM_VARIANTS] = {false, false, false, true, false, false, true, false, true, true,
                                                 false, false, false, false, false, false};
-  static constexpr int NT = NTV[V];
-  static constexpr int PPB_MAX = PPBV[V];
-  static constexpr bool LINE = LINEV[V];
-  static constexpr bool GSMEM = GSMEMV[V];
+  // variant VARIANT_PAPER_LEVELS: the default shape with the paper's p-level rule
+  static constexpr int VB = V == VARIANT_PAPER_LEVELS ? 0 : V;
+  static constexpr int LR = V == VARIANT_PAPER_LEVELS ? 1 : 0;
+  static constexpr int NT = NTV[VB];
+  static constexpr int PPB_MAX = PPBV[VB];
+  static constexpr bool LINE = LINEV[VB];
+  static constexpr bool GSMEM = GSMEMV[VB];
   static constexpr size_t bytes_per_patch =
-      sizeof(T) * Layout<DIM, P, LINE, GSMEM>::PS + sizeof(int) * ((1 << DIM) + 6);
+      sizeof(T) * Layout<DIM, P, LINE, GSMEM, LR>::PS + sizeof(int) * ((1 << DIM) + 6);
   static constexpr size_t SMEM_LIMIT = 227 * 1024;
   static constexpr int PPB_FIT = (int)(SMEM_LIMIT / bytes_per_patch);
   static constexpr int PPB = PPB_FIT < PPB_MAX ? (PPB_FIT < 1 ? 1 : PPB_FIT) : PPB_MAX;
   static constexpr size_t smem = bytes_per_patch * PPB;
   static constexpr bool fits = bytes_per_patch <= SMEM_LIMIT;
   // grouped only when the CTA really holds several patches
-  static constexpr bool GROUPED = GROUPV[V] && PPB > 1 && NT % PPB == 0 && (NT / PPB) % 32 == 0;
+  static constexpr bool GROUPED = GROUPV[VB] && PPB > 1 && NT % PPB == 0 && (NT / PPB) % 32 == 0;
   // register budget per thread (launch bound): 64 for FP32 up to degree 5,
   // 128 otherwise (FP64, or the larger line registers at high degree)
-  static constexpr int REG_TARGET = (sizeof(T) == 4 && P <= 5 && !GSMEMV[V]) ? 64 : 128;
+  static constexpr int REG_TARGET = (sizeof(T) == 4 && P <= 5 && !GSMEMV[VB]) ? 64 : 128;
   // resident CTAs per SM: by the register target, and at most what shared
   // memory allows (small CTAs then get the registers shared memory leaves)
   static constexpr int MINB_REG_RAW = 65536 / (NT * REG_TARGET);
@@ -223,7 +229,10 @@ struct Config {
     if constexpr (W >= V) return true;
     else return !same_as<W>() && distinct_from_lower<W + 1>();
   }
-  static constexpr bool distinct_impl() { return distinct_from_lower<0>(); }
+  static constexpr bool distinct_impl() {
+    if constexpr (V == VARIANT_PAPER_LEVELS) return rules_differ(P);   // exists where the rules differ
+    else return distinct_from_lower<0>();
+  }
   static constexpr bool distinct = distinct_impl();
   // worth compiling: a line variant keeps at most two lines' gradients and
   // fluxes per thread in registers (more spills and bloats the build); FP64,
@@ -234,15 +243,16 @@ struct Config {
   static constexpr int SPAN_ = GROUPED ? 1 : PPB;
   static constexpr int LPT_ = (SPAN_ * ipow(QPL, DIM - 1) + TPP_ - 1) / TPP_;
   static constexpr bool worth = (!LINE || LPT_ <= (GROUPED ? 4 : 2)) &&
-                                (sizeof(T) == 4 || V == 0 || ((V == 2 || V == 4 || V == 6) && P <= 6)) &&
-                                (V < 8 || (DIM == 3 && P >= 3)) && (V < 10 || (sizeof(T) == 4 && (V >= 13 || P <= 5)));
+                                (sizeof(T) == 4 || VB == 0 || ((VB == 2 || VB == 4 || VB == 6) && P <= 6)) &&
+                                (VB < 8 || (DIM == 3 && P >= 3)) &&
+                                (VB < 10 || (sizeof(T) == 4 && (VB >= 13 || P <= 5)));
   static constexpr bool exists = fits && distinct && worth;
 };
 
 template <int DIM, int P, typename T, int MODE, int V = 0>
 struct PatchKernel {
   using C = Config<DIM, P, T, V>;
-  using L = Layout<DIM, P, C::LINE, C::GSMEM>;
+  using L = Layout<DIM, P, C::LINE, C::GSMEM, C::LR>;
   using TM = Team<C::NT, C::PPB, C::GROUPED>;
   static constexpr int NT = C::NT, PPB = C::PPB, NL = L::NL, PS = L::PS;
   static constexpr int NCELL = 1 << DIM;
@@ -299,7 +309,7 @@ struct PatchKernel {
 
   template <int K>
   __device__ auto gfun() const {
-    constexpr int q = P >> K;
+    constexpr int q = L::q(K);
     constexpr int stride = Dims<DIM, 2, q>::NCOMP * ipow(q + 1, DIM);
     if constexpr (C::GSMEM && K == 0) {                 // staged in shared memory by load_level
       return SharedGeom<stride>{};
@@ -336,7 +346,7 @@ struct PatchKernel {
   // matrix on small levels).  Ends with a barrier.
   template <int K>
   __device__ void apply_int(int in_off, const PatchEpi<T>& e) {
-    constexpr int q = P >> K;
+    constexpr int q = L::q(K);
     if constexpr (dense_level(DIM, q)) {
       // the epilogue may overwrite the input, which other rows still read:
       // products first, epilogue after a barrier
@@ -365,7 +375,7 @@ struct PatchKernel {
   template <int K, int AX, bool ACC>
   __device__ static void prol_item(const T* __restrict__ in, T* __restrict__ out, int item, int Mc, int Mf,
                                    int I, int O) {
-    constexpr int qf = P >> K, qc = qf >> 1;
+    constexpr int qf = L::q(K), qc = L::q(K + 1);
     const int OI = O * I;
     const int c = item >= OI, pi = item - c * OI;
     const int i = pi % I, o = pi / I;
@@ -383,7 +393,7 @@ struct PatchKernel {
       if (a > amax) break;
       T s = T(0);
 #pragma unroll
-      for (int b = 0; b <= qc; ++b) s += tabE<T>(qf, a, b) * v[b];
+      for (int b = 0; b <= qc; ++b) s += tabT<T, C::LR>(qf, a, b) * v[b];
       const int kf = qf * c + a;
       T* p = dst + (kf - 1) * I;
       *p = ACC ? *p + s : s;
@@ -394,7 +404,7 @@ struct PatchKernel {
   template <int K>
   __device__ static void rest_item(const T* __restrict__ in, T* __restrict__ out, int item, int Mc, int Mf,
                                    int I, int O) {
-    constexpr int qf = P >> K, qc = qf >> 1;
+    constexpr int qf = L::q(K), qc = L::q(K + 1);
     const int OI = O * I;
     const int c = item >= OI, pi = item - c * OI;
     const int i = pi % I, o = pi / I;
@@ -415,10 +425,10 @@ struct PatchKernel {
       for (int b = 1; b <= qc; ++b) {
         T s = T(0);
 #pragma unroll
-        for (int a = 1; a <= qf; ++a) s += tabE<T>(qf, a, b) * f[a - 1];
+        for (int a = 1; a <= qf; ++a) s += tabT<T, C::LR>(qf, a, b) * f[a - 1];
         if (b == qc) {
 #pragma unroll
-          for (int a = 1; a < qf; ++a) s += tabE<T>(qf, a, 0) * w[a - 1];
+          for (int a = 1; a < qf; ++a) s += tabT<T, C::LR>(qf, a, 0) * w[a - 1];
         }
         dst[(b - 1) * I] = s;
       }
@@ -427,7 +437,7 @@ struct PatchKernel {
       for (int b = 1; b < qc; ++b) {
         T s = T(0);
 #pragma unroll
-        for (int a = 1; a < qf; ++a) s += tabE<T>(qf, a, b) * f[a - 1];
+        for (int a = 1; a < qf; ++a) s += tabT<T, C::LR>(qf, a, b) * f[a - 1];
         dst[(qc + b - 1) * I] = s;
       }
     }
@@ -436,7 +446,7 @@ struct PatchKernel {
   // r_{K+1} = E^T res_K
   template <int K>
   __device__ void restrict_res() {
-    constexpr int qf = P >> K, qc = qf >> 1;
+    constexpr int qf = L::q(K), qc = L::q(K + 1);
     constexpr int Mf = 2 * qf - 1, Mc = (qc == 1) ? 1 : 2 * qc - 1;
     T* t = vec(0, L::SCR);
     if constexpr (DIM == 3) {
@@ -465,7 +475,7 @@ struct PatchKernel {
   // d_K += E d_{K+1}
   template <int K>
   __device__ void prolong_add() {
-    constexpr int qf = P >> K, qc = qf >> 1;
+    constexpr int qf = L::q(K), qc = L::q(K + 1);
     constexpr int Mf = 2 * qf - 1, Mc = (qc == 1) ? 1 : 2 * qc - 1;
     T* t = vec(0, L::SCR);
     if constexpr (DIM == 3) {
@@ -521,7 +531,7 @@ struct PatchKernel {
 
   template <int K>
   __device__ void fdm_step(bool zero_start) {
-    constexpr int q = P >> K, Mi = L::mi(K), NI = L::ni(K);
+    constexpr int q = L::q(K), Mi = L::mi(K), NI = L::ni(K);
     constexpr int NLINE = NI / Mi;                     // lines along one axis
     static_assert(2 * NI <= L::SCRATCH, "the fast-diagonalisation buffers exceed the scratch region");
     int src = L::R_(K);
@@ -648,7 +658,7 @@ struct PatchKernel {
   // ---- Algorithm 2
   template <int K>
   __device__ void vcycle(bool zero_start) {
-    constexpr int q = P >> K;
+    constexpr int q = L::q(K);
     if constexpr (q == 1) {
       TM::template loop<1>([&](int pp, int) { vec(pp, L::D_(K))[0] = vec(pp, L::R_(K))[0] * vec(pp, L::DINV(K))[0]; });
       TM::sync();
@@ -731,7 +741,7 @@ struct PatchKernel {
 
   template <int K>
   __device__ void load_level() {
-    constexpr int q = P >> K;
+    constexpr int q = L::q(K);
     if constexpr (q == 1) {
       TM::template loop<1>([&](int pp, int) {
         const bool act = cells[pp * CST + NCELL + 1];

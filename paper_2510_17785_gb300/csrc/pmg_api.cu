@@ -197,6 +197,7 @@ int patch_launch(pmg_ctx* c, int mode, const PatchArgs<T>& a, cudaStream_t s, in
   int v = 0;
   if (mode == MODE_SWEEP)
     v = (level >= 0 && level < 16 && c->level_variant[level] >= 0) ? c->level_variant[level] : c->variant;
+  if (c->opt.level_rule == 1 && rules_differ(c->p)) v = VARIANT_PAPER_LEVELS;   // every mode
   return c->dim == 2 ? launch_patch<2, T>(c->p, mode, v, a, s) : launch_patch<3, T>(c->p, mode, v, a, s);
 }
 template <typename T>
@@ -534,7 +535,9 @@ int autotune_T(pmg_ctx* ctx) {
   int st = PMG_OK;
   for (int l = 0; l < 16; ++l)
     for (int v = 0; v < NUM_VARIANTS; ++v) ctx->level_ms[l][v] = -1.f;
-  for (int l = ctx->nlev - 1; l >= 0 && st == PMG_OK; --l) {
+  // the paper's level rule has one launch shape, and no persistent form
+  const bool paper = ctx->opt.level_rule == 1 && rules_differ(ctx->p);
+  for (int l = ctx->nlev - 1; l >= 0 && st == PMG_OK && !paper; --l) {
     HLevel& h = ctx->L[l];
     if (h.npatch == 0 || l >= 16) continue;
     T* u = Xof<T>(h);
@@ -579,7 +582,7 @@ int autotune_T(pmg_ctx* ctx) {
   for (int l = ctx->nlev - 1; l >= 0 && st == PMG_OK; --l) {
     HLevel& h = ctx->L[l];
     ctx->persist_ms[l][0] = ctx->persist_ms[l][1] = -1.f;
-    if (h.npatch == 0 || l >= 16 || ctx->opt.persistent == 0 || ctx->opt.additive) continue;
+    if (h.npatch == 0 || l >= 16 || ctx->opt.persistent == 0 || ctx->opt.additive || paper) continue;
     if (ctx->opt.persistent == 1 && (h.npatch > 4096 || ctx->opt.autotune == 2)) continue;
     T* u = Xof<T>(h);
     T* b = Bof<T>(h);
@@ -660,7 +663,7 @@ int autotune(pmg_ctx* ctx) {
   for (int l = 0; l < 16; ++l) ctx->persist_ms[l][0] = ctx->persist_ms[l][1] = -1.f;
   for (int l = 0; l < 16; ++l) ctx->dense_ms[l][0] = ctx->dense_ms[l][1] = -1.f;
   if (!ctx->opt.autotune) {
-    if (ctx->opt.persistent == 2 && !ctx->opt.additive) {
+    if (ctx->opt.persistent == 2 && !ctx->opt.additive && !(ctx->opt.level_rule == 1 && rules_differ(ctx->p))) {
       for (int l = 0; l < ctx->nlev && l < 16; ++l) ctx->level_persist[l] = ctx->L[l].npatch > 0;
       ctx->any_persist = true;
     }
@@ -730,6 +733,7 @@ void pmg_default_options(pmg_options* o) {
   o->sync_budget = 0;
   o->geometry_bf16 = 0;
   o->dense_local = 1;
+  o->level_rule = 0;
 }
 
 int pmg_create(int device, const pmg_options* opt, pmg_ctx** out) {
@@ -746,7 +750,8 @@ int pmg_create(int device, const pmg_options* opt, pmg_ctx** out) {
       o.bounds > 3 || !(o.bound_safety > 0) || !(o.mlp_safety > 0) || o.coarse_kappa < 0 || o.coarse_kappa > 2 || !(o.bound_ratio >= 1) || o.variant < 0 ||
       o.variant >= NUM_VARIANTS || (o.additive != 0 && o.additive != 1) || !(o.additive_theta > 0) ||
       o.persistent < 0 || o.persistent > 2 || o.sync_budget < 0 || o.geometry_bf16 < 0 || o.geometry_bf16 > 1 ||
-      (o.geometry_bf16 && o.precision != PMG_PREC_MIXED) || o.dense_local < 0 || o.dense_local > 2) {
+      (o.geometry_bf16 && o.precision != PMG_PREC_MIXED) || o.dense_local < 0 || o.dense_local > 2 ||
+      o.level_rule < 0 || o.level_rule > 1) {
     delete ctx;
     return PMG_ERR_ARG;
   }
@@ -814,7 +819,19 @@ int pmg_mesh_structured(pmg_ctx* ctx, int dim, int N, int p, int n_levels, const
   ctx->p = p;
   ctx->nlev = n_levels;
   ctx->npl = 0;
-  for (int q = p; q >= 1; q >>= 1) ctx->plevels[ctx->npl++] = q;
+  for (int q = p; q >= 1; q = coarse_degree(q, ctx->opt.level_rule)) ctx->plevels[ctx->npl++] = q;
+  if (ctx->opt.level_rule == 1 && rules_differ(p)) {
+    size_t s64 = 0, s32 = 0;
+    if (dim == 2) {
+      patch_config<2, double>(p, VARIANT_PAPER_LEVELS, &s64, &ppb, &nt);
+      patch_config<2, float>(p, VARIANT_PAPER_LEVELS, &s32, &ppb, &nt);
+    } else {
+      patch_config<3, double>(p, VARIANT_PAPER_LEVELS, &s64, &ppb, &nt);
+      patch_config<3, float>(p, VARIANT_PAPER_LEVELS, &s32, &ppb, &nt);
+    }
+    if ((ctx->opt.precision == PMG_PREC_FP64 ? s64 : s32) == 0)
+      return fail(ctx, PMG_ERR_UNSUPPORTED, "the paper's level rule is not built for this degree and precision");
+  }
   const size_t nv = ipow_sz(N + 1, dim), nc = ipow_sz(N, dim);
   ctx->h_coords.assign(coords, coords + nv * dim);
   ctx->h_kappa.assign(kappa, kappa + nc);
@@ -831,6 +848,8 @@ int pmg_set_degree(pmg_ctx* ctx, int p) {
   if (ctx->setup_ok) return fail(ctx, PMG_ERR_ARG, "already set up");
   if (ctx->mesh_ok && !ctx->um) return fail(ctx, PMG_ERR_ARG, "a structured mesh carries its own degree");
   if (p < 1 || p > 8) return fail(ctx, PMG_ERR_UNSUPPORTED, "degree must be in 1..8");
+  if (ctx->opt.level_rule != 0)
+    return fail(ctx, PMG_ERR_UNSUPPORTED, "unstructured meshes: the halving level rule only");
   ctx->p = p;
   ctx->npl = 0;
   for (int q = p; q >= 1; q >>= 1) ctx->plevels[ctx->npl++] = q;
@@ -2049,7 +2068,7 @@ double pmg_sweep_flops(const pmg_ctx* ctx, int level) {
       per += (pre + 1 + post) * fpatch(q);
       if (fdm)   // pre and post: 2d one-dimensional contractions of (2q-1)^(d+1) FMAs each
         per += 2.0 * 2.0 * (2.0 * d) * std::pow(2 * q - 1, d + 1);
-      const int qc = q / 2;
+      const int qc = coarse_degree(q, ctx->opt.level_rule);
       // restriction + prolongation: d sweeps per cell, each at most n_f^d * n_c FMAs
       per += 2.0 * (1 << d) * 2.0 * d * std::pow(q + 1, d) * (qc + 1);
     }

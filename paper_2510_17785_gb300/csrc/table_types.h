@@ -1,5 +1,6 @@
 // Layout of the one-dimensional tables (see tables.cuh for their meaning).
 #pragma once
+#include <cuda_runtime.h>
 
 #define PMG_MAXQ 8
 
@@ -17,11 +18,35 @@ namespace pmg {
 #define PMG_EOC ((PMG_MAXQ + 1) / 2)     // columns j < h
 enum { EO_B = 0, EO_BT = 1, EO_D = 2, EO_DT = 3 };
 
+// p-level sequences of the local V-cycle (Section 3.1): rule 0 halves the
+// degree (p, p/2, ..., 1); rule 1 is the paper's nested sequence 1, 3, 7,
+// 15, ... below p with p on top (p = 8: 8, 7, 3, 1)
+__host__ __device__ constexpr int coarse_degree(int q, int rule) {
+  if (q <= 1) return 0;
+  if (rule == 0) return q / 2;
+  int c = 1;
+  while (2 * c + 1 < q) c = 2 * c + 1;
+  return c;
+}
+__host__ __device__ constexpr int level_degree(int p, int rule, int k) {
+  return k == 0 ? p : coarse_degree(level_degree(p, rule, k - 1), rule);
+}
+__host__ __device__ constexpr int nlevels_rule(int p, int rule) {
+  return p <= 1 ? 1 : 1 + nlevels_rule(coarse_degree(p, rule), rule);
+}
+// the two rules give different sequences for degree p
+__host__ __device__ constexpr bool rules_differ(int p) {
+  for (int k = 0; k < 8; ++k)
+    if (level_degree(p, 0, k) != level_degree(p, 1, k)) return true;
+  return false;
+}
+
 template <typename T>
 struct Tables {
   T B[PMG_MAXQ + 1][PMG_MAXQ + 1][PMG_MAXQ + 1];
   T D[PMG_MAXQ + 1][PMG_MAXQ + 1][PMG_MAXQ + 1];
   T E[PMG_MAXQ + 1][PMG_MAXQ + 1][PMG_MAXQ + 1];
+  T EP[PMG_MAXQ + 1][PMG_MAXQ + 1][PMG_MAXQ + 1];
   T Ee[4][PMG_MAXQ + 1][PMG_EOR][PMG_EOC];
   T Eo[4][PMG_MAXQ + 1][PMG_EOR][PMG_EOC];
   T Em[4][PMG_MAXQ + 1][PMG_EOR];

@@ -8,7 +8,9 @@
 //   Bd[q][g][a] = l_a'(x_g): derivative of basis a at Gauss point g
 //   E[qf][a][b] = l^{qc}_b(xi^{qf}_a), qc = qf/2 (p-prolongation, Section 3.1:
 //                 the embedding V_{j,qc} -> V_{j,qf}; restriction is E^T)
-//   gx[q][g], gw[q][g]: Gauss points and weights (used in FP64 setup kernels)
+//   EP[qf][a][b]: the same for the paper's level rule (qc = 2^k - 1 < qf)
+//   gx[q][g], gw[q][g]: Gauss points and weights (used in FP64 setup kernels,
+//                 read from global memory)
 //
 // Each translation unit holds its own copy (static __constant__) and uploads
 // it through its own entry point.
@@ -21,7 +23,7 @@ namespace pmg {
 
 static __constant__ Tables<double> c_tab_f64;
 static __constant__ Tables<float> c_tab_f32;
-static __constant__ Rules c_rules;
+static __device__ Rules c_rules;          // set-up kernels only: global memory, not the constant bank
 
 template <typename T>
 __device__ __forceinline__ T tabB(int q, int g, int a);
@@ -43,6 +45,21 @@ template <>
 __device__ __forceinline__ double tabE<double>(int qf, int a, int b) { return c_tab_f64.E[qf][a][b]; }
 template <>
 __device__ __forceinline__ float tabE<float>(int qf, int a, int b) { return c_tab_f32.E[qf][a][b]; }
+
+// prolongation for the paper's level rule: EP[qf][a][b] = l^{qc}_b(xi^{qf}_a),
+// qc = the largest 2^k - 1 below qf (coarse_degree(qf, 1))
+template <typename T>
+__device__ __forceinline__ T tabEP(int qf, int a, int b);
+template <>
+__device__ __forceinline__ double tabEP<double>(int qf, int a, int b) { return c_tab_f64.EP[qf][a][b]; }
+template <>
+__device__ __forceinline__ float tabEP<float>(int qf, int a, int b) { return c_tab_f32.EP[qf][a][b]; }
+// the prolongation table of level rule LR
+template <typename T, int LR>
+__device__ __forceinline__ T tabT(int qf, int a, int b) {
+  if constexpr (LR == 1) return tabEP<T>(qf, a, b);
+  else return tabE<T>(qf, a, b);
+}
 
 // even/odd parts of B, B^T, D, D^T (table_types.h)
 template <typename T>

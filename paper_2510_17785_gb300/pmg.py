@@ -52,6 +52,7 @@ class Options(C.Structure):
         ("mlp_safety", C.c_double), ("coarse_kappa", C.c_int), ("post_reverse", C.c_int),
         ("additive", C.c_int), ("additive_theta", C.c_double), ("persistent", C.c_int),
         ("sync_budget", C.c_longlong), ("geometry_bf16", C.c_int), ("dense_local", C.c_int),
+        ("level_rule", C.c_int),
     ]
 
 
