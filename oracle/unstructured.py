@@ -449,3 +449,62 @@ class TwoLevel:
         e1[self.free1] = sla.cho_solve(self.chol, r1[self.free1])
         x = x + self.P @ e1
         return self.S.sweep(x, b, reverse=True)
+
+
+# ------------------------------------------------------ two mesh levels
+def h_prolongation(coarse: Mesh, fine: Mesh, parent, child, q: int) -> sp.csr_matrix:
+    """Embedding of the degree-q space of `coarse` into that of its uniform
+    refinement `fine` (fine cell c is child child[c] of coarse cell parent[c],
+    its frame the parent's): entry (g, G) is coarse basis function G at fine
+    DoF g, evaluated in the parent of a fine cell holding g at the reference
+    point (bits(child) + xi) / 2 (Section 2: transfers through the reference
+    cells, which makes them independent of the vertex positions)."""
+    d = fine.dim
+    gl = rules.gauss_lobatto_nodes(q)
+    cdf, cdc = fine.cell_dofs(q), coarse.cell_dofs(q)
+    rows, cols, vals = [], [], []
+    done = set()
+    for c in range(fine.nc):
+        P, k = int(parent[c]), int(child[c])
+        for li, m in enumerate(_lex(d, q + 1)):
+            g = int(cdf[c, li])
+            if g in done:
+                continue
+            done.add(g)
+            lx = [rules.lagrange(gl, np.array([(((k >> a) & 1) + gl[m[a]]) / 2.0]))[0] for a in range(d)]
+            for lj, mc in enumerate(_lex(d, q + 1)):
+                val = 1.0
+                for a in range(d):
+                    val *= lx[a][mc[a]]
+                if val != 0.0:
+                    rows.append(g)
+                    cols.append(int(cdc[P, lj]))
+                    vals.append(val)
+    return sp.coo_matrix((vals, (rows, cols)), shape=(fine.n_dofs(q), coarse.n_dofs(q))).tocsr()
+
+
+class TwoMeshLevels:
+    """Degree p on a fine mesh and on the coarse mesh it refines: one
+    multiplicative sweep on the fine mesh, the residual restricted by the
+    transposed h-embedding, the coarse mesh's two-level cycle (TwoLevel: its
+    sweep, its Q1 coarse space, its reversed sweep), the correction
+    prolongated, one sweep with the colours reversed: a symmetric
+    preconditioner for CG."""
+
+    def __init__(self, coarse: Mesh, fine: Mesh, parent, child, p: int, fine_smoother: PatchSmoother,
+                 coarse_smoother: PatchSmoother):
+        self.coarse, self.fine, self.p = coarse, fine, p
+        self.S = fine_smoother
+        self.TLc = TwoLevel(coarse, p, coarse_smoother)
+        self.free = ~fine.boundary_dofs(p)
+        self.A = fem.operator_with_dirichlet(fine.assemble(p), self.free)
+        freec = ~coarse.boundary_dofs(p)
+        Df = sp.diags(self.free.astype(float))
+        Dc = sp.diags(freec.astype(float))
+        self.P = (Df @ h_prolongation(coarse, fine, parent, child, p) @ Dc).tocsr()
+
+    def vcycle(self, b):
+        x = self.S.sweep(np.zeros_like(b), b, reverse=False)
+        r = b - self.A @ x
+        x = x + self.P @ self.TLc.vcycle(self.P.T @ r)
+        return self.S.sweep(x, b, reverse=True)

@@ -508,3 +508,58 @@ def make_unstructured_problem(u: UProblem):
     rng = np.random.default_rng(u.seed)
     kappa = 10.0 ** rng.uniform(-2.0, 2.0, len(C))
     return X, C, bnd, kappa
+
+
+def refine_unstructured(coords: np.ndarray, cells: np.ndarray):
+    """Uniform refinement of a quadrilateral / hexahedral mesh: every cell is cut
+    into 2^d children at the midpoints of its reference axes.  New vertices:
+    the old ones (same ids), then one per edge (sorted vertex pairs), one per
+    face in 3D (sorted vertex quadruples), one per cell, each at the average
+    of the entity's corners (the multilinear map's value there).  Child k of
+    cell P (bit a of k = upper half along axis a) has its corner c at the
+    reference point (bits(k) + bits(c)) / 2 of P, so its lexicographic frame is
+    P's.  Returns (coords, cells, parent, child_index) of the fine mesh, fine
+    cell 2^d P + k being child k of P."""
+    dim = coords.shape[1]
+    nv, nc, ncorner = len(coords), len(cells), 2 ** dim
+    edges, faces = {}, {}
+    for cv in cells:
+        for c in range(ncorner):
+            for a in range(dim):
+                if not (c >> a) & 1:
+                    edges.setdefault(tuple(sorted((int(cv[c]), int(cv[c | (1 << a)])))), None)
+        if dim == 3:
+            for a in range(3):
+                for side in (0, 1):
+                    faces.setdefault(tuple(sorted(int(cv[c]) for c in range(8) if ((c >> a) & 1) == side)), None)
+    ekeys, fkeys = sorted(edges), sorted(faces)
+    eid = {k: nv + i for i, k in enumerate(ekeys)}
+    fid = {k: nv + len(ekeys) + i for i, k in enumerate(fkeys)}
+    c0 = nv + len(ekeys) + len(fkeys)
+    out = [coords[i] for i in range(nv)]
+    out += [coords[list(k)].mean(axis=0) for k in ekeys]
+    out += [coords[list(k)].mean(axis=0) for k in fkeys]
+    out += [coords[cv].mean(axis=0) for cv in cells]
+
+    def point(P, t):
+        # the fine vertex at ternary reference position t (entries 0, 1, 2) of cell P
+        cv = cells[P]
+        mid = [a for a in range(dim) if t[a] == 1]
+        base = sum((t[a] // 2) << a for a in range(dim) if t[a] != 1)
+        corners = [int(cv[base | sum(((s >> i) & 1) << mid[i] for i in range(len(mid)))]) for s in range(2 ** len(mid))]
+        if not mid:
+            return corners[0]
+        if len(mid) == 1:
+            return eid[tuple(sorted(corners))]
+        if len(mid) == 2 and dim == 3:
+            return fid[tuple(sorted(corners))]
+        return c0 + P
+
+    fcells, parent, child = [], [], []
+    for P in range(nc):
+        for k in range(ncorner):
+            fcells.append([point(P, [((k >> a) & 1) + ((c >> a) & 1) for a in range(dim)]) for c in range(ncorner)])
+            parent.append(P)
+            child.append(k)
+    return np.array(out), np.array(fcells, dtype=np.int64), np.array(parent, dtype=np.int64), \
+        np.array(child, dtype=np.uint8)

@@ -218,3 +218,59 @@ def test_q1_embedding_and_two_level_cg():
         ref = np.zeros_like(b)
         ref[free] = spla.spsolve(T.A.tocsr()[free][:, free].tocsc(), b[free])
         assert np.linalg.norm(x - ref) < 1e-6 * np.linalg.norm(ref), name
+
+
+def _affine_mesh(dim, N, seed):
+    """A structured grid under a global affine map (every cell a
+    parallelogram / parallelepiped), cells listed in random orientations."""
+    sm, um = _structured_as_unstructured(dim, N, seed, perturb=0.0)
+    Amap = np.eye(dim) + 0.3 * np.random.default_rng(seed).uniform(-1, 1, (dim, dim))
+    return us.Mesh(dim, um.coords @ Amap.T, um.cells, np.full(um.nc, 1.7))
+
+
+@pytest.mark.parametrize("q", [1, 2, 3])
+def test_h_embedding_is_exact_on_linear_functions(q):
+    """On the unperturbed refinement of any Q1 mesh the geometry is nested:
+    a physically linear function is in both spaces and the embedding maps
+    its coarse interpolant to its fine one."""
+    for name, m in _meshes():
+        Xf, Cf, par, ch = inputs.refine_unstructured(m.coords, m.cells)
+        f = us.Mesh(m.dim, Xf, Cf, np.ones(len(Cf)))
+        P = us.h_prolongation(m, f, par, ch, q)
+        a = np.array([0.7, -0.4, 1.3][: m.dim])
+        uc = m.node_coords(q) @ a + 0.25
+        uf = f.node_coords(q) @ a + 0.25
+        assert np.abs(P @ uc - uf).max() <= 1e-12, name
+
+
+@pytest.mark.parametrize("dim,q", [(2, 2), (2, 3), (3, 2)])
+def test_h_galerkin_identity_on_affine_meshes(dim, q):
+    """Parallelogram cells and constant kappa: the coarse matrix equals
+    P^T A_fine P (exact quadrature, nested spaces)."""
+    m = _affine_mesh(dim, 3 if dim == 2 else 2, 5 + q)
+    Xf, Cf, par, ch = inputs.refine_unstructured(m.coords, m.cells)
+    f = us.Mesh(dim, Xf, Cf, np.full(len(Cf), 1.7))
+    P = us.h_prolongation(m, f, par, ch, q).toarray()
+    Ac, Af = m.assemble(q).toarray(), f.assemble(q).toarray()
+    assert np.abs(P.T @ Af @ P - Ac).max() <= 1e-11 * np.abs(Ac).max()
+
+
+def test_two_mesh_level_cycle_is_symmetric_and_preconditions_cg():
+    P0, T0 = inputs.triangulated_square(2, 3)
+    X, C = inputs.triangles_to_quads(P0, T0)
+    Xf, Cf, par, ch = inputs.refine_unstructured(X, C)
+    rng = np.random.default_rng(4)
+    mc = us.Mesh(2, X, C, 10.0 ** rng.uniform(-1, 1, len(C)))
+    mf = us.Mesh(2, Xf, Cf, np.repeat(mc.kappa, 4))
+    p = 3
+    H = us.TwoMeshLevels(mc, mf, par, ch, p,
+                         us.PatchSmoother(mf, p, bounds_fn=lz.lanczos_bounds_fn(seed=0)),
+                         us.PatchSmoother(mc, p, bounds_fn=lz.lanczos_bounds_fn(seed=0)))
+    free = H.free
+    x = rng.uniform(-1, 1, len(free)) * free
+    y = rng.uniform(-1, 1, len(free)) * free
+    assert abs(x @ H.vcycle(y) - y @ H.vcycle(x)) <= 1e-10 * abs(x @ H.vcycle(x))
+    from oracle import gmg
+    b = rng.uniform(-1, 1, len(free)) * free
+    _, it, hist = gmg.pcg(H.A, b, H.vcycle, 1e-8, 60)
+    assert hist[-1] <= 1e-8 and it < 30
