@@ -176,20 +176,29 @@ int pmg_mesh_structured(pmg_ctx* ctx, int dim, int N, int p, int n_levels,
  * setting of Section 2 without the Cartesian structure (the paper's vertex
  * patches on general meshes and its simplicial patches of 3 quadrilaterals /
  * 4 hexahedra, Section 3.2).  One mesh level: the patch smoother and the local
- * p-multigrid of Sections 2.1 and 3 act on degree p; the preconditioner of
- * pmg_solve_cg / pmg_solve_gmres / pmg_gmg_vcycle is two-level: a patch sweep,
- * the Q1 space of the same mesh as coarse space (operator re-evaluated with
- * the 2-point Gauss rule, dense Cholesky, at most 16384 free vertices), a
- * reverse sweep.
+ * p-multigrid of Sections 2.1 and 3 act on degree p.  Mesh levels are
+ * uploaded coarsest first (level 0, 1, ...); level l > 0 is the uniform
+ * refinement of level l - 1: parent_cell[c] is the level-(l-1) cell that fine
+ * cell c subdivides, child_index[c] its position (bit a: the upper half along
+ * reference axis a), and corner k of the child lies at the parent's reference
+ * point (bits(child) + bits(k)) / 2 (its frame is the parent's); every parent
+ * has its 2^dim children.  The preconditioner of pmg_solve_cg /
+ * pmg_solve_gmres / pmg_gmg_vcycle is the V-cycle over the levels (Section 2):
+ * a patch sweep, the residual restricted by the transposed h-embedding
+ * (per fine cell, through the reference cells), the next coarser level, the
+ * correction prolongated, a reverse sweep; on level 0 the coarse space is the
+ * Q1 space of that mesh (operator re-evaluated with the 2-point Gauss rule,
+ * dense Cholesky, at most 16384 free vertices).
  *
  * coords: n_vertices x dim doubles.  cell_vertices: n_cells x 2^dim vertex
  * ids, lexicographic corner order (corner c at the reference point whose k-th
  * coordinate is bit k of c), every cell positively oriented.
  * vertex_on_boundary: n_vertices flags or NULL (derived: the vertices of the
- * facets that belong to one cell).  level must be 0 and parent_cell,
- * child_index NULL (PMG_ERR_UNSUPPORTED otherwise).  Host arrays are copied.
- * Call pmg_set_degree before pmg_setup; kappa by pmg_coeff_upload (level 0,
- * default 1).  DoF numbering (pmg_get_dof_map): vertices by id; edges sorted
+ * facets that belong to one cell).  parent_cell and child_index are NULL on
+ * level 0 and given on finer levels (PMG_ERR_ARG otherwise).  Host arrays are
+ * copied.  Call pmg_set_degree before pmg_setup; kappa by pmg_coeff_upload
+ * per level (default: 1 on the finest level, the mean of the children on a
+ * coarser one).  DoF numbering (pmg_get_dof_map, finest level): vertices by id; edges sorted
  * by (smaller id, larger id), q - 1 nodes each from the smaller-id end; faces
  * sorted by their sorted vertex ids, (q - 1)^2 nodes in the frame of the
  * face's smallest-id corner (first axis toward its smaller-id face neighbour,

@@ -84,7 +84,8 @@ struct pmg_ctx {
   int plevels[8] = {0};
   std::vector<double> h_coords, h_kappa;
   std::vector<std::vector<double>> kappa_level;   // per-level coefficients from pmg_coeff_upload (empty: derived)
-  UMesh* um = nullptr;                             // unstructured mesh (pmg_mesh_upload), else NULL
+  UMesh* um = nullptr;                             // finest unstructured mesh (pmg_mesh_upload), else NULL
+  std::vector<UMesh*> umv;                         // unstructured meshes by level (0 = coarsest)
   std::vector<HLevel> L;
   bool mesh_ok = false, setup_ok = false;
   int* d_err = nullptr;
@@ -788,7 +789,7 @@ int pmg_destroy(pmg_ctx* ctx) {
   if (ctx->h_rr) cudaFreeHost(ctx->h_rr);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   if (ctx->ev_caller) cudaEventDestroy(ctx->ev_caller);
-  if (ctx->um) umesh_destroy(ctx->um);
+  for (UMesh* m : ctx->umv) umesh_destroy(m);
   delete ctx;
   return PMG_OK;
 }
@@ -860,11 +861,13 @@ int pmg_mesh_upload(pmg_ctx* ctx, int level, int dim, int64_t n_vertices, const 
                     const int64_t* cell_vertices, const uint8_t* vertex_on_boundary, const int64_t* parent_cell,
                     const uint8_t* child_index) {
   if (!ctx) return PMG_ERR_ARG;
-  if (ctx->mesh_ok) return fail(ctx, PMG_ERR_ARG, "mesh already uploaded");
-  if (level != 0 || parent_cell || child_index)
-    return fail(ctx, PMG_ERR_UNSUPPORTED,
-                "unstructured meshes: one mesh level (level 0, no parent cells); the coarse space is the Q1 space "
-                "of the same mesh");
+  if (ctx->setup_ok) return fail(ctx, PMG_ERR_ARG, "already set up");
+  if (ctx->mesh_ok && !ctx->um) return fail(ctx, PMG_ERR_ARG, "a structured mesh was uploaded");
+  const int have = (int)ctx->umv.size();
+  if (level != have) return fail(ctx, PMG_ERR_ARG, "upload the mesh levels in order, coarsest (level 0) first");
+  if (level >= 16) return fail(ctx, PMG_ERR_UNSUPPORTED, "at most 16 mesh levels");
+  if ((level == 0) != (parent_cell == nullptr) || (level == 0) != (child_index == nullptr))
+    return fail(ctx, PMG_ERR_ARG, "parent_cell and child_index: NULL on level 0, given on finer levels");
   if ((dim != 2 && dim != 3) || n_vertices < 1 || n_cells < 1 || !coords || !cell_vertices)
     return fail(ctx, PMG_ERR_ARG, "bad mesh arguments");
   if (n_vertices > INT32_MAX || n_cells > INT32_MAX) return fail(ctx, PMG_ERR_UNSUPPORTED, "mesh too large");
@@ -874,9 +877,14 @@ int pmg_mesh_upload(pmg_ctx* ctx, int level, int dim, int64_t n_vertices, const 
   std::string msg;
   UMesh* m = umesh_create(dim, n_vertices, coords, n_cells, cell_vertices, vertex_on_boundary, &msg);
   if (!m) return fail(ctx, PMG_ERR_ARG, msg);
+  if (level > 0 && umesh_set_parent(m, ctx->umv[level - 1], parent_cell, child_index, &msg)) {
+    umesh_destroy(m);
+    return fail(ctx, PMG_ERR_ARG, msg);
+  }
+  ctx->umv.push_back(m);
   ctx->um = m;
   ctx->dim = dim;
-  ctx->nlev = 1;
+  ctx->nlev = level + 1;
   ctx->N = 0;
   ctx->mesh_ok = true;
   return PMG_OK;
@@ -891,7 +899,7 @@ int pmg_get_dof_map(pmg_ctx* ctx, int k, int32_t* out) {
 
 int pmg_local_size(const pmg_ctx* ctx, int level, int64_t* n) {
   if (!ctx || !n || !ctx->setup_ok || level < 0 || level >= ctx->nlev) return PMG_ERR_ARG;
-  *n = ctx->um ? umesh_interior_max(ctx->um) : (int64_t)ipow_sz(2 * ctx->p - 1, ctx->dim);
+  *n = ctx->um ? umesh_interior_max(ctx->umv[level]) : (int64_t)ipow_sz(2 * ctx->p - 1, ctx->dim);
   return PMG_OK;
 }
 
@@ -901,7 +909,7 @@ int pmg_coeff_upload(pmg_ctx* ctx, int level, const double* kappa) {
   if (ctx->setup_ok) return fail(ctx, PMG_ERR_ARG, "coefficients must be uploaded before pmg_setup");
   if (level < 0 || level >= ctx->nlev || !kappa) return fail(ctx, PMG_ERR_ARG, "bad level or null array");
   if (ctx->um) {
-    if (umesh_set_kappa(ctx->um, kappa)) return fail(ctx, PMG_ERR_ARG, "kappa must be positive and finite");
+    if (umesh_set_kappa(ctx->umv[level], kappa)) return fail(ctx, PMG_ERR_ARG, "kappa must be positive and finite");
     return PMG_OK;
   }
   const size_t nc = ipow_sz(ctx->N >> (ctx->nlev - 1 - level), ctx->dim);
@@ -943,12 +951,20 @@ int pmg_setup(pmg_ctx* ctx) {
     o.fixed_lo = ctx->opt.fixed_lo;
     o.fixed_hi = ctx->opt.fixed_hi;
     o.seed = ctx->opt.seed;
-    CU(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s));
-    std::string msg;
-    const int ust = umesh_setup(ctx->um, ctx->p, o, s, ctx->d_err, &msg);
-    if (ust == ST_DEGENERATE) return fail(ctx, PMG_ERR_DEGENERATE, msg);
-    if (ust == ST_UNSUPPORTED) return fail(ctx, PMG_ERR_UNSUPPORTED, msg);
-    if (ust) return fail(ctx, PMG_ERR_CUDA, msg.empty() ? "unstructured set-up failed" : msg);
+    // a coarser mesh without a coefficient of its own takes the mean of its children's
+    for (int l = ctx->nlev - 2; l >= 0; --l)
+      if (!umesh_kappa_given(ctx->umv[l])) umesh_kappa_from_children(ctx->umv[l], ctx->umv[l + 1]);
+    for (int l = 0; l < ctx->nlev; ++l) {
+      CU(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s));
+      std::string msg;
+      o.coarse_space = l == 0;                       // the Q1 space of the coarsest mesh only
+      int ust = umesh_setup(ctx->umv[l], ctx->p, o, s, ctx->d_err, &msg);
+      if (!ust && l > 0) ust = umesh_link(ctx->umv[l], s, &msg);
+      if (ust == ST_DEGENERATE) return fail(ctx, PMG_ERR_DEGENERATE, msg);
+      if (ust == ST_UNSUPPORTED) return fail(ctx, PMG_ERR_UNSUPPORTED, msg);
+      if (ust == ST_ARG) return fail(ctx, PMG_ERR_ARG, msg);
+      if (ust) return fail(ctx, PMG_ERR_CUDA, msg.empty() ? "unstructured set-up failed" : msg);
+    }
     const size_t n = (size_t)umesh_ndofs(ctx->um);
     DALLOC(ctx->cg_x, n);
     DALLOC(ctx->cg_r, n);
@@ -959,9 +975,10 @@ int pmg_setup(pmg_ctx* ctx) {
     DALLOC(ctx->stage_u, n);
     DALLOC(ctx->partial, DOT_BLOCKS);
     DALLOC(ctx->scal, S_NSLOT);
-    if (ctx->opt.bounds == PMG_BOUNDS_LANCZOS &&
-        umesh_lanczos(ctx->um, ctx->opt.lanczos_steps, ctx->opt.seed, ctx->opt.bound_safety, ctx->opt.bound_ratio, s))
-      return fail(ctx, PMG_ERR_CUDA, "unstructured Lanczos intervals failed");
+    if (ctx->opt.bounds == PMG_BOUNDS_LANCZOS)
+      for (UMesh* m : ctx->umv)
+        if (umesh_lanczos(m, ctx->opt.lanczos_steps, ctx->opt.seed, ctx->opt.bound_safety, ctx->opt.bound_ratio, s))
+          return fail(ctx, PMG_ERR_CUDA, "unstructured Lanczos intervals failed");
     ctx->setup_ok = true;
     CU(cudaStreamSynchronize(s));
     return PMG_OK;
@@ -1237,18 +1254,21 @@ int pmg_compute_bounds(pmg_ctx* ctx, int source) {
     if (source == PMG_BOUNDS_LANCZOS) {
       if (ctx->opt.lanczos_steps < 1 || ctx->opt.lanczos_steps > 64)
         return fail(ctx, PMG_ERR_ARG, "lanczos_steps must be in 1..64");
-      return umesh_lanczos(ctx->um, ctx->opt.lanczos_steps, ctx->opt.seed, ctx->opt.bound_safety,
-                           ctx->opt.bound_ratio, ctx->stream)
-                 ? fail(ctx, PMG_ERR_CUDA, "unstructured Lanczos intervals failed")
-                 : PMG_OK;
+      for (UMesh* m : ctx->umv)
+        if (umesh_lanczos(m, ctx->opt.lanczos_steps, ctx->opt.seed, ctx->opt.bound_safety, ctx->opt.bound_ratio,
+                          ctx->stream))
+          return fail(ctx, PMG_ERR_CUDA, "unstructured Lanczos intervals failed");
+      return PMG_OK;
     }
     if (source != PMG_BOUNDS_FIXED)
       return fail(ctx, PMG_ERR_UNSUPPORTED, "unstructured meshes: Lanczos, fixed or user-given Chebyshev intervals");
-    const size_t np = (size_t)umesh_npatch(ctx->um);
-    std::vector<double> v(2 * np);
-    for (size_t j = 0; j < np; ++j) { v[2 * j] = ctx->opt.fixed_lo; v[2 * j + 1] = ctx->opt.fixed_hi; }
-    for (int k = 0; k < ctx->npl; ++k)
-      if (ctx->plevels[k] > 1 && umesh_set_bounds(ctx->um, k, v.data())) return fail(ctx, PMG_ERR_CUDA, "bounds");
+    for (UMesh* m : ctx->umv) {
+      const size_t np = (size_t)umesh_npatch(m);
+      std::vector<double> v(2 * np);
+      for (size_t j = 0; j < np; ++j) { v[2 * j] = ctx->opt.fixed_lo; v[2 * j + 1] = ctx->opt.fixed_hi; }
+      for (int k = 0; k < ctx->npl; ++k)
+        if (ctx->plevels[k] > 1 && umesh_set_bounds(m, k, v.data())) return fail(ctx, PMG_ERR_CUDA, "bounds");
+    }
     return PMG_OK;
   }
   cudaStream_t s = ctx->stream;
@@ -1353,8 +1373,8 @@ int pmg_num_dofs(const pmg_ctx* ctx, int level, int64_t* total, int64_t* n_free)
   if (!ctx || !ctx->mesh_ok || level < 0 || level >= ctx->nlev) return PMG_ERR_ARG;
   if (ctx->um) {
     if (!ctx->setup_ok) return PMG_ERR_ARG;
-    if (total) *total = umesh_ndofs(ctx->um);
-    if (n_free) *n_free = umesh_nfree(ctx->um);
+    if (total) *total = umesh_ndofs(ctx->umv[level]);
+    if (n_free) *n_free = umesh_nfree(ctx->umv[level]);
     return PMG_OK;
   }
   const int Nl = ctx->N >> (ctx->nlev - 1 - level);
@@ -1367,8 +1387,8 @@ int pmg_num_patches(const pmg_ctx* ctx, int level, int64_t* n_patches, int* n_co
   if (!ctx || !ctx->mesh_ok || level < 0 || level >= ctx->nlev) return PMG_ERR_ARG;
   if (ctx->um) {
     if (!ctx->setup_ok) return PMG_ERR_ARG;
-    if (n_patches) *n_patches = umesh_npatch(ctx->um);
-    if (n_colours) *n_colours = umesh_ncolours(ctx->um);
+    if (n_patches) *n_patches = umesh_npatch(ctx->umv[level]);
+    if (n_colours) *n_colours = umesh_ncolours(ctx->umv[level]);
     return PMG_OK;
   }
   const int Nl = ctx->N >> (ctx->nlev - 1 - level);
@@ -1397,7 +1417,7 @@ int pmg_apply(pmg_ctx* ctx, int level, const double* u, double* Au, void* stream
   if (st) return st;
   PMG_GUARD_CTX(ctx);
   if (!u || !Au) return fail(ctx, PMG_ERR_ARG, "null vector");
-  if (ctx->um) return umesh_apply(ctx->um, u, Au, (cudaStream_t)stream) ? fail(ctx, PMG_ERR_CUDA, "apply failed") : PMG_OK;
+  if (ctx->um) return umesh_apply(ctx->umv[level], u, Au, (cudaStream_t)stream) ? fail(ctx, PMG_ERR_CUDA, "apply failed") : PMG_OK;
   HLevel& h = ctx->L[level];
   LK(1 + (1 << ctx->dim), cell_apply<double>(ctx, ctx->p, u, Au, h.pl[0].G64, h.N, (cudaStream_t)stream));
   return PMG_OK;
@@ -1409,8 +1429,8 @@ int pmg_patch_smooth_colour(pmg_ctx* ctx, int level, int colour, const double* b
   PMG_GUARD_CTX(ctx);
   if (!b || !u) return fail(ctx, PMG_ERR_ARG, "null vector");
   if (ctx->um) {
-    if (colour < 0 || colour >= umesh_ncolours(ctx->um)) return fail(ctx, PMG_ERR_ARG, "colour out of range");
-    return umesh_sweep_colour(ctx->um, colour, b, u, (cudaStream_t)stream) ? fail(ctx, PMG_ERR_CUDA, "sweep failed")
+    if (colour < 0 || colour >= umesh_ncolours(ctx->umv[level])) return fail(ctx, PMG_ERR_ARG, "colour out of range");
+    return umesh_sweep_colour(ctx->umv[level], colour, b, u, (cudaStream_t)stream) ? fail(ctx, PMG_ERR_CUDA, "sweep failed")
                                                                            : PMG_OK;
   }
   if (colour < 0 || colour >= (1 << ctx->dim)) return fail(ctx, PMG_ERR_ARG, "colour out of range");
@@ -1435,7 +1455,7 @@ int pmg_patch_smooth(pmg_ctx* ctx, int level, const double* b, double* u, int n_
   if (!b || !u || n_sweeps < 0) return fail(ctx, PMG_ERR_ARG, "bad arguments");
   cudaStream_t s = (cudaStream_t)stream;
   if (ctx->um)
-    return umesh_sweep(ctx->um, b, u, n_sweeps, reverse != 0, s) ? fail(ctx, PMG_ERR_CUDA, "sweep failed") : PMG_OK;
+    return umesh_sweep(ctx->umv[level], b, u, n_sweeps, reverse != 0, s) ? fail(ctx, PMG_ERR_CUDA, "sweep failed") : PMG_OK;
   HLevel& h = ctx->L[level];
   // a persistent level's barrier status is read here, so the call waits for its stream
   const bool wait = level < 16 && ctx->level_persist[level] && n_sweeps > 0;
@@ -1468,8 +1488,8 @@ int pmg_local_vcycle(pmg_ctx* ctx, int level, int64_t n, const int64_t* ids, con
   if (n < 0 || (n > 0 && (!ids || !r || !dout)) || n_cycles < 1) return fail(ctx, PMG_ERR_ARG, "bad arguments");
   if (n == 0) return PMG_OK;
   if (ctx->um) {
-    if (n > umesh_npatch(ctx->um)) return fail(ctx, PMG_ERR_ARG, "more patches than the level has");
-    return umesh_local(ctx->um, n, ids, r, dout, n_cycles, (cudaStream_t)stream) ? fail(ctx, PMG_ERR_CUDA, "local solve failed")
+    if (n > umesh_npatch(ctx->umv[level])) return fail(ctx, PMG_ERR_ARG, "more patches than the level has");
+    return umesh_local(ctx->umv[level], n, ids, r, dout, n_cycles, (cudaStream_t)stream) ? fail(ctx, PMG_ERR_CUDA, "local solve failed")
                                                                                  : PMG_OK;
   }
   HLevel& h = ctx->L[level];
@@ -1503,12 +1523,12 @@ int pmg_get_bounds(pmg_ctx* ctx, int level, double* lohi) {
   if (st) return st;
   PMG_GUARD_CTX(ctx);
   if (ctx->um) {
-    const size_t np = (size_t)umesh_npatch(ctx->um);
+    const size_t np = (size_t)umesh_npatch(ctx->umv[level]);
     std::vector<double> out(2 * np * ctx->npl, 0.0), tmp(2 * np);
     CU(cudaStreamSynchronize(ctx->stream));
     for (int k = 0; k < ctx->npl; ++k) {
       if (ctx->plevels[k] == 1 || np == 0) continue;
-      if (umesh_get_bounds(ctx->um, k, tmp.data())) return fail(ctx, PMG_ERR_CUDA, "bounds copy failed");
+      if (umesh_get_bounds(ctx->umv[level], k, tmp.data())) return fail(ctx, PMG_ERR_CUDA, "bounds copy failed");
       for (size_t j = 0; j < np; ++j) {
         out[(j * ctx->npl + k) * 2] = tmp[2 * j];
         out[(j * ctx->npl + k) * 2 + 1] = tmp[2 * j + 1];
@@ -1537,12 +1557,12 @@ int pmg_get_ritz(pmg_ctx* ctx, int level, double* tm) {
   if (st) return st;
   PMG_GUARD_CTX(ctx);
   if (ctx->um) {
-    const size_t np = (size_t)umesh_npatch(ctx->um);
+    const size_t np = (size_t)umesh_npatch(ctx->umv[level]);
     std::vector<double> out(2 * np * ctx->npl, 0.0), tmp(2 * np);
     CU(cudaStreamSynchronize(ctx->stream));
     for (int k = 0; k < ctx->npl; ++k) {
       if (ctx->plevels[k] == 1 || np == 0) continue;
-      if (umesh_get_ritz(ctx->um, k, tmp.data())) return fail(ctx, PMG_ERR_CUDA, "copy failed");
+      if (umesh_get_ritz(ctx->umv[level], k, tmp.data())) return fail(ctx, PMG_ERR_CUDA, "copy failed");
       for (size_t j = 0; j < np; ++j) {
         out[(j * ctx->npl + k) * 2] = tmp[2 * j];
         out[(j * ctx->npl + k) * 2 + 1] = tmp[2 * j + 1];
@@ -1571,7 +1591,7 @@ int pmg_set_bounds(pmg_ctx* ctx, int level, const double* lohi) {
   if (st) return st;
   PMG_GUARD_CTX(ctx);
   if (ctx->um) {
-    const size_t np = (size_t)umesh_npatch(ctx->um);
+    const size_t np = (size_t)umesh_npatch(ctx->umv[level]);
     std::vector<double> tmp(2 * np);
     CU(cudaStreamSynchronize(ctx->stream));
     for (int k = 0; k < ctx->npl; ++k) {
@@ -1582,7 +1602,7 @@ int pmg_set_bounds(pmg_ctx* ctx, int level, const double* lohi) {
         tmp[2 * j] = lo;
         tmp[2 * j + 1] = hi;
       }
-      if (umesh_set_bounds(ctx->um, k, tmp.data())) return fail(ctx, PMG_ERR_CUDA, "bounds copy failed");
+      if (umesh_set_bounds(ctx->umv[level], k, tmp.data())) return fail(ctx, PMG_ERR_CUDA, "bounds copy failed");
     }
     return PMG_OK;
   }
@@ -2006,7 +2026,7 @@ int pmg_rhs_manufactured(pmg_ctx* ctx, double* b, void* stream) {
 
 int pmg_get_colours(const pmg_ctx* ctx, int level, uint8_t* out) {
   if (!ctx || !ctx->setup_ok || level < 0 || level >= ctx->nlev || !out) return PMG_ERR_ARG;
-  if (ctx->um) return umesh_colours(ctx->um, out) ? PMG_ERR_ARG : PMG_OK;
+  if (ctx->um) return umesh_colours(ctx->umv[level], out) ? PMG_ERR_ARG : PMG_OK;
   const HLevel& h = ctx->L[level];
   std::memcpy(out, h.colours.data(), h.npatch);
   return PMG_OK;
@@ -2014,7 +2034,7 @@ int pmg_get_colours(const pmg_ctx* ctx, int level, uint8_t* out) {
 
 int pmg_get_patch_map(const pmg_ctx* ctx, int level, int64_t* out) {
   if (!ctx || !ctx->setup_ok || level < 0 || level >= ctx->nlev || !out) return PMG_ERR_ARG;
-  if (ctx->um) return umesh_patches(ctx->um, out, 1 + PMG_UMAXC) ? PMG_ERR_ARG : PMG_OK;
+  if (ctx->um) return umesh_patches(ctx->umv[level], out, 1 + PMG_UMAXC) ? PMG_ERR_ARG : PMG_OK;
   const HLevel& h = ctx->L[level];
   const int d = ctx->dim, Nl = h.N, Nv = Nl - 1;
   const size_t Mg = (size_t)ctx->p * Nl + 1;

@@ -10,11 +10,123 @@
 #include <string>
 #include <vector>
 
+#include "basis.h"
 #include "umesh_kern.cuh"
 #include "umesh.h"
 #include "utopo.h"
 
 namespace pmg {
+
+// ------------------------------------------------------ h-transfers between meshes
+// The fine mesh is the uniform refinement of the coarse one and a fine cell
+// lies in its parent's reference frame, so the embedding is, per fine cell,
+// the tensor product of the 1D half-interval interpolations
+// H[b][a][m] = l_m((b + xi_a) / 2) (degree q, Gauss-Lobatto nodes xi), b the
+// child's bit along the axis: d one-dimensional passes over the cell.
+
+// one pass along axis `ax` of the (q+1)^d cell array: out = H_b (TRANS: H_b^T) in
+template <int DIM, bool TRANS, typename T>
+__device__ void uh_pass(const T* in, T* out, const double* __restrict__ H, int child, int ax, int n) {
+  int s = 1;
+  for (int k = 0; k < ax; ++k) s *= n;
+  int nl = 1;
+  for (int k = 0; k < DIM; ++k) nl *= n;
+  const double* Hb = H + ((child >> ax) & 1) * n * n;
+  for (int e = threadIdx.x; e < nl; e += blockDim.x) {
+    const int lo = e % s, o = (e / s) % n, hi = e / (s * n);
+    T acc = T(0);
+    for (int j = 0; j < n; ++j) {
+      const T h = TRANS ? T(Hb[j * n + o]) : T(Hb[o * n + j]);
+      acc += h * in[lo + s * (j + n * hi)];
+    }
+    out[e] = acc;
+  }
+  __syncthreads();
+}
+
+// Y[c][l] = (embedded parent values) at fine node l of cell c
+template <int DIM, typename T>
+__global__ void __launch_bounds__(128) k_uh_prolong_cells(const T* __restrict__ xc, const int32_t* __restrict__ cdofs_c,
+                                                          const int32_t* __restrict__ parent,
+                                                          const uint8_t* __restrict__ child, int64_t nc, int q,
+                                                          const double* __restrict__ H, T* __restrict__ Y) {
+  const int n = q + 1;
+  const int nl = DIM == 3 ? n * n * n : n * n;
+  T* a = reinterpret_cast<T*>(pmg_smem);
+  T* b = a + nl;
+  for (int64_t c = blockIdx.x; c < nc; c += gridDim.x) {
+    const int32_t P = parent[c];
+    const int k = child[c];
+    for (int e = threadIdx.x; e < nl; e += blockDim.x) a[e] = xc[cdofs_c[(size_t)P * nl + e]];
+    __syncthreads();
+    uh_pass<DIM, false>(a, b, H, k, 0, n);
+    uh_pass<DIM, false>(b, a, H, k, 1, n);
+    const T* res = a;
+    if (DIM == 3) {
+      uh_pass<DIM, false>(a, b, H, k, 2, n);
+      res = b;
+    }
+    for (int e = threadIdx.x; e < nl; e += blockDim.x) Y[(size_t)c * nl + e] = res[e];
+    __syncthreads();
+  }
+}
+
+// Yc[c][m] = sum_l H^T (fine residual at l / number of cells holding it)
+template <int DIM, typename T>
+__global__ void __launch_bounds__(128) k_uh_restrict_cells(const T* __restrict__ rf, const int32_t* __restrict__ cdofs_f,
+                                                           const int32_t* __restrict__ dstart_f,
+                                                           const uint8_t* __restrict__ bnd_f,
+                                                           const uint8_t* __restrict__ child, int64_t nc, int q,
+                                                           const double* __restrict__ H, T* __restrict__ Yc) {
+  const int n = q + 1;
+  const int nl = DIM == 3 ? n * n * n : n * n;
+  T* a = reinterpret_cast<T*>(pmg_smem);
+  T* b = a + nl;
+  for (int64_t c = blockIdx.x; c < nc; c += gridDim.x) {
+    const int k = child[c];
+    for (int e = threadIdx.x; e < nl; e += blockDim.x) {
+      const int32_t g = cdofs_f[(size_t)c * nl + e];
+      a[e] = bnd_f[g] ? T(0) : rf[g] / T(dstart_f[g + 1] - dstart_f[g]);
+    }
+    __syncthreads();
+    uh_pass<DIM, true>(a, b, H, k, 0, n);
+    uh_pass<DIM, true>(b, a, H, k, 1, n);
+    const T* res = a;
+    if (DIM == 3) {
+      uh_pass<DIM, true>(a, b, H, k, 2, n);
+      res = b;
+    }
+    for (int e = threadIdx.x; e < nl; e += blockDim.x) Yc[(size_t)c * nl + e] = res[e];
+    __syncthreads();
+  }
+}
+
+// xf[g] += Y at the first (cell, node) entry of fine DoF g (0 on Dirichlet DoFs)
+template <typename T>
+__global__ void k_uh_add_first(const T* __restrict__ Y, const int32_t* __restrict__ dstart,
+                               const int32_t* __restrict__ dlist, const uint8_t* __restrict__ bnd, int64_t n,
+                               T* __restrict__ xf) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x)
+    if (!bnd[g]) xf[g] += Y[dlist[dstart[g]]];
+}
+
+// rc[G] = sum over the (coarse cell, node) entries of G and the cell's children
+// of Yc (fixed order); 0 on Dirichlet DoFs
+template <typename T>
+__global__ void k_uh_assemble_coarse(const T* __restrict__ Yc, const int32_t* __restrict__ dstart_c,
+                                     const int32_t* __restrict__ dlist_c, const int32_t* __restrict__ children,
+                                     const uint8_t* __restrict__ bnd_c, int64_t n, int nl, int nch,
+                                     T* __restrict__ rc) {
+  for (int64_t G = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; G < n; G += (int64_t)gridDim.x * blockDim.x) {
+    T s = T(0);
+    if (!bnd_c[G])
+      for (int e = dstart_c[G]; e < dstart_c[G + 1]; ++e) {
+        const int32_t P = dlist_c[e] / nl, m = dlist_c[e] - P * nl;
+        for (int j = 0; j < nch; ++j) s += Yc[(size_t)children[(size_t)P * nch + j] * nl + m];
+      }
+    rc[G] = s;
+  }
+}
 
 // ------------------------------------------------------------------ host side
 struct ULevelD {
@@ -68,6 +180,14 @@ struct UMesh {
   int yoff = 0;
   int* err = nullptr;
   int64_t launches = 0;
+  bool kappa_given = false;
+  // mesh hierarchy: this mesh refines `coarser` (NULL on the coarsest mesh)
+  UMesh* coarser = nullptr;
+  std::vector<int32_t> h_parent, h_children;   // [nc] parents; [coarser->nc][2^d] children
+  std::vector<uint8_t> h_child;
+  int32_t *d_parent = nullptr, *d_children = nullptr;
+  uint8_t* d_child = nullptr;
+  double* d_H = nullptr;                        // [2][q+1][q+1] half-interval interpolation, degree p
   std::vector<void*> allocs;
   ~UMesh() {
     for (void* q : allocs) cudaFree(q);
@@ -125,6 +245,50 @@ int umesh_set_kappa(UMesh* m, const double* kappa) {
   for (int64_t c = 0; c < m->nc; ++c)
     if (!std::isfinite(kappa[c]) || !(kappa[c] > 0)) return ST_ARG;
   m->h_kappa.assign(kappa, kappa + m->nc);
+  m->kappa_given = true;
+  return ST_OK;
+}
+
+bool umesh_kappa_given(const UMesh* m) { return m->kappa_given; }
+int64_t umesh_ncells(const UMesh* m) { return m->nc; }
+
+int umesh_set_parent(UMesh* fine, UMesh* coarse, const int64_t* parent, const uint8_t* child, std::string* msg) {
+  const int nch = 1 << fine->dim;
+  if (coarse->dim != fine->dim) {
+    *msg = "the meshes of a hierarchy have one dimension";
+    return ST_ARG;
+  }
+  if (fine->nc != coarse->nc * nch) {
+    *msg = "a refined mesh has 2^dim cells per coarse cell";
+    return ST_ARG;
+  }
+  std::vector<int32_t> ch((size_t)coarse->nc * nch, -1);
+  for (int64_t c = 0; c < fine->nc; ++c) {
+    const int64_t P = parent[c];
+    const int k = child[c];
+    if (P < 0 || P >= coarse->nc || k >= nch || ch[(size_t)P * nch + k] >= 0) {
+      *msg = "parent_cell / child_index: every coarse cell needs its 2^dim children, each child index once";
+      return ST_ARG;
+    }
+    ch[(size_t)P * nch + k] = (int32_t)c;
+  }
+  fine->coarser = coarse;
+  fine->h_parent.assign(fine->nc, 0);
+  fine->h_child.assign(child, child + fine->nc);
+  for (int64_t c = 0; c < fine->nc; ++c) fine->h_parent[c] = (int32_t)parent[c];
+  fine->h_children = ch;
+  return ST_OK;
+}
+
+int umesh_kappa_from_children(UMesh* coarse, const UMesh* fine) {
+  const int nch = 1 << fine->dim;
+  std::vector<double> k(coarse->nc, 0.0);
+  for (int64_t P = 0; P < coarse->nc; ++P) {
+    double s = 0.0;
+    for (int j = 0; j < nch; ++j) s += fine->h_kappa[fine->h_children[(size_t)P * nch + j]];
+    k[P] = s / nch;
+  }
+  coarse->h_kappa = k;
   return ST_OK;
 }
 
@@ -468,7 +632,7 @@ int umesh_setup(UMesh* m, int p, const UOptions& o, cudaStream_t s, int* err_dev
     UCK(m->alloc(&m->x1_32, m->nv));
   }
   // coarse Q1 space: dense inverse of the Q1 operator on the free vertices
-  {
+  if (o.coarse_space) {
     const int k1 = m->npl - 1;                      // the q = 1 level
     const ULevelD& L1 = m->L[k1];
     std::vector<int> fidx;
@@ -523,7 +687,11 @@ int umesh_nplevels(const UMesh* m, int* q) {
   for (int k = 0; k < m->npl; ++k) q[k] = m->L[k].q;
   return m->npl;
 }
-int64_t umesh_kernel_launches(const UMesh* m) { return m->launches; }
+int64_t umesh_kernel_launches(const UMesh* m) {
+  int64_t n = 0;
+  for (const UMesh* x = m; x; x = x->coarser) n += x->launches;   // the chain's V-cycle launches them all
+  return n;
+}
 int64_t umesh_interior_max(const UMesh* m) { return m->L[0].nimax; }
 int umesh_max_valence(const UMesh* m) {
   int v = 0;
@@ -732,17 +900,89 @@ static int uvcycle_T(UMesh* m, const T* b, T* x, T* r, T* Y, T* r1, T* x1, cudaS
   return usweep_T<T>(m, b, x, true, s);                     // post-smoothing, colours reversed
 }
 
+// the work vectors of a mesh in precision T
+template <typename T>
+struct UVec {
+  T *x, *b, *r, *Y, *r1, *x1;
+};
+template <typename T>
+UVec<T> uvec(UMesh* m);
+template <>
+UVec<double> uvec<double>(UMesh* m) { return {m->x64, m->b64, m->r64, m->Y64, m->r1_64, m->x1_64}; }
+template <>
+UVec<float> uvec<float>(UMesh* m) { return {m->x32, m->b32, m->r32, m->Y32, m->r1_32, m->x1_32}; }
+
+int umesh_link(UMesh* m, cudaStream_t s, std::string* msg) {
+  if (!m->coarser) return ST_OK;
+  const UMesh* c = m->coarser;
+  if (c->p != m->p || c->opt.precision != m->opt.precision) {
+    *msg = "the meshes of a hierarchy share the degree and the precision";
+    return ST_ARG;
+  }
+  const int q = m->p, n = q + 1;
+  const std::vector<double> xi = gauss_lobatto(q);
+  std::vector<double> H(2 * n * n);
+  for (int b = 0; b < 2; ++b) {
+    std::vector<double> pts(n);
+    for (int a = 0; a < n; ++a) pts[a] = 0.5 * (b + xi[a]);
+    const auto L = lagrange_matrix(xi, pts);          // L[a][mm] = l_mm(pts_a)
+    for (int a = 0; a < n; ++a)
+      for (int mm = 0; mm < n; ++mm) H[(b * n + a) * n + mm] = L[a][mm];
+  }
+  UCK(m->upload(&m->d_H, H));
+  UCK(m->upload(&m->d_parent, m->h_parent));
+  UCK(m->upload(&m->d_child, m->h_child));
+  UCK(m->upload(&m->d_children, m->h_children));
+  (void)s;
+  return ST_OK;
+}
+
+// the V-cycle over the chain of meshes ending at m: x = B b in precision T
+template <typename T>
+static int uvcycle_chain_T(UMesh* m, const T* b, T* x, cudaStream_t s) {
+  UVec<T> v = uvec<T>(m);
+  if (!m->coarser) return uvcycle_T<T>(m, b, x, v.r, v.Y, v.r1, v.x1, s);
+  UMesh* c = m->coarser;
+  UVec<T> vc = uvec<T>(c);
+  const ULevelD& L0 = m->L[0];
+  const ULevelD& C0 = c->L[0];
+  const size_t n = (size_t)L0.ndofs;
+  const int q = L0.q, nl = L0.nloc, nch = 1 << m->dim;
+  const int grid = (int)std::min<int64_t>(m->nc, 152 * 16);
+  const size_t sm = 2 * (size_t)nl * sizeof(T);
+  UCK(launch_fill<T>(x, n, T(0), s));
+  UCK(usweep_T<T>(m, b, x, false, s));                     // pre-smoothing on this mesh
+  UCK(uglobal_apply<T>(m, 0, x, v.r, v.Y, s));              // r = b - A x
+  UCK(launch_sub_from<T>(b, v.r, n, s));
+  if (m->dim == 2)                                          // restriction to the coarser mesh
+    k_uh_restrict_cells<2, T><<<grid, 128, sm, s>>>(v.r, L0.cdofs, L0.dstart, L0.bnd, m->d_child, m->nc, q, m->d_H, v.Y);
+  else
+    k_uh_restrict_cells<3, T><<<grid, 128, sm, s>>>(v.r, L0.cdofs, L0.dstart, L0.bnd, m->d_child, m->nc, q, m->d_H, v.Y);
+  k_uh_assemble_coarse<T><<<grid_for((size_t)C0.ndofs, 256), 256, 0, s>>>(v.Y, C0.dstart, C0.dlist, m->d_children,
+                                                                          C0.bnd, C0.ndofs, nl, nch, vc.b);
+  UCU(cudaPeekAtLastError());
+  UCK(uvcycle_chain_T<T>(c, vc.b, vc.x, s));                // the coarser meshes
+  if (m->dim == 2)                                          // prolongation of the correction
+    k_uh_prolong_cells<2, T><<<grid, 128, sm, s>>>(vc.x, C0.cdofs, m->d_parent, m->d_child, m->nc, q, m->d_H, v.Y);
+  else
+    k_uh_prolong_cells<3, T><<<grid, 128, sm, s>>>(vc.x, C0.cdofs, m->d_parent, m->d_child, m->nc, q, m->d_H, v.Y);
+  k_uh_add_first<T><<<grid_for(n, 256), 256, 0, s>>>(v.Y, L0.dstart, L0.dlist, L0.bnd, L0.ndofs, x);
+  UCU(cudaPeekAtLastError());
+  m->launches += 4;
+  return usweep_T<T>(m, b, x, true, s);                     // post-smoothing, colours reversed
+}
+
 int umesh_precondition(UMesh* m, const double* r, double* z, cudaStream_t s) {
   const size_t n = (size_t)m->L[0].ndofs;
   if (m->opt.precision == PMG_PREC_MIXED) {
     UCK(launch_cast_d2f(r, m->b32, n, s));
-    UCK(uvcycle_T<float>(m, m->b32, m->x32, m->r32, m->Y32, m->r1_32, m->x1_32, s));
+    UCK(uvcycle_chain_T<float>(m, m->b32, m->x32, s));
     UCK(launch_cast_f2d(m->x32, z, n, s));
     m->launches += 2;
     return ST_OK;
   }
   UCU(cudaMemcpyAsync(m->b64, r, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  UCK(uvcycle_T<double>(m, m->b64, m->x64, m->r64, m->Y64, m->r1_64, m->x1_64, s));
+  UCK(uvcycle_chain_T<double>(m, m->b64, m->x64, s));
   UCU(cudaMemcpyAsync(z, m->x64, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   return ST_OK;
 }

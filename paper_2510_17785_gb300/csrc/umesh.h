@@ -22,6 +22,7 @@ struct UOptions {
   int n_mg;
   double fixed_lo, fixed_hi;
   uint64_t seed;         // colouring priority
+  bool coarse_space = true;  // build the Q1 coarse space (the coarsest mesh of a hierarchy only)
 };
 
 // host mesh (copied); kappa may be empty (1 everywhere)
@@ -29,6 +30,15 @@ UMesh* umesh_create(int dim, int64_t nv, const double* coords, int64_t nc, const
                     const uint8_t* vertex_on_boundary, std::string* msg);
 void umesh_destroy(UMesh* m);
 int umesh_set_kappa(UMesh* m, const double* kappa);     // nc values
+// `fine` is the uniform refinement of `coarse`: fine cell c is child child[c]
+// (corner bits in the parent's reference frame) of coarse cell parent[c]
+int umesh_set_parent(UMesh* fine, UMesh* coarse, const int64_t* parent, const uint8_t* child, std::string* msg);
+// kappa of a coarse mesh not given by the user: arithmetic mean of its children's
+int umesh_kappa_from_children(UMesh* coarse, const UMesh* fine);
+bool umesh_kappa_given(const UMesh* m);
+int64_t umesh_ncells(const UMesh* m);
+// after both meshes are set up: the h-transfer tables (degree p)
+int umesh_link(UMesh* fine, cudaStream_t s, std::string* msg);
 // build everything for degree p (p-levels p, p/2, ..., 1); ST_* codes, msg on error
 int umesh_setup(UMesh* m, int p, const UOptions& o, cudaStream_t s, int* err_dev, std::string* msg);
 
@@ -57,7 +67,8 @@ int umesh_sweep_colour(UMesh* m, int colour, const double* b, double* u, cudaStr
 int umesh_local(UMesh* m, int64_t n, const int64_t* ids_dev, const double* r, double* d, int n_cycles,
                 cudaStream_t s);
 int64_t umesh_interior_max(const UMesh* m);
-// z = M r (two-level V-cycle), FP64 in and out
+// z = M r: the V-cycle over the mesh chain ending at m (fine sweeps, h-restriction,
+// ..., the coarsest mesh's two-level cycle, ...), FP64 in and out
 int umesh_precondition(UMesh* m, const double* r, double* z, cudaStream_t s);
 // zero the Dirichlet DoFs of x
 int umesh_mask(UMesh* m, double* x, cudaStream_t s);

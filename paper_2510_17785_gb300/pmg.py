@@ -307,10 +307,13 @@ class Context:
                                                  kappa.ctypes.data))
         self.dim, self.N, self.p, self.n_levels = dim, N, p, n_levels
 
-    def mesh_upload(self, dim: int, coords: np.ndarray, cells: np.ndarray, p: int,
-                    vertex_on_boundary: Optional[np.ndarray] = None, kappa: Optional[np.ndarray] = None):
-        """Unstructured quadrilateral / hexahedral mesh: coords [n_v][dim],
-        cells [n_c][2^dim] vertex ids (lexicographic corner order); degree p."""
+    def mesh_upload(self, dim: int, coords: np.ndarray, cells: np.ndarray, p: Optional[int] = None,
+                    vertex_on_boundary: Optional[np.ndarray] = None, kappa: Optional[np.ndarray] = None,
+                    level: int = 0, parent: Optional[np.ndarray] = None, child: Optional[np.ndarray] = None):
+        """Unstructured quadrilateral / hexahedral mesh level: coords [n_v][dim],
+        cells [n_c][2^dim] vertex ids (lexicographic corner order).  Level 0
+        takes the degree p; a finer level gives each cell's parent cell and
+        child index in the level below."""
         coords = np.ascontiguousarray(coords, dtype=np.float64)
         cells = np.ascontiguousarray(cells, dtype=np.int64)
         nv, nc = coords.shape[0], cells.shape[0]
@@ -321,12 +324,26 @@ class Context:
             vob = np.ascontiguousarray(vertex_on_boundary, dtype=np.uint8)
             if vob.shape != (nv,):
                 raise ValueError("vertex_on_boundary must hold n_v flags")
-        self._check(self.lib.pmg_mesh_upload(self.h, 0, dim, nv, coords.ctypes.data, nc, cells.ctypes.data,
-                                             None if vob is None else vob.ctypes.data, None, None))
-        self._check(self.lib.pmg_set_degree(self.h, p))
+        par = ch = None
+        if parent is not None or child is not None:
+            par = np.ascontiguousarray(parent, dtype=np.int64)
+            ch = np.ascontiguousarray(child, dtype=np.uint8)
+            if par.shape != (nc,) or ch.shape != (nc,):
+                raise ValueError("parent and child must hold n_c entries")
+        self._check(self.lib.pmg_mesh_upload(self.h, level, dim, nv, coords.ctypes.data, nc, cells.ctypes.data,
+                                             None if vob is None else vob.ctypes.data,
+                                             None if par is None else par.ctypes.data,
+                                             None if ch is None else ch.ctypes.data))
+        if level == 0:
+            if p is None:
+                raise ValueError("level 0 takes the degree p")
+            self._check(self.lib.pmg_set_degree(self.h, p))
+            self.p = p
+            self.n_cells_levels = []
+        self.n_cells_levels.append(nc)
         if kappa is not None:
-            self.coeff_upload(0, kappa)
-        self.dim, self.N, self.p, self.n_levels = dim, None, p, 1
+            self.coeff_upload(level, kappa)
+        self.dim, self.N, self.n_levels = dim, None, level + 1
         self.n_cells = nc
 
     def set_degree(self, p: int):
