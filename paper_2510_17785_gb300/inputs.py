@@ -418,11 +418,32 @@ def corner_dets(coords: np.ndarray, cells: np.ndarray) -> np.ndarray:
     return out
 
 
-def perturb_unstructured(coords: np.ndarray, cells: np.ndarray, frac: float, rng: np.random.Generator):
+def jacobian_dets(coords: np.ndarray, cells: np.ndarray, xi=(0.0, 0.02, 0.5, 0.98, 1.0)) -> np.ndarray:
+    """[n_cells] smallest determinant of the multilinear map's Jacobian over the
+    tensor grid xi^d of reference points (corners included)."""
+    dim = coords.shape[1]
+    pts = np.array(np.meshgrid(*([np.asarray(xi)] * dim), indexing="ij")).reshape(dim, -1).T     # [np][d]
+    dN = np.ones((len(pts), 2 ** dim, dim))                                          # d N_c / d xi_a at pts
+    for c in range(2 ** dim):
+        for a in range(dim):
+            for b in range(dim):
+                bit = (c >> b) & 1
+                dN[:, c, a] *= (1.0 if bit else -1.0) if b == a else (pts[:, b] if bit else 1.0 - pts[:, b])
+    out = np.empty(len(cells))
+    for s0 in range(0, len(cells), 4096):
+        X = coords[cells[s0:s0 + 4096]]                                             # [n][2^d][d]
+        J = np.einsum("pca,ncd->npda", dN, X)
+        out[s0:s0 + 4096] = np.linalg.det(J).min(axis=1)
+    return out
+
+
+def perturb_unstructured(coords: np.ndarray, cells: np.ndarray, frac: float, rng: np.random.Generator,
+                         first_movable: int = 0):
     """Interior vertices moved by frac * h_v in a direction uniform on the
-    sphere, h_v the shortest edge at the vertex.  Vertices of a cell that
-    comes out with a non-positive corner determinant go back to their place,
-    repeated until every corner is positive."""
+    sphere, h_v the shortest edge at the vertex.  Vertices of a cell whose
+    Jacobian determinant comes out non-positive at a corner or at a point of a
+    5^d reference grid go back to their place, repeated until none does.
+    Vertices with ids below first_movable are not moved."""
     dim = coords.shape[1]
     nv = len(coords)
     bnd = boundary_vertices(dim, nv, cells)
@@ -439,9 +460,10 @@ def perturb_unstructured(coords: np.ndarray, cells: np.ndarray, frac: float, rng
     g /= np.linalg.norm(g, axis=1, keepdims=True)
     move = frac * h[:, None] * g
     move[bnd] = 0.0
+    move[:first_movable] = 0.0                          # vertices below first_movable stay
     out = coords + move
     for _ in range(64):
-        bad = (corner_dets(out, cells) <= 0).any(axis=1)
+        bad = (corner_dets(out, cells) <= 0).any(axis=1) | (jacobian_dets(out, cells) <= 0)
         if not bad.any():
             return out, bnd
         vs = np.unique(cells[bad])
@@ -563,3 +585,30 @@ def refine_unstructured(coords: np.ndarray, cells: np.ndarray):
             child.append(k)
     return np.array(out), np.array(fcells, dtype=np.int64), np.array(parent, dtype=np.int64), \
         np.array(child, dtype=np.uint8)
+
+
+def make_refined_problem(u: UProblem):
+    """Two mesh levels of one batched problem: the problem's mesh (level 0) and
+    its uniform refinement (level 1) whose new vertices move by 0.2 x their
+    shortest edge in a random direction; kappa 10^U(-2, 2) per fine cell
+    (the coarse cells take the mean of their children).  Returns
+    (coarse coords, coarse cells, fine coords, fine cells, parent, child,
+    fine vertex_on_boundary, fine kappa)."""
+    X, C, Xf, Cf, par, ch, bndf = _refined_mesh(u.kind, u.size)
+    kappa = 10.0 ** np.random.default_rng(u.seed).uniform(-2.0, 2.0, len(Cf))
+    return X, C, Xf, Cf, par, ch, bndf, kappa
+
+
+_REFINED = {}
+
+
+def _refined_mesh(kind: str, size: int):
+    """The two mesh levels of a mesh kind (seeded by the kind; shared by every
+    problem of that kind, built once per process)."""
+    if (kind, size) not in _REFINED:
+        ki = [k for k, _ in C4_KINDS].index(kind)
+        X, C, _ = unstructured_mesh(kind, size, 4004 + ki)
+        Xf, Cf, par, ch = refine_unstructured(X, C)
+        Xf, bndf = perturb_unstructured(Xf, Cf, 0.2, np.random.default_rng(4011 + ki), first_movable=len(X))
+        _REFINED[(kind, size)] = (X, C, Xf, Cf, par, ch, bndf)
+    return _REFINED[(kind, size)]
