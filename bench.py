@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-interval arm")
     ap.add_argument("--batch-structured", action="store_true",
                     help="--batch: structured 8^3 cubes instead of the unstructured meshes")
+    ap.add_argument("--batch-refined", action="store_true",
+                    help="--batch: every unstructured mesh refined once (two mesh levels, ~40k cells)")
     ap.add_argument("--batch", type=int, default=0,
                     help="instead: K independent problems (3D, 8^3 cells, degrees 2/4/6/8) solved together")
     ap.add_argument("--no-c3", action="store_true", help="skip the 48^3 Q7 sub-record (workloads.c3)")
@@ -491,11 +493,18 @@ def run_batch(args):
     else:
         meshes = {}
         for u in inputs.c4_problems(K):
-            X, C, bnd, kappa = inputs.make_unstructured_problem(u)
             c = pmg.Context(0, precision=pmg.PREC_MIXED, bounds=pmg.BOUNDS_LANCZOS)
-            c.mesh_upload(X.shape[1], X, C, u.p, vertex_on_boundary=bnd, kappa=kappa)
+            if args.batch_refined:
+                X, C, Xf, Cf, par, ch, bnd, kappa = inputs.make_refined_problem(u)
+                c.mesh_upload(X.shape[1], X, C, u.p)
+                c.mesh_upload(X.shape[1], Xf, Cf, level=1, parent=par, child=ch, vertex_on_boundary=bnd, kappa=kappa)
+                C = Cf
+            else:
+                X, C, bnd, kappa = inputs.make_unstructured_problem(u)
+                c.mesh_upload(X.shape[1], X, C, u.p, vertex_on_boundary=bnd, kappa=kappa)
             c.setup()
-            total, free = c.num_dofs(0)
+            lf = 1 if args.batch_refined else 0
+            total, free = c.num_dofs(lf)
             rhs = np.random.default_rng(u.seed + 1).uniform(-1.0, 1.0, total)
             ctxs.append(c)
             bs.append(torch.tensor(rhs, device="cuda"))
@@ -503,11 +512,17 @@ def run_batch(args):
             kinds.setdefault(u.kind, {"cells": len(C), "problems": 0, "valences": None})
             kinds[u.kind]["problems"] += 1
             if kinds[u.kind]["valences"] is None:
-                pm = c.get_patch_map(0)
+                pm = c.get_patch_map(lf)
                 kinds[u.kind]["valences"] = sorted({int(v) for v in (pm[:, 1:] >= 0).sum(axis=1)})
-        workload = (f"{K} unstructured problems (extruded / split-tetrahedron hexahedral and split-triangle "
-                    f"quadrilateral meshes, ~5k cells each), degrees 2/4/6/8, kappa 10^U(-2,2), Lanczos intervals, "
-                    f"two-level preconditioner with the Q1 coarse space")
+        if args.batch_refined:
+            workload = (f"{K} unstructured problems, each a ~5k-cell mesh (extruded / split-tetrahedron hexahedral, "
+                        f"split-triangle quadrilateral) refined once (~40k hexahedra, ~22k quadrilaterals), degrees "
+                        f"2/4/6/8, kappa 10^U(-2,2), Lanczos intervals, V-cycle over the two mesh levels with the "
+                        f"coarse mesh's Q1 space")
+        else:
+            workload = (f"{K} unstructured problems (extruded / split-tetrahedron hexahedral and split-triangle "
+                        f"quadrilateral meshes, ~5k cells each), degrees 2/4/6/8, kappa 10^U(-2,2), Lanczos "
+                        f"intervals, two-level preconditioner with the Q1 coarse space")
     t_setup = time.perf_counter() - t0
     us = [torch.zeros_like(b) for b in bs]
     stream = torch.cuda.current_stream()
