@@ -31,7 +31,10 @@ FP64_PEAK_NOMINAL = 1.25e12                      # GB300 FP64 rate (nominal)
 # DRAM bytes (read + write) of one finest-level colour launch of the FP32 patch kernel on the 3D Q4 32^3
 # workload (colour 0, 3,375 patches), from the ncu capture summarised in profiles/k_patch_q4_f32_sweep.md;
 # None while the kernel has changed since that capture
-PATCH_LAUNCH_TRAFFIC = None
+# DRAM bytes (read + write) of one finest-level colour launch of the benchmark workload from the ncu capture
+# summarised in profiles/k_patch_q4_f32_sweep.md (variant 10, colour 0: 3,375 patches, 118.7 MB), scaled to the
+# sweep's average launch (29,791 / 8 patches); valid for that variant only
+PATCH_LAUNCH_TRAFFIC = {"variant": 10, "bytes": 118.67e6 * (29791 / 8) / 3375}
 METRIC = "patch-smoother DoFs/s and CG time-to-1e-8 residual: mixed/learned vs plain FP64, 1 GB300"
 
 
@@ -726,9 +729,11 @@ def run_ours(args):
             "bound": "alu", "achieved": achieved / 1e12,
             "peak": FP32_PEAK_DERIVED / 1e12, "unit": "TFLOP/s",
             "frac": achieved / FP32_PEAK_DERIVED,
-            "traffic": PATCH_LAUNCH_TRAFFIC if w.name == "c2_3d_q4_n32_perturbed" else None,
-            "traffic_note": ("DRAM bytes of one colour launch (colour 0, 3,375 patches) from the ncu capture of "
-                             "profiles/k_patch_q4_f32_sweep.md (null: kernel changed since)"),
+            "traffic": (PATCH_LAUNCH_TRAFFIC["bytes"] if w.name == "c2_3d_q4_n32_perturbed"
+                        and head["tuning"][0] == PATCH_LAUNCH_TRAFFIC["variant"] else None),
+            "traffic_note": ("DRAM bytes per colour launch of the finest-level sweep (read + write, from the ncu "
+                             "capture of variant 10 in profiles/k_patch_q4_f32_sweep.md, scaled from colour 0 to the "
+                             "average launch; null when the set-up picked another variant)"),
             "kernel": "k_patch<3,4,float,SWEEP,variant> (finest-level patch sweep, 8 colour launches)",
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
             "measured_fma_peak": result["fma32"] / 1e12,

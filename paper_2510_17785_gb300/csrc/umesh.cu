@@ -400,6 +400,21 @@ static std::string build_patch_level(UMesh* m, int k) {
   return "";
 }
 
+// dynamic shared memory of the patch kernel without its workspace, degree p
+template <int DIM, typename T>
+static size_t upatch_base_bytes(int p) {
+  switch (p) {
+    case 1: return upatch_smem_aligned<DIM, 1, T>();
+    case 2: return upatch_smem_aligned<DIM, 2, T>();
+    case 3: return upatch_smem_aligned<DIM, 3, T>();
+    case 4: return upatch_smem_aligned<DIM, 4, T>();
+    case 5: return upatch_smem_aligned<DIM, 5, T>();
+    case 6: return upatch_smem_aligned<DIM, 6, T>();
+    case 7: return upatch_smem_aligned<DIM, 7, T>();
+    default: return upatch_smem_aligned<DIM, 8, T>();
+  }
+}
+
 template <typename T>
 static void fill_args(UMesh* m, UPatchArgs<T>& a) {
   std::memset(&a, 0, sizeof(a));
@@ -437,6 +452,9 @@ static void fill_args(UMesh* m, UPatchArgs<T>& a) {
   if constexpr (sizeof(T) == 8) a.ws = m->ws64;
   else a.ws = m->ws32;
   a.ws_stride = m->ws_stride;
+  // the workspace slice moves into shared memory when CTA and slice fit 100 KB (two CTAs per SM)
+  const size_t base = m->dim == 2 ? upatch_base_bytes<2, T>(m->p) : upatch_base_bytes<3, T>(m->p);
+  a.ws_shared = base + m->ws_stride * sizeof(T) <= 100 * 1024 ? 1 : 0;
   a.yoff = m->yoff;
 }
 
@@ -593,7 +611,7 @@ int umesh_setup(UMesh* m, int p, const UOptions& o, cudaStream_t s, int* err_dev
     std::vector<float> bf(bd.begin(), bd.end());
     UCK(m->upload(&L.bounds32, bf));
     UCK(m->upload(&L.ritz64, std::vector<double>(2 * np, 0.0)));
-    ymax = std::max(ymax, (size_t)UMAXC * L.nloc);
+    ymax = std::max(ymax, (size_t)umesh_max_valence(m) * L.nloc);   // cell outputs of the largest patch
   }
   int h_err = 0;
   UCU(cudaMemcpy(&h_err, err_dev, sizeof(int), cudaMemcpyDeviceToHost));
@@ -795,6 +813,7 @@ int umesh_lanczos(UMesh* m, int ksteps, uint64_t seed, double safety, double rat
   if (ksteps < 1 || ksteps > 64) return ST_ARG;
   UPatchArgs<double> a;
   fill_args(m, a);
+  a.ws_shared = 0;                                   // the Lanczos kernel keeps its slices in global memory
   const int grid = (int)std::min<int64_t>(np, std::min<int64_t>(m->ws_grid, 152 * 2));
   ULanczos z{};
   z.stride = ((size_t)(ksteps + 3) * m->L[0].nimax + 31) & ~size_t(31);

@@ -244,6 +244,7 @@ struct UPatchArgs {
   T omega;
   T* ws;                          // workspace [gridDim.x][ws_stride]
   size_t ws_stride;
+  int ws_shared;                  // 1: each CTA's workspace slice lives in its shared memory (it fits)
   int off[UMAXL][5];              // r, d, res, dir, dinv offsets in a slice
   int yoff;                       // cell-output buffer offset [UMAXC][nloc_max]
 };
@@ -750,11 +751,17 @@ constexpr size_t upatch_smem() {
   return sizeof(T) * m + sizeof(int) * (UMAXC + UMAXL) + sizeof(T) * UMAXL * 16 + 64;
 }
 
+template <int DIM, int P, typename T>
+__host__ __device__ constexpr size_t upatch_smem_aligned() {
+  return (upatch_smem<DIM, P, T>() + 15) & ~size_t(15);
+}
+
 template <int DIM, int P, typename T, int MODE>
 __global__ void __launch_bounds__(UNT) k_upatch(const __grid_constant__ UPatchArgs<T> args) {
   UPatch<DIM, P, T, MODE> k;
   k.a = &args;
-  k.ws = args.ws + (size_t)blockIdx.x * args.ws_stride;
+  constexpr size_t WS_OFF = upatch_smem_aligned<DIM, P, T>();
+  k.ws = args.ws_shared ? reinterpret_cast<T*>(pmg_smem + WS_OFF) : args.ws + (size_t)blockIdx.x * args.ws_stride;
   unsigned char* base = pmg_smem;
   k.cells = reinterpret_cast<int*>(base);
   k.nint = k.cells + UMAXC;

@@ -26,32 +26,41 @@ int ucell_apply_q(const T* u, const T* G, const int32_t* cd, const uint8_t* bnd,
 
 template <int DIM, int P, typename T>
 int upatch_launch_P(int mode, const UPatchArgs<T>& a, int grid, cudaStream_t s) {
-  constexpr size_t sm = upatch_smem<DIM, P, T>();
-  if constexpr (sm > 227 * 1024) {
+  constexpr size_t sm0 = upatch_smem<DIM, P, T>();
+  if constexpr (sm0 > 227 * 1024) {
     return ST_UNSUPPORTED;
   } else {
+    // the workspace slice joins the shared memory when the caller says it fits
+    const size_t sm = a.ws_shared ? upatch_smem_aligned<DIM, P, T>() + a.ws_stride * sizeof(T) : sm0;
+    if (sm > 227 * 1024) return ST_ARG;
     int dev = 0;
     cudaGetDevice(&dev);
-    static bool attr[2][64] = {};
+    static size_t attr[2][64] = {};                  // largest dynamic size set so far, per device
     if (mode == MODE_SWEEP) {
-      if (!attr[0][dev & 63]) {
+      if (attr[0][dev & 63] < sm) {
         if (cudaFuncSetAttribute(k_upatch<DIM, P, T, MODE_SWEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sm) != cudaSuccess)
           return ST_CUDA;
-        attr[0][dev & 63] = true;
+        attr[0][dev & 63] = sm;
       }
       k_upatch<DIM, P, T, MODE_SWEEP><<<grid, UNT, sm, s>>>(a);
     } else {
-      if (!attr[1][dev & 63]) {
+      if (attr[1][dev & 63] < sm) {
         if (cudaFuncSetAttribute(k_upatch<DIM, P, T, MODE_LOCAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sm) != cudaSuccess)
           return ST_CUDA;
-        attr[1][dev & 63] = true;
+        attr[1][dev & 63] = sm;
       }
       k_upatch<DIM, P, T, MODE_LOCAL><<<grid, UNT, sm, s>>>(a);
     }
     return cudaPeekAtLastError() == cudaSuccess ? ST_OK : ST_CUDA;
   }
+}
+
+// bytes of dynamic shared memory of the patch kernel without its workspace
+template <int DIM, int P, typename T>
+size_t upatch_smem_base() {
+  return upatch_smem_aligned<DIM, P, T>();
 }
 
 template <int DIM, int P>
