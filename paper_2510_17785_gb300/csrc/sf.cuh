@@ -39,6 +39,18 @@ __host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * i
 // accesses.
 extern __shared__ __align__(16) unsigned char pmg_smem[];
 
+// d = a * b + c on both lanes (one packed FP32 FMA, fma.rn.f32x2)
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  unsigned long long ra, rb, rc, rd;
+  memcpy(&ra, &a, 8);
+  memcpy(&rb, &b, 8);
+  memcpy(&rc, &c, 8);
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rd) : "l"(ra), "l"(rb), "l"(rc));
+  float2 d;
+  memcpy(&d, &rd, 8);
+  return d;
+}
+
 // Geometry functors (gcell) return the G base pointer of a cell; a functor
 // type that declares `static constexpr bool kShared = true` serves G from
 // shared memory, every other one from global memory, where it is read
@@ -203,12 +215,23 @@ struct SF {
     }
 #pragma unroll
     for (int i = 0; i < h; ++i) {
-      T e = odd ? tabEm<T>(KIND, Q, i) * x[h] : T(0);
+      T e, o;
+      if constexpr (sizeof(T) == 4) {
+        // the even and odd sums of output pair i as the two lanes of packed FMAs
+        // (each lane the same FMAs in the same order as the scalar form)
+        float2 acc = make_float2(odd ? tabEm<T>(KIND, Q, i) * x[h] : T(0), T(0));
 #pragma unroll
-      for (int j = 0; j < h; ++j) e += tabEe<T>(KIND, Q, i, j) * xe[j];
-      T o = T(0);
+        for (int j = 0; j < h; ++j) acc = ffma2(tabEO2(KIND, Q, i, j), make_float2(xe[j], xo[j]), acc);
+        e = acc.x;
+        o = acc.y;
+      } else {
+        e = odd ? tabEm<T>(KIND, Q, i) * x[h] : T(0);
 #pragma unroll
-      for (int j = 0; j < h; ++j) o += tabEo<T>(KIND, Q, i, j) * xo[j];
+        for (int j = 0; j < h; ++j) e += tabEe<T>(KIND, Q, i, j) * xe[j];
+        o = T(0);
+#pragma unroll
+        for (int j = 0; j < h; ++j) o += tabEo<T>(KIND, Q, i, j) * xo[j];
+      }
       y[i] = e + o;
       y[n - 1 - i] = anti ? o - e : e - o;
     }

@@ -23,6 +23,11 @@ namespace pmg {
 
 static __constant__ Tables<double> c_tab_f64;
 static __constant__ Tables<float> c_tab_f32;
+// FP32 even and odd parts side by side, (Ee[k][q][i][j], Eo[k][q][i][j]), for packed two-lane FMAs
+struct EOPacked {
+  float2 v[4][PMG_MAXQ + 1][PMG_EOR][PMG_EOC];
+};
+static __constant__ EOPacked c_eo2_f32;
 static __device__ Rules c_rules;          // set-up kernels only: global memory, not the constant bank
 
 template <typename T>
@@ -61,6 +66,8 @@ __device__ __forceinline__ T tabT(int qf, int a, int b) {
   else return tabE<T>(qf, a, b);
 }
 
+__device__ __forceinline__ float2 tabEO2(int k, int q, int i, int j) { return c_eo2_f32.v[k][q][i][j]; }
+
 // even/odd parts of B, B^T, D, D^T (table_types.h)
 template <typename T>
 __device__ __forceinline__ T tabEe(int k, int q, int i, int j);
@@ -85,6 +92,13 @@ static inline int upload_tables_tu(const Tables<double>& h64, const Tables<float
   cudaError_t e = cudaMemcpyToSymbol(c_tab_f64, &h64, sizeof(h64));
   if (e != cudaSuccess) return (int)e;
   e = cudaMemcpyToSymbol(c_tab_f32, &h32, sizeof(h32));
+  if (e != cudaSuccess) return (int)e;
+  EOPacked pk;
+  for (int k = 0; k < 4; ++k)
+    for (int q = 0; q <= PMG_MAXQ; ++q)
+      for (int i = 0; i < PMG_EOR; ++i)
+        for (int j = 0; j < PMG_EOC; ++j) pk.v[k][q][i][j] = make_float2(h32.Ee[k][q][i][j], h32.Eo[k][q][i][j]);
+  e = cudaMemcpyToSymbol(c_eo2_f32, &pk, sizeof(pk));
   if (e != cudaSuccess) return (int)e;
   return (int)cudaMemcpyToSymbol(c_rules, &r, sizeof(r));
 }
