@@ -590,12 +590,11 @@ def refine_unstructured(coords: np.ndarray, cells: np.ndarray):
 def make_refined_problem(u: UProblem):
     """Two mesh levels of one batched problem: the problem's mesh (level 0) and
     its uniform refinement (level 1) whose new vertices move by 0.2 x their
-    shortest edge in a random direction; kappa 10^U(-2, 2) per fine cell
-    (the coarse cells take the mean of their children).  Returns
-    (coarse coords, coarse cells, fine coords, fine cells, parent, child,
-    fine vertex_on_boundary, fine kappa)."""
+    shortest edge in a random direction; kappa 10^U(-2, 2) per coarse cell,
+    inherited by its children.  Returns (coarse coords, coarse cells, fine
+    coords, fine cells, parent, child, fine vertex_on_boundary, fine kappa)."""
     X, C, Xf, Cf, par, ch, bndf = _refined_mesh(u.kind, u.size)
-    kappa = 10.0 ** np.random.default_rng(u.seed).uniform(-2.0, 2.0, len(Cf))
+    kappa = (10.0 ** np.random.default_rng(u.seed).uniform(-2.0, 2.0, len(C)))[par]
     return X, C, Xf, Cf, par, ch, bndf, kappa
 
 
