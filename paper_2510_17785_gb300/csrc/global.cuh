@@ -217,7 +217,7 @@ __global__ void k_invert_diag(const double* __restrict__ diag, int M, double* __
 // on Dirichlet nodes, Dirichlet rows skipped.  CPB cells per CTA.
 template <int DIM, int Q, typename T, int NT, int CPB>
 struct CellApply {
-  using Dm = Dims<DIM, 1, Q>;
+  using Dm = Dims<DIM, 1, Q, (int)sizeof(T)>;
   static constexpr int NN = Dm::NN;
   static constexpr int PS = ((NN * 2 + Dm::SCRATCH) + 3) & ~3;
   static constexpr size_t smem = sizeof(T) * PS * CPB + sizeof(int) * CPB * 2;

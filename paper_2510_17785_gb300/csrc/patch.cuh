@@ -108,7 +108,8 @@ struct PatchEpi {
   }
 };
 
-template <int DIM, int P, bool LINE = false, bool GSMEM = false, int LR = 0>
+// per-patch shared-memory layout (ES-byte elements)
+template <int DIM, int P, int ES, bool LINE = false, bool GSMEM = false, int LR = 0>
 struct Layout {
   static constexpr int NL = nlevels_rule(P, LR);
   __host__ __device__ static constexpr int q(int k) { return level_degree(P, LR, k); }
@@ -136,7 +137,7 @@ struct Layout {
   static constexpr bool CLOS_SHARED = q(0) > 1 && !dn(0) && NN0 <= 3 * ni(0);
   static constexpr int CLOS = CLOS_SHARED ? D_(0) : doff(NL);
   static constexpr int SCR = CLOS_SHARED ? doff(NL) : doff(NL) + NN0;
-  static constexpr int SCRATCH = LINE ? Dims<DIM, 2, P>::SCRATCH_LINE : Dims<DIM, 2, P>::SCRATCH;
+  static constexpr int SCRATCH = LINE ? Dims<DIM, 2, P, ES>::SCRATCH_LINE : Dims<DIM, 2, P, ES>::SCRATCH;
   static constexpr int COEF = SCR + SCRATCH;      // per level: 1/theta, c1[1..7], c2[1..7]
   static constexpr int NCOEF = 16;
   // (the fast-diagonalisation tables of the Cartesian-reinforced smoother are
@@ -199,7 +200,7 @@ struct Config {
   static constexpr bool LINE = LINEV[VB];
   static constexpr bool GSMEM = GSMEMV[VB];
   static constexpr size_t bytes_per_patch =
-      sizeof(T) * Layout<DIM, P, LINE, GSMEM, LR>::PS + sizeof(int) * ((1 << DIM) + 6);
+      sizeof(T) * Layout<DIM, P, (int)sizeof(T), LINE, GSMEM, LR>::PS + sizeof(int) * ((1 << DIM) + 6);
   static constexpr size_t SMEM_LIMIT = 227 * 1024;
   static constexpr int PPB_FIT = (int)(SMEM_LIMIT / bytes_per_patch);
   static constexpr int PPB = PPB_FIT < PPB_MAX ? (PPB_FIT < 1 ? 1 : PPB_FIT) : PPB_MAX;
@@ -252,7 +253,7 @@ struct Config {
 template <int DIM, int P, typename T, int MODE, int V = 0>
 struct PatchKernel {
   using C = Config<DIM, P, T, V>;
-  using L = Layout<DIM, P, C::LINE, C::GSMEM, C::LR>;
+  using L = Layout<DIM, P, (int)sizeof(T), C::LINE, C::GSMEM, C::LR>;
   using TM = Team<C::NT, C::PPB, C::GROUPED>;
   static constexpr int NT = C::NT, PPB = C::PPB, NL = L::NL, PS = L::PS;
   static constexpr int NCELL = 1 << DIM;
@@ -310,7 +311,7 @@ struct PatchKernel {
   template <int K>
   __device__ auto gfun() const {
     constexpr int q = L::q(K);
-    constexpr int stride = Dims<DIM, 2, q>::NCOMP * ipow(q + 1, DIM);
+    constexpr int stride = Dims<DIM, 2, q, (int)sizeof(T)>::NCOMP * ipow(q + 1, DIM);
     if constexpr (C::GSMEM && K == 0) {                 // staged in shared memory by load_level
       return SharedGeom<stride>{};
     } else {
@@ -365,6 +366,7 @@ struct PatchKernel {
         TM::sync();
       }
     } else {
+      static_assert(sf_scratch(DIM, 2, q, C::LINE, (int)sizeof(T)) <= L::SCRATCH, "level scratch exceeds the top level's");
       SF<DIM, 2, q, T, NT, PPB, C::LINE, C::GROUPED>::template apply_epi<true>(vec(0, in_off), PS, vec(0, L::SCR), PS,
                                                                   gfun<K>(), e);
     }
@@ -1019,7 +1021,7 @@ template <int DIM, int Q>
 __global__ void __launch_bounds__(128) k_dense_patch(const double* __restrict__ G, int N, int first_patch,
                                                      int n_items, double* __restrict__ A) {
   constexpr int NT = 128;
-  using Dm = Dims<DIM, 2, Q>;
+  using Dm = Dims<DIM, 2, Q, 8>;
   constexpr int NI = Dm::NI;
   constexpr int NCELL = 1 << DIM;
   double* x = reinterpret_cast<double*>(pmg_smem);
@@ -1055,7 +1057,7 @@ __global__ void __launch_bounds__(128) k_dense_patch(const double* __restrict__ 
 
 template <int DIM, int Q>
 constexpr size_t dense_patch_smem() {
-  using Dm = Dims<DIM, 2, Q>;
+  using Dm = Dims<DIM, 2, Q, 8>;
   return sizeof(double) * (2 * Dm::NI + Dm::SCRATCH) + sizeof(int) * (1 << DIM);
 }
 
@@ -1121,7 +1123,7 @@ __device__ inline int sturm_count_dev(const double* al, const double* be, int n,
 template <int DIM, int Q, typename T>
 __global__ void __launch_bounds__(256) k_lanczos(const __grid_constant__ LanczosArgs<T> a) {
   constexpr int NT = 256;
-  using Dm = Dims<DIM, 2, Q>;
+  using Dm = Dims<DIM, 2, Q, (int)sizeof(T)>;
   constexpr int NI = Dm::NI;
   constexpr int NCELL = 1 << DIM;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1260,7 +1262,7 @@ __global__ void __launch_bounds__(256) k_lanczos(const __grid_constant__ Lanczos
 
 template <int DIM, int Q, typename T>
 constexpr size_t lanczos_smem() {
-  using Dm = Dims<DIM, 2, Q>;
+  using Dm = Dims<DIM, 2, Q, (int)sizeof(T)>;
   return sizeof(T) * (2 * Dm::NI + Dm::SCRATCH + 2) + 16 +
          sizeof(double) * (3 * Dm::NI + 256 / 32 + 2 + 3 * 64) + sizeof(int) * 16;
 }

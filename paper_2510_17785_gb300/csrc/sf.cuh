@@ -76,8 +76,43 @@ __device__ __forceinline__ T* smem_ptr(T* p) {
   return reinterpret_cast<T*>(pmg_smem + off);
 }
 __host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
+__host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
 
-template <int DIM, int NC, int Q>
+// Shared-memory layout of the point arrays of the sum factorisation: rows of
+// QP values along x.  A stage along x gives each thread one row, so a warp
+// reads one element of 32 consecutive rows at a time; with rows packed at
+// pitch QP those fall into 32 / gcd(QP, 32) banks (QP = 16: two banks, a
+// 16-way conflict).  For QP a power of two the rows are therefore stored in
+// groups of G rows (G * QP = one sweep of the 32 banks) with one element of
+// slack after each group: row r starts at r * QP + r / G.  The 32 rows of a
+// warp then start in 32 distinct banks, and the points of one group (what a
+// stage along the last direction reads, one line per thread) stay
+// contiguous.  A group holds at least two rows: where a single row would
+// fill the banks (8-byte elements at QP = 16) the slack is halved at the
+// price of a 2-way conflict (that keeps the FP64 degree-7 patch within
+// shared memory).  sf_rows() is the size of an array of r rows of es-byte
+// elements (128 / es of them per sweep of the banks).
+__host__ __device__ constexpr bool sf_skew(int qp) { return (qp & (qp - 1)) == 0; }
+__host__ __device__ constexpr int sf_group(int qp, int es) { return sf_skew(qp) ? cmax(128 / es / qp, 2) : 1; }
+__host__ __device__ constexpr int sf_rows(int qp, int r, int es) {
+  return r * qp + (sf_skew(qp) ? r / sf_group(qp, es) : 0);
+}
+// scratch elements of one block (V and R below; line: the line design)
+__host__ __device__ constexpr int sf_scratch(int dim, int nc, int q, bool line, int es) {
+  const int n = q + 1, M = nc * q + 1, QP = nc * n;
+  const int Lo = nc == 2 ? 2 * q - 1 : M;
+  const int NQS = sf_rows(QP, ipow(QP, dim - 1), es);
+  // forward temporaries for the widest input (all nodes): [M]^(d-1) x QP and M x QP x QP
+  const int T1 = sf_rows(QP, ipow(M, dim - 1), es), T2 = dim == 3 ? sf_rows(QP, M * QP, es) : 0;
+  // backward temporaries: [Lo][QP][QP] and [Lo][Lo][QP] (3D), [Lo][QP] (2D)
+  const int B = dim == 3 ? sf_rows(QP, Lo * Lo, es) + sf_rows(QP, Lo * QP, es) : sf_rows(QP, Lo, es);
+  // stage design: all DIM flux arrays in R; line design: DIM - 1 of them
+  const int R = line ? cmax(cmax(T1 + T2, (dim - 1) * NQS), B) : cmax(T1 + T2, dim * NQS);
+  return NQS + R;
+}
+
+// sizes of the NC^DIM block of degree Q with ES-byte elements
+template <int DIM, int NC, int Q, int ES>
 struct Dims {
   static constexpr int n = Q + 1;
   static constexpr int M = NC * Q + 1;
@@ -88,16 +123,8 @@ struct Dims {
   static constexpr int NI = ipow(Mi, DIM);        // interior nodes (patch) / all (cell)
   static constexpr int NCOMP = DIM * (DIM + 1) / 2;
   static constexpr int NGC = ipow(n, DIM);        // quadrature points per cell
-  // forward temporaries for the widest input (all nodes)
-  static constexpr int T1 = ipow(M, DIM - 1) * QP;
-  static constexpr int T2 = (DIM == 3) ? M * QP * QP : 0;
-  static constexpr int Lo = (NC == 2) ? Mi : M;
-  static constexpr int B = (DIM == 3) ? Lo * Lo * QP + Lo * QP * QP : Lo * QP;   // backward temporaries
-  // stage design: all DIM flux arrays in R; line design: DIM - 1 of them
-  static constexpr int R = cmax(T1 + T2, DIM * NQ);
-  static constexpr int R_LINE = cmax(cmax(T1 + T2, (DIM - 1) * NQ), B);
-  static constexpr int SCRATCH = NQ + R;          // V + R (stage design)
-  static constexpr int SCRATCH_LINE = NQ + R_LINE;
+  static constexpr int SCRATCH = sf_scratch(DIM, NC, Q, false, ES);      // V + R (stage design)
+  static constexpr int SCRATCH_LINE = sf_scratch(DIM, NC, Q, true, ES);  // V + R (line design)
 };
 
 // Number of vertex patches whose interior holds the node with per-axis index
@@ -181,9 +208,38 @@ struct Team {
 
 template <int DIM, int NC, int Q, typename T, int NT, int PPB, bool LINE = false, bool GROUPED = false>
 struct SF {
-  using D = Dims<DIM, NC, Q>;
+  using D = Dims<DIM, NC, Q, (int)sizeof(T)>;
   using TM = Team<NT, PPB, GROUPED>;
   static constexpr int n = D::n, M = D::M, Mi = D::Mi, QP = D::QP, NQ = D::NQ;
+
+  // ---- point-array addressing (see sf_rows): row r starts at rowa(r)
+  static constexpr bool SKEW = sf_skew(QP);
+  static constexpr int G = sf_group(QP, (int)sizeof(T));     // rows per group
+  static constexpr int LG = ilog2(G);
+  static_assert((1 << LG) == G, "");
+  __host__ __device__ static constexpr int rowa(int r) { return r * QP + (SKEW ? (r >> LG) : 0); }
+  static constexpr int NQS = rowa(ipow(QP, DIM - 1));         // one array of all points
+  static_assert(NQS == sf_rows(QP, ipow(QP, DIM - 1), (int)sizeof(T)), "");
+  // Along the last direction (z in 3D, y in 2D) point g of line i sits at
+  // loff(g) + lbase(i): with QP rows per plane, rowa(z QP + y) = rowa(z QP) +
+  // rowa(y) for y < QP (G divides QP, or QP divides G and the group index
+  // does not change within a plane's first QP rows)
+  __host__ __device__ static constexpr int loff(int g) { return DIM == 3 ? rowa(g * QP) : rowa(g); }
+  __device__ __forceinline__ static int lbase(int i) {
+    if constexpr (DIM == 3 && SKEW) return rowa(i / QP) + i % QP;
+    else return i;
+  }
+  // lines along x (AX = 0: row `item`) and y (AX = 1, 3D: x = item % QP in
+  // plane item / QP) of an array with QP rows per plane: first point, and
+  // the offset of point h
+  template <int AX>
+  __device__ __forceinline__ static int lstart(int item) {
+    static_assert(AX == 0 || (AX == 1 && DIM == 3), "lines along x, or along y in 3D");
+    if constexpr (AX == 0) return rowa(item);
+    else return rowa((item / QP) * QP) + item % QP;
+  }
+  template <int AX>
+  __host__ __device__ static constexpr int lstep(int h) { return AX == 0 ? h : rowa(h); }
 
   // ---- line helpers: one item is a whole line of the block along an axis
   // (all NC cells).  The node values of a line with the patch's Dirichlet
@@ -286,13 +342,14 @@ struct SF {
       }
     }
   }
-  // output sinks for integ_line: strided store (ACC: add) / epilogue
+  // output sinks for integ_line: column x of rows row0, row0 + 1, ... of a
+  // point array (ACC: add) / epilogue
   template <bool ACC>
   struct LineStore {
     T* dst;
-    int stride;
-    __device__ __forceinline__ T init(int k) const { return ACC ? dst[k * stride] : T(0); }
-    __device__ __forceinline__ void operator()(int k, T s) const { dst[k * stride] = s; }
+    int row0, x;
+    __device__ __forceinline__ T init(int k) const { return ACC ? dst[rowa(row0 + k) + x] : T(0); }
+    __device__ __forceinline__ void operator()(int k, T s) const { dst[rowa(row0 + k) + x] = s; }
   };
   template <typename EPI>
   struct LineEpi {
@@ -302,18 +359,43 @@ struct SF {
     __device__ __forceinline__ void operator()(int k, T s) const { epi(pp, base + k, s); }
   };
 
-  // ---- forward interpolation along axis AX: [O][L][I] -> [O][QP][I], one line per item
+  // ---- forward interpolation along axis AX, one line per item.  AX = 0: the
+  // block's nodes [..][L] (packed) -> row `item` of T1; AX = 1 (3D): T1
+  // [L][L][QP] -> T2 [L][QP][QP] (x = item % QP in plane item / QP)
   template <int AX, bool INTIN>
   __device__ __forceinline__ static void fwd_item(const T* __restrict__ in, T* __restrict__ out, int item) {
     constexpr int L = INTIN ? Mi : M;
-    constexpr int I = ipow(QP, AX);
-    const int i = item % I, o = item / I;
     T v[M], w[QP];
-    load_line<INTIN>(in + o * L * I + i, I, v);
-    interp_line<INTIN>(v, w);
-    T* dst = out + o * QP * I + i;
+    if constexpr (AX == 0) {
+      load_line<INTIN>(in + item * L, 1, v);
+      interp_line<INTIN>(v, w);
+      T* dst = out + rowa(item);
 #pragma unroll
-    for (int g = 0; g < QP; ++g) dst[g * I] = w[g];
+      for (int g = 0; g < QP; ++g) dst[g] = w[g];
+    } else {
+      static_assert(AX == 1 && DIM == 3, "x, or y in 3D");
+      const int i = item % QP, o = item / QP;
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        if (INTIN && NC == 2) v[k] = (k == 0 || k == M - 1) ? T(0) : in[rowa(o * L + k - 1) + i];
+        else v[k] = in[rowa(o * L + k) + i];
+      }
+      interp_line<INTIN>(v, w);
+      T* dst = out + rowa(o * QP) + i;
+#pragma unroll
+      for (int g = 0; g < QP; ++g) dst[rowa(g)] = w[g];
+    }
+  }
+
+  // the M node values of line i along the last direction (INTIN: rows of the
+  // interior nodes only, the patch's Dirichlet ends zero)
+  template <bool INTIN>
+  __device__ __forceinline__ static void load_last(const T* __restrict__ in, int b, T (&v)[M]) {
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      if (INTIN && NC == 2) v[k] = (k == 0 || k == M - 1) ? T(0) : in[loff(k - 1) + b];
+      else v[k] = in[loff(k) + b];
+    }
   }
 
   // ---- forward interpolation along the last axis fused with the collocation
@@ -321,24 +403,22 @@ struct SF {
   template <bool INTIN>
   __device__ __forceinline__ static void fwd_der_last_item(const T* __restrict__ in, T* __restrict__ V,
                                                            T* __restrict__ F, int i) {
-    constexpr int AX = DIM - 1;
-    constexpr int I = ipow(QP, AX);
+    const int b = lbase(i);
     T v[M], w[QP], f[QP];
-    load_line<INTIN>(in + i, I, v);
+    load_last<INTIN>(in, b, v);
     interp_line<INTIN>(v, w);
 #pragma unroll
-    for (int g = 0; g < QP; ++g) V[g * I + i] = w[g];
+    for (int g = 0; g < QP; ++g) V[loff(g) + b] = w[g];
 #pragma unroll
     for (int c = 0; c < NC; ++c) eo_cell<EO_D>(w, c * n, f, c * n);
 #pragma unroll
-    for (int g = 0; g < QP; ++g) F[g * I + i] = f[g];
+    for (int g = 0; g < QP; ++g) F[loff(g) + b] = f[g];
   }
 
   // ---- backward along the last axis for one line: w = (partial sums of the
-  // other directions) + D^T f per cell, then B^T per cell; out[(k - 1) * I]
-  // receives interior node k (NC = 2) or node k (NC = 1).
-  __device__ __forceinline__ static void last_bwd(const T (&part)[QP], const T (&f)[QP], T* __restrict__ out,
-                                                  int I) {
+  // other directions) + D^T f per cell, then B^T per cell; out[loff(k - 1)]
+  // receives interior node k (NC = 2), out[loff(k)] node k (NC = 1).
+  __device__ __forceinline__ static void last_bwd(const T (&part)[QP], const T (&f)[QP], T* __restrict__ out) {
     T t[QP], w[QP], y[QP];
 #pragma unroll
     for (int c = 0; c < NC; ++c) eo_cell<EO_DT>(f, c * n, t, c * n);
@@ -348,11 +428,11 @@ struct SF {
     for (int c = 0; c < NC; ++c) eo_cell<EO_BT>(w, c * n, y, c * n);
     if constexpr (NC == 1) {
 #pragma unroll
-      for (int a = 0; a <= Q; ++a) out[a * I] = y[a];
+      for (int a = 0; a <= Q; ++a) out[loff(a)] = y[a];
     } else {
 #pragma unroll
       for (int k = 1; k <= M - 2; ++k)
-        out[(k - 1) * I] = (k < Q) ? y[k] : (k == Q ? y[Q] + y[n] : y[n + k - Q]);
+        out[loff(k - 1)] = (k < Q) ? y[k] : (k == Q ? y[Q] + y[n] : y[n + k - Q]);
     }
   }
 
@@ -362,49 +442,15 @@ struct SF {
   // (3D: the partial sums are the two arrays Vp + Vq)
   __device__ __forceinline__ static void dert_bwd_last_item(const T* __restrict__ F, const T* __restrict__ Vp,
                                                             const T* __restrict__ Vq, T* __restrict__ out, int i) {
-    constexpr int AX = DIM - 1;
-    constexpr int I = ipow(QP, AX);
+    const int b = lbase(i);
     T f[QP], part[QP];
 #pragma unroll
     for (int g = 0; g < QP; ++g) {
-      f[g] = F[g * I + i];
-      part[g] = Vp[g * I + i];
-      if (DIM == 3) part[g] += Vq[g * I + i];
+      f[g] = F[loff(g) + b];
+      part[g] = Vp[loff(g) + b];
+      if (DIM == 3) part[g] += Vq[loff(g) + b];
     }
-    last_bwd(part, f, out + i, I);
-  }
-
-  // ---- quadrature-point product: F_k <- sum_l G_kl F_l
-  // gcell(pp, slot) returns the G base pointer of cell `slot` of block pp.
-  template <typename GF>
-  __device__ __forceinline__ static void quad_item(T* __restrict__ F, int pt, const GF& gcell, int pp) {
-    constexpr int NGC = D::NGC;
-    int cslot = 0, lg = 0, rem = pt, mul = 1, cmul = 1;
-#pragma unroll
-    for (int ax = 0; ax < DIM; ++ax) {
-      const int qa = rem % QP;
-      rem /= QP;
-      const int ca = (NC == 2) ? (qa >= n) : 0;
-      const int ga = qa - ca * n;
-      cslot += ca * cmul;
-      lg += ga * mul;
-      cmul *= NC;
-      mul *= n;
-    }
-    const T* G = gcell(pp, cslot) + lg;
-    if (DIM == 3) {
-      const T g0 = F[pt], g1 = F[NQ + pt], g2 = F[2 * NQ + pt];
-      const T G00 = gload<GF>(G), G01 = gload<GF>(G + NGC), G02 = gload<GF>(G + 2 * NGC),
-              G11 = gload<GF>(G + 3 * NGC), G12 = gload<GF>(G + 4 * NGC), G22 = gload<GF>(G + 5 * NGC);
-      F[pt] = G00 * g0 + G01 * g1 + G02 * g2;
-      F[NQ + pt] = G01 * g0 + G11 * g1 + G12 * g2;
-      F[2 * NQ + pt] = G02 * g0 + G12 * g1 + G22 * g2;
-    } else {
-      const T g0 = F[pt], g1 = F[NQ + pt];
-      const T G00 = gload<GF>(G), G01 = gload<GF>(G + NGC), G11 = gload<GF>(G + 2 * NGC);
-      F[pt] = G00 * g0 + G01 * g1;
-      F[NQ + pt] = G01 * g0 + G11 * g1;
-    }
+    last_bwd(part, f, out + b);
   }
 
   // ---- line-owner stages along the last axis (z in 3D, y in 2D).
@@ -417,18 +463,12 @@ struct SF {
   // writes V (point values), keeps the last-axis gradient in gz
   template <bool INTIN>
   __device__ __forceinline__ static void line_fwd(const T* __restrict__ in, T* __restrict__ V, int i, T (&gz)[QP]) {
-    constexpr int L = INTIN ? Mi : M;
-    constexpr int I = NLINE;
-    static_assert(L > 0, "");
+    const int b = lbase(i);
     T v[M], w[QP];
-#pragma unroll
-    for (int k = 0; k < M; ++k) {
-      if (INTIN) v[k] = (k >= 1 && k <= M - 2) ? in[(k - 1) * I + i] : T(0);
-      else v[k] = in[k * I + i];
-    }
+    load_last<INTIN>(in, b, v);
     interp_line<INTIN>(v, w);
 #pragma unroll
-    for (int g = 0; g < QP; ++g) V[g * I + i] = w[g];
+    for (int g = 0; g < QP; ++g) V[loff(g) + b] = w[g];
 #pragma unroll
     for (int c = 0; c < NC; ++c) eo_cell<EO_D>(w, c * n, gz, c * n);
   }
@@ -439,7 +479,7 @@ struct SF {
   __device__ __forceinline__ static void line_quad(T* __restrict__ F, int i, const T (&gz)[QP], T (&fz)[QP],
                                                    const GF& gcell, int pp) {
     constexpr int NGC = D::NGC;
-    constexpr int I = NLINE;
+    const int b = lbase(i);
     // position of the line in the other directions
     int cslot0 = 0, lg0 = 0;
     {
@@ -462,14 +502,14 @@ struct SF {
       const T* Gc = gcell(pp, cslot0 + c * CSTRIDE) + lg0;
 #pragma unroll
       for (int g = 0; g < n; ++g) {
-        const int pt = (c * n + g) * I + i;
+        const int pt = loff(c * n + g) + b;
         const T* G = Gc + g * GSTRIDE;
         if (DIM == 3) {
           const T G00 = gload<GF>(G), G01 = gload<GF>(G + NGC), G02 = gload<GF>(G + 2 * NGC),
                   G11 = gload<GF>(G + 3 * NGC), G12 = gload<GF>(G + 4 * NGC), G22 = gload<GF>(G + 5 * NGC);
-          const T g0 = F[pt], g1 = F[NQ + pt], g2 = gz[c * n + g];
+          const T g0 = F[pt], g1 = F[NQS + pt], g2 = gz[c * n + g];
           F[pt] = G00 * g0 + G01 * g1 + G02 * g2;
-          F[NQ + pt] = G01 * g0 + G11 * g1 + G12 * g2;
+          F[NQS + pt] = G01 * g0 + G11 * g1 + G12 * g2;
           fz[c * n + g] = G02 * g0 + G12 * g1 + G22 * g2;
         } else {
           const T G00 = gload<GF>(G), G01 = gload<GF>(G + NGC), G11 = gload<GF>(G + 2 * NGC);
@@ -486,62 +526,59 @@ struct SF {
   // along that axis: output [Lo][I]
   __device__ __forceinline__ static void line_bwd(const T (&fz)[QP], const T* __restrict__ Vp,
                                                   const T* __restrict__ Vq, T* __restrict__ out, int i) {
-    constexpr int I = NLINE;
+    const int b = lbase(i);
     T part[QP];
 #pragma unroll
     for (int g = 0; g < QP; ++g) {
-      part[g] = Vp[g * I + i];
-      if (DIM == 3) part[g] += Vq[g * I + i];
+      part[g] = Vp[loff(g) + b];
+      if (DIM == 3) part[g] += Vq[loff(g) + b];
     }
-    last_bwd(part, fz, out + i, I);
+    last_bwd(part, fz, out + b);
   }
 
-  // ---- collocation derivative along AX on [O][QP][I], one line per item
+  // ---- collocation derivative along AX (x, or y in 3D) on an array of all
+  // points, one line per item
   template <int AX>
   __device__ __forceinline__ static void der_item(const T* __restrict__ in, T* __restrict__ out, int item) {
-    constexpr int I = ipow(QP, AX);
-    const int i = item % I, o = item / I;
-    const T* src = in + o * QP * I + i;
-    T* dst = out + o * QP * I + i;
+    const int s = lstart<AX>(item);
+    const T* src = in + s;
+    T* dst = out + s;
     T v[QP], y[QP];
 #pragma unroll
-    for (int h = 0; h < QP; ++h) v[h] = src[h * I];
+    for (int h = 0; h < QP; ++h) v[h] = src[lstep<AX>(h)];
 #pragma unroll
     for (int c = 0; c < NC; ++c) eo_cell<EO_D>(v, c * n, y, c * n);
 #pragma unroll
-    for (int g = 0; g < QP; ++g) dst[g * I] = y[g];
+    for (int g = 0; g < QP; ++g) dst[lstep<AX>(g)] = y[g];
   }
 
   // ---- transposed derivative along AX, written (ACC = false) or added
   template <int AX, bool ACC>
   __device__ __forceinline__ static void dert_item(const T* __restrict__ in, T* __restrict__ out, int item) {
-    constexpr int I = ipow(QP, AX);
-    const int i = item % I, o = item / I;
-    const T* src = in + o * QP * I + i;
-    T* dst = out + o * QP * I + i;
+    const int s = lstart<AX>(item);
+    const T* src = in + s;
+    T* dst = out + s;
     T v[QP], y[QP];
 #pragma unroll
-    for (int g = 0; g < QP; ++g) v[g] = src[g * I];
+    for (int g = 0; g < QP; ++g) v[g] = src[lstep<AX>(g)];
 #pragma unroll
     for (int c = 0; c < NC; ++c) eo_cell<EO_DT>(v, c * n, y, c * n);
 #pragma unroll
-    for (int g = 0; g < QP; ++g) dst[g * I] = ACC ? dst[g * I] + y[g] : y[g];
+    for (int g = 0; g < QP; ++g) dst[lstep<AX>(g)] = ACC ? dst[lstep<AX>(g)] + y[g] : y[g];
   }
 
   // ---- transposed derivative along AX in place: the thread reads its whole
   // line before writing it back
   template <int AX>
   __device__ __forceinline__ static void dert_inplace_item(T* __restrict__ F, int item) {
-    constexpr int I = ipow(QP, AX);
-    const int i = item % I, o = item / I;
-    T* p = F + o * QP * I + i;
+    T* p = F + lstart<AX>(item);
     T v[QP], y[QP];
 #pragma unroll
-    for (int g = 0; g < QP; ++g) v[g] = p[g * I];
+    for (int g = 0; g < QP; ++g) v[g] = p[lstep<AX>(g)];
 #pragma unroll
     for (int c = 0; c < NC; ++c) eo_cell<EO_DT>(v, c * n, y, c * n);
 #pragma unroll
-    for (int g = 0; g < QP; ++g) p[g * I] = y[g];
+    for (int g = 0; g < QP; ++g) p[lstep<AX>(g)] = y[g];
   }
 
   // ---- final backward integration along x: like bwd_item<0, false> but every
@@ -549,26 +586,27 @@ struct SF {
   template <typename PUT>
   __device__ __forceinline__ static void bwd0_item(const T* __restrict__ in, int o, int pp, const PUT& put) {
     constexpr int Lout = (NC == 2) ? Mi : M;
-    const T* src = in + o * QP;
+    const T* src = in + rowa(o);
     T w[QP];
 #pragma unroll
     for (int g = 0; g < QP; ++g) w[g] = src[g];
     integ_line<false>(w, LineEpi<PUT>{put, pp, o * Lout});
   }
 
-  // ---- backward integration along AX: [O][QP][I] -> [O][Lout][I], one line per item
-  // NC = 2: interior nodes only (Lout = Mi); NC = 1: all nodes (Lout = M).
-  // ACC: add into the output instead of writing.
+  // ---- backward integration along y (3D): [O][QP][QP] -> [O][Lout][QP], one
+  // line per item (x = item % QP in plane item / QP).  NC = 2: interior
+  // nodes only (Lout = Mi); NC = 1: all nodes (Lout = M).  ACC: add into the
+  // output instead of writing.
   template <int AX, bool ACC>
   __device__ __forceinline__ static void bwd_item(const T* __restrict__ in, T* __restrict__ out, int item) {
-    constexpr int I = ipow(QP, AX);
+    static_assert(AX == 1 && DIM == 3, "backward integration along y in 3D");
     constexpr int Lout = (NC == 2) ? Mi : M;
-    const int i = item % I, o = item / I;
-    const T* src = in + o * QP * I + i;
+    const int i = item % QP, o = item / QP;
+    const T* src = in + lstart<1>(item);
     T w[QP];
 #pragma unroll
-    for (int g = 0; g < QP; ++g) w[g] = src[g * I];
-    integ_line<ACC>(w, LineStore<ACC>{out + o * Lout * I + i, I});
+    for (int g = 0; g < QP; ++g) w[g] = src[lstep<1>(g)];
+    integ_line<ACC>(w, LineStore<ACC>{out, o * Lout, i});
   }
 
   template <bool INTIN, typename GF, typename EPI>
@@ -576,13 +614,13 @@ struct SF {
                                                     const EPI& epi) {
     constexpr int L = INTIN ? Mi : M;
     constexpr int Lo = (NC == 2) ? Mi : M;
-    // scratch: V = scr[0..NQ) (point values, later the transposed sums),
-    // R = scr[NQ..): forward temporaries, then F_0 (and F_1 in 3D).
+    // scratch: V = scr[0..NQS) (point values, later the transposed sums),
+    // R = scr[NQS..): forward temporaries, then F_0 (and F_1 in 3D).
     auto Vp = [&](int pp) { return scr + pp * sscr; };
-    auto Rp = [&](int pp) { return scr + pp * sscr + NQ; };
+    auto Rp = [&](int pp) { return scr + pp * sscr + NQS; };
     T gz[LPT][QP], fz[LPT][QP];
     if constexpr (DIM == 3) {
-      constexpr int T1 = L * L * QP;
+      constexpr int T1 = rowa(L * L);
       TM::template loop<L * L>([&](int pp, int it) { fwd_item<0, INTIN>(in + pp * sin, Rp(pp), it); });
       TM::sync();
       TM::template loop<L * QP>([&](int pp, int it) { fwd_item<1, INTIN>(Rp(pp), Rp(pp) + T1, it); });
@@ -599,7 +637,7 @@ struct SF {
       TM::template loop<2 * ND>([&](int pp, int it) {
         const int ax = it / ND, r = it - ax * ND;
         if (ax == 0) der_item<0>(Vp(pp), Rp(pp), r);
-        else der_item<1>(Vp(pp), Rp(pp) + NQ, r);
+        else der_item<1>(Vp(pp), Rp(pp) + NQS, r);
       });
       TM::sync();
 #pragma unroll
@@ -614,16 +652,16 @@ struct SF {
       TM::template loop<2 * ND>([&](int pp, int it) {
         const int ax = it / ND, r = it - ax * ND;
         if (ax == 0) dert_inplace_item<0>(Rp(pp), r);
-        else dert_inplace_item<1>(Rp(pp) + NQ, r);
+        else dert_inplace_item<1>(Rp(pp) + NQS, r);
       });
       TM::sync();
       // z: their sum + D^T of the z flux, integrated along z into V [Lo][QP][QP]
-      static_assert(Lo * QP * QP <= NQ, "z output exceeds V");
+      static_assert(rowa(Lo * QP) <= NQS, "z output exceeds V");
 #pragma unroll
       for (int l = 0; l < LPT; ++l) {
         int pp, line;
         if (TM::template slot<NLINE>(l, pp, line)) {
-          line_bwd(fz[l], Rp(pp), Rp(pp) + NQ, Vp(pp), line);
+          line_bwd(fz[l], Rp(pp), Rp(pp) + NQS, Vp(pp), line);
         }
       }
       TM::sync();
@@ -710,9 +748,9 @@ struct SF {
           mul *= n;
         }
         const T* Gp = gcell(pp, cslot) + lg;
-        off[u] = pp * sscr + NQ + pt;
+        off[u] = pp * sscr + NQS + (SKEW ? rowa(pt / QP) + pt % QP : pt);
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) g[u][d] = scr[off[u] + d * NQ];
+        for (int d = 0; d < DIM; ++d) g[u][d] = scr[off[u] + d * NQS];
 #pragma unroll
         for (int k = 0; k < NCOMP; ++k) G[u][k] = gload<GF>(Gp + k * NGC);
       }
@@ -722,11 +760,11 @@ struct SF {
         T* F = scr + off[u];
         if (DIM == 3) {
           F[0] = G[u][0] * g[u][0] + G[u][1] * g[u][1] + G[u][2] * g[u][2];
-          F[NQ] = G[u][1] * g[u][0] + G[u][3] * g[u][1] + G[u][4] * g[u][2];
-          F[2 * NQ] = G[u][2] * g[u][0] + G[u][4] * g[u][1] + G[u][5] * g[u][2];
+          F[NQS] = G[u][1] * g[u][0] + G[u][3] * g[u][1] + G[u][4] * g[u][2];
+          F[2 * NQS] = G[u][2] * g[u][0] + G[u][4] * g[u][1] + G[u][5] * g[u][2];
         } else {
           F[0] = G[u][0] * g[u][0] + G[u][1] * g[u][1];
-          F[NQ] = G[u][1] * g[u][0] + G[u][2] * g[u][1];
+          F[NQS] = G[u][1] * g[u][0] + G[u][2] * g[u][1];
         }
       }
     }
@@ -734,8 +772,9 @@ struct SF {
 
   // collocation derivative (TRANS = false: out[g] = sum_h D[g][h] v[h]) or its
   // transpose (TRANS = true: out[h] (+)= sum_g D[g][h] v[g]) on every cell of
-  // a line, ITEMS lines per block; map(pp, item, src, dst, stride) locates an
-  // item's line.
+  // a line, ITEMS lines per block; map(pp, item, src, dst, ax) locates an
+  // item's line (its first point in the input and the output, and its
+  // direction: 0 = x, 1 = y).
   template <bool TRANS, bool ACC, int ITEMS, typename Map>
   __device__ __forceinline__ static void dseg_stage(const Map& map) {
     constexpr int TOT = TM::SPAN * ITEMS;
@@ -744,7 +783,7 @@ struct SF {
     for (int base = TM::lane(); base < TOT; base += U * STEP) {
       T v[U][QP], a[U][QP];
       T* dst[U];
-      int str[U];
+      int axu[U];
       bool ok[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
@@ -760,12 +799,12 @@ struct SF {
           r = it - pp * ITEMS;
         }
         const T* src;
-        map(pp, r, src, dst[u], str[u]);
+        map(pp, r, src, dst[u], axu[u]);
 #pragma unroll
-        for (int h = 0; h < QP; ++h) v[u][h] = src[h * str[u]];
+        for (int h = 0; h < QP; ++h) v[u][h] = src[axu[u] ? lstep<1>(h) : h];
         if (ACC) {
 #pragma unroll
-          for (int h = 0; h < QP; ++h) a[u][h] = dst[u][h * str[u]];
+          for (int h = 0; h < QP; ++h) a[u][h] = dst[u][axu[u] ? lstep<1>(h) : h];
         }
       }
 #pragma unroll
@@ -775,21 +814,19 @@ struct SF {
 #pragma unroll
         for (int c = 0; c < NC; ++c) eo_cell<TRANS ? EO_DT : EO_D>(v[u], c * n, y, c * n);
 #pragma unroll
-        for (int g = 0; g < QP; ++g) dst[u][g * str[u]] = ACC ? a[u][g] + y[g] : y[g];
+        for (int g = 0; g < QP; ++g) dst[u][axu[u] ? lstep<1>(g) : g] = ACC ? a[u][g] + y[g] : y[g];
       }
     }
   }
 
-  // line r of direction AX (I = QP^AX) of a block in arrays [O][QP][I]
+  // line r of direction AX (x, or y in 3D) of a block in point arrays
   // starting at in / out
   template <int AX>
-  __device__ __forceinline__ static void seg(int r, const T* in, T* out, const T*& src, T*& dst, int& stride) {
-    constexpr int I = ipow(QP, AX);
-    const int i = r % I, o = r / I;
-    const int offs = o * QP * I + i;
+  __device__ __forceinline__ static void seg(int r, const T* in, T* out, const T*& src, T*& dst, int& ax) {
+    const int offs = lstart<AX>(r);
     src = in + offs;
     dst = out + offs;
-    stride = I;
+    ax = AX;
   }
 
   template <bool INTIN, typename GF, typename EPI>
@@ -797,27 +834,27 @@ struct SF {
                                                      const EPI& epi) {
     constexpr int L = INTIN ? Mi : M;
     constexpr int Lo = (NC == 2) ? Mi : M;
-    // scratch: V = scr[0..NQ), R = scr[NQ..); F_ax = R + ax*NQ
+    // scratch: V = scr[0..NQS), R = scr[NQS..); F_ax = R + ax*NQS
     auto Vp = [&](int pp) { return scr + pp * sscr; };
-    auto Rp = [&](int pp) { return scr + pp * sscr + NQ; };
+    auto Rp = [&](int pp) { return scr + pp * sscr + NQS; };
     if constexpr (DIM == 3) {
-      constexpr int T1 = L * L * QP;
+      constexpr int T1 = rowa(L * L);
       TM::template loop<L * L>([&](int pp, int it) { fwd_item<0, INTIN>(in + pp * sin, Rp(pp), it); });
       TM::sync();
       TM::template loop<L * QP>([&](int pp, int it) { fwd_item<1, INTIN>(Rp(pp), Rp(pp) + T1, it); });
       TM::sync();
       // z: interpolate to the Gauss points and differentiate along z in registers;
-      // T2 (R + T1) is read while F_2 (R + 2 NQ) is written: 2 NQ >= T1 + T2.
-      static_assert(2 * NQ >= L * L * QP + L * QP * QP, "F_2 overlaps the z input");
+      // T2 (R + T1) is read while F_2 (R + 2 NQS) is written: 2 NQS >= T1 + T2.
+      static_assert(2 * NQS >= rowa(L * L) + rowa(L * QP), "F_2 overlaps the z input");
       TM::template loop<QP * QP>([&](int pp, int it) {
-        fwd_der_last_item<INTIN>(Rp(pp) + T1, Vp(pp), Rp(pp) + 2 * NQ, it);
+        fwd_der_last_item<INTIN>(Rp(pp) + T1, Vp(pp), Rp(pp) + 2 * NQS, it);
       });
       TM::sync();
       constexpr int ND = QP * QP;           // lines per direction
       dseg_stage<false, false, 2 * ND>([&](int pp, int r2, const T*& src, T*& dst, int& st) {
         const int ax = r2 / ND, r = r2 - ax * ND;
         if (ax == 0) seg<0>(r, Vp(pp), Rp(pp), src, dst, st);
-        else seg<1>(r, Vp(pp), Rp(pp) + NQ, src, dst, st);
+        else seg<1>(r, Vp(pp), Rp(pp) + NQS, src, dst, st);
       });
       TM::sync();
       quad_stage(scr, sscr, gcell);
@@ -826,13 +863,13 @@ struct SF {
       dseg_stage<true, false, 2 * ND>([&](int pp, int r2, const T*& src, T*& dst, int& st) {
         const int ax = r2 / ND, r = r2 - ax * ND;
         if (ax == 0) seg<0>(r, Rp(pp), Rp(pp), src, dst, st);
-        else seg<1>(r, Rp(pp) + NQ, Rp(pp) + NQ, src, dst, st);
+        else seg<1>(r, Rp(pp) + NQS, Rp(pp) + NQS, src, dst, st);
       });
       TM::sync();
       // z: F_0 + F_1 + D^T F_2 -> B^T along z -> V [Lo][QP][QP]
-      static_assert(Lo * QP * QP <= NQ, "z output exceeds V");
+      static_assert(rowa(Lo * QP) <= NQS, "z output exceeds V");
       TM::template loop<QP * QP>([&](int pp, int it) {
-        dert_bwd_last_item(Rp(pp) + 2 * NQ, Rp(pp), Rp(pp) + NQ, Vp(pp), it);
+        dert_bwd_last_item(Rp(pp) + 2 * NQS, Rp(pp), Rp(pp) + NQS, Vp(pp), it);
       });
       TM::sync();
       TM::template loop<Lo * QP>([&](int pp, int it) { bwd_item<1, false>(Vp(pp), Rp(pp), it); });
@@ -842,8 +879,9 @@ struct SF {
     } else {
       TM::template loop<L>([&](int pp, int it) { fwd_item<0, INTIN>(in + pp * sin, Rp(pp), it); });
       TM::sync();
-      // y: R [L][QP] -> V [QP][QP] and F_1 = R + NQ (R holds L*QP <= NQ values)
-      TM::template loop<QP>([&](int pp, int it) { fwd_der_last_item<INTIN>(Rp(pp), Vp(pp), Rp(pp) + NQ, it); });
+      // y: R [L][QP] -> V [QP][QP] and F_1 = R + NQS (R holds rowa(L) <= NQS values)
+      static_assert(rowa(L) <= NQS, "F_1 overlaps the y input");
+      TM::template loop<QP>([&](int pp, int it) { fwd_der_last_item<INTIN>(Rp(pp), Vp(pp), Rp(pp) + NQS, it); });
       TM::sync();
       constexpr int ND = QP;                // lines per direction
       dseg_stage<false, false, ND>([&](int pp, int r, const T*& src, T*& dst, int& st) {
@@ -857,7 +895,7 @@ struct SF {
       });
       TM::sync();
       // y: D^T F_1 + V -> B^T along y -> R [Lo][QP] (F_0 = R is dead)
-      TM::template loop<QP>([&](int pp, int it) { dert_bwd_last_item(Rp(pp) + NQ, Vp(pp), nullptr, Rp(pp), it); });
+      TM::template loop<QP>([&](int pp, int it) { dert_bwd_last_item(Rp(pp) + NQS, Vp(pp), nullptr, Rp(pp), it); });
       TM::sync();
       TM::template loop<Lo>([&](int pp, int it) { bwd0_item(Rp(pp), it, pp, epi); });
       TM::sync();

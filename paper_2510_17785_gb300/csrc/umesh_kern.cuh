@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(128) k_ucell_apply(const T* __restrict__ u, co
 
 template <int DIM, int Q, typename T>
 constexpr size_t ucell_smem() {
-  using Dm = Dims<DIM, 1, Q>;
+  using Dm = Dims<DIM, 1, Q, (int)sizeof(T)>;
   return sizeof(T) * (size_t)(2 * Dm::NN + Dm::SCRATCH) * ucpb(Q);
 }
 
@@ -740,10 +740,7 @@ constexpr size_t upatch_smem() {
   for (int k = 0, q = P; q >= 1; ++k, q >>= 1) {
     const int n = q + 1;
     const int nl = DIM == 3 ? n * n * n : n * n;
-    const int NQ = DIM == 3 ? n * n * n : n * n;
-    const int T1 = DIM == 3 ? n * n * n : n * n, T2 = DIM == 3 ? n * n * n : 0;
-    const int R = (T1 + T2) > DIM * NQ ? (T1 + T2) : DIM * NQ;
-    const size_t ap = (size_t)ucpb(q) * (2 * nl + NQ + R);
+    const size_t ap = (size_t)ucpb(q) * (2 * nl + sf_scratch(DIM, 1, q, false, (int)sizeof(T)));
     const size_t tr = (size_t)ucpb(q) * 4 * nl;
     m = ap > m ? ap : m;
     m = tr > m ? tr : m;
