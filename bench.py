@@ -28,13 +28,10 @@ sys.path.insert(0, ROOT)
 
 FP32_PEAK_DERIVED = 152 * 128 * 2 * 2.070e9      # SMs x FP32 lanes x 2 flops x max SM clock
 FP64_PEAK_NOMINAL = 1.25e12                      # GB300 FP64 rate (nominal)
-# DRAM bytes (read + write) of one finest-level colour launch of the FP32 patch kernel on the 3D Q4 32^3
-# workload (colour 0, 3,375 patches), from the ncu capture summarised in profiles/k_patch_q4_f32_sweep.md;
-# None while the kernel has changed since that capture
 # DRAM bytes (read + write) of one finest-level colour launch of the benchmark workload from the ncu capture
-# summarised in profiles/k_patch_q4_f32_sweep.md (variant 10, colour 0: 3,375 patches, 118.7 MB), scaled to the
-# sweep's average launch (29,791 / 8 patches); valid for that variant only
-PATCH_LAUNCH_TRAFFIC = {"variant": 10, "bytes": 118.67e6 * (29791 / 8) / 3375}
+# summarised in profiles/k_patch_q4_f32_sweep.md (variant 10, colour 0: 3,375 patches, 111.6 MB read + 6.7 MB
+# written), scaled to the sweep's average launch (29,791 / 8 patches); valid for that variant only
+PATCH_LAUNCH_TRAFFIC = {"variant": 10, "bytes": (111.555e6 + 6.728e6) * (29791 / 8) / 3375}
 METRIC = "patch-smoother DoFs/s and CG time-to-1e-8 residual: mixed/learned vs plain FP64, 1 GB300"
 
 
