@@ -121,8 +121,12 @@ typedef struct pmg_options {
                             p-MG and the Evaluate step) read the geometry
                             tensors G rounded to BF16 (8-bit significand,
                             round to nearest even); the GMG level operators
-                            keep FP32 G.  An accuracy evaluation of BF16 G:
-                            the values are held in FP32 arrays              */
+                            keep FP32 G.  The patch kernels load them as
+                            packed pairs of BF16 components (half the bytes
+                            and load instructions of FP32 G); launch shapes
+                            that stage G in shared memory read an FP32 copy
+                            of the same rounded values, so every shape gives
+                            the same bits                                    */
   int dense_local;       /* tabulated local solves: the local solve of a patch
                             (N_MG V-cycles from zero with fixed intervals) is
                             a fixed linear map, tabulated at set-up by

@@ -106,6 +106,39 @@ def element_matrix(cell_x: np.ndarray, kappa: float, q: int, n_quad: int | None 
     return np.einsum("g,gaj,gbj->ab", wts * kappa * det, grad, grad)
 
 
+def bf16_round(x) -> np.ndarray:
+    """x rounded to FP32 and then to the nearest BF16 number (8-bit
+    significand, ties to even), returned in FP64: the value that a BF16 copy of
+    an FP32 quantity holds (the mixed-precision form's operator data, where
+    the error budget allows it).  Finite inputs."""
+    f = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    b = f.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def element_matrix_G(cell_x: np.ndarray, kappa: float, q: int, n_quad: int | None = None,
+                     g_round=None) -> np.ndarray:
+    """The element matrix of element_matrix written through the per-point
+    tensors G_g = w_g kappa det J J^-1 J^-T (A^c_ab = sum_g grad_hat phi_a . G_g
+    grad_hat phi_b), each component of G passed through g_round first (None:
+    exact).  With g_round = bf16_round it is the operator the patch kernels
+    apply when they read BF16 geometry."""
+    dim = cell_x.shape[1]
+    n_quad = q + 1 if n_quad is None else n_quad
+    pts, wts = tensor_rule(dim, n_quad)
+    _, gphi = basis_at(dim, q, n_quad)
+    J = jacobians(cell_x, pts)
+    det = np.linalg.det(J)
+    if np.any(det <= 0.0):
+        raise DegenerateCell("det J <= 0 at a quadrature point")
+    Jinv = np.linalg.inv(J)
+    G = np.einsum("g,gkj,glj->gkl", wts * kappa * det, Jinv, Jinv)
+    if g_round is not None:
+        G = g_round(G)
+    return np.einsum("gak,gkl,gbl->ab", gphi, G, gphi)
+
+
 def element_load(cell_x: np.ndarray, f, q: int, n_quad: int) -> np.ndarray:
     """int f phi_a over the cell with the n_quad-point Gauss rule per direction."""
     dim = cell_x.shape[1]

@@ -87,8 +87,10 @@ class PatchLevel:
 
 
 class Patch:
-    def __init__(self, mesh: fem.StructuredMesh, v, levels, elem_cache=None):
+    def __init__(self, mesh: fem.StructuredMesh, v, levels, elem_cache=None, element_fn=None):
         self.mesh, self.v, self.levels = mesh, tuple(v), list(levels)
+        # element matrices: element_fn(cell vertices, kappa, q), default fem.element_matrix
+        self.element_fn = fem.element_matrix if element_fn is None else element_fn
         d = mesh.dim
         self.cells = [tuple(v[k] - 1 + s[k] for k in range(d)) for s in fem._lex(d, 2)]
         cache = {} if elem_cache is None else elem_cache
@@ -108,7 +110,7 @@ class Patch:
         for c in self.cells:
             key = (q, c)
             if key not in cache:
-                cache[key] = fem.element_matrix(m.cell_vertices(c), m.kappa[m.cell_index(c)], q)
+                cache[key] = self.element_fn(m.cell_vertices(c), m.kappa[m.cell_index(c)], q)
             idx = [pos[int(n)] for n in m.cell_nodes(q, c)]
             Acl[np.ix_(idx, idx)] += cache[key]
         ii = [pos[n] for n in interior]
@@ -257,8 +259,9 @@ class PatchSmoother:
 
     def __init__(self, mesh: fem.StructuredMesh, p: int, levels=None, sm: Smoother | None = None,
                  bounds_fn=None, n_cycles: int = 1, order: str = "colour", additive: bool = False,
-                 theta: float = 1.0):
+                 theta: float = 1.0, element_fn=None):
         self.mesh, self.p = mesh, p
+        self.element_fn = element_fn   # patch element matrices (None: fem.element_matrix)
         self.order = order             # "colour": colour-major; "vertex": plain vertex order
         self.additive, self.theta = additive, theta
         self._mult = None
@@ -274,7 +277,7 @@ class PatchSmoother:
     def patch(self, v) -> Patch:
         v = tuple(v)
         if v not in self._patches:
-            self._patches[v] = Patch(self.mesh, v, self.levels, self._cache)
+            self._patches[v] = Patch(self.mesh, v, self.levels, self._cache, self.element_fn)
         return self._patches[v]
 
     def bounds(self, v):

@@ -29,4 +29,27 @@ int launch_round_bf16(const float* x, float* y, size_t n, cudaStream_t s) {
   PMG_CHECK_LAUNCH();
   return ST_OK;
 }
+
+// [cell][ncomp][npt] FP32 values that are BF16 numbers -> [cell][(ncomp + 1) / 2][npt] words holding
+// components 2j (low half) and 2j + 1 (high half, zero past the last component); exact
+__global__ void k_pack_bf16(const float* __restrict__ x, unsigned* __restrict__ y, size_t ncell, int ncomp,
+                            int npt) {
+  const int npair = (ncomp + 1) / 2;
+  const size_t n = ncell * npair * (size_t)npt;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int pt = (int)(i % npt);
+    const size_t r = i / npt;
+    const int j = (int)(r % npair);
+    const size_t c = r / npair;
+    const float* xc = x + c * ncomp * (size_t)npt + pt;
+    const unsigned lo = __float_as_uint(xc[(2 * j) * (size_t)npt]) >> 16;
+    const unsigned hi = 2 * j + 1 < ncomp ? __float_as_uint(xc[(2 * j + 1) * (size_t)npt]) & 0xffff0000u : 0u;
+    y[i] = hi | lo;
+  }
+}
+int launch_pack_bf16(const float* x, unsigned* y, size_t ncell, int ncomp, int npt, cudaStream_t s) {
+  k_pack_bf16<<<grid_for(ncell * ((ncomp + 1) / 2) * (size_t)npt, 256), 256, 0, s>>>(x, y, ncell, ncomp, npt);
+  PMG_CHECK_LAUNCH();
+  return ST_OK;
+}
 }  // namespace pmg

@@ -21,6 +21,10 @@ template <int DIM, typename T>
 int launch_patch(int P, int mode, int variant, const PatchArgs<T>& a, cudaStream_t s);
 // y = x rounded to BF16 (round to nearest even) and widened back to FP32
 int launch_round_bf16(const float* x, float* y, size_t n, cudaStream_t s);
+// geometry tensors already rounded to BF16, [cell][ncomp][npt] FP32 -> the
+// packed pairs the FP32 patch kernels read, [cell][(ncomp + 1) / 2][npt]
+// words (component 2j in the low half, 2j + 1 in the high half)
+int launch_pack_bf16(const float* x, unsigned* y, size_t ncell, int ncomp, int npt, cudaStream_t s);
 // one persistent cooperative launch sweeping every colour of a level
 // (pa.n_colours lists, grid barrier between colours); *grid_out = CTAs used
 template <int DIM, typename T>

@@ -28,6 +28,8 @@ __host__ __device__ constexpr int nlevels(int P) { return P <= 1 ? 1 : 1 + nleve
 template <typename T>
 struct LevelArgs {
   const T* G;          // geometry tensors of degree q: [cells][ncomp][(q+1)^d]
+  const unsigned* Gb;  // FP32 kernels: the same tensors as BF16 pairs, [cells][(ncomp+1)/2][(q+1)^d]
+                       // (component 2j in the low half of a word, 2j + 1 in the high half), or NULL
   const T* dinv;       // 1 / diag(A_q) on the global degree-q grid, 0 on Dirichlet
   const T* bounds;     // [patches][2]: Chebyshev interval (lo, hi), q > 1
   const T* dense;      // small levels: [patches][Ni][Ni] row-major patch matrix A_{j,q}
@@ -308,19 +310,32 @@ struct PatchKernel {
     }
   };
 
+  // geometry of cell `slot` of patch pp in global memory: FP32/FP64 tensors,
+  // or (FP32, when the level has them) the packed BF16 pairs, one word per
+  // pair addressed like an FP32 value
+  template <int stride, int pstride>
+  struct GlobalGeom {
+    static constexpr bool kPackable = sizeof(T) == 4;
+    const T* G;
+    bool packed;
+    __device__ const T* operator()(int pp, int slot) const {
+      // the cell list follows the PPB patch arrays in dynamic shared memory
+      const int* cl = reinterpret_cast<const int*>(pmg_smem + sizeof(T) * (size_t)PS * PPB);
+      return G + (size_t)cl[pp * CST + slot] * (packed ? pstride : stride);
+    }
+  };
+
   template <int K>
   __device__ auto gfun() const {
     constexpr int q = L::q(K);
-    constexpr int stride = Dims<DIM, 2, q, (int)sizeof(T)>::NCOMP * ipow(q + 1, DIM);
+    using Dq = Dims<DIM, 2, q, (int)sizeof(T)>;
+    constexpr int stride = Dq::NCOMP * Dq::NGC;
     if constexpr (C::GSMEM && K == 0) {                 // staged in shared memory by load_level
       return SharedGeom<stride>{};
     } else {
-      const T* G = a->lv[K].G;
-      // the cell list follows the PPB patch arrays in dynamic shared memory
-      return [G](int pp, int slot) {
-        const int* cl = reinterpret_cast<const int*>(pmg_smem + sizeof(T) * (size_t)PS * PPB);
-        return G + (size_t)cl[pp * CST + slot] * stride;
-      };
+      const bool packed = sizeof(T) == 4 && a->lv[K].Gb != nullptr;
+      const T* G = packed ? reinterpret_cast<const T*>(a->lv[K].Gb) : a->lv[K].G;
+      return GlobalGeom<stride, ((Dq::NCOMP + 1) / 2) * Dq::NGC>{G, packed};
     }
   }
 

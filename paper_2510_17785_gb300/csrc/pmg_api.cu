@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/pmg.h"
@@ -35,6 +36,7 @@ struct PLevel {
   double* G64 = nullptr;
   float* G32 = nullptr;
   float* Gp32 = nullptr;       // the G the FP32 patch kernels read: G32, or G32 rounded to BF16
+  unsigned* Gb32 = nullptr;    // geometry_bf16: Gp32 as packed BF16 pairs (what the FP32 patch kernels load)
   double* dinv64 = nullptr;
   float* dinv32 = nullptr;
   double* bounds64 = nullptr;
@@ -223,6 +225,8 @@ const double* GPatchof<double>(const PLevel& pl) { return pl.G64; }
 template <>
 const float* GPatchof<float>(const PLevel& pl) { return pl.Gp32; }
 template <typename T>
+const unsigned* GPackedof(const PLevel& pl) { return std::is_same<T, float>::value ? pl.Gb32 : nullptr; }
+template <typename T>
 const T* Dinvof(const PLevel& pl);
 template <>
 const double* Dinvof<double>(const PLevel& pl) { return pl.dinv64; }
@@ -265,6 +269,7 @@ PatchArgs<T> patch_args(pmg_ctx* c, int level) {
   for (int k = 0; k < c->npl; ++k) {
     a.lv[k].fdm = Fdmof<T>(c, c->plevels[k]);
     a.lv[k].G = GPatchof<T>(h.pl[k]);
+    a.lv[k].Gb = GPackedof<T>(h.pl[k]);
     a.lv[k].dinv = Dinvof<T>(h.pl[k]);
     a.lv[k].bounds = Boundsof<T>(h.pl[k]);
     a.lv[k].dense = Denseof<T>(h.pl[k]);
@@ -1053,6 +1058,9 @@ int pmg_setup(pmg_ctx* ctx) {
         if (ctx->opt.geometry_bf16) {
           DALLOC(pl.Gp32, ng);
           ST(launch_round_bf16(pl.G32, pl.Gp32, ng, s));
+          const int ncomp = d * (d + 1) / 2;
+          DALLOC(pl.Gb32, h.ncells * (size_t)((ncomp + 1) / 2) * ipow_sz(q + 1, d));
+          ST(launch_pack_bf16(pl.Gp32, pl.Gb32, h.ncells, ncomp, (int)ipow_sz(q + 1, d), s));
         }
       }
       if (d == 2) ST(launch_diag<2>(pl.G64, h.N, q, diag, pl.dinv64, pl.dinv32, s));

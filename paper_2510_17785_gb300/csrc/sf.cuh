@@ -69,6 +69,36 @@ __device__ __forceinline__ T gload(const T* p) {
   if constexpr (GeomInShared<GF>::value) return *p;
   else return __ldg(p);
 }
+// A functor that declares `static constexpr bool kPackable = true` and a
+// member `bool packed` may serve FP32 geometry as BF16 pairs: when `packed`
+// is set, its base pointers address words of two BF16 components (2j in the
+// low half, 2j + 1 in the high half), pair j at offset j * (points per cell).
+template <typename GF, typename = void>
+struct GeomPackable {
+  static constexpr bool value = false;
+};
+template <typename GF>
+struct GeomPackable<GF, decltype((void)GF::kPackable)> {
+  static constexpr bool value = GF::kPackable;
+};
+// the NCOMP components of G at point p of a cell (component stride NGC)
+template <int NCOMP, int NGC, typename GF, typename T>
+__device__ __forceinline__ void gtensor(const GF& gcell, const T* p, T (&g)[NCOMP]) {
+  if constexpr (sizeof(T) == 4 && GeomPackable<GF>::value) {
+    if (gcell.packed) {
+      const unsigned* w = reinterpret_cast<const unsigned*>(p);
+#pragma unroll
+      for (int j = 0; j < (NCOMP + 1) / 2; ++j) {
+        const unsigned x = __ldg(w + j * NGC);
+        g[2 * j] = __uint_as_float(x << 16);                 // BF16 -> FP32 is exact
+        if (2 * j + 1 < NCOMP) g[2 * j + 1] = __uint_as_float(x & 0xffff0000u);
+      }
+      return;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NCOMP; ++k) g[k] = gload<GF>(p + k * NGC);
+}
 
 template <typename T>
 __device__ __forceinline__ T* smem_ptr(T* p) {
@@ -503,16 +533,16 @@ struct SF {
 #pragma unroll
       for (int g = 0; g < n; ++g) {
         const int pt = loff(c * n + g) + b;
-        const T* G = Gc + g * GSTRIDE;
+        T Gv[D::NCOMP];
+        gtensor<D::NCOMP, NGC>(gcell, Gc + g * GSTRIDE, Gv);
         if (DIM == 3) {
-          const T G00 = gload<GF>(G), G01 = gload<GF>(G + NGC), G02 = gload<GF>(G + 2 * NGC),
-                  G11 = gload<GF>(G + 3 * NGC), G12 = gload<GF>(G + 4 * NGC), G22 = gload<GF>(G + 5 * NGC);
+          const T G00 = Gv[0], G01 = Gv[1], G02 = Gv[2], G11 = Gv[3], G12 = Gv[4], G22 = Gv[5];
           const T g0 = F[pt], g1 = F[NQS + pt], g2 = gz[c * n + g];
           F[pt] = G00 * g0 + G01 * g1 + G02 * g2;
           F[NQS + pt] = G01 * g0 + G11 * g1 + G12 * g2;
           fz[c * n + g] = G02 * g0 + G12 * g1 + G22 * g2;
         } else {
-          const T G00 = gload<GF>(G), G01 = gload<GF>(G + NGC), G11 = gload<GF>(G + 2 * NGC);
+          const T G00 = Gv[0], G01 = Gv[1], G11 = Gv[2];
           const T g0 = F[pt], g1 = gz[c * n + g];
           F[pt] = G00 * g0 + G01 * g1;
           fz[c * n + g] = G01 * g0 + G11 * g1;
@@ -751,8 +781,7 @@ struct SF {
         off[u] = pp * sscr + NQS + (SKEW ? rowa(pt / QP) + pt % QP : pt);
 #pragma unroll
         for (int d = 0; d < DIM; ++d) g[u][d] = scr[off[u] + d * NQS];
-#pragma unroll
-        for (int k = 0; k < NCOMP; ++k) G[u][k] = gload<GF>(Gp + k * NGC);
+        gtensor<NCOMP, NGC>(gcell, Gp, G[u]);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {

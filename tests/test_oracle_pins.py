@@ -119,6 +119,36 @@ def test_element_matrix_rigid_motion_and_scaling():
     assert np.allclose(fem.element_matrix(0.25 * X, 1.0, 3), 0.25 * A, atol=1e-12)   # h^(d-2)
 
 
+def test_bf16_rounding_matches_torch_and_hand_cases():
+    """The oracle's BF16 rounding against torch's float32 -> bfloat16
+    conversion (a library routine) and hand-worked ties: BF16 keeps 7 stored
+    significand bits, so 1 + 2^-8 and 1 + 3 2^-8 are ties between neighbours
+    2^-7 apart and go to the even significand."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(4)
+    x = rng.uniform(-3, 3, 20000) * 10.0 ** rng.uniform(-8, 8, 20000)
+    ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).double().numpy()
+    assert np.array_equal(fem.bf16_round(x), ref)
+    assert fem.bf16_round(1 + 2.0 ** -8) == 1.0
+    assert fem.bf16_round(1 + 3 * 2.0 ** -8) == 1 + 2.0 ** -6
+    assert fem.bf16_round(-(1 + 2.0 ** -7)) == -(1 + 2.0 ** -7)       # representable: unchanged
+
+
+@pytest.mark.parametrize("dim,q", [(2, 5), (3, 3)])
+def test_element_matrix_through_G_and_its_bf16_form(dim, q):
+    """The explicit-G element matrix equals the plain one; with G rounded to
+    BF16 it stays symmetric with constants in its kernel, and differs from the
+    exact matrix by at most the rounding of G (relative 2^-8 per component)."""
+    X = _random_cell(dim, 5)
+    A = fem.element_matrix(X, 2.5, q)
+    assert np.abs(fem.element_matrix_G(X, 2.5, q) - A).max() < 1e-13 * np.abs(A).max()
+    B = fem.element_matrix_G(X, 2.5, q, g_round=fem.bf16_round)
+    assert np.abs(B - B.T).max() < 1e-14 * np.abs(B).max()
+    assert np.abs(B @ np.ones(len(B))).max() < 1e-13 * np.abs(B).max()
+    d = np.abs(B - A).max() / np.abs(A).max()
+    assert 1e-5 < d < dim * 2.0 ** -8
+
+
 # ----------------------------------------------------------------- meshes
 def _read_golden(name):
     rows = []
