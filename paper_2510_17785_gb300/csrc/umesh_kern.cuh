@@ -47,7 +47,13 @@
 namespace pmg {
 
 constexpr int UMAXC = PMG_UMAXC;      // cells per patch the kernels accept
-constexpr int UNT = 128;              // threads per CTA of the patch kernel
+// threads per CTA of the patch kernel at degree p.  One CTA works on one
+// patch at a time, so the threads are the patch's parallelism: measured on a
+// batch of eight problems of degrees 2-8, 128 threads everywhere took 2.60 s,
+// 256 everywhere 1.65 s, 512 from degree 6 on (256 below) 1.27 s, 384 there
+// 1.36 s; giving the workspace slice to shared memory at one CTA per SM was
+// slower (1.85 s) than keeping it in L1/L2 at several.
+__host__ __device__ constexpr int unt(int p) { return p >= 6 ? 512 : 256; }
 constexpr int UMAXL = 4;              // p-levels (p <= 8: p, p/2, p/4, 1)
 
 __host__ __device__ constexpr int ucpb(int q) { return q <= 4 ? 4 : 2; }   // cells per pass
@@ -265,7 +271,7 @@ struct ULanczos {
 template <int DIM, int P, typename T, int MODE>
 struct UPatch {
   static constexpr int NL = nlevels(P);
-  static constexpr int NT = UNT;
+  static constexpr int NT = unt(P);
   const UPatchArgs<T>* a;
   T* ws;               // this CTA's slice
   int pid, ncell, item;
@@ -754,7 +760,7 @@ __host__ __device__ constexpr size_t upatch_smem_aligned() {
 }
 
 template <int DIM, int P, typename T, int MODE>
-__global__ void __launch_bounds__(UNT) k_upatch(const __grid_constant__ UPatchArgs<T> args) {
+__global__ void __launch_bounds__(unt(P)) k_upatch(const __grid_constant__ UPatchArgs<T> args) {
   UPatch<DIM, P, T, MODE> k;
   k.a = &args;
   constexpr size_t WS_OFF = upatch_smem_aligned<DIM, P, T>();
@@ -771,9 +777,9 @@ __global__ void __launch_bounds__(UNT) k_upatch(const __grid_constant__ UPatchAr
 }
 
 template <int DIM, int P>
-__global__ void __launch_bounds__(UNT) k_ulanczos(const __grid_constant__ UPatchArgs<double> args,
+__global__ void __launch_bounds__(unt(P)) k_ulanczos(const __grid_constant__ UPatchArgs<double> args,
                                                   const __grid_constant__ ULanczos z) {
-  __shared__ double red[UNT / 32 + 2], al[64], be[64], cf[64];
+  __shared__ double red[unt(P) / 32 + 2], al[64], be[64], cf[64];
   UPatch<DIM, P, double, MODE_LOCAL> k;
   k.a = &args;
   k.ws = args.ws + (size_t)blockIdx.x * args.ws_stride;

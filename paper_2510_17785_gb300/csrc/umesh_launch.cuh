@@ -43,7 +43,7 @@ int upatch_launch_P(int mode, const UPatchArgs<T>& a, int grid, cudaStream_t s) 
           return ST_CUDA;
         attr[0][dev & 63] = sm;
       }
-      k_upatch<DIM, P, T, MODE_SWEEP><<<grid, UNT, sm, s>>>(a);
+      k_upatch<DIM, P, T, MODE_SWEEP><<<grid, unt(P), sm, s>>>(a);
     } else {
       if (attr[1][dev & 63] < sm) {
         if (cudaFuncSetAttribute(k_upatch<DIM, P, T, MODE_LOCAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -51,7 +51,7 @@ int upatch_launch_P(int mode, const UPatchArgs<T>& a, int grid, cudaStream_t s) 
           return ST_CUDA;
         attr[1][dev & 63] = sm;
       }
-      k_upatch<DIM, P, T, MODE_LOCAL><<<grid, UNT, sm, s>>>(a);
+      k_upatch<DIM, P, T, MODE_LOCAL><<<grid, unt(P), sm, s>>>(a);
     }
     return cudaPeekAtLastError() == cudaSuccess ? ST_OK : ST_CUDA;
   }
@@ -77,7 +77,7 @@ int ulanczos_launch(const UPatchArgs<double>& a, const ULanczos& z, int grid, cu
         return ST_CUDA;
       attr[dev & 63] = true;
     }
-    k_ulanczos<DIM, P><<<grid, UNT, sm, s>>>(a, z);
+    k_ulanczos<DIM, P><<<grid, unt(P), sm, s>>>(a, z);
     return cudaPeekAtLastError() == cudaSuccess ? ST_OK : ST_CUDA;
   }
 }
