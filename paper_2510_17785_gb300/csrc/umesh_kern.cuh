@@ -56,7 +56,20 @@ constexpr int UMAXC = PMG_UMAXC;      // cells per patch the kernels accept
 __host__ __device__ constexpr int unt(int p) { return p >= 6 ? 512 : 256; }
 constexpr int UMAXL = 4;              // p-levels (p <= 8: p, p/2, p/4, 1)
 
-__host__ __device__ constexpr int ucpb(int q) { return q <= 4 ? 4 : 2; }   // cells per pass
+__host__ __device__ constexpr int ucpb(int q) { return q <= 4 ? 4 : 2; }   // cells per pass (global operator)
+
+// cells per pass of the patch kernel (nt threads) on a level of degree q:
+// about one work item per thread in the line stages (n^(d-1) lines per cell
+// and direction, n = q + 1), at most 16, and the cell buffers within 96 KB
+template <int DIM, typename T>
+__host__ __device__ constexpr int ucpb_patch(int q, int nt) {
+  const int n = q + 1;
+  const int lines = DIM == 3 ? n * n : n;
+  const int per_cell = (int)sizeof(T) * (2 * lines * n + sf_scratch(DIM, 1, q, false, (int)sizeof(T)));
+  const int by_threads = nt / lines < 1 ? 1 : (nt / lines > 16 ? 16 : nt / lines);
+  const int by_smem = (96 * 1024) / per_cell < 1 ? 1 : (96 * 1024) / per_cell;
+  return by_threads < by_smem ? by_threads : by_smem;
+}
 
 __device__ __forceinline__ double gl_node(int q, int i) { return c_rules.gll[q][i]; }
 
@@ -324,7 +337,7 @@ struct UPatch {
   // closure of u), every output through the epilogue
   template <int K, bool CLOSURE>
   __device__ void apply(int which, int kind, int it) {
-    constexpr int Q = q<K>(), NLOC = nloc<K>(), CPB = ucpb(Q);
+    constexpr int Q = q<K>(), NLOC = nloc<K>(), CPB = ucpb_patch<DIM, T>(Q, NT);
     using S = SF<DIM, 1, Q, T, NT, CPB>;
     using Dm = typename S::D;
     constexpr int PS = 2 * NLOC + Dm::SCRATCH;
@@ -420,7 +433,7 @@ struct UPatch {
   // r_{K+1} = P^T res_K
   template <int K>
   __device__ void restrict_res() {
-    constexpr int QF = q<K>(), QC = q<K + 1>(), NF = nloc<K>(), NCL = nloc<K + 1>(), CPB = ucpb(QF);
+    constexpr int QF = q<K>(), QC = q<K + 1>(), NF = nloc<K>(), NCL = nloc<K + 1>(), CPB = ucpb_patch<DIM, T>(QF, NT);
     const int16_t* cmap = a->p_cmap[K] + (size_t)pid * UMAXC * NF;
     const int32_t* as = a->p_astart[K] + (size_t)pid * (a->nimax[K] + 1);
     const T* res = vec(K, UV_RES);
@@ -461,7 +474,7 @@ struct UPatch {
   // d_K += P d_{K+1}
   template <int K>
   __device__ void prolong_add() {
-    constexpr int QF = q<K>(), QC = q<K + 1>(), NF = nloc<K>(), NCL = nloc<K + 1>(), CPB = ucpb(QF);
+    constexpr int QF = q<K>(), QC = q<K + 1>(), NF = nloc<K>(), NCL = nloc<K + 1>(), CPB = ucpb_patch<DIM, T>(QF, NT);
     const int16_t* cmapc = a->p_cmap[K + 1] + (size_t)pid * UMAXC * NCL;
     const T* dc = vec(K + 1, UV_D);
     T* Y = Yg();
@@ -746,8 +759,9 @@ constexpr size_t upatch_smem() {
   for (int k = 0, q = P; q >= 1; ++k, q >>= 1) {
     const int n = q + 1;
     const int nl = DIM == 3 ? n * n * n : n * n;
-    const size_t ap = (size_t)ucpb(q) * (2 * nl + sf_scratch(DIM, 1, q, false, (int)sizeof(T)));
-    const size_t tr = (size_t)ucpb(q) * 4 * nl;
+    const int cpb = ucpb_patch<DIM, T>(q, unt(P));
+    const size_t ap = (size_t)cpb * (2 * nl + sf_scratch(DIM, 1, q, false, (int)sizeof(T)));
+    const size_t tr = (size_t)cpb * 4 * nl;
     m = ap > m ? ap : m;
     m = tr > m ? tr : m;
   }
