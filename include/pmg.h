@@ -434,8 +434,11 @@ int pmg_mlp_grad(int device, const float* params_dev, const float* norm_dev, con
  * mean batch loss of every epoch to loss_hist_host (may be NULL). */
 int pmg_mlp_train(int device, float* params_dev, const float* norm_dev, const float* X_dev,
                   const float* T_dev, int64_t n, const pmg_train_opts* opt, float* loss_hist_host);
-/* Y (n x 2 device) = predicted (log theta_max, log theta_min); bf16 != 0
- * rounds weights and activations to BF16 (FP32 accumulation). */
+/* Y (n x 2 device) = predicted (log theta_max, log theta_min); bf16 != 0:
+ * BF16 weights, biases, inputs and hidden activations, the three layers as
+ * tensor-core products (warp-level m16n8k16) with FP32 accumulation; bf16 = 0:
+ * FP32 throughout.  Any n >= 0 (a last tile of fewer than 16 samples is
+ * padded internally, nothing is written past Y_dev[2n - 1]). */
 int pmg_mlp_predict(int device, const float* params_dev, const float* norm_dev, const float* X_dev,
                     int64_t n, int bf16, float* Y_dev, void* stream);
 /* Install a trained network (host arrays) for PMG_BOUNDS_MLP. */

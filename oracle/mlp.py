@@ -68,6 +68,17 @@ def forward(theta, X):
     return y, (X, z1, h1, z2, h2)
 
 
+def forward_rounded(theta, X, rnd):
+    """forward with every stored quantity passed through rnd: the weights
+    and biases, the inputs and the two hidden activations (after the ReLU);
+    the sums themselves in FP64.  With rnd = fem.bf16_round this is the
+    BF16-inference form (BF16 operands, wide accumulation)."""
+    W1, b1, W2, b2, W3, b3 = (rnd(a) for a in unpack(theta))
+    h1 = rnd(np.maximum(rnd(X) @ W1.T + b1, 0.0))
+    h2 = rnd(np.maximum(h1 @ W2.T + b2, 0.0))
+    return h2 @ W3.T + b3
+
+
 def loss(theta, X, T, asym: float = 4.0) -> float:
     y, _ = forward(theta, X)
     w = np.ones_like(y)

@@ -208,11 +208,10 @@ __global__ void k_features(const double* __restrict__ coords, const double* __re
 }
 
 // ------------------------------------------------------------ inference
-// one thread per sample; parameters in shared memory (BF16 or FP32)
-template <bool BF16>
+// FP32 inference: one thread per sample, parameters in shared memory
 __global__ void k_mlp_infer(const float* __restrict__ params, const float* __restrict__ norm,
                             const float* __restrict__ X, int64_t n, float* __restrict__ Y) {
-  using W = typename std::conditional<BF16, __nv_bfloat16, float>::type;
+  using W = float;
   __shared__ W w[NP];
   __shared__ float nm[36];
   for (int i = threadIdx.x; i < NP; i += blockDim.x) w[i] = (W)params[i];
@@ -221,28 +220,148 @@ __global__ void k_mlp_infer(const float* __restrict__ params, const float* __res
   for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
     float x[NF];
     for (int i = 0; i < NF; ++i) {
-      float v = (X[s * NF + i] - nm[i]) / nm[NF + i];
-      x[i] = BF16 ? __bfloat162float(__float2bfloat16(v)) : v;
+      x[i] = (X[s * NF + i] - nm[i]) / nm[NF + i];
     }
     float h1[NH];
     for (int r = 0; r < NH; ++r) {
       float a = (float)w[OB1 + r];
       for (int i = 0; i < NF; ++i) a += (float)w[OW1 + r * NF + i] * x[i];
-      a = fmaxf(a, 0.f);
-      h1[r] = BF16 ? __bfloat162float(__float2bfloat16(a)) : a;
+      h1[r] = fmaxf(a, 0.f);
     }
     float y0 = (float)w[OB3], y1 = (float)w[OB3 + 1];
     for (int r = 0; r < NH; ++r) {
       float a = (float)w[OB2 + r];
       for (int i = 0; i < NH; ++i) a += (float)w[OW2 + r * NH + i] * h1[i];
       a = fmaxf(a, 0.f);
-      if (BF16) a = __bfloat162float(__float2bfloat16(a));
       y0 += (float)w[OW3 + r] * a;
       y1 += (float)w[OW3 + NH + r] * a;
     }
     // back to (log theta_max, log theta_min)
     Y[s * NO] = y0 * nm[2 * NF + 2] + nm[2 * NF];
     Y[s * NO + 1] = y1 * nm[2 * NF + 3] + nm[2 * NF + 1];
+  }
+}
+
+// BF16 inference on the tensor cores: one warp per tile of 16 samples, the
+// three layers as mma.sync m16n8k16 products with BF16 operands and FP32
+// accumulation (16x16 inputs x 16x64 W1^T, 16x64 x 64x64 W2^T, 16x64 x 64x8
+// W3^T with W3 padded to 8 rows).  Weights, biases, inputs and the two hidden
+// activations are BF16 values; sums are FP32.  Fragment layouts (PTX ISA,
+// m16n8k16 with .bf16): lane = 4 g + t; A holds rows g and g + 8, columns
+// 2t, 2t+1, 2t+8, 2t+9 of the 16x16 tile; B holds rows (k) 2t, 2t+1, 2t+8,
+// 2t+9 of column (n) g; C/D holds rows g, g + 8 and columns 2t, 2t+1.  The
+// C tiles 2k and 2k+1 of one layer are exactly the A tile k of the next, so
+// activations never leave the registers.
+constexpr int MW1 = NF / 2 + 4;     // words per W1 row in shared memory (padded: conflict-free B loads)
+constexpr int MW2 = NH / 2 + 4;     // words per W2 / W3 row
+constexpr int MMA_THREADS = 128;
+
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);    // lo in the low half
+  unsigned u;
+  memcpy(&u, &v, 4);
+  return u;
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// C tiles (n-tiles 0..7 of a 16x64 layer output) + bias, ReLU, rounded to BF16
+// -> the four A tiles of the next layer
+__device__ __forceinline__ void act_to_a(float (&c)[8][4], const float* bias, int t, unsigned (&a)[4][4]) {
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    const float b0 = bias[nt * 8 + 2 * t], b1 = bias[nt * 8 + 2 * t + 1];
+    c[nt][0] = fmaxf(c[nt][0] + b0, 0.f);
+    c[nt][1] = fmaxf(c[nt][1] + b1, 0.f);
+    c[nt][2] = fmaxf(c[nt][2] + b0, 0.f);
+    c[nt][3] = fmaxf(c[nt][3] + b1, 0.f);
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    a[k][0] = pack_bf16(c[2 * k][0], c[2 * k][1]);
+    a[k][1] = pack_bf16(c[2 * k][2], c[2 * k][3]);
+    a[k][2] = pack_bf16(c[2 * k + 1][0], c[2 * k + 1][1]);
+    a[k][3] = pack_bf16(c[2 * k + 1][2], c[2 * k + 1][3]);
+  }
+}
+
+__global__ void __launch_bounds__(MMA_THREADS) k_mlp_infer_mma(const float* __restrict__ params,
+                                                               const float* __restrict__ norm,
+                                                               const float* __restrict__ X, int64_t n,
+                                                               float* __restrict__ Y) {
+  __shared__ unsigned w1[NH * MW1], w2[NH * MW2], w3[8 * MW2];
+  __shared__ float bs[2 * NH + NO], nm[36];
+  for (int i = threadIdx.x; i < NH * NF / 2; i += blockDim.x) {
+    const int r = i / (NF / 2), c = i - r * (NF / 2);
+    w1[r * MW1 + c] = pack_bf16(params[OW1 + 2 * i], params[OW1 + 2 * i + 1]);
+  }
+  for (int i = threadIdx.x; i < NH * NH / 2; i += blockDim.x) {
+    const int r = i / (NH / 2), c = i - r * (NH / 2);
+    w2[r * MW2 + c] = pack_bf16(params[OW2 + 2 * i], params[OW2 + 2 * i + 1]);
+  }
+  for (int i = threadIdx.x; i < 8 * NH / 2; i += blockDim.x) {
+    const int r = i / (NH / 2), c = i - r * (NH / 2);
+    w3[r * MW2 + c] = r < NO ? pack_bf16(params[OW3 + 2 * i], params[OW3 + 2 * i + 1]) : 0u;
+  }
+  // biases as BF16 values (the weights' precision), kept in FP32 registers
+  for (int i = threadIdx.x; i < NH; i += blockDim.x) {
+    bs[i] = __bfloat162float(__float2bfloat16_rn(params[OB1 + i]));
+    bs[NH + i] = __bfloat162float(__float2bfloat16_rn(params[OB2 + i]));
+  }
+  if (threadIdx.x < NO) bs[2 * NH + threadIdx.x] = __bfloat162float(__float2bfloat16_rn(params[OB3 + threadIdx.x]));
+  for (int i = threadIdx.x; i < 36; i += blockDim.x) nm[i] = norm[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int64_t ntile = (n + 15) / 16;
+  const int64_t warps = (int64_t)gridDim.x * (MMA_THREADS / 32);
+  for (int64_t tile = blockIdx.x * (int64_t)(MMA_THREADS / 32) + (threadIdx.x >> 5); tile < ntile; tile += warps) {
+    const int64_t s0 = tile * 16 + g, s1 = s0 + 8;      // the two samples (rows) of this thread
+    // layer-1 A tile: standardised inputs, rounded to BF16
+    auto xin = [&](int64_t s, int c) { return s < n ? (X[s * NF + c] - nm[c]) / nm[NF + c] : 0.f; };
+    unsigned a[4];
+    a[0] = pack_bf16(xin(s0, 2 * t), xin(s0, 2 * t + 1));
+    a[1] = pack_bf16(xin(s1, 2 * t), xin(s1, 2 * t + 1));
+    a[2] = pack_bf16(xin(s0, 2 * t + 8), xin(s0, 2 * t + 9));
+    a[3] = pack_bf16(xin(s1, 2 * t + 8), xin(s1, 2 * t + 9));
+    float c[8][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.f;
+      const unsigned* wr = w1 + (nt * 8 + g) * MW1;
+      mma_bf16(c[nt], a, wr[t], wr[t + 4]);
+    }
+    unsigned h[4][4];
+    act_to_a(c, bs, t, h);
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.f;
+      const unsigned* wr = w2 + (nt * 8 + g) * MW2;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) mma_bf16(c[nt], h[k], wr[k * 8 + t], wr[k * 8 + t + 4]);
+    }
+    act_to_a(c, bs + NH, t, h);
+    float y[4] = {0.f, 0.f, 0.f, 0.f};
+    const unsigned* wr = w3 + g * MW2;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) mma_bf16(y, h[k], wr[k * 8 + t], wr[k * 8 + t + 4]);
+    // columns 0 and 1 of the output tile sit in lanes with t = 0
+    if (t == 0) {
+      const float b0 = bs[2 * NH], b1 = bs[2 * NH + 1];
+      if (s0 < n) {
+        Y[s0 * NO] = (y[0] + b0) * nm[2 * NF + 2] + nm[2 * NF];
+        Y[s0 * NO + 1] = (y[1] + b1) * nm[2 * NF + 3] + nm[2 * NF + 1];
+      }
+      if (s1 < n) {
+        Y[s1 * NO] = (y[2] + b0) * nm[2 * NF + 2] + nm[2 * NF];
+        Y[s1 * NO + 1] = (y[3] + b1) * nm[2 * NF + 3] + nm[2 * NF + 1];
+      }
+    }
   }
 }
 
@@ -414,8 +533,12 @@ int features_launch(int dim, const double* coords, const double* kappa, int N, i
 int mlp_infer_launch(const float* params, const float* norm, const float* X, int64_t n, int bf16, float* Y,
                      cudaStream_t s) {
   if (n <= 0) return PMG_OK;
-  if (bf16) k_mlp_infer<true><<<grid_for((size_t)n, 128), 128, 0, s>>>(params, norm, X, n, Y);
-  else k_mlp_infer<false><<<grid_for((size_t)n, 128), 128, 0, s>>>(params, norm, X, n, Y);
+  if (bf16) {
+    const size_t tiles = ((size_t)n + 15) / 16;
+    k_mlp_infer_mma<<<grid_for(tiles, MMA_THREADS / 32), MMA_THREADS, 0, s>>>(params, norm, X, n, Y);
+  } else {
+    k_mlp_infer<<<grid_for((size_t)n, 128), 128, 0, s>>>(params, norm, X, n, Y);
+  }
   return cudaPeekAtLastError() == cudaSuccess ? PMG_OK : PMG_ERR_CUDA;
 }
 

@@ -64,3 +64,25 @@ def test_features_invariant_under_rigid_motion_and_scaling():
     assert np.allclose(mlp.patch_features(m2, (1, 2, 1), 3, 1), f, atol=1e-12)
     m3 = fem.StructuredMesh(3, 3, m.coords, 10.0 * m.kappa)        # kappa enters through ratios only
     assert np.allclose(mlp.patch_features(m3, (1, 2, 1), 3, 1), f, atol=1e-12)
+
+
+def test_rounded_forward_reduces_to_forward_and_rounds_what_it_says():
+    """forward_rounded with the identity is forward; with BF16 rounding every
+    stored quantity (weights, biases, inputs, hidden activations) is a BF16
+    number, checked by recomputing it step by step."""
+    from oracle import fem
+    rng = np.random.default_rng(3)
+    theta = mlp.init_params(4)
+    theta[mlp.NF * mlp.H:mlp.NF * mlp.H + mlp.H] = rng.uniform(-0.2, 0.2, mlp.H)
+    X = rng.standard_normal((40, mlp.NF))
+    y, _ = mlp.forward(theta, X)
+    assert np.array_equal(mlp.forward_rounded(theta, X, lambda a: np.asarray(a, dtype=float)), y)
+    r = fem.bf16_round
+    W1, b1, W2, b2, W3, b3 = (r(a) for a in mlp.unpack(theta))
+    h1 = r(np.maximum(r(X) @ W1.T + b1, 0.0))
+    for a in (W1, b1, W2, b2, W3, b3, h1):
+        assert np.array_equal(r(a), a)
+    h2 = r(np.maximum(h1 @ W2.T + b2, 0.0))
+    assert np.array_equal(mlp.forward_rounded(theta, X, r), h2 @ W3.T + b3)
+    d = np.abs(mlp.forward_rounded(theta, X, r) - y).max() / np.abs(y).max()
+    assert 1e-4 < d < 5e-2
