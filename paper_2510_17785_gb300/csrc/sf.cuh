@@ -25,6 +25,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "tables.cuh"
 
 namespace pmg {
@@ -81,23 +83,36 @@ template <typename GF>
 struct GeomPackable<GF, decltype((void)GF::kPackable)> {
   static constexpr bool value = GF::kPackable;
 };
-// the NCOMP components of G at point p of a cell (component stride NGC)
-template <int NCOMP, int NGC, typename GF, typename T>
-__device__ __forceinline__ void gtensor(const GF& gcell, const T* p, T (&g)[NCOMP]) {
+// the NCOMP components of G at point p of a cell (component stride NGC),
+// from packed BF16 pairs (PACKED) or from values of type T
+template <bool PACKED, int NCOMP, int NGC, typename GF, typename T>
+__device__ __forceinline__ void gtensor(const T* p, T (&g)[NCOMP]) {
+  if constexpr (PACKED) {
+    static_assert(sizeof(T) == 4, "packed BF16 geometry feeds FP32 kernels");
+    const unsigned* w = reinterpret_cast<const unsigned*>(p);
+#pragma unroll
+    for (int j = 0; j < (NCOMP + 1) / 2; ++j) {
+      const unsigned x = __ldg(w + j * NGC);
+      g[2 * j] = __uint_as_float(x << 16);                   // BF16 -> FP32 is exact
+      if (2 * j + 1 < NCOMP) g[2 * j + 1] = __uint_as_float(x & 0xffff0000u);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < NCOMP; ++k) g[k] = gload<GF>(p + k * NGC);
+  }
+}
+// f(std::true_type) when gcell serves packed BF16 pairs, else
+// f(std::false_type): the geometry format is decided once per stage, so
+// each stage body is compiled for one format (no per-point selection)
+template <typename T, typename GF, typename F>
+__device__ __forceinline__ void with_geom_format(const GF& gcell, F&& f) {
   if constexpr (sizeof(T) == 4 && GeomPackable<GF>::value) {
     if (gcell.packed) {
-      const unsigned* w = reinterpret_cast<const unsigned*>(p);
-#pragma unroll
-      for (int j = 0; j < (NCOMP + 1) / 2; ++j) {
-        const unsigned x = __ldg(w + j * NGC);
-        g[2 * j] = __uint_as_float(x << 16);                 // BF16 -> FP32 is exact
-        if (2 * j + 1 < NCOMP) g[2 * j + 1] = __uint_as_float(x & 0xffff0000u);
-      }
+      f(std::true_type{});
       return;
     }
   }
-#pragma unroll
-  for (int k = 0; k < NCOMP; ++k) g[k] = gload<GF>(p + k * NGC);
+  f(std::false_type{});
 }
 
 template <typename T>
@@ -527,28 +542,31 @@ struct SF {
     }
     constexpr int CSTRIDE = ipow(NC, DIM - 1);   // cell-slot step along the last axis
     constexpr int GSTRIDE = ipow(n, DIM - 1);    // local point step along the last axis
+    with_geom_format<T>(gcell, [&](auto packed) {
+      constexpr bool PK = decltype(packed)::value;
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const T* Gc = gcell(pp, cslot0 + c * CSTRIDE) + lg0;
+      for (int c = 0; c < NC; ++c) {
+        const T* Gc = gcell(pp, cslot0 + c * CSTRIDE) + lg0;
 #pragma unroll
-      for (int g = 0; g < n; ++g) {
-        const int pt = loff(c * n + g) + b;
-        T Gv[D::NCOMP];
-        gtensor<D::NCOMP, NGC>(gcell, Gc + g * GSTRIDE, Gv);
-        if (DIM == 3) {
-          const T G00 = Gv[0], G01 = Gv[1], G02 = Gv[2], G11 = Gv[3], G12 = Gv[4], G22 = Gv[5];
-          const T g0 = F[pt], g1 = F[NQS + pt], g2 = gz[c * n + g];
-          F[pt] = G00 * g0 + G01 * g1 + G02 * g2;
-          F[NQS + pt] = G01 * g0 + G11 * g1 + G12 * g2;
-          fz[c * n + g] = G02 * g0 + G12 * g1 + G22 * g2;
-        } else {
-          const T G00 = Gv[0], G01 = Gv[1], G11 = Gv[2];
-          const T g0 = F[pt], g1 = gz[c * n + g];
-          F[pt] = G00 * g0 + G01 * g1;
-          fz[c * n + g] = G01 * g0 + G11 * g1;
+        for (int g = 0; g < n; ++g) {
+          const int pt = loff(c * n + g) + b;
+          T Gv[D::NCOMP];
+          gtensor<PK, D::NCOMP, NGC, GF>(Gc + g * GSTRIDE, Gv);
+          if (DIM == 3) {
+            const T G00 = Gv[0], G01 = Gv[1], G02 = Gv[2], G11 = Gv[3], G12 = Gv[4], G22 = Gv[5];
+            const T g0 = F[pt], g1 = F[NQS + pt], g2 = gz[c * n + g];
+            F[pt] = G00 * g0 + G01 * g1 + G02 * g2;
+            F[NQS + pt] = G01 * g0 + G11 * g1 + G12 * g2;
+            fz[c * n + g] = G02 * g0 + G12 * g1 + G22 * g2;
+          } else {
+            const T G00 = Gv[0], G01 = Gv[1], G11 = Gv[2];
+            const T g0 = F[pt], g1 = gz[c * n + g];
+            F[pt] = G00 * g0 + G01 * g1;
+            fz[c * n + g] = G01 * g0 + G11 * g1;
+          }
         }
       }
-    }
+    });
   }
 
   // transposed derivative along the last axis (fz in registers) added to the
@@ -744,6 +762,10 @@ struct SF {
   // quadrature-point products over all points of the served blocks (stage design)
   template <typename GF>
   __device__ __forceinline__ static void quad_stage(T* scr, int sscr, const GF& gcell) {
+    with_geom_format<T>(gcell, [&](auto packed) { quad_stage_as<decltype(packed)::value>(scr, sscr, gcell); });
+  }
+  template <bool PK, typename GF>
+  __device__ __forceinline__ static void quad_stage_as(T* scr, int sscr, const GF& gcell) {
     constexpr int NGC = D::NGC;
     constexpr int NCOMP = D::NCOMP;
     constexpr int TOT = TM::SPAN * NQ;
@@ -781,7 +803,7 @@ struct SF {
         off[u] = pp * sscr + NQS + (SKEW ? rowa(pt / QP) + pt % QP : pt);
 #pragma unroll
         for (int d = 0; d < DIM; ++d) g[u][d] = scr[off[u] + d * NQS];
-        gtensor<NCOMP, NGC>(gcell, Gp, G[u]);
+        gtensor<PK, NCOMP, NGC, GF>(Gp, G[u]);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
