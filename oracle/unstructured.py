@@ -33,7 +33,7 @@ p-levels, transfers, smoothers and the V-cycle are those of patch.py
 (Section 3.1, Algorithm 2); the p-prolongation entry (k, i) is coarse basis
 function i at fine node k, evaluated in a patch cell containing node k.
 
-Colours (reading C-A9 of the build's survey: the paper does not colour): two
+Colours (the paper does not colour; this greedy rule is a reading): two
 patches conflict when they share a cell; vertices are visited in decreasing
 priority (splitmix64(vertex id XOR seed), vertex id) and each takes the
 smallest colour no conflicting, already coloured patch has.  Within a colour
