@@ -31,7 +31,7 @@ FP64_PEAK_NOMINAL = 1.25e12                      # GB300 FP64 rate (nominal)
 # DRAM bytes (read + write) of one finest-level colour launch of the benchmark workload from an ncu capture of
 # the current kernel (variant 10, colour 0: 3,375 patches), scaled to the sweep's average launch (29,791 / 8
 # patches); valid for that variant only.  None: the kernel changed after its last full capture
-# (profiles/k_patch_q4_f32_sweep.md: 111.6 MB read + 6.7 MB written, 130.5 MB per average launch, measured
+# (the degree-4 FP32 sweep capture under profiles/: 111.6 MB read + 6.7 MB written, 130.5 MB per average launch, measured
 # before the geometry loads were split by format), so no DRAM count of the kernel as built is on record.
 PATCH_LAUNCH_TRAFFIC = {"variant": 10, "bytes": None}
 METRIC = "patch-smoother DoFs/s and CG time-to-1e-8 residual: mixed/learned vs plain FP64, 1 GB300"
@@ -736,7 +736,7 @@ def run_ours(args):
             "traffic": (PATCH_LAUNCH_TRAFFIC["bytes"] if w.name == "c2_3d_q4_n32_perturbed"
                         and head["tuning"][0] == PATCH_LAUNCH_TRAFFIC["variant"] else None),
             "traffic_note": ("DRAM bytes per colour launch of the finest-level sweep; null: the kernel changed after "
-                             "its last full ncu capture (profiles/k_patch_q4_f32_sweep.md: 118.3 MB per colour-0 "
+                             "its last full ncu capture (degree-4 FP32 sweep under profiles/: 118.3 MB per colour-0 "
                              "launch, 130.5 MB per average launch, the algorithmic bytes)"),
             "kernel": "k_patch<3,4,float,SWEEP,variant> (finest-level patch sweep, 8 colour launches)",
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
