@@ -30,9 +30,10 @@ FP32_PEAK_DERIVED = 152 * 128 * 2 * 2.070e9      # SMs x FP32 lanes x 2 flops x 
 FP64_PEAK_NOMINAL = 1.25e12                      # GB300 FP64 rate (nominal)
 # DRAM bytes (read + write) of one finest-level colour launch of the benchmark workload from an ncu capture of
 # the current kernel (variant 10, colour 0: 3,375 patches), scaled to the sweep's average launch (29,791 / 8
-# patches); valid for that variant only.  None: the kernel changed after its last full capture
-# (the degree-4 FP32 sweep capture under profiles/: 111.6 MB read + 6.7 MB written, 130.5 MB per average launch, measured
-# before the geometry loads were split by format), so no DRAM count of the kernel as built is on record.
+# patches); valid for that variant only.  None: the kernel changed after its last full capture (the
+# degree-4 FP32 sweep capture under profiles/: 111.6 MB read + 6.7 MB written, 130.5 MB per average
+# launch, measured before the geometry loads were split by format), so no DRAM count of the kernel as
+# built is on record.
 PATCH_LAUNCH_TRAFFIC = {"variant": 10, "bytes": None}
 METRIC = "patch-smoother DoFs/s and CG time-to-1e-8 residual: mixed/learned vs plain FP64, 1 GB300"
 
